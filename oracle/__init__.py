@@ -1,0 +1,370 @@
+"""Plain FP64 CPU oracle for mask-decoupled ADMM deconvolution (TV-MD, FA-MD).
+
+TEST INFRASTRUCTURE ONLY. Nothing in the product path may import this
+package; only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline
+leg of ``bench.py`` use it. It shares no code with the CUDA path.
+
+It follows M. S. C. Almeida and M. A. T. Figueiredo, "Deconvolving Images with
+Unknown Boundaries Using the Alternating Direction Method of Multipliers":
+
+* observation model  y = M A x + n                     (Sec. IV-A, eq. model_unknown_BC)
+* ADMM-2 (Algorithm 2) with the mask-decoupled g1 of eq. g_1_uBC, whose prox is
+  eq. prox_g_1_uBC
+* TV-MD  = Algorithm 3 (ADMM-TV) with line 7 replaced by eq. new_line (Sec. IV-D)
+* FA-MD  = Algorithm 2 with H1 = A, H2 = P, x-step eqs. invAnalysis/invAnalysisp1
+  and the soft threshold of eq. soft (Sec. IV-C)
+
+Conventions (readings of points the paper leaves open; each is listed with
+its justification in the design notes):
+
+* DFT: unnormalised forward, 1/n inverse (numpy.fft); U of eq. DFT_fact is the
+  unitary version, the diagonal ratios of eq. fast_inversion are unchanged.
+* A is periodic convolution on the full domain with the kernel centred at
+  (0, 0):  (A x)[r,c] = sum_{a,b} h[a+l_r, b+l_c] x[(r-a) mod H, (c-b) mod W].
+* D^h, D^v are forward periodic differences:
+  (D^h x)[r,c] = x[r,(c+1) mod W] - x[r,c],  (D^v x)[r,c] = x[(r+1) mod H,c] - x[r,c].
+* P is the 4-level undecimated (a-trous) 2-D Haar frame with periodic wrap;
+  level j filters with h = [1/2, 1/2] and g = [1/2, -1/2] at taps {0, 2^j}
+  along each axis. Each level emits three detail bands and passes the
+  low-low band on; the last low-low band is kept: 3 L + 1 bands. P^T P = I.
+* vector-soft maps 0 to 0 (Sec. III-C); soft(v, t) = sign(v) max(|v| - t, 0).
+
+Every function below is written to be checked by eye against the equation
+it cites, not for speed.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+__all__ = [
+    "psf_otf", "A_fft", "At_fft", "A_direct", "At_direct",
+    "Dh", "Dv", "DhT", "DvT", "tv_denominator_diag",
+    "haar_analysis", "haar_synthesis", "haar_nbands",
+    "soft", "vsoft", "mask_prox",
+    "objective_tv", "objective_haar",
+    "State", "tvmd_step", "famd_step", "solve",
+    "isnr", "snr",
+]
+
+
+# --------------------------------------------------------------------------
+# circulant operators (Sec. III-C, eq. DFT_fact: A = U* Lambda U)
+# --------------------------------------------------------------------------
+def _centred_kernel(psf: np.ndarray, H: int, W: int) -> np.ndarray:
+    """The blur kernel laid out on the H x W torus with its centre at (0,0)."""
+    ph, pw = psf.shape
+    lr, lc = ph // 2, pw // 2
+    k = np.zeros((H, W))
+    for a in range(-lr, lr + 1):
+        for b in range(-lc, lc + 1):
+            k[a % H, b % W] += psf[a + lr, b + lc]
+    return k
+
+
+def psf_otf(psf: np.ndarray, H: int, W: int) -> np.ndarray:
+    """Lambda: the DFT of the convolution kernel (diagonal of eq. DFT_fact)."""
+    return np.fft.fft2(_centred_kernel(psf, H, W))
+
+
+def A_fft(x: np.ndarray, psf: np.ndarray) -> np.ndarray:
+    """A x = U* Lambda U x (eq. DFT_fact)."""
+    H, W = x.shape
+    return np.real(np.fft.ifft2(psf_otf(psf, H, W) * np.fft.fft2(x)))
+
+
+def At_fft(x: np.ndarray, psf: np.ndarray) -> np.ndarray:
+    """A^T x = U* conj(Lambda) U x."""
+    H, W = x.shape
+    return np.real(np.fft.ifft2(np.conj(psf_otf(psf, H, W)) * np.fft.fft2(x)))
+
+
+def A_direct(x: np.ndarray, psf: np.ndarray) -> np.ndarray:
+    """Periodic convolution by its definition, one kernel tap at a time."""
+    ph, pw = psf.shape
+    lr, lc = ph // 2, pw // 2
+    out = np.zeros_like(x, dtype=np.float64)
+    for a in range(-lr, lr + 1):
+        for b in range(-lc, lc + 1):
+            # x[(r-a) mod H, (c-b) mod W] is np.roll(x, (a, b))
+            out += psf[a + lr, b + lc] * np.roll(x, (a, b), axis=(0, 1))
+    return out
+
+
+def At_direct(x: np.ndarray, psf: np.ndarray) -> np.ndarray:
+    """Adjoint of A_direct: periodic correlation with the same taps."""
+    ph, pw = psf.shape
+    lr, lc = ph // 2, pw // 2
+    out = np.zeros_like(x, dtype=np.float64)
+    for a in range(-lr, lr + 1):
+        for b in range(-lc, lc + 1):
+            out += psf[a + lr, b + lc] * np.roll(x, (-a, -b), axis=(0, 1))
+    return out
+
+
+# --------------------------------------------------------------------------
+# TV differences (Sec. III-C: D_i = horizontal and vertical differences,
+# periodic BC)
+# --------------------------------------------------------------------------
+def Dh(x):
+    return np.roll(x, -1, axis=1) - x
+
+
+def Dv(x):
+    return np.roll(x, -1, axis=0) - x
+
+
+def DhT(p):
+    return np.roll(p, 1, axis=1) - p
+
+
+def DvT(p):
+    return np.roll(p, 1, axis=0) - p
+
+
+def tv_denominator_diag(psf, H, W, mu1, mu2):
+    """Diagonal of eq. fast_inversion: mu1|Lambda|^2 + mu2|Delta^h|^2 + mu2|Delta^v|^2,
+    with Delta^h, Delta^v the DFTs of the difference kernels."""
+    lam = psf_otf(psf, H, W)
+    eh = np.zeros((H, W)); eh[0, 0] = -1.0; eh[0, (-1) % W] += 1.0   # D^h x = e_h (*) x
+    ev = np.zeros((H, W)); ev[0, 0] = -1.0; ev[(-1) % H, 0] += 1.0
+    dh = np.fft.fft2(eh)
+    dv = np.fft.fft2(ev)
+    return mu1 * np.abs(lam) ** 2 + mu2 * np.abs(dh) ** 2 + mu2 * np.abs(dv) ** 2
+
+
+# --------------------------------------------------------------------------
+# undecimated Haar Parseval frame (Sec. V: redundant Haar frame, 4 levels;
+# Sec. III-B requires P^T P = I)
+# --------------------------------------------------------------------------
+def haar_nbands(levels: int) -> int:
+    return 3 * levels + 1
+
+
+def _lo(v, s, axis):
+    return 0.5 * (v + np.roll(v, -s, axis=axis))
+
+
+def _hi(v, s, axis):
+    return 0.5 * (v - np.roll(v, -s, axis=axis))
+
+
+def _loT(v, s, axis):
+    return 0.5 * (v + np.roll(v, s, axis=axis))
+
+
+def _hiT(v, s, axis):
+    return 0.5 * (v - np.roll(v, s, axis=axis))
+
+
+def haar_analysis(x: np.ndarray, levels: int = 4) -> np.ndarray:
+    """P x as an array (3 L + 1, H, W). Band order for level j: [rows low /
+    columns high, rows high / columns low, rows high / columns high]; the
+    final band is the low-low approximation. 'columns high' means the
+    high-pass acts along the column index (axis 1)."""
+    bands = []
+    a = np.asarray(x, dtype=np.float64)
+    for j in range(levels):
+        s = 1 << j
+        lo_c = _lo(a, s, 1)
+        hi_c = _hi(a, s, 1)
+        bands.append(_lo(hi_c, s, 0))
+        bands.append(_hi(lo_c, s, 0))
+        bands.append(_hi(hi_c, s, 0))
+        a = _lo(lo_c, s, 0)
+    bands.append(a)
+    return np.stack(bands)
+
+
+def haar_synthesis(c: np.ndarray, levels: int = 4) -> np.ndarray:
+    """P^T c, the adjoint of haar_analysis."""
+    a = c[3 * levels].copy()
+    for j in reversed(range(levels)):
+        s = 1 << j
+        b0, b1, b2 = c[3 * j], c[3 * j + 1], c[3 * j + 2]
+        lo_c = _loT(a, s, 0) + _hiT(b1, s, 0)
+        hi_c = _loT(b0, s, 0) + _hiT(b2, s, 0)
+        a = _loT(lo_c, s, 1) + _hiT(hi_c, s, 1)
+    return a
+
+
+# --------------------------------------------------------------------------
+# proximity operators
+# --------------------------------------------------------------------------
+def soft(v, tau):
+    """eq. soft: sign(v) * max(|v| - tau, 0), componentwise."""
+    return np.sign(v) * np.maximum(np.abs(v) - tau, 0.0)
+
+
+def vsoft(vh, vv, tau):
+    """vector-soft of Sec. III-C applied per pixel to (vh, vv), with 0/0 = 0:
+    v / ||v|| * max(||v|| - tau, 0)."""
+    nrm = np.sqrt(vh * vh + vv * vv)
+    scale = np.where(nrm > tau, (nrm - tau) / np.where(nrm > 0, nrm, 1.0), 0.0)
+    return scale * vh, scale * vv
+
+
+def mask_prox(v, ybar, mask, mu1):
+    """eq. prox_g_1_uBC: (M^T M + mu1 I)^{-1} (M^T y + mu1 v); M^T M = diag(mask),
+    M^T y = ybar (observations zero-extended to the full domain)."""
+    m = mask.astype(np.float64)
+    return (m * ybar + mu1 * v) / (m + mu1)
+
+
+# --------------------------------------------------------------------------
+# objectives (eq. unconstrained_TV_uBC and eq. unconstrained_analysis_uBC)
+# --------------------------------------------------------------------------
+def objective_tv(x, ybar, mask, psf, lam):
+    m = mask.astype(np.float64)
+    r = m * (ybar - A_fft(x, psf))
+    return 0.5 * float(np.sum(r * r)) + lam * float(np.sum(np.sqrt(Dh(x) ** 2 + Dv(x) ** 2)))
+
+
+def objective_haar(x, ybar, mask, psf, lam, levels=4):
+    m = mask.astype(np.float64)
+    r = m * (ybar - A_fft(x, psf))
+    return 0.5 * float(np.sum(r * r)) + lam * float(np.sum(np.abs(haar_analysis(x, levels))))
+
+
+# --------------------------------------------------------------------------
+# ADMM iterations
+# --------------------------------------------------------------------------
+@dataclass
+class State:
+    """ADMM split and dual variables. TV: u2/d2 have shape (2, H, W) holding
+    the (horizontal, vertical) components; Haar: (3 L + 1, H, W)."""
+    u1: np.ndarray
+    d1: np.ndarray
+    u2: np.ndarray
+    d2: np.ndarray
+    x: np.ndarray
+    k: int = 0
+
+    @staticmethod
+    def zeros(H, W, reg="tv", levels=4):
+        nb = 2 if reg == "tv" else haar_nbands(levels)
+        z = np.zeros((H, W))
+        return State(z.copy(), z.copy(), np.zeros((nb, H, W)), np.zeros((nb, H, W)), z.copy(), 0)
+
+    def copy(self):
+        return State(self.u1.copy(), self.d1.copy(), self.u2.copy(), self.d2.copy(),
+                     self.x.copy(), self.k)
+
+
+def tvmd_step(st: State, ybar, mask, psf, lam, mu1, mu2, otf=None, denom=None) -> State:
+    """One iteration of TV-MD: Algorithm 3 with line 7 replaced by eq. new_line."""
+    H, W = ybar.shape
+    if otf is None:
+        otf = psf_otf(psf, H, W)
+    if denom is None:
+        denom = tv_denominator_diag(psf, H, W, mu1, mu2)
+    # Alg. 3, lines 3-5: zeta = u_k + d_k, split into zeta1 and (delta_h, delta_v)
+    zeta1 = st.u1 + st.d1
+    delta_h = st.u2[0] + st.d2[0]
+    delta_v = st.u2[1] + st.d2[1]
+    # line 6: z = K (mu1 A^T zeta1 + mu2 Dh^T delta_h + mu2 Dv^T delta_v), K of eq. fast_inversion
+    rhs = mu1 * np.real(np.fft.ifft2(np.conj(otf) * np.fft.fft2(zeta1))) \
+        + mu2 * DhT(delta_h) + mu2 * DvT(delta_v)
+    x = np.real(np.fft.ifft2(np.fft.fft2(rhs) / denom))
+    # line 7 -> eq. new_line: u1 = (M^T M + mu1 I)^{-1} (M^T y + mu1 (A z - d1))
+    ax = np.real(np.fft.ifft2(otf * np.fft.fft2(x)))
+    u1 = mask_prox(ax - st.d1, ybar, mask, mu1)
+    # line 8: d1 = d1 - (A z - u1)
+    d1 = st.d1 - (ax - u1)
+    # lines 9-11: per pixel vector-soft and dual update
+    gh, gv = Dh(x), Dv(x)
+    uh, uv = vsoft(gh - st.d2[0], gv - st.d2[1], lam / mu2)
+    d2 = np.stack([st.d2[0] - (gh - uh), st.d2[1] - (gv - uv)])
+    return State(u1, d1, np.stack([uh, uv]), d2, x, st.k + 1)
+
+
+def famd_step(st: State, ybar, mask, psf, lam, mu1, mu2, levels=4, otf=None) -> State:
+    """One iteration of FA-MD: Algorithm 2 with H1 = A, H2 = P, line 4 from
+    eqs. invAnalysis/invAnalysisp1 and line 6 from eqs. prox_g_1_uBC and prox_g_2."""
+    H, W = ybar.shape
+    if otf is None:
+        otf = psf_otf(psf, H, W)
+    gam = mu2 / mu1
+    # line 3
+    zeta1 = st.u1 + st.d1
+    zeta2 = st.u2 + st.d2
+    # line 4 with P^T P = I: z = U* (|Lambda|^2 + gamma)^{-1} U (A^T zeta1 + gamma P^T zeta2)
+    rhs = np.real(np.fft.ifft2(np.conj(otf) * np.fft.fft2(zeta1))) + gam * haar_synthesis(zeta2, levels)
+    x = np.real(np.fft.ifft2(np.fft.fft2(rhs) / (np.abs(otf) ** 2 + gam)))
+    # lines 6-7, j = 1: mask-decoupled prox and dual update
+    ax = np.real(np.fft.ifft2(otf * np.fft.fft2(x)))
+    u1 = mask_prox(ax - st.d1, ybar, mask, mu1)
+    d1 = st.d1 - (ax - u1)
+    # lines 6-7, j = 2: soft threshold of the frame coefficients
+    c = haar_analysis(x, levels)
+    u2 = soft(c - st.d2, lam / mu2)
+    d2 = st.d2 - (c - u2)
+    return State(u1, d1, u2, d2, x, st.k + 1)
+
+
+@dataclass
+class SolveResult:
+    x: np.ndarray
+    state: State
+    iters: int
+    converged: bool
+    objective: float
+    rel_x: float
+    rel_obj: float
+    history: list = field(default_factory=list)
+
+
+def solve(ybar, mask, psf, lam, mu1, mu2, reg="tv", iters=200, stop="iters", tol=0.0,
+          levels=4, state0: State | None = None, record=False) -> SolveResult:
+    """Run TV-MD or FA-MD from ``state0`` (default: u0 = d0 = 0) until ``iters``
+    iterations or, for stop = 'rel_x' / 'rel_obj', until the relative change of
+    x / of the objective between consecutive iterations is below ``tol``."""
+    H, W = ybar.shape
+    st = state0.copy() if state0 is not None else State.zeros(H, W, reg, levels)
+    otf = psf_otf(psf, H, W)
+    denom = tv_denominator_diag(psf, H, W, mu1, mu2) if reg == "tv" else None
+    obj_fn = (lambda x: objective_tv(x, ybar, mask, psf, lam)) if reg == "tv" else \
+             (lambda x: objective_haar(x, ybar, mask, psf, lam, levels))
+    hist = []
+    f_prev = None
+    rel_x = rel_obj = float("inf")
+    converged = False
+    n = 0
+    for n in range(1, iters + 1):
+        x_prev = st.x
+        if reg == "tv":
+            st = tvmd_step(st, ybar, mask, psf, lam, mu1, mu2, otf, denom)
+        else:
+            st = famd_step(st, ybar, mask, psf, lam, mu1, mu2, levels, otf)
+        nx = float(np.linalg.norm(st.x))
+        rel_x = float(np.linalg.norm(st.x - x_prev)) / nx if nx > 0 else float("inf")
+        f = obj_fn(st.x) if (stop == "rel_obj" or record) else float("nan")
+        if f_prev is not None and f == f:
+            rel_obj = abs(f - f_prev) / abs(f) if f != 0 else float("inf")
+        f_prev = f
+        if record:
+            hist.append((n, f, rel_x))
+        if stop == "rel_x" and rel_x < tol:
+            converged = True
+            break
+        if stop == "rel_obj" and n > 1 and rel_obj < tol:
+            converged = True
+            break
+    return SolveResult(st.x, st, n, converged, obj_fn(st.x), rel_x, rel_obj, hist)
+
+
+# --------------------------------------------------------------------------
+# figures of merit (Sec. V uses ISNR and SNR without defining them)
+# --------------------------------------------------------------------------
+def isnr(x_true, ybar, x_hat, region):
+    """10 log10(||x - ybar||^2 / ||x - x_hat||^2) over the boolean region."""
+    r = region.astype(bool)
+    num = np.sum((x_true[r] - ybar[r]) ** 2)
+    den = np.sum((x_true[r] - x_hat[r]) ** 2)
+    return 10.0 * math.log10(num / den)
+
+
+def snr(x_true, x_hat):
+    return 10.0 * math.log10(np.sum(x_true ** 2) / np.sum((x_true - x_hat) ** 2))

@@ -1,0 +1,433 @@
+"""Pins for the FP64 oracle: each check compares it with something other than
+itself -- a definition written out as loops, a closed form, an invariant, a
+dense linear-algebra solve, an independent convex solver, or a value printed
+in the paper. A dropped term, wrong sign, wrong index or transposed operand in
+any oracle function fails at least one of these."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+import synth as S
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _rand_psf(g, ph, pw):
+    k = g.uniform(0.0, 1.0, size=(ph, pw))
+    k[0, -1] += 2.0          # make it clearly asymmetric
+    return k / k.sum()
+
+
+# ----------------------------------------------------------------------------
+# A, A^T, M
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("H,W,ph,pw", [(5, 7, 3, 3), (8, 8, 5, 3), (16, 12, 7, 5), (9, 16, 9, 9)])
+def test_convolution_matches_definition_loops(H, W, ph, pw):
+    """Periodic convolution (Sec. IV-A: A with periodic BC on the full domain)
+    written as explicit index loops equals the FFT-diagonalised A of eq.
+    DFT_fact and the tap-sum A_direct; the adjoint equals the correlation."""
+    g = S.rng(1)
+    x = g.standard_normal((H, W))
+    h = _rand_psf(g, ph, pw)
+    lr, lc = ph // 2, pw // 2
+    ref = np.zeros((H, W))
+    reft = np.zeros((H, W))
+    for r in range(H):
+        for c in range(W):
+            s = st = 0.0
+            for a in range(-lr, lr + 1):
+                for b in range(-lc, lc + 1):
+                    s += h[a + lr, b + lc] * x[(r - a) % H, (c - b) % W]
+                    st += h[a + lr, b + lc] * x[(r + a) % H, (c + b) % W]
+            ref[r, c] = s
+            reft[r, c] = st
+    np.testing.assert_allclose(O.A_fft(x, h), ref, rtol=0, atol=1e-13)
+    np.testing.assert_allclose(O.A_direct(x, h), ref, rtol=0, atol=1e-13)
+    np.testing.assert_allclose(O.At_fft(x, h), reft, rtol=0, atol=1e-13)
+    np.testing.assert_allclose(O.At_direct(x, h), reft, rtol=0, atol=1e-13)
+
+
+def test_adjoint_identities():
+    """<Ax, y> = <x, A^T y>, and the same for D^h, D^v and the Haar frame."""
+    g = S.rng(2)
+    H, W = 16, 24
+    x = g.standard_normal((H, W))
+    y = g.standard_normal((H, W))
+    h = _rand_psf(g, 7, 5)
+    for fwd, adj in ((lambda v: O.A_fft(v, h), lambda v: O.At_fft(v, h)),
+                     (O.Dh, O.DhT), (O.Dv, O.DvT)):
+        lhs = np.vdot(fwd(x), y)
+        rhs = np.vdot(x, adj(y))
+        assert abs(lhs - rhs) <= 1e-13 * max(1.0, abs(lhs))
+    c = g.standard_normal((13, H, W))
+    lhs = np.vdot(O.haar_analysis(x, 4), c)
+    rhs = np.vdot(x, O.haar_synthesis(c, 4))
+    assert abs(lhs - rhs) <= 1e-12 * max(1.0, abs(lhs))
+
+
+def test_periodic_model_equals_valid_convolution():
+    """Sec. IV-A: on the valid region the periodic A x equals the
+    non-periodic blur used to form observations (so the BC is irrelevant)."""
+    g = S.rng(3)
+    x = g.uniform(size=(40, 33))
+    h = S.psf_motion(9.0, 30.0, 9)
+    vm = S.valid_mask(40, 33, 9, 9).astype(bool)
+    np.testing.assert_allclose(O.A_fft(x, h)[vm], S.conv_valid(x, h)[vm], rtol=0, atol=1e-13)
+
+
+def test_paper_valid_region_sizes():
+    """Sec. V: 256 x 256 image with 19 x 19 blurs gives a 238 x 238 observed
+    region, m = 56644 and 8892 unknown boundary pixels."""
+    with open(os.path.join(GOLDEN, "paper_sizes.json")) as f:
+        gold = json.load(f)
+    m = S.valid_mask(gold["H"], gold["W"], gold["psf_side"], gold["psf_side"])
+    assert int(m.sum()) == gold["m"] == gold["observed_side"] ** 2
+    assert m.size - int(m.sum()) == gold["unknown_boundary_pixels"]
+    assert m.size == gold["n"]
+    assert gold["psf_side"] == 2 * gold["l"] + 1
+    # m = (sqrt(n) - 2 l)^2 (Sec. IV-A)
+    assert (int(math.isqrt(gold["n"])) - 2 * gold["l"]) ** 2 == gold["m"]
+
+
+def test_lowpass_dc_gain():
+    """Sec. III-C, after the ADMM-TV convergence proposition: A 1 = beta 1
+    with beta the DC gain of the filter."""
+    g = S.rng(4)
+    h = _rand_psf(g, 9, 9) * 0.7
+    one = np.ones((20, 20))
+    np.testing.assert_allclose(O.A_fft(one, h), 0.7 * one, atol=1e-14)
+    np.testing.assert_allclose(abs(O.psf_otf(h, 20, 20)[0, 0]), 0.7, atol=1e-14)
+
+
+# ----------------------------------------------------------------------------
+# D, the TV denominator, Haar
+# ----------------------------------------------------------------------------
+def test_differences_and_spectrum_closed_form():
+    """D 1 = 0 (Sec. III-C, proof of the ADMM-TV proposition); |Delta^h|^2 =
+    4 sin^2(pi k_c / W) and |Delta^v|^2 = 4 sin^2(pi k_r / H) for forward
+    periodic differences, so the denominator of eq. fast_inversion is known
+    in closed form."""
+    one = np.ones((6, 10))
+    assert np.all(O.Dh(one) == 0) and np.all(O.Dv(one) == 0)
+    H, W = 12, 10
+    h = S.psf_box(3)
+    mu1, mu2 = 0.7, 0.3
+    kr = np.arange(H)[:, None]
+    kc = np.arange(W)[None, :]
+    lam = np.zeros((H, W), dtype=complex)
+    for a in range(-1, 2):
+        for b in range(-1, 2):
+            lam += h[a + 1, b + 1] * np.exp(-2j * np.pi * (kr * a / H + kc * b / W))
+    closed = mu1 * np.abs(lam) ** 2 + mu2 * 4 * np.sin(np.pi * kc / W) ** 2 \
+        + mu2 * 4 * np.sin(np.pi * kr / H) ** 2
+    np.testing.assert_allclose(O.tv_denominator_diag(h, H, W, mu1, mu2), closed, rtol=1e-13, atol=1e-14)
+
+
+def _dense(op, H, W):
+    n = H * W
+    cols = []
+    for i in range(n):
+        e = np.zeros(n)
+        e[i] = 1.0
+        cols.append(np.asarray(op(e.reshape(H, W))).reshape(-1))
+    return np.stack(cols, axis=1)
+
+
+@pytest.mark.parametrize("H,W", [(8, 8), (16, 16), (8, 12)])
+def test_haar_parseval_dense(H, W):
+    """Sec. III-B requires a Parseval frame, P^T P = I; 4 levels give 13 bands."""
+    assert O.haar_nbands(4) == 13
+    P = _dense(lambda v: O.haar_analysis(v, 4), H, W)
+    assert P.shape == (13 * H * W, H * W)
+    np.testing.assert_allclose(P.T @ P, np.eye(H * W), atol=1e-14)
+    # the frame is redundant: P P^T is not the identity
+    assert np.linalg.norm(P @ P.T - np.eye(13 * H * W)) > 1.0
+
+
+def test_haar_bands_closed_form():
+    """The last low-low band of the 4-level a-trous Haar is the mean of x over
+    the 16 x 16 periodic window starting at the pixel; the level-0 detail
+    bands are the 2 x 2 Haar differences. Written out as loops."""
+    g = S.rng(5)
+    H, W = 20, 18
+    x = g.standard_normal((H, W))
+    c = O.haar_analysis(x, 4)
+    ll = np.zeros((H, W))
+    b0 = np.zeros((H, W)); b1 = np.zeros((H, W)); b2 = np.zeros((H, W))
+    for r in range(H):
+        for q in range(W):
+            ll[r, q] = sum(x[(r + i) % H, (q + j) % W] for i in range(16) for j in range(16)) / 256.0
+            p00, p01 = x[r, q], x[r, (q + 1) % W]
+            p10, p11 = x[(r + 1) % H, q], x[(r + 1) % H, (q + 1) % W]
+            b0[r, q] = (p00 - p01 + p10 - p11) / 4.0     # rows low, columns high
+            b1[r, q] = (p00 + p01 - p10 - p11) / 4.0     # rows high, columns low
+            b2[r, q] = (p00 - p01 - p10 + p11) / 4.0     # rows high, columns high
+    np.testing.assert_allclose(c[12], ll, atol=1e-13)
+    np.testing.assert_allclose(c[0], b0, atol=1e-14)
+    np.testing.assert_allclose(c[1], b1, atol=1e-14)
+    np.testing.assert_allclose(c[2], b2, atol=1e-14)
+    # level-1 uses taps {0, 2}
+    r, q = 3, 4
+    p = [[x[(r + 2 * i) % H, (q + 2 * j) % W] for j in range(2)] for i in range(2)]
+    a1 = np.array([[sum(x[(r + 2 * i + ii) % H, (q + 2 * j + jj) % W] for ii in range(2) for jj in range(2)) / 4
+                    for j in range(2)] for i in range(2)])
+    del p
+    assert abs(c[5][r, q] - (a1[0, 0] - a1[0, 1] - a1[1, 0] + a1[1, 1]) / 4.0) < 1e-14
+
+
+# ----------------------------------------------------------------------------
+# proximity operators: closed forms vs brute-force minimisation
+# ----------------------------------------------------------------------------
+def test_soft_is_l1_prox():
+    """eq. soft: soft(v, t) = argmin_u t|u| + (u - v)^2 / 2, checked on a grid."""
+    grid = np.linspace(-3, 3, 600001)
+    for v in (-2.0, -0.3, 0.0, 0.2, 0.5, 1.7):
+        t = 0.4
+        u_star = grid[np.argmin(t * np.abs(grid) + 0.5 * (grid - v) ** 2)]
+        assert abs(O.soft(np.array(v), t) - u_star) < 2e-5
+
+
+def test_vsoft_is_l2_prox_with_zero_convention():
+    """vector-soft (Sec. III-C) = argmin_u t||u|| + ||u - v||^2 / 2, incl. v = 0."""
+    g1 = np.linspace(-1.5, 1.5, 1501)
+    U, V = np.meshgrid(g1, g1, indexing="ij")
+    t = 0.3
+    for vh, vv in ((0.0, 0.0), (0.1, -0.1), (0.9, 0.4), (-1.0, 0.2), (0.25, 0.15)):
+        f = t * np.sqrt(U ** 2 + V ** 2) + 0.5 * ((U - vh) ** 2 + (V - vv) ** 2)
+        i = np.unravel_index(np.argmin(f), f.shape)
+        uh, uv = O.vsoft(np.array(vh), np.array(vv), t)
+        assert abs(uh - g1[i[0]]) < 3e-3 and abs(uv - g1[i[1]]) < 3e-3
+    uh, uv = O.vsoft(np.zeros(3), np.zeros(3), 0.0)
+    assert np.all(uh == 0) and np.all(uv == 0) and not np.any(np.isnan(uh))
+
+
+def test_mask_prox_minimises():
+    """eq. prox_g_1_uBC: u = argmin ||M u - y||^2 + mu1 ||u - v||^2 (per pixel)."""
+    grid = np.linspace(-4, 4, 800001)
+    mu1 = 0.35
+    for m, y, v in ((1, 1.2, -0.4), (0, 1.2, -0.4), (1, -0.7, 2.0), (0, 0.0, 0.9)):
+        f = m * (grid - y) ** 2 + mu1 * (grid - v) ** 2
+        u_star = grid[np.argmin(f)]
+        u = O.mask_prox(np.array(v), np.array(y * m), np.array(m, dtype=np.uint8), mu1)
+        assert abs(u - u_star) < 2e-5
+
+
+# ----------------------------------------------------------------------------
+# the x-step against a dense solve (Algorithm 2 line 4, eq. quadratic_problem)
+# ----------------------------------------------------------------------------
+def _one_step_inputs(reg, H=8, W=8, seed=6):
+    g = S.rng(seed)
+    h = _rand_psf(g, 3, 5)
+    nb = 2 if reg == "tv" else 13
+    st = O.State(g.standard_normal((H, W)), g.standard_normal((H, W)),
+                 g.standard_normal((nb, H, W)), g.standard_normal((nb, H, W)),
+                 np.zeros((H, W)))
+    ybar = g.standard_normal((H, W))
+    mask = (g.uniform(size=(H, W)) > 0.3).astype(np.uint8)
+    return g, h, st, ybar, mask
+
+
+def test_tv_xstep_dense_solve():
+    """x_{k+1} = (sum mu_j H_j^T H_j)^{-1} sum mu_j H_j^T zeta_j with dense
+    A, D^h, D^v (eq. quadratic_problem) equals the oracle's Fourier solve."""
+    H = W = 8
+    g, h, st, ybar, mask = _one_step_inputs("tv")
+    mu1, mu2, lam = 0.8, 0.05, 0.01
+    A = _dense(lambda v: O.A_direct(v, h), H, W)
+    Dh = _dense(O.Dh, H, W)
+    Dv = _dense(O.Dv, H, W)
+    Mat = mu1 * A.T @ A + mu2 * (Dh.T @ Dh + Dv.T @ Dv)
+    z1 = (st.u1 + st.d1).ravel()
+    dh = (st.u2[0] + st.d2[0]).ravel()
+    dv = (st.u2[1] + st.d2[1]).ravel()
+    x_dense = np.linalg.solve(Mat, mu1 * A.T @ z1 + mu2 * (Dh.T @ dh + Dv.T @ dv))
+    nxt = O.tvmd_step(st, ybar, mask, h, lam, mu1, mu2)
+    np.testing.assert_allclose(nxt.x.ravel(), x_dense, atol=1e-12)
+    # the rest of the step, restated with dense operators
+    a = A @ x_dense
+    m = mask.ravel().astype(float)
+    u1 = (m * ybar.ravel() + mu1 * (a - st.d1.ravel())) / (m + mu1)
+    np.testing.assert_allclose(nxt.u1.ravel(), u1, atol=1e-12)
+    np.testing.assert_allclose(nxt.d1.ravel(), st.d1.ravel() - a + u1, atol=1e-12)
+    gh, gv = Dh @ x_dense, Dv @ x_dense
+    sh, sv = gh - st.d2[0].ravel(), gv - st.d2[1].ravel()
+    nrm = np.hypot(sh, sv)
+    sc = np.maximum(nrm - lam / mu2, 0) / np.where(nrm > 0, nrm, 1)
+    np.testing.assert_allclose(nxt.u2[0].ravel(), sc * sh, atol=1e-12)
+    np.testing.assert_allclose(nxt.d2[1].ravel(), st.d2[1].ravel() - gv + sc * sv, atol=1e-12)
+
+
+def test_haar_xstep_dense_solve():
+    """FA-MD x-step (eq. invAnalysis) with dense A and P; P^T P = I is not
+    assumed by the dense side."""
+    H = W = 8
+    g, h, st, ybar, mask = _one_step_inputs("haar")
+    mu1, mu2, lam = 0.6, 0.09, 0.02
+    A = _dense(lambda v: O.A_direct(v, h), H, W)
+    P = _dense(lambda v: O.haar_analysis(v, 4), H, W)
+    gam = mu2 / mu1
+    Mat = A.T @ A + gam * P.T @ P
+    x_dense = np.linalg.solve(Mat, A.T @ (st.u1 + st.d1).ravel() + gam * P.T @ (st.u2 + st.d2).ravel())
+    nxt = O.famd_step(st, ybar, mask, h, lam, mu1, mu2, 4)
+    np.testing.assert_allclose(nxt.x.ravel(), x_dense, atol=1e-12)
+    c = P @ x_dense
+    s = c - st.d2.ravel()
+    u2 = np.sign(s) * np.maximum(np.abs(s) - lam / mu2, 0)
+    np.testing.assert_allclose(nxt.u2.ravel(), u2, atol=1e-12)
+    np.testing.assert_allclose(nxt.d2.ravel(), st.d2.ravel() - c + u2, atol=1e-12)
+
+
+# ----------------------------------------------------------------------------
+# whole-iteration pins
+# ----------------------------------------------------------------------------
+def _small_problem(H=16, W=16, seed=7, side=5, keep=0.8, bsnr=40.0):
+    g = S.rng(seed)
+    x = S.shapes_image(H, W, g, 6, rmax=5.0)
+    h = S.psf_gaussian(side, 1.2)
+    keepm = (g.uniform(size=(H, W)) < keep).astype(np.uint8)
+    ybar, mask, _ = S.observe(x, h, keepm, bsnr, g)
+    return x, h, ybar, mask
+
+
+def test_tv_kkt_certificate_at_convergence():
+    """At a fixed point of TV-MD the scaled duals certify optimality of eq.
+    unconstrained_TV_uBC (from Algorithm 2 lines 4-7 with u = G z):
+    -mu1 d1 = M^T (M A x - y),  mu1 A^T d1 + mu2 D^T d2 = 0,
+    ||mu2 d2_i|| <= lambda with equality and alignment where D_i x != 0."""
+    x, h, ybar, mask = _small_problem()
+    lam, mu1, mu2 = 2e-3, 1.0, 2e-2
+    r = O.solve(ybar, mask, h, lam, mu1, mu2, "tv", iters=20000, stop="rel_x", tol=1e-13)
+    st = r.state
+    ax = O.A_fft(st.x, h)
+    m = mask.astype(float)
+    np.testing.assert_allclose(-mu1 * st.d1, m * (ax - ybar), atol=1e-9)
+    stat = mu1 * O.At_fft(st.d1, h) + mu2 * (O.DhT(st.d2[0]) + O.DvT(st.d2[1]))
+    assert np.max(np.abs(stat)) < 1e-9
+    pn = mu2 * np.hypot(st.d2[0], st.d2[1])
+    assert np.max(pn) <= lam * (1 + 1e-9)
+    gh, gv = O.Dh(st.x), O.Dv(st.x)
+    gn = np.hypot(gh, gv)
+    act = gn > 1e-6
+    assert act.sum() > 10
+    np.testing.assert_allclose(pn[act], lam, rtol=1e-6)
+    # -mu2 d2_i points along D_i x
+    np.testing.assert_allclose(-mu2 * st.d2[0][act], lam * gh[act] / gn[act], atol=1e-6 * lam + 1e-9)
+
+
+def test_haar_kkt_certificate_at_convergence():
+    """Same certificate for FA-MD (eq. unconstrained_analysis_uBC):
+    -mu1 d1 = M^T(MAx - y), mu1 A^T d1 + mu2 P^T d2 = 0, |mu2 d2| <= lambda."""
+    x, h, ybar, mask = _small_problem(seed=8)
+    lam, mu1, mu2 = 1e-2, 1.0, 1e-1
+    r = O.solve(ybar, mask, h, lam, mu1, mu2, "haar", iters=20000, stop="rel_x", tol=1e-13)
+    assert r.converged
+    st = r.state
+    ax = O.A_fft(st.x, h)
+    m = mask.astype(float)
+    np.testing.assert_allclose(-mu1 * st.d1, m * (ax - ybar), atol=1e-9)
+    stat = mu1 * O.At_fft(st.d1, h) + mu2 * O.haar_synthesis(st.d2, 4)
+    assert np.max(np.abs(stat)) < 1e-9
+    assert np.max(np.abs(mu2 * st.d2)) <= lam * (1 + 1e-9)
+    c = O.haar_analysis(st.x, 4)
+    act = np.abs(c) > 1e-7
+    np.testing.assert_allclose(-mu2 * st.d2[act], lam * np.sign(c[act]), atol=1e-6 * lam)
+
+
+def _pdhg_tv(A, Dh, Dv, m, ybar, lam, iters=200000):
+    """Chambolle-Pock primal-dual hybrid gradient on
+    min_x 1/2 sum_i m_i (A x - y)_i^2 + lam sum_i ||(Dh x, Dv x)_i||,
+    with K = [A; Dh; Dv]; written independently of the ADMM oracle."""
+    n = A.shape[1]
+    K = np.vstack([A, Dh, Dv])
+    L = np.linalg.norm(K, 2)
+    tau = sig = 0.99 / L
+    x = np.zeros(n); xb = x.copy()
+    p = np.zeros(n); q = np.zeros((2, n))
+    for _ in range(iters):
+        # dual step for F1*(p): F1(v) = 1/2 sum m (v - y)^2
+        v = p + sig * (A @ xb)
+        p = np.where(m > 0, (v - sig * ybar) / (1.0 + sig), 0.0)
+        # dual step for F2*: projection on ||q_i|| <= lam
+        w = q + sig * np.stack([Dh @ xb, Dv @ xb])
+        nrm = np.maximum(1.0, np.hypot(w[0], w[1]) / lam)
+        q = w / nrm
+        x_new = x - tau * (A.T @ p + Dh.T @ q[0] + Dv.T @ q[1])
+        xb = 2 * x_new - x
+        x = x_new
+    return x
+
+
+def test_tv_optimum_matches_independent_pdhg():
+    """8 x 8 problem: the objective reached by TV-MD equals the one reached by
+    an independent dense-matrix PDHG (Chambolle-Pock) solver."""
+    H = W = 8
+    g = S.rng(9)
+    xt = S.shapes_image(H, W, g, 3, rmax=3.0)
+    h = S.psf_gaussian(3, 0.8)
+    keep = (g.uniform(size=(H, W)) < 0.9).astype(np.uint8)
+    ybar, mask, _ = S.observe(xt, h, keep, 30.0, g)
+    lam, mu1, mu2 = 5e-3, 1.0, 5e-2
+    r = O.solve(ybar, mask, h, lam, mu1, mu2, "tv", iters=50000, stop="rel_x", tol=1e-14)
+    A = _dense(lambda v: O.A_direct(v, h), H, W)
+    Dh = _dense(O.Dh, H, W)
+    Dv = _dense(O.Dv, H, W)
+    xp = _pdhg_tv(A, Dh, Dv, mask.ravel().astype(float), ybar.ravel(), lam, iters=60000)
+    f_pd = O.objective_tv(xp.reshape(H, W), ybar, mask, h, lam)
+    assert abs(r.objective - f_pd) <= 1e-8 * abs(f_pd) + 1e-12
+
+
+def test_periodic_unregularised_closed_form():
+    """Special cases of Sec. IV-A: with M = I (periodic deconvolution) and
+    lambda = 0 the minimiser is x = U* (Y / Lambda) for an invertible blur."""
+    H, W = 16, 16
+    g = S.rng(10)
+    h = np.zeros((3, 3)); h[1, 1] = 0.8; h[1, 2] = 0.1; h[0, 1] = 0.1
+    xt = g.uniform(size=(H, W))
+    y = O.A_fft(xt, h)
+    mask = np.ones((H, W), dtype=np.uint8)
+    r = O.solve(y, mask, h, 0.0, 1.0, 0.1, "tv", iters=3000, stop="rel_x", tol=1e-15)
+    closed = np.real(np.fft.ifft2(np.fft.fft2(y) / O.psf_otf(h, H, W)))
+    np.testing.assert_allclose(r.x, closed, atol=1e-9)
+    np.testing.assert_allclose(closed, xt, atol=1e-12)
+
+
+def test_pure_inpainting_special_case():
+    """A = I (a 1 x 1 unit kernel) turns the model into inpainting (Sec. IV-A):
+    observed pixels with lambda -> 0 are reproduced; the TV-MD iterate
+    matches the data on the mask."""
+    H, W = 12, 12
+    g = S.rng(11)
+    xt = S.shapes_image(H, W, g, 4, rmax=4.0)
+    h = np.ones((1, 1))
+    mask = (g.uniform(size=(H, W)) < 0.7).astype(np.uint8)
+    ybar = xt * mask
+    r = O.solve(ybar, mask, h, 1e-9, 1.0, 1e-8, "tv", iters=4000, stop="rel_x", tol=1e-14)
+    assert np.max(np.abs((r.x - xt)[mask.astype(bool)])) < 1e-6
+
+
+def test_arbitrary_initialisation_converges_to_same_objective():
+    """Theorem 1 (Eckstein-Bertsekas): ADMM converges from arbitrary u0, d0."""
+    x, h, ybar, mask = _small_problem(seed=12)
+    lam, mu1, mu2 = 2e-3, 1.0, 2e-2
+    r0 = O.solve(ybar, mask, h, lam, mu1, mu2, "tv", iters=20000, stop="rel_x", tol=1e-13)
+    g = S.rng(13)
+    H, W = ybar.shape
+    st = O.State(g.standard_normal((H, W)), g.standard_normal((H, W)),
+                 g.standard_normal((2, H, W)), g.standard_normal((2, H, W)), np.zeros((H, W)))
+    r1 = O.solve(ybar, mask, h, lam, mu1, mu2, "tv", iters=20000, stop="rel_x", tol=1e-13, state0=st)
+    assert abs(r0.objective - r1.objective) <= 1e-7 * r0.objective
+    np.testing.assert_allclose(r0.x, r1.x, atol=1e-6)
+
+
+def test_objective_decreases_after_burn_in():
+    """ADMM gives no per-step monotone decrease (Theorem 1 is a convergence
+    result), but on these problems f(x_k) <= f(x_{k-20}) after 20 iterations."""
+    p = S.config1_problem(0)
+    r = O.solve(p.ybar, p.mask, p.psf, p.lam, p.mu1, p.mu2, "tv", iters=200, record=True)
+    f = [h[1] for h in r.history]
+    for k in range(40, len(f)):
+        assert f[k] <= f[k - 20] * (1 + 1e-12)
