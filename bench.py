@@ -1,0 +1,344 @@
+"""Benchmark: batched TV-MD deconvolution + inpainting at 512 x 512, solved
+to a relative change of x below 1e-5.
+
+One step = one call of admm_deconv_solve_batch over a batch of synthetic
+512 x 512 problems (19 x 19 Gaussian sigma 3 and 15-px / 30 degree motion
+blur, BSNR 40 and 60 dB, valid region AND 60% of interior pixels kept), each
+run from u0 = d0 = 0 until ||x_k - x_{k-1}|| / ||x_k|| < 1e-5 (at most 5000
+iterations). The batch's working set (~11 MB per problem) is larger than L2.
+
+Prints one JSON line. `value` = ADMM iterations per second summed over the
+batch (device-resident inputs); `e2e` = the same through the C ABI with host
+buffers (host->device and device->host copies inside the timed region).
+`--impl reference` times the FP64 CPU oracle on the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth as S  # noqa: E402
+
+METRIC = "ADMM iters/s and images/s to tol at fixed ISNR; fraction of HBM roofline"
+H = W = 512
+TOL = 1e-5
+MAX_ITERS = 5000
+CHECK_EVERY = 10
+COMBOS = [("gauss", 40), ("motion", 40), ("gauss", 60), ("motion", 60)]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--batch", type=int, default=32, help="problems per step per GPU")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def make_batch(batch, rank):
+    probs = []
+    for i in range(batch):
+        blur, bsnr = COMBOS[i % len(COMBOS)]
+        probs.append(S.config2_problem(seed=1000 * rank + i, blur=blur, bsnr=bsnr))
+    return probs
+
+
+def bytes_per_pixel_iter():
+    """Algorithmic HBM bytes per pixel and iteration of each phase (FP32).
+    Row phase: half spectra in and out (8 + 8), d1 and d2 read and written
+    (8 + 16), M^T y and the mask read (4 + 1), x_prev for the rel-x rule
+    (read + write once per CHECK_EVERY iterations). Column phase: half
+    spectra in and out (8 + 8) and Lambda, K over the half spectrum (6)."""
+    half = (W // 2 + 1) / W
+    row = 8 + 8 + 8 + 16 + 4 + 1 + 8.0 / CHECK_EVERY
+    col = (16 + 16 + 8 + 4) * half
+    return row, col
+
+
+def read_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index),
+                 "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+                 "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None:
+            return None
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 7:
+                    continue
+                try:
+                    sm.append(float(parts[0]))
+                    mx = float(parts[1])
+                except ValueError:
+                    continue
+                for n, v in zip(names, parts[3:7]):
+                    if v.lower().startswith("active"):
+                        reasons.add(n)
+        except OSError:
+            return None
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline_oracle(probs, seconds=12.0):
+    """The FP64 oracle as it stands on one 512^2 problem of the workload,
+    iterating until about `seconds` of CPU time; iterations per second."""
+    import oracle as O
+    p = probs[0]
+    st = O.State.zeros(H, W, "tv")
+    otf = O.psf_otf(p.psf, H, W)
+    den = O.tv_denominator_diag(p.psf, H, W, p.mu1, p.mu2)
+    t0 = time.perf_counter()
+    n = 0
+    while time.perf_counter() - t0 < seconds:
+        st = O.tvmd_step(st, p.ybar, p.mask, p.psf, p.lam, p.mu1, p.mu2, otf, den)
+        n += 1
+    dt = time.perf_counter() - t0
+    return n / dt, n, dt
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    probs = make_batch(1, 0)
+    per_step = []
+    iters_step = 0
+    for s in range(args.warmup + args.steps):
+        v, n, dt = cpu_baseline_oracle(probs, seconds=3.0)
+        if s >= args.warmup:
+            per_step.append((n, dt))
+            iters_step = n
+    tot_n = sum(n for n, _ in per_step)
+    tot_t = sum(t for _, t in per_step)
+    value = tot_n / tot_t
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "iters/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000.0 * tot_t / max(1, len(per_step)), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "tv_md_512x512_inpaint40_gauss19_motion15_relx1e-5",
+                   "sample": f"{iters_step} oracle iterations on one 512x512 problem per step"},
+        "cpu_baseline": {"value": value, "unit": "iters/s", "cores": 1, "kind": "oracle",
+                         "sample": "TV-MD FP64 numpy oracle, one 512x512 problem, ~3 s per step"},
+        "e2e": {"value": value, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1210_2687_gb300 as ad
+
+    dev = torch.device("cuda", local)
+    probs = make_batch(args.batch, rank)
+    n = H * W
+    plans = [ad.Plan(H, W, p.psf, p.lam, p.mu1, p.mu2, "tv", stop="rel_x", tol=TOL,
+                     max_iters=MAX_ITERS, check_every=CHECK_EVERY) for p in probs]
+    ys = [torch.from_numpy(p.ybar.astype(np.float32)).to(dev) for p in probs]
+    ms = [torch.from_numpy(p.mask).to(dev) for p in probs]
+    xs = [torch.empty((H, W), dtype=torch.float32, device=dev) for _ in probs]
+    stream = torch.cuda.current_stream()
+
+    def step():
+        return ad.solve_batch(plans, ys, ms, xs, stream)
+
+    for _ in range(args.warmup):
+        res = step()
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    # ---- timed region: device-resident inputs ----
+    ad.admm_deconv_profile(True)
+    barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        total_iters = 0
+        for _ in range(args.steps):
+            res = step()
+            total_iters += sum(r.iters for r in res)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    prof = ad.admm_deconv_profile(False)
+    ms_total = ev0.elapsed_time(ev1)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms_total, float(total_iters)], device=dev, dtype=torch.float64)
+        tmax = t.clone()
+        dist.all_reduce(tmax[:1], op=dist.ReduceOp.MAX)
+        dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
+        ms_total, total_iters = float(tmax[0]), float(t[1])
+    sec = ms_total / 1000.0
+    value = total_iters / sec
+    images_per_s = args.batch * world * args.steps / sec
+
+    # ---- ISNR of the last solve (accuracy context) ----
+    import oracle as O  # accuracy context only, not on the timed path
+    isnrs = []
+    for p, x in zip(probs, xs):
+        vm = S.valid_mask(H, W, *p.psf.shape)
+        isnrs.append(O.isnr(p.x_true, p.ybar, x.cpu().numpy().astype(np.float64), vm))
+
+    # ---- roofline of the dominant kernel ----
+    row_b, col_b = bytes_per_pixel_iter()
+    img_iters = sum(r.iters for r in res) * args.steps / world if world > 1 else total_iters
+    row_gbs = img_iters * n * row_b / (prof.row_ms * 1e-3) / 1e9 if prof.row_ms > 0 else 0.0
+    col_gbs = img_iters * n * col_b / (prof.col_ms * 1e-3) / 1e9 if prof.col_ms > 0 else 0.0
+    peak, peak_kind = read_peak()
+    dom = "row_phase_tv<512,16>" if prof.row_ms >= prof.col_ms else "col_phase<512,4>"
+    ach = row_gbs if prof.row_ms >= prof.col_ms else col_gbs
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tpath):
+        try:
+            traffic = json.load(open(tpath)).get(dom)
+        except Exception:
+            traffic = None
+
+    # ---- end to end through the C ABI with host buffers ----
+    yh = [torch.from_numpy(p.ybar.astype(np.float32)).pin_memory() for p in probs]
+    mh = [torch.from_numpy(p.mask).pin_memory() for p in probs]
+    xh = [torch.empty((H, W), dtype=torch.float32).pin_memory() for _ in probs]
+    ad.solve_batch(plans, yh, mh, xh, stream)
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    e2e_iters = 0
+    for _ in range(args.steps):
+        r2 = ad.solve_batch(plans, yh, mh, xh, stream)
+        e2e_iters += sum(r.iters for r in r2)
+    torch.cuda.synchronize()
+    e2e_sec = time.perf_counter() - t0
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([e2e_sec, float(e2e_iters)], device=dev, dtype=torch.float64)
+        tm = t.clone()
+        dist.all_reduce(tm[:1], op=dist.ReduceOp.MAX)
+        dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
+        e2e_sec, e2e_iters = float(tm[0]), float(t[1])
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, nit, dt = cpu_baseline_oracle(probs, seconds=12.0)
+        cpu = {"value": v, "unit": "iters/s", "cores": 1, "kind": "oracle",
+               "sample": f"{nit} TV-MD iterations of the FP64 numpy oracle on one 512x512 problem "
+                         f"({dt:.1f} s, single thread)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "tv_md_512x512_inpaint40_gauss19_motion15_relx1e-5",
+                       "batch_per_gpu": args.batch, "H": H, "W": W, "tol_rel_x": TOL,
+                       "check_every": CHECK_EVERY, "max_iters": MAX_ITERS,
+                       "l2": "inputs larger than L2 (~11 MB per problem x batch)",
+                       "parallelism": f"replicas x{world}"},
+            "images_per_s": images_per_s,
+            "iters_per_image_mean": total_iters / (args.batch * world * args.steps),
+            "isnr_db_mean": float(np.mean(isnrs)),
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": peak,
+                         "peak_kind": peak_kind, "unit": "GB/s", "frac": ach / peak,
+                         "traffic": traffic,
+                         "bytes_per_px_iter": {"row_phase": row_b, "col_phase": col_b},
+                         "row_phase_gbs": row_gbs, "col_phase_gbs": col_gbs,
+                         "row_ms": prof.row_ms, "col_ms": prof.col_ms},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_iters / e2e_sec, "unit": "iters/s",
+                    "h2d_bytes_per_step": args.batch * (4 * n + n),
+                    "d2h_bytes_per_step": args.batch * 4 * n},
+            "gpu_launches": int(prof.kernel_launches),
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,192 @@
+/*
+ * admm_deconv.h -- C ABI of the GB300 (sm_103a) mask-decoupled ADMM solver for
+ * image deconvolution with unknown boundaries.
+ *
+ * Method: M. S. C. Almeida, M. A. T. Figueiredo, "Deconvolving Images with
+ * Unknown Boundaries Using the Alternating Direction Method of Multipliers".
+ *   observation model   y = M A x + n                      (Sec. IV-A, eq. model_unknown_BC)
+ *   TV-MD               Algorithm 3 with line 7 -> eq. new_line (Sec. IV-D)
+ *   FA-MD               Algorithm 2, H1 = A, H2 = P, eqs. invAnalysis/invAnalysisp1,
+ *                       prox eqs. prox_g_1_uBC and prox_g_2    (Sec. IV-C)
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Images are row-major float32, H rows x W columns, on the FULL unknown
+ *    domain (the observed region is a subset of it).
+ *  - The blur A is periodic convolution on the full domain with the kernel
+ *    centre at (0,0); its boundary condition is irrelevant on the observed
+ *    pixels (Sec. IV-A). Kernels have odd sides, l = (side - 1) / 2 per axis.
+ *  - TV uses forward periodic differences; the frame is the undecimated Haar
+ *    frame (Parseval, P^T P = I) with `haar_levels` levels (3 L + 1 bands).
+ *  - Every call is ordered on the CUDA stream passed as `stream` (a
+ *    cudaStream_t, NULL = legacy default stream). Calls that run the solver
+ *    return after the solve has finished on that stream.
+ *  - Return values: ADMM_OK (0) or a negative ADMM_E* code; admm_strerror()
+ *    names it. No call throws or aborts. A solve that reaches max_iters
+ *    without meeting its tolerance is not an error (result.converged = 0).
+ *  - Device pointers must be allocated with cudaMalloc (or equivalent) on the
+ *    current device; host pointers may be pageable or pinned. The library
+ *    never takes ownership of caller memory.
+ *  - One library instance serialises its solve calls internally (a mutex).
+ */
+#ifndef ADMM_DECONV_H
+#define ADMM_DECONV_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define ADMM_API __attribute__((visibility("default")))
+#else
+#define ADMM_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------- */
+#define ADMM_OK                   0
+#define ADMM_EINVAL              -1  /* bad argument (null, non-odd kernel, mu <= 0, ...) */
+#define ADMM_ENOMEM              -2  /* device or host allocation failed                   */
+#define ADMM_ECUDA               -3  /* a CUDA runtime call failed                         */
+#define ADMM_EUNSUPPORTED_SIZE   -4  /* H or W not in {64,...,2048} powers of two          */
+#define ADMM_ENONFINITE          -5  /* the iterate became NaN/Inf (divergence, Theorem 1) */
+#define ADMM_ETIMEOUT            -6  /* a bounded device wait expired                      */
+
+/* ---- enums -------------------------------------------------------------- */
+#define ADMM_REG_TV     0   /* isotropic TV, eq. unconstrained_TV_uBC            */
+#define ADMM_REG_HAAR   1   /* l1 of undecimated Haar analysis coefficients,
+                               eq. unconstrained_analysis_uBC                    */
+
+#define ADMM_STOP_ITERS   0 /* run exactly max_iters iterations                  */
+#define ADMM_STOP_REL_X   1 /* ||x_k - x_{k-1}|| / ||x_k|| < tol                 */
+#define ADMM_STOP_REL_OBJ 2 /* |f_k - f_{k-1}| / |f_k| < tol (Sec. V's rule)     */
+
+typedef struct admm_plan_s* admm_plan_t;   /* opaque; owned by the library */
+
+/* Parameters of one problem (one image). */
+typedef struct {
+    int   H, W;            /* full unknown-image domain; powers of two in [64, 2048]        */
+    int   psf_h, psf_w;    /* odd kernel sides, each <= the matching image side             */
+    const float* psf;      /* HOST pointer, psf_h x psf_w row-major, centre at
+                              (psf_h/2, psf_w/2); copied during admm_deconv_plan; the
+                              DC gain sum(psf) must be nonzero (Sec. III-C proposition)     */
+    float lambda;          /* regularisation weight lambda >= 0                             */
+    float mu1, mu2;        /* ADMM penalties mu_1 (observation split), mu_2 (regulariser);
+                              a value <= 0 selects the rule of Sec. V:
+                              mu2 = 10 lambda, mu1 = min(1, 5000 mu2)                       */
+    int   reg;             /* ADMM_REG_TV or ADMM_REG_HAAR                                  */
+    int   haar_levels;     /* frame levels for ADMM_REG_HAAR, 1..4 (0 = 4)                 */
+    int   stop;            /* ADMM_STOP_*                                                   */
+    double tol;            /* tolerance of the stop rule                                    */
+    int   max_iters;       /* iteration cap (> 0)                                           */
+    int   check_every;     /* evaluate the rel-x rule every this many iterations (>= 1);
+                              the rule always compares two consecutive iterates             */
+    int   raw_mask;        /* 0: the observation mask is ANDed with the valid region
+                              (pixels whose blurred value does not touch the unknown
+                              boundary, Sec. IV-A); 1: use the mask exactly as given
+                              (e.g. M = I for periodic deconvolution)                        */
+} admm_params_t;
+
+/* Per-problem outcome, written before a solve call returns. */
+typedef struct {
+    int    iters;          /* iterations run                                                */
+    int    converged;      /* 1 if the stop rule was met before max_iters                  */
+    int    status;         /* ADMM_OK or ADMM_ENONFINITE for this problem                  */
+    int    reserved;
+    double objective;      /* objective of eq. unconstrained_TV_uBC / _analysis_uBC at the
+                              final iterate (FP32 data, compensated reduction)              */
+    double rel_x;          /* last evaluated ||x_k - x_{k-1}|| / ||x_k||, or -1 if never    */
+    double rel_obj;        /* last evaluated |f_k - f_{k-1}| / |f_k|, or -1 if never        */
+} admm_result_t;
+
+/*
+ * admm_deconv_plan -- validate `p`, allocate the plan's device state and
+ * precompute its spectra (a0 of the iteration: Lambda = DFT of the centred
+ * kernel, and the diagonal of eq. fast_inversion for TV or eq. invAnalysisp1
+ * for Haar, with the 1/(H W) of the inverse DFT folded in).
+ *   out     [out] receives the plan handle (unchanged on error)
+ *   p       [in]  parameters; p->psf is read before the call returns
+ *   stream  [in]  cudaStream_t the precompute kernels are ordered on
+ * Errors: ADMM_EINVAL, ADMM_EUNSUPPORTED_SIZE, ADMM_ENOMEM, ADMM_ECUDA.
+ */
+ADMM_API int admm_deconv_plan(admm_plan_t* out, const admm_params_t* p, void* stream);
+
+/*
+ * admm_deconv_solve -- run the ADMM of the plan on one observation.
+ *   y      [in]  H x W float32, observed values on observed pixels (other values
+ *                are ignored); device or host memory
+ *   mask   [in]  H x W uint8, nonzero = observed; NULL = the valid region only;
+ *                device or host memory
+ *   x_out  [out] H x W float32 estimate of the full image; device or host memory
+ *   res    [out] host pointer, may be NULL
+ * The solve starts from u0 = d0 = 0 (Algorithm 3 initialisation).
+ * Errors: ADMM_EINVAL, ADMM_ECUDA, ADMM_ENONFINITE (also in res->status).
+ */
+ADMM_API int admm_deconv_solve(admm_plan_t plan, const float* y, const uint8_t* mask, float* x_out,
+                      admm_result_t* res, void* stream);
+
+/*
+ * admm_deconv_solve_batch -- solve `count` independent problems together.
+ * Problems with the same (H, W, regulariser) advance in lock-step launches
+ * (one launch per phase and iteration for the whole group); each problem
+ * retires when its own stop rule is met. Arguments are arrays of `count`
+ * entries with the meaning of admm_deconv_solve; masks may be NULL (then
+ * every mask is the valid region) and any masks[i] may be NULL.
+ * A plan may appear at most once per call.
+ * Errors: as admm_deconv_solve; the first failing problem's code is returned.
+ */
+ADMM_API int admm_deconv_solve_batch(const admm_plan_t* plans, int count, const float* const* y,
+                            const uint8_t* const* masks, float* const* x_out,
+                            admm_result_t* res, void* stream);
+
+/*
+ * admm_deconv_state_size -- number of floats of the dual state d = (d1, d2)
+ * of the plan: (1 + 2) H W for TV, (1 + 3 L + 1) H W for Haar.
+ */
+ADMM_API long long admm_deconv_state_size(admm_plan_t plan);
+
+/*
+ * admm_deconv_get_state -- copy the dual variables (d1 then d2, band-major)
+ * left by the last solve into `d_out` (device or host, state_size floats).
+ * Errors: ADMM_EINVAL, ADMM_ECUDA.
+ */
+ADMM_API int admm_deconv_get_state(admm_plan_t plan, float* d_out, void* stream);
+
+/* Device-time counters of the solver's launches (observability; not in the paper). */
+typedef struct {
+    double    col_ms;            /* summed device time of column-phase launches          */
+    double    row_ms;            /* summed device time of the row-side launches of each
+                                    iteration (one kernel for TV, three for the frame)  */
+    long long col_launches;      /* column-phase launches timed                          */
+    long long row_launches;      /* iterations whose row side was timed                  */
+    long long kernel_launches;   /* every kernel the library launched (always counted)   */
+} admm_profile_t;
+
+/*
+ * admm_deconv_profile -- read-and-reset the counters, then switch timing.
+ *   enable  nonzero: following solves record a CUDA event on their stream
+ *           between consecutive phase launches and add the elapsed times to
+ *           the counters when the solve ends; zero: no events are recorded
+ *   out     [out] if not NULL, receives the counters accumulated so far,
+ *           which are then reset to zero
+ * Timing is stream-ordered: a phase's time is the interval between the
+ * events around it, so it includes any idle gap between launches.
+ */
+ADMM_API int admm_deconv_profile(int enable, admm_profile_t* out);
+
+/* admm_deconv_destroy -- free everything the plan owns (NULL is a no-op).
+ * Synchronises the device first. */
+ADMM_API void admm_deconv_destroy(admm_plan_t plan);
+
+/* admm_strerror -- static string naming a status code. */
+ADMM_API const char* admm_strerror(int code);
+
+/* admm_deconv_version -- library version string. */
+ADMM_API const char* admm_deconv_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ADMM_DECONV_H */

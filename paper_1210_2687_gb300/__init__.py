@@ -1,0 +1,251 @@
+"""Python binding of libadmm_deconv (mask-decoupled ADMM deconvolution on sm_103a).
+
+Argument marshalling only: every step of the solve runs in the CUDA library
+declared by include/admm_deconv.h. Importing this module loads the in-tree
+``libadmm_deconv.so`` and raises if it is missing -- there is no CPU fallback.
+Build it with ``python paper_1210_2687_gb300/build.py``.
+
+The function names mirror the C ABI (admm_deconv_plan, admm_deconv_solve,
+admm_deconv_solve_batch, admm_deconv_destroy, admm_strerror, ...); ``Plan``
+and ``solve`` are conveniences on top that take numpy arrays or torch tensors
+(host or CUDA) and pass their data pointers.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Sequence
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libadmm_deconv.so")
+
+ADMM_OK = 0
+ADMM_EINVAL = -1
+ADMM_ENOMEM = -2
+ADMM_ECUDA = -3
+ADMM_EUNSUPPORTED_SIZE = -4
+ADMM_ENONFINITE = -5
+ADMM_ETIMEOUT = -6
+
+ADMM_REG_TV = 0
+ADMM_REG_HAAR = 1
+ADMM_STOP_ITERS = 0
+ADMM_STOP_REL_X = 1
+ADMM_STOP_REL_OBJ = 2
+
+_REG = {"tv": ADMM_REG_TV, "haar": ADMM_REG_HAAR}
+_STOP = {"iters": ADMM_STOP_ITERS, "rel_x": ADMM_STOP_REL_X, "rel_obj": ADMM_STOP_REL_OBJ}
+
+EXPORTED = ("admm_deconv_plan", "admm_deconv_solve", "admm_deconv_solve_batch",
+            "admm_deconv_state_size", "admm_deconv_get_state", "admm_deconv_destroy",
+            "admm_strerror", "admm_deconv_version", "admm_deconv_profile")
+
+
+class admm_params_t(ctypes.Structure):
+    _fields_ = [("H", ctypes.c_int), ("W", ctypes.c_int),
+                ("psf_h", ctypes.c_int), ("psf_w", ctypes.c_int),
+                ("psf", ctypes.POINTER(ctypes.c_float)),
+                ("lambda_", ctypes.c_float), ("mu1", ctypes.c_float), ("mu2", ctypes.c_float),
+                ("reg", ctypes.c_int), ("haar_levels", ctypes.c_int),
+                ("stop", ctypes.c_int), ("tol", ctypes.c_double),
+                ("max_iters", ctypes.c_int), ("check_every", ctypes.c_int),
+                ("raw_mask", ctypes.c_int)]
+
+
+class admm_result_t(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("converged", ctypes.c_int),
+                ("status", ctypes.c_int), ("reserved", ctypes.c_int),
+                ("objective", ctypes.c_double), ("rel_x", ctypes.c_double),
+                ("rel_obj", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+
+
+class admm_profile_t(ctypes.Structure):
+    _fields_ = [("col_ms", ctypes.c_double), ("row_ms", ctypes.c_double),
+                ("col_launches", ctypes.c_longlong), ("row_launches", ctypes.c_longlong),
+                ("kernel_launches", ctypes.c_longlong)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class AdmmError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        super().__init__(f"{what}: {admm_strerror(code)} ({code})")
+        self.code = code
+
+
+def _load() -> ctypes.CDLL:
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing; build it with `python paper_1210_2687_gb300/build.py`")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp = ctypes.c_void_p
+    lib.admm_deconv_plan.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(admm_params_t), vp]
+    lib.admm_deconv_plan.restype = ctypes.c_int
+    lib.admm_deconv_solve.argtypes = [vp, vp, vp, vp, ctypes.POINTER(admm_result_t), vp]
+    lib.admm_deconv_solve.restype = ctypes.c_int
+    lib.admm_deconv_solve_batch.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(vp),
+                                            ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                            ctypes.POINTER(admm_result_t), vp]
+    lib.admm_deconv_solve_batch.restype = ctypes.c_int
+    lib.admm_deconv_state_size.argtypes = [vp]
+    lib.admm_deconv_state_size.restype = ctypes.c_longlong
+    lib.admm_deconv_get_state.argtypes = [vp, vp, vp]
+    lib.admm_deconv_get_state.restype = ctypes.c_int
+    lib.admm_deconv_destroy.argtypes = [vp]
+    lib.admm_deconv_destroy.restype = None
+    lib.admm_strerror.argtypes = [ctypes.c_int]
+    lib.admm_strerror.restype = ctypes.c_char_p
+    lib.admm_deconv_version.argtypes = []
+    lib.admm_deconv_version.restype = ctypes.c_char_p
+    lib.admm_deconv_profile.argtypes = [ctypes.c_int, ctypes.POINTER(admm_profile_t)]
+    lib.admm_deconv_profile.restype = ctypes.c_int
+    return lib
+
+
+lib = _load()
+
+
+# ---- thin C-ABI mirrors ----------------------------------------------------
+def admm_strerror(code: int) -> str:
+    return lib.admm_strerror(int(code)).decode()
+
+
+def admm_deconv_version() -> str:
+    return lib.admm_deconv_version().decode()
+
+
+def admm_deconv_plan(params: admm_params_t, stream=None) -> int:
+    h = ctypes.c_void_p()
+    rc = lib.admm_deconv_plan(ctypes.byref(h), ctypes.byref(params), _stream(stream))
+    if rc != ADMM_OK:
+        raise AdmmError(rc, "admm_deconv_plan")
+    return h.value
+
+
+def admm_deconv_solve(plan: int, y_ptr: int, mask_ptr: int | None, x_ptr: int, stream=None) -> admm_result_t:
+    res = admm_result_t()
+    rc = lib.admm_deconv_solve(ctypes.c_void_p(plan), ctypes.c_void_p(y_ptr), ctypes.c_void_p(mask_ptr or 0),
+                               ctypes.c_void_p(x_ptr), ctypes.byref(res), _stream(stream))
+    if rc != ADMM_OK and rc != ADMM_ENONFINITE:
+        raise AdmmError(rc, "admm_deconv_solve")
+    return res
+
+
+def admm_deconv_solve_batch(plans: Sequence[int], y_ptrs, mask_ptrs, x_ptrs, stream=None):
+    n = len(plans)
+    P = (ctypes.c_void_p * n)(*plans)
+    Y = (ctypes.c_void_p * n)(*y_ptrs)
+    M = (ctypes.c_void_p * n)(*[m or 0 for m in mask_ptrs]) if mask_ptrs is not None else None
+    X = (ctypes.c_void_p * n)(*x_ptrs)
+    R = (admm_result_t * n)()
+    rc = lib.admm_deconv_solve_batch(P, n, Y, M, X, R, _stream(stream))
+    if rc != ADMM_OK and rc != ADMM_ENONFINITE:
+        raise AdmmError(rc, "admm_deconv_solve_batch")
+    return list(R)
+
+
+def admm_deconv_state_size(plan: int) -> int:
+    return int(lib.admm_deconv_state_size(ctypes.c_void_p(plan)))
+
+
+def admm_deconv_get_state(plan: int, out_ptr: int, stream=None) -> None:
+    rc = lib.admm_deconv_get_state(ctypes.c_void_p(plan), ctypes.c_void_p(out_ptr), _stream(stream))
+    if rc != ADMM_OK:
+        raise AdmmError(rc, "admm_deconv_get_state")
+
+
+def admm_deconv_profile(enable: bool) -> admm_profile_t:
+    """Read-and-reset the launch counters, then switch per-phase timing."""
+    out = admm_profile_t()
+    lib.admm_deconv_profile(int(bool(enable)), ctypes.byref(out))
+    return out
+
+
+def admm_deconv_destroy(plan: int) -> None:
+    lib.admm_deconv_destroy(ctypes.c_void_p(plan))
+
+
+# ---- conveniences -----------------------------------------------------------
+def _stream(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available() and torch.cuda.is_initialized():
+                return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        except ImportError:
+            pass
+        return ctypes.c_void_p(0)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(a, dtype) -> int:
+    """Data pointer of a contiguous numpy array or torch tensor of `dtype`."""
+    if a is None:
+        return 0
+    if isinstance(a, np.ndarray):
+        if a.dtype != dtype or not a.flags.c_contiguous:
+            raise TypeError(f"expected a C-contiguous {np.dtype(dtype).name} array")
+        return a.ctypes.data
+    import torch
+    tmap = {np.float32: torch.float32, np.uint8: torch.uint8}
+    if not isinstance(a, torch.Tensor) or a.dtype != tmap[dtype] or not a.is_contiguous():
+        raise TypeError(f"expected a contiguous {tmap[dtype]} tensor")
+    return a.data_ptr()
+
+
+class Plan:
+    """Owns one admm_plan_t. psf: 2-D array with odd sides (host)."""
+
+    def __init__(self, H, W, psf, lam, mu1=0.0, mu2=0.0, reg="tv", levels=4, stop="iters",
+                 tol=0.0, max_iters=200, check_every=1, raw_mask=False, stream=None):
+        k = np.ascontiguousarray(np.asarray(psf, dtype=np.float32))
+        self._psf = k
+        p = admm_params_t()
+        p.H, p.W = int(H), int(W)
+        p.psf_h, p.psf_w = k.shape
+        p.psf = k.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+        p.lambda_ = float(lam)
+        p.mu1, p.mu2 = float(mu1), float(mu2)
+        p.reg = _REG[reg] if isinstance(reg, str) else int(reg)
+        p.haar_levels = int(levels)
+        p.stop = _STOP[stop] if isinstance(stop, str) else int(stop)
+        p.tol = float(tol)
+        p.max_iters = int(max_iters)
+        p.check_every = int(check_every)
+        p.raw_mask = int(bool(raw_mask))
+        self.params = p
+        self.H, self.W = p.H, p.W
+        self.handle = admm_deconv_plan(p, stream)
+
+    def state_size(self) -> int:
+        return admm_deconv_state_size(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            admm_deconv_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def solve(plan: Plan, y, mask, x_out, stream=None) -> admm_result_t:
+    """Run one solve; y/x_out float32 and mask uint8 (or None), numpy or torch, host or CUDA."""
+    return admm_deconv_solve(plan.handle, _ptr(y, np.float32), _ptr(mask, np.uint8), _ptr(x_out, np.float32),
+                             stream)
+
+
+def solve_batch(plans: Sequence[Plan], ys, masks, x_outs, stream=None):
+    return admm_deconv_solve_batch([p.handle for p in plans], [_ptr(y, np.float32) for y in ys],
+                                   None if masks is None else [_ptr(m, np.uint8) for m in masks],
+                                   [_ptr(x, np.float32) for x in x_outs], stream)

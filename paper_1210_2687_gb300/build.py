@@ -1,0 +1,66 @@
+"""Build step: compile the CUDA library libadmm_deconv.so in-tree for sm_103a.
+
+    python paper_1210_2687_gb300/build.py        # or __graft_entry__.build()
+
+nvcc cross-compiles on machines without a GPU. The library links the shared
+CUDA runtime so that it shares one runtime instance with PyTorch.
+"""
+from __future__ import annotations
+
+import os
+import shutil
+import subprocess
+import sys
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(PKG)
+CSRC = os.path.join(PKG, "csrc")
+LIB = os.path.join(PKG, "libadmm_deconv.so")
+SOURCES = [os.path.join(CSRC, "engine.cu")]
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def _nvcc() -> str:
+    for cand in (shutil.which("nvcc"), "/usr/local/cuda/bin/nvcc"):
+        if cand and os.path.exists(cand):
+            return cand
+    raise RuntimeError("nvcc not found: the CUDA toolkit is required to build libadmm_deconv.so")
+
+
+def _inputs():
+    files = list(SOURCES)
+    for f in os.listdir(CSRC):
+        if f.endswith((".cuh", ".h")):
+            files.append(os.path.join(CSRC, f))
+    files.append(os.path.join(ROOT, "include", "admm_deconv.h"))
+    files.append(os.path.abspath(__file__))
+    return files
+
+
+def up_to_date() -> bool:
+    if not os.path.exists(LIB):
+        return False
+    t = os.path.getmtime(LIB)
+    return all(os.path.getmtime(f) <= t for f in _inputs())
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile libadmm_deconv.so (skipped when newer than every source)."""
+    if not force and up_to_date():
+        return LIB
+    nvcc = _nvcc()
+    cuda_lib = os.path.join(os.path.dirname(os.path.dirname(nvcc)), "lib64")
+    tmp = LIB + ".tmp"
+    cmd = [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-fvisibility=hidden", "-shared",
+           "-cudart", "shared", f"-Xlinker=-rpath,{cuda_lib}", "-I", os.path.join(ROOT, "include"),
+           "-o", tmp, *SOURCES]
+    if verbose:
+        cmd.insert(1, "-Xptxas=-v")
+        print(" ".join(cmd), flush=True)
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, LIB)
+    return LIB
+
+
+if __name__ == "__main__":
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))

@@ -1,0 +1,606 @@
+// engine.cu -- host engine and C ABI of the batched mask-decoupled ADMM.
+//
+// A plan owns one problem's device state (the duals d1, d2, the two
+// half-spectrum buffers exchanged between the row and column phases, the
+// spectra Lambda and K, M^T y and the effective mask). admm_deconv_solve_batch
+// groups problems of equal (H, W, regulariser) and advances each group with
+// one column-phase and one row-phase launch per iteration; a device control
+// block per problem counts iterations and retires the problem when its stop
+// rule holds (Sec. V: relative change of the objective; or of x; or a fixed
+// iteration count). The host polls the number of active problems once per
+// chunk of iterations, one chunk behind the device.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <tuple>
+#include <vector>
+
+#include "../../include/admm_deconv.h"
+#include "kernels.cuh"
+#include "haar.cuh"
+
+using namespace admm;
+
+struct admm_plan_s {
+    admm_params_t p{};
+    std::vector<float> psf;
+    int device = 0;
+    int Wc = 0, Wp = 0, cb = 0, R = 0, n_strips = 0, nb = 0, levels = 0;
+    float lam = 0.f, mu1 = 0.f, mu2 = 0.f;
+    void* slab = nullptr;
+    float4* Sa = nullptr;
+    float4* Sb = nullptr;
+    float* d1 = nullptr;
+    float* d2 = nullptr;
+    float* ybar = nullptr;
+    float* xprev = nullptr;
+    float* work = nullptr;      // frame prior: x / zeta1 / w scratch planes
+    uint8_t* mask = nullptr;
+    float2* lamT = nullptr;
+    float* kT = nullptr;
+    double* partials = nullptr;
+    ProbCtl* ctl = nullptr;
+    float* ystage = nullptr;
+    uint8_t* mstage = nullptr;
+    float* xstage = nullptr;
+    float* psf_dev = nullptr;
+};
+
+namespace {
+
+std::mutex g_mutex;
+
+struct DeviceCtx {
+    bool ready = false;
+    float2* tw = nullptr;            // exp(-2 pi i k / 2048), k < 2048
+    ProbDesc* desc = nullptr;        // descriptor table
+    float** xptr = nullptr;          // finalize destinations
+    int cap = 0;
+    int* n_active = nullptr;
+    int* h_active = nullptr;         // pinned, 2 slots
+    ProbCtl* h_ctl = nullptr;        // pinned copy-back area
+    ProbDesc* h_desc = nullptr;      // pinned staging for the table
+    float** h_xptr = nullptr;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+};
+std::map<int, DeviceCtx> g_ctx;
+
+struct Profile {
+    bool on = false;
+    admm_profile_t acc{};
+    std::vector<cudaEvent_t> ev;     // reused across solves
+} g_prof;
+
+long long g_launches = 0;            // every kernel launched (under g_mutex)
+
+int prof_event(size_t i, cudaStream_t s) {
+    while (g_prof.ev.size() <= i) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return ADMM_ECUDA;
+        g_prof.ev.push_back(e);
+    }
+    return cudaEventRecord(g_prof.ev[i], s) == cudaSuccess ? ADMM_OK : ADMM_ECUDA;
+}
+
+bool is_pow2_size(int n) { return n >= 64 && n <= 2048 && (n & (n - 1)) == 0; }
+
+int cuda_fail(cudaError_t e) {
+    (void)e;
+    return ADMM_ECUDA;
+}
+#define CK(call)                                   \
+    do {                                           \
+        cudaError_t e_ = (call);                   \
+        if (e_ != cudaSuccess) return cuda_fail(e_); \
+    } while (0)
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+int ensure_ctx(int dev, int count, DeviceCtx** out) {
+    DeviceCtx& c = g_ctx[dev];
+    if (!c.ready) {
+        std::vector<float2> tw(2048);
+        for (int k = 0; k < 2048; ++k) {
+            // exact reduction: angle = 2 pi k / 2048
+            const double a = 2.0 * M_PI * (double)k / 2048.0;
+            tw[k] = make_float2((float)std::cos(a), (float)(-std::sin(a)));
+        }
+        CK(cudaMalloc(&c.tw, 2048 * sizeof(float2)));
+        CK(cudaMemcpy(c.tw, tw.data(), 2048 * sizeof(float2), cudaMemcpyHostToDevice));
+        CK(cudaMalloc(&c.n_active, sizeof(int)));
+        CK(cudaHostAlloc(&c.h_active, 2 * sizeof(int), cudaHostAllocDefault));
+        CK(cudaEventCreateWithFlags(&c.ev[0], cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&c.ev[1], cudaEventDisableTiming));
+        c.ready = true;
+    }
+    if (count > c.cap) {
+        int cap = std::max(count, 2 * c.cap);
+        if (c.desc) cudaFree(c.desc);
+        if (c.xptr) cudaFree(c.xptr);
+        if (c.h_ctl) cudaFreeHost(c.h_ctl);
+        if (c.h_desc) cudaFreeHost(c.h_desc);
+        if (c.h_xptr) cudaFreeHost(c.h_xptr);
+        c.desc = nullptr; c.xptr = nullptr; c.h_ctl = nullptr; c.h_desc = nullptr; c.h_xptr = nullptr;
+        c.cap = 0;
+        CK(cudaMalloc(&c.desc, cap * sizeof(ProbDesc)));
+        CK(cudaMalloc(&c.xptr, cap * sizeof(float*)));
+        CK(cudaHostAlloc(&c.h_ctl, cap * sizeof(ProbCtl), cudaHostAllocDefault));
+        CK(cudaHostAlloc(&c.h_desc, cap * sizeof(ProbDesc), cudaHostAllocDefault));
+        CK(cudaHostAlloc(&c.h_xptr, cap * sizeof(float*), cudaHostAllocDefault));
+        c.cap = cap;
+    }
+    *out = &c;
+    return ADMM_OK;
+}
+
+// ---- tiling choices -----------------------------------------------------
+int col_block(int H) {
+    switch (H) {
+        case 64: return 32;
+        case 128: return 16;
+        case 256: return 8;
+        case 512: return 4;
+        case 1024: return 4;
+        default: return 2;
+    }
+}
+int row_strip_tv(int W) { return W <= 512 ? 16 : (W == 1024 ? 8 : 4); }
+
+// ---- template dispatch ---------------------------------------------------
+template <int H, int CB>
+cudaError_t launch_col_t(const ProbDesc* d, int count, int Wc, int Wp, const float2* tw, cudaStream_t s) {
+    static bool attr = false;
+    const size_t smem = ColCfg<H, CB>::SMEM;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(col_phase<H, CB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    dim3 grid(Wp / CB, count);
+    col_phase<H, CB><<<grid, kThreads, smem, s>>>(d, Wc, Wp, tw);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_col(int H, const ProbDesc* d, int count, int Wc, int Wp, const float2* tw, cudaStream_t s) {
+    switch (H) {
+        case 64: return launch_col_t<64, 32>(d, count, Wc, Wp, tw, s);
+        case 128: return launch_col_t<128, 16>(d, count, Wc, Wp, tw, s);
+        case 256: return launch_col_t<256, 8>(d, count, Wc, Wp, tw, s);
+        case 512: return launch_col_t<512, 4>(d, count, Wc, Wp, tw, s);
+        case 1024: return launch_col_t<1024, 4>(d, count, Wc, Wp, tw, s);
+        case 2048: return launch_col_t<2048, 2>(d, count, Wc, Wp, tw, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <int W, int R>
+cudaError_t launch_row_tv_t(const ProbDesc* d, int count, int H, int Wp, const float2* tw, int* n_active,
+                            cudaStream_t s) {
+    static bool attr = false;
+    const size_t smem = RowCfg<W, R>::SMEM;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(row_phase_tv<W, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    dim3 grid(H / R, count);
+    row_phase_tv<W, R><<<grid, kThreads, smem, s>>>(d, H, Wp, tw, n_active);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_row_tv(int W, const ProbDesc* d, int count, int H, int Wp, const float2* tw, int* n_active,
+                          cudaStream_t s) {
+    switch (W) {
+        case 64: return launch_row_tv_t<64, 16>(d, count, H, Wp, tw, n_active, s);
+        case 128: return launch_row_tv_t<128, 16>(d, count, H, Wp, tw, n_active, s);
+        case 256: return launch_row_tv_t<256, 16>(d, count, H, Wp, tw, n_active, s);
+        case 512: return launch_row_tv_t<512, 16>(d, count, H, Wp, tw, n_active, s);
+        case 1024: return launch_row_tv_t<1024, 8>(d, count, H, Wp, tw, n_active, s);
+        case 2048: return launch_row_tv_t<2048, 4>(d, count, H, Wp, tw, n_active, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <int W>
+cudaError_t launch_fin_t(const ProbDesc* d, float* const* xo, int count, int H, int Wp, const float2* tw,
+                         cudaStream_t s) {
+    constexpr int FT = W / 8, G = kThreads / FT;
+    const size_t smem = (size_t)(G * pad8(W) + W) * sizeof(float2);
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(finalize_x<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    dim3 grid((H + G - 1) / G, count);
+    finalize_x<W><<<grid, kThreads, smem, s>>>(d, xo, H, Wp, tw);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fin(int W, const ProbDesc* d, float* const* xo, int count, int H, int Wp, const float2* tw,
+                       cudaStream_t s) {
+    switch (W) {
+        case 64: return launch_fin_t<64>(d, xo, count, H, Wp, tw, s);
+        case 128: return launch_fin_t<128>(d, xo, count, H, Wp, tw, s);
+        case 256: return launch_fin_t<256>(d, xo, count, H, Wp, tw, s);
+        case 512: return launch_fin_t<512>(d, xo, count, H, Wp, tw, s);
+        case 1024: return launch_fin_t<1024>(d, xo, count, H, Wp, tw, s);
+        case 2048: return launch_fin_t<2048>(d, xo, count, H, Wp, tw, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+bool is_device_ptr(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+void free_plan(admm_plan_s* pl) {
+    if (!pl) return;
+    if (pl->slab) cudaFree(pl->slab);
+    delete pl;
+}
+
+ProbDesc make_desc(const admm_plan_s* pl) {
+    ProbDesc d{};
+    d.Sa = pl->Sa;
+    d.Sb = pl->Sb;
+    d.d1 = pl->d1;
+    d.d2 = pl->d2;
+    d.ybar = pl->ybar;
+    d.mask = pl->mask;
+    d.lamT = pl->lamT;
+    d.kT = pl->kT;
+    d.xprev = pl->xprev;
+    d.work = pl->work;
+    d.partials = pl->partials;
+    d.ctl = pl->ctl;
+    d.lam = pl->lam;
+    d.mu1 = pl->mu1;
+    d.mu2 = pl->mu2;
+    d.gamma = (float)((double)pl->mu2 / (double)pl->mu1);
+    d.tau = (float)((double)pl->lam / (double)pl->mu2);
+    d.inv1pmu1 = (float)(1.0 / (1.0 + (double)pl->mu1));
+    d.stop = pl->p.stop;
+    d.max_iters = pl->p.max_iters;
+    d.check_every = pl->p.check_every;
+    d.n_strips = pl->n_strips;
+    d.tol = pl->p.tol;
+    return d;
+}
+
+}  // namespace
+
+// ===========================================================================
+extern "C" {
+
+const char* admm_deconv_version(void) { return "admm_deconv 0.1 (sm_103a)"; }
+
+const char* admm_strerror(int code) {
+    switch (code) {
+        case ADMM_OK: return "ok";
+        case ADMM_EINVAL: return "invalid argument";
+        case ADMM_ENOMEM: return "out of memory";
+        case ADMM_ECUDA: return "CUDA runtime error";
+        case ADMM_EUNSUPPORTED_SIZE: return "unsupported image size (powers of two 64..2048)";
+        case ADMM_ENONFINITE: return "iterate became non-finite";
+        case ADMM_ETIMEOUT: return "device wait timed out";
+    }
+    return "unknown status";
+}
+
+int admm_deconv_plan(admm_plan_t* out, const admm_params_t* p, void* stream) {
+    if (!out || !p || !p->psf) return ADMM_EINVAL;
+    if (!is_pow2_size(p->H) || !is_pow2_size(p->W)) return ADMM_EUNSUPPORTED_SIZE;
+    if (p->psf_h < 1 || p->psf_w < 1 || (p->psf_h & 1) == 0 || (p->psf_w & 1) == 0) return ADMM_EINVAL;
+    if (p->psf_h > std::min(p->H, kMaxPsfSide) || p->psf_w > std::min(p->W, kMaxPsfSide)) return ADMM_EINVAL;
+    if (!(p->lambda >= 0.f) || !std::isfinite(p->lambda)) return ADMM_EINVAL;
+    if (p->reg != ADMM_REG_TV && p->reg != ADMM_REG_HAAR) return ADMM_EINVAL;
+    if (p->stop < ADMM_STOP_ITERS || p->stop > ADMM_STOP_REL_OBJ) return ADMM_EINVAL;
+    if (p->max_iters <= 0 || p->check_every < 1 || !(p->tol >= 0.0)) return ADMM_EINVAL;
+    const int levels = p->reg == ADMM_REG_HAAR ? (p->haar_levels == 0 ? 4 : p->haar_levels) : 0;
+    if (p->reg == ADMM_REG_HAAR && (levels < 1 || levels > kMaxHaarLevels)) return ADMM_EINVAL;
+    double psum = 0.0;
+    for (int i = 0; i < p->psf_h * p->psf_w; ++i) {
+        if (!std::isfinite(p->psf[i])) return ADMM_EINVAL;
+        psum += p->psf[i];
+    }
+    if (psum == 0.0) return ADMM_EINVAL;
+    float mu1 = p->mu1, mu2 = p->mu2;
+    if (mu2 <= 0.f) mu2 = 10.f * p->lambda;
+    if (mu1 <= 0.f) mu1 = std::min(1.f, 5000.f * mu2);
+    if (!(mu1 > 0.f) || !(mu2 > 0.f)) return ADMM_EINVAL;
+
+    std::lock_guard<std::mutex> lk(g_mutex);
+    admm_plan_s* pl = new (std::nothrow) admm_plan_s();
+    if (!pl) return ADMM_ENOMEM;
+    pl->p = *p;
+    pl->p.psf = nullptr;
+    pl->psf.assign(p->psf, p->psf + p->psf_h * p->psf_w);
+    pl->lam = p->lambda;
+    pl->mu1 = mu1;
+    pl->mu2 = mu2;
+    pl->levels = levels;
+    if (cudaGetDevice(&pl->device) != cudaSuccess) { free_plan(pl); return ADMM_ECUDA; }
+    const int H = p->H, W = p->W;
+    const size_t n = (size_t)H * W;
+    pl->Wc = W / 2 + 1;
+    pl->cb = col_block(H);
+    pl->Wp = (int)align_up(pl->Wc, pl->cb);
+    if (p->reg == ADMM_REG_TV) {
+        pl->R = row_strip_tv(W);
+        pl->nb = 2;
+    } else {
+        pl->R = haar_row_strip(W);
+        pl->nb = 3 * levels + 1;
+    }
+    pl->n_strips = p->reg == ADMM_REG_TV ? H / pl->R : haar_num_partial_blocks(H, W);
+
+    // one slab for everything the plan owns
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 256); return o; };
+    const size_t oSa = take((size_t)H * pl->Wp * sizeof(float4));
+    const size_t oSb = take((size_t)H * pl->Wp * sizeof(float4));
+    const size_t od1 = take(n * sizeof(float));
+    const size_t od2 = take((size_t)pl->nb * n * sizeof(float));
+    const size_t oyb = take(n * sizeof(float));
+    const size_t oxp = take(n * sizeof(float));
+    const size_t owk = take(p->reg == ADMM_REG_HAAR ? 3 * n * sizeof(float) : 0);
+    const size_t omk = take(n);
+    const size_t olm = take((size_t)pl->Wc * H * sizeof(float2));
+    const size_t okt = take((size_t)pl->Wc * H * sizeof(float));
+    const size_t opt = take((size_t)pl->n_strips * kNumPartials * sizeof(double));
+    const size_t oct = take(sizeof(ProbCtl));
+    const size_t oys = take(n * sizeof(float));
+    const size_t oms = take(n);
+    const size_t oxs = take(n * sizeof(float));
+    const size_t ops = take(pl->psf.size() * sizeof(float));
+    if (cudaMalloc(&pl->slab, off) != cudaSuccess) {
+        cudaGetLastError();
+        free_plan(pl);
+        return ADMM_ENOMEM;
+    }
+    char* b = static_cast<char*>(pl->slab);
+    pl->Sa = reinterpret_cast<float4*>(b + oSa);
+    pl->Sb = reinterpret_cast<float4*>(b + oSb);
+    pl->d1 = reinterpret_cast<float*>(b + od1);
+    pl->d2 = reinterpret_cast<float*>(b + od2);
+    pl->ybar = reinterpret_cast<float*>(b + oyb);
+    pl->xprev = reinterpret_cast<float*>(b + oxp);
+    pl->work = p->reg == ADMM_REG_HAAR ? reinterpret_cast<float*>(b + owk) : nullptr;
+    pl->mask = reinterpret_cast<uint8_t*>(b + omk);
+    pl->lamT = reinterpret_cast<float2*>(b + olm);
+    pl->kT = reinterpret_cast<float*>(b + okt);
+    pl->partials = reinterpret_cast<double*>(b + opt);
+    pl->ctl = reinterpret_cast<ProbCtl*>(b + oct);
+    pl->ystage = reinterpret_cast<float*>(b + oys);
+    pl->mstage = reinterpret_cast<uint8_t*>(b + oms);
+    pl->xstage = reinterpret_cast<float*>(b + oxs);
+    pl->psf_dev = reinterpret_cast<float*>(b + ops);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int rc = ADMM_OK;
+    do {
+        if (cudaMemsetAsync(pl->slab, 0, off, s) != cudaSuccess) { rc = ADMM_ECUDA; break; }
+        if (cudaMemcpyAsync(pl->psf_dev, pl->psf.data(), pl->psf.size() * sizeof(float), cudaMemcpyHostToDevice, s) !=
+            cudaSuccess) { rc = ADMM_ECUDA; break; }
+        const int tot = H * pl->Wc;
+        spectra_kernel<<<(tot + 255) / 256, 256, 0, s>>>(pl->lamT, pl->kT, pl->psf_dev, p->psf_h, p->psf_w, H, W,
+                                                         pl->Wc, p->reg == ADMM_REG_TV ? 0 : 1,
+                                                         (double)mu2 / (double)mu1);
+        if (cudaGetLastError() != cudaSuccess) { rc = ADMM_ECUDA; break; }
+        if (cudaStreamSynchronize(s) != cudaSuccess) { rc = ADMM_ECUDA; break; }
+    } while (0);
+    if (rc != ADMM_OK) {
+        free_plan(pl);
+        return rc;
+    }
+    *out = pl;
+    return ADMM_OK;
+}
+
+void admm_deconv_destroy(admm_plan_t plan) {
+    if (!plan) return;
+    std::lock_guard<std::mutex> lk(g_mutex);
+    cudaDeviceSynchronize();
+    free_plan(plan);
+}
+
+long long admm_deconv_state_size(admm_plan_t plan) {
+    if (!plan) return -1;
+    return (long long)(1 + plan->nb) * plan->p.H * plan->p.W;
+}
+
+int admm_deconv_get_state(admm_plan_t plan, float* d_out, void* stream) {
+    if (!plan || !d_out) return ADMM_EINVAL;
+    std::lock_guard<std::mutex> lk(g_mutex);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t n = (size_t)plan->p.H * plan->p.W;
+    CK(cudaMemcpyAsync(d_out, plan->d1, n * sizeof(float), cudaMemcpyDefault, s));
+    CK(cudaMemcpyAsync(d_out + n, plan->d2, (size_t)plan->nb * n * sizeof(float), cudaMemcpyDefault, s));
+    CK(cudaStreamSynchronize(s));
+    return ADMM_OK;
+}
+
+static int solve_group(DeviceCtx* ctx, const std::vector<int>& idx, const admm_plan_t* plans,
+                       const float* const* y, const uint8_t* const* masks, float* const* x_out,
+                       admm_result_t* res, cudaStream_t s) {
+    const int count = (int)idx.size();
+    const admm_plan_s* p0 = plans[idx[0]];
+    const int H = p0->p.H, W = p0->p.W, Wc = p0->Wc, Wp = p0->Wp;
+    const bool tv = p0->p.reg == ADMM_REG_TV;
+    const size_t n = (size_t)H * W;
+    int max_iters = 0;
+    std::vector<char> x_host(count, 0);
+    for (int j = 0; j < count; ++j) {
+        admm_plan_s* pl = plans[idx[j]];
+        const float* yj = y[idx[j]];
+        const uint8_t* mj = masks ? masks[idx[j]] : nullptr;
+        if (!is_device_ptr(yj)) {
+            CK(cudaMemcpyAsync(pl->ystage, yj, n * sizeof(float), cudaMemcpyHostToDevice, s));
+            yj = pl->ystage;
+        }
+        if (mj && !is_device_ptr(mj)) {
+            CK(cudaMemcpyAsync(pl->mstage, mj, n, cudaMemcpyHostToDevice, s));
+            mj = pl->mstage;
+        }
+        const int lr = pl->p.psf_h / 2, lc = pl->p.psf_w / 2;
+        prepare_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(pl->ybar, pl->mask, yj, mj, H, W, lr, lc,
+                                                                   pl->p.raw_mask);
+        CK(cudaGetLastError());
+        ++g_launches;
+        CK(cudaMemsetAsync(pl->d1, 0, n * sizeof(float), s));
+        CK(cudaMemsetAsync(pl->d2, 0, (size_t)pl->nb * n * sizeof(float), s));
+        CK(cudaMemsetAsync(pl->Sb, 0, (size_t)H * Wp * sizeof(float4), s));
+        CK(cudaMemsetAsync(pl->xprev, 0, n * sizeof(float), s));
+        ctx->h_desc[j] = make_desc(pl);
+        x_host[j] = !is_device_ptr(x_out[idx[j]]);
+        ctx->h_xptr[j] = x_host[j] ? pl->xstage : x_out[idx[j]];
+        max_iters = std::max(max_iters, pl->p.max_iters);
+    }
+    CK(cudaMemcpyAsync(ctx->desc, ctx->h_desc, count * sizeof(ProbDesc), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ctx->xptr, ctx->h_xptr, count * sizeof(float*), cudaMemcpyHostToDevice, s));
+    init_ctl_kernel<<<(count + 127) / 128, 128, 0, s>>>(ctx->desc, count);
+    CK(cudaGetLastError());
+    ++g_launches;
+    ctx->h_active[0] = count;
+    CK(cudaMemcpyAsync(ctx->n_active, ctx->h_active, sizeof(int), cudaMemcpyHostToDevice, s));
+    // the host buffers of the descriptor table are reused by the next group
+    CK(cudaStreamSynchronize(s));
+
+    const int chunk = 8;
+    const bool prof = g_prof.on;
+    size_t nev = 0;
+    if (prof) {
+        int r = prof_event(nev++, s);
+        if (r != ADMM_OK) return r;
+    }
+    int launched = 0, j = 0;
+    while (launched < max_iters) {
+        const int nit = std::min(chunk, max_iters - launched);
+        for (int it = 0; it < nit; ++it) {
+            CK(launch_col(H, ctx->desc, count, Wc, Wp, ctx->tw, s));
+            ++g_launches;
+            if (prof) {
+                int r = prof_event(nev++, s);
+                if (r != ADMM_OK) return r;
+            }
+            if (tv) {
+                CK(launch_row_tv(W, ctx->desc, count, H, Wp, ctx->tw, ctx->n_active, s));
+                ++g_launches;
+            } else {
+                CK(launch_haar_iteration_rows(W, H, Wp, ctx->desc, count, p0->levels, ctx->tw, ctx->n_active, s));
+                g_launches += 3;
+            }
+            if (prof) {
+                int r = prof_event(nev++, s);
+                if (r != ADMM_OK) return r;
+            }
+        }
+        launched += nit;
+        CK(cudaMemcpyAsync(&ctx->h_active[j & 1], ctx->n_active, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK(cudaEventRecord(ctx->ev[j & 1], s));
+        if (j > 0) {
+            CK(cudaEventSynchronize(ctx->ev[(j - 1) & 1]));
+            if (ctx->h_active[(j - 1) & 1] == 0) break;
+        }
+        ++j;
+    }
+    CK(launch_fin(W, ctx->desc, ctx->xptr, count, H, Wp, ctx->tw, s));
+    ++g_launches;
+    for (int q = 0; q < count; ++q) {
+        admm_plan_s* pl = plans[idx[q]];
+        if (x_host[q]) CK(cudaMemcpyAsync(x_out[idx[q]], pl->xstage, n * sizeof(float), cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(&ctx->h_ctl[q], pl->ctl, sizeof(ProbCtl), cudaMemcpyDeviceToHost, s));
+    }
+    CK(cudaStreamSynchronize(s));
+    if (prof) {
+        for (size_t e = 1; e + 1 < nev; e += 2) {
+            float a = 0.f, b = 0.f;
+            CK(cudaEventElapsedTime(&a, g_prof.ev[e - 1], g_prof.ev[e]));
+            CK(cudaEventElapsedTime(&b, g_prof.ev[e], g_prof.ev[e + 1]));
+            g_prof.acc.col_ms += a;
+            g_prof.acc.row_ms += b;
+            g_prof.acc.col_launches += 1;
+            g_prof.acc.row_launches += 1;
+        }
+    }
+    int rc = ADMM_OK;
+    for (int q = 0; q < count; ++q) {
+        const ProbCtl& c = ctx->h_ctl[q];
+        if (c.status != 0 && rc == ADMM_OK) rc = c.status;
+        if (res) {
+            admm_result_t& r = res[idx[q]];
+            r.iters = c.iter;
+            r.converged = c.converged;
+            r.status = c.status;
+            r.reserved = 0;
+            r.objective = c.have_obj ? c.obj : NAN;
+            r.rel_x = c.rel_x;
+            r.rel_obj = c.rel_obj;
+        }
+    }
+    return rc;
+}
+
+int admm_deconv_solve_batch(const admm_plan_t* plans, int count, const float* const* y,
+                            const uint8_t* const* masks, float* const* x_out, admm_result_t* res, void* stream) {
+    if (count < 0) return ADMM_EINVAL;
+    if (count == 0) return ADMM_OK;
+    if (!plans || !y || !x_out) return ADMM_EINVAL;
+    for (int i = 0; i < count; ++i) {
+        if (!plans[i] || !y[i] || !x_out[i]) return ADMM_EINVAL;
+        for (int j = 0; j < i; ++j)
+            if (plans[j] == plans[i]) return ADMM_EINVAL;
+    }
+    std::lock_guard<std::mutex> lk(g_mutex);
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    for (int i = 0; i < count; ++i)
+        if (plans[i]->device != dev) return ADMM_EINVAL;
+    DeviceCtx* ctx = nullptr;
+    int rc = ensure_ctx(dev, count, &ctx);
+    if (rc != ADMM_OK) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    std::map<std::tuple<int, int, int, int>, std::vector<int>> groups;
+    for (int i = 0; i < count; ++i) {
+        const admm_plan_s* p = plans[i];
+        groups[std::make_tuple(p->p.H, p->p.W, p->p.reg, p->levels)].push_back(i);
+    }
+    int first_err = ADMM_OK;
+    for (auto& kv : groups) {
+        const int r = solve_group(ctx, kv.second, plans, y, masks, x_out, res, s);
+        if (r == ADMM_ECUDA) return r;
+        if (r != ADMM_OK && first_err == ADMM_OK) first_err = r;
+    }
+    return first_err;
+}
+
+int admm_deconv_profile(int enable, admm_profile_t* out) {
+    std::lock_guard<std::mutex> lk(g_mutex);
+    if (out) {
+        *out = g_prof.acc;
+        out->kernel_launches = g_launches;
+        g_prof.acc = admm_profile_t{};
+        g_launches = 0;
+    }
+    g_prof.on = enable != 0;
+    return ADMM_OK;
+}
+
+int admm_deconv_solve(admm_plan_t plan, const float* y, const uint8_t* mask, float* x_out, admm_result_t* res,
+                      void* stream) {
+    const uint8_t* m[1] = {mask};
+    return admm_deconv_solve_batch(&plan, 1, &y, m, &x_out, res, stream);
+}
+
+}  // extern "C"

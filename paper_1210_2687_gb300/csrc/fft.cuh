@@ -1,0 +1,169 @@
+// fft.cuh -- shared-memory Stockham FFTs for power-of-two lengths 64..2048.
+//
+// The x-update of the ADMM (Algorithm 2 line 4; eq. fast_inversion for TV,
+// eq. invAnalysisp1 for the frame prior) is diagonal in the DFT domain. These
+// routines provide the 1-D transforms that the row and column phases apply to
+// whole image rows / spectrum columns.
+//
+// Layout: one length-N transform is owned by a group of N/8 threads. Thread t
+// holds, in registers, the 8 elements t + m*(N/8), m = 0..7, both before and
+// after the transform (natural order), so that the first pass reads and the
+// last pass writes registers directly; intermediate passes exchange through a
+// padded shared-memory buffer of pad8(N) float2 owned by the group.
+// Pass radices: the leading pass (no twiddles) is 2, 4 or 8 so that the
+// remaining passes are all radix 8: 64=8.8, 128=2.8.8, 256=4.8.8, 512=8.8.8,
+// 1024=2.8.8.8, 2048=4.8.8.8.
+//
+// DIR = -1: X[k] = sum_n x[n] exp(-2 pi i k n / N) (unnormalised forward)
+// DIR = +1: x[n] = sum_k X[k] exp(+2 pi i k n / N) (unnormalised inverse)
+#pragma once
+#include <cuda_runtime.h>
+
+namespace admm {
+
+__device__ __forceinline__ float2 operator+(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 operator-(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 operator*(float s, float2 a) { return make_float2(s * a.x, s * a.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b) {  // a * conj(b)
+    return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.y, b.x, -a.x * b.y));
+}
+__device__ __forceinline__ float2 conjf2(float2 a) { return make_float2(a.x, -a.y); }
+
+// one float2 of padding after every 8 elements: spreads the radix-8 scatter
+// of the first pass over all banks
+__host__ __device__ constexpr int pad8(int i) { return i + (i >> 3); }
+
+template <int N> struct FftShape {
+    static constexpr int LOG = (N == 64) ? 6 : (N == 128) ? 7 : (N == 256) ? 8 : (N == 512) ? 9
+                             : (N == 1024) ? 10 : (N == 2048) ? 11 : -1;
+    static_assert(LOG > 0, "unsupported FFT length");
+    static constexpr int R0 = (LOG % 3 == 0) ? 8 : (LOG % 3 == 1) ? 2 : 4;  // leading radix
+    static constexpr int NP8 = (LOG - (R0 == 8 ? 3 : R0 == 4 ? 2 : 1)) / 3; // radix-8 passes after it
+    static constexpr int THREADS = N / 8;
+};
+
+// multiply by DIR * i
+template <int DIR> __device__ __forceinline__ float2 mul_i(float2 a) {
+    return DIR < 0 ? make_float2(a.y, -a.x) : make_float2(-a.y, a.x);
+}
+
+template <int DIR> __device__ __forceinline__ void dft2(float2& a, float2& b) {
+    float2 t = a;
+    a = t + b;
+    b = t - b;
+}
+
+template <int DIR> __device__ __forceinline__ void dft4(float2& a0, float2& a1, float2& a2, float2& a3) {
+    float2 s02 = a0 + a2, d02 = a0 - a2, s13 = a1 + a3, d13 = a1 - a3;
+    float2 j13 = mul_i<DIR>(d13);
+    a0 = s02 + s13;
+    a2 = s02 - s13;
+    a1 = d02 + j13;
+    a3 = d02 - j13;
+}
+
+// natural-order 8-point DFT in registers (radix-2 split of two 4-point DFTs)
+template <int DIR> __device__ __forceinline__ void dft8(float2 (&v)[8]) {
+    float2 e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
+    float2 o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
+    dft4<DIR>(e0, e1, e2, e3);
+    dft4<DIR>(o0, o1, o2, o3);
+    const float c = 0.70710678118654752440f;
+    // o_k *= exp(DIR * 2 pi i k / 8)
+    o1 = make_float2(c * (o1.x - (float)DIR * o1.y), c * (o1.y + (float)DIR * o1.x));
+    o2 = mul_i<DIR>(o2);
+    o3 = make_float2(c * (-o3.x - (float)DIR * o3.y), c * ((float)DIR * o3.x - o3.y));
+    v[0] = e0 + o0; v[4] = e0 - o0;
+    v[1] = e1 + o1; v[5] = e1 - o1;
+    v[2] = e2 + o2; v[6] = e2 - o2;
+    v[3] = e3 + o3; v[7] = e3 - o3;
+}
+
+// twiddle exp(DIR * 2 pi i * idx / N) from the forward table tw[i] = exp(-2 pi i i / N)
+template <int DIR> __device__ __forceinline__ float2 twid(const float2* tw, int idx) {
+    float2 w = tw[idx];
+    return DIR < 0 ? w : conjf2(w);
+}
+
+// One Stockham pass on the registers of thread t (elements t + m N/8 as
+// input): twiddles, butterflies, and the output index of every register.
+template <int N, int R, int DIR>
+__device__ __forceinline__ void stockham_compute(float2 (&v)[8], int t, int Ns, const float2* tw,
+                                                 int (&oidx)[8]) {
+    constexpr int Q = N / 8;
+    if constexpr (R == 8) {
+        const int j = t, k = j & (Ns - 1);
+        if (Ns > 1) {
+            const int step = N / (Ns * 8);
+#pragma unroll
+            for (int r = 1; r < 8; ++r) v[r] = cmul(v[r], twid<DIR>(tw, r * k * step));
+        }
+        dft8<DIR>(v);
+        const int base = (j - k) * 8 + k;
+#pragma unroll
+        for (int r = 0; r < 8; ++r) oidx[r] = base + r * Ns;
+    } else if constexpr (R == 4) {
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            const int j = t + b * Q, k = j & (Ns - 1);
+            if (Ns > 1) {
+                const int step = N / (Ns * 4);
+#pragma unroll
+                for (int q = 1; q < 4; ++q) v[2 * q + b] = cmul(v[2 * q + b], twid<DIR>(tw, q * k * step));
+            }
+            dft4<DIR>(v[b], v[2 + b], v[4 + b], v[6 + b]);
+            const int base = (j - k) * 4 + k;
+#pragma unroll
+            for (int r = 0; r < 4; ++r) oidx[2 * r + b] = base + r * Ns;
+        }
+    } else {
+        static_assert(R == 2, "radix");
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            const int j = t + s * Q, k = j & (Ns - 1);
+            if (Ns > 1) v[s + 4] = cmul(v[s + 4], twid<DIR>(tw, k * (N / (Ns * 2))));
+            dft2<DIR>(v[s], v[s + 4]);
+            const int base = (j - k) * 2 + k;
+            oidx[s] = base;
+            oidx[s + 4] = base + Ns;
+        }
+    }
+}
+
+// Full length-N transform for a group of N/8 threads.
+//   v    : in/out registers, element t + m N/8 in v[m] (natural order both ways)
+//   buf  : the group's shared buffer, >= pad8(N) float2
+//   tw   : forward twiddle table of length N (shared or global)
+// All threads of the block must call this together (it uses __syncthreads).
+template <int N, int DIR>
+__device__ __forceinline__ void fft_group(float2 (&v)[8], float2* buf, const float2* tw, int t) {
+    using S = FftShape<N>;
+    constexpr int Q = N / 8;
+    int oidx[8];
+    int Ns = 1;
+    stockham_compute<N, S::R0, DIR>(v, t, Ns, tw, oidx);
+    Ns *= S::R0;
+#pragma unroll
+    for (int p = 0; p < S::NP8; ++p) {
+        // exchange through shared memory into the input order of the next
+        // pass; the leading barrier also orders any reads of `buf` the caller
+        // made before the transform
+        __syncthreads();
+#pragma unroll
+        for (int m = 0; m < 8; ++m) buf[pad8(oidx[m])] = v[m];
+        __syncthreads();
+#pragma unroll
+        for (int m = 0; m < 8; ++m) v[m] = buf[pad8(t + m * Q)];
+        stockham_compute<N, 8, DIR>(v, t, Ns, tw, oidx);
+        Ns *= 8;
+    }
+    // after the last radix-8 pass (Ns = N/8 before it) oidx[m] = t + m N/8:
+    // registers already hold the natural-order output. The trailing barrier
+    // lets the caller overwrite `buf` right away.
+    __syncthreads();
+}
+
+}  // namespace admm

@@ -1,0 +1,566 @@
+// kernels.cuh -- device kernels of one ADMM iteration for a batch of problems.
+//
+// One iteration of TV-MD (Algorithm 3 with line 7 replaced by eq. new_line)
+// or FA-MD (Algorithm 2 with H1 = A, H2 = P) is split into two phases that
+// each stream the batch once through HBM:
+//
+//  column phase  (col_phase):  the row-DFTs of (zeta1, w) -> forward column
+//                 DFTs -> x^ = K (conj(Lambda) Z1^ + W^)  [eq. fast_inversion /
+//                 eq. invAnalysisp1, 1/(HW) folded into K] and (A x)^ = Lambda x^
+//                 -> inverse column DFTs -> row-DFTs of (x, A x)
+//  row phase     (row_phase_tv):  inverse row DFT -> x, A x on a strip of rows
+//                 -> mask-decoupled prox + dual update (eq. new_line, Alg. 3
+//                 line 8) -> TV differences, vector-soft, dual update (Alg. 3
+//                 lines 9-11) -> zeta1 = u1 + d1, w = gamma (Dh^T dh + Dv^T dv)
+//                 with delta = u2 + d2 (Alg. 3 lines 3-5 of the next iteration)
+//                 -> forward row DFT of the packed p = zeta1 + i w, split into
+//                 the half spectra of zeta1 and w.
+//
+// Both real signals of each phase share one complex transform: a real pair
+// (a, b) is carried as a + i b and separated with the Hermitian symmetry of
+// real-signal spectra. Only the half spectrum k_c = 0..W/2 is stored between
+// phases, as float4 (Re, Im of the first signal, Re, Im of the second).
+//
+// Persistent state per problem is the scaled dual d = (d1, d2) only; u is
+// formed on the fly (zeta = u + d, Algorithm 2 line 3).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include "fft.cuh"
+
+namespace admm {
+
+constexpr int kThreads = 256;
+constexpr int kNumPartials = 4;   // data term, regulariser sum, ||x||^2, ||x - x_prev||^2
+
+// Mutable per-problem control block.
+struct ProbCtl {
+    int iter;          // iterations completed
+    int active;        // 1 while iterating
+    int converged;
+    int status;        // 0 or ADMM_ENONFINITE
+    unsigned arrive;   // row-phase CTAs of the current iteration that finished
+    int have_obj;      // obj_prev valid
+    double obj;        // objective at the last evaluation
+    double obj_prev;
+    double rel_x;      // -1 until evaluated
+    double rel_obj;    // -1 until evaluated
+};
+
+// Per-problem constants and buffers (all device pointers).
+struct ProbDesc {
+    float4* Sa;               // H x Wp: column-phase output (row-DFTs of x, A x)
+    float4* Sb;               // H x Wp: row-phase output (row-DFTs of zeta1, w)
+    float* d1;                // H x W
+    float* d2;                // TV: H x W float2 (h, v); frame: nb x H x W
+    const float* ybar;        // H x W, M^T y (0 where unobserved)
+    const uint8_t* mask;      // H x W, 1 = observed (effective mask)
+    const float2* lamT;       // Wc x H, Lambda (column-major half spectrum)
+    const float* kT;          // Wc x H, diagonal inverse with 1/(HW) folded in
+    float* xprev;             // H x W, x of the previous iteration (rel-x rule)
+    float* work;              // frame prior: 3 x H x W scratch planes (x, zeta1, w)
+    double* partials;         // n_strips x kNumPartials
+    ProbCtl* ctl;
+    float lam, mu1, mu2, gamma, tau, inv1pmu1;
+    int stop, max_iters, check_every, n_strips;
+    double tol;
+};
+
+// stop rules (values of ADMM_STOP_*)
+constexpr int kStopIters = 0, kStopRelX = 1, kStopRelObj = 2;
+constexpr int kStatusNonFinite = -5;
+
+__device__ __forceinline__ bool is_check_iter(const ProbDesc& P, int k) {
+    return P.stop == kStopRelX && ((k % P.check_every) == 0 || k == P.max_iters);
+}
+__device__ __forceinline__ bool store_prev_iter(const ProbDesc& P, int k) {
+    return P.stop == kStopRelX && (((k + 1) % P.check_every) == 0 || k + 1 == P.max_iters);
+}
+__device__ __forceinline__ bool need_obj_iter(const ProbDesc& P, int k) {
+    return P.stop == kStopRelObj || is_check_iter(P, k) || k == P.max_iters;
+}
+
+// Neumaier-compensated FP32 accumulator
+struct CompSum {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float v) {
+        float t = s + v;
+        c += (fabsf(s) >= fabsf(v)) ? ((s - t) + v) : ((v - t) + s);
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
+// ---------------------------------------------------------------------------
+// a0: plan precompute. Lambda[kr,kc] = sum_{a,b} h[a+lr,b+lc] exp(-2 pi i (kr a/H + kc b/W))
+// (DFT of the kernel centred at (0,0), eq. DFT_fact) for the half spectrum
+// kc = 0..W/2, and the diagonal inverse of eq. fast_inversion (TV, divided by
+// mu1) or eq. invAnalysisp1 (frame), times 1/(HW). FP64, rounded once to FP32.
+// ---------------------------------------------------------------------------
+constexpr int kMaxPsfSide = 63;
+
+__global__ void spectra_kernel(float2* __restrict__ lamT, float* __restrict__ kT,
+                               const float* __restrict__ psf, int ph, int pw, int H, int W, int Wc,
+                               int reg, double gamma) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= H * Wc) return;
+    const int kc = idx / H, kr = idx % H;
+    const int lr = ph / 2, lc = pw / 2;
+    double fre[kMaxPsfSide], fim[kMaxPsfSide];
+    for (int b = -lc; b <= lc; ++b) {
+        long long m = ((long long)kc * b) % W;
+        if (m < 0) m += W;
+        double s, c;
+        sincospi(-2.0 * (double)m / (double)W, &s, &c);
+        fre[b + lc] = c;
+        fim[b + lc] = s;
+    }
+    double re = 0.0, im = 0.0;
+    for (int a = -lr; a <= lr; ++a) {
+        double sre = 0.0, sim = 0.0;
+        const float* hr = psf + (a + lr) * pw;
+        for (int b = 0; b < pw; ++b) {
+            sre += (double)hr[b] * fre[b];
+            sim += (double)hr[b] * fim[b];
+        }
+        long long m = ((long long)kr * a) % H;
+        if (m < 0) m += H;
+        double s, c;
+        sincospi(-2.0 * (double)m / (double)H, &s, &c);
+        re += sre * c - sim * s;
+        im += sre * s + sim * c;
+    }
+    double den = re * re + im * im;
+    if (reg == 0) {
+        double sh = sinpi((double)kc / (double)W), sv = sinpi((double)kr / (double)H);
+        den += gamma * 4.0 * (sh * sh + sv * sv);
+    } else {
+        den += gamma;
+    }
+    lamT[idx] = make_float2((float)re, (float)im);
+    kT[idx] = (float)(1.0 / (den * (double)H * (double)W));
+}
+
+// ---------------------------------------------------------------------------
+// Per-solve preparation: effective mask (optionally ANDed with the valid
+// region of Sec. IV-A) and M^T y (observations zero-extended, eq.
+// prox_g_1_uBC). Also zeroes the state of a cold start (u0 = d0 = 0).
+// ---------------------------------------------------------------------------
+__global__ void prepare_kernel(float* __restrict__ ybar, uint8_t* __restrict__ mask_eff,
+                               const float* __restrict__ y, const uint8_t* __restrict__ mask_in,
+                               int H, int W, int lr, int lc, int raw_mask) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= H * W) return;
+    const int r = i / W, c = i % W;
+    bool obs = (mask_in == nullptr) ? true : (mask_in[i] != 0);
+    if (!raw_mask || mask_in == nullptr)
+        obs = obs && r >= lr && r < H - lr && c >= lc && c < W - lc;
+    mask_eff[i] = obs ? 1 : 0;
+    ybar[i] = obs ? y[i] : 0.0f;
+}
+
+__global__ void init_ctl_kernel(ProbDesc* __restrict__ probs, int count) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= count) return;
+    ProbCtl* c = probs[b].ctl;
+    c->iter = 0;
+    c->active = 1;
+    c->converged = 0;
+    c->status = 0;
+    c->arrive = 0;
+    c->have_obj = 0;
+    c->obj = 0.0;
+    c->obj_prev = 0.0;
+    c->rel_x = -1.0;
+    c->rel_obj = -1.0;
+}
+
+// ---------------------------------------------------------------------------
+// Column phase. Grid: (ceil(Wc / CB), problems). CTA = CB spectrum columns of
+// one problem, whole height H.
+// ---------------------------------------------------------------------------
+template <int H, int CB>
+struct ColCfg {
+    static constexpr int FT = H / 8;                 // threads per transform
+    static constexpr int G = kThreads / FT;          // transforms in flight
+    static_assert(G >= 1 && (kThreads % FT) == 0, "H");
+    static_assert(CB % G == 0, "column block must be a multiple of the groups");
+    static constexpr int CPG = CB / G;               // columns per group
+    static constexpr int SIG = pad8(H);              // float2 per signal slot
+    static constexpr size_t SMEM = (size_t)(2 * CB * SIG + H) * sizeof(float2);
+};
+
+// Grid: (Wp / CB, problems). Wp (the stored half-spectrum width) is a
+// multiple of CB; columns >= Wc = W/2 + 1 are padding and are not read by
+// the row phase.
+template <int H, int CB>
+__global__ void __launch_bounds__(kThreads)
+col_phase(const ProbDesc* __restrict__ probs, int Wc, int Wp, const float2* __restrict__ tw_g) {
+    using C = ColCfg<H, CB>;
+    const ProbDesc& P = probs[blockIdx.y];
+    if (P.ctl->active == 0) return;
+    extern __shared__ float2 smem[];
+    float2* sig = smem;                      // 2*CB signal slots
+    float2* tw = smem + 2 * CB * C::SIG;     // H twiddles
+    const int tid = threadIdx.x;
+    const int c0 = blockIdx.x * CB;
+    for (int i = tid; i < H; i += kThreads) tw[i] = tw_g[i * (2048 / H)];
+    // load the tile: rows 0..H-1, columns c0..c0+CB-1 (coalesced along columns)
+    const float4* __restrict__ src = P.Sb;
+    for (int e = tid; e < H * CB; e += kThreads) {
+        const int r = e / CB, c = e % CB;
+        const float4 f = src[(size_t)r * Wp + c0 + c];
+        sig[(2 * c) * C::SIG + pad8(r)] = make_float2(f.x, f.y);
+        sig[(2 * c + 1) * C::SIG + pad8(r)] = make_float2(f.z, f.w);
+    }
+    __syncthreads();
+    const int g = tid / C::FT, t = tid % C::FT;
+    for (int j = 0; j < C::CPG; ++j) {
+        const int c = g + j * C::G;
+        float2 v[8], u[8];
+        float2* bz = sig + (2 * c) * C::SIG;
+        float2* bw = sig + (2 * c + 1) * C::SIG;
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+            v[m] = bz[pad8(t + m * C::FT)];
+            u[m] = bw[pad8(t + m * C::FT)];
+        }
+        fft_group<H, -1>(v, bz, tw, t);
+        fft_group<H, -1>(u, bw, tw, t);
+        const int kc = c0 + c;
+        if (kc < Wc) {
+            const float2* __restrict__ lcol = P.lamT + (size_t)kc * H;
+            const float* __restrict__ kcol = P.kT + (size_t)kc * H;
+#pragma unroll
+            for (int m = 0; m < 8; ++m) {
+                const int kr = t + m * C::FT;
+                const float2 L = lcol[kr];
+                const float Kv = kcol[kr];
+                // x^ = K (conj(Lambda) Z1^ + W^);  (A x)^ = Lambda x^
+                const float2 xh = Kv * (cmulc(v[m], L) + u[m]);
+                v[m] = xh;
+                u[m] = cmul(L, xh);
+            }
+        }
+        fft_group<H, 1>(v, bz, tw, t);
+        fft_group<H, 1>(u, bw, tw, t);
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+            bz[pad8(t + m * C::FT)] = v[m];
+            bw[pad8(t + m * C::FT)] = u[m];
+        }
+    }
+    __syncthreads();
+    float4* __restrict__ dst = P.Sa;
+    for (int e = tid; e < H * CB; e += kThreads) {
+        const int r = e / CB, c = e % CB;
+        const float2 a = sig[(2 * c) * C::SIG + pad8(r)];
+        const float2 b = sig[(2 * c + 1) * C::SIG + pad8(r)];
+        dst[(size_t)r * Wp + c0 + c] = make_float4(a.x, a.y, b.x, b.y);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Shared pieces of the row phase.
+// ---------------------------------------------------------------------------
+// Rebuild the full row spectrum of the complex row x + i (A x) from the
+// stored half spectra of the two real rows and return it in fft_group order.
+template <int W>
+__device__ __forceinline__ void load_row_xax(float2 (&v)[8], const float4* __restrict__ srow, int t) {
+    constexpr int FT = W / 8;
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+        const int k = t + m * FT;
+        if (k <= W / 2) {
+            const float4 s = srow[k];             // (X, AX) at k
+            v[m] = make_float2(s.x - s.w, s.y + s.z);
+        } else {
+            const float4 s = srow[W - k];         // X[k] = conj X[W-k], same for AX
+            v[m] = make_float2(s.x + s.w, s.z - s.y);
+        }
+    }
+}
+
+// Split the spectrum P of p = a + i b (stored natural order in `row`) into
+// the half spectra A[k] = (P[k] + conj P[W-k]) / 2, B[k] = (P[k] - conj P[W-k]) / 2i.
+template <int W>
+__device__ __forceinline__ void store_split(float4* __restrict__ drow, const float2* row, int t) {
+    constexpr int FT = W / 8;
+#pragma unroll
+    for (int m = 0; m <= 4; ++m) {
+        const int k = t + m * FT;
+        if (k > W / 2) break;
+        const float2 pk = row[pad8(k)];
+        const float2 pn = row[pad8((W - k) & (W - 1))];
+        const float2 a = 0.5f * make_float2(pk.x + pn.x, pk.y - pn.y);
+        const float2 dd = make_float2(pk.x - pn.x, pk.y + pn.y);
+        drow[k] = make_float4(a.x, a.y, 0.5f * dd.y, -0.5f * dd.x);
+    }
+}
+
+// Block reduction of kNumPartials doubles; result valid in thread 0.
+__device__ __forceinline__ void block_reduce_partials(double (&v)[kNumPartials], double* red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int j = 0; j < kNumPartials; ++j) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[j] += __shfl_down_sync(0xffffffffu, v[j], o);
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int j = 0; j < kNumPartials; ++j) red[warp * kNumPartials + j] = v[j];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < kThreads / 32; ++w) {
+#pragma unroll
+            for (int j = 0; j < kNumPartials; ++j) v[j] += red[w * kNumPartials + j];
+        }
+    }
+}
+
+// Called by thread 0 of every row-phase CTA after its partial sums are in
+// v: publishes them; the last CTA of the problem to arrive reduces all
+// strips in strip order, evaluates the stop rule of iteration k and
+// advances the problem's control block.
+__device__ void finish_iteration(const ProbDesc& P, int k, bool chk, bool nobj,
+                                 const double (&v)[kNumPartials], int* n_active) {
+    ProbCtl* ctl = P.ctl;
+#pragma unroll
+    for (int j = 0; j < kNumPartials; ++j) P.partials[blockIdx.x * kNumPartials + j] = v[j];
+    __threadfence();
+    const unsigned prev = atomicAdd(&ctl->arrive, 1u);
+    if (prev != (unsigned)(P.n_strips - 1)) return;
+    __threadfence();
+    double acc[kNumPartials] = {0.0, 0.0, 0.0, 0.0};
+    for (int s = 0; s < P.n_strips; ++s) {
+#pragma unroll
+        for (int j = 0; j < kNumPartials; ++j) acc[j] += __ldcg(P.partials + s * kNumPartials + j);
+    }
+    bool done = false, conv = false;
+    if (nobj) {
+        const double f = acc[0] + (double)P.lam * acc[1];
+        if (!isfinite(f)) {
+            ctl->status = kStatusNonFinite;
+            done = true;
+        }
+        if (P.stop == kStopRelObj && ctl->have_obj) {
+            const double ro = (f != 0.0) ? fabs(f - ctl->obj_prev) / fabs(f) : INFINITY;
+            ctl->rel_obj = ro;
+            if (ro < P.tol) conv = true;
+        }
+        ctl->obj_prev = f;
+        ctl->obj = f;
+        ctl->have_obj = 1;
+    }
+    if (chk) {
+        if (!isfinite(acc[2]) || !isfinite(acc[3])) {
+            ctl->status = kStatusNonFinite;
+            done = true;
+        }
+        const double rx = (acc[2] > 0.0) ? sqrt(acc[3] / acc[2]) : INFINITY;
+        ctl->rel_x = rx;
+        if (rx < P.tol) conv = true;
+    }
+    ctl->iter = k;
+    if (conv && !done) ctl->converged = 1;
+    if (conv || done || k >= P.max_iters) {
+        ctl->active = 0;
+        atomicSub(n_active, 1);
+    }
+    ctl->arrive = 0u;
+}
+
+// ---------------------------------------------------------------------------
+// TV row phase. Grid: (H / R, problems). CTA = strip of R rows of one
+// problem; the inverse transforms also cover one halo row above and below
+// (the forward differences and their adjoints reach one row each way).
+// ---------------------------------------------------------------------------
+template <int W, int R>
+struct RowCfg {
+    static constexpr int FT = W / 8;
+    static constexpr int G = kThreads / FT;                        // row transforms in flight
+    static constexpr int NB_INV = ((R + 2 + G - 1) / G) * G;
+    static constexpr int NB_FWD = 1 + ((R + G - 1) / G) * G;
+    static constexpr int NB = NB_INV > NB_FWD ? NB_INV : NB_FWD;  // buffer rows
+    static constexpr int ROW = pad8(W);
+    static constexpr int CPT = W >= kThreads ? W / kThreads : 1;    // columns per thread
+    static constexpr size_t SMEM = (size_t)NB * ROW * sizeof(float2) + (size_t)W * sizeof(float2)
+                                 + 2 * (size_t)W * sizeof(float) + 8 * kNumPartials * sizeof(double);
+};
+
+template <int W, int R>
+__global__ void __launch_bounds__(kThreads)
+row_phase_tv(const ProbDesc* __restrict__ probs, int H, int Wp, const float2* __restrict__ tw_g,
+             int* __restrict__ n_active) {
+    using C = RowCfg<W, R>;
+    const ProbDesc& P = probs[blockIdx.y];
+    ProbCtl* ctl = P.ctl;
+    if (ctl->active == 0) return;
+    const int k = ctl->iter + 1;                 // iteration being completed
+    const bool chk = is_check_iter(P, k), sprev = store_prev_iter(P, k), nobj = need_obj_iter(P, k);
+    extern __shared__ float2 smem[];
+    float2* buf = smem;
+    float2* tw = buf + C::NB * C::ROW;
+    float* dhs = reinterpret_cast<float*>(tw + W);
+    double* red = reinterpret_cast<double*>(dhs + 2 * W);
+    const int tid = threadIdx.x;
+    const int r0 = blockIdx.x * R;
+    for (int i = tid; i < W; i += kThreads) tw[i] = tw_g[i * (2048 / W)];
+    __syncthreads();
+    const int g = tid / C::FT, t = tid % C::FT;
+
+    // (1) x + i A x on buffer rows 0..R+1 = image rows r0-1..r0+R: inverse row DFTs
+    for (int rb = 0; rb < C::NB_INV; rb += C::G) {
+        const int i = rb + g;
+        float2 v[8];
+        if (i < R + 2) {
+            const int q = (r0 - 1 + i + H) & (H - 1);
+            load_row_xax<W>(v, P.Sa + (size_t)q * Wp, t);
+        } else {
+#pragma unroll
+            for (int m = 0; m < 8; ++m) v[m] = make_float2(0.f, 0.f);
+        }
+        float2* row = buf + i * C::ROW;
+        fft_group<W, 1>(v, row, tw, t);
+#pragma unroll
+        for (int m = 0; m < 8; ++m) row[pad8(t + m * C::FT)] = v[m];
+    }
+    __syncthreads();
+
+    // (2) proxes and dual updates, walking down the strip
+    const float tau = P.tau, gam = P.gamma, mu1 = P.mu1, inv1 = P.inv1pmu1;
+    CompSum s_data, s_reg, s_xx, s_dxx;
+    float dvprev[C::CPT], dhcur[C::CPT], dvcur[C::CPT], z1cur[C::CPT];
+#pragma unroll
+    for (int j = 0; j < C::CPT; ++j) dvprev[j] = 0.f;
+    const bool colthr = (W >= kThreads) || (tid < W);
+    float2* __restrict__ d2v = reinterpret_cast<float2*>(P.d2);
+    for (int i = 0; i <= R; ++i) {
+        const int q = (r0 - 1 + i + H) & (H - 1);
+        const bool owned = i >= 1;
+        if (colthr) {
+#pragma unroll
+            for (int j = 0; j < C::CPT; ++j) {
+                const int c = tid + j * kThreads;
+                const float2 z = buf[i * C::ROW + pad8(c)];
+                const float x = z.x, ax = z.y;
+                const float xr = buf[i * C::ROW + pad8((c + 1) & (W - 1))].x;
+                const float xd = buf[(i + 1) * C::ROW + pad8(c)].x;
+                // D_i x (forward periodic differences)
+                const float gh = xr - x, gv = xd - x;
+                const size_t pix = (size_t)q * W + c;
+                const float2 dd = d2v[pix];
+                // u2 = v-soft(D_i x - d2, lambda/mu2)  (Alg. 3 line 10, 0/0 = 0)
+                const float sh = gh - dd.x, sv = gv - dd.y;
+                const float nrm = sqrtf(fmaf(sh, sh, sv * sv));
+                const float sc = nrm > tau ? (nrm - tau) / nrm : 0.f;
+                const float uh = sc * sh, uv = sc * sv;
+                // d2 <- d2 - (D_i x - u2)  (Alg. 3 line 11)
+                const float nh = uh - sh, nv = uv - sv;
+                // delta = u2 + d2 for the next x-step (Alg. 3 lines 3-5)
+                dhcur[j] = uh + nh;
+                dvcur[j] = uv + nv;
+                if (owned) {
+                    d2v[pix] = make_float2(nh, nv);
+                    // u1 = (M^T M + mu1 I)^{-1} (M^T y + mu1 (A x - d1))  (eq. new_line)
+                    const float dd1 = P.d1[pix];
+                    const float s1 = ax - dd1;
+                    const bool obs = P.mask[pix] != 0;
+                    const float yb = P.ybar[pix];
+                    const float u1 = obs ? fmaf(mu1, s1, yb) * inv1 : s1;
+                    // d1 <- d1 - (A x - u1)  (Alg. 3 line 8)
+                    const float nd1 = dd1 - (ax - u1);
+                    P.d1[pix] = nd1;
+                    z1cur[j] = u1 + nd1;
+                    if (nobj) {
+                        if (obs) {
+                            const float e = ax - yb;
+                            s_data.add(0.5f * e * e);
+                        }
+                        s_reg.add(sqrtf(fmaf(gh, gh, gv * gv)));
+                    }
+                    if (chk) {
+                        const float dx = x - P.xprev[pix];
+                        s_dxx.add(dx * dx);
+                        s_xx.add(x * x);
+                    }
+                    if (sprev) P.xprev[pix] = x;
+                }
+                dhs[(i & 1) * W + c] = dhcur[j];
+            }
+        }
+        __syncthreads();
+        if (owned && colthr) {
+            // w = gamma (Dh^T delta_h + Dv^T delta_v): adjoint of forward differences
+#pragma unroll
+            for (int j = 0; j < C::CPT; ++j) {
+                const int c = tid + j * kThreads;
+                const float dhl = dhs[(i & 1) * W + ((c - 1) & (W - 1))];
+                const float w = gam * ((dhl - dhcur[j]) + (dvprev[j] - dvcur[j]));
+                buf[i * C::ROW + pad8(c)] = make_float2(z1cur[j], w);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < C::CPT; ++j) dvprev[j] = dvcur[j];
+    }
+    __syncthreads();
+
+    // (3) partial sums -> last CTA evaluates the stop rule
+    {
+        double v[kNumPartials] = {s_data.value(), s_reg.value(), s_xx.value(), s_dxx.value()};
+        block_reduce_partials(v, red);
+        if (tid == 0) finish_iteration(P, k, chk, nobj, v, n_active);
+    }
+
+    // (4) forward row DFTs of p = zeta1 + i w on rows 1..R and split
+    for (int rb = 1; rb < C::NB_FWD; rb += C::G) {
+        const int i = rb + g;
+        float2* row = buf + i * C::ROW;
+        float2 v[8];
+#pragma unroll
+        for (int m = 0; m < 8; ++m) v[m] = row[pad8(t + m * C::FT)];
+        fft_group<W, -1>(v, row, tw, t);
+#pragma unroll
+        for (int m = 0; m < 8; ++m) row[pad8(t + m * C::FT)] = v[m];
+        __syncthreads();
+        if (i <= R) {
+            const int q = r0 - 1 + i;
+            store_split<W>(P.Sb + (size_t)q * Wp, row, t);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Final iterate: x from the last column-phase output by inverse row DFTs.
+// Grid: (H / G, problems) with G rows per CTA.
+// ---------------------------------------------------------------------------
+template <int W>
+__global__ void __launch_bounds__(kThreads)
+finalize_x(const ProbDesc* __restrict__ probs, float* const* __restrict__ xout, int H, int Wp,
+           const float2* __restrict__ tw_g) {
+    constexpr int FT = W / 8, G = kThreads / FT, ROW = pad8(W);
+    extern __shared__ float2 smem[];
+    float2* buf = smem;
+    float2* tw = buf + G * ROW;
+    const ProbDesc& P = probs[blockIdx.y];
+    const int tid = threadIdx.x, g = tid / FT, t = tid % FT;
+    for (int i = tid; i < W; i += kThreads) tw[i] = tw_g[i * (2048 / W)];
+    __syncthreads();
+    const int q = blockIdx.x * G + g;
+    float2 v[8];
+    if (q < H) {
+        load_row_xax<W>(v, P.Sa + (size_t)q * Wp, t);
+    } else {
+#pragma unroll
+        for (int m = 0; m < 8; ++m) v[m] = make_float2(0.f, 0.f);
+    }
+    fft_group<W, 1>(v, buf + g * ROW, tw, t);
+    if (q < H) {
+        float* xo = xout[blockIdx.y] + (size_t)q * W;
+#pragma unroll
+        for (int m = 0; m < 8; ++m) xo[t + m * FT] = v[m].x;
+    }
+}
+
+}  // namespace admm

@@ -1,0 +1,85 @@
+"""Host-side checks of the C ABI that need no GPU: the library builds, loads,
+exports every function include/admm_deconv.h declares, and rejects invalid
+parameters before touching the device."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "admm_deconv.h")
+
+
+@pytest.fixture(scope="module")
+def ad():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1210_2687_gb300 as mod
+    return mod
+
+
+def _declared_functions():
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"ADMM_API\s+[\w\s\*]+?\b(admm_\w+)\s*\(", txt)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for required in ("admm_deconv_plan", "admm_deconv_solve", "admm_deconv_solve_batch",
+                     "admm_deconv_destroy", "admm_strerror"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(ad):
+    so = ctypes.CDLL(ad.LIB_PATH)
+    for name in _declared_functions():
+        assert hasattr(so, name), name
+    assert set(_declared_functions()) <= set(ad.EXPORTED)
+
+
+def test_strerror_and_version(ad):
+    assert ad.admm_strerror(0) == "ok"
+    for code in (-1, -2, -3, -4, -5, -6):
+        assert ad.admm_strerror(code) not in ("ok", "unknown status")
+    assert ad.admm_strerror(-99) == "unknown status"
+    assert "sm_103a" in ad.admm_deconv_version()
+
+
+def test_struct_layout_matches_header(ad):
+    # admm_params_t: 4 ints, pointer, 3 floats, 3 ints, double, 3 ints
+    assert ctypes.sizeof(ad.admm_params_t) == 72
+    assert ad.admm_params_t.tol.offset == 48
+    assert ctypes.sizeof(ad.admm_result_t) == 40
+
+
+@pytest.mark.parametrize("change,code", [
+    (dict(H=100), -4), (dict(W=32), -4), (dict(H=4096), -4),
+    (dict(psf=np.ones((4, 5)) / 20), -1),          # even side
+    (dict(psf=np.zeros((3, 3))), -1),              # zero DC gain
+    (dict(lam=-1.0), -1),
+    (dict(reg=7), -1), (dict(stop=9), -1),
+    (dict(max_iters=0), -1), (dict(check_every=0), -1),
+    (dict(reg="haar", levels=5), -1),
+    (dict(psf=np.ones((65, 65)) / 65 ** 2), -1),   # larger than supported kernel side
+])
+def test_plan_rejects_invalid_parameters_on_host(ad, change, code):
+    kw = dict(H=64, W=64, psf=np.ones((3, 3)) / 9, lam=1e-3, reg="tv", levels=4, stop="iters",
+              max_iters=10, check_every=1)
+    kw.update(change)
+    H, W, psf, lam = kw.pop("H"), kw.pop("W"), kw.pop("psf"), kw.pop("lam")
+    with pytest.raises(ad.AdmmError) as e:
+        ad.Plan(H, W, psf, lam, **kw)
+    assert e.value.code == code
+
+
+def test_null_arguments(ad):
+    lib = ad.lib
+    assert lib.admm_deconv_plan(None, None, None) == ad.ADMM_EINVAL
+    assert lib.admm_deconv_solve_batch(None, 1, None, None, None, None, None) == ad.ADMM_EINVAL
+    assert lib.admm_deconv_solve_batch(None, 0, None, None, None, None, None) == ad.ADMM_OK
+    assert lib.admm_deconv_solve_batch(None, -1, None, None, None, None, None) == ad.ADMM_EINVAL
+    assert lib.admm_deconv_state_size(None) == -1
+    lib.admm_deconv_destroy(None)   # no-op
