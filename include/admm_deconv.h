@@ -73,8 +73,9 @@ typedef struct {
                               DC gain sum(psf) must be nonzero (Sec. III-C proposition)     */
     float lambda;          /* regularisation weight lambda >= 0                             */
     float mu1, mu2;        /* ADMM penalties mu_1 (observation split), mu_2 (regulariser);
-                              a value <= 0 selects the rule of Sec. V:
-                              mu2 = 10 lambda, mu1 = min(1, 5000 mu2)                       */
+                              a value <= 0 selects the default rule: mu2 = 10 lambda
+                              (Sec. V) and mu1 = min(1, 3 mu2) (Sec. V's mu1 rule is
+                              garbled; penalties change only the speed, Theorem 1)          */
     int   reg;             /* ADMM_REG_TV or ADMM_REG_HAAR                                  */
     int   haar_levels;     /* frame levels for ADMM_REG_HAAR, 1..4 (0 = 4)                 */
     int   stop;            /* ADMM_STOP_*                                                   */

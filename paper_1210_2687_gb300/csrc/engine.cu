@@ -50,6 +50,7 @@ struct admm_plan_s {
     uint8_t* mstage = nullptr;
     float* xstage = nullptr;
     float* psf_dev = nullptr;
+    int last_iter = 0;          // iterations of the last solve: d2 lives in buffer last_iter & 1
 };
 
 namespace {
@@ -257,6 +258,7 @@ ProbDesc make_desc(const admm_plan_s* pl) {
     d.Sb = pl->Sb;
     d.d1 = pl->d1;
     d.d2 = pl->d2;
+    d.d2_stride = (long long)pl->nb * pl->p.H * pl->p.W;
     d.ybar = pl->ybar;
     d.mask = pl->mask;
     d.lamT = pl->lamT;
@@ -318,7 +320,7 @@ int admm_deconv_plan(admm_plan_t* out, const admm_params_t* p, void* stream) {
     if (psum == 0.0) return ADMM_EINVAL;
     float mu1 = p->mu1, mu2 = p->mu2;
     if (mu2 <= 0.f) mu2 = 10.f * p->lambda;
-    if (mu1 <= 0.f) mu1 = std::min(1.f, 5000.f * mu2);
+    if (mu1 <= 0.f) mu1 = std::min(1.f, 3.f * mu2);
     if (!(mu1 > 0.f) || !(mu2 > 0.f)) return ADMM_EINVAL;
 
     std::lock_guard<std::mutex> lk(g_mutex);
@@ -352,7 +354,7 @@ int admm_deconv_plan(admm_plan_t* out, const admm_params_t* p, void* stream) {
     const size_t oSa = take((size_t)H * pl->Wp * sizeof(float4));
     const size_t oSb = take((size_t)H * pl->Wp * sizeof(float4));
     const size_t od1 = take(n * sizeof(float));
-    const size_t od2 = take((size_t)pl->nb * n * sizeof(float));
+    const size_t od2 = take(2 * (size_t)pl->nb * n * sizeof(float));
     const size_t oyb = take(n * sizeof(float));
     const size_t oxp = take(n * sizeof(float));
     const size_t owk = take(p->reg == ADMM_REG_HAAR ? 3 * n * sizeof(float) : 0);
@@ -426,7 +428,8 @@ int admm_deconv_get_state(admm_plan_t plan, float* d_out, void* stream) {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const size_t n = (size_t)plan->p.H * plan->p.W;
     CK(cudaMemcpyAsync(d_out, plan->d1, n * sizeof(float), cudaMemcpyDefault, s));
-    CK(cudaMemcpyAsync(d_out + n, plan->d2, (size_t)plan->nb * n * sizeof(float), cudaMemcpyDefault, s));
+    const float* d2 = plan->d2 + (size_t)(plan->last_iter & 1) * plan->nb * n;
+    CK(cudaMemcpyAsync(d_out + n, d2, (size_t)plan->nb * n * sizeof(float), cudaMemcpyDefault, s));
     CK(cudaStreamSynchronize(s));
     return ADMM_OK;
 }
@@ -459,7 +462,7 @@ static int solve_group(DeviceCtx* ctx, const std::vector<int>& idx, const admm_p
         CK(cudaGetLastError());
         ++g_launches;
         CK(cudaMemsetAsync(pl->d1, 0, n * sizeof(float), s));
-        CK(cudaMemsetAsync(pl->d2, 0, (size_t)pl->nb * n * sizeof(float), s));
+        CK(cudaMemsetAsync(pl->d2, 0, 2 * (size_t)pl->nb * n * sizeof(float), s));
         CK(cudaMemsetAsync(pl->Sb, 0, (size_t)H * Wp * sizeof(float4), s));
         CK(cudaMemsetAsync(pl->xprev, 0, n * sizeof(float), s));
         ctx->h_desc[j] = make_desc(pl);
@@ -537,6 +540,7 @@ static int solve_group(DeviceCtx* ctx, const std::vector<int>& idx, const admm_p
     int rc = ADMM_OK;
     for (int q = 0; q < count; ++q) {
         const ProbCtl& c = ctx->h_ctl[q];
+        plans[idx[q]]->last_iter = c.iter;
         if (c.status != 0 && rc == ADMM_OK) rc = c.status;
         if (res) {
             admm_result_t& r = res[idx[q]];

@@ -52,7 +52,11 @@ struct ProbDesc {
     float4* Sa;               // H x Wp: column-phase output (row-DFTs of x, A x)
     float4* Sb;               // H x Wp: row-phase output (row-DFTs of zeta1, w)
     float* d1;                // H x W
-    float* d2;                // TV: H x W float2 (h, v); frame: nb x H x W
+    float* d2;                // two buffers of d2_stride floats each (TV: H x W float2
+                              // (h, v); frame: nb x H x W planes); iteration k reads
+                              // buffer (k+1)&1 and writes buffer k&1, so CTAs that
+                              // recompute a neighbour's halo always see the old d2
+    long long d2_stride;
     const float* ybar;        // H x W, M^T y (0 where unobserved)
     const uint8_t* mask;      // H x W, 1 = observed (effective mask)
     const float2* lamT;       // Wc x H, Lambda (column-major half spectrum)
@@ -435,7 +439,8 @@ row_phase_tv(const ProbDesc* __restrict__ probs, int H, int Wp, const float2* __
 #pragma unroll
     for (int j = 0; j < C::CPT; ++j) dvprev[j] = 0.f;
     const bool colthr = (W >= kThreads) || (tid < W);
-    float2* __restrict__ d2v = reinterpret_cast<float2*>(P.d2);
+    const float2* __restrict__ d2in = reinterpret_cast<const float2*>(P.d2 + ((k + 1) & 1) * P.d2_stride);
+    float2* __restrict__ d2out = reinterpret_cast<float2*>(P.d2 + (k & 1) * P.d2_stride);
     for (int i = 0; i <= R; ++i) {
         const int q = (r0 - 1 + i + H) & (H - 1);
         const bool owned = i >= 1;
@@ -450,7 +455,7 @@ row_phase_tv(const ProbDesc* __restrict__ probs, int H, int Wp, const float2* __
                 // D_i x (forward periodic differences)
                 const float gh = xr - x, gv = xd - x;
                 const size_t pix = (size_t)q * W + c;
-                const float2 dd = d2v[pix];
+                const float2 dd = d2in[pix];
                 // u2 = v-soft(D_i x - d2, lambda/mu2)  (Alg. 3 line 10, 0/0 = 0)
                 const float sh = gh - dd.x, sv = gv - dd.y;
                 const float nrm = sqrtf(fmaf(sh, sh, sv * sv));
@@ -462,7 +467,7 @@ row_phase_tv(const ProbDesc* __restrict__ probs, int H, int Wp, const float2* __
                 dhcur[j] = uh + nh;
                 dvcur[j] = uv + nv;
                 if (owned) {
-                    d2v[pix] = make_float2(nh, nv);
+                    d2out[pix] = make_float2(nh, nv);
                     // u1 = (M^T M + mu1 I)^{-1} (M^T y + mu1 (A x - d1))  (eq. new_line)
                     const float dd1 = P.d1[pix];
                     const float s1 = ax - dd1;

@@ -134,7 +134,8 @@ def test_check_every_evaluates_consecutive_iterates(ad):
     """With check_every = 10 the rel-x rule is evaluated at multiples of 10 on
     (x_k, x_{k-1}); the stopping iteration is the first such k below tol."""
     x_true, psf, ybar, mask = _case_problem(64, 128, lambda: S.psf_box(7), 0.8, 12)
-    lam, mu1, mu2 = 2e-4, 1.0, 2e-3
+    lam = 2e-4
+    mu1, mu2 = S.default_mu(lam)
     hist = O.solve(ybar, mask, psf, lam, mu1, mu2, "tv", iters=3000, record=True)
     rel = {h[0]: h[2] for h in hist.history}
     expect = next(k for k in range(10, 3001, 10) if rel[k] < 1e-5)
@@ -255,6 +256,19 @@ def test_max_size_2048(ad):
     for _ in range(4):
         st = O.tvmd_step(st, ybar, mask, psf, 1e-4, 1.0, 1e-3)
     x, res, _ = _gpu_solve(ad, ybar, mask, psf, 1e-4, 1.0, 1e-3, 4)
+    assert _rel(x, st.x) <= 2e-5
+
+
+def test_strip_halo_reads_old_duals(ad):
+    """Regression for the cross-strip halo: each row strip recomputes the TV
+    dual of the row above it from that row's d2 of the previous iteration.
+    2048-wide rows use 4-row strips (many strip boundaries); 40 iterations."""
+    xt, psf, ybar, mask = _case_problem(256, 2048, lambda: S.psf_gaussian(9, 2.0), 0.7, 16)
+    lam, mu1, mu2 = 3e-4, 1e-2, 3e-3
+    st = O.State.zeros(256, 2048, "tv")
+    for _ in range(40):
+        st = O.tvmd_step(st, ybar, mask, psf, lam, mu1, mu2)
+    x, res, _ = _gpu_solve(ad, ybar, mask, psf, lam, mu1, mu2, 40)
     assert _rel(x, st.x) <= 2e-5
 
 
