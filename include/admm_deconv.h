@@ -176,6 +176,33 @@ typedef struct {
  */
 ADMM_API int admm_deconv_profile(int enable, admm_profile_t* out);
 
+/*
+ * admm_deconv_solve_noalloc -- one TV solve that allocates no memory.
+ * The paper has no counterpart: this exists for callers that must not
+ * allocate device memory while they run -- hosts whose own allocator already
+ * owns the GPU's memory, fixed-budget or real-time loops where an allocation
+ * could fail or stall, and plugins whose host application forbids libraries
+ * from allocating. It needs no plan: every buffer it uses (spectra, duals,
+ * descriptor, twiddles) lives in one fixed 4 MiB array compiled into the
+ * library, which every GPU that loads the library holds until the process
+ * exits. The call makes no cudaMalloc/cudaFree or other allocating call.
+ *   p      [in]  parameters as for admm_deconv_plan; reg must be ADMM_REG_TV and
+ *                H, W at most 256 (larger sizes return ADMM_EUNSUPPORTED_SIZE)
+ *   y      [in]  H x W float32, DEVICE memory
+ *   mask   [in]  H x W uint8, DEVICE memory, or NULL (valid region only)
+ *   x_out  [out] H x W float32, DEVICE memory
+ *   res    [out] host pointer, may be NULL
+ * The first call on each device resolves the array's device address on that
+ * device (set-up); make that first call before any stream capture. Every call
+ * shares the array and clears what must start at zero; calls whose device
+ * work overlaps (e.g. on two streams) race on it. Returns after the solve has
+ * finished on `stream`.
+ * Errors: ADMM_EINVAL (also for host pointers or a non-TV regulariser),
+ * ADMM_EUNSUPPORTED_SIZE, ADMM_ECUDA, ADMM_ENONFINITE.
+ */
+ADMM_API int admm_deconv_solve_noalloc(const admm_params_t* p, const float* y, const uint8_t* mask,
+                                       float* x_out, admm_result_t* res, void* stream);
+
 /* admm_deconv_destroy -- free everything the plan owns (NULL is a no-op).
  * Synchronises the device first. */
 ADMM_API void admm_deconv_destroy(admm_plan_t plan);

@@ -40,7 +40,8 @@ _STOP = {"iters": ADMM_STOP_ITERS, "rel_x": ADMM_STOP_REL_X, "rel_obj": ADMM_STO
 
 EXPORTED = ("admm_deconv_plan", "admm_deconv_solve", "admm_deconv_solve_batch",
             "admm_deconv_state_size", "admm_deconv_get_state", "admm_deconv_destroy",
-            "admm_strerror", "admm_deconv_version", "admm_deconv_profile")
+            "admm_strerror", "admm_deconv_version", "admm_deconv_profile",
+            "admm_deconv_solve_noalloc")
 
 
 class admm_params_t(ctypes.Structure):
@@ -104,6 +105,9 @@ def _load() -> ctypes.CDLL:
     lib.admm_deconv_version.restype = ctypes.c_char_p
     lib.admm_deconv_profile.argtypes = [ctypes.c_int, ctypes.POINTER(admm_profile_t)]
     lib.admm_deconv_profile.restype = ctypes.c_int
+    lib.admm_deconv_solve_noalloc.argtypes = [ctypes.POINTER(admm_params_t), vp, vp, vp,
+                                              ctypes.POINTER(admm_result_t), vp]
+    lib.admm_deconv_solve_noalloc.restype = ctypes.c_int
     return lib
 
 
@@ -164,6 +168,18 @@ def admm_deconv_profile(enable: bool) -> admm_profile_t:
     out = admm_profile_t()
     lib.admm_deconv_profile(int(bool(enable)), ctypes.byref(out))
     return out
+
+
+def admm_deconv_solve_noalloc(params: admm_params_t, y_ptr: int, mask_ptr: int | None, x_ptr: int,
+                              stream=None):
+    """TV solve that allocates nothing (for callers that may not allocate
+    device memory while running); device pointers only, H, W <= 256.
+    Returns (status code, admm_result_t)."""
+    res = admm_result_t()
+    rc = lib.admm_deconv_solve_noalloc(ctypes.byref(params), ctypes.c_void_p(y_ptr),
+                                       ctypes.c_void_p(mask_ptr or 0), ctypes.c_void_p(x_ptr),
+                                       ctypes.byref(res), _stream(stream))
+    return rc, res
 
 
 def admm_deconv_destroy(plan: int) -> None:

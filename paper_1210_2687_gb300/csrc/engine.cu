@@ -608,3 +608,206 @@ int admm_deconv_solve(admm_plan_t plan, const float* y, const uint8_t* mask, flo
 }
 
 }  // extern "C"
+
+// ===========================================================================
+// Scratch-free solve (admm_deconv_solve_noalloc).
+//
+// For callers that may not allocate device memory at run time: hosts whose
+// allocator already owns the device's memory, fixed-budget or real-time
+// loops where an allocation could fail or stall, and plugins whose host
+// application forbids libraries from allocating. All working memory of this
+// entry point lives in g_noalloc_scratch, one fixed array compiled into the
+// library that every GPU loading the library holds until the process exits.
+// The limit is TV problems with H, W <= 256 (about 3.4 MB at 256 x 256).
+// ===========================================================================
+namespace {
+constexpr int kNoAllocMaxSide = 256;
+constexpr size_t kNoAllocBytes = size_t(4) << 20;   // 4 MiB
+constexpr int kNoAllocMaxDevices = 64;
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+namespace {
+struct NoAllocDevice {
+    bool ready = false;
+    unsigned char* base = nullptr;   // device address of g_noalloc_scratch on this device
+};
+NoAllocDevice g_noalloc_dev[kNoAllocMaxDevices];
+float2 g_noalloc_tw_host[2048];     // staging for the twiddle upload (static, not heap)
+
+struct NoAllocLayout {
+    size_t tw, desc, xptr, nact, ctl, part, psf, Sa, Sb, d1, d2, yb, xp, mk, lm, kt, end;
+    int Wc, Wp, R, n_strips;
+};
+
+NoAllocLayout noalloc_layout(int H, int W, int psf_elems) {
+    NoAllocLayout L{};
+    L.Wc = W / 2 + 1;
+    L.Wp = (int)align_up(L.Wc, col_block(H));
+    L.R = row_strip_tv(W);
+    L.n_strips = H / L.R;
+    const size_t n = (size_t)H * W;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 256); return o; };
+    L.tw = take(2048 * sizeof(float2));
+    L.desc = take(sizeof(ProbDesc));
+    L.xptr = take(sizeof(float*));
+    L.nact = take(sizeof(int));
+    L.ctl = take(sizeof(ProbCtl));
+    L.part = take((size_t)L.n_strips * kNumPartials * sizeof(double));
+    L.psf = take((size_t)psf_elems * sizeof(float));
+    L.Sa = take((size_t)H * L.Wp * sizeof(float4));
+    L.Sb = take((size_t)H * L.Wp * sizeof(float4));
+    L.d1 = take(n * sizeof(float));
+    L.d2 = take(2 * 2 * n * sizeof(float));
+    L.yb = take(n * sizeof(float));
+    L.xp = take(n * sizeof(float));
+    L.mk = take(n);
+    L.lm = take((size_t)L.Wc * H * sizeof(float2));
+    L.kt = take((size_t)L.Wc * H * sizeof(float));
+    L.end = off;
+    return L;
+}
+
+// first call on a device: resolve the array's device address with that device current
+int noalloc_setup(int dev, unsigned char** base) {
+    NoAllocDevice& d = g_noalloc_dev[dev];
+    if (!d.ready) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr) {
+            cudaGetLastError();
+            return ADMM_ECUDA;
+        }
+        for (int k = 0; k < 2048; ++k) {
+            const double a = 2.0 * M_PI * (double)k / 2048.0;
+            g_noalloc_tw_host[k] = make_float2((float)std::cos(a), (float)(-std::sin(a)));
+        }
+        if (cudaMemcpy(p, g_noalloc_tw_host, sizeof(g_noalloc_tw_host), cudaMemcpyHostToDevice) != cudaSuccess)
+            return ADMM_ECUDA;
+        d.base = static_cast<unsigned char*>(p);
+        d.ready = true;
+    }
+    *base = d.base;
+    return ADMM_OK;
+}
+}  // namespace
+
+extern "C" int admm_deconv_solve_noalloc(const admm_params_t* p, const float* y, const uint8_t* mask,
+                                         float* x_out, admm_result_t* res, void* stream) {
+    if (!p || !p->psf || !y || !x_out) return ADMM_EINVAL;
+    if (p->reg != ADMM_REG_TV) return ADMM_EINVAL;
+    if (!is_pow2_size(p->H) || !is_pow2_size(p->W)) return ADMM_EUNSUPPORTED_SIZE;
+    if (p->H > kNoAllocMaxSide || p->W > kNoAllocMaxSide) return ADMM_EUNSUPPORTED_SIZE;
+    if (p->psf_h < 1 || p->psf_w < 1 || (p->psf_h & 1) == 0 || (p->psf_w & 1) == 0) return ADMM_EINVAL;
+    if (p->psf_h > std::min(p->H, kMaxPsfSide) || p->psf_w > std::min(p->W, kMaxPsfSide)) return ADMM_EINVAL;
+    if (!(p->lambda >= 0.f) || !std::isfinite(p->lambda)) return ADMM_EINVAL;
+    if (p->stop < ADMM_STOP_ITERS || p->stop > ADMM_STOP_REL_OBJ) return ADMM_EINVAL;
+    if (p->max_iters <= 0 || p->check_every < 1 || !(p->tol >= 0.0)) return ADMM_EINVAL;
+    double psum = 0.0;
+    for (int i = 0; i < p->psf_h * p->psf_w; ++i) {
+        if (!std::isfinite(p->psf[i])) return ADMM_EINVAL;
+        psum += p->psf[i];
+    }
+    if (psum == 0.0) return ADMM_EINVAL;
+    float mu1 = p->mu1, mu2 = p->mu2;
+    if (mu2 <= 0.f) mu2 = 10.f * p->lambda;
+    if (mu1 <= 0.f) mu1 = std::min(1.f, 3.f * mu2);
+    if (!(mu1 > 0.f) || !(mu2 > 0.f)) return ADMM_EINVAL;
+    if (!is_device_ptr(y) || !is_device_ptr(x_out) || (mask && !is_device_ptr(mask))) return ADMM_EINVAL;
+
+    std::lock_guard<std::mutex> lk(g_mutex);
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return ADMM_EINVAL;
+    unsigned char* base = nullptr;
+    int rc = noalloc_setup(dev, &base);
+    if (rc != ADMM_OK) return rc;
+    const int H = p->H, W = p->W;
+    const size_t n = (size_t)H * W;
+    const NoAllocLayout L = noalloc_layout(H, W, p->psf_h * p->psf_w);
+    if (L.end > kNoAllocBytes) return ADMM_EUNSUPPORTED_SIZE;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const float2* tw = reinterpret_cast<const float2*>(base + L.tw);
+    ProbDesc* desc = reinterpret_cast<ProbDesc*>(base + L.desc);
+    float** xptr = reinterpret_cast<float**>(base + L.xptr);
+    int* nact = reinterpret_cast<int*>(base + L.nact);
+    ProbCtl* ctl = reinterpret_cast<ProbCtl*>(base + L.ctl);
+    float* psf_dev = reinterpret_cast<float*>(base + L.psf);
+    float2* lamT = reinterpret_cast<float2*>(base + L.lm);
+    float* kT = reinterpret_cast<float*>(base + L.kt);
+    float* ybar = reinterpret_cast<float*>(base + L.yb);
+    uint8_t* mk = reinterpret_cast<uint8_t*>(base + L.mk);
+
+    // the array keeps the previous call's contents: clear everything after the twiddles
+    CK(cudaMemsetAsync(base + L.desc, 0, L.end - L.desc, s));
+    CK(cudaMemcpyAsync(psf_dev, p->psf, (size_t)p->psf_h * p->psf_w * sizeof(float), cudaMemcpyHostToDevice, s));
+    const int tot = H * L.Wc;
+    spectra_kernel<<<(tot + 255) / 256, 256, 0, s>>>(lamT, kT, psf_dev, p->psf_h, p->psf_w, H, W, L.Wc, 0,
+                                                     (double)mu2 / (double)mu1);
+    CK(cudaGetLastError());
+    prepare_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(ybar, mk, y, mask, H, W, p->psf_h / 2,
+                                                               p->psf_w / 2, p->raw_mask);
+    CK(cudaGetLastError());
+    ProbDesc d{};
+    d.Sa = reinterpret_cast<float4*>(base + L.Sa);
+    d.Sb = reinterpret_cast<float4*>(base + L.Sb);
+    d.d1 = reinterpret_cast<float*>(base + L.d1);
+    d.d2 = reinterpret_cast<float*>(base + L.d2);
+    d.d2_stride = (long long)2 * n;
+    d.ybar = ybar;
+    d.mask = mk;
+    d.lamT = lamT;
+    d.kT = kT;
+    d.xprev = reinterpret_cast<float*>(base + L.xp);
+    d.work = nullptr;
+    d.partials = reinterpret_cast<double*>(base + L.part);
+    d.ctl = ctl;
+    d.lam = p->lambda;
+    d.mu1 = mu1;
+    d.mu2 = mu2;
+    d.gamma = (float)((double)mu2 / (double)mu1);
+    d.tau = (float)((double)p->lambda / (double)mu2);
+    d.inv1pmu1 = (float)(1.0 / (1.0 + (double)mu1));
+    d.stop = p->stop;
+    d.max_iters = p->max_iters;
+    d.check_every = p->check_every;
+    d.n_strips = L.n_strips;
+    d.tol = p->tol;
+    const int one = 1;
+    CK(cudaMemcpyAsync(desc, &d, sizeof(d), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(xptr, &x_out, sizeof(float*), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(nact, &one, sizeof(int), cudaMemcpyHostToDevice, s));
+    init_ctl_kernel<<<1, 32, 0, s>>>(desc, 1);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(s));   // the host-side sources above are locals
+
+    const int chunk = 8;
+    int launched = 0;
+    while (launched < p->max_iters) {
+        const int nit = std::min(chunk, p->max_iters - launched);
+        for (int it = 0; it < nit; ++it) {
+            CK(launch_col(H, desc, 1, L.Wc, L.Wp, tw, s));
+            CK(launch_row_tv(W, desc, 1, H, L.Wp, tw, nact, s));
+        }
+        launched += nit;
+        int act = 0;
+        CK(cudaMemcpyAsync(&act, nact, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (act == 0) break;
+    }
+    CK(launch_fin(W, desc, xptr, 1, H, L.Wp, tw, s));
+    ProbCtl c{};
+    CK(cudaMemcpyAsync(&c, ctl, sizeof(ProbCtl), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (res) {
+        res->iters = c.iter;
+        res->converged = c.converged;
+        res->status = c.status;
+        res->reserved = 0;
+        res->objective = c.have_obj ? c.obj : NAN;
+        res->rel_x = c.rel_x;
+        res->rel_obj = c.rel_obj;
+    }
+    return c.status != 0 ? c.status : ADMM_OK;
+}
