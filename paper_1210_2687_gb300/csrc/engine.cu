@@ -31,7 +31,7 @@ struct admm_plan_s {
     admm_params_t p{};
     std::vector<float> psf;
     int device = 0;
-    int Wc = 0, Wp = 0, cb = 0, R = 0, n_strips = 0, nb = 0, levels = 0;
+    int Wc = 0, Wp = 0, cb = 0, R = 0, n_strips = 0, n_slots = 0, nb = 0, levels = 0;
     float lam = 0.f, mu1 = 0.f, mu2 = 0.f;
     void* slab = nullptr;
     float4* Sa = nullptr;
@@ -277,6 +277,7 @@ ProbDesc make_desc(const admm_plan_s* pl) {
     d.max_iters = pl->p.max_iters;
     d.check_every = pl->p.check_every;
     d.n_strips = pl->n_strips;
+    d.n_slots = pl->n_slots;
     d.tol = pl->p.tol;
     return d;
 }
@@ -346,7 +347,14 @@ int admm_deconv_plan(admm_plan_t* out, const admm_params_t* p, void* stream) {
         pl->R = haar_row_strip(W);
         pl->nb = 3 * levels + 1;
     }
-    pl->n_strips = p->reg == ADMM_REG_TV ? H / pl->R : haar_num_partial_blocks(H, W);
+    if (p->reg == ADMM_REG_TV) {
+        pl->n_strips = H / pl->R;
+        pl->n_slots = pl->n_strips;
+    } else {
+        // the tile kernel finishes the iteration; it also sums the row kernel's partials
+        pl->n_strips = haar_num_tiles(H, W);
+        pl->n_slots = haar_num_row_ctas(H, W) + pl->n_strips;
+    }
 
     // one slab for everything the plan owns
     size_t off = 0;
@@ -361,7 +369,7 @@ int admm_deconv_plan(admm_plan_t* out, const admm_params_t* p, void* stream) {
     const size_t omk = take(n);
     const size_t olm = take((size_t)pl->Wc * H * sizeof(float2));
     const size_t okt = take((size_t)pl->Wc * H * sizeof(float));
-    const size_t opt = take((size_t)pl->n_strips * kNumPartials * sizeof(double));
+    const size_t opt = take((size_t)pl->n_slots * kNumPartials * sizeof(double));
     const size_t oct = take(sizeof(ProbCtl));
     const size_t oys = take(n * sizeof(float));
     const size_t oms = take(n);

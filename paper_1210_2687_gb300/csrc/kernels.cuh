@@ -66,7 +66,9 @@ struct ProbDesc {
     double* partials;         // n_strips x kNumPartials
     ProbCtl* ctl;
     float lam, mu1, mu2, gamma, tau, inv1pmu1;
-    int stop, max_iters, check_every, n_strips;
+    int stop, max_iters, check_every;
+    int n_strips;             // CTAs per problem of the kernel that finishes an iteration
+    int n_slots;              // partial-sum slots to reduce (0: n_strips)
     double tol;
 };
 
@@ -328,16 +330,17 @@ __device__ __forceinline__ void block_reduce_partials(double (&v)[kNumPartials],
 // strips in strip order, evaluates the stop rule of iteration k and
 // advances the problem's control block.
 __device__ void finish_iteration(const ProbDesc& P, int k, bool chk, bool nobj,
-                                 const double (&v)[kNumPartials], int* n_active) {
+                                 const double (&v)[kNumPartials], int* n_active, int slot) {
     ProbCtl* ctl = P.ctl;
 #pragma unroll
-    for (int j = 0; j < kNumPartials; ++j) P.partials[blockIdx.x * kNumPartials + j] = v[j];
+    for (int j = 0; j < kNumPartials; ++j) P.partials[slot * kNumPartials + j] = v[j];
     __threadfence();
     const unsigned prev = atomicAdd(&ctl->arrive, 1u);
     if (prev != (unsigned)(P.n_strips - 1)) return;
     __threadfence();
+    const int nslots = P.n_slots > 0 ? P.n_slots : P.n_strips;
     double acc[kNumPartials] = {0.0, 0.0, 0.0, 0.0};
-    for (int s = 0; s < P.n_strips; ++s) {
+    for (int s = 0; s < nslots; ++s) {
 #pragma unroll
         for (int j = 0; j < kNumPartials; ++j) acc[j] += __ldcg(P.partials + s * kNumPartials + j);
     }
@@ -515,7 +518,7 @@ row_phase_tv(const ProbDesc* __restrict__ probs, int H, int Wp, const float2* __
     {
         double v[kNumPartials] = {s_data.value(), s_reg.value(), s_xx.value(), s_dxx.value()};
         block_reduce_partials(v, red);
-        if (tid == 0) finish_iteration(P, k, chk, nobj, v, n_active);
+        if (tid == 0) finish_iteration(P, k, chk, nobj, v, n_active, blockIdx.x);
     }
 
     // (4) forward row DFTs of p = zeta1 + i w on rows 1..R and split
