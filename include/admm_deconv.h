@@ -50,7 +50,8 @@ extern "C" {
 #define ADMM_ENOMEM              -2  /* device or host allocation failed                   */
 #define ADMM_ECUDA               -3  /* a CUDA runtime call failed                         */
 #define ADMM_EUNSUPPORTED_SIZE   -4  /* H or W not in {64,...,2048} powers of two          */
-#define ADMM_ENONFINITE          -5  /* the iterate became NaN/Inf (divergence, Theorem 1) */
+#define ADMM_ENONFINITE          -5  /* an observed value or the iterate is NaN/Inf
+                                        (divergence, Theorem 1)                            */
 #define ADMM_ETIMEOUT            -6  /* a bounded device wait expired                      */
 
 /* ---- enums -------------------------------------------------------------- */

@@ -151,7 +151,7 @@ int col_block(int H) {
         default: return 2;
     }
 }
-int row_strip_tv(int W) { return W <= 512 ? 16 : (W == 1024 ? 8 : 4); }
+int row_strip_tv(int W) { return W <= 128 ? 16 : (W <= 512 ? 8 : 4); }
 
 // ---- template dispatch ---------------------------------------------------
 template <int H, int CB>
@@ -180,30 +180,32 @@ cudaError_t launch_col(int H, const ProbDesc* d, int count, int Wc, int Wp, cons
     return cudaErrorInvalidValue;
 }
 
-template <int W, int R>
+template <int W, int R, int D>
 cudaError_t launch_row_tv_t(const ProbDesc* d, int count, int H, int Wp, const float2* tw, int* n_active,
                             cudaStream_t s) {
     static bool attr = false;
-    const size_t smem = RowCfg<W, R>::SMEM;
+    const size_t smem = RowCfg<W, R, D>::SMEM;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(row_phase_tv<W, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(row_phase_tv<W, R, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
         if (e != cudaSuccess) return e;
         attr = true;
     }
     dim3 grid(H / R, count);
-    row_phase_tv<W, R><<<grid, kThreads, smem, s>>>(d, H, Wp, tw, n_active);
+    row_phase_tv<W, R, D><<<grid, kThreads, smem, s>>>(d, H, Wp, tw, n_active);
     return cudaGetLastError();
 }
 
 cudaError_t launch_row_tv(int W, const ProbDesc* d, int count, int H, int Wp, const float2* tw, int* n_active,
                           cudaStream_t s) {
     switch (W) {
-        case 64: return launch_row_tv_t<64, 16>(d, count, H, Wp, tw, n_active, s);
-        case 128: return launch_row_tv_t<128, 16>(d, count, H, Wp, tw, n_active, s);
-        case 256: return launch_row_tv_t<256, 16>(d, count, H, Wp, tw, n_active, s);
-        case 512: return launch_row_tv_t<512, 16>(d, count, H, Wp, tw, n_active, s);
-        case 1024: return launch_row_tv_t<1024, 8>(d, count, H, Wp, tw, n_active, s);
-        case 2048: return launch_row_tv_t<2048, 4>(d, count, H, Wp, tw, n_active, s);
+        // (rows per strip, walk rows in flight); must agree with row_strip_tv
+        case 64: return launch_row_tv_t<64, 16, 4>(d, count, H, Wp, tw, n_active, s);
+        case 128: return launch_row_tv_t<128, 16, 4>(d, count, H, Wp, tw, n_active, s);
+        case 256: return launch_row_tv_t<256, 8, 4>(d, count, H, Wp, tw, n_active, s);
+        case 512: return launch_row_tv_t<512, 8, 4>(d, count, H, Wp, tw, n_active, s);
+        case 1024: return launch_row_tv_t<1024, 4, 2>(d, count, H, Wp, tw, n_active, s);
+        case 2048: return launch_row_tv_t<2048, 4, 1>(d, count, H, Wp, tw, n_active, s);
     }
     return cudaErrorInvalidValue;
 }
@@ -465,8 +467,9 @@ static int solve_group(DeviceCtx* ctx, const std::vector<int>& idx, const admm_p
             mj = pl->mstage;
         }
         const int lr = pl->p.psf_h / 2, lc = pl->p.psf_w / 2;
+        CK(cudaMemsetAsync(pl->ctl, 0, sizeof(ProbCtl), s));
         prepare_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(pl->ybar, pl->mask, yj, mj, H, W, lr, lc,
-                                                                   pl->p.raw_mask);
+                                                                   pl->p.raw_mask, pl->ctl);
         CK(cudaGetLastError());
         ++g_launches;
         CK(cudaMemsetAsync(pl->d1, 0, n * sizeof(float), s));
@@ -480,11 +483,11 @@ static int solve_group(DeviceCtx* ctx, const std::vector<int>& idx, const admm_p
     }
     CK(cudaMemcpyAsync(ctx->desc, ctx->h_desc, count * sizeof(ProbDesc), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(ctx->xptr, ctx->h_xptr, count * sizeof(float*), cudaMemcpyHostToDevice, s));
-    init_ctl_kernel<<<(count + 127) / 128, 128, 0, s>>>(ctx->desc, count);
-    CK(cudaGetLastError());
-    ++g_launches;
     ctx->h_active[0] = count;
     CK(cudaMemcpyAsync(ctx->n_active, ctx->h_active, sizeof(int), cudaMemcpyHostToDevice, s));
+    init_ctl_kernel<<<(count + 127) / 128, 128, 0, s>>>(ctx->desc, count, ctx->n_active);
+    CK(cudaGetLastError());
+    ++g_launches;
     // the host buffers of the descriptor table are reused by the next group
     CK(cudaStreamSynchronize(s));
 
@@ -755,7 +758,7 @@ extern "C" int admm_deconv_solve_noalloc(const admm_params_t* p, const float* y,
                                                      (double)mu2 / (double)mu1);
     CK(cudaGetLastError());
     prepare_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(ybar, mk, y, mask, H, W, p->psf_h / 2,
-                                                               p->psf_w / 2, p->raw_mask);
+                                                               p->psf_w / 2, p->raw_mask, ctl);
     CK(cudaGetLastError());
     ProbDesc d{};
     d.Sa = reinterpret_cast<float4*>(base + L.Sa);
@@ -786,7 +789,7 @@ extern "C" int admm_deconv_solve_noalloc(const admm_params_t* p, const float* y,
     CK(cudaMemcpyAsync(desc, &d, sizeof(d), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(xptr, &x_out, sizeof(float*), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(nact, &one, sizeof(int), cudaMemcpyHostToDevice, s));
-    init_ctl_kernel<<<1, 32, 0, s>>>(desc, 1);
+    init_ctl_kernel<<<1, 32, 0, s>>>(desc, 1, nact);
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(s));   // the host-side sources above are locals
 

@@ -72,8 +72,8 @@ haar_row_inverse(const ProbDesc* __restrict__ probs, int H, int Wp, const float2
         // u1 = (M^T M + mu1 I)^{-1} (M^T y + mu1 (A x - d1)); d1 <- d1 - (A x - u1)
         const float dd1 = P.d1[pix];
         const float s1 = ax - dd1;
-        const bool obs = P.mask[pix] != 0;
         const float yb = P.ybar[pix];
+        const bool obs = is_observed(yb);
         const float u1 = obs ? fmaf(mu1, s1, yb) * inv1 : s1;
         const float nd1 = dd1 - (ax - u1);
         P.d1[pix] = nd1;

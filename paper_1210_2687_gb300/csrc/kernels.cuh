@@ -45,6 +45,8 @@ struct ProbCtl {
     double obj_prev;
     double rel_x;      // -1 until evaluated
     double rel_obj;    // -1 until evaluated
+    int input_bad;     // set by prepare_kernel: an observed value is not finite
+    int pad_;
 };
 
 // Per-problem constants and buffers (all device pointers).
@@ -58,7 +60,9 @@ struct ProbDesc {
                               // recompute a neighbour's halo always see the old d2
     long long d2_stride;
     const float* ybar;        // H x W, M^T y (0 where unobserved)
-    const uint8_t* mask;      // H x W, 1 = observed (effective mask)
+    const uint8_t* mask;      // H x W, 1 = observed (effective mask); the iteration
+                              // kernels read the same information from ybar (NaN =
+                              // unobserved), which saves the mask's byte per pixel
     const float2* lamT;       // Wc x H, Lambda (column-major half spectrum)
     const float* kT;          // Wc x H, diagonal inverse with 1/(HW) folded in
     float* xprev;             // H x W, x of the previous iteration (rel-x rule)
@@ -96,6 +100,29 @@ struct CompSum {
     }
     __device__ __forceinline__ double value() const { return (double)s + (double)c; }
 };
+
+// Asynchronous global->shared copies (cp.async); completion is tracked per
+// thread with commit/wait groups, so a thread that only reads what it copied
+// itself needs no block barrier.
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void cp_async16(void* s, const void* g) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(s)), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* s, const void* g) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_u32(s)), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* s, const void* g) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_u32(s)), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// observed pixels carry M^T y, unobserved ones a quiet NaN (eq. prox_g_1_uBC)
+__device__ __forceinline__ bool is_observed(float yb) { return yb == yb; }
 
 // ---------------------------------------------------------------------------
 // a0: plan precompute. Lambda[kr,kc] = sum_{a,b} h[a+lr,b+lc] exp(-2 pi i (kr a/H + kc b/W))
@@ -150,11 +177,13 @@ __global__ void spectra_kernel(float2* __restrict__ lamT, float* __restrict__ kT
 // ---------------------------------------------------------------------------
 // Per-solve preparation: effective mask (optionally ANDed with the valid
 // region of Sec. IV-A) and M^T y (observations zero-extended, eq.
-// prox_g_1_uBC). Also zeroes the state of a cold start (u0 = d0 = 0).
+// prox_g_1_uBC), stored as ybar with a quiet NaN on unobserved pixels. A
+// non-finite observed value marks the problem (it then retires at once with
+// ADMM_ENONFINITE). ctl must be zeroed before this kernel runs.
 // ---------------------------------------------------------------------------
 __global__ void prepare_kernel(float* __restrict__ ybar, uint8_t* __restrict__ mask_eff,
                                const float* __restrict__ y, const uint8_t* __restrict__ mask_in,
-                               int H, int W, int lr, int lc, int raw_mask) {
+                               int H, int W, int lr, int lc, int raw_mask, ProbCtl* __restrict__ ctl) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= H * W) return;
     const int r = i / W, c = i % W;
@@ -162,23 +191,27 @@ __global__ void prepare_kernel(float* __restrict__ ybar, uint8_t* __restrict__ m
     if (!raw_mask || mask_in == nullptr)
         obs = obs && r >= lr && r < H - lr && c >= lc && c < W - lc;
     mask_eff[i] = obs ? 1 : 0;
-    ybar[i] = obs ? y[i] : 0.0f;
+    const float v = obs ? y[i] : 0.0f;
+    if (obs && !isfinite(v)) atomicOr(&ctl->input_bad, 1);
+    ybar[i] = obs ? v : __int_as_float(0x7fc00000);
 }
 
-__global__ void init_ctl_kernel(ProbDesc* __restrict__ probs, int count) {
+__global__ void init_ctl_kernel(ProbDesc* __restrict__ probs, int count, int* __restrict__ n_active) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= count) return;
     ProbCtl* c = probs[b].ctl;
+    const bool bad = c->input_bad != 0;
     c->iter = 0;
-    c->active = 1;
+    c->active = bad ? 0 : 1;
     c->converged = 0;
-    c->status = 0;
+    c->status = bad ? kStatusNonFinite : 0;
     c->arrive = 0;
     c->have_obj = 0;
     c->obj = 0.0;
     c->obj_prev = 0.0;
     c->rel_x = -1.0;
     c->rel_obj = -1.0;
+    if (bad) atomicSub(n_active, 1);
 }
 
 // ---------------------------------------------------------------------------
@@ -190,79 +223,89 @@ struct ColCfg {
     static constexpr int FT = H / 8;                 // threads per transform
     static constexpr int G = kThreads / FT;          // transforms in flight
     static_assert(G >= 1 && (kThreads % FT) == 0, "H");
-    static_assert(CB % G == 0, "column block must be a multiple of the groups");
+    static_assert(CB % G == 0 && (CB & (CB - 1)) == 0, "column block");
     static constexpr int CPG = CB / G;               // columns per group
-    static constexpr int SIG = pad8(H);              // float2 per signal slot
-    static constexpr size_t SMEM = (size_t)(2 * CB * SIG + H) * sizeof(float2);
+    static constexpr int SIG = pad8(H);              // float2 per exchange buffer
+    static constexpr size_t SMEM = (size_t)H * CB * sizeof(float4) + (size_t)(G * 2 * SIG + H) * sizeof(float2);
 };
 
 // Grid: (Wp / CB, problems). Wp (the stored half-spectrum width) is a
-// multiple of CB; columns >= Wc = W/2 + 1 are padding and are not read by
-// the row phase.
+// multiple of CB; columns >= Wc = W/2 + 1 are padding, transformed but never
+// read by the row phase. The H x CB tile is staged in shared memory by
+// cp.async with row r's CB entries rotated by r, so that the column-wise
+// reads of the transforms hit distinct banks.
 template <int H, int CB>
 __global__ void __launch_bounds__(kThreads)
 col_phase(const ProbDesc* __restrict__ probs, int Wc, int Wp, const float2* __restrict__ tw_g) {
     using C = ColCfg<H, CB>;
     const ProbDesc& P = probs[blockIdx.y];
     if (P.ctl->active == 0) return;
-    extern __shared__ float2 smem[];
-    float2* sig = smem;                      // 2*CB signal slots
-    float2* tw = smem + 2 * CB * C::SIG;     // H twiddles
+    extern __shared__ float4 smem4[];
+    float4* stage = smem4;                                       // H x CB
+    float2* xb = reinterpret_cast<float2*>(stage + H * CB);      // G x 2 exchange buffers
+    float2* tw = xb + C::G * 2 * C::SIG;
     const int tid = threadIdx.x;
     const int c0 = blockIdx.x * CB;
-    for (int i = tid; i < H; i += kThreads) tw[i] = tw_g[i * (2048 / H)];
-    // load the tile: rows 0..H-1, columns c0..c0+CB-1 (coalesced along columns)
     const float4* __restrict__ src = P.Sb;
     for (int e = tid; e < H * CB; e += kThreads) {
         const int r = e / CB, c = e % CB;
-        const float4 f = src[(size_t)r * Wp + c0 + c];
-        sig[(2 * c) * C::SIG + pad8(r)] = make_float2(f.x, f.y);
-        sig[(2 * c + 1) * C::SIG + pad8(r)] = make_float2(f.z, f.w);
+        cp_async16(stage + r * CB + ((c + r) & (CB - 1)), src + (size_t)r * Wp + c0 + c);
     }
-    __syncthreads();
+    cp_async_commit();
+    for (int i = tid; i < H; i += kThreads) tw[i] = tw_g[i * (2048 / H)];
     const int g = tid / C::FT, t = tid % C::FT;
+    float2* bz = xb + (2 * g) * C::SIG;
+    float2* bw = xb + (2 * g + 1) * C::SIG;
+    cp_async_wait<0>();
+    __syncthreads();
     for (int j = 0; j < C::CPG; ++j) {
         const int c = g + j * C::G;
-        float2 v[8], u[8];
-        float2* bz = sig + (2 * c) * C::SIG;
-        float2* bw = sig + (2 * c + 1) * C::SIG;
-#pragma unroll
-        for (int m = 0; m < 8; ++m) {
-            v[m] = bz[pad8(t + m * C::FT)];
-            u[m] = bw[pad8(t + m * C::FT)];
-        }
-        fft_group<H, -1>(v, bz, tw, t);
-        fft_group<H, -1>(u, bw, tw, t);
         const int kc = c0 + c;
-        if (kc < Wc) {
+        const bool spec = kc < Wc;
+        // spectra of this column, requested before the transforms
+        float2 L[8];
+        float Kv[8];
+        if (spec) {
             const float2* __restrict__ lcol = P.lamT + (size_t)kc * H;
             const float* __restrict__ kcol = P.kT + (size_t)kc * H;
 #pragma unroll
             for (int m = 0; m < 8; ++m) {
-                const int kr = t + m * C::FT;
-                const float2 L = lcol[kr];
-                const float Kv = kcol[kr];
+                L[m] = lcol[t + m * C::FT];
+                Kv[m] = kcol[t + m * C::FT];
+            }
+        }
+        float2 v[8], u[8];
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+            const int r = t + m * C::FT;
+            const float4 f = stage[r * CB + ((c + r) & (CB - 1))];
+            v[m] = make_float2(f.x, f.y);
+            u[m] = make_float2(f.z, f.w);
+        }
+        fft_group<H, -1>(v, bz, tw, t);
+        fft_group<H, -1>(u, bw, tw, t);
+        if (spec) {
+#pragma unroll
+            for (int m = 0; m < 8; ++m) {
                 // x^ = K (conj(Lambda) Z1^ + W^);  (A x)^ = Lambda x^
-                const float2 xh = Kv * (cmulc(v[m], L) + u[m]);
+                const float2 xh = Kv[m] * (cmulc(v[m], L[m]) + u[m]);
                 v[m] = xh;
-                u[m] = cmul(L, xh);
+                u[m] = cmul(L[m], xh);
             }
         }
         fft_group<H, 1>(v, bz, tw, t);
         fft_group<H, 1>(u, bw, tw, t);
 #pragma unroll
         for (int m = 0; m < 8; ++m) {
-            bz[pad8(t + m * C::FT)] = v[m];
-            bw[pad8(t + m * C::FT)] = u[m];
+            const int r = t + m * C::FT;
+            stage[r * CB + ((c + r) & (CB - 1))] = make_float4(v[m].x, v[m].y, u[m].x, u[m].y);
         }
     }
     __syncthreads();
     float4* __restrict__ dst = P.Sa;
     for (int e = tid; e < H * CB; e += kThreads) {
         const int r = e / CB, c = e % CB;
-        const float2 a = sig[(2 * c) * C::SIG + pad8(r)];
-        const float2 b = sig[(2 * c + 1) * C::SIG + pad8(r)];
-        dst[(size_t)r * Wp + c0 + c] = make_float4(a.x, a.y, b.x, b.y);
+        dst[(size_t)r * Wp + c0 + c] = stage[r * CB + ((c + r) & (CB - 1))];
     }
 }
 
@@ -382,25 +425,35 @@ __device__ void finish_iteration(const ProbDesc& P, int k, bool chk, bool nobj,
 // TV row phase. Grid: (H / R, problems). CTA = strip of R rows of one
 // problem; the inverse transforms also cover one halo row above and below
 // (the forward differences and their adjoints reach one row each way).
+//
+// Data movement: at entry every half-spectrum row of the strip (R + 2 rows)
+// is requested with cp.async into the row buffers, and the per-pixel inputs
+// of the first D rows of the walk (d2, d1, M^T y, x_prev) into a per-thread
+// ring of D row slots; each walk step consumes one slot and refills it with
+// the row D ahead, so D rows of loads stay in flight behind the arithmetic.
 // ---------------------------------------------------------------------------
-template <int W, int R>
+template <int W, int R, int D>
 struct RowCfg {
     static constexpr int FT = W / 8;
     static constexpr int G = kThreads / FT;                        // row transforms in flight
     static constexpr int NB_INV = ((R + 2 + G - 1) / G) * G;
     static constexpr int NB_FWD = 1 + ((R + G - 1) / G) * G;
     static constexpr int NB = NB_INV > NB_FWD ? NB_INV : NB_FWD;  // buffer rows
-    static constexpr int ROW = pad8(W);
+    static constexpr int ROW = pad8(W);                            // float2 per buffer row
+    static constexpr int RAW = W / 2 + 1;                          // float4 per half-spectrum row
     static constexpr int CPT = W >= kThreads ? W / kThreads : 1;    // columns per thread
+    static constexpr int SLOT = 5 * W;                             // floats per ring slot
+    static_assert(RAW * 16 <= ROW * 8, "raw row must fit a buffer row");
     static constexpr size_t SMEM = (size_t)NB * ROW * sizeof(float2) + (size_t)W * sizeof(float2)
-                                 + 2 * (size_t)W * sizeof(float) + 8 * kNumPartials * sizeof(double);
+                                 + (size_t)D * SLOT * sizeof(float) + 2 * (size_t)W * sizeof(float)
+                                 + 8 * kNumPartials * sizeof(double);
 };
 
-template <int W, int R>
-__global__ void __launch_bounds__(kThreads)
+template <int W, int R, int D>
+__global__ void __launch_bounds__(kThreads, 2)
 row_phase_tv(const ProbDesc* __restrict__ probs, int H, int Wp, const float2* __restrict__ tw_g,
              int* __restrict__ n_active) {
-    using C = RowCfg<W, R>;
+    using C = RowCfg<W, R, D>;
     const ProbDesc& P = probs[blockIdx.y];
     ProbCtl* ctl = P.ctl;
     if (ctl->active == 0) return;
@@ -409,26 +462,60 @@ row_phase_tv(const ProbDesc* __restrict__ probs, int H, int Wp, const float2* __
     extern __shared__ float2 smem[];
     float2* buf = smem;
     float2* tw = buf + C::NB * C::ROW;
-    float* dhs = reinterpret_cast<float*>(tw + W);
+    float* ring = reinterpret_cast<float*>(tw + W);
+    float* dhs = ring + D * C::SLOT;
     double* red = reinterpret_cast<double*>(dhs + 2 * W);
     const int tid = threadIdx.x;
     const int r0 = blockIdx.x * R;
+    const bool colthr = (W >= kThreads) || (tid < W);
+    const float2* __restrict__ d2in = reinterpret_cast<const float2*>(P.d2 + ((k + 1) & 1) * P.d2_stride);
+    float2* __restrict__ d2out = reinterpret_cast<float2*>(P.d2 + (k & 1) * P.d2_stride);
+
+    // ring slot of walk row i: d2 (float2 per column), d1, M^T y, x_prev
+    auto issue = [&](int i) {
+        if (i <= R && colthr) {
+            const int q = (r0 - 1 + i + H) & (H - 1);
+            float* slot = ring + (i % D) * C::SLOT;
+#pragma unroll
+            for (int j = 0; j < C::CPT; ++j) {
+                const int c = tid + j * kThreads;
+                const size_t pix = (size_t)q * W + c;
+                cp_async8(slot + 2 * c, d2in + pix);
+                if (i >= 1) {
+                    cp_async4(slot + 2 * W + c, P.d1 + pix);
+                    cp_async4(slot + 3 * W + c, P.ybar + pix);
+                    if (chk) cp_async4(slot + 4 * W + c, P.xprev + pix);
+                }
+            }
+        }
+        cp_async_commit();   // possibly empty: keeps one group per walk row
+    };
+
+    // (0) requests: half spectra of rows r0-1 .. r0+R, then the first D walk rows
+    for (int e = tid; e < (R + 2) * C::RAW; e += kThreads) {
+        const int i = e / C::RAW, kk = e % C::RAW;
+        const int q = (r0 - 1 + i + H) & (H - 1);
+        cp_async16(reinterpret_cast<float4*>(buf + i * C::ROW) + kk, P.Sa + (size_t)q * Wp + kk);
+    }
+    cp_async_commit();
+#pragma unroll
+    for (int i = 0; i < D; ++i) issue(i);
     for (int i = tid; i < W; i += kThreads) tw[i] = tw_g[i * (2048 / W)];
+    cp_async_wait<D>();          // the spectra have landed
     __syncthreads();
     const int g = tid / C::FT, t = tid % C::FT;
 
     // (1) x + i A x on buffer rows 0..R+1 = image rows r0-1..r0+R: inverse row DFTs
     for (int rb = 0; rb < C::NB_INV; rb += C::G) {
         const int i = rb + g;
+        float2* row = buf + i * C::ROW;
         float2 v[8];
         if (i < R + 2) {
-            const int q = (r0 - 1 + i + H) & (H - 1);
-            load_row_xax<W>(v, P.Sa + (size_t)q * Wp, t);
+            load_row_xax<W>(v, reinterpret_cast<const float4*>(row), t);
         } else {
 #pragma unroll
             for (int m = 0; m < 8; ++m) v[m] = make_float2(0.f, 0.f);
         }
-        float2* row = buf + i * C::ROW;
         fft_group<W, 1>(v, row, tw, t);
 #pragma unroll
         for (int m = 0; m < 8; ++m) row[pad8(t + m * C::FT)] = v[m];
@@ -441,12 +528,11 @@ row_phase_tv(const ProbDesc* __restrict__ probs, int H, int Wp, const float2* __
     float dvprev[C::CPT], dhcur[C::CPT], dvcur[C::CPT], z1cur[C::CPT];
 #pragma unroll
     for (int j = 0; j < C::CPT; ++j) dvprev[j] = 0.f;
-    const bool colthr = (W >= kThreads) || (tid < W);
-    const float2* __restrict__ d2in = reinterpret_cast<const float2*>(P.d2 + ((k + 1) & 1) * P.d2_stride);
-    float2* __restrict__ d2out = reinterpret_cast<float2*>(P.d2 + (k & 1) * P.d2_stride);
     for (int i = 0; i <= R; ++i) {
         const int q = (r0 - 1 + i + H) & (H - 1);
         const bool owned = i >= 1;
+        cp_async_wait<D - 1>();      // this thread's copies of walk row i have landed
+        const float* slot = ring + (i % D) * C::SLOT;
         if (colthr) {
 #pragma unroll
             for (int j = 0; j < C::CPT; ++j) {
@@ -458,7 +544,7 @@ row_phase_tv(const ProbDesc* __restrict__ probs, int H, int Wp, const float2* __
                 // D_i x (forward periodic differences)
                 const float gh = xr - x, gv = xd - x;
                 const size_t pix = (size_t)q * W + c;
-                const float2 dd = d2in[pix];
+                const float2 dd = *reinterpret_cast<const float2*>(slot + 2 * c);
                 // u2 = v-soft(D_i x - d2, lambda/mu2)  (Alg. 3 line 10, 0/0 = 0)
                 const float sh = gh - dd.x, sv = gv - dd.y;
                 const float nrm = sqrtf(fmaf(sh, sh, sv * sv));
@@ -472,10 +558,10 @@ row_phase_tv(const ProbDesc* __restrict__ probs, int H, int Wp, const float2* __
                 if (owned) {
                     d2out[pix] = make_float2(nh, nv);
                     // u1 = (M^T M + mu1 I)^{-1} (M^T y + mu1 (A x - d1))  (eq. new_line)
-                    const float dd1 = P.d1[pix];
+                    const float dd1 = slot[2 * W + c];
+                    const float yb = slot[3 * W + c];
                     const float s1 = ax - dd1;
-                    const bool obs = P.mask[pix] != 0;
-                    const float yb = P.ybar[pix];
+                    const bool obs = is_observed(yb);
                     const float u1 = obs ? fmaf(mu1, s1, yb) * inv1 : s1;
                     // d1 <- d1 - (A x - u1)  (Alg. 3 line 8)
                     const float nd1 = dd1 - (ax - u1);
@@ -489,7 +575,7 @@ row_phase_tv(const ProbDesc* __restrict__ probs, int H, int Wp, const float2* __
                         s_reg.add(sqrtf(fmaf(gh, gh, gv * gv)));
                     }
                     if (chk) {
-                        const float dx = x - P.xprev[pix];
+                        const float dx = x - slot[4 * W + c];
                         s_dxx.add(dx * dx);
                         s_xx.add(x * x);
                     }
@@ -498,6 +584,7 @@ row_phase_tv(const ProbDesc* __restrict__ probs, int H, int Wp, const float2* __
                 dhs[(i & 1) * W + c] = dhcur[j];
             }
         }
+        issue(i + D);                // slot (i % D) is consumed: refill it D rows ahead
         __syncthreads();
         if (owned && colthr) {
             // w = gamma (Dh^T delta_h + Dv^T delta_v): adjoint of forward differences
@@ -512,6 +599,7 @@ row_phase_tv(const ProbDesc* __restrict__ probs, int H, int Wp, const float2* __
 #pragma unroll
         for (int j = 0; j < C::CPT; ++j) dvprev[j] = dvcur[j];
     }
+    cp_async_wait<0>();              // only empty groups remain; nothing left in flight
     __syncthreads();
 
     // (3) partial sums -> last CTA evaluates the stop rule
