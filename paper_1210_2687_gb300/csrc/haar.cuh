@@ -48,7 +48,7 @@ haar_row_inverse(const ProbDesc* __restrict__ probs, int H, int Wp, const float2
     if (P.ctl->active == 0) return;
     const int k = P.ctl->iter + 1;
     const bool chk = is_check_iter(P, k), sprev = store_prev_iter(P, k), nobj = need_obj_iter(P, k);
-    extern __shared__ float2 smem[];
+    extern __shared__ __align__(16) float2 smem[];
     float2* buf = smem;
     float2* tw = buf + G * ROW;
     double* red = reinterpret_cast<double*>(tw + W);
@@ -113,7 +113,10 @@ struct HaarTileCfg {
         return o;
     }
     static constexpr int ZTOT = zoff(L);
-    static constexpr size_t SMEM = (size_t)(2 * XD * XD + ZTOT) * sizeof(float) + 8 * kNumPartials * sizeof(double);
+    // the FP64 reduction scratch follows the float arrays: round up to 8 bytes
+    static constexpr int RED_OFF = (2 * XD * XD + ZTOT + 1) & ~1;   // in floats
+    static_assert((RED_OFF * sizeof(float)) % sizeof(double) == 0, "double alignment");
+    static constexpr size_t SMEM = (size_t)RED_OFF * sizeof(float) + 8 * kNumPartials * sizeof(double);
 };
 
 __device__ __forceinline__ float soft_thresh(float v, float t) {
@@ -131,11 +134,11 @@ haar_tile(const ProbDesc* __restrict__ probs, int H, int W, int n_row_ctas, int*
     if (ctl->active == 0) return;
     const int k = ctl->iter + 1;
     const bool chk = is_check_iter(P, k), nobj = need_obj_iter(P, k);
-    extern __shared__ float sm[];
+    extern __shared__ __align__(16) float sm[];
     float* A0 = sm;
     float* A1 = A0 + XD * XD;
     float* Z = A1 + XD * XD;
-    double* red = reinterpret_cast<double*>(Z + C::ZTOT);
+    double* red = reinterpret_cast<double*>(sm + C::RED_OFF);
     const int tid = threadIdx.x;
     const int tiles_x = W / T;
     const int R0 = (blockIdx.x / tiles_x) * T, C0 = (blockIdx.x % tiles_x) * T;
@@ -259,7 +262,7 @@ haar_row_forward(const ProbDesc* __restrict__ probs, int H, int Wp, const float2
     constexpr int FT = W / 8, G = kThreads / FT, ROW = pad8(W);
     const ProbDesc& P = probs[blockIdx.y];
     if (P.ctl->active == 0) return;
-    extern __shared__ float2 smem[];
+    extern __shared__ __align__(16) float2 smem[];
     float2* buf = smem;
     float2* tw = buf + G * ROW;
     const int tid = threadIdx.x, g = tid / FT, t = tid % FT;

@@ -240,7 +240,7 @@ col_phase(const ProbDesc* __restrict__ probs, int Wc, int Wp, const float2* __re
     using C = ColCfg<H, CB>;
     const ProbDesc& P = probs[blockIdx.y];
     if (P.ctl->active == 0) return;
-    extern __shared__ float4 smem4[];
+    extern __shared__ __align__(16) float4 smem4[];
     float4* stage = smem4;                                       // H x CB
     float2* xb = reinterpret_cast<float2*>(stage + H * CB);      // G x 2 exchange buffers
     float2* tw = xb + C::G * 2 * C::SIG;
@@ -444,6 +444,9 @@ struct RowCfg {
     static constexpr int CPT = W >= kThreads ? W / kThreads : 1;    // columns per thread
     static constexpr int SLOT = 5 * W;                             // floats per ring slot
     static_assert(RAW * 16 <= ROW * 8, "raw row must fit a buffer row");
+    static_assert(((size_t)NB * ROW * 8 + (size_t)W * 8 + (size_t)D * SLOT * 4 + 2 * (size_t)W * 4) % 8 == 0,
+                  "double alignment of the reduction scratch");
+    static_assert(((size_t)NB * ROW * 8 + (size_t)W * 8) % 16 == 0, "ring alignment");
     static constexpr size_t SMEM = (size_t)NB * ROW * sizeof(float2) + (size_t)W * sizeof(float2)
                                  + (size_t)D * SLOT * sizeof(float) + 2 * (size_t)W * sizeof(float)
                                  + 8 * kNumPartials * sizeof(double);
@@ -459,7 +462,7 @@ row_phase_tv(const ProbDesc* __restrict__ probs, int H, int Wp, const float2* __
     if (ctl->active == 0) return;
     const int k = ctl->iter + 1;                 // iteration being completed
     const bool chk = is_check_iter(P, k), sprev = store_prev_iter(P, k), nobj = need_obj_iter(P, k);
-    extern __shared__ float2 smem[];
+    extern __shared__ __align__(16) float2 smem[];
     float2* buf = smem;
     float2* tw = buf + C::NB * C::ROW;
     float* ring = reinterpret_cast<float*>(tw + W);
@@ -636,7 +639,7 @@ __global__ void __launch_bounds__(kThreads)
 finalize_x(const ProbDesc* __restrict__ probs, float* const* __restrict__ xout, int H, int Wp,
            const float2* __restrict__ tw_g) {
     constexpr int FT = W / 8, G = kThreads / FT, ROW = pad8(W);
-    extern __shared__ float2 smem[];
+    extern __shared__ __align__(16) float2 smem[];
     float2* buf = smem;
     float2* tw = buf + G * ROW;
     const ProbDesc& P = probs[blockIdx.y];
