@@ -155,6 +155,18 @@ ADMM_API long long admm_deconv_state_size(admm_plan_t plan);
  */
 ADMM_API int admm_deconv_get_state(admm_plan_t plan, float* d_out, void* stream);
 
+/* Options (admm_deconv_set_option); not in the paper. */
+#define ADMM_OPT_MAX_SLOTS 1   /* value > 0: at most this many problems of a size class
+                                  iterate at once in admm_deconv_solve_batch; the rest
+                                  wait in a queue and start as problems retire.
+                                  0 (default): chosen from the launch size            */
+
+/*
+ * admm_deconv_set_option -- set a library-wide option (see ADMM_OPT_*).
+ * Errors: ADMM_EINVAL for an unknown option or a negative value.
+ */
+ADMM_API int admm_deconv_set_option(int option, long long value);
+
 /* Device-time counters of the solver's launches (observability; not in the paper). */
 typedef struct {
     double    col_ms;            /* summed device time of column-phase launches          */

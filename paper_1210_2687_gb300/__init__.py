@@ -41,7 +41,9 @@ _STOP = {"iters": ADMM_STOP_ITERS, "rel_x": ADMM_STOP_REL_X, "rel_obj": ADMM_STO
 EXPORTED = ("admm_deconv_plan", "admm_deconv_solve", "admm_deconv_solve_batch",
             "admm_deconv_state_size", "admm_deconv_get_state", "admm_deconv_destroy",
             "admm_strerror", "admm_deconv_version", "admm_deconv_profile",
-            "admm_deconv_solve_noalloc")
+            "admm_deconv_solve_noalloc", "admm_deconv_set_option")
+
+ADMM_OPT_MAX_SLOTS = 1
 
 
 class admm_params_t(ctypes.Structure):
@@ -108,6 +110,8 @@ def _load() -> ctypes.CDLL:
     lib.admm_deconv_solve_noalloc.argtypes = [ctypes.POINTER(admm_params_t), vp, vp, vp,
                                               ctypes.POINTER(admm_result_t), vp]
     lib.admm_deconv_solve_noalloc.restype = ctypes.c_int
+    lib.admm_deconv_set_option.argtypes = [ctypes.c_int, ctypes.c_longlong]
+    lib.admm_deconv_set_option.restype = ctypes.c_int
     return lib
 
 
@@ -180,6 +184,12 @@ def admm_deconv_solve_noalloc(params: admm_params_t, y_ptr: int, mask_ptr: int |
                                        ctypes.c_void_p(mask_ptr or 0), ctypes.c_void_p(x_ptr),
                                        ctypes.byref(res), _stream(stream))
     return rc, res
+
+
+def admm_deconv_set_option(option: int, value: int) -> None:
+    rc = lib.admm_deconv_set_option(int(option), int(value))
+    if rc != ADMM_OK:
+        raise AdmmError(rc, "admm_deconv_set_option")
 
 
 def admm_deconv_destroy(plan: int) -> None:

@@ -64,6 +64,8 @@ struct DeviceCtx {
     float** xptr = nullptr;          // finalize destinations
     int cap = 0;
     int* n_active = nullptr;
+    int* queue = nullptr;            // next problem of the pool to start
+    int* slot_map = nullptr;         // problem index per launch slot (cap entries)
     int* h_active = nullptr;         // pinned, 2 slots
     ProbCtl* h_ctl = nullptr;        // pinned copy-back area
     ProbDesc* h_desc = nullptr;      // pinned staging for the table
@@ -79,6 +81,7 @@ struct Profile {
 } g_prof;
 
 long long g_launches = 0;            // every kernel launched (under g_mutex)
+int g_max_slots = 0;                 // ADMM_OPT_MAX_SLOTS
 
 int prof_event(size_t i, cudaStream_t s) {
     while (g_prof.ev.size() <= i) {
@@ -115,6 +118,7 @@ int ensure_ctx(int dev, int count, DeviceCtx** out) {
         CK(cudaMalloc(&c.tw, 2048 * sizeof(float2)));
         CK(cudaMemcpy(c.tw, tw.data(), 2048 * sizeof(float2), cudaMemcpyHostToDevice));
         CK(cudaMalloc(&c.n_active, sizeof(int)));
+        CK(cudaMalloc(&c.queue, sizeof(int)));
         CK(cudaHostAlloc(&c.h_active, 2 * sizeof(int), cudaHostAllocDefault));
         CK(cudaEventCreateWithFlags(&c.ev[0], cudaEventDisableTiming));
         CK(cudaEventCreateWithFlags(&c.ev[1], cudaEventDisableTiming));
@@ -124,12 +128,15 @@ int ensure_ctx(int dev, int count, DeviceCtx** out) {
         int cap = std::max(count, 2 * c.cap);
         if (c.desc) cudaFree(c.desc);
         if (c.xptr) cudaFree(c.xptr);
+        if (c.slot_map) cudaFree(c.slot_map);
         if (c.h_ctl) cudaFreeHost(c.h_ctl);
         if (c.h_desc) cudaFreeHost(c.h_desc);
         if (c.h_xptr) cudaFreeHost(c.h_xptr);
         c.desc = nullptr; c.xptr = nullptr; c.h_ctl = nullptr; c.h_desc = nullptr; c.h_xptr = nullptr;
+        c.slot_map = nullptr;
         c.cap = 0;
         CK(cudaMalloc(&c.desc, cap * sizeof(ProbDesc)));
+        CK(cudaMalloc(&c.slot_map, cap * sizeof(int)));
         CK(cudaMalloc(&c.xptr, cap * sizeof(float*)));
         CK(cudaHostAlloc(&c.h_ctl, cap * sizeof(ProbCtl), cudaHostAllocDefault));
         CK(cudaHostAlloc(&c.h_desc, cap * sizeof(ProbDesc), cudaHostAllocDefault));
@@ -153,9 +160,19 @@ int col_block(int H) {
 }
 int row_strip_tv(int W) { return W <= 128 ? 16 : (W <= 512 ? 8 : 4); }
 
+// launch slots of a group: enough problems in flight that a row-side launch
+// has about 2400 CTAs (some eight waves of two CTAs per SM on 152 SMs)
+int choose_slots(int H, int W, bool tv, int count) {
+    const int per = tv ? H / row_strip_tv(W) : haar_num_tiles(H, W);
+    int want = (2400 + per - 1) / per;
+    if (g_max_slots > 0) want = std::min(want, g_max_slots);
+    return std::max(1, std::min(count, want));
+}
+
 // ---- template dispatch ---------------------------------------------------
 template <int H, int CB>
-cudaError_t launch_col_t(const ProbDesc* d, int count, int Wc, int Wp, const float2* tw, cudaStream_t s) {
+cudaError_t launch_col_t(const ProbDesc* d, SlotTable sl, int count, int Wc, int Wp, const float2* tw,
+                         cudaStream_t s) {
     static bool attr = false;
     const size_t smem = ColCfg<H, CB>::SMEM;
     if (!attr) {
@@ -164,25 +181,26 @@ cudaError_t launch_col_t(const ProbDesc* d, int count, int Wc, int Wp, const flo
         attr = true;
     }
     dim3 grid(Wp / CB, count);
-    col_phase<H, CB><<<grid, kThreads, smem, s>>>(d, Wc, Wp, tw);
+    col_phase<H, CB><<<grid, kThreads, smem, s>>>(d, sl, Wc, Wp, tw);
     return cudaGetLastError();
 }
 
-cudaError_t launch_col(int H, const ProbDesc* d, int count, int Wc, int Wp, const float2* tw, cudaStream_t s) {
+cudaError_t launch_col(int H, const ProbDesc* d, SlotTable sl, int count, int Wc, int Wp, const float2* tw,
+                       cudaStream_t s) {
     switch (H) {
-        case 64: return launch_col_t<64, 32>(d, count, Wc, Wp, tw, s);
-        case 128: return launch_col_t<128, 16>(d, count, Wc, Wp, tw, s);
-        case 256: return launch_col_t<256, 8>(d, count, Wc, Wp, tw, s);
-        case 512: return launch_col_t<512, 4>(d, count, Wc, Wp, tw, s);
-        case 1024: return launch_col_t<1024, 4>(d, count, Wc, Wp, tw, s);
-        case 2048: return launch_col_t<2048, 2>(d, count, Wc, Wp, tw, s);
+        case 64: return launch_col_t<64, 32>(d, sl, count, Wc, Wp, tw, s);
+        case 128: return launch_col_t<128, 16>(d, sl, count, Wc, Wp, tw, s);
+        case 256: return launch_col_t<256, 8>(d, sl, count, Wc, Wp, tw, s);
+        case 512: return launch_col_t<512, 4>(d, sl, count, Wc, Wp, tw, s);
+        case 1024: return launch_col_t<1024, 4>(d, sl, count, Wc, Wp, tw, s);
+        case 2048: return launch_col_t<2048, 2>(d, sl, count, Wc, Wp, tw, s);
     }
     return cudaErrorInvalidValue;
 }
 
 template <int W, int R, int D>
-cudaError_t launch_row_tv_t(const ProbDesc* d, int count, int H, int Wp, const float2* tw, int* n_active,
-                            cudaStream_t s) {
+cudaError_t launch_row_tv_t(const ProbDesc* d, SlotTable sl, int count, int H, int Wp, const float2* tw,
+                            int* n_active, cudaStream_t s) {
     static bool attr = false;
     const size_t smem = RowCfg<W, R, D>::SMEM;
     if (!attr) {
@@ -192,20 +210,20 @@ cudaError_t launch_row_tv_t(const ProbDesc* d, int count, int H, int Wp, const f
         attr = true;
     }
     dim3 grid(H / R, count);
-    row_phase_tv<W, R, D><<<grid, kThreads, smem, s>>>(d, H, Wp, tw, n_active);
+    row_phase_tv<W, R, D><<<grid, kThreads, smem, s>>>(d, sl, H, Wp, tw, n_active);
     return cudaGetLastError();
 }
 
-cudaError_t launch_row_tv(int W, const ProbDesc* d, int count, int H, int Wp, const float2* tw, int* n_active,
-                          cudaStream_t s) {
+cudaError_t launch_row_tv(int W, const ProbDesc* d, SlotTable sl, int count, int H, int Wp, const float2* tw,
+                          int* n_active, cudaStream_t s) {
     switch (W) {
         // (rows per strip, walk rows in flight); must agree with row_strip_tv
-        case 64: return launch_row_tv_t<64, 16, 4>(d, count, H, Wp, tw, n_active, s);
-        case 128: return launch_row_tv_t<128, 16, 4>(d, count, H, Wp, tw, n_active, s);
-        case 256: return launch_row_tv_t<256, 8, 4>(d, count, H, Wp, tw, n_active, s);
-        case 512: return launch_row_tv_t<512, 8, 4>(d, count, H, Wp, tw, n_active, s);
-        case 1024: return launch_row_tv_t<1024, 4, 2>(d, count, H, Wp, tw, n_active, s);
-        case 2048: return launch_row_tv_t<2048, 4, 1>(d, count, H, Wp, tw, n_active, s);
+        case 64: return launch_row_tv_t<64, 16, 4>(d, sl, count, H, Wp, tw, n_active, s);
+        case 128: return launch_row_tv_t<128, 16, 4>(d, sl, count, H, Wp, tw, n_active, s);
+        case 256: return launch_row_tv_t<256, 8, 4>(d, sl, count, H, Wp, tw, n_active, s);
+        case 512: return launch_row_tv_t<512, 8, 4>(d, sl, count, H, Wp, tw, n_active, s);
+        case 1024: return launch_row_tv_t<1024, 4, 2>(d, sl, count, H, Wp, tw, n_active, s);
+        case 2048: return launch_row_tv_t<2048, 4, 1>(d, sl, count, H, Wp, tw, n_active, s);
     }
     return cudaErrorInvalidValue;
 }
@@ -472,10 +490,6 @@ static int solve_group(DeviceCtx* ctx, const std::vector<int>& idx, const admm_p
                                                                    pl->p.raw_mask, pl->ctl);
         CK(cudaGetLastError());
         ++g_launches;
-        CK(cudaMemsetAsync(pl->d1, 0, n * sizeof(float), s));
-        CK(cudaMemsetAsync(pl->d2, 0, 2 * (size_t)pl->nb * n * sizeof(float), s));
-        CK(cudaMemsetAsync(pl->Sb, 0, (size_t)H * Wp * sizeof(float4), s));
-        CK(cudaMemsetAsync(pl->xprev, 0, n * sizeof(float), s));
         ctx->h_desc[j] = make_desc(pl);
         x_host[j] = !is_device_ptr(x_out[idx[j]]);
         ctx->h_xptr[j] = x_host[j] ? pl->xstage : x_out[idx[j]];
@@ -487,10 +501,21 @@ static int solve_group(DeviceCtx* ctx, const std::vector<int>& idx, const admm_p
     CK(cudaMemcpyAsync(ctx->n_active, ctx->h_active, sizeof(int), cudaMemcpyHostToDevice, s));
     init_ctl_kernel<<<(count + 127) / 128, 128, 0, s>>>(ctx->desc, count, ctx->n_active);
     CK(cudaGetLastError());
-    ++g_launches;
+    const int nslots = choose_slots(H, W, tv, count);
+    const SlotTable sl{ctx->slot_map, ctx->queue, count};
+    assign_slots_kernel<<<1, 32, 0, s>>>(ctx->desc, sl, nslots);
+    CK(cudaGetLastError());
+    g_launches += 2;
     // the host buffers of the descriptor table are reused by the next group
     CK(cudaStreamSynchronize(s));
 
+    // with more problems than slots, problems start as slots free up: the
+    // launches needed are bounded by the sum of the per-slot work
+    long long launch_cap = 0;
+    for (int q = 0; q < count; ++q) launch_cap += plans[idx[q]]->p.max_iters;
+    launch_cap = (launch_cap + nslots - 1) / nslots + max_iters;
+    if (launch_cap > (long long)INT32_MAX) launch_cap = INT32_MAX;
+    max_iters = (int)launch_cap;
     const int chunk = 8;
     const bool prof = g_prof.on;
     size_t nev = 0;
@@ -502,17 +527,18 @@ static int solve_group(DeviceCtx* ctx, const std::vector<int>& idx, const admm_p
     while (launched < max_iters) {
         const int nit = std::min(chunk, max_iters - launched);
         for (int it = 0; it < nit; ++it) {
-            CK(launch_col(H, ctx->desc, count, Wc, Wp, ctx->tw, s));
+            CK(launch_col(H, ctx->desc, sl, nslots, Wc, Wp, ctx->tw, s));
             ++g_launches;
             if (prof) {
                 int r = prof_event(nev++, s);
                 if (r != ADMM_OK) return r;
             }
             if (tv) {
-                CK(launch_row_tv(W, ctx->desc, count, H, Wp, ctx->tw, ctx->n_active, s));
+                CK(launch_row_tv(W, ctx->desc, sl, nslots, H, Wp, ctx->tw, ctx->n_active, s));
                 ++g_launches;
             } else {
-                CK(launch_haar_iteration_rows(W, H, Wp, ctx->desc, count, p0->levels, ctx->tw, ctx->n_active, s));
+                CK(launch_haar_iteration_rows(W, H, Wp, ctx->desc, sl, nslots, p0->levels, ctx->tw, ctx->n_active,
+                                              s));
                 g_launches += 3;
             }
             if (prof) {
@@ -600,6 +626,16 @@ int admm_deconv_solve_batch(const admm_plan_t* plans, int count, const float* co
     return first_err;
 }
 
+int admm_deconv_set_option(int option, long long value) {
+    std::lock_guard<std::mutex> lk(g_mutex);
+    if (option == ADMM_OPT_MAX_SLOTS) {
+        if (value < 0 || value > INT32_MAX) return ADMM_EINVAL;
+        g_max_slots = (int)value;
+        return ADMM_OK;
+    }
+    return ADMM_EINVAL;
+}
+
 int admm_deconv_profile(int enable, admm_profile_t* out) {
     std::lock_guard<std::mutex> lk(g_mutex);
     if (out) {
@@ -648,7 +684,7 @@ NoAllocDevice g_noalloc_dev[kNoAllocMaxDevices];
 float2 g_noalloc_tw_host[2048];     // staging for the twiddle upload (static, not heap)
 
 struct NoAllocLayout {
-    size_t tw, desc, xptr, nact, ctl, part, psf, Sa, Sb, d1, d2, yb, xp, mk, lm, kt, end;
+    size_t tw, desc, xptr, nact, slots, ctl, part, psf, Sa, Sb, d1, d2, yb, xp, mk, lm, kt, end;
     int Wc, Wp, R, n_strips;
 };
 
@@ -665,6 +701,7 @@ NoAllocLayout noalloc_layout(int H, int W, int psf_elems) {
     L.desc = take(sizeof(ProbDesc));
     L.xptr = take(sizeof(float*));
     L.nact = take(sizeof(int));
+    L.slots = take(2 * sizeof(int));   // slot map (one slot) and queue head
     L.ctl = take(sizeof(ProbCtl));
     L.part = take((size_t)L.n_strips * kNumPartials * sizeof(double));
     L.psf = take((size_t)psf_elems * sizeof(float));
@@ -791,6 +828,10 @@ extern "C" int admm_deconv_solve_noalloc(const admm_params_t* p, const float* y,
     CK(cudaMemcpyAsync(nact, &one, sizeof(int), cudaMemcpyHostToDevice, s));
     init_ctl_kernel<<<1, 32, 0, s>>>(desc, 1, nact);
     CK(cudaGetLastError());
+    int* slot_words = reinterpret_cast<int*>(base + L.slots);
+    const SlotTable sl{slot_words, slot_words + 1, 1};
+    assign_slots_kernel<<<1, 32, 0, s>>>(desc, sl, 1);
+    CK(cudaGetLastError());
     CK(cudaStreamSynchronize(s));   // the host-side sources above are locals
 
     const int chunk = 8;
@@ -798,8 +839,8 @@ extern "C" int admm_deconv_solve_noalloc(const admm_params_t* p, const float* y,
     while (launched < p->max_iters) {
         const int nit = std::min(chunk, p->max_iters - launched);
         for (int it = 0; it < nit; ++it) {
-            CK(launch_col(H, desc, 1, L.Wc, L.Wp, tw, s));
-            CK(launch_row_tv(W, desc, 1, H, L.Wp, tw, nact, s));
+            CK(launch_col(H, desc, sl, 1, L.Wc, L.Wp, tw, s));
+            CK(launch_row_tv(W, desc, sl, 1, H, L.Wp, tw, nact, s));
         }
         launched += nit;
         int act = 0;

@@ -42,11 +42,14 @@ inline int haar_num_tiles(int H, int W) { return (H / kHaarTile) * (W / kHaarTil
 // ---------------------------------------------------------------------------
 template <int W>
 __global__ void __launch_bounds__(kThreads)
-haar_row_inverse(const ProbDesc* __restrict__ probs, int H, int Wp, const float2* __restrict__ tw_g) {
+haar_row_inverse(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp, const float2* __restrict__ tw_g) {
     constexpr int FT = W / 8, G = kThreads / FT, ROW = pad8(W);
-    const ProbDesc& P = probs[blockIdx.y];
+    const int pi = sl.map[blockIdx.y];
+    if (pi < 0) return;
+    const ProbDesc& P = probs[pi];
     if (P.ctl->active == 0) return;
     const int k = P.ctl->iter + 1;
+    const bool first = k == 1;                   // d1 = x_prev = 0 (cold start)
     const bool chk = is_check_iter(P, k), sprev = store_prev_iter(P, k), nobj = need_obj_iter(P, k);
     extern __shared__ __align__(16) float2 smem[];
     float2* buf = smem;
@@ -70,7 +73,7 @@ haar_row_inverse(const ProbDesc* __restrict__ probs, int H, int Wp, const float2
         const size_t pix = (size_t)q * W + c;
         const float x = v[m].x, ax = v[m].y;
         // u1 = (M^T M + mu1 I)^{-1} (M^T y + mu1 (A x - d1)); d1 <- d1 - (A x - u1)
-        const float dd1 = P.d1[pix];
+        const float dd1 = first ? 0.f : P.d1[pix];
         const float s1 = ax - dd1;
         const float yb = P.ybar[pix];
         const bool obs = is_observed(yb);
@@ -84,7 +87,7 @@ haar_row_inverse(const ProbDesc* __restrict__ probs, int H, int Wp, const float2
             s_data.add(0.5f * e * e);
         }
         if (chk) {
-            const float dx = x - P.xprev[pix];
+            const float dx = first ? x : x - P.xprev[pix];
             s_dxx.add(dx * dx);
             s_xx.add(x * x);
         }
@@ -126,13 +129,16 @@ __device__ __forceinline__ float soft_thresh(float v, float t) {
 
 template <int L>
 __global__ void __launch_bounds__(kThreads)
-haar_tile(const ProbDesc* __restrict__ probs, int H, int W, int n_row_ctas, int* __restrict__ n_active) {
+haar_tile(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W, int n_row_ctas, int* __restrict__ n_active) {
     using C = HaarTileCfg<L>;
     constexpr int T = C::T, HALO = C::HALO, XD = C::XD;
-    const ProbDesc& P = probs[blockIdx.y];
+    const int pi = sl.map[blockIdx.y];
+    if (pi < 0) return;
+    const ProbDesc& P = probs[pi];
     ProbCtl* ctl = P.ctl;
     if (ctl->active == 0) return;
     const int k = ctl->iter + 1;
+    const bool first = k == 1;                   // d2 = 0 (cold start)
     const bool chk = is_check_iter(P, k), nobj = need_obj_iter(P, k);
     extern __shared__ __align__(16) float sm[];
     float* A0 = sm;
@@ -182,7 +188,7 @@ haar_tile(const ProbDesc* __restrict__ probs, int H, int W, int n_row_ctas, int*
 #pragma unroll
                 for (int j = 0; j < 3; ++j) {
                     const size_t bi = (size_t)(3 * lvl + j) * n + gpix;
-                    const float sv = cb[j] - d2in[bi];
+                    const float sv = first ? cb[j] : cb[j] - d2in[bi];
                     const float u = soft_thresh(sv, tau);
                     const float nd = u - sv;                   // d2 - (c - u2)
                     Zl[j * BD * BD + iz] = u + nd;              // zeta2 = u2 + d2
@@ -205,7 +211,7 @@ haar_tile(const ProbDesc* __restrict__ probs, int H, int W, int n_row_ctas, int*
             const float cb = Ain[i];
             const size_t gpix = (size_t)((R0 + r) & (H - 1)) * W + ((C0 + c) & (W - 1));
             const size_t bi = (size_t)(3 * L) * n + gpix;
-            const float sv = cb - d2in[bi];
+            const float sv = first ? cb : cb - d2in[bi];
             const float u = soft_thresh(sv, tau);
             const float nd = u - sv;
             Ain[i] = u + nd;
@@ -250,7 +256,7 @@ haar_tile(const ProbDesc* __restrict__ probs, int H, int W, int n_row_ctas, int*
     }
     double pv[kNumPartials] = {0.0, l1.value(), 0.0, 0.0};
     block_reduce_partials(pv, red);
-    if (tid == 0) finish_iteration(P, k, chk, nobj, pv, n_active, n_row_ctas + blockIdx.x);
+    if (tid == 0) finish_iteration(P, k, chk, nobj, pv, n_active, n_row_ctas + blockIdx.x, probs, sl);
 }
 
 // ---------------------------------------------------------------------------
@@ -258,10 +264,13 @@ haar_tile(const ProbDesc* __restrict__ probs, int H, int W, int n_row_ctas, int*
 // ---------------------------------------------------------------------------
 template <int W>
 __global__ void __launch_bounds__(kThreads)
-haar_row_forward(const ProbDesc* __restrict__ probs, int H, int Wp, const float2* __restrict__ tw_g) {
+haar_row_forward(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp, const float2* __restrict__ tw_g) {
     constexpr int FT = W / 8, G = kThreads / FT, ROW = pad8(W);
-    const ProbDesc& P = probs[blockIdx.y];
-    if (P.ctl->active == 0) return;
+    const int pi = sl.map[blockIdx.y];
+    if (pi < 0) return;
+    const ProbDesc& P = probs[pi];
+    // a problem that has just taken over this slot starts with the column phase
+    if (P.ctl->active == 0 || P.ctl->iter == 0) return;
     extern __shared__ __align__(16) float2 smem[];
     float2* buf = smem;
     float2* tw = buf + G * ROW;
@@ -287,8 +296,8 @@ haar_row_forward(const ProbDesc* __restrict__ probs, int H, int Wp, const float2
 // host-side launch of the three row-side kernels of one FA-MD iteration
 // ---------------------------------------------------------------------------
 template <int W>
-cudaError_t launch_haar_rows_t(int H, int Wp, const ProbDesc* d, int count, int levels, const float2* tw,
-                               int* n_active, cudaStream_t s) {
+cudaError_t launch_haar_rows_t(int H, int Wp, const ProbDesc* d, SlotTable sl, int count, int levels,
+                               const float2* tw, int* n_active, cudaStream_t s) {
     constexpr int FT = W / 8, G = kThreads / FT;
     const size_t smem_row = (size_t)(G * pad8(W) + W) * sizeof(float2) + 8 * kNumPartials * sizeof(double);
     static bool attr = false;
@@ -300,19 +309,19 @@ cudaError_t launch_haar_rows_t(int H, int Wp, const ProbDesc* d, int count, int 
         attr = true;
     }
     const int nrow = H / G;
-    haar_row_inverse<W><<<dim3(nrow, count), kThreads, smem_row, s>>>(d, H, Wp, tw);
+    haar_row_inverse<W><<<dim3(nrow, count), kThreads, smem_row, s>>>(d, sl, H, Wp, tw);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const dim3 tgrid(haar_num_tiles(H, W), count);
     switch (levels) {
-        case 1: haar_tile<1><<<tgrid, kThreads, HaarTileCfg<1>::SMEM, s>>>(d, H, W, nrow, n_active); break;
-        case 2: haar_tile<2><<<tgrid, kThreads, HaarTileCfg<2>::SMEM, s>>>(d, H, W, nrow, n_active); break;
-        case 3: haar_tile<3><<<tgrid, kThreads, HaarTileCfg<3>::SMEM, s>>>(d, H, W, nrow, n_active); break;
-        default: haar_tile<4><<<tgrid, kThreads, HaarTileCfg<4>::SMEM, s>>>(d, H, W, nrow, n_active); break;
+        case 1: haar_tile<1><<<tgrid, kThreads, HaarTileCfg<1>::SMEM, s>>>(d, sl, H, W, nrow, n_active); break;
+        case 2: haar_tile<2><<<tgrid, kThreads, HaarTileCfg<2>::SMEM, s>>>(d, sl, H, W, nrow, n_active); break;
+        case 3: haar_tile<3><<<tgrid, kThreads, HaarTileCfg<3>::SMEM, s>>>(d, sl, H, W, nrow, n_active); break;
+        default: haar_tile<4><<<tgrid, kThreads, HaarTileCfg<4>::SMEM, s>>>(d, sl, H, W, nrow, n_active); break;
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    haar_row_forward<W><<<dim3(nrow, count), kThreads, smem_row, s>>>(d, H, Wp, tw);
+    haar_row_forward<W><<<dim3(nrow, count), kThreads, smem_row, s>>>(d, sl, H, Wp, tw);
     return cudaGetLastError();
 }
 
@@ -332,17 +341,17 @@ inline cudaError_t haar_tile_attributes() {
     return cudaSuccess;
 }
 
-inline cudaError_t launch_haar_iteration_rows(int W, int H, int Wp, const ProbDesc* d, int count, int levels,
-                                              const float2* tw, int* n_active, cudaStream_t s) {
+inline cudaError_t launch_haar_iteration_rows(int W, int H, int Wp, const ProbDesc* d, SlotTable sl, int count,
+                                              int levels, const float2* tw, int* n_active, cudaStream_t s) {
     cudaError_t e = haar_tile_attributes();
     if (e != cudaSuccess) return e;
     switch (W) {
-        case 64: return launch_haar_rows_t<64>(H, Wp, d, count, levels, tw, n_active, s);
-        case 128: return launch_haar_rows_t<128>(H, Wp, d, count, levels, tw, n_active, s);
-        case 256: return launch_haar_rows_t<256>(H, Wp, d, count, levels, tw, n_active, s);
-        case 512: return launch_haar_rows_t<512>(H, Wp, d, count, levels, tw, n_active, s);
-        case 1024: return launch_haar_rows_t<1024>(H, Wp, d, count, levels, tw, n_active, s);
-        case 2048: return launch_haar_rows_t<2048>(H, Wp, d, count, levels, tw, n_active, s);
+        case 64: return launch_haar_rows_t<64>(H, Wp, d, sl, count, levels, tw, n_active, s);
+        case 128: return launch_haar_rows_t<128>(H, Wp, d, sl, count, levels, tw, n_active, s);
+        case 256: return launch_haar_rows_t<256>(H, Wp, d, sl, count, levels, tw, n_active, s);
+        case 512: return launch_haar_rows_t<512>(H, Wp, d, sl, count, levels, tw, n_active, s);
+        case 1024: return launch_haar_rows_t<1024>(H, Wp, d, sl, count, levels, tw, n_active, s);
+        case 2048: return launch_haar_rows_t<2048>(H, Wp, d, sl, count, levels, tw, n_active, s);
     }
     return cudaErrorInvalidValue;
 }

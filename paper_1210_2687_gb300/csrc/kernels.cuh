@@ -76,6 +76,18 @@ struct ProbDesc {
     double tol;
 };
 
+// Continuous batching: a launch covers gridDim.y slots; slot s works on
+// problem map[s] (or nothing when map[s] < 0). When a problem retires, the
+// CTA that finishes its iteration hands the slot to the next queued problem,
+// so launches stay full until the queue drains. A problem's first iteration
+// (k = 1) treats its whole state as zero (u0 = d0 = 0), so a slot needs no
+// reset before it starts a new problem.
+struct SlotTable {
+    int* map;       // gridDim.y entries
+    int* queue;     // next problem index to hand out
+    int pool;       // problems in the descriptor table
+};
+
 // stop rules (values of ADMM_STOP_*)
 constexpr int kStopIters = 0, kStopRelX = 1, kStopRelObj = 2;
 constexpr int kStatusNonFinite = -5;
@@ -214,6 +226,18 @@ __global__ void init_ctl_kernel(ProbDesc* __restrict__ probs, int count, int* __
     if (bad) atomicSub(n_active, 1);
 }
 
+// first `nslots` problems that are still active go to the slots (one thread)
+__global__ void assign_slots_kernel(const ProbDesc* __restrict__ probs, SlotTable sl, int nslots) {
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    int next = 0;
+    for (int s = 0; s < nslots; ++s) {
+        while (next < sl.pool && probs[next].ctl->active == 0) ++next;
+        sl.map[s] = next < sl.pool ? next : -1;
+        if (next < sl.pool) ++next;
+    }
+    *sl.queue = next;
+}
+
 // ---------------------------------------------------------------------------
 // Column phase. Grid: (ceil(Wc / CB), problems). CTA = CB spectrum columns of
 // one problem, whole height H.
@@ -236,10 +260,19 @@ struct ColCfg {
 // reads of the transforms hit distinct banks.
 template <int H, int CB>
 __global__ void __launch_bounds__(kThreads)
-col_phase(const ProbDesc* __restrict__ probs, int Wc, int Wp, const float2* __restrict__ tw_g) {
+col_phase(const ProbDesc* __restrict__ probs, SlotTable sl, int Wc, int Wp, const float2* __restrict__ tw_g) {
     using C = ColCfg<H, CB>;
-    const ProbDesc& P = probs[blockIdx.y];
+    const int pi = sl.map[blockIdx.y];
+    if (pi < 0) return;
+    const ProbDesc& P = probs[pi];
     if (P.ctl->active == 0) return;
+    if (P.ctl->iter == 0) {
+        // first iteration from u0 = d0 = 0: the right-hand side is zero, so x1 = 0
+        const int c0 = blockIdx.x * CB;
+        for (int e = threadIdx.x; e < H * CB; e += kThreads)
+            P.Sa[(size_t)(e / CB) * Wp + c0 + e % CB] = make_float4(0.f, 0.f, 0.f, 0.f);
+        return;
+    }
     extern __shared__ __align__(16) float4 smem4[];
     float4* stage = smem4;                                       // H x CB
     float2* xb = reinterpret_cast<float2*>(stage + H * CB);      // G x 2 exchange buffers
@@ -373,7 +406,8 @@ __device__ __forceinline__ void block_reduce_partials(double (&v)[kNumPartials],
 // strips in strip order, evaluates the stop rule of iteration k and
 // advances the problem's control block.
 __device__ void finish_iteration(const ProbDesc& P, int k, bool chk, bool nobj,
-                                 const double (&v)[kNumPartials], int* n_active, int slot) {
+                                 const double (&v)[kNumPartials], int* n_active, int slot,
+                                 const ProbDesc* __restrict__ probs, SlotTable sl) {
     ProbCtl* ctl = P.ctl;
 #pragma unroll
     for (int j = 0; j < kNumPartials; ++j) P.partials[slot * kNumPartials + j] = v[j];
@@ -417,6 +451,11 @@ __device__ void finish_iteration(const ProbDesc& P, int k, bool chk, bool nobj,
     if (conv || done || k >= P.max_iters) {
         ctl->active = 0;
         atomicSub(n_active, 1);
+        // hand this slot to the next queued problem that is still active
+        // (bounded: every pass consumes one queue entry)
+        int nx = atomicAdd(sl.queue, 1);
+        while (nx < sl.pool && probs[nx].ctl->active == 0) nx = atomicAdd(sl.queue, 1);
+        sl.map[blockIdx.y] = nx < sl.pool ? nx : -1;
     }
     ctl->arrive = 0u;
 }
@@ -454,13 +493,16 @@ struct RowCfg {
 
 template <int W, int R, int D>
 __global__ void __launch_bounds__(kThreads, 2)
-row_phase_tv(const ProbDesc* __restrict__ probs, int H, int Wp, const float2* __restrict__ tw_g,
+row_phase_tv(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp, const float2* __restrict__ tw_g,
              int* __restrict__ n_active) {
     using C = RowCfg<W, R, D>;
-    const ProbDesc& P = probs[blockIdx.y];
+    const int pi = sl.map[blockIdx.y];
+    if (pi < 0) return;
+    const ProbDesc& P = probs[pi];
     ProbCtl* ctl = P.ctl;
     if (ctl->active == 0) return;
     const int k = ctl->iter + 1;                 // iteration being completed
+    const bool first = k == 1;                   // d1 = d2 = x_prev = 0 (cold start)
     const bool chk = is_check_iter(P, k), sprev = store_prev_iter(P, k), nobj = need_obj_iter(P, k);
     extern __shared__ __align__(16) float2 smem[];
     float2* buf = smem;
@@ -483,11 +525,11 @@ row_phase_tv(const ProbDesc* __restrict__ probs, int H, int Wp, const float2* __
             for (int j = 0; j < C::CPT; ++j) {
                 const int c = tid + j * kThreads;
                 const size_t pix = (size_t)q * W + c;
-                cp_async8(slot + 2 * c, d2in + pix);
+                if (!first) cp_async8(slot + 2 * c, d2in + pix);
                 if (i >= 1) {
-                    cp_async4(slot + 2 * W + c, P.d1 + pix);
+                    if (!first) cp_async4(slot + 2 * W + c, P.d1 + pix);
                     cp_async4(slot + 3 * W + c, P.ybar + pix);
-                    if (chk) cp_async4(slot + 4 * W + c, P.xprev + pix);
+                    if (chk && !first) cp_async4(slot + 4 * W + c, P.xprev + pix);
                 }
             }
         }
@@ -547,7 +589,7 @@ row_phase_tv(const ProbDesc* __restrict__ probs, int H, int Wp, const float2* __
                 // D_i x (forward periodic differences)
                 const float gh = xr - x, gv = xd - x;
                 const size_t pix = (size_t)q * W + c;
-                const float2 dd = *reinterpret_cast<const float2*>(slot + 2 * c);
+                const float2 dd = first ? make_float2(0.f, 0.f) : *reinterpret_cast<const float2*>(slot + 2 * c);
                 // u2 = v-soft(D_i x - d2, lambda/mu2)  (Alg. 3 line 10, 0/0 = 0)
                 const float sh = gh - dd.x, sv = gv - dd.y;
                 const float nrm = sqrtf(fmaf(sh, sh, sv * sv));
@@ -561,7 +603,7 @@ row_phase_tv(const ProbDesc* __restrict__ probs, int H, int Wp, const float2* __
                 if (owned) {
                     d2out[pix] = make_float2(nh, nv);
                     // u1 = (M^T M + mu1 I)^{-1} (M^T y + mu1 (A x - d1))  (eq. new_line)
-                    const float dd1 = slot[2 * W + c];
+                    const float dd1 = first ? 0.f : slot[2 * W + c];
                     const float yb = slot[3 * W + c];
                     const float s1 = ax - dd1;
                     const bool obs = is_observed(yb);
@@ -578,7 +620,7 @@ row_phase_tv(const ProbDesc* __restrict__ probs, int H, int Wp, const float2* __
                         s_reg.add(sqrtf(fmaf(gh, gh, gv * gv)));
                     }
                     if (chk) {
-                        const float dx = x - slot[4 * W + c];
+                        const float dx = first ? x : x - slot[4 * W + c];
                         s_dxx.add(dx * dx);
                         s_xx.add(x * x);
                     }
@@ -609,7 +651,7 @@ row_phase_tv(const ProbDesc* __restrict__ probs, int H, int Wp, const float2* __
     {
         double v[kNumPartials] = {s_data.value(), s_reg.value(), s_xx.value(), s_dxx.value()};
         block_reduce_partials(v, red);
-        if (tid == 0) finish_iteration(P, k, chk, nobj, v, n_active, blockIdx.x);
+        if (tid == 0) finish_iteration(P, k, chk, nobj, v, n_active, blockIdx.x, probs, sl);
     }
 
     // (4) forward row DFTs of p = zeta1 + i w on rows 1..R and split

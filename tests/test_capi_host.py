@@ -83,3 +83,9 @@ def test_null_arguments(ad):
     assert lib.admm_deconv_solve_batch(None, -1, None, None, None, None, None) == ad.ADMM_EINVAL
     assert lib.admm_deconv_state_size(None) == -1
     lib.admm_deconv_destroy(None)   # no-op
+
+
+def test_set_option_validates(ad):
+    assert ad.lib.admm_deconv_set_option(ad.ADMM_OPT_MAX_SLOTS, -1) == ad.ADMM_EINVAL
+    assert ad.lib.admm_deconv_set_option(99, 1) == ad.ADMM_EINVAL
+    assert ad.lib.admm_deconv_set_option(ad.ADMM_OPT_MAX_SLOTS, 0) == ad.ADMM_OK

@@ -178,6 +178,39 @@ def test_batch_equals_individual_solves(ad):
         assert torch.equal(xo, xs[i])
 
 
+def test_queued_problems_start_as_slots_free_up(ad):
+    """More problems than launch slots: with ADMM_OPT_MAX_SLOTS = 2, seven
+    problems (TV and frame, different sizes, stop rules and iteration
+    counts) queue and take over slots as others retire; every result is the
+    bit-exact result of solving the problem alone."""
+    import torch
+    specs = [(64, 64, "tv", "rel_x", 1e-5, 3000), (64, 64, "tv", "iters", 0.0, 9),
+             (64, 64, "tv", "iters", 0.0, 31), (64, 64, "tv", "rel_x", 1e-4, 3000),
+             (128, 64, "haar", "iters", 0.0, 12), (128, 64, "haar", "rel_x", 1e-4, 3000),
+             (128, 64, "haar", "iters", 0.0, 5)]
+    plans, ys, ms, xs = [], [], [], []
+    for i, (H, W, reg, stop, tol, it) in enumerate(specs):
+        xt, psf, ybar, mask = _case_problem(H, W, lambda: S.psf_gaussian(7, 1.5), 0.8, 60 + i)
+        lam = 3e-4
+        mu1, mu2 = S.default_mu(lam)
+        plans.append(ad.Plan(H, W, psf, lam, mu1, mu2, reg, stop=stop, tol=tol, max_iters=it, check_every=2))
+        ys.append(torch.from_numpy(ybar.astype(np.float32)).cuda())
+        ms.append(torch.from_numpy(mask).cuda())
+        xs.append(torch.empty((H, W), dtype=torch.float32, device="cuda"))
+    ad.admm_deconv_set_option(ad.ADMM_OPT_MAX_SLOTS, 2)
+    try:
+        res = ad.solve_batch(plans, ys, ms, xs)
+        torch.cuda.synchronize()
+    finally:
+        ad.admm_deconv_set_option(ad.ADMM_OPT_MAX_SLOTS, 0)
+    for i in range(len(specs)):
+        xo = torch.empty_like(xs[i])
+        r = ad.solve(plans[i], ys[i], ms[i], xo)
+        torch.cuda.synchronize()
+        assert r.iters == res[i].iters and r.converged == res[i].converged
+        assert torch.equal(xo, xs[i]), i
+
+
 def test_host_buffers_equal_device_buffers(ad):
     """y, mask and x_out in host memory take the staging path; same bits."""
     import torch
