@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--batch", type=int, default=64, help="problems per step per GPU")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--steady-only", action="store_true",
+                    help="only the fixed-iteration pass with every slot busy (for profiler captures)")
     return ap.parse_args()
 
 
@@ -69,11 +71,12 @@ def make_batch(batch, rank):
 def bytes_per_pixel_iter():
     """Algorithmic HBM bytes per pixel and iteration of each phase (FP32).
     Row phase: half spectra in and out (8 + 8), d1 and d2 read and written
-    (8 + 16), M^T y and the mask read (4 + 1), x_prev for the rel-x rule
-    (read + write once per CHECK_EVERY iterations). Column phase: half
-    spectra in and out (8 + 8) and Lambda, K over the half spectrum (6)."""
+    (8 + 16), M^T y read (4; the observation mask is folded into it), x_prev
+    for the rel-x rule (read + write once per CHECK_EVERY iterations).
+    Column phase: half spectra in and out (8 + 8) and Lambda, K over the half
+    spectrum (6)."""
     half = (W // 2 + 1) / W
-    row = 8 + 8 + 8 + 16 + 4 + 1 + 8.0 / CHECK_EVERY
+    row = 8 + 8 + 8 + 16 + 4 + 8.0 / CHECK_EVERY
     col = (16 + 16 + 8 + 4) * half
     return row, col
 
@@ -210,6 +213,21 @@ def run_ours(args):
     ms = [torch.from_numpy(p.mask).to(dev) for p in probs]
     xs = [torch.empty((H, W), dtype=torch.float32, device=dev) for _ in probs]
     stream = torch.cuda.current_stream()
+
+    if args.steady_only:
+        fixed = [ad.Plan(H, W, p.psf, p.lam, p.mu1, p.mu2, "tv", max_iters=STEADY_ITERS) for p in probs]
+        ad.solve_batch(fixed, ys, ms, xs, stream)
+        ad.admm_deconv_profile(True)
+        ad.solve_batch(fixed, ys, ms, xs, stream)
+        pf = ad.admm_deconv_profile(False)
+        row_b, col_b = bytes_per_pixel_iter()
+        its = STEADY_ITERS * len(fixed)
+        print(json.dumps({"steady_state": {
+            "problems": len(fixed), "iters": STEADY_ITERS,
+            "row_phase_gbs": its * n * row_b / (pf.row_ms * 1e-3) / 1e9,
+            "col_phase_gbs": its * n * col_b / (pf.col_ms * 1e-3) / 1e9,
+            "iters_per_s": its / ((pf.row_ms + pf.col_ms) * 1e-3)}}), flush=True)
+        return
 
     def step():
         return ad.solve_batch(plans, ys, ms, xs, stream)
