@@ -158,7 +158,7 @@ int col_block(int H) {
         default: return 2;
     }
 }
-int row_strip_tv(int W) { return W <= 128 ? 16 : (W == 256 ? 8 : 4); }
+int row_strip_tv(int W) { return W <= 128 ? 16 : (W <= 512 ? 8 : 4); }
 
 // launch slots of a group: enough problems in flight that a row-side launch
 // has about 2400 CTAs (some eight waves of two CTAs per SM on 152 SMs)
@@ -220,9 +220,8 @@ cudaError_t launch_row_tv(int W, const ProbDesc* d, SlotTable sl, int count, int
         // (rows per strip, walk rows in flight); must agree with row_strip_tv
         case 64: return launch_row_tv_t<64, 16, 4>(d, sl, count, H, Wp, tw, n_active, s);
         case 128: return launch_row_tv_t<128, 16, 4>(d, sl, count, H, Wp, tw, n_active, s);
-        // D = R + 1: every walk row of the strip is requested at kernel entry
-        case 256: return launch_row_tv_t<256, 8, 9>(d, sl, count, H, Wp, tw, n_active, s);
-        case 512: return launch_row_tv_t<512, 4, 5>(d, sl, count, H, Wp, tw, n_active, s);
+        case 256: return launch_row_tv_t<256, 8, 4>(d, sl, count, H, Wp, tw, n_active, s);
+        case 512: return launch_row_tv_t<512, 8, 4>(d, sl, count, H, Wp, tw, n_active, s);
         case 1024: return launch_row_tv_t<1024, 4, 2>(d, sl, count, H, Wp, tw, n_active, s);
         case 2048: return launch_row_tv_t<2048, 4, 1>(d, sl, count, H, Wp, tw, n_active, s);
     }

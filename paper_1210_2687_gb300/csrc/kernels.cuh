@@ -259,7 +259,7 @@ struct ColCfg {
 // cp.async with row r's CB entries rotated by r, so that the column-wise
 // reads of the transforms hit distinct banks.
 template <int H, int CB>
-__global__ void __launch_bounds__(kThreads, (H >= 1024 ? 1 : 3))
+__global__ void __launch_bounds__(kThreads)
 col_phase(const ProbDesc* __restrict__ probs, SlotTable sl, int Wc, int Wp, const float2* __restrict__ tw_g) {
     using C = ColCfg<H, CB>;
     const int pi = sl.map[blockIdx.y];
@@ -295,6 +295,18 @@ col_phase(const ProbDesc* __restrict__ probs, SlotTable sl, int Wc, int Wp, cons
         const int c = g + j * C::G;
         const int kc = c0 + c;
         const bool spec = kc < Wc;
+        // spectra of this column, requested before the transforms
+        float2 L[8];
+        float Kv[8];
+        if (spec) {
+            const float2* __restrict__ lcol = P.lamT + (size_t)kc * H;
+            const float* __restrict__ kcol = P.kT + (size_t)kc * H;
+#pragma unroll
+            for (int m = 0; m < 8; ++m) {
+                L[m] = lcol[t + m * C::FT];
+                Kv[m] = kcol[t + m * C::FT];
+            }
+        }
         float2 v[8], u[8];
 #pragma unroll
         for (int m = 0; m < 8; ++m) {
@@ -306,16 +318,12 @@ col_phase(const ProbDesc* __restrict__ probs, SlotTable sl, int Wc, int Wp, cons
         fft_group<H, -1>(v, bz, tw, t);
         fft_group<H, -1>(u, bw, tw, t);
         if (spec) {
-            const float2* __restrict__ lcol = P.lamT + (size_t)kc * H;
-            const float* __restrict__ kcol = P.kT + (size_t)kc * H;
 #pragma unroll
             for (int m = 0; m < 8; ++m) {
-                const float2 L = lcol[t + m * C::FT];
-                const float Kv = kcol[t + m * C::FT];
                 // x^ = K (conj(Lambda) Z1^ + W^);  (A x)^ = Lambda x^
-                const float2 xh = Kv * (cmulc(v[m], L) + u[m]);
+                const float2 xh = Kv[m] * (cmulc(v[m], L[m]) + u[m]);
                 v[m] = xh;
-                u[m] = cmul(L, xh);
+                u[m] = cmul(L[m], xh);
             }
         }
         fft_group<H, 1>(v, bz, tw, t);
