@@ -133,13 +133,30 @@ __device__ __forceinline__ void stockham_compute(float2 (&v)[8], int t, int Ns, 
     }
 }
 
+// Barrier over the N/8 threads of one transform group (group g of the
+// block, threads g*N/8 .. g*N/8 + N/8 - 1): a warp barrier when the group
+// fits in one warp, else named barrier 1 + g (barrier 0 is __syncthreads).
+template <int N>
+__device__ __forceinline__ void group_sync(int g) {
+    constexpr int FT = N / 8;
+    if constexpr (FT <= 32) {
+        constexpr unsigned lanes = FT == 32 ? 0xffffffffu : ((1u << FT) - 1u);
+        const unsigned mask = lanes << ((g * FT) & 31);
+        __syncwarp(mask);
+    } else {
+        asm volatile("bar.sync %0, %1;\n" ::"r"(1 + g), "n"(FT) : "memory");
+    }
+}
+
 // Full length-N transform for a group of N/8 threads.
 //   v    : in/out registers, element t + m N/8 in v[m] (natural order both ways)
 //   buf  : the group's shared buffer, >= pad8(N) float2
 //   tw   : forward twiddle table of length N (shared or global)
-// All threads of the block must call this together (it uses __syncthreads).
+//   g    : index of the group in the block (threads g*N/8 .. g*N/8 + N/8 - 1)
+// Only the threads of the group synchronise (group_sync); the other groups of
+// the block run independently. Block-wide ordering is the caller's business.
 template <int N, int DIR>
-__device__ __forceinline__ void fft_group(float2 (&v)[8], float2* buf, const float2* tw, int t) {
+__device__ __forceinline__ void fft_group(float2 (&v)[8], float2* buf, const float2* tw, int t, int g) {
     using S = FftShape<N>;
     constexpr int Q = N / 8;
     int oidx[8];
@@ -151,10 +168,10 @@ __device__ __forceinline__ void fft_group(float2 (&v)[8], float2* buf, const flo
         // exchange through shared memory into the input order of the next
         // pass; the leading barrier also orders any reads of `buf` the caller
         // made before the transform
-        __syncthreads();
+        group_sync<N>(g);
 #pragma unroll
         for (int m = 0; m < 8; ++m) buf[pad8(oidx[m])] = v[m];
-        __syncthreads();
+        group_sync<N>(g);
 #pragma unroll
         for (int m = 0; m < 8; ++m) v[m] = buf[pad8(t + m * Q)];
         stockham_compute<N, 8, DIR>(v, t, Ns, tw, oidx);
@@ -162,8 +179,8 @@ __device__ __forceinline__ void fft_group(float2 (&v)[8], float2* buf, const flo
     }
     // after the last radix-8 pass (Ns = N/8 before it) oidx[m] = t + m N/8:
     // registers already hold the natural-order output. The trailing barrier
-    // lets the caller overwrite `buf` right away.
-    __syncthreads();
+    // lets the group overwrite `buf` right away.
+    group_sync<N>(g);
 }
 
 }  // namespace admm

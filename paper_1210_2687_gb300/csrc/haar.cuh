@@ -61,7 +61,7 @@ haar_row_inverse(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp
     const int q = blockIdx.x * G + g;
     float2 v[8];
     load_row_xax<W>(v, P.Sa + (size_t)q * Wp, t);
-    fft_group<W, 1>(v, buf + g * ROW, tw, t);
+    fft_group<W, 1>(v, buf + g * ROW, tw, t, g);
     const size_t n = (size_t)H * W;
     float* __restrict__ xw = P.work;
     float* __restrict__ z1w = P.work + n;
@@ -285,10 +285,10 @@ haar_row_forward(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp
 #pragma unroll
     for (int m = 0; m < 8; ++m) v[m] = make_float2(z1w[t + m * FT], ww[t + m * FT]);
     float2* row = buf + g * ROW;
-    fft_group<W, -1>(v, row, tw, t);
+    fft_group<W, -1>(v, row, tw, t, g);
 #pragma unroll
     for (int m = 0; m < 8; ++m) row[pad8(t + m * FT)] = v[m];
-    __syncthreads();
+    group_sync<W>(g);                // the split reads this group's row only
     store_split<W>(P.Sb + (size_t)q * Wp, row, t);
 }
 

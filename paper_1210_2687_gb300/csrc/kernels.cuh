@@ -315,8 +315,8 @@ col_phase(const ProbDesc* __restrict__ probs, SlotTable sl, int Wc, int Wp, cons
             v[m] = make_float2(f.x, f.y);
             u[m] = make_float2(f.z, f.w);
         }
-        fft_group<H, -1>(v, bz, tw, t);
-        fft_group<H, -1>(u, bw, tw, t);
+        fft_group<H, -1>(v, bz, tw, t, g);
+        fft_group<H, -1>(u, bw, tw, t, g);
         if (spec) {
 #pragma unroll
             for (int m = 0; m < 8; ++m) {
@@ -326,8 +326,8 @@ col_phase(const ProbDesc* __restrict__ probs, SlotTable sl, int Wc, int Wp, cons
                 u[m] = cmul(L[m], xh);
             }
         }
-        fft_group<H, 1>(v, bz, tw, t);
-        fft_group<H, 1>(u, bw, tw, t);
+        fft_group<H, 1>(v, bz, tw, t, g);
+        fft_group<H, 1>(u, bw, tw, t, g);
 #pragma unroll
         for (int m = 0; m < 8; ++m) {
             const int r = t + m * C::FT;
@@ -561,7 +561,7 @@ row_phase_tv(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp, co
 #pragma unroll
             for (int m = 0; m < 8; ++m) v[m] = make_float2(0.f, 0.f);
         }
-        fft_group<W, 1>(v, row, tw, t);
+        fft_group<W, 1>(v, row, tw, t, g);
 #pragma unroll
         for (int m = 0; m < 8; ++m) row[pad8(t + m * C::FT)] = v[m];
     }
@@ -661,10 +661,10 @@ row_phase_tv(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp, co
         float2 v[8];
 #pragma unroll
         for (int m = 0; m < 8; ++m) v[m] = row[pad8(t + m * C::FT)];
-        fft_group<W, -1>(v, row, tw, t);
+        fft_group<W, -1>(v, row, tw, t, g);
 #pragma unroll
         for (int m = 0; m < 8; ++m) row[pad8(t + m * C::FT)] = v[m];
-        __syncthreads();
+        group_sync<W>(g);            // the split reads this group's row only
         if (i <= R) {
             const int q = r0 - 1 + i;
             store_split<W>(P.Sb + (size_t)q * Wp, row, t);
@@ -696,7 +696,7 @@ finalize_x(const ProbDesc* __restrict__ probs, float* const* __restrict__ xout, 
 #pragma unroll
         for (int m = 0; m < 8; ++m) v[m] = make_float2(0.f, 0.f);
     }
-    fft_group<W, 1>(v, buf + g * ROW, tw, t);
+    fft_group<W, 1>(v, buf + g * ROW, tw, t, g);
     if (q < H) {
         float* xo = xout[blockIdx.y] + (size_t)q * W;
 #pragma unroll
