@@ -461,34 +461,40 @@ __device__ void finish_iteration(const ProbDesc& P, int k, bool chk, bool nobj,
 }
 
 // ---------------------------------------------------------------------------
-// TV row phase. Grid: (H / R, problems). CTA = strip of R rows of one
-// problem; the inverse transforms also cover one halo row above and below
-// (the forward differences and their adjoints reach one row each way).
+// TV row phase. Grid: (H / R, slots). CTA = strip of R rows of one problem;
+// the inverse transforms also cover one halo row above and below (the
+// forward differences and their adjoints reach one row each way).
 //
 // Data movement: at entry every half-spectrum row of the strip (R + 2 rows)
 // is requested with cp.async into the row buffers, and the per-pixel inputs
 // of the first D rows of the walk (d2, d1, M^T y, x_prev) into a per-thread
 // ring of D row slots; each walk step consumes one slot and refills it with
 // the row D ahead, so D rows of loads stay in flight behind the arithmetic.
+//
+// The walk needs no block barrier: warp w owns the contiguous columns
+// [w W/8, (w+1) W/8) and walks its rows on its own. The left neighbour's
+// delta_h comes by shuffle from the next lower lane; the first lane
+// recomputes the pixel left of the chunk itself (its d2 is in the ring's
+// halo entry). x values of the neighbouring warps' boundary columns are
+// captured in registers before any warp overwrites its rows with p.
 // ---------------------------------------------------------------------------
 template <int W, int R, int D>
 struct RowCfg {
     static constexpr int FT = W / 8;
     static constexpr int G = kThreads / FT;                        // row transforms in flight
-    static constexpr int NB_INV = ((R + 2 + G - 1) / G) * G;
-    static constexpr int NB_FWD = 1 + ((R + G - 1) / G) * G;
-    static constexpr int NB = NB_INV > NB_FWD ? NB_INV : NB_FWD;  // buffer rows
+    static constexpr int NB = R + 2;                               // buffer rows
     static constexpr int ROW = pad8(W);                            // float2 per buffer row
     static constexpr int RAW = W / 2 + 1;                          // float4 per half-spectrum row
-    static constexpr int CPT = W >= kThreads ? W / kThreads : 1;    // columns per thread
-    static constexpr int SLOT = 5 * W;                             // floats per ring slot
+    static constexpr int NWARP = kThreads / 32;
+    static constexpr int CW = W / NWARP;                           // columns per warp
+    static constexpr int CPT = CW >= 32 ? CW / 32 : 1;              // columns per thread
+    static constexpr int SLOT = 5 * W + 2 * NWARP;                 // floats per ring slot
     static_assert(RAW * 16 <= ROW * 8, "raw row must fit a buffer row");
-    static_assert(((size_t)NB * ROW * 8 + (size_t)W * 8 + (size_t)D * SLOT * 4 + 2 * (size_t)W * 4) % 8 == 0,
-                  "double alignment of the reduction scratch");
+    static_assert(R + 2 <= 32, "boundary capture holds one row per lane");
     static_assert(((size_t)NB * ROW * 8 + (size_t)W * 8) % 16 == 0, "ring alignment");
+    static_assert(((size_t)NB * ROW * 8 + (size_t)W * 8 + (size_t)D * SLOT * 4) % 8 == 0, "scratch alignment");
     static constexpr size_t SMEM = (size_t)NB * ROW * sizeof(float2) + (size_t)W * sizeof(float2)
-                                 + (size_t)D * SLOT * sizeof(float) + 2 * (size_t)W * sizeof(float)
-                                 + 8 * kNumPartials * sizeof(double);
+                                 + (size_t)D * SLOT * sizeof(float) + 8 * kNumPartials * sizeof(double);
 };
 
 template <int W, int R, int D>
@@ -508,22 +514,25 @@ row_phase_tv(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp, co
     float2* buf = smem;
     float2* tw = buf + C::NB * C::ROW;
     float* ring = reinterpret_cast<float*>(tw + W);
-    float* dhs = ring + D * C::SLOT;
-    double* red = reinterpret_cast<double*>(dhs + 2 * W);
+    double* red = reinterpret_cast<double*>(ring + D * C::SLOT);
     const int tid = threadIdx.x;
+    const int lane = tid & 31, wid = tid >> 5;
     const int r0 = blockIdx.x * R;
-    const bool colthr = (W >= kThreads) || (tid < W);
+    const bool colthr = lane < C::CW;            // narrow rows leave some lanes idle
+    const int cbase = wid * C::CW + lane;        // column j of this thread: cbase + 32 j
+    const int chalo = (wid * C::CW - 1) & (W - 1);
     const float2* __restrict__ d2in = reinterpret_cast<const float2*>(P.d2 + ((k + 1) & 1) * P.d2_stride);
     float2* __restrict__ d2out = reinterpret_cast<float2*>(P.d2 + (k & 1) * P.d2_stride);
 
-    // ring slot of walk row i: d2 (float2 per column), d1, M^T y, x_prev
+    // ring slot of walk row i: d2 (float2 per column), d1, M^T y, x_prev, and
+    // per warp the d2 of the pixel left of its chunk
     auto issue = [&](int i) {
         if (i <= R && colthr) {
             const int q = (r0 - 1 + i + H) & (H - 1);
             float* slot = ring + (i % D) * C::SLOT;
 #pragma unroll
             for (int j = 0; j < C::CPT; ++j) {
-                const int c = tid + j * kThreads;
+                const int c = cbase + 32 * j;
                 const size_t pix = (size_t)q * W + c;
                 if (!first) cp_async8(slot + 2 * c, d2in + pix);
                 if (i >= 1) {
@@ -532,6 +541,7 @@ row_phase_tv(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp, co
                     if (chk && !first) cp_async4(slot + 4 * W + c, P.xprev + pix);
                 }
             }
+            if (lane == 0 && !first) cp_async8(slot + 5 * W + 2 * wid, d2in + (size_t)q * W + chalo);
         }
         cp_async_commit();   // possibly empty: keeps one group per walk row
     };
@@ -551,26 +561,27 @@ row_phase_tv(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp, co
     const int g = tid / C::FT, t = tid % C::FT;
 
     // (1) x + i A x on buffer rows 0..R+1 = image rows r0-1..r0+R: inverse row DFTs
-    for (int rb = 0; rb < C::NB_INV; rb += C::G) {
-        const int i = rb + g;
+    for (int i = g; i < R + 2; i += C::G) {
         float2* row = buf + i * C::ROW;
         float2 v[8];
-        if (i < R + 2) {
-            load_row_xax<W>(v, reinterpret_cast<const float4*>(row), t);
-        } else {
-#pragma unroll
-            for (int m = 0; m < 8; ++m) v[m] = make_float2(0.f, 0.f);
-        }
+        load_row_xax<W>(v, reinterpret_cast<const float4*>(row), t);
         fft_group<W, 1>(v, row, tw, t, g);
 #pragma unroll
         for (int m = 0; m < 8; ++m) row[pad8(t + m * C::FT)] = v[m];
     }
     __syncthreads();
+    // x of the neighbouring warps' boundary columns, one row per lane
+    float xnb_right = 0.f, xnb_left = 0.f;
+    if (lane < R + 2) {
+        xnb_right = buf[lane * C::ROW + pad8((wid * C::CW + C::CW) & (W - 1))].x;
+        xnb_left = buf[lane * C::ROW + pad8(chalo)].x;
+    }
+    __syncthreads();             // nobody overwrites a row before every warp captured
 
-    // (2) proxes and dual updates, walking down the strip
+    // (2) proxes and dual updates, each warp walking down its columns
     const float tau = P.tau, gam = P.gamma, mu1 = P.mu1, inv1 = P.inv1pmu1;
     CompSum s_data, s_reg, s_xx, s_dxx;
-    float dvprev[C::CPT], dhcur[C::CPT], dvcur[C::CPT], z1cur[C::CPT];
+    float dvprev[C::CPT];
 #pragma unroll
     for (int j = 0; j < C::CPT; ++j) dvprev[j] = 0.f;
     for (int i = 0; i <= R; ++i) {
@@ -578,13 +589,21 @@ row_phase_tv(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp, co
         const bool owned = i >= 1;
         cp_async_wait<D - 1>();      // this thread's copies of walk row i have landed
         const float* slot = ring + (i % D) * C::SLOT;
+        const float xr_nb = __shfl_sync(0xffffffffu, xnb_right, i);
+        const float xl_nb = __shfl_sync(0xffffffffu, xnb_left, i);
+        const float xl_nb_dn = __shfl_sync(0xffffffffu, xnb_left, i + 1);
+        float dhcur[C::CPT], dvcur[C::CPT], z1cur[C::CPT];
+#pragma unroll
+        for (int j = 0; j < C::CPT; ++j) dhcur[j] = dvcur[j] = z1cur[j] = 0.f;
+        float dh_halo = 0.f;
         if (colthr) {
 #pragma unroll
             for (int j = 0; j < C::CPT; ++j) {
-                const int c = tid + j * kThreads;
+                const int c = cbase + 32 * j;
                 const float2 z = buf[i * C::ROW + pad8(c)];
                 const float x = z.x, ax = z.y;
-                const float xr = buf[i * C::ROW + pad8((c + 1) & (W - 1))].x;
+                const bool last_col = (lane == C::CW - 1 || lane == 31) && j == C::CPT - 1;
+                const float xr = last_col ? xr_nb : buf[i * C::ROW + pad8(c + 1)].x;
                 const float xd = buf[(i + 1) * C::ROW + pad8(c)].x;
                 // D_i x (forward periodic differences)
                 const float gh = xr - x, gv = xd - x;
@@ -600,6 +619,7 @@ row_phase_tv(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp, co
                 // delta = u2 + d2 for the next x-step (Alg. 3 lines 3-5)
                 dhcur[j] = uh + nh;
                 dvcur[j] = uv + nv;
+                z1cur[j] = 0.f;
                 if (owned) {
                     d2out[pix] = make_float2(nh, nv);
                     // u1 = (M^T M + mu1 I)^{-1} (M^T y + mu1 (A x - d1))  (eq. new_line)
@@ -626,18 +646,35 @@ row_phase_tv(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp, co
                     }
                     if (sprev) P.xprev[pix] = x;
                 }
-                dhs[(i & 1) * W + c] = dhcur[j];
+            }
+            if (lane == 0 && owned) {
+                // delta_h of the pixel left of the chunk (its owner updates its d2)
+                const float xh = xl_nb;
+                const float xhr = buf[i * C::ROW + pad8(wid * C::CW)].x;
+                const float2 dd = first ? make_float2(0.f, 0.f)
+                                        : *reinterpret_cast<const float2*>(slot + 5 * W + 2 * wid);
+                const float sh = (xhr - xh) - dd.x, sv = (xl_nb_dn - xh) - dd.y;
+                const float nrm = sqrtf(fmaf(sh, sh, sv * sv));
+                const float sc = nrm > tau ? (nrm - tau) / nrm : 0.f;
+                dh_halo = 2.f * sc * sh - sh;
             }
         }
         issue(i + D);                // slot (i % D) is consumed: refill it D rows ahead
-        __syncthreads();
+        // left neighbours' delta_h within the warp
+        float dhl[C::CPT];
+#pragma unroll
+        for (int j = 0; j < C::CPT; ++j) {
+            const float up = __shfl_up_sync(0xffffffffu, dhcur[j], 1);
+            const float wrap = j > 0 ? __shfl_sync(0xffffffffu, dhcur[j > 0 ? j - 1 : 0], 31) : dh_halo;
+            dhl[j] = lane == 0 ? wrap : up;
+        }
+        __syncwarp();                // every lane has read row i before it is overwritten
         if (owned && colthr) {
             // w = gamma (Dh^T delta_h + Dv^T delta_v): adjoint of forward differences
 #pragma unroll
             for (int j = 0; j < C::CPT; ++j) {
-                const int c = tid + j * kThreads;
-                const float dhl = dhs[(i & 1) * W + ((c - 1) & (W - 1))];
-                const float w = gam * ((dhl - dhcur[j]) + (dvprev[j] - dvcur[j]));
+                const int c = cbase + 32 * j;
+                const float w = gam * ((dhl[j] - dhcur[j]) + (dvprev[j] - dvcur[j]));
                 buf[i * C::ROW + pad8(c)] = make_float2(z1cur[j], w);
             }
         }
@@ -655,8 +692,7 @@ row_phase_tv(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp, co
     }
 
     // (4) forward row DFTs of p = zeta1 + i w on rows 1..R and split
-    for (int rb = 1; rb < C::NB_FWD; rb += C::G) {
-        const int i = rb + g;
+    for (int i = 1 + g; i <= R; i += C::G) {
         float2* row = buf + i * C::ROW;
         float2 v[8];
 #pragma unroll
@@ -665,10 +701,7 @@ row_phase_tv(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp, co
 #pragma unroll
         for (int m = 0; m < 8; ++m) row[pad8(t + m * C::FT)] = v[m];
         group_sync<W>(g);            // the split reads this group's row only
-        if (i <= R) {
-            const int q = r0 - 1 + i;
-            store_split<W>(P.Sb + (size_t)q * Wp, row, t);
-        }
+        store_split<W>(P.Sb + (size_t)(r0 - 1 + i) * Wp, row, t);
     }
 }
 
