@@ -183,4 +183,52 @@ __device__ __forceinline__ void fft_group(float2 (&v)[8], float2* buf, const flo
     group_sync<N>(g);
 }
 
+// Two transforms of the same length and direction on one group, interleaved
+// pass by pass: the twiddles, index arithmetic and barriers are shared and the
+// two dependency chains overlap. Same layout and contract as fft_group.
+template <int N, int DIR>
+__device__ __forceinline__ void fft_group2(float2 (&v)[8], float2 (&u)[8], float2* bv, float2* bu,
+                                           const float2* tw, int t, int g) {
+    using S = FftShape<N>;
+    constexpr int Q = N / 8;
+    int oidx[8];
+    int Ns = 1;
+    stockham_compute<N, S::R0, DIR>(v, t, Ns, tw, oidx);
+    stockham_compute<N, S::R0, DIR>(u, t, Ns, tw, oidx);
+    Ns *= S::R0;
+#pragma unroll
+    for (int p = 0; p < S::NP8; ++p) {
+        group_sync<N>(g);
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+            bv[pad8(oidx[m])] = v[m];
+            bu[pad8(oidx[m])] = u[m];
+        }
+        group_sync<N>(g);
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+            v[m] = bv[pad8(t + m * Q)];
+            u[m] = bu[pad8(t + m * Q)];
+        }
+        // shared twiddles: exp(DIR 2 pi i r k / (8 Ns)), k = t mod Ns
+        const int k = t & (Ns - 1);
+        if (Ns > 1) {
+            const int step = N / (Ns * 8);
+#pragma unroll
+            for (int r = 1; r < 8; ++r) {
+                const float2 w = twid<DIR>(tw, r * k * step);
+                v[r] = cmul(v[r], w);
+                u[r] = cmul(u[r], w);
+            }
+        }
+        dft8<DIR>(v);
+        dft8<DIR>(u);
+        const int base = (t - k) * 8 + k;
+#pragma unroll
+        for (int r = 0; r < 8; ++r) oidx[r] = base + r * Ns;
+        Ns *= 8;
+    }
+    group_sync<N>(g);
+}
+
 }  // namespace admm

@@ -93,8 +93,9 @@ haar_row_inverse(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp
         }
         if (sprev) P.xprev[pix] = x;
     }
-    double pv[kNumPartials] = {s_data.value(), 0.0, s_xx.value(), s_dxx.value()};
-    block_reduce_partials(pv, red);
+    const CompSum acc[kNumPartials] = {s_data, CompSum(), s_xx, s_dxx};
+    double pv[kNumPartials];
+    block_reduce_comp(acc, reinterpret_cast<float*>(red), pv);
     if (tid == 0) {
 #pragma unroll
         for (int j = 0; j < kNumPartials; ++j) P.partials[blockIdx.x * kNumPartials + j] = pv[j];
@@ -254,8 +255,9 @@ haar_tile(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W, int n_
         const int r = e / T, c = e % T;
         ww[(size_t)(R0 + r) * W + (C0 + c)] = gam * At[(r + HALO) * XD + (c + HALO)];
     }
-    double pv[kNumPartials] = {0.0, l1.value(), 0.0, 0.0};
-    block_reduce_partials(pv, red);
+    const CompSum acc[kNumPartials] = {CompSum(), l1, CompSum(), CompSum()};
+    double pv[kNumPartials];
+    block_reduce_comp(acc, reinterpret_cast<float*>(red), pv);
     if (tid == 0) finish_iteration(P, k, chk, nobj, pv, n_active, n_row_ctas + blockIdx.x, probs, sl);
 }
 

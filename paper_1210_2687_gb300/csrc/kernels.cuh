@@ -315,8 +315,7 @@ col_phase(const ProbDesc* __restrict__ probs, SlotTable sl, int Wc, int Wp, cons
             v[m] = make_float2(f.x, f.y);
             u[m] = make_float2(f.z, f.w);
         }
-        fft_group<H, -1>(v, bz, tw, t, g);
-        fft_group<H, -1>(u, bw, tw, t, g);
+        fft_group2<H, -1>(v, u, bz, bw, tw, t, g);
         if (spec) {
 #pragma unroll
             for (int m = 0; m < 8; ++m) {
@@ -326,8 +325,7 @@ col_phase(const ProbDesc* __restrict__ probs, SlotTable sl, int Wc, int Wp, cons
                 u[m] = cmul(L[m], xh);
             }
         }
-        fft_group<H, 1>(v, bz, tw, t, g);
-        fft_group<H, 1>(u, bw, tw, t, g);
+        fft_group2<H, 1>(v, u, bz, bw, tw, t, g);
 #pragma unroll
         for (int m = 0; m < 8; ++m) {
             const int r = t + m * C::FT;
@@ -397,6 +395,45 @@ __device__ __forceinline__ void block_reduce_partials(double (&v)[kNumPartials],
         for (int w = 1; w < kThreads / 32; ++w) {
 #pragma unroll
             for (int j = 0; j < kNumPartials; ++j) v[j] += red[w * kNumPartials + j];
+        }
+    }
+}
+
+// Block reduction of kNumPartials compensated FP32 sums: the running sums
+// and their compensation terms are reduced separately in FP32 across the
+// block (FP64 arithmetic is slow on this part) and combined in FP64 by
+// thread 0, which receives the block's totals in `out`.
+__device__ __forceinline__ void block_reduce_comp(const CompSum (&a)[kNumPartials], float* red,
+                                                  double (&out)[kNumPartials]) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float s[kNumPartials], c[kNumPartials];
+#pragma unroll
+    for (int j = 0; j < kNumPartials; ++j) {
+        s[j] = a[j].s;
+        c[j] = a[j].c;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            s[j] += __shfl_down_sync(0xffffffffu, s[j], o);
+            c[j] += __shfl_down_sync(0xffffffffu, c[j], o);
+        }
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int j = 0; j < kNumPartials; ++j) {
+            red[warp * 2 * kNumPartials + j] = s[j];
+            red[warp * 2 * kNumPartials + kNumPartials + j] = c[j];
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int j = 0; j < kNumPartials; ++j) {
+            double acc = 0.0, cmp = 0.0;
+            for (int w = 0; w < kThreads / 32; ++w) {
+                acc += (double)red[w * 2 * kNumPartials + j];
+                cmp += (double)red[w * 2 * kNumPartials + kNumPartials + j];
+            }
+            out[j] = acc + cmp;
         }
     }
 }
@@ -684,11 +721,11 @@ row_phase_tv(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp, co
     cp_async_wait<0>();              // only empty groups remain; nothing left in flight
     __syncthreads();
 
-    // (3) partial sums -> last CTA evaluates the stop rule
+    // (3) block partial sums (published after the transforms below)
+    double part[kNumPartials];
     {
-        double v[kNumPartials] = {s_data.value(), s_reg.value(), s_xx.value(), s_dxx.value()};
-        block_reduce_partials(v, red);
-        if (tid == 0) finish_iteration(P, k, chk, nobj, v, n_active, blockIdx.x, probs, sl);
+        const CompSum acc[kNumPartials] = {s_data, s_reg, s_xx, s_dxx};
+        block_reduce_comp(acc, reinterpret_cast<float*>(red), part);
     }
 
     // (4) forward row DFTs of p = zeta1 + i w on rows 1..R and split
@@ -703,6 +740,10 @@ row_phase_tv(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp, co
         group_sync<W>(g);            // the split reads this group's row only
         store_split<W>(P.Sb + (size_t)(r0 - 1 + i) * Wp, row, t);
     }
+
+    // (5) the last CTA of the problem evaluates the stop rule; done last so
+    // that the memory fence it needs does not hold up the transforms
+    if (tid == 0) finish_iteration(P, k, chk, nobj, part, n_active, blockIdx.x, probs, sl);
 }
 
 // ---------------------------------------------------------------------------
