@@ -198,19 +198,19 @@ cudaError_t launch_col(int H, const ProbDesc* d, SlotTable sl, int count, int Wc
     return cudaErrorInvalidValue;
 }
 
-template <int W, int R, int D>
+template <int W, int R, int D, int NT>
 cudaError_t launch_row_tv_t(const ProbDesc* d, SlotTable sl, int count, int H, int Wp, const float2* tw,
                             int* n_active, cudaStream_t s) {
     static bool attr = false;
-    const size_t smem = RowCfg<W, R, D>::SMEM;
+    const size_t smem = RowCfg<W, R, D, NT>::SMEM;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(row_phase_tv<W, R, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(row_phase_tv<W, R, D, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
         if (e != cudaSuccess) return e;
         attr = true;
     }
     dim3 grid(H / R, count);
-    row_phase_tv<W, R, D><<<grid, kThreads, smem, s>>>(d, sl, H, Wp, tw, n_active);
+    row_phase_tv<W, R, D, NT><<<grid, NT, smem, s>>>(d, sl, H, Wp, tw, n_active);
     return cudaGetLastError();
 }
 
@@ -218,12 +218,12 @@ cudaError_t launch_row_tv(int W, const ProbDesc* d, SlotTable sl, int count, int
                           int* n_active, cudaStream_t s) {
     switch (W) {
         // (rows per strip, walk rows in flight); must agree with row_strip_tv
-        case 64: return launch_row_tv_t<64, 16, 4>(d, sl, count, H, Wp, tw, n_active, s);
-        case 128: return launch_row_tv_t<128, 16, 4>(d, sl, count, H, Wp, tw, n_active, s);
-        case 256: return launch_row_tv_t<256, 8, 4>(d, sl, count, H, Wp, tw, n_active, s);
-        case 512: return launch_row_tv_t<512, 8, 4>(d, sl, count, H, Wp, tw, n_active, s);
-        case 1024: return launch_row_tv_t<1024, 4, 2>(d, sl, count, H, Wp, tw, n_active, s);
-        case 2048: return launch_row_tv_t<2048, 4, 1>(d, sl, count, H, Wp, tw, n_active, s);
+        case 64: return launch_row_tv_t<64, 16, 4, 256>(d, sl, count, H, Wp, tw, n_active, s);
+        case 128: return launch_row_tv_t<128, 16, 4, 256>(d, sl, count, H, Wp, tw, n_active, s);
+        case 256: return launch_row_tv_t<256, 8, 4, 256>(d, sl, count, H, Wp, tw, n_active, s);
+        case 512: return launch_row_tv_t<512, 8, 4, 256>(d, sl, count, H, Wp, tw, n_active, s);
+        case 1024: return launch_row_tv_t<1024, 4, 2, 256>(d, sl, count, H, Wp, tw, n_active, s);
+        case 2048: return launch_row_tv_t<2048, 4, 1, 256>(d, sl, count, H, Wp, tw, n_active, s);
     }
     return cudaErrorInvalidValue;
 }

@@ -403,6 +403,7 @@ __device__ __forceinline__ void block_reduce_partials(double (&v)[kNumPartials],
 // and their compensation terms are reduced separately in FP32 across the
 // block (FP64 arithmetic is slow on this part) and combined in FP64 by
 // thread 0, which receives the block's totals in `out`.
+template <int NT = kThreads>
 __device__ __forceinline__ void block_reduce_comp(const CompSum (&a)[kNumPartials], float* red,
                                                   double (&out)[kNumPartials]) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -429,7 +430,7 @@ __device__ __forceinline__ void block_reduce_comp(const CompSum (&a)[kNumPartial
 #pragma unroll
         for (int j = 0; j < kNumPartials; ++j) {
             double acc = 0.0, cmp = 0.0;
-            for (int w = 0; w < kThreads / 32; ++w) {
+            for (int w = 0; w < NT / 32; ++w) {
                 acc += (double)red[w * 2 * kNumPartials + j];
                 cmp += (double)red[w * 2 * kNumPartials + kNumPartials + j];
             }
@@ -515,14 +516,15 @@ __device__ void finish_iteration(const ProbDesc& P, int k, bool chk, bool nobj,
 // halo entry). x values of the neighbouring warps' boundary columns are
 // captured in registers before any warp overwrites its rows with p.
 // ---------------------------------------------------------------------------
-template <int W, int R, int D>
+template <int W, int R, int D, int NT>
 struct RowCfg {
     static constexpr int FT = W / 8;
-    static constexpr int G = kThreads / FT;                        // row transforms in flight
+    static constexpr int G = NT / FT;                              // row transforms in flight
+    static_assert(G >= 1 && NT % FT == 0, "block too small for one row transform");
     static constexpr int NB = R + 2;                               // buffer rows
     static constexpr int ROW = pad8(W);                            // float2 per buffer row
     static constexpr int RAW = W / 2 + 1;                          // float4 per half-spectrum row
-    static constexpr int NWARP = kThreads / 32;
+    static constexpr int NWARP = NT / 32;
     static constexpr int CW = W / NWARP;                           // columns per warp
     static constexpr int CPT = CW >= 32 ? CW / 32 : 1;              // columns per thread
     static constexpr int SLOT = 5 * W + 2 * NWARP;                 // floats per ring slot
@@ -531,14 +533,14 @@ struct RowCfg {
     static_assert(((size_t)NB * ROW * 8 + (size_t)W * 8) % 16 == 0, "ring alignment");
     static_assert(((size_t)NB * ROW * 8 + (size_t)W * 8 + (size_t)D * SLOT * 4) % 8 == 0, "scratch alignment");
     static constexpr size_t SMEM = (size_t)NB * ROW * sizeof(float2) + (size_t)W * sizeof(float2)
-                                 + (size_t)D * SLOT * sizeof(float) + 8 * kNumPartials * sizeof(double);
+                                 + (size_t)D * SLOT * sizeof(float) + NWARP * 2 * kNumPartials * sizeof(float);
 };
 
-template <int W, int R, int D>
-__global__ void __launch_bounds__(kThreads, 2)
+template <int W, int R, int D, int NT>
+__global__ void __launch_bounds__(NT, (NT == 128 ? 4 : 2))
 row_phase_tv(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp, const float2* __restrict__ tw_g,
              int* __restrict__ n_active) {
-    using C = RowCfg<W, R, D>;
+    using C = RowCfg<W, R, D, NT>;
     const int pi = sl.map[blockIdx.y];
     if (pi < 0) return;
     const ProbDesc& P = probs[pi];
@@ -584,7 +586,7 @@ row_phase_tv(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp, co
     };
 
     // (0) requests: half spectra of rows r0-1 .. r0+R, then the first D walk rows
-    for (int e = tid; e < (R + 2) * C::RAW; e += kThreads) {
+    for (int e = tid; e < (R + 2) * C::RAW; e += NT) {
         const int i = e / C::RAW, kk = e % C::RAW;
         const int q = (r0 - 1 + i + H) & (H - 1);
         cp_async16(reinterpret_cast<float4*>(buf + i * C::ROW) + kk, P.Sa + (size_t)q * Wp + kk);
@@ -592,7 +594,7 @@ row_phase_tv(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp, co
     cp_async_commit();
 #pragma unroll
     for (int i = 0; i < D; ++i) issue(i);
-    for (int i = tid; i < W; i += kThreads) tw[i] = tw_g[i * (2048 / W)];
+    for (int i = tid; i < W; i += NT) tw[i] = tw_g[i * (2048 / W)];
     cp_async_wait<D>();          // the spectra have landed
     __syncthreads();
     const int g = tid / C::FT, t = tid % C::FT;
@@ -725,7 +727,7 @@ row_phase_tv(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp, co
     double part[kNumPartials];
     {
         const CompSum acc[kNumPartials] = {s_data, s_reg, s_xx, s_dxx};
-        block_reduce_comp(acc, reinterpret_cast<float*>(red), part);
+        block_reduce_comp<NT>(acc, reinterpret_cast<float*>(red), part);
     }
 
     // (4) forward row DFTs of p = zeta1 + i w on rows 1..R and split
