@@ -71,6 +71,10 @@ struct DeviceCtx {
     ProbDesc* h_desc = nullptr;      // pinned staging for the table
     float** h_xptr = nullptr;
     cudaEvent_t ev[2] = {nullptr, nullptr};
+    cudaStream_t cap = nullptr;      // private stream for graph capture
+    // chunk graphs: (H, W, reg, levels, slots, chunk) -> executable graph;
+    // cleared whenever the descriptor or slot tables move
+    std::map<std::tuple<int, int, int, int, int, int>, cudaGraphExec_t> graphs;
 };
 std::map<int, DeviceCtx> g_ctx;
 
@@ -122,10 +126,13 @@ int ensure_ctx(int dev, int count, DeviceCtx** out) {
         CK(cudaHostAlloc(&c.h_active, 2 * sizeof(int), cudaHostAllocDefault));
         CK(cudaEventCreateWithFlags(&c.ev[0], cudaEventDisableTiming));
         CK(cudaEventCreateWithFlags(&c.ev[1], cudaEventDisableTiming));
+        CK(cudaStreamCreateWithFlags(&c.cap, cudaStreamNonBlocking));
         c.ready = true;
     }
     if (count > c.cap) {
         int cap = std::max(count, 2 * c.cap);
+        for (auto& kv : c.graphs) cudaGraphExecDestroy(kv.second);
+        c.graphs.clear();
         if (c.desc) cudaFree(c.desc);
         if (c.xptr) cudaFree(c.xptr);
         if (c.slot_map) cudaFree(c.slot_map);
@@ -462,6 +469,45 @@ int admm_deconv_get_state(admm_plan_t plan, float* d_out, void* stream) {
     return ADMM_OK;
 }
 
+// one ADMM iteration of a group: the column phase, then the row side
+static cudaError_t launch_iteration(DeviceCtx* ctx, int H, int W, int Wc, int Wp, bool tv, int levels, SlotTable sl,
+                                    int nslots, cudaStream_t s) {
+    cudaError_t e = launch_col(H, ctx->desc, sl, nslots, Wc, Wp, ctx->tw, s);
+    if (e != cudaSuccess) return e;
+    if (tv) return launch_row_tv(W, ctx->desc, sl, nslots, H, Wp, ctx->tw, ctx->n_active, s);
+    return launch_haar_iteration_rows(W, H, Wp, ctx->desc, sl, nslots, levels, ctx->tw, ctx->n_active, s);
+}
+
+// executable graph of `chunk` iterations (captured on the private stream)
+static cudaError_t chunk_graph(DeviceCtx* ctx, int H, int W, int Wc, int Wp, bool tv, int levels, SlotTable sl,
+                               int nslots, int chunk, cudaGraphExec_t* out) {
+    const auto key = std::make_tuple(H, W, tv ? 0 : 1, levels, nslots, chunk);
+    auto it = ctx->graphs.find(key);
+    if (it != ctx->graphs.end()) {
+        *out = it->second;
+        return cudaSuccess;
+    }
+    cudaError_t e = cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    cudaError_t le = cudaSuccess;
+    for (int i = 0; i < chunk && le == cudaSuccess; ++i)
+        le = launch_iteration(ctx, H, W, Wc, Wp, tv, levels, sl, nslots, ctx->cap);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(ctx->cap, &g);
+    if (le != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return le;
+    }
+    if (e != cudaSuccess) return e;
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return e;
+    ctx->graphs[key] = exec;
+    *out = exec;
+    return cudaSuccess;
+}
+
 static int solve_group(DeviceCtx* ctx, const std::vector<int>& idx, const admm_plan_t* plans,
                        const float* const* y, const uint8_t* const* masks, float* const* x_out,
                        admm_result_t* res, cudaStream_t s) {
@@ -526,6 +572,14 @@ static int solve_group(DeviceCtx* ctx, const std::vector<int>& idx, const admm_p
     int launched = 0, j = 0;
     while (launched < max_iters) {
         const int nit = std::min(chunk, max_iters - launched);
+        if (!prof && j > 0 && nit == chunk) {
+            // steady state: one graph replay per chunk (the first chunk ran
+            // as plain launches, which also set the kernels' attributes)
+            cudaGraphExec_t exec = nullptr;
+            CK(chunk_graph(ctx, H, W, Wc, Wp, tv, p0->levels, sl, nslots, chunk, &exec));
+            CK(cudaGraphLaunch(exec, s));
+            g_launches += (long long)chunk * (tv ? 2 : 4);
+        } else
         for (int it = 0; it < nit; ++it) {
             CK(launch_col(H, ctx->desc, sl, nslots, Wc, Wp, ctx->tw, s));
             ++g_launches;

@@ -211,6 +211,26 @@ def test_queued_problems_start_as_slots_free_up(ad):
         assert torch.equal(xo, xs[i]), i
 
 
+def test_graph_replay_equals_direct_launches(ad):
+    """Chunks of iterations replay as CUDA graphs; with per-phase timing on,
+    the same iterations run as individual launches. Same bits either way."""
+    import torch
+    xt, psf, ybar, mask = _case_problem(128, 128, lambda: S.psf_gaussian(9, 2.0), 0.7, 70)
+    plan = ad.Plan(128, 128, psf, 3e-4, 1e-2, 3e-3, "tv", max_iters=37)
+    y = torch.from_numpy(ybar.astype(np.float32)).cuda()
+    m = torch.from_numpy(mask).cuda()
+    xa = torch.empty((128, 128), dtype=torch.float32, device="cuda")
+    xb = torch.empty_like(xa)
+    ra = ad.solve(plan, y, m, xa)
+    ad.admm_deconv_profile(True)
+    rb = ad.solve(plan, y, m, xb)
+    prof = ad.admm_deconv_profile(False)
+    torch.cuda.synchronize()
+    assert prof.col_launches == 37 and prof.row_launches == 37
+    assert ra.iters == rb.iters == 37
+    assert torch.equal(xa, xb)
+
+
 def test_host_buffers_equal_device_buffers(ad):
     """y, mask and x_out in host memory take the staging path; same bits."""
     import torch
