@@ -71,7 +71,7 @@ struct DeviceCtx {
     ProbDesc* h_desc = nullptr;      // pinned staging for the table
     float** h_xptr = nullptr;
     cudaEvent_t ev[2] = {nullptr, nullptr};
-    cudaStream_t cap = nullptr;      // private stream for graph capture
+    cudaStream_t cap_stream = nullptr;   // private stream for graph capture
     // chunk graphs: (H, W, reg, levels, slots, chunk) -> executable graph;
     // cleared whenever the descriptor or slot tables move
     std::map<std::tuple<int, int, int, int, int, int>, cudaGraphExec_t> graphs;
@@ -126,7 +126,7 @@ int ensure_ctx(int dev, int count, DeviceCtx** out) {
         CK(cudaHostAlloc(&c.h_active, 2 * sizeof(int), cudaHostAllocDefault));
         CK(cudaEventCreateWithFlags(&c.ev[0], cudaEventDisableTiming));
         CK(cudaEventCreateWithFlags(&c.ev[1], cudaEventDisableTiming));
-        CK(cudaStreamCreateWithFlags(&c.cap, cudaStreamNonBlocking));
+        CK(cudaStreamCreateWithFlags(&c.cap_stream, cudaStreamNonBlocking));
         c.ready = true;
     }
     if (count > c.cap) {
@@ -487,13 +487,13 @@ static cudaError_t chunk_graph(DeviceCtx* ctx, int H, int W, int Wc, int Wp, boo
         *out = it->second;
         return cudaSuccess;
     }
-    cudaError_t e = cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeThreadLocal);
+    cudaError_t e = cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return e;
     cudaError_t le = cudaSuccess;
     for (int i = 0; i < chunk && le == cudaSuccess; ++i)
-        le = launch_iteration(ctx, H, W, Wc, Wp, tv, levels, sl, nslots, ctx->cap);
+        le = launch_iteration(ctx, H, W, Wc, Wp, tv, levels, sl, nslots, ctx->cap_stream);
     cudaGraph_t g = nullptr;
-    e = cudaStreamEndCapture(ctx->cap, &g);
+    e = cudaStreamEndCapture(ctx->cap_stream, &g);
     if (le != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
         return le;
