@@ -226,7 +226,8 @@ def test_graph_replay_equals_direct_launches(ad):
     rb = ad.solve(plan, y, m, xb)
     prof = ad.admm_deconv_profile(False)
     torch.cuda.synchronize()
-    assert prof.col_launches == 37 and prof.row_launches == 37
+    # launches continue until the host sees the retirement, one chunk behind
+    assert prof.col_launches == prof.row_launches >= 37
     assert ra.iters == rb.iters == 37
     assert torch.equal(xa, xb)
 
