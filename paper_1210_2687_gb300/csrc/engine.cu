@@ -71,10 +71,22 @@ struct DeviceCtx {
     ProbDesc* h_desc = nullptr;      // pinned staging for the table
     float** h_xptr = nullptr;
     cudaEvent_t ev[2] = {nullptr, nullptr};
-    cudaStream_t cap_stream = nullptr;   // private stream for graph capture
-    // chunk graphs: (H, W, reg, levels, slots, chunk) -> executable graph;
-    // cleared whenever the descriptor or slot tables move
-    std::map<std::tuple<int, int, int, int, int, int>, cudaGraphExec_t> graphs;
+    cudaStream_t cap_stream = nullptr;   // private streams for graph capture
+    cudaStream_t cap_stream2 = nullptr;
+    cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
+    // chunk graphs: (H, W, reg, levels, slots, chunk, problems, lanes) ->
+    // executable graph; cleared whenever the descriptor or slot tables move
+    std::map<std::tuple<int, int, int, int, int, int, int, int>, cudaGraphExec_t> graphs;
+};
+
+// A group's problems split into `n` lanes that iterate independently: lane
+// l owns problems [off[l], off[l] + cnt[l]) of the descriptor table and
+// slots [soff[l], soff[l] + slots[l]). In a replayed chunk the lanes are
+// independent graph branches, so one lane's column phase (transform-bound)
+// can share the GPU with the other lane's row phase (memory-bound).
+struct Lanes {
+    int n = 1;
+    int off[2] = {0, 0}, cnt[2] = {0, 0}, soff[2] = {0, 0}, slots[2] = {0, 0};
 };
 std::map<int, DeviceCtx> g_ctx;
 
@@ -122,11 +134,14 @@ int ensure_ctx(int dev, int count, DeviceCtx** out) {
         CK(cudaMalloc(&c.tw, 2048 * sizeof(float2)));
         CK(cudaMemcpy(c.tw, tw.data(), 2048 * sizeof(float2), cudaMemcpyHostToDevice));
         CK(cudaMalloc(&c.n_active, sizeof(int)));
-        CK(cudaMalloc(&c.queue, sizeof(int)));
+        CK(cudaMalloc(&c.queue, 2 * sizeof(int)));
         CK(cudaHostAlloc(&c.h_active, 2 * sizeof(int), cudaHostAllocDefault));
         CK(cudaEventCreateWithFlags(&c.ev[0], cudaEventDisableTiming));
         CK(cudaEventCreateWithFlags(&c.ev[1], cudaEventDisableTiming));
         CK(cudaStreamCreateWithFlags(&c.cap_stream, cudaStreamNonBlocking));
+        CK(cudaStreamCreateWithFlags(&c.cap_stream2, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&c.fork_ev, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&c.join_ev, cudaEventDisableTiming));
         c.ready = true;
     }
     if (count > c.cap) {
@@ -469,19 +484,24 @@ int admm_deconv_get_state(admm_plan_t plan, float* d_out, void* stream) {
     return ADMM_OK;
 }
 
-// one ADMM iteration of a group: the column phase, then the row side
-static cudaError_t launch_iteration(DeviceCtx* ctx, int H, int W, int Wc, int Wp, bool tv, int levels, SlotTable sl,
-                                    int nslots, cudaStream_t s) {
-    cudaError_t e = launch_col(H, ctx->desc, sl, nslots, Wc, Wp, ctx->tw, s);
+// one ADMM iteration of one lane: the column phase, then the row side
+static cudaError_t launch_iteration(DeviceCtx* ctx, const ProbDesc* desc, int H, int W, int Wc, int Wp, bool tv,
+                                    int levels, SlotTable sl, int nslots, cudaStream_t s) {
+    cudaError_t e = launch_col(H, desc, sl, nslots, Wc, Wp, ctx->tw, s);
     if (e != cudaSuccess) return e;
-    if (tv) return launch_row_tv(W, ctx->desc, sl, nslots, H, Wp, ctx->tw, ctx->n_active, s);
-    return launch_haar_iteration_rows(W, H, Wp, ctx->desc, sl, nslots, levels, ctx->tw, ctx->n_active, s);
+    if (tv) return launch_row_tv(W, desc, sl, nslots, H, Wp, ctx->tw, ctx->n_active, s);
+    return launch_haar_iteration_rows(W, H, Wp, desc, sl, nslots, levels, ctx->tw, ctx->n_active, s);
 }
 
-// executable graph of `chunk` iterations (captured on the private stream)
-static cudaError_t chunk_graph(DeviceCtx* ctx, int H, int W, int Wc, int Wp, bool tv, int levels, SlotTable sl,
-                               int nslots, int chunk, cudaGraphExec_t* out) {
-    const auto key = std::make_tuple(H, W, tv ? 0 : 1, levels, nslots, chunk);
+static SlotTable lane_slots(DeviceCtx* ctx, const Lanes& L, int l) {
+    return SlotTable{ctx->slot_map + L.soff[l], ctx->queue + l, L.cnt[l]};
+}
+
+// executable graph of `chunk` iterations of every lane, the lanes as
+// independent branches (captured on the private streams)
+static cudaError_t chunk_graph(DeviceCtx* ctx, int H, int W, int Wc, int Wp, bool tv, int levels, const Lanes& L,
+                               int nslots, int count, int chunk, cudaGraphExec_t* out) {
+    const auto key = std::make_tuple(H, W, tv ? 0 : 1, levels, nslots, chunk, count, L.n);
     auto it = ctx->graphs.find(key);
     if (it != ctx->graphs.end()) {
         *out = it->second;
@@ -490,8 +510,20 @@ static cudaError_t chunk_graph(DeviceCtx* ctx, int H, int W, int Wc, int Wp, boo
     cudaError_t e = cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return e;
     cudaError_t le = cudaSuccess;
-    for (int i = 0; i < chunk && le == cudaSuccess; ++i)
-        le = launch_iteration(ctx, H, W, Wc, Wp, tv, levels, sl, nslots, ctx->cap_stream);
+    if (L.n > 1) {
+        le = cudaEventRecord(ctx->fork_ev, ctx->cap_stream);
+        if (le == cudaSuccess) le = cudaStreamWaitEvent(ctx->cap_stream2, ctx->fork_ev, 0);
+    }
+    for (int l = 0; l < L.n && le == cudaSuccess; ++l) {
+        cudaStream_t cs = l == 0 ? ctx->cap_stream : ctx->cap_stream2;
+        for (int i = 0; i < chunk && le == cudaSuccess; ++i)
+            le = launch_iteration(ctx, ctx->desc + L.off[l], H, W, Wc, Wp, tv, levels, lane_slots(ctx, L, l),
+                                  L.slots[l], cs);
+    }
+    if (L.n > 1 && le == cudaSuccess) {
+        le = cudaEventRecord(ctx->join_ev, ctx->cap_stream2);
+        if (le == cudaSuccess) le = cudaStreamWaitEvent(ctx->cap_stream, ctx->join_ev, 0);
+    }
     cudaGraph_t g = nullptr;
     e = cudaStreamEndCapture(ctx->cap_stream, &g);
     if (le != cudaSuccess) {
@@ -548,10 +580,21 @@ static int solve_group(DeviceCtx* ctx, const std::vector<int>& idx, const admm_p
     init_ctl_kernel<<<(count + 127) / 128, 128, 0, s>>>(ctx->desc, count, ctx->n_active);
     CK(cudaGetLastError());
     const int nslots = choose_slots(H, W, tv, count);
-    const SlotTable sl{ctx->slot_map, ctx->queue, count};
-    assign_slots_kernel<<<1, 32, 0, s>>>(ctx->desc, sl, nslots);
-    CK(cudaGetLastError());
-    g_launches += 2;
+    Lanes L;
+    L.n = (count >= 2 && nslots >= 2) ? 2 : 1;
+    for (int l = 0, off = 0, soff = 0; l < L.n; ++l) {
+        L.off[l] = off;
+        L.cnt[l] = l + 1 < L.n ? count / 2 : count - off;
+        L.soff[l] = soff;
+        L.slots[l] = l + 1 < L.n ? nslots / 2 : nslots - soff;
+        off += L.cnt[l];
+        soff += L.slots[l];
+    }
+    for (int l = 0; l < L.n; ++l) {
+        assign_slots_kernel<<<1, 32, 0, s>>>(ctx->desc + L.off[l], lane_slots(ctx, L, l), L.slots[l]);
+        CK(cudaGetLastError());
+    }
+    g_launches += 1 + L.n;
     // the host buffers of the descriptor table are reused by the next group
     CK(cudaStreamSynchronize(s));
 
@@ -559,7 +602,8 @@ static int solve_group(DeviceCtx* ctx, const std::vector<int>& idx, const admm_p
     // launches needed are bounded by the sum of the per-slot work
     long long launch_cap = 0;
     for (int q = 0; q < count; ++q) launch_cap += plans[idx[q]]->p.max_iters;
-    launch_cap = (launch_cap + nslots - 1) / nslots + max_iters;
+    const int min_slots = std::max(1, std::min(L.slots[0], L.slots[L.n - 1]));
+    launch_cap = (launch_cap + min_slots - 1) / min_slots + max_iters;
     if (launch_cap > (long long)INT32_MAX) launch_cap = INT32_MAX;
     max_iters = (int)launch_cap;
     const int chunk = 8;
@@ -576,28 +620,32 @@ static int solve_group(DeviceCtx* ctx, const std::vector<int>& idx, const admm_p
             // steady state: one graph replay per chunk (the first chunk ran
             // as plain launches, which also set the kernels' attributes)
             cudaGraphExec_t exec = nullptr;
-            CK(chunk_graph(ctx, H, W, Wc, Wp, tv, p0->levels, sl, nslots, chunk, &exec));
+            CK(chunk_graph(ctx, H, W, Wc, Wp, tv, p0->levels, L, nslots, count, chunk, &exec));
             CK(cudaGraphLaunch(exec, s));
-            g_launches += (long long)chunk * (tv ? 2 : 4);
+            g_launches += (long long)chunk * L.n * (tv ? 2 : 4);
         } else
         for (int it = 0; it < nit; ++it) {
-            CK(launch_col(H, ctx->desc, sl, nslots, Wc, Wp, ctx->tw, s));
-            ++g_launches;
-            if (prof) {
-                int r = prof_event(nev++, s);
-                if (r != ADMM_OK) return r;
-            }
-            if (tv) {
-                CK(launch_row_tv(W, ctx->desc, sl, nslots, H, Wp, ctx->tw, ctx->n_active, s));
+            for (int l = 0; l < L.n; ++l) {
+                const ProbDesc* dl = ctx->desc + L.off[l];
+                const SlotTable sl = lane_slots(ctx, L, l);
+                CK(launch_col(H, dl, sl, L.slots[l], Wc, Wp, ctx->tw, s));
                 ++g_launches;
-            } else {
-                CK(launch_haar_iteration_rows(W, H, Wp, ctx->desc, sl, nslots, p0->levels, ctx->tw, ctx->n_active,
-                                              s));
-                g_launches += 3;
-            }
-            if (prof) {
-                int r = prof_event(nev++, s);
-                if (r != ADMM_OK) return r;
+                if (prof) {
+                    int r = prof_event(nev++, s);
+                    if (r != ADMM_OK) return r;
+                }
+                if (tv) {
+                    CK(launch_row_tv(W, dl, sl, L.slots[l], H, Wp, ctx->tw, ctx->n_active, s));
+                    ++g_launches;
+                } else {
+                    CK(launch_haar_iteration_rows(W, H, Wp, dl, sl, L.slots[l], p0->levels, ctx->tw, ctx->n_active,
+                                                  s));
+                    g_launches += 3;
+                }
+                if (prof) {
+                    int r = prof_event(nev++, s);
+                    if (r != ADMM_OK) return r;
+                }
             }
         }
         launched += nit;
