@@ -580,8 +580,11 @@ static int solve_group(DeviceCtx* ctx, const std::vector<int>& idx, const admm_p
     init_ctl_kernel<<<(count + 127) / 128, 128, 0, s>>>(ctx->desc, count, ctx->n_active);
     CK(cudaGetLastError());
     const int nslots = choose_slots(H, W, tv, count);
+    const bool prof = g_prof.on;
     Lanes L;
-    L.n = (count >= 2 && nslots >= 2) ? 2 : 1;
+    // with per-phase timing on, one lane: every launch covers all slots, so
+    // the timed phases are the full-size kernels
+    L.n = (!prof && count >= 2 && nslots >= 2) ? 2 : 1;
     for (int l = 0, off = 0, soff = 0; l < L.n; ++l) {
         L.off[l] = off;
         L.cnt[l] = l + 1 < L.n ? count / 2 : count - off;
@@ -607,7 +610,6 @@ static int solve_group(DeviceCtx* ctx, const std::vector<int>& idx, const admm_p
     if (launch_cap > (long long)INT32_MAX) launch_cap = INT32_MAX;
     max_iters = (int)launch_cap;
     const int chunk = 8;
-    const bool prof = g_prof.on;
     size_t nev = 0;
     if (prof) {
         int r = prof_event(nev++, s);
