@@ -254,7 +254,7 @@ template <int W>
 cudaError_t launch_fin_t(const ProbDesc* d, float* const* xo, int count, int H, int Wp, const float2* tw,
                          cudaStream_t s) {
     constexpr int FT = W / 8, G = kThreads / FT;
-    const size_t smem = (size_t)(G * pad8(W) + W) * sizeof(float2);
+    const size_t smem = (size_t)(G * W + W) * sizeof(float2);
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(finalize_x<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

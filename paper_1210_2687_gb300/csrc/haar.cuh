@@ -43,7 +43,7 @@ inline int haar_num_tiles(int H, int W) { return (H / kHaarTile) * (W / kHaarTil
 template <int W>
 __global__ void __launch_bounds__(kThreads)
 haar_row_inverse(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp, const float2* __restrict__ tw_g) {
-    constexpr int FT = W / 8, G = kThreads / FT, ROW = pad8(W);
+    constexpr int FT = W / 8, G = kThreads / FT, ROW = W;
     const int pi = sl.map[blockIdx.y];
     if (pi < 0) return;
     const ProbDesc& P = probs[pi];
@@ -267,7 +267,7 @@ haar_tile(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W, int n_
 template <int W>
 __global__ void __launch_bounds__(kThreads)
 haar_row_forward(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp, const float2* __restrict__ tw_g) {
-    constexpr int FT = W / 8, G = kThreads / FT, ROW = pad8(W);
+    constexpr int FT = W / 8, G = kThreads / FT, ROW = W;
     const int pi = sl.map[blockIdx.y];
     if (pi < 0) return;
     const ProbDesc& P = probs[pi];
@@ -289,7 +289,7 @@ haar_row_forward(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp
     float2* row = buf + g * ROW;
     fft_group<W, -1>(v, row, tw, t, g);
 #pragma unroll
-    for (int m = 0; m < 8; ++m) row[pad8(t + m * FT)] = v[m];
+    for (int m = 0; m < 8; ++m) row[swz(t + m * FT)] = v[m];
     group_sync<W>(g);                // the split reads this group's row only
     store_split<W>(P.Sb + (size_t)q * Wp, row, t);
 }
@@ -301,7 +301,7 @@ template <int W>
 cudaError_t launch_haar_rows_t(int H, int Wp, const ProbDesc* d, SlotTable sl, int count, int levels,
                                const float2* tw, int* n_active, cudaStream_t s) {
     constexpr int FT = W / 8, G = kThreads / FT;
-    const size_t smem_row = (size_t)(G * pad8(W) + W) * sizeof(float2) + 8 * kNumPartials * sizeof(double);
+    const size_t smem_row = (size_t)(G * W + W) * sizeof(float2) + 8 * kNumPartials * sizeof(double);
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(haar_row_inverse<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_row);

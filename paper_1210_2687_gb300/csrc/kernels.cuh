@@ -249,15 +249,22 @@ struct ColCfg {
     static_assert(G >= 1 && (kThreads % FT) == 0, "H");
     static_assert(CB % G == 0 && (CB & (CB - 1)) == 0, "column block");
     static constexpr int CPG = CB / G;               // columns per group
-    static constexpr int SIG = pad8(H);              // float2 per exchange buffer
+    static constexpr int SIG = H;                     // float2 per exchange buffer
     static constexpr size_t SMEM = (size_t)H * CB * sizeof(float4) + (size_t)(G * 2 * SIG + H) * sizeof(float2);
 };
 
 // Grid: (Wp / CB, problems). Wp (the stored half-spectrum width) is a
 // multiple of CB; columns >= Wc = W/2 + 1 are padding, transformed but never
 // read by the row phase. The H x CB tile is staged in shared memory by
-// cp.async with row r's CB entries rotated by r, so that the column-wise
-// reads of the transforms hit distinct banks.
+// cp.async with row r's CB entries rotated (tile_slot), so that the
+// column-wise float4 reads of the transforms hit distinct banks.
+template <int CB>
+__device__ __forceinline__ int tile_slot(int r, int c) {
+    // eight consecutive rows must fill the eight 16-byte slots of a 128-byte
+    // window: rows that share a window position get distinct rotations
+    constexpr int SH = CB >= 8 ? 0 : (CB == 4 ? 1 : (CB == 2 ? 2 : 3));
+    return r * CB + ((c + (r >> SH)) & (CB - 1));
+}
 template <int H, int CB>
 __global__ void __launch_bounds__(kThreads)
 col_phase(const ProbDesc* __restrict__ probs, SlotTable sl, int Wc, int Wp, const float2* __restrict__ tw_g) {
@@ -282,7 +289,7 @@ col_phase(const ProbDesc* __restrict__ probs, SlotTable sl, int Wc, int Wp, cons
     const float4* __restrict__ src = P.Sb;
     for (int e = tid; e < H * CB; e += kThreads) {
         const int r = e / CB, c = e % CB;
-        cp_async16(stage + r * CB + ((c + r) & (CB - 1)), src + (size_t)r * Wp + c0 + c);
+        cp_async16(stage + tile_slot<CB>(r, c), src + (size_t)r * Wp + c0 + c);
     }
     cp_async_commit();
     for (int i = tid; i < H; i += kThreads) tw[i] = tw_g[i * (2048 / H)];
@@ -311,7 +318,7 @@ col_phase(const ProbDesc* __restrict__ probs, SlotTable sl, int Wc, int Wp, cons
 #pragma unroll
         for (int m = 0; m < 8; ++m) {
             const int r = t + m * C::FT;
-            const float4 f = stage[r * CB + ((c + r) & (CB - 1))];
+            const float4 f = stage[tile_slot<CB>(r, c)];
             v[m] = make_float2(f.x, f.y);
             u[m] = make_float2(f.z, f.w);
         }
@@ -329,14 +336,14 @@ col_phase(const ProbDesc* __restrict__ probs, SlotTable sl, int Wc, int Wp, cons
 #pragma unroll
         for (int m = 0; m < 8; ++m) {
             const int r = t + m * C::FT;
-            stage[r * CB + ((c + r) & (CB - 1))] = make_float4(v[m].x, v[m].y, u[m].x, u[m].y);
+            stage[tile_slot<CB>(r, c)] = make_float4(v[m].x, v[m].y, u[m].x, u[m].y);
         }
     }
     __syncthreads();
     float4* __restrict__ dst = P.Sa;
     for (int e = tid; e < H * CB; e += kThreads) {
         const int r = e / CB, c = e % CB;
-        dst[(size_t)r * Wp + c0 + c] = stage[r * CB + ((c + r) & (CB - 1))];
+        dst[(size_t)r * Wp + c0 + c] = stage[tile_slot<CB>(r, c)];
     }
 }
 
@@ -370,8 +377,8 @@ __device__ __forceinline__ void store_split(float4* __restrict__ drow, const flo
     for (int m = 0; m <= 4; ++m) {
         const int k = t + m * FT;
         if (k > W / 2) break;
-        const float2 pk = row[pad8(k)];
-        const float2 pn = row[pad8((W - k) & (W - 1))];
+        const float2 pk = row[swz(k)];
+        const float2 pn = row[swz((W - k) & (W - 1))];
         const float2 a = 0.5f * make_float2(pk.x + pn.x, pk.y - pn.y);
         const float2 dd = make_float2(pk.x - pn.x, pk.y + pn.y);
         drow[k] = make_float4(a.x, a.y, 0.5f * dd.y, -0.5f * dd.x);
@@ -522,7 +529,7 @@ struct RowCfg {
     static constexpr int G = NT / FT;                              // row transforms in flight
     static_assert(G >= 1 && NT % FT == 0, "block too small for one row transform");
     static constexpr int NB = R + 2;                               // buffer rows
-    static constexpr int ROW = pad8(W);                            // float2 per buffer row
+    static constexpr int ROW = W + 2;                              // float2 per buffer row (raw spectrum fits)
     static constexpr int RAW = W / 2 + 1;                          // float4 per half-spectrum row
     static constexpr int NWARP = NT / 32;
     static constexpr int CW = W / NWARP;                           // columns per warp
@@ -606,14 +613,14 @@ row_phase_tv(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp, co
         load_row_xax<W>(v, reinterpret_cast<const float4*>(row), t);
         fft_group<W, 1>(v, row, tw, t, g);
 #pragma unroll
-        for (int m = 0; m < 8; ++m) row[pad8(t + m * C::FT)] = v[m];
+        for (int m = 0; m < 8; ++m) row[swz(t + m * C::FT)] = v[m];
     }
     __syncthreads();
     // x of the neighbouring warps' boundary columns, one row per lane
     float xnb_right = 0.f, xnb_left = 0.f;
     if (lane < R + 2) {
-        xnb_right = buf[lane * C::ROW + pad8((wid * C::CW + C::CW) & (W - 1))].x;
-        xnb_left = buf[lane * C::ROW + pad8(chalo)].x;
+        xnb_right = buf[lane * C::ROW + swz((wid * C::CW + C::CW) & (W - 1))].x;
+        xnb_left = buf[lane * C::ROW + swz(chalo)].x;
     }
     __syncthreads();             // nobody overwrites a row before every warp captured
 
@@ -639,11 +646,11 @@ row_phase_tv(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp, co
 #pragma unroll
             for (int j = 0; j < C::CPT; ++j) {
                 const int c = cbase + 32 * j;
-                const float2 z = buf[i * C::ROW + pad8(c)];
+                const float2 z = buf[i * C::ROW + swz(c)];
                 const float x = z.x, ax = z.y;
                 const bool last_col = (lane == C::CW - 1 || lane == 31) && j == C::CPT - 1;
-                const float xr = last_col ? xr_nb : buf[i * C::ROW + pad8(c + 1)].x;
-                const float xd = buf[(i + 1) * C::ROW + pad8(c)].x;
+                const float xr = last_col ? xr_nb : buf[i * C::ROW + swz(c + 1)].x;
+                const float xd = buf[(i + 1) * C::ROW + swz(c)].x;
                 // D_i x (forward periodic differences)
                 const float gh = xr - x, gv = xd - x;
                 const size_t pix = (size_t)q * W + c;
@@ -689,7 +696,7 @@ row_phase_tv(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp, co
             if (lane == 0 && owned) {
                 // delta_h of the pixel left of the chunk (its owner updates its d2)
                 const float xh = xl_nb;
-                const float xhr = buf[i * C::ROW + pad8(wid * C::CW)].x;
+                const float xhr = buf[i * C::ROW + swz(wid * C::CW)].x;
                 const float2 dd = first ? make_float2(0.f, 0.f)
                                         : *reinterpret_cast<const float2*>(slot + 5 * W + 2 * wid);
                 const float sh = (xhr - xh) - dd.x, sv = (xl_nb_dn - xh) - dd.y;
@@ -714,7 +721,7 @@ row_phase_tv(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp, co
             for (int j = 0; j < C::CPT; ++j) {
                 const int c = cbase + 32 * j;
                 const float w = gam * ((dhl[j] - dhcur[j]) + (dvprev[j] - dvcur[j]));
-                buf[i * C::ROW + pad8(c)] = make_float2(z1cur[j], w);
+                buf[i * C::ROW + swz(c)] = make_float2(z1cur[j], w);
             }
         }
 #pragma unroll
@@ -735,10 +742,10 @@ row_phase_tv(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp, co
         float2* row = buf + i * C::ROW;
         float2 v[8];
 #pragma unroll
-        for (int m = 0; m < 8; ++m) v[m] = row[pad8(t + m * C::FT)];
+        for (int m = 0; m < 8; ++m) v[m] = row[swz(t + m * C::FT)];
         fft_group<W, -1>(v, row, tw, t, g);
 #pragma unroll
-        for (int m = 0; m < 8; ++m) row[pad8(t + m * C::FT)] = v[m];
+        for (int m = 0; m < 8; ++m) row[swz(t + m * C::FT)] = v[m];
         group_sync<W>(g);            // the split reads this group's row only
         store_split<W>(P.Sb + (size_t)(r0 - 1 + i) * Wp, row, t);
     }
@@ -756,7 +763,7 @@ template <int W>
 __global__ void __launch_bounds__(kThreads)
 finalize_x(const ProbDesc* __restrict__ probs, float* const* __restrict__ xout, int H, int Wp,
            const float2* __restrict__ tw_g) {
-    constexpr int FT = W / 8, G = kThreads / FT, ROW = pad8(W);
+    constexpr int FT = W / 8, G = kThreads / FT, ROW = W;
     extern __shared__ __align__(16) float2 smem[];
     float2* buf = smem;
     float2* tw = buf + G * ROW;
