@@ -35,7 +35,7 @@ TOL = 1e-5
 MAX_ITERS = 5000
 CHECK_EVERY = 10
 COMBOS = [("gauss", 40), ("motion", 40), ("gauss", 60), ("motion", 60)]
-ROW_KERNEL = "row_phase_tv<512,8,2,128>"
+ROW_KERNEL = "row_phase_tv<512,8,1,128>"
 COL_KERNEL = "col_phase<512,4>"
 STEADY_ITERS = 40
 

@@ -243,7 +243,7 @@ cudaError_t launch_row_tv(int W, const ProbDesc* d, SlotTable sl, int count, int
         case 64: return launch_row_tv_t<64, 16, 4, 256>(d, sl, count, H, Wp, tw, n_active, s);
         case 128: return launch_row_tv_t<128, 16, 4, 256>(d, sl, count, H, Wp, tw, n_active, s);
         case 256: return launch_row_tv_t<256, 8, 4, 256>(d, sl, count, H, Wp, tw, n_active, s);
-        case 512: return launch_row_tv_t<512, 8, 2, 128>(d, sl, count, H, Wp, tw, n_active, s);
+        case 512: return launch_row_tv_t<512, 8, 1, 128>(d, sl, count, H, Wp, tw, n_active, s);
         case 1024: return launch_row_tv_t<1024, 4, 2, 256>(d, sl, count, H, Wp, tw, n_active, s);
         case 2048: return launch_row_tv_t<2048, 4, 1, 256>(d, sl, count, H, Wp, tw, n_active, s);
     }
