@@ -315,11 +315,15 @@ def run_ours(args):
                   "iters_per_s": its / (e0.elapsed_time(e1) * 1e-3)}
         for f in fixed:
             f.close()
+    # DRAM bytes per launch from the committed ncu capture (bytes per pixel
+    # there) scaled to the pixels an average launch of this pass processed
     traffic = None
     tpath = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tpath):
+    launches_dom = prof.row_launches if dom == ROW_KERNEL else prof.col_launches
+    if os.path.exists(tpath) and launches_dom > 0:
         try:
-            traffic = json.load(open(tpath)).get(dom)
+            bpp = json.load(open(tpath))[dom]["bytes_per_px"]
+            traffic = bpp * n * img_iters / launches_dom
         except Exception:
             traffic = None
 
