@@ -60,6 +60,21 @@ def dist_env():
     return rank, world, local
 
 
+def reduce_over_ranks(seconds, work, device=None):
+    """Whole-job figures of a replicated run: the slowest rank's time and the
+    work summed over ranks (one process per GPU, no data-path collective;
+    this is bookkeeping after the timed region)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(seconds), float(work)
+    t = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+    w = torch.tensor([float(work)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(w, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(w.item())
+
+
 def make_batch(batch, rank):
     probs = []
     for i in range(batch):
@@ -265,13 +280,8 @@ def run_ours(args):
         step()
     torch.cuda.synchronize()
     prof = ad.admm_deconv_profile(False)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms_total, float(total_iters)], device=dev, dtype=torch.float64)
-        tmax = t.clone()
-        dist.all_reduce(tmax[:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
-        ms_total, total_iters = float(tmax[0]), float(t[1])
+    my_iters = total_iters
+    ms_total, total_iters = reduce_over_ranks(ms_total, total_iters, dev)
     sec = ms_total / 1000.0
     value = total_iters / sec
     images_per_s = args.batch * world * args.steps / sec
@@ -285,7 +295,7 @@ def run_ours(args):
 
     # ---- roofline of the dominant kernel ----
     row_b, col_b = bytes_per_pixel_iter()
-    img_iters = sum(r.iters for r in res) * args.steps / world if world > 1 else total_iters
+    img_iters = my_iters          # this rank's kernels ran this rank's image-iterations
     # the profiled pass ran the same steps: the same image-iterations per kernel
     row_gbs = img_iters * n * row_b / (prof.row_ms * 1e-3) / 1e9 if prof.row_ms > 0 else 0.0
     col_gbs = img_iters * n * col_b / (prof.col_ms * 1e-3) / 1e9 if prof.col_ms > 0 else 0.0
@@ -341,13 +351,7 @@ def run_ours(args):
         e2e_iters += sum(r.iters for r in r2)
     torch.cuda.synchronize()
     e2e_sec = time.perf_counter() - t0
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([e2e_sec, float(e2e_iters)], device=dev, dtype=torch.float64)
-        tm = t.clone()
-        dist.all_reduce(tm[:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
-        e2e_sec, e2e_iters = float(tm[0]), float(t[1])
+    e2e_sec, e2e_iters = reduce_over_ranks(e2e_sec, e2e_iters, dev)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
