@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--batch", type=int, default=64, help="problems per step per GPU")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-secondary", action="store_true", help="skip the frame-prior workload")
     ap.add_argument("--steady-only", action="store_true",
                     help="only the fixed-iteration pass with every slot busy (for profiler captures)")
     return ap.parse_args()
@@ -160,6 +161,45 @@ class ClockSampler:
             return None
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+FRAME_ITERS = 500
+
+
+def frame_secondary(ad, torch, stream):
+    """Frame-prior (FA-MD) workload: 4-level undecimated Haar, 13 x 13
+    uniform blur, valid region, BSNR 50 dB, 1024^2 and 2048^2, a fixed 500
+    iterations (throughput); kernel time per phase from a profiled pass.
+    Algorithmic bytes per pixel and iteration: column phase 22.1, row side
+    28 (inverse rows) + 112 (Haar tile, d2 13 bands in and out) + 16
+    (forward rows) + 0.8 (x_prev at check_every 10)."""
+    out = {}
+    for size in (1024, 2048):
+        p = S.config3_problem(0, size)
+        n = size * size
+        plan = ad.Plan(size, size, p.psf, p.lam, p.mu1, p.mu2, "haar", stop="iters", max_iters=FRAME_ITERS)
+        y = torch.from_numpy(p.ybar.astype(np.float32)).to("cuda")
+        m = torch.from_numpy(p.mask).to("cuda")
+        x = torch.empty((size, size), dtype=torch.float32, device="cuda")
+        ad.solve(plan, y, m, x, stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ad.solve(plan, y, m, x, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        sec = e0.elapsed_time(e1) * 1e-3
+        ad.admm_deconv_profile(True)
+        ad.solve(plan, y, m, x, stream)
+        pf = ad.admm_deconv_profile(False)
+        row_b = 28.0 + 112.0 + 16.0 + 0.8
+        col_b = 44.0 * (size // 2 + 1) / size
+        out[f"fa_md_{size}"] = {
+            "iters_per_s": FRAME_ITERS / sec,
+            "row_side_gbs": FRAME_ITERS * n * row_b / (pf.row_ms * 1e-3) / 1e9,
+            "col_phase_gbs": FRAME_ITERS * n * col_b / (pf.col_ms * 1e-3) / 1e9,
+            "bytes_per_px_iter": {"row_side": row_b, "col_phase": col_b}}
+        plan.close()
+    return out
 
 
 def cpu_baseline_oracle(probs, seconds=12.0):
@@ -353,6 +393,8 @@ def run_ours(args):
     e2e_sec = time.perf_counter() - t0
     e2e_sec, e2e_iters = reduce_over_ranks(e2e_sec, e2e_iters, dev)
 
+    secondary = frame_secondary(ad, torch, stream) if (rank == 0 and not args.no_secondary) else None
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, nit, dt = cpu_baseline_oracle(probs, seconds=12.0)
@@ -387,6 +429,7 @@ def run_ours(args):
                     "h2d_bytes_per_step": args.batch * (4 * n + n),
                     "d2h_bytes_per_step": args.batch * 4 * n},
             "gpu_launches": int(launches),
+            "secondary": secondary,
             "clocks": clk.summary(),
         }
         print(json.dumps(line), flush=True)
