@@ -117,8 +117,9 @@ struct HaarTileCfg {
         return o;
     }
     static constexpr int ZTOT = zoff(L);
-    // the FP64 reduction scratch follows the float arrays: round up to 8 bytes
-    static constexpr int RED_OFF = (2 * XD * XD + ZTOT + 1) & ~1;   // in floats
+    static constexpr int LLD = T + HALO;          // side of the low-low band region
+    // the reduction scratch follows the float arrays: round up to 8 bytes
+    static constexpr int RED_OFF = (2 * XD * XD + ZTOT + LLD * LLD + 1) & ~1;   // in floats
     static_assert((RED_OFF * sizeof(float)) % sizeof(double) == 0, "double alignment");
     static constexpr size_t SMEM = (size_t)RED_OFF * sizeof(float) + 8 * kNumPartials * sizeof(double);
 };
@@ -144,7 +145,8 @@ haar_tile(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W, int n_
     extern __shared__ __align__(16) float sm[];
     float* A0 = sm;
     float* A1 = A0 + XD * XD;
-    float* Z = A1 + XD * XD;
+    float* Z = A1 + XD * XD;                     // detail bands: d2 staged, then zeta2
+    float* ZLL = Z + C::ZTOT;                    // low-low band: d2 staged
     double* red = reinterpret_cast<double*>(sm + C::RED_OFF);
     const int tid = threadIdx.x;
     const int tiles_x = W / T;
@@ -156,12 +158,34 @@ haar_tile(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W, int n_
     float* __restrict__ d2out = P.d2 + (k & 1) * P.d2_stride;
     const float tau = P.tau;
 
-    // x on [-HALO, T + HALO)^2 around the tile (periodic wrap)
+    // every input of the tile is requested at once (cp.async): x on
+    // [-HALO, T + HALO)^2 and the previous d2 of each band on the region where
+    // its zeta2 is needed (periodic wrap)
     for (int e = tid; e < XD * XD; e += kThreads) {
         const int r = e / XD - HALO, c = e % XD - HALO;
         const int gr = (R0 + r) & (H - 1), gc = (C0 + c) & (W - 1);
-        A0[e] = xw[(size_t)gr * W + gc];
+        cp_async4(A0 + e, xw + (size_t)gr * W + gc);
     }
+    if (!first) {
+#pragma unroll 1
+        for (int lvl = 0; lvl < L; ++lvl) {
+            const int BO = 2 * (1 << lvl) - 1, BD = T + 2 * (1 << lvl) - 1;
+            float* Zl = Z + C::zoff(lvl);
+            for (int e = tid; e < 3 * BD * BD; e += kThreads) {
+                const int j = e / (BD * BD), e2 = e % (BD * BD);
+                const int r = e2 / BD - BO, c = e2 % BD - BO;
+                const size_t gpix = (size_t)((R0 + r) & (H - 1)) * W + ((C0 + c) & (W - 1));
+                cp_async4(Zl + e, d2in + (size_t)(3 * lvl + j) * n + gpix);
+            }
+        }
+        for (int e = tid; e < C::LLD * C::LLD; e += kThreads) {
+            const int r = e / C::LLD - HALO, c = e % C::LLD - HALO;
+            const size_t gpix = (size_t)((R0 + r) & (H - 1)) * W + ((C0 + c) & (W - 1));
+            cp_async4(ZLL + e, d2in + (size_t)(3 * L) * n + gpix);
+        }
+    }
+    cp_async_commit();
+    cp_async_wait<0>();
     __syncthreads();
 
     CompSum l1;
@@ -189,7 +213,7 @@ haar_tile(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W, int n_
 #pragma unroll
                 for (int j = 0; j < 3; ++j) {
                     const size_t bi = (size_t)(3 * lvl + j) * n + gpix;
-                    const float sv = first ? cb[j] : cb[j] - d2in[bi];
+                    const float sv = first ? cb[j] : cb[j] - Zl[j * BD * BD + iz];
                     const float u = soft_thresh(sv, tau);
                     const float nd = u - sv;                   // d2 - (c - u2)
                     Zl[j * BD * BD + iz] = u + nd;              // zeta2 = u2 + d2
@@ -212,7 +236,7 @@ haar_tile(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W, int n_
             const float cb = Ain[i];
             const size_t gpix = (size_t)((R0 + r) & (H - 1)) * W + ((C0 + c) & (W - 1));
             const size_t bi = (size_t)(3 * L) * n + gpix;
-            const float sv = first ? cb : cb - d2in[bi];
+            const float sv = first ? cb : cb - ZLL[(r + HALO) * C::LLD + (c + HALO)];
             const float u = soft_thresh(sv, tau);
             const float nd = u - sv;
             Ain[i] = u + nd;
