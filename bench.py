@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--batch", type=int, default=64, help="problems per step per GPU")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-secondary", action="store_true", help="skip the frame-prior workload")
+    ap.add_argument("--frame-only", action="store_true", help="only the frame-prior workload (profiler captures)")
     ap.add_argument("--steady-only", action="store_true",
                     help="only the fixed-iteration pass with every slot busy (for profiler captures)")
     return ap.parse_args()
@@ -260,6 +261,9 @@ def run_ours(args):
     import paper_1210_2687_gb300 as ad
 
     dev = torch.device("cuda", local)
+    if args.frame_only:
+        print(json.dumps({"secondary": frame_secondary(ad, torch, torch.cuda.current_stream())}), flush=True)
+        return
     probs = make_batch(args.batch, rank)
     n = H * W
     plans = [ad.Plan(H, W, p.psf, p.lam, p.mu1, p.mu2, "tv", stop="rel_x", tol=TOL,

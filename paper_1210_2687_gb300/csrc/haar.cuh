@@ -167,7 +167,7 @@ haar_tile(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W, int n_
         cp_async4(A0 + e, xw + (size_t)gr * W + gc);
     }
     if (!first) {
-#pragma unroll 1
+#pragma unroll
         for (int lvl = 0; lvl < L; ++lvl) {
             const int BO = 2 * (1 << lvl) - 1, BD = T + 2 * (1 << lvl) - 1;
             float* Zl = Z + C::zoff(lvl);
@@ -192,7 +192,8 @@ haar_tile(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W, int n_
     float* Ain = A0;
     float* Aout = A1;
     // analysis, level by level: a_{j+1} and the three detail bands from a_j
-#pragma unroll 1
+    // (levels unrolled: every region size below is a compile-time constant)
+#pragma unroll
     for (int lvl = 0; lvl < L; ++lvl) {
         const int s = 1 << lvl;
         const int D = T + 2 * HALO + 1 - 2 * s;       // a_{j+1} is needed on [-HALO, D - HALO)
@@ -250,7 +251,7 @@ haar_tile(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W, int n_
     // synthesis (adjoint), coarse to fine: a~_j from a~_{j+1} and the zeta bands of level j
     float* At = Ain;
     float* Ao = Aout;
-#pragma unroll 1
+#pragma unroll
     for (int lvl = L - 1; lvl >= 0; --lvl) {
         const int s = 1 << lvl;
         const int D = T + s - 1;                       // output on [-(s-1), T)
