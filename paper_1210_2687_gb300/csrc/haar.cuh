@@ -283,7 +283,7 @@ haar_tile(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W, int n_
     const CompSum acc[kNumPartials] = {CompSum(), l1, CompSum(), CompSum()};
     double pv[kNumPartials];
     block_reduce_comp(acc, reinterpret_cast<float*>(red), pv);
-    if (tid == 0) finish_iteration(P, k, chk, nobj, pv, n_active, n_row_ctas + blockIdx.x, probs, sl);
+    finish_iteration<kThreads>(P, k, chk, nobj, pv, n_active, n_row_ctas + blockIdx.x, probs, sl);
 }
 
 // ---------------------------------------------------------------------------

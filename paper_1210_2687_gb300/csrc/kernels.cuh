@@ -446,25 +446,49 @@ __device__ __forceinline__ void block_reduce_comp(const CompSum (&a)[kNumPartial
     }
 }
 
-// Called by thread 0 of every row-phase CTA after its partial sums are in
-// v: publishes them; the last CTA of the problem to arrive reduces all
-// strips in strip order, evaluates the stop rule of iteration k and
-// advances the problem's control block.
+// Called by every thread of a CTA that finishes an iteration, with the
+// CTA's partial sums in v (valid in thread 0): thread 0 publishes them; the
+// last CTA of the problem to arrive reduces all slots (every thread takes a
+// fixed strided share, then a fixed tree, so the order is reproducible),
+// evaluates the stop rule of iteration k and advances the control block.
+template <int NT>
 __device__ void finish_iteration(const ProbDesc& P, int k, bool chk, bool nobj,
                                  const double (&v)[kNumPartials], int* n_active, int slot,
                                  const ProbDesc* __restrict__ probs, SlotTable sl) {
+    __shared__ int s_last;
+    __shared__ double s_red[NT / 32][kNumPartials];
     ProbCtl* ctl = P.ctl;
+    const int tid = threadIdx.x;
+    if (tid == 0) {
 #pragma unroll
-    for (int j = 0; j < kNumPartials; ++j) P.partials[slot * kNumPartials + j] = v[j];
-    __threadfence();
-    const unsigned prev = atomicAdd(&ctl->arrive, 1u);
-    if (prev != (unsigned)(P.n_strips - 1)) return;
+        for (int j = 0; j < kNumPartials; ++j) P.partials[slot * kNumPartials + j] = v[j];
+        __threadfence();
+        const unsigned prev = atomicAdd(&ctl->arrive, 1u);
+        s_last = prev == (unsigned)(P.n_strips - 1);
+    }
+    __syncthreads();
+    if (!s_last) return;
     __threadfence();
     const int nslots = P.n_slots > 0 ? P.n_slots : P.n_strips;
     double acc[kNumPartials] = {0.0, 0.0, 0.0, 0.0};
-    for (int s = 0; s < nslots; ++s) {
+    for (int s = tid; s < nslots; s += NT) {
 #pragma unroll
         for (int j = 0; j < kNumPartials; ++j) acc[j] += __ldcg(P.partials + s * kNumPartials + j);
+    }
+#pragma unroll
+    for (int j = 0; j < kNumPartials; ++j) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc[j] += __shfl_down_sync(0xffffffffu, acc[j], o);
+    }
+    if ((tid & 31) == 0) {
+#pragma unroll
+        for (int j = 0; j < kNumPartials; ++j) s_red[tid >> 5][j] = acc[j];
+    }
+    __syncthreads();
+    if (tid != 0) return;
+    for (int w = 1; w < NT / 32; ++w) {
+#pragma unroll
+        for (int j = 0; j < kNumPartials; ++j) acc[j] += s_red[w][j];
     }
     bool done = false, conv = false;
     if (nobj) {
@@ -752,7 +776,7 @@ row_phase_tv(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp, co
 
     // (5) the last CTA of the problem evaluates the stop rule; done last so
     // that the memory fence it needs does not hold up the transforms
-    if (tid == 0) finish_iteration(P, k, chk, nobj, part, n_active, blockIdx.x, probs, sl);
+    finish_iteration<NT>(P, k, chk, nobj, part, n_active, blockIdx.x, probs, sl);
 }
 
 // ---------------------------------------------------------------------------
