@@ -158,30 +158,40 @@ haar_tile(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W, int n_
     float* __restrict__ d2out = P.d2 + (k & 1) * P.d2_stride;
     const float tau = P.tau;
 
+    // Regions are visited two-dimensionally: warp w takes rows w, w + 8, ...
+    // and lane l columns l, l + 32, ... of the region, so positions come from
+    // counters rather than divisions, and the wrapped global row is computed
+    // once per row.
+    const int lane = tid & 31, warp = tid >> 5;
+    constexpr int NWARP = kThreads / 32;
+
     // every input of the tile is requested at once (cp.async): x on
     // [-HALO, T + HALO)^2 and the previous d2 of each band on the region where
     // its zeta2 is needed (periodic wrap)
-    for (int e = tid; e < XD * XD; e += kThreads) {
-        const int r = e / XD - HALO, c = e % XD - HALO;
-        const int gr = (R0 + r) & (H - 1), gc = (C0 + c) & (W - 1);
-        cp_async4(A0 + e, xw + (size_t)gr * W + gc);
+    for (int rr = warp; rr < XD; rr += NWARP) {
+        const float* src = xw + (size_t)((R0 + rr - HALO) & (H - 1)) * W;
+        for (int cc = lane; cc < XD; cc += 32) cp_async4(A0 + rr * XD + cc, src + ((C0 + cc - HALO) & (W - 1)));
     }
     if (!first) {
 #pragma unroll
         for (int lvl = 0; lvl < L; ++lvl) {
             const int BO = 2 * (1 << lvl) - 1, BD = T + 2 * (1 << lvl) - 1;
             float* Zl = Z + C::zoff(lvl);
-            for (int e = tid; e < 3 * BD * BD; e += kThreads) {
-                const int j = e / (BD * BD), e2 = e % (BD * BD);
-                const int r = e2 / BD - BO, c = e2 % BD - BO;
-                const size_t gpix = (size_t)((R0 + r) & (H - 1)) * W + ((C0 + c) & (W - 1));
-                cp_async4(Zl + e, d2in + (size_t)(3 * lvl + j) * n + gpix);
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                const float* band = d2in + (size_t)(3 * lvl + j) * n;
+                for (int rr = warp; rr < BD; rr += NWARP) {
+                    const float* src = band + (size_t)((R0 + rr - BO) & (H - 1)) * W;
+                    for (int cc = lane; cc < BD; cc += 32)
+                        cp_async4(Zl + j * BD * BD + rr * BD + cc, src + ((C0 + cc - BO) & (W - 1)));
+                }
             }
         }
-        for (int e = tid; e < C::LLD * C::LLD; e += kThreads) {
-            const int r = e / C::LLD - HALO, c = e % C::LLD - HALO;
-            const size_t gpix = (size_t)((R0 + r) & (H - 1)) * W + ((C0 + c) & (W - 1));
-            cp_async4(ZLL + e, d2in + (size_t)(3 * L) * n + gpix);
+        const float* band = d2in + (size_t)(3 * L) * n;
+        for (int rr = warp; rr < C::LLD; rr += NWARP) {
+            const float* src = band + (size_t)((R0 + rr - HALO) & (H - 1)) * W;
+            for (int cc = lane; cc < C::LLD; cc += 32)
+                cp_async4(ZLL + rr * C::LLD + cc, src + ((C0 + cc - HALO) & (W - 1)));
         }
     }
     cp_async_commit();
@@ -199,28 +209,32 @@ haar_tile(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W, int n_
         const int D = T + 2 * HALO + 1 - 2 * s;       // a_{j+1} is needed on [-HALO, D - HALO)
         const int BO = 2 * s - 1, BD = T + 2 * s - 1;  // band region [-BO, T)
         float* Zl = Z + C::zoff(lvl);
-        for (int e = tid; e < D * D; e += kThreads) {
-            const int r = e / D - HALO, c = e % D - HALO;
-            const int i00 = (r + HALO) * XD + (c + HALO);
-            const float a00 = Ain[i00], a01 = Ain[i00 + s];
-            const float a10 = Ain[i00 + s * XD], a11 = Ain[i00 + s * XD + s];
-            const float p0 = a00 + a01, m0 = a00 - a01, p1 = a10 + a11, m1 = a10 - a11;
-            Aout[i00] = 0.25f * (p0 + p1);
-            if (r >= -BO && c >= -BO && r < T && c < T) {
-                const float cb[3] = {0.25f * (m0 + m1), 0.25f * (p0 - p1), 0.25f * (m0 - m1)};
-                const size_t gpix = (size_t)((R0 + r) & (H - 1)) * W + ((C0 + c) & (W - 1));
-                const bool own = r >= 0 && c >= 0;
-                const int iz = (r + BO) * BD + (c + BO);
+        for (int rr = warp; rr < D; rr += NWARP) {
+            const int r = rr - HALO;
+            const bool band_row = r >= -BO && r < T;
+            const size_t grow = (size_t)((R0 + r) & (H - 1)) * W;
+            for (int cc = lane; cc < D; cc += 32) {
+                const int c = cc - HALO;
+                const int i00 = rr * XD + cc;
+                const float a00 = Ain[i00], a01 = Ain[i00 + s];
+                const float a10 = Ain[i00 + s * XD], a11 = Ain[i00 + s * XD + s];
+                const float p0 = a00 + a01, m0 = a00 - a01, p1 = a10 + a11, m1 = a10 - a11;
+                Aout[i00] = 0.25f * (p0 + p1);
+                if (band_row && c >= -BO && c < T) {
+                    const float cb[3] = {0.25f * (m0 + m1), 0.25f * (p0 - p1), 0.25f * (m0 - m1)};
+                    const size_t gpix = grow + ((C0 + c) & (W - 1));
+                    const bool own = r >= 0 && c >= 0;
+                    const int iz = (r + BO) * BD + (c + BO);
 #pragma unroll
-                for (int j = 0; j < 3; ++j) {
-                    const size_t bi = (size_t)(3 * lvl + j) * n + gpix;
-                    const float sv = first ? cb[j] : cb[j] - Zl[j * BD * BD + iz];
-                    const float u = soft_thresh(sv, tau);
-                    const float nd = u - sv;                   // d2 - (c - u2)
-                    Zl[j * BD * BD + iz] = u + nd;              // zeta2 = u2 + d2
-                    if (own) {
-                        d2out[bi] = nd;
-                        if (nobj) l1.add(fabsf(cb[j]));
+                    for (int j = 0; j < 3; ++j) {
+                        const float sv = first ? cb[j] : cb[j] - Zl[j * BD * BD + iz];
+                        const float u = soft_thresh(sv, tau);
+                        const float nd = u - sv;                   // d2 - (c - u2)
+                        Zl[j * BD * BD + iz] = u + nd;              // zeta2 = u2 + d2
+                        if (own) {
+                            d2out[(size_t)(3 * lvl + j) * n + gpix] = nd;
+                            if (nobj) l1.add(fabsf(cb[j]));
+                        }
                     }
                 }
             }
@@ -230,20 +244,22 @@ haar_tile(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W, int n_
     }
     // last low-low band (a_L on [-HALO, T)), thresholded in place
     {
-        const int D = T + HALO;
-        for (int e = tid; e < D * D; e += kThreads) {
-            const int r = e / D - HALO, c = e % D - HALO;
-            const int i = (r + HALO) * XD + (c + HALO);
-            const float cb = Ain[i];
-            const size_t gpix = (size_t)((R0 + r) & (H - 1)) * W + ((C0 + c) & (W - 1));
-            const size_t bi = (size_t)(3 * L) * n + gpix;
-            const float sv = first ? cb : cb - ZLL[(r + HALO) * C::LLD + (c + HALO)];
-            const float u = soft_thresh(sv, tau);
-            const float nd = u - sv;
-            Ain[i] = u + nd;
-            if (r >= 0 && c >= 0) {
-                d2out[bi] = nd;
-                if (nobj) l1.add(fabsf(cb));
+        constexpr int D = T + HALO;
+        for (int rr = warp; rr < D; rr += NWARP) {
+            const int r = rr - HALO;
+            const size_t grow = (size_t)((R0 + r) & (H - 1)) * W;
+            for (int cc = lane; cc < D; cc += 32) {
+                const int c = cc - HALO;
+                const int i = rr * XD + cc;
+                const float cb = Ain[i];
+                const float sv = first ? cb : cb - ZLL[rr * C::LLD + cc];
+                const float u = soft_thresh(sv, tau);
+                const float nd = u - sv;
+                Ain[i] = u + nd;
+                if (r >= 0 && c >= 0) {
+                    d2out[(size_t)(3 * L) * n + grow + ((C0 + c) & (W - 1))] = nd;
+                    if (nobj) l1.add(fabsf(cb));
+                }
             }
         }
         __syncthreads();
@@ -259,27 +275,28 @@ haar_tile(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W, int n_
         const float* Z0 = Z + C::zoff(lvl);
         const float* Z1 = Z0 + BD * BD;
         const float* Z2 = Z1 + BD * BD;
-        for (int e = tid; e < D * D; e += kThreads) {
-            const int r = e / D - (s - 1), c = e % D - (s - 1);
-            const int ia = (r + HALO) * XD + (c + HALO);
-            const int iz = (r + BO) * BD + (c + BO);
-            const int ra = s * XD, rz = s * BD;
-            // rows adjoint at columns c and c - s
-            const float lo_c = (At[ia] + At[ia - ra]) + (Z1[iz] - Z1[iz - rz]);
-            const float lo_l = (At[ia - s] + At[ia - ra - s]) + (Z1[iz - s] - Z1[iz - rz - s]);
-            const float hi_c = (Z0[iz] + Z0[iz - rz]) + (Z2[iz] - Z2[iz - rz]);
-            const float hi_l = (Z0[iz - s] + Z0[iz - rz - s]) + (Z2[iz - s] - Z2[iz - rz - s]);
-            Ao[ia] = 0.25f * ((lo_c + lo_l) + (hi_c - hi_l));
+        const int ra = s * XD, rz = s * BD;
+        for (int rr = warp; rr < D; rr += NWARP) {
+            const int r = rr - (s - 1);
+            for (int cc = lane; cc < D; cc += 32) {
+                const int c = cc - (s - 1);
+                const int ia = (r + HALO) * XD + (c + HALO);
+                const int iz = (r + BO) * BD + (c + BO);
+                // rows adjoint at columns c and c - s
+                const float lo_c = (At[ia] + At[ia - ra]) + (Z1[iz] - Z1[iz - rz]);
+                const float lo_l = (At[ia - s] + At[ia - ra - s]) + (Z1[iz - s] - Z1[iz - rz - s]);
+                const float hi_c = (Z0[iz] + Z0[iz - rz]) + (Z2[iz] - Z2[iz - rz]);
+                const float hi_l = (Z0[iz - s] + Z0[iz - rz - s]) + (Z2[iz - s] - Z2[iz - rz - s]);
+                Ao[ia] = 0.25f * ((lo_c + lo_l) + (hi_c - hi_l));
+            }
         }
         __syncthreads();
         float* tmp = At; At = Ao; Ao = tmp;
     }
     // w = gamma P^T zeta2 on the tile
     const float gam = P.gamma;
-    for (int e = tid; e < T * T; e += kThreads) {
-        const int r = e / T, c = e % T;
-        ww[(size_t)(R0 + r) * W + (C0 + c)] = gam * At[(r + HALO) * XD + (c + HALO)];
-    }
+    for (int r = warp; r < T; r += NWARP)
+        ww[(size_t)(R0 + r) * W + (C0 + lane)] = gam * At[(r + HALO) * XD + (lane + HALO)];
     const CompSum acc[kNumPartials] = {CompSum(), l1, CompSum(), CompSum()};
     double pv[kNumPartials];
     block_reduce_comp(acc, reinterpret_cast<float*>(red), pv);
