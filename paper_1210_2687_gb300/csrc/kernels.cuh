@@ -133,6 +133,12 @@ template <int N> __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
+// Bulk prefetch of a contiguous global range into L2 (no shared memory and no
+// completion to wait for); `bytes` a multiple of 16, `p` 16-byte aligned.
+__device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(p), "r"(bytes) : "memory");
+}
+
 // observed pixels carry M^T y, unobserved ones a quiet NaN (eq. prox_g_1_uBC)
 __device__ __forceinline__ bool is_observed(float yb) { return yb == yb; }
 
@@ -616,7 +622,21 @@ row_phase_tv(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp, co
         cp_async_commit();   // possibly empty: keeps one group per walk row
     };
 
-    // (0) requests: half spectra of rows r0-1 .. r0+R, then the first D walk rows
+    // (0) requests: the walk's rows go to L2 in bulk (they are consumed after
+    // the inverse transforms), the half spectra of rows r0-1 .. r0+R into
+    // shared memory, then the first D walk rows into the ring
+    if (tid == 0) {
+        const int qh = (r0 - 1 + H) & (H - 1);
+        if (!first) {
+            prefetch_l2(d2in + (size_t)qh * W, W * sizeof(float2));
+            for (int i = 0; i < R; ++i) {
+                prefetch_l2(d2in + (size_t)(r0 + i) * W, W * sizeof(float2));
+                prefetch_l2(P.d1 + (size_t)(r0 + i) * W, W * sizeof(float));
+                if (chk) prefetch_l2(P.xprev + (size_t)(r0 + i) * W, W * sizeof(float));
+            }
+        }
+        for (int i = 0; i < R; ++i) prefetch_l2(P.ybar + (size_t)(r0 + i) * W, W * sizeof(float));
+    }
     for (int e = tid; e < (R + 2) * C::RAW; e += NT) {
         const int i = e / C::RAW, kk = e % C::RAW;
         const int q = (r0 - 1 + i + H) & (H - 1);
