@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-secondary", action="store_true", help="skip the frame-prior workload")
     ap.add_argument("--frame-only", action="store_true", help="only the frame-prior workload (profiler captures)")
+    ap.add_argument("--uneven-only", action="store_true", help="only the batched uneven workload")
     ap.add_argument("--steady-only", action="store_true",
                     help="only the fixed-iteration pass with every slot busy (for profiler captures)")
     return ap.parse_args()
@@ -203,6 +204,69 @@ def frame_secondary(ad, torch, stream):
     return out
 
 
+UNEVEN_COUNT = 256
+
+
+def uneven_secondary(ad, torch, stream, count=UNEVEN_COUNT):
+    """Batched uneven workload: ``count`` problems (seed 0) with sides drawn
+    from {128, 256, 384 (solved on 512, padding unobserved), 512, 1024},
+    box / Gaussian / motion kernels of side 5..25, missing fraction
+    U[0, 0.5], TV or 4-level Haar, BSNR 40 dB, all in one solve_batch call to
+    rel-x < 1e-5 (checked every iteration). Time to tolerance per problem
+    comes from its device-clock start and retirement stamps."""
+    import oracle as O  # ISNR of the results, outside the timed region
+    t_gen = time.perf_counter()
+    probs = S.config4_batch(0, count)
+    t_gen = time.perf_counter() - t_gen
+    plans, ys, ms, xs = [], [], [], []
+    for p in probs:
+        N = p.ybar.shape[0]
+        plans.append(ad.Plan(N, N, p.psf, p.lam, p.mu1, p.mu2, p.reg, stop="rel_x", tol=TOL,
+                             max_iters=MAX_ITERS, check_every=1))
+        ys.append(torch.from_numpy(p.ybar.astype(np.float32)).to("cuda"))
+        ms.append(torch.from_numpy(p.mask).to("cuda"))
+        xs.append(torch.empty((N, N), dtype=torch.float32, device="cuda"))
+    ad.solve_batch(plans, ys, ms, xs, stream)          # warm-up: graphs, attributes
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    res = ad.solve_batch(plans, ys, ms, xs, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    sec = e0.elapsed_time(e1) * 1e-3
+    done = np.array([r.t_done_ms for r in res])
+    solve = np.array([r.t_done_ms - r.t_start_ms for r in res])
+    iters = np.array([r.iters for r in res])
+    px_iters = sum(int(r.iters) * p.ybar.size for r, p in zip(res, probs))
+    isnr = []
+    for p, x in zip(probs, xs):
+        n = p.meta["window"]
+        N = p.ybar.shape[0]
+        vm = np.zeros((N, N), dtype=np.uint8)
+        vm[:n, :n] = S.valid_mask(n, n, *p.psf.shape)
+        isnr.append(O.isnr(p.x_true, p.ybar, x.cpu().numpy().astype(np.float64), vm))
+    for pl in plans:
+        pl.close()
+    return {
+        "workload": f"{count} problems, sides {{128,256,384->512,512,1024}}, box/gauss/motion 5..25, "
+                    "missing U[0,0.5], TV or Haar, BSNR 40, rel-x < 1e-5",
+        "images_per_s": count / sec,
+        "iters_per_s": float(iters.sum()) / sec,
+        "mpix_iters_per_s": px_iters / sec / 1e6,
+        "wall_s": sec,
+        "converged": int(sum(r.converged for r in res)),
+        "iters_mean": float(iters.mean()),
+        "iters_p50": float(np.percentile(iters, 50)),
+        "iters_max": int(iters.max()),
+        "latency_ms_p50": float(np.percentile(done, 50)),
+        "latency_ms_p99": float(np.percentile(done, 99)),
+        "time_to_tol_ms_p50": float(np.percentile(solve, 50)),
+        "time_to_tol_ms_p99": float(np.percentile(solve, 99)),
+        "isnr_db_mean": float(np.mean(isnr)),
+        "input_generation_s": t_gen,
+    }
+
+
 def cpu_baseline_oracle(probs, seconds=12.0):
     """The FP64 oracle as it stands on one 512^2 problem of the workload,
     iterating until about `seconds` of CPU time; iterations per second."""
@@ -263,6 +327,9 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     if args.frame_only:
         print(json.dumps({"secondary": frame_secondary(ad, torch, torch.cuda.current_stream())}), flush=True)
+        return
+    if args.uneven_only:
+        print(json.dumps({"uneven_batch": uneven_secondary(ad, torch, torch.cuda.current_stream())}), flush=True)
         return
     probs = make_batch(args.batch, rank)
     n = H * W
@@ -397,7 +464,10 @@ def run_ours(args):
     e2e_sec = time.perf_counter() - t0
     e2e_sec, e2e_iters = reduce_over_ranks(e2e_sec, e2e_iters, dev)
 
-    secondary = frame_secondary(ad, torch, stream) if (rank == 0 and not args.no_secondary) else None
+    secondary = None
+    if rank == 0 and not args.no_secondary:
+        secondary = frame_secondary(ad, torch, stream)
+        secondary["uneven_batch"] = uneven_secondary(ad, torch, stream)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

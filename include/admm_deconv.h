@@ -100,6 +100,9 @@ typedef struct {
                               final iterate (FP32 data, compensated reduction)              */
     double rel_x;          /* last evaluated ||x_k - x_{k-1}|| / ||x_k||, or -1 if never    */
     double rel_obj;        /* last evaluated |f_k - f_{k-1}| / |f_k|, or -1 if never        */
+    double t_start_ms;     /* device clock: from the call's set-up until the problem started
+                              iterating (later than 0 when it waited for a free slot)       */
+    double t_done_ms;      /* device clock: from the call's set-up until it retired        */
 } admm_result_t;
 
 /*

@@ -16,6 +16,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <string>
 #include <mutex>
 #include <new>
 #include <tuple>
@@ -63,20 +64,21 @@ struct DeviceCtx {
     ProbDesc* desc = nullptr;        // descriptor table
     float** xptr = nullptr;          // finalize destinations
     int cap = 0;
-    int* n_active = nullptr;
+    int* n_active = nullptr;         // unretired problems per size class (cap entries)
     int* queue = nullptr;            // next problem of the pool to start
     int* slot_map = nullptr;         // problem index per launch slot (cap entries)
-    int* h_active = nullptr;         // pinned, 2 slots
+    int* h_active = nullptr;         // pinned, 2 x cap (double-buffered copy of n_active)
     ProbCtl* h_ctl = nullptr;        // pinned copy-back area
     ProbDesc* h_desc = nullptr;      // pinned staging for the table
     float** h_xptr = nullptr;
     cudaEvent_t ev[2] = {nullptr, nullptr};
-    cudaStream_t cap_stream = nullptr;   // private streams for graph capture
-    cudaStream_t cap_stream2 = nullptr;
-    cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
-    // chunk graphs: (H, W, reg, levels, slots, chunk, problems, lanes) ->
-    // executable graph; cleared whenever the descriptor or slot tables move
-    std::map<std::tuple<int, int, int, int, int, int, int, int>, cudaGraphExec_t> graphs;
+    static constexpr int kBranches = 8;             // capture streams (graph branches)
+    cudaStream_t branch[kBranches] = {};
+    cudaEvent_t fork_ev = nullptr;
+    cudaEvent_t join_ev[kBranches] = {};
+    // chunk graphs keyed by the batch's layout (size classes, offsets, slots,
+    // lanes); cleared whenever the descriptor or slot tables move
+    std::map<std::string, cudaGraphExec_t> graphs;
 };
 
 // A group's problems split into `n` lanes that iterate independently: lane
@@ -133,15 +135,14 @@ int ensure_ctx(int dev, int count, DeviceCtx** out) {
         }
         CK(cudaMalloc(&c.tw, 2048 * sizeof(float2)));
         CK(cudaMemcpy(c.tw, tw.data(), 2048 * sizeof(float2), cudaMemcpyHostToDevice));
-        CK(cudaMalloc(&c.n_active, sizeof(int)));
-        CK(cudaMalloc(&c.queue, 2 * sizeof(int)));
-        CK(cudaHostAlloc(&c.h_active, 2 * sizeof(int), cudaHostAllocDefault));
+
         CK(cudaEventCreateWithFlags(&c.ev[0], cudaEventDisableTiming));
         CK(cudaEventCreateWithFlags(&c.ev[1], cudaEventDisableTiming));
-        CK(cudaStreamCreateWithFlags(&c.cap_stream, cudaStreamNonBlocking));
-        CK(cudaStreamCreateWithFlags(&c.cap_stream2, cudaStreamNonBlocking));
+        for (int b = 0; b < DeviceCtx::kBranches; ++b) {
+            CK(cudaStreamCreateWithFlags(&c.branch[b], cudaStreamNonBlocking));
+            CK(cudaEventCreateWithFlags(&c.join_ev[b], cudaEventDisableTiming));
+        }
         CK(cudaEventCreateWithFlags(&c.fork_ev, cudaEventDisableTiming));
-        CK(cudaEventCreateWithFlags(&c.join_ev, cudaEventDisableTiming));
         c.ready = true;
     }
     if (count > c.cap) {
@@ -151,15 +152,24 @@ int ensure_ctx(int dev, int count, DeviceCtx** out) {
         if (c.desc) cudaFree(c.desc);
         if (c.xptr) cudaFree(c.xptr);
         if (c.slot_map) cudaFree(c.slot_map);
+        if (c.queue) cudaFree(c.queue);
+        if (c.n_active) cudaFree(c.n_active);
+        if (c.h_active) cudaFreeHost(c.h_active);
         if (c.h_ctl) cudaFreeHost(c.h_ctl);
         if (c.h_desc) cudaFreeHost(c.h_desc);
         if (c.h_xptr) cudaFreeHost(c.h_xptr);
         c.desc = nullptr; c.xptr = nullptr; c.h_ctl = nullptr; c.h_desc = nullptr; c.h_xptr = nullptr;
         c.slot_map = nullptr;
+        c.queue = nullptr;
+        c.n_active = nullptr;
+        c.h_active = nullptr;
         c.cap = 0;
         CK(cudaMalloc(&c.desc, cap * sizeof(ProbDesc)));
         CK(cudaMalloc(&c.slot_map, cap * sizeof(int)));
+        CK(cudaMalloc(&c.queue, 2 * cap * sizeof(int)));   // two lanes per size class at most
         CK(cudaMalloc(&c.xptr, cap * sizeof(float*)));
+        CK(cudaMalloc(&c.n_active, cap * sizeof(int)));
+        CK(cudaHostAlloc(&c.h_active, 2 * cap * sizeof(int), cudaHostAllocDefault));
         CK(cudaHostAlloc(&c.h_ctl, cap * sizeof(ProbCtl), cudaHostAllocDefault));
         CK(cudaHostAlloc(&c.h_desc, cap * sizeof(ProbDesc), cudaHostAllocDefault));
         CK(cudaHostAlloc(&c.h_xptr, cap * sizeof(float*), cudaHostAllocDefault));
@@ -484,187 +494,272 @@ int admm_deconv_get_state(admm_plan_t plan, float* d_out, void* stream) {
     return ADMM_OK;
 }
 
+// One size class of a batch: problems [off, off + count) of the descriptor
+// table, split into L.n lanes (absolute table offsets and slot ranges; lane l
+// uses queue word qbase + l).
+struct GroupRun {
+    int H = 0, W = 0, Wc = 0, Wp = 0, levels = 0;
+    bool tv = true;
+    int off = 0, count = 0, nslots = 0, max_iters = 0, qbase = 0;
+    int gi = 0;                  // index of the class's n_active counter
+    long long launch_cap = 0;    // iterations after which every problem has retired
+    long long launched = 0;
+    Lanes L;
+};
+
+static SlotTable lane_slots(DeviceCtx* ctx, const GroupRun& g, int l) {
+    return SlotTable{ctx->slot_map + g.L.soff[l], ctx->queue + g.qbase + l, g.L.cnt[l]};
+}
+
 // one ADMM iteration of one lane: the column phase, then the row side
-static cudaError_t launch_iteration(DeviceCtx* ctx, const ProbDesc* desc, int H, int W, int Wc, int Wp, bool tv,
-                                    int levels, SlotTable sl, int nslots, cudaStream_t s) {
-    cudaError_t e = launch_col(H, desc, sl, nslots, Wc, Wp, ctx->tw, s);
+static cudaError_t launch_iteration(DeviceCtx* ctx, const GroupRun& g, int l, cudaStream_t s) {
+    const ProbDesc* desc = ctx->desc + g.L.off[l];
+    const SlotTable sl = lane_slots(ctx, g, l);
+    cudaError_t e = launch_col(g.H, desc, sl, g.L.slots[l], g.Wc, g.Wp, ctx->tw, s);
     if (e != cudaSuccess) return e;
-    if (tv) return launch_row_tv(W, desc, sl, nslots, H, Wp, ctx->tw, ctx->n_active, s);
-    return launch_haar_iteration_rows(W, H, Wp, desc, sl, nslots, levels, ctx->tw, ctx->n_active, s);
+    int* nact = ctx->n_active + g.gi;
+    if (g.tv) return launch_row_tv(g.W, desc, sl, g.L.slots[l], g.H, g.Wp, ctx->tw, nact, s);
+    return launch_haar_iteration_rows(g.W, g.H, g.Wp, desc, sl, g.L.slots[l], g.levels, ctx->tw, nact, s);
 }
 
-static SlotTable lane_slots(DeviceCtx* ctx, const Lanes& L, int l) {
-    return SlotTable{ctx->slot_map + L.soff[l], ctx->queue + l, L.cnt[l]};
+static std::string graph_key(const std::vector<GroupRun>& groups, int chunk) {
+    std::string k = std::to_string(chunk);
+    for (const GroupRun& g : groups) {
+        k += "|" + std::to_string(g.H) + "," + std::to_string(g.W) + "," + std::to_string(g.tv) + "," +
+             std::to_string(g.levels) + "," + std::to_string(g.off) + "," + std::to_string(g.count) + "," +
+             std::to_string(g.qbase) + "," + std::to_string(g.L.n);
+        for (int l = 0; l < g.L.n; ++l)
+            k += ";" + std::to_string(g.L.off[l]) + "," + std::to_string(g.L.cnt[l]) + "," +
+                 std::to_string(g.L.soff[l]) + "," + std::to_string(g.L.slots[l]);
+    }
+    return k;
 }
 
-// executable graph of `chunk` iterations of every lane, the lanes as
-// independent branches (captured on the private streams)
-static cudaError_t chunk_graph(DeviceCtx* ctx, int H, int W, int Wc, int Wp, bool tv, int levels, const Lanes& L,
-                               int nslots, int count, int chunk, cudaGraphExec_t* out) {
-    const auto key = std::make_tuple(H, W, tv ? 0 : 1, levels, nslots, chunk, count, L.n);
+// executable graph of `chunk` iterations of every lane of every size class,
+// each lane an independent branch (captured on the private streams; lanes
+// beyond the stream pool share a branch)
+static cudaError_t chunk_graph(DeviceCtx* ctx, const std::vector<GroupRun>& groups, int chunk,
+                               cudaGraphExec_t* out) {
+    const std::string key = graph_key(groups, chunk);
     auto it = ctx->graphs.find(key);
     if (it != ctx->graphs.end()) {
         *out = it->second;
         return cudaSuccess;
     }
-    cudaError_t e = cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (ctx->graphs.size() >= 64) {     // bound the cache: drop every layout seen so far
+        for (auto& kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
+        ctx->graphs.clear();
+    }
+    int nb = 0;
+    for (const GroupRun& g : groups) nb += g.L.n;
+    nb = std::min(nb, (int)DeviceCtx::kBranches);
+    cudaStream_t origin = ctx->branch[0];
+    cudaError_t e = cudaStreamBeginCapture(origin, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return e;
     cudaError_t le = cudaSuccess;
-    if (L.n > 1) {
-        le = cudaEventRecord(ctx->fork_ev, ctx->cap_stream);
-        if (le == cudaSuccess) le = cudaStreamWaitEvent(ctx->cap_stream2, ctx->fork_ev, 0);
+    if (nb > 1) {
+        le = cudaEventRecord(ctx->fork_ev, origin);
+        for (int b = 1; b < nb && le == cudaSuccess; ++b) le = cudaStreamWaitEvent(ctx->branch[b], ctx->fork_ev, 0);
     }
-    for (int l = 0; l < L.n && le == cudaSuccess; ++l) {
-        cudaStream_t cs = l == 0 ? ctx->cap_stream : ctx->cap_stream2;
-        for (int i = 0; i < chunk && le == cudaSuccess; ++i)
-            le = launch_iteration(ctx, ctx->desc + L.off[l], H, W, Wc, Wp, tv, levels, lane_slots(ctx, L, l),
-                                  L.slots[l], cs);
+    int br = 0;
+    for (const GroupRun& g : groups) {
+        for (int l = 0; l < g.L.n && le == cudaSuccess; ++l, ++br) {
+            cudaStream_t cs = ctx->branch[br % nb];
+            for (int i = 0; i < chunk && le == cudaSuccess; ++i) le = launch_iteration(ctx, g, l, cs);
+        }
     }
-    if (L.n > 1 && le == cudaSuccess) {
-        le = cudaEventRecord(ctx->join_ev, ctx->cap_stream2);
-        if (le == cudaSuccess) le = cudaStreamWaitEvent(ctx->cap_stream, ctx->join_ev, 0);
+    if (nb > 1 && le == cudaSuccess) {
+        for (int b = 1; b < nb && le == cudaSuccess; ++b) {
+            le = cudaEventRecord(ctx->join_ev[b], ctx->branch[b]);
+            if (le == cudaSuccess) le = cudaStreamWaitEvent(origin, ctx->join_ev[b], 0);
+        }
     }
-    cudaGraph_t g = nullptr;
-    e = cudaStreamEndCapture(ctx->cap_stream, &g);
+    cudaGraph_t gr = nullptr;
+    e = cudaStreamEndCapture(origin, &gr);
     if (le != cudaSuccess) {
-        if (g) cudaGraphDestroy(g);
+        if (gr) cudaGraphDestroy(gr);
         return le;
     }
     if (e != cudaSuccess) return e;
     cudaGraphExec_t exec = nullptr;
-    e = cudaGraphInstantiate(&exec, g, 0);
-    cudaGraphDestroy(g);
+    e = cudaGraphInstantiate(&exec, gr, 0);
+    cudaGraphDestroy(gr);
     if (e != cudaSuccess) return e;
     ctx->graphs[key] = exec;
     *out = exec;
     return cudaSuccess;
 }
 
-static int solve_group(DeviceCtx* ctx, const std::vector<int>& idx, const admm_plan_t* plans,
-                       const float* const* y, const uint8_t* const* masks, float* const* x_out,
-                       admm_result_t* res, cudaStream_t s) {
-    const int count = (int)idx.size();
-    const admm_plan_s* p0 = plans[idx[0]];
-    const int H = p0->p.H, W = p0->p.W, Wc = p0->Wc, Wp = p0->Wp;
-    const bool tv = p0->p.reg == ADMM_REG_TV;
-    const size_t n = (size_t)H * W;
-    int max_iters = 0;
-    std::vector<char> x_host(count, 0);
-    for (int j = 0; j < count; ++j) {
-        admm_plan_s* pl = plans[idx[j]];
-        const float* yj = y[idx[j]];
-        const uint8_t* mj = masks ? masks[idx[j]] : nullptr;
-        if (!is_device_ptr(yj)) {
-            CK(cudaMemcpyAsync(pl->ystage, yj, n * sizeof(float), cudaMemcpyHostToDevice, s));
-            yj = pl->ystage;
+// Solve every problem of a batch: all size classes iterate in the same loop
+// (their lanes are independent branches of one replayed graph).
+static int solve_all(DeviceCtx* ctx, const std::vector<std::vector<int>>& classes, const admm_plan_t* plans,
+                     const float* const* y, const uint8_t* const* masks, float* const* x_out,
+                     admm_result_t* res, cudaStream_t s) {
+    const bool prof = g_prof.on;
+    std::vector<GroupRun> groups;
+    std::vector<int> order;                       // table position -> index into plans
+    std::vector<char> x_host;
+    int soff = 0, qbase = 0;
+    for (const std::vector<int>& idx : classes) {
+        GroupRun g;
+        const admm_plan_s* p0 = plans[idx[0]];
+        g.H = p0->p.H;
+        g.W = p0->p.W;
+        g.Wc = p0->Wc;
+        g.Wp = p0->Wp;
+        g.levels = p0->levels;
+        g.tv = p0->p.reg == ADMM_REG_TV;
+        g.off = (int)order.size();
+        g.count = (int)idx.size();
+        g.qbase = qbase;
+        g.gi = (int)groups.size();
+        const size_t n = (size_t)g.H * g.W;
+        for (int j : idx) {
+            admm_plan_s* pl = plans[j];
+            const float* yj = y[j];
+            const uint8_t* mj = masks ? masks[j] : nullptr;
+            if (!is_device_ptr(yj)) {
+                CK(cudaMemcpyAsync(pl->ystage, yj, n * sizeof(float), cudaMemcpyHostToDevice, s));
+                yj = pl->ystage;
+            }
+            if (mj && !is_device_ptr(mj)) {
+                CK(cudaMemcpyAsync(pl->mstage, mj, n, cudaMemcpyHostToDevice, s));
+                mj = pl->mstage;
+            }
+            CK(cudaMemsetAsync(pl->ctl, 0, sizeof(ProbCtl), s));
+            prepare_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(pl->ybar, pl->mask, yj, mj, g.H, g.W,
+                                                                       pl->p.psf_h / 2, pl->p.psf_w / 2,
+                                                                       pl->p.raw_mask, pl->ctl);
+            CK(cudaGetLastError());
+            ++g_launches;
+            const int t = (int)order.size();
+            ctx->h_desc[t] = make_desc(pl);
+            x_host.push_back(!is_device_ptr(x_out[j]));
+            ctx->h_xptr[t] = x_host.back() ? pl->xstage : x_out[j];
+            order.push_back(j);
+            g.max_iters = std::max(g.max_iters, pl->p.max_iters);
         }
-        if (mj && !is_device_ptr(mj)) {
-            CK(cudaMemcpyAsync(pl->mstage, mj, n, cudaMemcpyHostToDevice, s));
-            mj = pl->mstage;
+        g.nslots = choose_slots(g.H, g.W, g.tv, g.count);
+        // with per-phase timing on, one lane: every launch covers all slots,
+        // so the timed phases are the full-size kernels
+        g.L.n = (!prof && g.count >= 2 && g.nslots >= 2) ? 2 : 1;
+        for (int l = 0, o = g.off, so = soff; l < g.L.n; ++l) {
+            g.L.off[l] = o;
+            g.L.cnt[l] = l + 1 < g.L.n ? g.count / 2 : g.off + g.count - o;
+            g.L.soff[l] = so;
+            g.L.slots[l] = l + 1 < g.L.n ? g.nslots / 2 : soff + g.nslots - so;
+            o += g.L.cnt[l];
+            so += g.L.slots[l];
         }
-        const int lr = pl->p.psf_h / 2, lc = pl->p.psf_w / 2;
-        CK(cudaMemsetAsync(pl->ctl, 0, sizeof(ProbCtl), s));
-        prepare_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(pl->ybar, pl->mask, yj, mj, H, W, lr, lc,
-                                                                   pl->p.raw_mask, pl->ctl);
+        soff += g.nslots;
+        qbase += g.L.n;
+        groups.push_back(g);
+    }
+    const int total = (int)order.size();
+    const int ng = (int)groups.size();
+    CK(cudaMemcpyAsync(ctx->desc, ctx->h_desc, total * sizeof(ProbDesc), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ctx->xptr, ctx->h_xptr, total * sizeof(float*), cudaMemcpyHostToDevice, s));
+    for (int gi = 0; gi < ng; ++gi) ctx->h_active[gi] = groups[gi].count;
+    CK(cudaMemcpyAsync(ctx->n_active, ctx->h_active, ng * sizeof(int), cudaMemcpyHostToDevice, s));
+    for (const GroupRun& g : groups) {
+        init_ctl_kernel<<<(g.count + 127) / 128, 128, 0, s>>>(ctx->desc + g.off, g.count, ctx->n_active + g.gi);
         CK(cudaGetLastError());
         ++g_launches;
-        ctx->h_desc[j] = make_desc(pl);
-        x_host[j] = !is_device_ptr(x_out[idx[j]]);
-        ctx->h_xptr[j] = x_host[j] ? pl->xstage : x_out[idx[j]];
-        max_iters = std::max(max_iters, pl->p.max_iters);
+        for (int l = 0; l < g.L.n; ++l) {
+            assign_slots_kernel<<<1, 32, 0, s>>>(ctx->desc + g.L.off[l], lane_slots(ctx, g, l), g.L.slots[l]);
+            CK(cudaGetLastError());
+            ++g_launches;
+        }
     }
-    CK(cudaMemcpyAsync(ctx->desc, ctx->h_desc, count * sizeof(ProbDesc), cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(ctx->xptr, ctx->h_xptr, count * sizeof(float*), cudaMemcpyHostToDevice, s));
-    ctx->h_active[0] = count;
-    CK(cudaMemcpyAsync(ctx->n_active, ctx->h_active, sizeof(int), cudaMemcpyHostToDevice, s));
-    init_ctl_kernel<<<(count + 127) / 128, 128, 0, s>>>(ctx->desc, count, ctx->n_active);
-    CK(cudaGetLastError());
-    const int nslots = choose_slots(H, W, tv, count);
-    const bool prof = g_prof.on;
-    Lanes L;
-    // with per-phase timing on, one lane: every launch covers all slots, so
-    // the timed phases are the full-size kernels
-    L.n = (!prof && count >= 2 && nslots >= 2) ? 2 : 1;
-    for (int l = 0, off = 0, soff = 0; l < L.n; ++l) {
-        L.off[l] = off;
-        L.cnt[l] = l + 1 < L.n ? count / 2 : count - off;
-        L.soff[l] = soff;
-        L.slots[l] = l + 1 < L.n ? nslots / 2 : nslots - soff;
-        off += L.cnt[l];
-        soff += L.slots[l];
-    }
-    for (int l = 0; l < L.n; ++l) {
-        assign_slots_kernel<<<1, 32, 0, s>>>(ctx->desc + L.off[l], lane_slots(ctx, L, l), L.slots[l]);
-        CK(cudaGetLastError());
-    }
-    g_launches += 1 + L.n;
-    // the host buffers of the descriptor table are reused by the next group
+    // the host-side tables are reused by the next call
     CK(cudaStreamSynchronize(s));
 
     // with more problems than slots, problems start as slots free up: the
-    // launches needed are bounded by the sum of the per-slot work
-    long long launch_cap = 0;
-    for (int q = 0; q < count; ++q) launch_cap += plans[idx[q]]->p.max_iters;
-    const int min_slots = std::max(1, std::min(L.slots[0], L.slots[L.n - 1]));
-    launch_cap = (launch_cap + min_slots - 1) / min_slots + max_iters;
-    if (launch_cap > (long long)INT32_MAX) launch_cap = INT32_MAX;
-    max_iters = (int)launch_cap;
+    // iterations needed by a class are bounded by the sum of its per-slot work
+    for (GroupRun& g : groups) {
+        long long work = 0;
+        for (int t = g.off; t < g.off + g.count; ++t) work += plans[order[t]]->p.max_iters;
+        const int min_slots = std::max(1, std::min(g.L.slots[0], g.L.slots[g.L.n - 1]));
+        g.launch_cap = std::min((work + min_slots - 1) / min_slots + g.max_iters, (long long)INT32_MAX);
+    }
+    // classes still iterating; a class leaves once the host has seen its
+    // counter reach zero (one chunk behind the device) or its cap run out
+    std::vector<GroupRun> live = groups;
     const int chunk = 8;
     size_t nev = 0;
     if (prof) {
         int r = prof_event(nev++, s);
         if (r != ADMM_OK) return r;
     }
-    int launched = 0, j = 0;
-    while (launched < max_iters) {
-        const int nit = std::min(chunk, max_iters - launched);
-        if (!prof && j > 0 && nit == chunk) {
+    for (int j = 0; !live.empty(); ++j) {
+        bool full = true;
+        for (const GroupRun& g : live) full = full && g.launch_cap - g.launched >= chunk;
+        if (!prof && j > 0 && full) {
             // steady state: one graph replay per chunk (the first chunk ran
             // as plain launches, which also set the kernels' attributes)
             cudaGraphExec_t exec = nullptr;
-            CK(chunk_graph(ctx, H, W, Wc, Wp, tv, p0->levels, L, nslots, count, chunk, &exec));
+            CK(chunk_graph(ctx, live, chunk, &exec));
             CK(cudaGraphLaunch(exec, s));
-            g_launches += (long long)chunk * L.n * (tv ? 2 : 4);
-        } else
-        for (int it = 0; it < nit; ++it) {
-            for (int l = 0; l < L.n; ++l) {
-                const ProbDesc* dl = ctx->desc + L.off[l];
-                const SlotTable sl = lane_slots(ctx, L, l);
-                CK(launch_col(H, dl, sl, L.slots[l], Wc, Wp, ctx->tw, s));
-                ++g_launches;
-                if (prof) {
-                    int r = prof_event(nev++, s);
-                    if (r != ADMM_OK) return r;
-                }
-                if (tv) {
-                    CK(launch_row_tv(W, dl, sl, L.slots[l], H, Wp, ctx->tw, ctx->n_active, s));
-                    ++g_launches;
-                } else {
-                    CK(launch_haar_iteration_rows(W, H, Wp, dl, sl, L.slots[l], p0->levels, ctx->tw, ctx->n_active,
-                                                  s));
-                    g_launches += 3;
-                }
-                if (prof) {
-                    int r = prof_event(nev++, s);
-                    if (r != ADMM_OK) return r;
+            for (GroupRun& g : live) {
+                g_launches += (long long)chunk * g.L.n * (g.tv ? 2 : 4);
+                g.launched += chunk;
+            }
+        } else {
+            for (int it = 0; it < chunk; ++it) {
+                for (GroupRun& g : live) {
+                    if (g.launched >= g.launch_cap) continue;
+                    for (int l = 0; l < g.L.n; ++l) {
+                        const ProbDesc* dl = ctx->desc + g.L.off[l];
+                        const SlotTable sl = lane_slots(ctx, g, l);
+                        int* nact = ctx->n_active + g.gi;
+                        CK(launch_col(g.H, dl, sl, g.L.slots[l], g.Wc, g.Wp, ctx->tw, s));
+                        ++g_launches;
+                        if (prof) {
+                            int r = prof_event(nev++, s);
+                            if (r != ADMM_OK) return r;
+                        }
+                        if (g.tv) {
+                            CK(launch_row_tv(g.W, dl, sl, g.L.slots[l], g.H, g.Wp, ctx->tw, nact, s));
+                            ++g_launches;
+                        } else {
+                            CK(launch_haar_iteration_rows(g.W, g.H, g.Wp, dl, sl, g.L.slots[l], g.levels, ctx->tw,
+                                                          nact, s));
+                            g_launches += 3;
+                        }
+                        if (prof) {
+                            int r = prof_event(nev++, s);
+                            if (r != ADMM_OK) return r;
+                        }
+                    }
+                    ++g.launched;
                 }
             }
         }
-        launched += nit;
-        CK(cudaMemcpyAsync(&ctx->h_active[j & 1], ctx->n_active, sizeof(int), cudaMemcpyDeviceToHost, s));
+        int* hbuf = ctx->h_active + (size_t)(j & 1) * ctx->cap;
+        CK(cudaMemcpyAsync(hbuf, ctx->n_active, ng * sizeof(int), cudaMemcpyDeviceToHost, s));
         CK(cudaEventRecord(ctx->ev[j & 1], s));
+        std::vector<GroupRun> next;
         if (j > 0) {
             CK(cudaEventSynchronize(ctx->ev[(j - 1) & 1]));
-            if (ctx->h_active[(j - 1) & 1] == 0) break;
+            const int* prev = ctx->h_active + (size_t)((j - 1) & 1) * ctx->cap;
+            for (const GroupRun& g : live)
+                if (prev[g.gi] > 0 && g.launched < g.launch_cap) next.push_back(g);
+        } else {
+            for (const GroupRun& g : live)
+                if (g.launched < g.launch_cap) next.push_back(g);
         }
-        ++j;
+        live.swap(next);
     }
-    CK(launch_fin(W, ctx->desc, ctx->xptr, count, H, Wp, ctx->tw, s));
-    ++g_launches;
-    for (int q = 0; q < count; ++q) {
-        admm_plan_s* pl = plans[idx[q]];
-        if (x_host[q]) CK(cudaMemcpyAsync(x_out[idx[q]], pl->xstage, n * sizeof(float), cudaMemcpyDeviceToHost, s));
-        CK(cudaMemcpyAsync(&ctx->h_ctl[q], pl->ctl, sizeof(ProbCtl), cudaMemcpyDeviceToHost, s));
+    for (const GroupRun& g : groups) {
+        CK(launch_fin(g.W, ctx->desc + g.off, ctx->xptr + g.off, g.count, g.H, g.Wp, ctx->tw, s));
+        ++g_launches;
+    }
+    for (int t = 0; t < total; ++t) {
+        admm_plan_s* pl = plans[order[t]];
+        if (x_host[t])
+            CK(cudaMemcpyAsync(x_out[order[t]], pl->xstage, (size_t)pl->p.H * pl->p.W * sizeof(float),
+                               cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(&ctx->h_ctl[t], pl->ctl, sizeof(ProbCtl), cudaMemcpyDeviceToHost, s));
     }
     CK(cudaStreamSynchronize(s));
     if (prof) {
@@ -679,12 +774,12 @@ static int solve_group(DeviceCtx* ctx, const std::vector<int>& idx, const admm_p
         }
     }
     int rc = ADMM_OK;
-    for (int q = 0; q < count; ++q) {
-        const ProbCtl& c = ctx->h_ctl[q];
-        plans[idx[q]]->last_iter = c.iter;
+    for (int t = 0; t < total; ++t) {
+        const ProbCtl& c = ctx->h_ctl[t];
+        plans[order[t]]->last_iter = c.iter;
         if (c.status != 0 && rc == ADMM_OK) rc = c.status;
         if (res) {
-            admm_result_t& r = res[idx[q]];
+            admm_result_t& r = res[order[t]];
             r.iters = c.iter;
             r.converged = c.converged;
             r.status = c.status;
@@ -692,6 +787,8 @@ static int solve_group(DeviceCtx* ctx, const std::vector<int>& idx, const admm_p
             r.objective = c.have_obj ? c.obj : NAN;
             r.rel_x = c.rel_x;
             r.rel_obj = c.rel_obj;
+            r.t_start_ms = c.t_start >= c.t0 ? (double)(c.t_start - c.t0) * 1e-6 : 0.0;
+            r.t_done_ms = c.t_done >= c.t0 ? (double)(c.t_done - c.t0) * 1e-6 : 0.0;
         }
     }
     return rc;
@@ -721,13 +818,9 @@ int admm_deconv_solve_batch(const admm_plan_t* plans, int count, const float* co
         const admm_plan_s* p = plans[i];
         groups[std::make_tuple(p->p.H, p->p.W, p->p.reg, p->levels)].push_back(i);
     }
-    int first_err = ADMM_OK;
-    for (auto& kv : groups) {
-        const int r = solve_group(ctx, kv.second, plans, y, masks, x_out, res, s);
-        if (r == ADMM_ECUDA) return r;
-        if (r != ADMM_OK && first_err == ADMM_OK) first_err = r;
-    }
-    return first_err;
+    std::vector<std::vector<int>> classes;
+    for (auto& kv : groups) classes.push_back(kv.second);
+    return solve_all(ctx, classes, plans, y, masks, x_out, res, s);
 }
 
 int admm_deconv_set_option(int option, long long value) {
@@ -964,6 +1057,8 @@ extern "C" int admm_deconv_solve_noalloc(const admm_params_t* p, const float* y,
         res->objective = c.have_obj ? c.obj : NAN;
         res->rel_x = c.rel_x;
         res->rel_obj = c.rel_obj;
+        res->t_start_ms = c.t_start >= c.t0 ? (double)(c.t_start - c.t0) * 1e-6 : 0.0;
+        res->t_done_ms = c.t_done >= c.t0 ? (double)(c.t_done - c.t0) * 1e-6 : 0.0;
     }
     return c.status != 0 ? c.status : ADMM_OK;
 }

@@ -47,7 +47,16 @@ struct ProbCtl {
     double rel_obj;    // -1 until evaluated
     int input_bad;     // set by prepare_kernel: an observed value is not finite
     int pad_;
+    unsigned long long t0;       // device clock (ns) when the batch was set up
+    unsigned long long t_start;  // ... when the problem took a slot
+    unsigned long long t_done;   // ... when it retired
 };
+
+__device__ __forceinline__ unsigned long long device_clock_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 
 // Per-problem constants and buffers (all device pointers).
 struct ProbDesc {
@@ -229,6 +238,9 @@ __global__ void init_ctl_kernel(ProbDesc* __restrict__ probs, int count, int* __
     c->obj_prev = 0.0;
     c->rel_x = -1.0;
     c->rel_obj = -1.0;
+    c->t0 = device_clock_ns();
+    c->t_start = 0;
+    c->t_done = bad ? c->t0 : 0;
     if (bad) atomicSub(n_active, 1);
 }
 
@@ -236,10 +248,11 @@ __global__ void init_ctl_kernel(ProbDesc* __restrict__ probs, int count, int* __
 __global__ void assign_slots_kernel(const ProbDesc* __restrict__ probs, SlotTable sl, int nslots) {
     if (blockIdx.x != 0 || threadIdx.x != 0) return;
     int next = 0;
+    const unsigned long long now = device_clock_ns();
     for (int s = 0; s < nslots; ++s) {
         while (next < sl.pool && probs[next].ctl->active == 0) ++next;
         sl.map[s] = next < sl.pool ? next : -1;
-        if (next < sl.pool) ++next;
+        if (next < sl.pool) probs[next++].ctl->t_start = now;
     }
     *sl.queue = next;
 }
@@ -524,13 +537,16 @@ __device__ void finish_iteration(const ProbDesc& P, int k, bool chk, bool nobj,
     ctl->iter = k;
     if (conv && !done) ctl->converged = 1;
     if (conv || done || k >= P.max_iters) {
+        const unsigned long long now = device_clock_ns();
         ctl->active = 0;
+        ctl->t_done = now;
         atomicSub(n_active, 1);
         // hand this slot to the next queued problem that is still active
         // (bounded: every pass consumes one queue entry)
         int nx = atomicAdd(sl.queue, 1);
         while (nx < sl.pool && probs[nx].ctl->active == 0) nx = atomicAdd(sl.queue, 1);
         sl.map[blockIdx.y] = nx < sl.pool ? nx : -1;
+        if (nx < sl.pool) probs[nx].ctl->t_start = now;
     }
     ctl->arrive = 0u;
 }

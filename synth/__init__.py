@@ -38,6 +38,10 @@ __all__ = [
     "config1_problem",
     "config2_problem",
     "config3_problem",
+    "conv_valid_fft",
+    "fft_domain",
+    "config4_problem",
+    "config4_batch",
 ]
 
 
@@ -228,15 +232,34 @@ class Problem:
         return self.x_true.shape
 
 
+def conv_valid_fft(x: np.ndarray, psf: np.ndarray) -> np.ndarray:
+    """conv_valid through a zero-padded (linear, not periodic) FFT product:
+    the same valid-region values up to rounding, at O(n log n) for the large
+    kernels of the batched workload."""
+    H, W = x.shape
+    ph, pw = psf.shape
+    lr, lc = ph // 2, pw // 2
+    out = np.zeros((H, W))
+    Hv, Wv = H - 2 * lr, W - 2 * lc
+    if Hv <= 0 or Wv <= 0:
+        return out
+    fh, fw = H + ph - 1, W + pw - 1
+    full = np.fft.irfft2(np.fft.rfft2(x, (fh, fw)) * np.fft.rfft2(psf, (fh, fw)), (fh, fw))
+    # full[i, j] = sum psf[a', b'] x[i - a', j - b']; the valid output at
+    # (r, c) is full[r + lr, c + lc] for r in [lr, H - lr)
+    out[lr:lr + Hv, lc:lc + Wv] = full[2 * lr:2 * lr + Hv, 2 * lc:2 * lc + Wv]
+    return out
+
+
 def observe(x: np.ndarray, psf: np.ndarray, keep: np.ndarray | None,
-            bsnr_db: float, g: np.random.Generator):
+            bsnr_db: float, g: np.random.Generator, fast: bool = False):
     """Blur x (valid region only), drop the pixels outside ``keep`` and add
     white Gaussian noise whose variance gives the requested BSNR
     = 10 log10(var(blurred observed pixels) / sigma^2)."""
     H, W = x.shape
     vm = valid_mask(H, W, *psf.shape)
     mask = vm if keep is None else (vm & keep.astype(np.uint8))
-    blurred = conv_valid(x, psf)
+    blurred = conv_valid_fft(x, psf) if fast else conv_valid(x, psf)
     obs = mask.astype(bool)
     v = blurred[obs].var() if obs.any() else 0.0
     sigma = math.sqrt(v / (10.0 ** (bsnr_db / 10.0))) if v > 0 else 0.0
@@ -299,3 +322,90 @@ def config3_problem(seed: int = 0, size: int = 1024, lam: float = 5e-5) -> Probl
     mu1, mu2 = default_mu(lam)
     return Problem(x, psf, ybar, mask, sigma, lam, mu1, mu2, "haar",
                    {"config": f"haar{size}_box13_bsnr50"})
+
+
+# --------------------------------------------------------------------------
+# batched uneven workload
+# --------------------------------------------------------------------------
+CONFIG4_SIZES = (128, 256, 384, 512, 1024)
+
+# lambda per (regularizer, blur family) at BSNR 40: best oracle ISNR after
+# 300 iterations on one 256 x 256 calibration image (seed 1000) per family
+# (box 13, Gaussian sigma 2.5, motion 15 px at 30 degrees) over
+# {1e-5, 3e-5, 1e-4, 3e-4, 1e-3, 3e-3}; oracle/calibrate_lambda.py
+CONFIG4_LAMBDA = {("tv", "box"): 1e-3, ("tv", "gauss"): 1e-3, ("tv", "motion"): 3e-4,
+                  ("haar", "box"): 1e-4, ("haar", "gauss"): 1e-4, ("haar", "motion"): 1e-4}
+
+
+def fft_domain(n: int) -> int:
+    """Smallest power of two >= n (at least 64): the unknown domain a side of
+    n pixels is solved on. The extra rows and columns are more unknown
+    boundary, never observed (Sec. IV-A: the domain only has to hold the
+    image and the kernel support)."""
+    d = 64
+    while d < n:
+        d *= 2
+    return d
+
+
+def config4_psf(g: np.random.Generator):
+    """One kernel from the batched workload's law: box (odd side 5..21),
+    Gaussian (sigma U[1, 4], side 2 ceil(3 sigma) + 1) or motion (length
+    U{5..25} at angle U[0, 180) degrees, odd side >= length), each with
+    probability 1/3. Returns (psf, family)."""
+    kind = int(g.integers(3))
+    if kind == 0:
+        side = 2 * int(g.integers(2, 11)) + 1
+        return psf_box(side), "box"
+    if kind == 1:
+        sigma = float(g.uniform(1.0, 4.0))
+        return psf_gaussian(2 * math.ceil(3.0 * sigma) + 1, sigma), "gauss"
+    length = int(g.integers(5, 26))
+    angle = float(g.uniform(0.0, 180.0))
+    return psf_motion(float(length), angle, length + 1 - length % 2), "motion"
+
+
+def config4_problem(g: np.random.Generator, size: int | None = None, reg: str | None = None) -> Problem:
+    """One problem of the batched uneven workload: side uniform over
+    CONFIG4_SIZES, kernel from config4_psf, missing fraction U[0, 0.5],
+    TV or 4-level Haar with probability 1/2, BSNR 40 dB, textured image.
+    A side that is not a power of two is solved on the padded domain
+    fft_domain(side): the image sits in the top-left corner and the padding
+    is unobserved; meta["window"] is the image's side, x_true is zero on the
+    padding."""
+    if size is None:
+        size = CONFIG4_SIZES[int(g.integers(len(CONFIG4_SIZES)))]
+    psf, family = config4_psf(g)
+    missing = float(g.uniform(0.0, 0.5))
+    r = ("tv" if g.uniform() < 0.5 else "haar")
+    reg = reg or r
+    x = textured_image(size, size, g)
+    keep = (g.uniform(0.0, 1.0, size=(size, size)) >= missing).astype(np.uint8)
+    ybar, mask, sigma = observe(x, psf, keep, 40.0, g, fast=True)
+    N = fft_domain(size)
+    if N != size:
+        xp = np.zeros((N, N))
+        yp = np.zeros((N, N))
+        mp = np.zeros((N, N), dtype=np.uint8)
+        xp[:size, :size] = x
+        yp[:size, :size] = ybar
+        mp[:size, :size] = mask
+        x, ybar, mask = xp, yp, mp
+    lam = CONFIG4_LAMBDA[(reg, family)]
+    mu1, mu2 = default_mu(lam)
+    return Problem(x, psf, ybar, mask, sigma, lam, mu1, mu2, reg,
+                   {"config": f"{reg}{size}_{family}{psf.shape[0]}_miss{missing:.2f}",
+                    "window": size, "family": family, "missing": missing})
+
+
+def config4_batch(seed: int = 0, count: int = 256, sizes=None) -> list:
+    """``count`` problems of the batched uneven workload from one stream;
+    ``sizes`` (optional) restricts the side law to a subset."""
+    g = rng(seed)
+    out = []
+    for _ in range(count):
+        size = None
+        if sizes is not None:
+            size = sizes[int(g.integers(len(sizes)))]
+        out.append(config4_problem(g, size))
+    return out

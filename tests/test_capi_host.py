@@ -52,7 +52,7 @@ def test_struct_layout_matches_header(ad):
     # admm_params_t: 4 ints, pointer, 3 floats, 3 ints, double, 3 ints
     assert ctypes.sizeof(ad.admm_params_t) == 72
     assert ad.admm_params_t.tol.offset == 48
-    assert ctypes.sizeof(ad.admm_result_t) == 40
+    assert ctypes.sizeof(ad.admm_result_t) == 56
 
 
 @pytest.mark.parametrize("change,code", [
