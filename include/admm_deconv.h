@@ -152,11 +152,32 @@ ADMM_API int admm_deconv_solve_batch(const admm_plan_t* plans, int count, const 
 ADMM_API long long admm_deconv_state_size(admm_plan_t plan);
 
 /*
- * admm_deconv_get_state -- copy the dual variables (d1 then d2, band-major)
- * left by the last solve into `d_out` (device or host, state_size floats).
+ * admm_deconv_get_state -- copy the dual variables left by the last solve
+ * into `d_out` (device or host, state_size floats). Layout: d1 (H x W, row-
+ * major), then d2: TV -- H x W pairs (horizontal, vertical) interleaved per
+ * pixel; Haar -- 3 L + 1 planes of H x W in band order.
  * Errors: ADMM_EINVAL, ADMM_ECUDA.
  */
 ADMM_API int admm_deconv_get_state(admm_plan_t plan, float* d_out, void* stream);
+
+/*
+ * admm_deconv_warm_start -- make the next solve of `plan` (admm_deconv_solve
+ * or one entry of admm_deconv_solve_batch) start from a given point instead
+ * of u0 = d0 = 0. Algorithm 2 converges from any (u0, d0) (Theorem 1); the
+ * start used here is u0 = H x0 - d0, d0 given, with H = (A, D) for TV or
+ * (A, P) for the frame prior, so that the first x-step returns x0 and the
+ * first dual update starts from d0. The paper has no warm start: a learned
+ * predictor (or an earlier solution) supplies x0 and d0.
+ *   x0  H x W float32 starting image, device or host; NULL = zero image
+ *   d0  state_size floats in the layout of admm_deconv_get_state, device or
+ *       host; NULL = zero duals
+ * The plan keeps the start until its next solve, which consumes it (later
+ * solves start cold again). The stop rule compares consecutive iterates, so
+ * it is first evaluated at the second iteration. Stream-ordered on `stream`;
+ * returns after the copies have completed, so x0/d0 may be released then.
+ * Errors: ADMM_EINVAL (NULL plan, plan made on another device), ADMM_ECUDA.
+ */
+ADMM_API int admm_deconv_warm_start(admm_plan_t plan, const float* x0, const float* d0, void* stream);
 
 /* Options (admm_deconv_set_option); not in the paper. */
 #define ADMM_OPT_MAX_SLOTS 1   /* value > 0: at most this many problems of a size class

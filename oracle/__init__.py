@@ -346,7 +346,9 @@ def solve(ybar, mask, psf, lam, mu1, mu2, reg="tv", iters=200, stop="iters", tol
         f_prev = f
         if record:
             hist.append((n, f, rel_x))
-        if stop == "rel_x" and rel_x < tol:
+        # the rule compares consecutive iterates of this run: x_1 has no
+        # predecessor (from a warm start it is the given x0 itself)
+        if stop == "rel_x" and n > 1 and rel_x < tol:
             converged = True
             break
         if stop == "rel_obj" and n > 1 and rel_obj < tol:

@@ -1,60 +1,75 @@
-"""Pick lambda per (blur, BSNR) for the 512 x 512 TV inpainting workload by
-best oracle ISNR after 300 TV-MD iterations on one calibration image (seed
-1000), as the paper tuned lambda per condition for the best ISNR (Sec. V).
-Run as a script; prints the table stored in synth.CONFIG2_LAMBDA (with the
-argument "batched": the table synth.CONFIG4_LAMBDA).
-Test infrastructure: uses the oracle only."""
-import sys
+"""Pick the regularisation weight lambda per condition by the best oracle ISNR
+of the converged solution, as the paper tuned lambda per condition for the
+best ISNR (Sec. V). One calibration image per condition (seed 1000), the
+grid {1e-5, 3e-5, 1e-4, 3e-4, 1e-3, 3e-3}, penalties by synth.default_mu,
+solved to rel-x < 1e-5 (at most 3000 iterations).
+
+Conditions:
+  inpainting TV workload   (blur, BSNR) in {Gaussian 19 sigma 3, motion 15 at 30}
+                           x {40, 60} dB, 40 % of interior pixels missing
+                           -> synth.CONFIG2_LAMBDA
+  batched uneven workload  (regularizer, blur family) in {TV, Haar}
+                           x {box 13, Gaussian 17 sigma 2.5, motion 15 at 30},
+                           25 % missing, 40 dB -> synth.CONFIG4_LAMBDA
+
+Run as a script (prints the tables). Test infrastructure: uses the oracle
+only."""
+import multiprocessing as mp
 import os
+import sys
 
 sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
 
 import oracle as O  # noqa: E402
 import synth as S  # noqa: E402
 
+GRID = [1e-5, 3e-5, 1e-4, 3e-4, 1e-3, 3e-3]
 
-def main(size=256, iters=300):
-    grid = [1e-5, 3e-5, 1e-4, 3e-4, 1e-3, 3e-3]
-    for blur in ("gauss", "motion"):
+
+def _kernel(name):
+    return {"gauss19": lambda: S.psf_gaussian(19, 3.0),
+            "motion15": lambda: S.psf_motion(15.0, 30.0, 15),
+            "box13": lambda: S.psf_box(13),
+            "gauss17": lambda: S.psf_gaussian(17, 2.5)}[name]()
+
+
+def _isnr(job):
+    table, key, kname, bsnr, missing, reg, lam, size = job
+    psf = _kernel(kname)
+    g = S.rng(1000)
+    x = S.textured_image(size, size, g)
+    keep = (g.uniform(0.0, 1.0, size=(size, size)) >= missing).astype("uint8")
+    ybar, mask, _ = S.observe(x, psf, keep, float(bsnr), g, fast=True)
+    mu1, mu2 = S.default_mu(lam)
+    r = O.solve(ybar, mask, psf, lam, mu1, mu2, reg, iters=3000, stop="rel_x", tol=1e-5)
+    v = O.isnr(x, ybar, r.x, S.valid_mask(size, size, *psf.shape))
+    return table, key, lam, v, r.iters
+
+
+def jobs(size):
+    out = []
+    for blur, kname in (("gauss", "gauss19"), ("motion", "motion15")):
         for bsnr in (40, 60):
-            best = None
-            for lam in grid:
-                S.CONFIG2_LAMBDA[(blur, bsnr)] = lam
-                p = S.config2_problem(1000, blur, bsnr, size=size)
-                r = O.solve(p.ybar, p.mask, p.psf, p.lam, p.mu1, p.mu2, "tv", iters=iters)
-                v = O.isnr(p.x_true, p.ybar, r.x, S.valid_mask(size, size, *p.psf.shape))
-                print(blur, bsnr, lam, round(v, 3), flush=True)
-                if best is None or v > best[1]:
-                    best = (lam, v)
-            print("BEST", blur, bsnr, best, flush=True)
-
-
-
-
-def main_batched(size=256, iters=300):
-    """lambda per (regularizer, blur family) for the batched uneven workload
-    at BSNR 40 dB, on one calibration image per family (seed 1000)."""
-    grid = [1e-5, 3e-5, 1e-4, 3e-4, 1e-3, 3e-3]
-    kernels = {"box": S.psf_box(13), "gauss": S.psf_gaussian(17, 2.5), "motion": S.psf_motion(15.0, 30.0, 15)}
+            for lam in GRID:
+                out.append(("CONFIG2_LAMBDA", (blur, bsnr), kname, bsnr, 0.4, "tv", lam, size))
     for reg in ("tv", "haar"):
-        for fam, psf in kernels.items():
-            g = S.rng(1000)
-            x = S.textured_image(size, size, g)
-            keep = (g.uniform(0.0, 1.0, size=(size, size)) >= 0.25).astype("uint8")
-            ybar, mask, _ = S.observe(x, psf, keep, 40.0, g, fast=True)
-            best = None
-            for lam in grid:
-                mu1, mu2 = S.default_mu(lam)
-                r = O.solve(ybar, mask, psf, lam, mu1, mu2, reg, iters=iters)
-                v = O.isnr(x, ybar, r.x, S.valid_mask(size, size, *psf.shape))
-                print(reg, fam, lam, round(v, 3), flush=True)
-                if best is None or v > best[1]:
-                    best = (lam, v)
-            print("BEST", reg, fam, best, flush=True)
+        for fam, kname in (("box", "box13"), ("gauss", "gauss17"), ("motion", "motion15")):
+            for lam in GRID:
+                out.append(("CONFIG4_LAMBDA", (reg, fam), kname, 40, 0.25, reg, lam, size))
+    return out
+
+
+def main(size=128, procs=8):
+    best = {}
+    with mp.get_context("spawn").Pool(procs) as pool:
+        for table, key, lam, v, it in pool.imap_unordered(_isnr, jobs(size)):
+            print(table, key, lam, round(v, 3), it, flush=True)
+            k = (table, key)
+            if k not in best or v > best[k][1]:
+                best[k] = (lam, v)
+    for (table, key), (lam, v) in sorted(best.items()):
+        print("BEST", table, key, lam, round(v, 3))
 
 
 if __name__ == "__main__":
-    if len(sys.argv) > 1 and sys.argv[1] == "batched":
-        main_batched(*(int(a) for a in sys.argv[2:]))
-    else:
-        main(*(int(a) for a in sys.argv[1:]))
+    main(*(int(a) for a in sys.argv[1:]))

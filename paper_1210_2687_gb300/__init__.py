@@ -41,7 +41,7 @@ _STOP = {"iters": ADMM_STOP_ITERS, "rel_x": ADMM_STOP_REL_X, "rel_obj": ADMM_STO
 EXPORTED = ("admm_deconv_plan", "admm_deconv_solve", "admm_deconv_solve_batch",
             "admm_deconv_state_size", "admm_deconv_get_state", "admm_deconv_destroy",
             "admm_strerror", "admm_deconv_version", "admm_deconv_profile",
-            "admm_deconv_solve_noalloc", "admm_deconv_set_option")
+            "admm_deconv_solve_noalloc", "admm_deconv_set_option", "admm_deconv_warm_start")
 
 ADMM_OPT_MAX_SLOTS = 1
 
@@ -100,6 +100,8 @@ def _load() -> ctypes.CDLL:
     lib.admm_deconv_state_size.restype = ctypes.c_longlong
     lib.admm_deconv_get_state.argtypes = [vp, vp, vp]
     lib.admm_deconv_get_state.restype = ctypes.c_int
+    lib.admm_deconv_warm_start.argtypes = [vp, vp, vp, vp]
+    lib.admm_deconv_warm_start.restype = ctypes.c_int
     lib.admm_deconv_destroy.argtypes = [vp]
     lib.admm_deconv_destroy.restype = None
     lib.admm_strerror.argtypes = [ctypes.c_int]
@@ -166,6 +168,13 @@ def admm_deconv_get_state(plan: int, out_ptr: int, stream=None) -> None:
     rc = lib.admm_deconv_get_state(ctypes.c_void_p(plan), ctypes.c_void_p(out_ptr), _stream(stream))
     if rc != ADMM_OK:
         raise AdmmError(rc, "admm_deconv_get_state")
+
+
+def admm_deconv_warm_start(plan: int, x0_ptr, d0_ptr, stream=None) -> None:
+    rc = lib.admm_deconv_warm_start(ctypes.c_void_p(plan), ctypes.c_void_p(x0_ptr),
+                                    ctypes.c_void_p(d0_ptr), _stream(stream))
+    if rc != ADMM_OK:
+        raise AdmmError(rc, "admm_deconv_warm_start")
 
 
 def admm_deconv_profile(enable: bool) -> admm_profile_t:
@@ -253,6 +262,11 @@ class Plan:
 
     def state_size(self) -> int:
         return admm_deconv_state_size(self.handle)
+
+    def warm_start(self, x0=None, d0=None, stream=None) -> None:
+        """Start the next solve from x0 (H x W) and duals d0 (state_size
+        floats, admm_deconv_get_state layout); None = zeros."""
+        admm_deconv_warm_start(self.handle, _ptr(x0, np.float32), _ptr(d0, np.float32), stream)
 
     def close(self):
         if getattr(self, "handle", None):

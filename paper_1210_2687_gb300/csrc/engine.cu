@@ -52,6 +52,7 @@ struct admm_plan_s {
     float* xstage = nullptr;
     float* psf_dev = nullptr;
     int last_iter = 0;          // iterations of the last solve: d2 lives in buffer last_iter & 1
+    bool warm_pending = false;  // the next solve starts from admm_deconv_warm_start's state
 };
 
 namespace {
@@ -276,6 +277,22 @@ cudaError_t launch_fin_t(const ProbDesc* d, float* const* xo, int count, int H, 
     return cudaGetLastError();
 }
 
+cudaError_t launch_warm_rows(int W, const float* x0, float4* Sb, int H, int Wp, const float2* tw, cudaStream_t s) {
+    const int G = kThreads / (W / 8);
+    const size_t smem = (size_t)(G * W + W) * sizeof(float2);
+    const unsigned grid = (unsigned)((H + G - 1) / G);
+    switch (W) {
+        case 64: warm_rows<64><<<grid, kThreads, smem, s>>>(x0, Sb, H, Wp, tw); break;
+        case 128: warm_rows<128><<<grid, kThreads, smem, s>>>(x0, Sb, H, Wp, tw); break;
+        case 256: warm_rows<256><<<grid, kThreads, smem, s>>>(x0, Sb, H, Wp, tw); break;
+        case 512: warm_rows<512><<<grid, kThreads, smem, s>>>(x0, Sb, H, Wp, tw); break;
+        case 1024: warm_rows<1024><<<grid, kThreads, smem, s>>>(x0, Sb, H, Wp, tw); break;
+        case 2048: warm_rows<2048><<<grid, kThreads, smem, s>>>(x0, Sb, H, Wp, tw); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t launch_fin(int W, const ProbDesc* d, float* const* xo, int count, int H, int Wp, const float2* tw,
                        cudaStream_t s) {
     switch (W) {
@@ -330,6 +347,7 @@ ProbDesc make_desc(const admm_plan_s* pl) {
     d.check_every = pl->p.check_every;
     d.n_strips = pl->n_strips;
     d.n_slots = pl->n_slots;
+    d.warm = pl->warm_pending ? 1 : 0;
     d.tol = pl->p.tol;
     return d;
 }
@@ -491,6 +509,42 @@ int admm_deconv_get_state(admm_plan_t plan, float* d_out, void* stream) {
     const float* d2 = plan->d2 + (size_t)(plan->last_iter & 1) * plan->nb * n;
     CK(cudaMemcpyAsync(d_out + n, d2, (size_t)plan->nb * n * sizeof(float), cudaMemcpyDefault, s));
     CK(cudaStreamSynchronize(s));
+    return ADMM_OK;
+}
+
+int admm_deconv_warm_start(admm_plan_t plan, const float* x0, const float* d0, void* stream) {
+    if (!plan) return ADMM_EINVAL;
+    std::lock_guard<std::mutex> lk(g_mutex);
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    if (plan->device != dev) return ADMM_EINVAL;
+    DeviceCtx* ctx = nullptr;
+    const int rc = ensure_ctx(dev, 1, &ctx);
+    if (rc != ADMM_OK) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int H = plan->p.H, W = plan->p.W;
+    const size_t n = (size_t)H * W;
+    if (x0) {
+        const float* src = x0;
+        if (!is_device_ptr(x0)) {
+            CK(cudaMemcpyAsync(plan->xstage, x0, n * sizeof(float), cudaMemcpyHostToDevice, s));
+            src = plan->xstage;
+        }
+        CK(launch_warm_rows(W, src, plan->Sb, H, plan->Wp, ctx->tw, s));
+        ++g_launches;
+    } else {
+        CK(cudaMemsetAsync(plan->Sb, 0, n / W * plan->Wp * sizeof(float4), s));
+    }
+    // the first iteration reads d2 buffer (1 + 1) & 1 = 0
+    if (d0) {
+        CK(cudaMemcpyAsync(plan->d1, d0, n * sizeof(float), cudaMemcpyDefault, s));
+        CK(cudaMemcpyAsync(plan->d2, d0 + n, (size_t)plan->nb * n * sizeof(float), cudaMemcpyDefault, s));
+    } else {
+        CK(cudaMemsetAsync(plan->d1, 0, n * sizeof(float), s));
+        CK(cudaMemsetAsync(plan->d2, 0, (size_t)plan->nb * n * sizeof(float), s));
+    }
+    CK(cudaStreamSynchronize(s));       // host sources may be released on return
+    plan->warm_pending = true;
     return ADMM_OK;
 }
 
@@ -777,6 +831,7 @@ static int solve_all(DeviceCtx* ctx, const std::vector<std::vector<int>>& classe
     for (int t = 0; t < total; ++t) {
         const ProbCtl& c = ctx->h_ctl[t];
         plans[order[t]]->last_iter = c.iter;
+        plans[order[t]]->warm_pending = false;   // a warm start serves one solve
         if (c.status != 0 && rc == ADMM_OK) rc = c.status;
         if (res) {
             admm_result_t& r = res[order[t]];

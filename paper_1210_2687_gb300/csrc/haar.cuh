@@ -49,7 +49,8 @@ haar_row_inverse(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp
     const ProbDesc& P = probs[pi];
     if (P.ctl->active == 0) return;
     const int k = P.ctl->iter + 1;
-    const bool first = k == 1;                   // d1 = x_prev = 0 (cold start)
+    const bool first = k == 1;                   // x_prev = 0 (no earlier iterate)
+    const bool cold = first && !P.warm;          // d1 = 0 (u0 = d0 = 0)
     const bool chk = is_check_iter(P, k), sprev = store_prev_iter(P, k), nobj = need_obj_iter(P, k);
     extern __shared__ __align__(16) float2 smem[];
     float2* buf = smem;
@@ -73,7 +74,7 @@ haar_row_inverse(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp
         const size_t pix = (size_t)q * W + c;
         const float x = v[m].x, ax = v[m].y;
         // u1 = (M^T M + mu1 I)^{-1} (M^T y + mu1 (A x - d1)); d1 <- d1 - (A x - u1)
-        const float dd1 = first ? 0.f : P.d1[pix];
+        const float dd1 = cold ? 0.f : P.d1[pix];
         const float s1 = ax - dd1;
         const float yb = P.ybar[pix];
         const bool obs = is_observed(yb);
@@ -140,7 +141,7 @@ haar_tile(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W, int n_
     ProbCtl* ctl = P.ctl;
     if (ctl->active == 0) return;
     const int k = ctl->iter + 1;
-    const bool first = k == 1;                   // d2 = 0 (cold start)
+    const bool first = k == 1 && !P.warm;        // d2 = 0 (cold start: u0 = d0 = 0)
     const bool chk = is_check_iter(P, k), nobj = need_obj_iter(P, k);
     extern __shared__ __align__(16) float sm[];
     float* A0 = sm;

@@ -82,6 +82,8 @@ struct ProbDesc {
     int stop, max_iters, check_every;
     int n_strips;             // CTAs per problem of the kernel that finishes an iteration
     int n_slots;              // partial-sum slots to reduce (0: n_strips)
+    int warm;                 // 1: start from x1 = x0, d0 given (Sb holds the row-DFTs
+                              // of x0, d1/d2 buffer 0 hold d0); 0: u0 = d0 = 0
     double tol;
 };
 
@@ -292,7 +294,8 @@ col_phase(const ProbDesc* __restrict__ probs, SlotTable sl, int Wc, int Wp, cons
     if (pi < 0) return;
     const ProbDesc& P = probs[pi];
     if (P.ctl->active == 0) return;
-    if (P.ctl->iter == 0) {
+    const bool warm0 = P.ctl->iter == 0;         // (only reached with a warm start)
+    if (warm0 && !P.warm) {
         // first iteration from u0 = d0 = 0: the right-hand side is zero, so x1 = 0
         const int c0 = blockIdx.x * CB;
         for (int e = threadIdx.x; e < H * CB; e += kThreads)
@@ -343,10 +346,13 @@ col_phase(const ProbDesc* __restrict__ probs, SlotTable sl, int Wc, int Wp, cons
         }
         fft_group2<H, -1>(v, u, bz, bw, tw, t, g);
         if (spec) {
+            // warm start: u0 = H x0 - d0 makes the first x-step return x0, whose
+            // 2-D DFT is the first signal here (1/(HW) for the inverse)
+            const float inv_hw = 1.0f / (float)(H * 2 * (Wc - 1));
 #pragma unroll
             for (int m = 0; m < 8; ++m) {
                 // x^ = K (conj(Lambda) Z1^ + W^);  (A x)^ = Lambda x^
-                const float2 xh = Kv[m] * (cmulc(v[m], L[m]) + u[m]);
+                const float2 xh = warm0 ? inv_hw * v[m] : Kv[m] * (cmulc(v[m], L[m]) + u[m]);
                 v[m] = xh;
                 u[m] = cmul(L[m], xh);
             }
@@ -600,7 +606,8 @@ row_phase_tv(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp, co
     ProbCtl* ctl = P.ctl;
     if (ctl->active == 0) return;
     const int k = ctl->iter + 1;                 // iteration being completed
-    const bool first = k == 1;                   // d1 = d2 = x_prev = 0 (cold start)
+    const bool first = k == 1;                   // x_prev = 0 (no earlier iterate)
+    const bool cold = first && !P.warm;          // d1 = d2 = 0 (u0 = d0 = 0)
     const bool chk = is_check_iter(P, k), sprev = store_prev_iter(P, k), nobj = need_obj_iter(P, k);
     extern __shared__ __align__(16) float2 smem[];
     float2* buf = smem;
@@ -626,14 +633,14 @@ row_phase_tv(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp, co
             for (int j = 0; j < C::CPT; ++j) {
                 const int c = cbase + 32 * j;
                 const size_t pix = (size_t)q * W + c;
-                if (!first) cp_async8(slot + 2 * c, d2in + pix);
+                if (!cold) cp_async8(slot + 2 * c, d2in + pix);
                 if (i >= 1) {
-                    if (!first) cp_async4(slot + 2 * W + c, P.d1 + pix);
+                    if (!cold) cp_async4(slot + 2 * W + c, P.d1 + pix);
                     cp_async4(slot + 3 * W + c, P.ybar + pix);
                     if (chk && !first) cp_async4(slot + 4 * W + c, P.xprev + pix);
                 }
             }
-            if (lane == 0 && !first) cp_async8(slot + 5 * W + 2 * wid, d2in + (size_t)q * W + chalo);
+            if (lane == 0 && !cold) cp_async8(slot + 5 * W + 2 * wid, d2in + (size_t)q * W + chalo);
         }
         cp_async_commit();   // possibly empty: keeps one group per walk row
     };
@@ -643,12 +650,12 @@ row_phase_tv(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp, co
     // shared memory, then the first D walk rows into the ring
     if (tid == 0) {
         const int qh = (r0 - 1 + H) & (H - 1);
-        if (!first) {
+        if (!cold) {
             prefetch_l2(d2in + (size_t)qh * W, W * sizeof(float2));
             for (int i = 0; i < R; ++i) {
                 prefetch_l2(d2in + (size_t)(r0 + i) * W, W * sizeof(float2));
                 prefetch_l2(P.d1 + (size_t)(r0 + i) * W, W * sizeof(float));
-                if (chk) prefetch_l2(P.xprev + (size_t)(r0 + i) * W, W * sizeof(float));
+                if (chk && !first) prefetch_l2(P.xprev + (size_t)(r0 + i) * W, W * sizeof(float));
             }
         }
         for (int i = 0; i < R; ++i) prefetch_l2(P.ybar + (size_t)(r0 + i) * W, W * sizeof(float));
@@ -714,7 +721,7 @@ row_phase_tv(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp, co
                 // D_i x (forward periodic differences)
                 const float gh = xr - x, gv = xd - x;
                 const size_t pix = (size_t)q * W + c;
-                const float2 dd = first ? make_float2(0.f, 0.f) : *reinterpret_cast<const float2*>(slot + 2 * c);
+                const float2 dd = cold ? make_float2(0.f, 0.f) : *reinterpret_cast<const float2*>(slot + 2 * c);
                 // u2 = v-soft(D_i x - d2, lambda/mu2)  (Alg. 3 line 10, 0/0 = 0)
                 const float sh = gh - dd.x, sv = gv - dd.y;
                 const float nrm = sqrtf(fmaf(sh, sh, sv * sv));
@@ -729,7 +736,7 @@ row_phase_tv(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp, co
                 if (owned) {
                     d2out[pix] = make_float2(nh, nv);
                     // u1 = (M^T M + mu1 I)^{-1} (M^T y + mu1 (A x - d1))  (eq. new_line)
-                    const float dd1 = first ? 0.f : slot[2 * W + c];
+                    const float dd1 = cold ? 0.f : slot[2 * W + c];
                     const float yb = slot[3 * W + c];
                     const float s1 = ax - dd1;
                     const bool obs = is_observed(yb);
@@ -757,7 +764,7 @@ row_phase_tv(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp, co
                 // delta_h of the pixel left of the chunk (its owner updates its d2)
                 const float xh = xl_nb;
                 const float xhr = buf[i * C::ROW + swz(wid * C::CW)].x;
-                const float2 dd = first ? make_float2(0.f, 0.f)
+                const float2 dd = cold ? make_float2(0.f, 0.f)
                                         : *reinterpret_cast<const float2*>(slot + 5 * W + 2 * wid);
                 const float sh = (xhr - xh) - dd.x, sv = (xl_nb_dn - xh) - dd.y;
                 const float nrm = sqrtf(fmaf(sh, sh, sv * sv));
@@ -845,6 +852,33 @@ finalize_x(const ProbDesc* __restrict__ probs, float* const* __restrict__ xout, 
 #pragma unroll
         for (int m = 0; m < 8; ++m) xo[t + m * FT] = v[m].x;
     }
+}
+
+// ---------------------------------------------------------------------------
+// Warm start: the row-DFTs of a real starting image x0 (first signal; the
+// second signal is zero) into Sb, where the first iteration's column phase
+// finds them. Grid: ceil(H / G) CTAs, one row per group of W/8 threads.
+// ---------------------------------------------------------------------------
+template <int W>
+__global__ void __launch_bounds__(kThreads)
+warm_rows(const float* __restrict__ x0, float4* __restrict__ Sb, int H, int Wp, const float2* __restrict__ tw_g) {
+    constexpr int FT = W / 8, G = kThreads / FT, ROW = W;
+    extern __shared__ __align__(16) float2 smem[];
+    float2* buf = smem;
+    float2* tw = buf + G * ROW;
+    const int tid = threadIdx.x, g = tid / FT, t = tid % FT;
+    for (int i = tid; i < W; i += kThreads) tw[i] = tw_g[i * (2048 / W)];
+    __syncthreads();
+    const int q = blockIdx.x * G + g;
+    float2 v[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) v[m] = make_float2(q < H ? x0[(size_t)q * W + t + m * FT] : 0.f, 0.f);
+    float2* row = buf + g * ROW;
+    fft_group<W, -1>(v, row, tw, t, g);
+#pragma unroll
+    for (int m = 0; m < 8; ++m) row[swz(t + m * FT)] = v[m];
+    group_sync<W>(g);                // the split reads this group's row only
+    if (q < H) store_split<W>(Sb + (size_t)q * Wp, row, t);
 }
 
 }  // namespace admm
