@@ -2,7 +2,8 @@
 of the converged solution, as the paper tuned lambda per condition for the
 best ISNR (Sec. V). One calibration image per condition (seed 1000), the
 grid {1e-5, 3e-5, 1e-4, 3e-4, 1e-3, 3e-3}, penalties by synth.default_mu,
-solved to rel-x < 1e-5 (at most 3000 iterations).
+solved to rel-x < 1e-5 (at most 3000 iterations); a value whose run did not
+converge within the cap is not a candidate (its ISNR is not the method's).
 
 Conditions:
   inpainting TV workload   (blur, BSNR) in {Gaussian 19 sigma 3, motion 15 at 30}
@@ -43,7 +44,7 @@ def _isnr(job):
     mu1, mu2 = S.default_mu(lam)
     r = O.solve(ybar, mask, psf, lam, mu1, mu2, reg, iters=3000, stop="rel_x", tol=1e-5)
     v = O.isnr(x, ybar, r.x, S.valid_mask(size, size, *psf.shape))
-    return table, key, lam, v, r.iters
+    return table, key, lam, v, r.iters, r.converged
 
 
 def jobs(size):
@@ -62,10 +63,10 @@ def jobs(size):
 def main(size=128, procs=8):
     best = {}
     with mp.get_context("spawn").Pool(procs) as pool:
-        for table, key, lam, v, it in pool.imap_unordered(_isnr, jobs(size)):
-            print(table, key, lam, round(v, 3), it, flush=True)
+        for table, key, lam, v, it, conv in pool.imap_unordered(_isnr, jobs(size)):
+            print(table, key, lam, round(v, 3), it, "converged" if conv else "not converged", flush=True)
             k = (table, key)
-            if k not in best or v > best[k][1]:
+            if conv and (k not in best or v > best[k][1]):
                 best[k] = (lam, v)
     for (table, key), (lam, v) in sorted(best.items()):
         print("BEST", table, key, lam, round(v, 3))

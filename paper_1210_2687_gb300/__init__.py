@@ -41,7 +41,10 @@ _STOP = {"iters": ADMM_STOP_ITERS, "rel_x": ADMM_STOP_REL_X, "rel_obj": ADMM_STO
 EXPORTED = ("admm_deconv_plan", "admm_deconv_solve", "admm_deconv_solve_batch",
             "admm_deconv_state_size", "admm_deconv_get_state", "admm_deconv_destroy",
             "admm_strerror", "admm_deconv_version", "admm_deconv_profile",
-            "admm_deconv_solve_noalloc", "admm_deconv_set_option", "admm_deconv_warm_start")
+            "admm_deconv_solve_noalloc", "admm_deconv_set_option", "admm_deconv_warm_start",
+            "admm_cnn_param_count", "admm_cnn_create", "admm_cnn_set_params", "admm_cnn_get_params",
+            "admm_cnn_forward", "admm_cnn_gradients", "admm_cnn_train_step", "admm_cnn_predict_start",
+            "admm_cnn_launches", "admm_cnn_destroy")
 
 ADMM_OPT_MAX_SLOTS = 1
 
@@ -115,6 +118,28 @@ def _load() -> ctypes.CDLL:
     lib.admm_deconv_solve_noalloc.restype = ctypes.c_int
     lib.admm_deconv_set_option.argtypes = [ctypes.c_int, ctypes.c_longlong]
     lib.admm_deconv_set_option.restype = ctypes.c_int
+    ci, fp = ctypes.c_int, ctypes.c_float
+    dp = ctypes.POINTER(ctypes.c_double)
+    lib.admm_cnn_param_count.argtypes = []
+    lib.admm_cnn_param_count.restype = ctypes.c_longlong
+    lib.admm_cnn_launches.argtypes = []
+    lib.admm_cnn_launches.restype = ctypes.c_longlong
+    lib.admm_cnn_create.argtypes = [ctypes.POINTER(vp), ctypes.c_longlong, ci]
+    lib.admm_cnn_create.restype = ci
+    lib.admm_cnn_set_params.argtypes = [vp, vp]
+    lib.admm_cnn_set_params.restype = ci
+    lib.admm_cnn_get_params.argtypes = [vp, vp]
+    lib.admm_cnn_get_params.restype = ci
+    lib.admm_cnn_forward.argtypes = [vp, ci, ci, ci, vp, vp, vp, vp]
+    lib.admm_cnn_forward.restype = ci
+    lib.admm_cnn_gradients.argtypes = [vp, ci, ci, ci, vp, vp, vp, ctypes.POINTER(fp), vp, dp, vp]
+    lib.admm_cnn_gradients.restype = ci
+    lib.admm_cnn_train_step.argtypes = [vp, ci, ci, ci, vp, vp, vp, ctypes.POINTER(fp), fp, dp, vp]
+    lib.admm_cnn_train_step.restype = ci
+    lib.admm_cnn_predict_start.argtypes = [vp, ci, ci, ci, vp, vp, ctypes.POINTER(fp), vp, vp, vp]
+    lib.admm_cnn_predict_start.restype = ci
+    lib.admm_cnn_destroy.argtypes = [vp]
+    lib.admm_cnn_destroy.restype = None
     return lib
 
 
@@ -194,6 +219,89 @@ def admm_deconv_solve_noalloc(params: admm_params_t, y_ptr: int, mask_ptr: int |
                                        ctypes.c_void_p(mask_ptr or 0), ctypes.c_void_p(x_ptr),
                                        ctypes.byref(res), _stream(stream))
     return rc, res
+
+
+def _f4(vals):
+    arr = (ctypes.c_float * 4)(*[float(v) for v in vals])
+    return arr
+
+
+def _check(rc, what):
+    if rc != ADMM_OK:
+        raise AdmmError(rc, what)
+
+
+class Cnn:
+    """Owns one admm_cnn_t (the warm-start network). Images are passed as
+    contiguous CUDA tensors of shape (count, H, W) (float32 ybar, uint8 mask);
+    targets (count, H, W, 4) float32."""
+
+    def __init__(self, max_pixels: int, training: bool = False):
+        h = ctypes.c_void_p()
+        _check(lib.admm_cnn_create(ctypes.byref(h), int(max_pixels), int(bool(training))), "admm_cnn_create")
+        self.handle = h.value
+
+    @staticmethod
+    def param_count() -> int:
+        return int(lib.admm_cnn_param_count())
+
+    def set_params(self, params) -> None:
+        _check(lib.admm_cnn_set_params(ctypes.c_void_p(self.handle), ctypes.c_void_p(_ptr(params, np.float32))),
+               "admm_cnn_set_params")
+
+    def get_params(self) -> np.ndarray:
+        out = np.empty(self.param_count(), dtype=np.float32)
+        _check(lib.admm_cnn_get_params(ctypes.c_void_p(self.handle), ctypes.c_void_p(out.ctypes.data)),
+               "admm_cnn_get_params")
+        return out
+
+    def forward(self, ybar, mask, out, stream=None) -> None:
+        n, H, W = ybar.shape
+        _check(lib.admm_cnn_forward(ctypes.c_void_p(self.handle), n, H, W, ctypes.c_void_p(_ptr(ybar, np.float32)),
+                                    ctypes.c_void_p(_ptr(mask, np.uint8)), ctypes.c_void_p(_ptr(out, np.float32)),
+                                    _stream(stream)), "admm_cnn_forward")
+
+    def gradients(self, ybar, mask, target, chan_w, grads, stream=None) -> float:
+        n, H, W = ybar.shape
+        loss = ctypes.c_double()
+        _check(lib.admm_cnn_gradients(ctypes.c_void_p(self.handle), n, H, W, ctypes.c_void_p(_ptr(ybar, np.float32)),
+                                      ctypes.c_void_p(_ptr(mask, np.uint8)), ctypes.c_void_p(_ptr(target, np.float32)),
+                                      _f4(chan_w), ctypes.c_void_p(_ptr(grads, np.float32)), ctypes.byref(loss),
+                                      _stream(stream)), "admm_cnn_gradients")
+        return loss.value
+
+    def train_step(self, ybar, mask, target, chan_w, lr, want_loss=True, stream=None):
+        n, H, W = ybar.shape
+        loss = ctypes.c_double()
+        _check(lib.admm_cnn_train_step(ctypes.c_void_p(self.handle), n, H, W, ctypes.c_void_p(_ptr(ybar, np.float32)),
+                                       ctypes.c_void_p(_ptr(mask, np.uint8)),
+                                       ctypes.c_void_p(_ptr(target, np.float32)), _f4(chan_w), float(lr),
+                                       ctypes.byref(loss) if want_loss else None, _stream(stream)),
+               "admm_cnn_train_step")
+        return loss.value if want_loss else None
+
+    def predict_start(self, ybar, mask, scales, x0, d0, stream=None) -> None:
+        n, H, W = ybar.shape
+        _check(lib.admm_cnn_predict_start(ctypes.c_void_p(self.handle), n, H, W,
+                                          ctypes.c_void_p(_ptr(ybar, np.float32)),
+                                          ctypes.c_void_p(_ptr(mask, np.uint8)), _f4(scales),
+                                          ctypes.c_void_p(_ptr(x0, np.float32)), ctypes.c_void_p(_ptr(d0, np.float32)),
+                                          _stream(stream)), "admm_cnn_predict_start")
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib.admm_cnn_destroy(ctypes.c_void_p(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def admm_cnn_launches() -> int:
+    return int(lib.admm_cnn_launches())
 
 
 def admm_deconv_set_option(option: int, value: int) -> None:

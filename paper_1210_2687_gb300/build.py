@@ -16,7 +16,7 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 LIB = os.path.join(PKG, "libadmm_deconv.so")
-SOURCES = [os.path.join(CSRC, "engine.cu")]
+SOURCES = [os.path.join(CSRC, "engine.cu"), os.path.join(CSRC, "cnn.cu")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -32,7 +32,8 @@ def _inputs():
     for f in os.listdir(CSRC):
         if f.endswith((".cuh", ".h")):
             files.append(os.path.join(CSRC, f))
-    files.append(os.path.join(ROOT, "include", "admm_deconv.h"))
+    inc = os.path.join(ROOT, "include")
+    files += [os.path.join(inc, f) for f in os.listdir(inc) if f.endswith(".h")]
     files.append(os.path.abspath(__file__))
     return files
 
@@ -45,20 +46,33 @@ def up_to_date() -> bool:
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile libadmm_deconv.so (skipped when newer than every source)."""
+    """Compile libadmm_deconv.so (skipped when newer than every source): one
+    object per translation unit, compiled in parallel, then one link."""
     if not force and up_to_date():
         return LIB
     nvcc = _nvcc()
     cuda_lib = os.path.join(os.path.dirname(os.path.dirname(nvcc)), "lib64")
-    tmp = LIB + ".tmp"
-    cmd = [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-fvisibility=hidden", "-shared",
-           "-cudart", "shared", f"-Xlinker=-rpath,{cuda_lib}", "-I", os.path.join(ROOT, "include"),
-           "-o", tmp, *SOURCES]
+    common = [*ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-fvisibility=hidden",
+              "-I", os.path.join(ROOT, "include")]
     if verbose:
-        cmd.insert(1, "-Xptxas=-v")
-        print(" ".join(cmd), flush=True)
-    subprocess.run(cmd, check=True)
+        common.insert(0, "-Xptxas=-v")
+    objs, procs = [], []
+    for src in SOURCES:
+        obj = os.path.join(CSRC, os.path.basename(src) + ".o")
+        cmd = [nvcc, *common, "-c", "-o", obj, src]
+        if verbose:
+            print(" ".join(cmd), flush=True)
+        procs.append((cmd, subprocess.Popen(cmd)))
+        objs.append(obj)
+    for cmd, pr in procs:
+        if pr.wait() != 0:
+            raise subprocess.CalledProcessError(pr.returncode, cmd)
+    tmp = LIB + ".tmp"
+    link = [nvcc, *ARCH, "-shared", "-cudart", "shared", f"-Xlinker=-rpath,{cuda_lib}", "-o", tmp, *objs]
+    subprocess.run(link, check=True)
     os.replace(tmp, LIB)
+    for obj in objs:
+        os.remove(obj)
     return LIB
 
 

@@ -1,0 +1,724 @@
+// cnn.cu -- the learned warm start: a stack of 3 x 3 convolutions on BF16
+// tensor cores (mma.sync m16n8k16, FP32 accumulate), its backward pass and
+// Adam. Not part of the paper; Theorem 1 (convergence from any u0, d0) is
+// what lets a predicted start feed Algorithm 2.
+//
+// Layout. Activations are NHWC BF16 with the channel count padded to 16 or
+// 32 (64 B per pixel at 32 channels), so a pixel's channels are one
+// contiguous run: the input tile of a CTA is a few coalesced row segments.
+// Packed weights are BF16 [tap][cout][cin] (cin contiguous), the order in
+// which the B operand of the MMA consumes them.
+//
+// Forward / input-gradient kernel: a CTA computes a 16 x 16 pixel tile for
+// all output channels. Its input tile (18 x 18 pixels with halo, zero outside
+// the image) and all nine taps of the weights sit in shared memory with the
+// pixel and weight-row strides padded by 8 elements, which makes every
+// fragment load conflict-free. Warp w owns tile rows 2w and 2w + 1 (one
+// m16 block each: 16 pixels of a row); the K loop runs over the 9 taps and
+// the input channels in steps of 16. The same kernel computes the gradient
+// in the input of a layer (a convolution with the flipped, transposed
+// weights), gated by the ReLU of the layer below.
+//
+// Weight-gradient kernel: per tap, dW_tap = G^T A_tap, a contraction over
+// pixels. A CTA of 9 warps (one per tap) loops over tiles; the gradient and
+// activation tiles are stored channel-major in shared memory so the MMA
+// operands are pixel pairs of one channel; the CTA's FP32 partial sums go to
+// global memory with one atomic add per element at the end.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "../../include/admm_warmstart.h"
+
+namespace {
+
+using bf16 = __nv_bfloat16;
+
+constexpr int kLayers = ADMM_CNN_LAYERS;
+constexpr int kWidth = ADMM_CNN_WIDTH;
+constexpr int kIn = 2, kOut = 4;
+constexpr int kTile = 16;
+
+// real (cout, cin) and padded channel counts of layer l
+__host__ __device__ constexpr int layer_cin(int l) { return l == 0 ? kIn : kWidth; }
+__host__ __device__ constexpr int layer_cout(int l) { return l == kLayers - 1 ? kOut : kWidth; }
+constexpr int pad16(int c) { return c <= 16 ? 16 : 32; }
+constexpr int layer_cinp(int l) { return pad16(layer_cin(l)); }
+constexpr int layer_coutp(int l) { return l == kLayers - 1 ? 8 : kWidth; }
+
+long long param_offset(int l) {
+    long long o = 0;
+    for (int j = 0; j < l; ++j) o += (long long)layer_cout(j) * layer_cin(j) * 9 + layer_cout(j);
+    return o;
+}
+long long param_count() { return param_offset(kLayers); }
+
+std::mutex g_cnn_mutex;
+long long g_cnn_launches = 0;
+
+int fail(cudaError_t) { return ADMM_ECUDA; }
+#define CKC(call)                                  \
+    do {                                           \
+        cudaError_t e_ = (call);                   \
+        if (e_ != cudaSuccess) return fail(e_);    \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// device helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void mma_bf16(float (&c)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                         uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ uint32_t ld32(const bf16* p) { return *reinterpret_cast<const uint32_t*>(p); }
+
+__device__ __forceinline__ uint32_t pack2(bf16 lo, bf16 hi) {
+    return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+}
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
+// ---------------------------------------------------------------------------
+// network input: [M^T y, mask] in channels 0 and 1 of a 16-channel tensor
+// ---------------------------------------------------------------------------
+__global__ void cnn_input_kernel(const float* __restrict__ ybar, const uint8_t* __restrict__ mask,
+                                 bf16* __restrict__ a0, long long npx) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= npx) return;
+    const bool obs = mask[i] != 0;
+    const float y = obs ? ybar[i] : 0.f;
+    uint4 lo = make_uint4(pack2(__float2bfloat16(y), __float2bfloat16(obs ? 1.f : 0.f)), 0u, 0u, 0u);
+    uint4* dst = reinterpret_cast<uint4*>(a0 + i * 16);
+    dst[0] = lo;
+    dst[1] = make_uint4(0u, 0u, 0u, 0u);
+}
+
+// ---------------------------------------------------------------------------
+// 3 x 3 convolution on a 16 x 16 output tile (see the file comment)
+// ---------------------------------------------------------------------------
+enum { kModeReluBf16 = 0, kModeOutF32 = 1, kModeGateBf16 = 2 };
+
+template <int CIN, int COUT>
+struct ConvCfg {
+    static constexpr int PS = CIN + 8;               // pixel stride in shared memory (elements)
+    static constexpr int WS = CIN + 8;               // weight row stride
+    static constexpr int HALO = kTile + 2;
+    static constexpr int IN_ELEMS = HALO * HALO * PS;
+    static constexpr int W_ELEMS = 9 * COUT * WS;
+    static constexpr size_t SMEM = (size_t)(IN_ELEMS + W_ELEMS) * sizeof(bf16);
+    static_assert(CIN % 16 == 0 && COUT % 8 == 0, "channel padding");
+    static_assert(SMEM <= 48 * 1024, "fits the default shared-memory window");
+};
+
+// in: [img][H][W][CIN]; wpk: [9][COUT][CIN]; bias: [COUT real] or null;
+// out: bf16 [img][H][W][COUT] (modes 0, 2) or float [img][H][W][4] (mode 1);
+// gate (mode 2): bf16 [img][H][W][COUT], the gradient passes where gate > 0.
+template <int CIN, int COUT, int MODE>
+__global__ void __launch_bounds__(256)
+conv3x3_kernel(const bf16* __restrict__ in, const bf16* __restrict__ wpk, const float* __restrict__ bias,
+               int cout_real, void* __restrict__ out, const bf16* __restrict__ gate, int H, int W) {
+    using C = ConvCfg<CIN, COUT>;
+    extern __shared__ __align__(16) bf16 sm[];
+    bf16* sIn = sm;
+    bf16* sW = sm + C::IN_ELEMS;
+    const int tid = threadIdx.x;
+    const int c0 = blockIdx.x * kTile, r0 = blockIdx.y * kTile;
+    const size_t img = (size_t)blockIdx.z * H * W;
+
+    // input tile with halo: CIN / 8 chunks of 16 B per pixel
+    constexpr int CH = CIN / 8;
+    for (int e = tid; e < C::HALO * C::HALO * CH; e += 256) {
+        const int pix = e / CH, ch = e % CH;
+        const int ty = pix / C::HALO, tx = pix % C::HALO;
+        const int gr = r0 + ty - 1, gc = c0 + tx - 1;
+        bf16* dst = sIn + pix * C::PS + ch * 8;
+        if (gr >= 0 && gr < H && gc >= 0 && gc < W)
+            cp_async16(dst, in + (img + (size_t)gr * W + gc) * CIN + ch * 8);
+        else
+            *reinterpret_cast<uint4*>(dst) = make_uint4(0u, 0u, 0u, 0u);
+    }
+    for (int e = tid; e < 9 * COUT * CH; e += 256) {
+        const int row = e / CH, ch = e % CH;
+        cp_async16(sW + row * C::WS + ch * 8, wpk + (size_t)row * CIN + ch * 8);
+    }
+    cp_async_wait_all();
+    __syncthreads();
+
+    const int lane = tid & 31, warp = tid >> 5;
+    const int g = lane >> 2, t = lane & 3;
+    constexpr int NT = COUT / 8;
+    float acc[2][NT][4];
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[mt][nt][j] = 0.f;
+
+#pragma unroll
+    for (int tap = 0; tap < 9; ++tap) {
+        const int p = tap / 3, q = tap % 3;           // input offset (p - 1, q - 1)
+#pragma unroll
+        for (int kc = 0; kc < CIN / 16; ++kc) {
+            uint32_t b[NT][2];
+#pragma unroll
+            for (int nt = 0; nt < NT; ++nt) {
+                const bf16* wr = sW + (tap * COUT + nt * 8 + g) * C::WS + kc * 16 + 2 * t;
+                b[nt][0] = ld32(wr);
+                b[nt][1] = ld32(wr + 8);
+            }
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt) {
+                const int rr = 2 * warp + mt;         // tile row of this m block
+                // A[m][k]: m = output column, k = input channel; halo offset +1 cancels -1
+                const bf16* ar = sIn + ((rr + p) * C::HALO + q) * C::PS + kc * 16 + 2 * t;
+                const uint32_t a0 = ld32(ar + g * C::PS);
+                const uint32_t a1 = ld32(ar + (g + 8) * C::PS);
+                const uint32_t a2 = ld32(ar + g * C::PS + 8);
+                const uint32_t a3 = ld32(ar + (g + 8) * C::PS + 8);
+#pragma unroll
+                for (int nt = 0; nt < NT; ++nt) mma_bf16(acc[mt][nt], a0, a1, a2, a3, b[nt][0], b[nt][1]);
+            }
+        }
+    }
+
+    // epilogue: c0, c1 -> (column g, channels 2t, 2t+1); c2, c3 -> column g + 8
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt) {
+        const int gr = r0 + 2 * warp + mt;
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+            const int gc = c0 + g + 8 * half;
+            const size_t px = img + (size_t)gr * W + gc;
+#pragma unroll
+            for (int nt = 0; nt < NT; ++nt) {
+                const int ch = nt * 8 + 2 * t;
+                float v0 = acc[mt][nt][2 * half], v1 = acc[mt][nt][2 * half + 1];
+                if (MODE == kModeReluBf16) {
+                    v0 = ch < cout_real ? fmaxf(v0 + bias[ch], 0.f) : 0.f;
+                    v1 = ch + 1 < cout_real ? fmaxf(v1 + bias[ch + 1], 0.f) : 0.f;
+                    *reinterpret_cast<__nv_bfloat162*>(static_cast<bf16*>(out) + px * COUT + ch) =
+                        __floats2bfloat162_rn(v0, v1);
+                } else if (MODE == kModeOutF32) {
+                    if (ch < kOut)
+                        *reinterpret_cast<float2*>(static_cast<float*>(out) + px * kOut + ch) =
+                            make_float2(v0 + bias[ch], v1 + bias[ch + 1]);
+                } else {
+                    const __nv_bfloat162 gt = *reinterpret_cast<const __nv_bfloat162*>(gate + px * COUT + ch);
+                    v0 = __bfloat162float(gt.x) > 0.f ? v0 : 0.f;
+                    v1 = __bfloat162float(gt.y) > 0.f ? v1 : 0.f;
+                    *reinterpret_cast<__nv_bfloat162*>(static_cast<bf16*>(out) + px * COUT + ch) =
+                        __floats2bfloat162_rn(v0, v1);
+                }
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// weight and bias gradients of one layer
+// a: [img][H][W][CIN] (layer input), g: [img][H][W][COUT] (gradient in the
+// layer's pre-activation output). dw: FP32 [cout_real][cin_real][9] slice of
+// the gradient vector, db: [cout_real].
+// ---------------------------------------------------------------------------
+template <int CIN, int COUT>
+struct WgradCfg {
+    static constexpr int HALO = kTile + 2;
+    static constexpr int PA = HALO * HALO + 4;       // activation plane stride (elements)
+    static constexpr int PG = kTile * kTile + 8;     // gradient plane stride
+    static constexpr size_t SMEM = (size_t)(CIN * PA + COUT * PG) * sizeof(bf16) + COUT * sizeof(float);
+    static_assert(SMEM <= 48 * 1024, "fits the default shared-memory window");
+};
+
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(288)
+conv3x3_wgrad_kernel(const bf16* __restrict__ a, const bf16* __restrict__ gr, float* __restrict__ dw,
+                     float* __restrict__ db, int cin_real, int cout_real, int H, int W, int images) {
+    using C = WgradCfg<CIN, COUT>;
+    extern __shared__ __align__(16) bf16 sm[];
+    bf16* sA = sm;                                   // [CIN][PA]
+    bf16* sG = sm + CIN * C::PA;                     // [COUT][PG]
+    float* sDb = reinterpret_cast<float*>(sG + COUT * C::PG);
+    const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;     // warp = tap
+    const int g = lane >> 2, t = lane & 3;
+    const int p = warp / 3, q = warp % 3;
+    constexpr int MT = COUT / 16, NT = CIN / 8;
+    float acc[MT][NT][4];
+#pragma unroll
+    for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[mt][nt][j] = 0.f;
+    for (int o = tid; o < COUT; o += 288) sDb[o] = 0.f;
+
+    const int tx = W / kTile, ty = H / kTile;
+    const int tiles = tx * ty * images;
+    for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        const int im = tile / (tx * ty), rem = tile % (tx * ty);
+        const int r0 = (rem / tx) * kTile, c0 = (rem % tx) * kTile;
+        const size_t img = (size_t)im * H * W;
+        __syncthreads();                             // previous tile's operands are consumed
+        // activation tile with halo, channel-major (8 channels per thread and pixel)
+        for (int e = tid; e < C::HALO * C::HALO * (CIN / 8); e += 288) {
+            const int pix = e / (CIN / 8), ch = (e % (CIN / 8)) * 8;
+            const int yy = pix / C::HALO, xx = pix % C::HALO;
+            const int gy = r0 + yy - 1, gx = c0 + xx - 1;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (gy >= 0 && gy < H && gx >= 0 && gx < W)
+                v = *reinterpret_cast<const uint4*>(a + (img + (size_t)gy * W + gx) * CIN + ch);
+            const bf16* vv = reinterpret_cast<const bf16*>(&v);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) sA[(ch + j) * C::PA + pix] = vv[j];
+        }
+        for (int e = tid; e < kTile * kTile * (COUT / 8); e += 288) {
+            const int pix = e / (COUT / 8), ch = (e % (COUT / 8)) * 8;
+            const int gy = r0 + pix / kTile, gx = c0 + pix % kTile;
+            const uint4 v = *reinterpret_cast<const uint4*>(gr + (img + (size_t)gy * W + gx) * COUT + ch);
+            const bf16* vv = reinterpret_cast<const bf16*>(&v);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) sG[(ch + j) * C::PG + pix] = vv[j];
+        }
+        __syncthreads();
+        // bias gradient: channel o = tid % 32 sums every 9th pixel row
+        if ((tid & 31) < COUT) {
+            const int o = tid & 31;
+            float s = 0.f;
+            for (int px = warp; px < kTile * kTile; px += 9) s += __bfloat162float(sG[o * C::PG + px]);
+            atomicAdd(sDb + o, s);
+        }
+        // K loop: one output row of 16 pixels per step
+#pragma unroll 2
+        for (int rr = 0; rr < kTile; ++rr) {
+            uint32_t af[MT][4];
+#pragma unroll
+            for (int mt = 0; mt < MT; ++mt) {
+                // A[m][k] = G[pixel k][channel m]
+                const bf16* gp = sG + (mt * 16 + g) * C::PG + rr * kTile + 2 * t;
+                af[mt][0] = ld32(gp);
+                af[mt][1] = ld32(gp + 8 * C::PG);
+                af[mt][2] = ld32(gp + 8);
+                af[mt][3] = ld32(gp + 8 * C::PG + 8);
+            }
+            const int base = (rr + p) * C::HALO + q + 2 * t;  // pixel (rr + p - 1, 2t + q - 1) + halo
+#pragma unroll
+            for (int nt = 0; nt < NT; ++nt) {
+                // B[k][n] = A_tap[pixel k][channel n]: two pixels of one channel
+                const bf16* ap = sA + (nt * 8 + g) * C::PA + base;
+                const uint32_t b0 = pack2(ap[0], ap[1]);
+                const uint32_t b1 = pack2(ap[8], ap[9]);
+#pragma unroll
+                for (int mt = 0; mt < MT; ++mt) mma_bf16(acc[mt][nt], af[mt][0], af[mt][1], af[mt][2], af[mt][3], b0, b1);
+            }
+        }
+    }
+    // C[m][n] = dW[o = m][i = n] of this tap
+#pragma unroll
+    for (int mt = 0; mt < MT; ++mt) {
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int o = mt * 16 + g + (j >= 2 ? 8 : 0);
+                const int i = nt * 8 + 2 * t + (j & 1);
+                if (o < cout_real && i < cin_real) atomicAdd(dw + ((size_t)o * cin_real + i) * 9 + warp, acc[mt][nt][j]);
+            }
+        }
+    }
+    __syncthreads();
+    for (int o = tid; o < cout_real; o += 288) atomicAdd(db + o, sDb[o]);
+}
+
+// ---------------------------------------------------------------------------
+// loss and its gradient in the output: g = 2 c_k (o - t) / npx (16 channels,
+// 4 used); per-block FP64 partial sums of the loss
+// ---------------------------------------------------------------------------
+__global__ void cnn_loss_kernel(const float* __restrict__ o, const float* __restrict__ tg, float4 cw,
+                                bf16* __restrict__ gout, double* __restrict__ loss, long long npx) {
+    __shared__ double red[8];
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    double l = 0.0;
+    if (i < npx) {
+        const float4 ov = reinterpret_cast<const float4*>(o)[i];
+        const float4 tv = reinterpret_cast<const float4*>(tg)[i];
+        const float e0 = ov.x - tv.x, e1 = ov.y - tv.y, e2 = ov.z - tv.z, e3 = ov.w - tv.w;
+        l = (double)cw.x * e0 * e0 + (double)cw.y * e1 * e1 + (double)cw.z * e2 * e2 + (double)cw.w * e3 * e3;
+        const float s = 2.0f / (float)npx;
+        uint4* dst = reinterpret_cast<uint4*>(gout + i * 16);
+        dst[0] = make_uint4(pack2(__float2bfloat16(s * cw.x * e0), __float2bfloat16(s * cw.y * e1)),
+                            pack2(__float2bfloat16(s * cw.z * e2), __float2bfloat16(s * cw.w * e3)), 0u, 0u);
+        dst[1] = make_uint4(0u, 0u, 0u, 0u);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) l += __shfl_down_sync(0xffffffffu, l, off);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = l;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+        atomicAdd(loss, s / (double)npx);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Adam (Kingma and Ba, Algorithm 1) on the FP32 parameter vector
+// ---------------------------------------------------------------------------
+__global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ gd, float* __restrict__ m,
+                            float* __restrict__ v, long long n, float lr, float b1, float b2, float eps,
+                            float c1, float c2) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gi = gd[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+// ---------------------------------------------------------------------------
+// BF16 weight packing: forward [tap][coutp][cinp], and for the input
+// gradient the flipped transpose [tap'][cinp][coutp_g] with
+// w'[tap'][i][o] = w[o][i][8 - tap'] (zero in the padding)
+// ---------------------------------------------------------------------------
+__global__ void pack_kernel(const float* __restrict__ w, bf16* __restrict__ fwd, bf16* __restrict__ bwd,
+                            int cin, int cout, int cinp, int coutp, int coutg) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nf = 9 * coutp * cinp;
+    if (e < nf) {
+        const int tap = e / (coutp * cinp), o = (e / cinp) % coutp, i = e % cinp;
+        const float x = (o < cout && i < cin) ? w[((size_t)o * cin + i) * 9 + tap] : 0.f;
+        fwd[e] = __float2bfloat16(x);
+    }
+    const int nb = 9 * cinp * coutg;
+    if (bwd && e < nb) {
+        const int tap = e / (cinp * coutg), i = (e / coutg) % cinp, o = e % coutg;
+        const float x = (o < cout && i < cin) ? w[((size_t)o * cin + i) * 9 + (8 - tap)] : 0.f;
+        bwd[e] = __float2bfloat16(x);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// output -> warm start (x0, d1, (d2h, d2v) interleaved)
+// ---------------------------------------------------------------------------
+__global__ void split_start_kernel(const float* __restrict__ o, float s0, float s1, float s2,
+                                   float* __restrict__ x0, float* __restrict__ d0, long long n, long long npx) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= npx) return;
+    const long long im = i / n, px = i % n;
+    const float4 v = reinterpret_cast<const float4*>(o)[i];
+    x0[i] = s0 * v.x;
+    float* d = d0 + im * 3 * n;
+    d[px] = s1 * v.y;
+    reinterpret_cast<float2*>(d + n)[px] = make_float2(s2 * v.z, s2 * v.w);
+}
+
+// ---------------------------------------------------------------------------
+// launch helpers
+// ---------------------------------------------------------------------------
+template <int CIN, int COUT, int MODE>
+cudaError_t conv(const bf16* in, const bf16* w, const float* bias, int cout_real, void* out, const bf16* gate,
+                 int count, int H, int W, cudaStream_t s) {
+    dim3 grid(W / kTile, H / kTile, count);
+    conv3x3_kernel<CIN, COUT, MODE><<<grid, 256, ConvCfg<CIN, COUT>::SMEM, s>>>(in, w, bias, cout_real, out, gate,
+                                                                                 H, W);
+    ++g_cnn_launches;
+    return cudaGetLastError();
+}
+
+template <int CIN, int COUT>
+cudaError_t wgrad(const bf16* a, const bf16* g, float* dw, float* db, int cin_real, int cout_real, int count,
+                  int H, int W, int sms, cudaStream_t s) {
+    const int tiles = (H / kTile) * (W / kTile) * count;
+    const int grid = std::min(tiles, 2 * sms);
+    conv3x3_wgrad_kernel<CIN, COUT><<<grid, 288, WgradCfg<CIN, COUT>::SMEM, s>>>(a, g, dw, db, cin_real, cout_real, H,
+                                                                                  W, count);
+    ++g_cnn_launches;
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+struct admm_cnn_s {
+    int device = 0;
+    int sms = 152;
+    long long max_px = 0;
+    bool training = false;
+    float* params = nullptr;       // FP32 master vector
+    float* grads = nullptr;
+    float* m = nullptr;
+    float* v = nullptr;
+    long long adam_t = 0;
+    bf16* wf[kLayers] = {};        // packed forward weights
+    bf16* wb[kLayers] = {};        // packed input-gradient weights (layers 1..)
+    bf16* a0 = nullptr;            // input, 16 channels
+    bf16* act[kLayers - 1] = {};   // activations after layers 0..6 (training keeps all)
+    float* out = nullptr;          // output, 4 channels FP32
+    bf16* gbuf[2] = {};            // gradient ping-pong, 32 channels
+    bf16* gout = nullptr;          // output gradient, 16 channels
+    double* loss = nullptr;        // device accumulator
+    double* h_loss = nullptr;      // pinned
+    std::vector<void*> allocs;
+};
+
+namespace {
+
+template <typename T>
+int dalloc(admm_cnn_s* n, T** p, size_t count) {
+    void* q = nullptr;
+    if (cudaMalloc(&q, count * sizeof(T)) != cudaSuccess) {
+        cudaGetLastError();
+        return ADMM_ENOMEM;
+    }
+    n->allocs.push_back(q);
+    *p = static_cast<T*>(q);
+    return ADMM_OK;
+}
+
+int check_shape(const admm_cnn_s* n, int count, int H, int W) {
+    if (count <= 0 || H < kTile || W < kTile || H % kTile || W % kTile) return ADMM_EINVAL;
+    if ((long long)count * H * W > n->max_px) return ADMM_EINVAL;
+    return ADMM_OK;
+}
+
+int pack_all(admm_cnn_s* n, cudaStream_t s) {
+    for (int l = 0; l < kLayers; ++l) {
+        const int cin = layer_cin(l), cout = layer_cout(l);
+        const int cinp = layer_cinp(l), coutp = layer_coutp(l);
+        const int coutg = pad16(cout);
+        const int nmax = std::max(9 * coutp * cinp, 9 * cinp * coutg);
+        pack_kernel<<<(nmax + 255) / 256, 256, 0, s>>>(n->params + param_offset(l), n->wf[l], n->wb[l], cin, cout,
+                                                        cinp, coutp, coutg);
+        ++g_cnn_launches;
+        CKC(cudaGetLastError());
+    }
+    return ADMM_OK;
+}
+
+// forward pass; with `keep` every activation is stored for the backward pass,
+// otherwise two buffers alternate
+int forward(admm_cnn_s* n, int count, int H, int W, const float* ybar, const uint8_t* mask, bool keep,
+            cudaStream_t s) {
+    const long long npx = (long long)count * H * W;
+    cnn_input_kernel<<<(unsigned)((npx + 255) / 256), 256, 0, s>>>(ybar, mask, n->a0, npx);
+    ++g_cnn_launches;
+    CKC(cudaGetLastError());
+    const bf16* cur = n->a0;
+    for (int l = 0; l < kLayers; ++l) {
+        const float* b = n->params + param_offset(l) + (long long)layer_cout(l) * layer_cin(l) * 9;
+        if (l == kLayers - 1) {
+            CKC((conv<32, 8, kModeOutF32>(cur, n->wf[l], b, kOut, n->out, nullptr, count, H, W, s)));
+        } else {
+            bf16* dst = keep ? n->act[l] : n->act[l & 1];
+            if (l == 0)
+                CKC((conv<16, 32, kModeReluBf16>(cur, n->wf[l], b, kWidth, dst, nullptr, count, H, W, s)));
+            else
+                CKC((conv<32, 32, kModeReluBf16>(cur, n->wf[l], b, kWidth, dst, nullptr, count, H, W, s)));
+            cur = dst;
+        }
+    }
+    return ADMM_OK;
+}
+
+// loss, gradients into n->grads (zeroed first)
+int backward(admm_cnn_s* n, int count, int H, int W, const float* target, const float* chan_w, cudaStream_t s) {
+    const long long npx = (long long)count * H * W;
+    CKC(cudaMemsetAsync(n->loss, 0, sizeof(double), s));
+    CKC(cudaMemsetAsync(n->grads, 0, param_count() * sizeof(float), s));
+    const float4 cw = make_float4(chan_w[0], chan_w[1], chan_w[2], chan_w[3]);
+    cnn_loss_kernel<<<(unsigned)((npx + 255) / 256), 256, 0, s>>>(n->out, target, cw, n->gout, n->loss, npx);
+    ++g_cnn_launches;
+    CKC(cudaGetLastError());
+    const bf16* g = n->gout;                        // gradient in the output of layer l
+    for (int l = kLayers - 1; l >= 0; --l) {
+        float* dw = n->grads + param_offset(l);
+        float* db = dw + (long long)layer_cout(l) * layer_cin(l) * 9;
+        const bf16* a_in = l == 0 ? n->a0 : n->act[l - 1];
+        if (l == kLayers - 1)
+            CKC((wgrad<32, 16>(a_in, g, dw, db, kWidth, kOut, count, H, W, n->sms, s)));
+        else if (l == 0)
+            CKC((wgrad<16, 32>(a_in, g, dw, db, kIn, kWidth, count, H, W, n->sms, s)));
+        else
+            CKC((wgrad<32, 32>(a_in, g, dw, db, kWidth, kWidth, count, H, W, n->sms, s)));
+        if (l == 0) break;
+        bf16* gnext = n->gbuf[l & 1];
+        if (l == kLayers - 1)
+            CKC((conv<16, 32, kModeGateBf16>(g, n->wb[l], nullptr, kWidth, gnext, a_in, count, H, W, s)));
+        else
+            CKC((conv<32, 32, kModeGateBf16>(g, n->wb[l], nullptr, kWidth, gnext, a_in, count, H, W, s)));
+        g = gnext;
+    }
+    return ADMM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+long long admm_cnn_param_count(void) { return param_count(); }
+
+long long admm_cnn_launches(void) {
+    std::lock_guard<std::mutex> lk(g_cnn_mutex);
+    return g_cnn_launches;
+}
+
+void admm_cnn_destroy(admm_cnn_t net) {
+    if (!net) return;
+    for (void* p : net->allocs) cudaFree(p);
+    if (net->h_loss) cudaFreeHost(net->h_loss);
+    delete net;
+}
+
+int admm_cnn_create(admm_cnn_t* out, long long max_pixels, int training) {
+    if (!out || max_pixels <= 0) return ADMM_EINVAL;
+    *out = nullptr;
+    std::lock_guard<std::mutex> lk(g_cnn_mutex);
+    admm_cnn_s* n = new (std::nothrow) admm_cnn_s();
+    if (!n) return ADMM_ENOMEM;
+    int rc = ADMM_OK;
+    auto bail = [&](int r) {
+        admm_cnn_destroy(n);
+        return r;
+    };
+    if (cudaGetDevice(&n->device) != cudaSuccess) return bail(ADMM_ECUDA);
+    cudaDeviceGetAttribute(&n->sms, cudaDevAttrMultiProcessorCount, n->device);
+    n->max_px = max_pixels;
+    n->training = training != 0;
+    const long long P = param_count();
+    const size_t px = (size_t)max_pixels;
+    if ((rc = dalloc(n, &n->params, P)) || (rc = dalloc(n, &n->a0, px * 16)) || (rc = dalloc(n, &n->out, px * 4)))
+        return bail(rc);
+    for (int l = 0; l < kLayers; ++l) {
+        if ((rc = dalloc(n, &n->wf[l], (size_t)9 * layer_coutp(l) * layer_cinp(l)))) return bail(rc);
+        if (l > 0 && (rc = dalloc(n, &n->wb[l], (size_t)9 * layer_cinp(l) * pad16(layer_cout(l))))) return bail(rc);
+    }
+    const int nact = n->training ? kLayers - 1 : 2;
+    for (int l = 0; l < nact; ++l)
+        if ((rc = dalloc(n, &n->act[l], px * kWidth))) return bail(rc);
+    if (n->training) {
+        if ((rc = dalloc(n, &n->grads, P)) || (rc = dalloc(n, &n->m, P)) || (rc = dalloc(n, &n->v, P)) ||
+            (rc = dalloc(n, &n->gbuf[0], px * kWidth)) || (rc = dalloc(n, &n->gbuf[1], px * kWidth)) ||
+            (rc = dalloc(n, &n->gout, px * 16)) || (rc = dalloc(n, &n->loss, 1)))
+            return bail(rc);
+        if (cudaHostAlloc(&n->h_loss, sizeof(double), cudaHostAllocDefault) != cudaSuccess) return bail(ADMM_ENOMEM);
+    }
+    if (cudaMemset(n->params, 0, P * sizeof(float)) != cudaSuccess) return bail(ADMM_ECUDA);
+    if (pack_all(n, nullptr) != ADMM_OK || cudaDeviceSynchronize() != cudaSuccess) return bail(ADMM_ECUDA);
+    *out = n;
+    return ADMM_OK;
+}
+
+int admm_cnn_set_params(admm_cnn_t net, const float* params) {
+    if (!net || !params) return ADMM_EINVAL;
+    std::lock_guard<std::mutex> lk(g_cnn_mutex);
+    const long long P = param_count();
+    CKC(cudaMemcpy(net->params, params, P * sizeof(float), cudaMemcpyDefault));
+    if (net->training) {
+        CKC(cudaMemset(net->m, 0, P * sizeof(float)));
+        CKC(cudaMemset(net->v, 0, P * sizeof(float)));
+        net->adam_t = 0;
+    }
+    const int rc = pack_all(net, nullptr);
+    if (rc != ADMM_OK) return rc;
+    CKC(cudaDeviceSynchronize());
+    return ADMM_OK;
+}
+
+int admm_cnn_get_params(admm_cnn_t net, float* params) {
+    if (!net || !params) return ADMM_EINVAL;
+    std::lock_guard<std::mutex> lk(g_cnn_mutex);
+    CKC(cudaMemcpy(params, net->params, param_count() * sizeof(float), cudaMemcpyDefault));
+    return ADMM_OK;
+}
+
+int admm_cnn_forward(admm_cnn_t net, int count, int H, int W, const float* ybar, const uint8_t* mask, float* out,
+                     void* stream) {
+    if (!net || !ybar || !mask || !out) return ADMM_EINVAL;
+    std::lock_guard<std::mutex> lk(g_cnn_mutex);
+    int rc = check_shape(net, count, H, W);
+    if (rc != ADMM_OK) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if ((rc = forward(net, count, H, W, ybar, mask, false, s)) != ADMM_OK) return rc;
+    CKC(cudaMemcpyAsync(out, net->out, (size_t)count * H * W * 4 * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    return ADMM_OK;
+}
+
+int admm_cnn_gradients(admm_cnn_t net, int count, int H, int W, const float* ybar, const uint8_t* mask,
+                       const float* target, const float* chan_w, float* grads, double* loss, void* stream) {
+    if (!net || !ybar || !mask || !target || !chan_w || !grads || !net->training) return ADMM_EINVAL;
+    std::lock_guard<std::mutex> lk(g_cnn_mutex);
+    int rc = check_shape(net, count, H, W);
+    if (rc != ADMM_OK) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if ((rc = forward(net, count, H, W, ybar, mask, true, s)) != ADMM_OK) return rc;
+    if ((rc = backward(net, count, H, W, target, chan_w, s)) != ADMM_OK) return rc;
+    CKC(cudaMemcpyAsync(grads, net->grads, param_count() * sizeof(float), cudaMemcpyDefault, s));
+    CKC(cudaMemcpyAsync(net->h_loss, net->loss, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CKC(cudaStreamSynchronize(s));
+    if (loss) *loss = *net->h_loss;
+    return ADMM_OK;
+}
+
+int admm_cnn_train_step(admm_cnn_t net, int count, int H, int W, const float* ybar, const uint8_t* mask,
+                        const float* target, const float* chan_w, float lr, double* loss, void* stream) {
+    if (!net || !ybar || !mask || !target || !chan_w || !net->training || !(lr > 0.f)) return ADMM_EINVAL;
+    std::lock_guard<std::mutex> lk(g_cnn_mutex);
+    int rc = check_shape(net, count, H, W);
+    if (rc != ADMM_OK) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if ((rc = forward(net, count, H, W, ybar, mask, true, s)) != ADMM_OK) return rc;
+    if ((rc = backward(net, count, H, W, target, chan_w, s)) != ADMM_OK) return rc;
+    net->adam_t += 1;
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = (float)(1.0 - std::pow(0.9, (double)net->adam_t));
+    const float c2 = (float)(1.0 - std::pow(0.999, (double)net->adam_t));
+    const long long P = param_count();
+    adam_kernel<<<(unsigned)((P + 255) / 256), 256, 0, s>>>(net->params, net->grads, net->m, net->v, P, lr, b1, b2,
+                                                            1e-8f, c1, c2);
+    ++g_cnn_launches;
+    CKC(cudaGetLastError());
+    if ((rc = pack_all(net, s)) != ADMM_OK) return rc;
+    if (loss) {
+        CKC(cudaMemcpyAsync(net->h_loss, net->loss, sizeof(double), cudaMemcpyDeviceToHost, s));
+        CKC(cudaStreamSynchronize(s));
+        *loss = *net->h_loss;
+    }
+    return ADMM_OK;
+}
+
+int admm_cnn_predict_start(admm_cnn_t net, int count, int H, int W, const float* ybar, const uint8_t* mask,
+                           const float* scales, float* x0, float* d0, void* stream) {
+    if (!net || !ybar || !mask || !scales || !x0 || !d0) return ADMM_EINVAL;
+    std::lock_guard<std::mutex> lk(g_cnn_mutex);
+    int rc = check_shape(net, count, H, W);
+    if (rc != ADMM_OK) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if ((rc = forward(net, count, H, W, ybar, mask, false, s)) != ADMM_OK) return rc;
+    const long long n = (long long)H * W, npx = n * count;
+    split_start_kernel<<<(unsigned)((npx + 255) / 256), 256, 0, s>>>(net->out, scales[0], scales[1], scales[2], x0,
+                                                                     d0, n, npx);
+    ++g_cnn_launches;
+    CKC(cudaGetLastError());
+    return ADMM_OK;
+}
+
+}  // extern "C"

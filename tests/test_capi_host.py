@@ -9,7 +9,8 @@ import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADER = os.path.join(ROOT, "include", "admm_deconv.h")
+HEADERS = [os.path.join(ROOT, "include", f) for f in sorted(os.listdir(os.path.join(ROOT, "include")))
+           if f.endswith(".h")]
 
 
 @pytest.fixture(scope="module")
@@ -21,7 +22,7 @@ def ad():
 
 
 def _declared_functions():
-    txt = open(HEADER).read()
+    txt = "".join(open(h).read() for h in HEADERS)
     txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
     return sorted(set(re.findall(r"ADMM_API\s+[\w\s\*]+?\b(admm_\w+)\s*\(", txt)))
 
@@ -29,7 +30,8 @@ def _declared_functions():
 def test_header_declares_the_boundary():
     names = _declared_functions()
     for required in ("admm_deconv_plan", "admm_deconv_solve", "admm_deconv_solve_batch",
-                     "admm_deconv_destroy", "admm_strerror"):
+                     "admm_deconv_destroy", "admm_strerror", "admm_deconv_warm_start",
+                     "admm_cnn_create", "admm_cnn_train_step", "admm_cnn_predict_start"):
         assert required in names
 
 
@@ -89,3 +91,18 @@ def test_set_option_validates(ad):
     assert ad.lib.admm_deconv_set_option(ad.ADMM_OPT_MAX_SLOTS, -1) == ad.ADMM_EINVAL
     assert ad.lib.admm_deconv_set_option(99, 1) == ad.ADMM_EINVAL
     assert ad.lib.admm_deconv_set_option(ad.ADMM_OPT_MAX_SLOTS, 0) == ad.ADMM_OK
+
+
+def test_cnn_parameter_count_matches_the_oracle_network(ad):
+    import oracle.cnn as C
+    n = sum(co * ci * 9 + co for co, ci in C.layer_shapes())
+    assert ad.Cnn.param_count() == n == 57252
+
+
+def test_cnn_null_arguments(ad):
+    lib = ad.lib
+    assert lib.admm_cnn_create(None, 1, 0) == ad.ADMM_EINVAL
+    assert lib.admm_cnn_set_params(None, None) == ad.ADMM_EINVAL
+    assert lib.admm_cnn_forward(None, 1, 16, 16, None, None, None, None) == ad.ADMM_EINVAL
+    assert lib.admm_deconv_warm_start(None, None, None, None) == ad.ADMM_EINVAL
+    lib.admm_cnn_destroy(None)
