@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--no-secondary", action="store_true", help="skip the frame-prior workload")
     ap.add_argument("--frame-only", action="store_true", help="only the frame-prior workload (profiler captures)")
     ap.add_argument("--uneven-only", action="store_true", help="only the batched uneven workload")
+    ap.add_argument("--warm-only", action="store_true", help="only the learned warm-start comparison")
     ap.add_argument("--steady-only", action="store_true",
                     help="only the fixed-iteration pass with every slot busy (for profiler captures)")
     return ap.parse_args()
@@ -267,6 +268,42 @@ def uneven_secondary(ad, torch, stream, count=UNEVEN_COUNT):
     }
 
 
+CNN_FLOP_PER_PX = 2 * 9 * (2 * 32 + 6 * 32 * 32 + 32 * 4)   # eight 3x3 convolutions
+
+
+def warm_secondary(ad, torch, stream, count=32):
+    """Learned warm start against the cold start on unseen 512^2 problems
+    (piecewise-constant law, 9 x 9 box, valid region, BSNR 40, lambda 1e-3),
+    both to rel-x < 1e-5; and the network's forward throughput on the tensor
+    cores (16 images of 512^2, FLOPs of the eight convolutions)."""
+    import paper_1210_2687_gb300.warmstart as WS
+    params, scales, meta = WS.load()
+    ev = WS.evaluate(params, scales, count=count, seed=1)
+    n = 16
+    net = ad.Cnn(n * 512 * 512)
+    net.set_params(params)
+    g = np.random.default_rng(0)
+    y = torch.from_numpy(g.uniform(size=(n, 512, 512)).astype(np.float32)).cuda()
+    m = torch.ones((n, 512, 512), dtype=torch.uint8, device="cuda")
+    out = torch.empty((n, 512, 512, 4), dtype=torch.float32, device="cuda")
+    for _ in range(3):
+        net.forward(y, m, out, stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 10
+    e0.record(stream)
+    for _ in range(reps):
+        net.forward(y, m, out, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    sec = e0.elapsed_time(e1) * 1e-3 / reps
+    tflops = CNN_FLOP_PER_PX * n * 512 * 512 / sec / 1e12
+    net.close()
+    ev["cnn_forward"] = {"images": n, "size": 512, "ms": sec * 1e3, "tflops": tflops,
+                         "note": "mma.sync BF16 m16n8k16, FP32 accumulate; 9 launches per forward"}
+    ev["trained"] = {k: meta[k] for k in ("count", "epochs", "lr", "train_s", "steps") if k in meta}
+    return ev
+
+
 def cpu_baseline_oracle(probs, seconds=12.0):
     """The FP64 oracle as it stands on one 512^2 problem of the workload,
     iterating until about `seconds` of CPU time; iterations per second."""
@@ -327,6 +364,9 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     if args.frame_only:
         print(json.dumps({"secondary": frame_secondary(ad, torch, torch.cuda.current_stream())}), flush=True)
+        return
+    if args.warm_only:
+        print(json.dumps({"warm_start": warm_secondary(ad, torch, torch.cuda.current_stream())}), flush=True)
         return
     if args.uneven_only:
         print(json.dumps({"uneven_batch": uneven_secondary(ad, torch, torch.cuda.current_stream())}), flush=True)
@@ -468,6 +508,7 @@ def run_ours(args):
     if rank == 0 and not args.no_secondary:
         secondary = frame_secondary(ad, torch, stream)
         secondary["uneven_batch"] = uneven_secondary(ad, torch, stream)
+        secondary["warm_start"] = warm_secondary(ad, torch, stream)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -123,9 +123,11 @@ def test_restart_from_own_solution_stops_at_once(ad):
     within a few iterations of the first one where it is evaluated."""
     import torch
     p = S.config2_problem(3, "gauss", 40, size=256)
+    lam = 1e-3                      # a weight at which rel-x < 1e-5 means close to the fixed point
+    mu1, mu2 = S.default_mu(lam)
     y = torch.from_numpy(p.ybar.astype(np.float32)).cuda()
     m = torch.from_numpy(p.mask).cuda()
-    plan = ad.Plan(256, 256, p.psf, p.lam, p.mu1, p.mu2, "tv", stop="rel_x", tol=1e-5, max_iters=5000,
+    plan = ad.Plan(256, 256, p.psf, lam, mu1, mu2, "tv", stop="rel_x", tol=1e-5, max_iters=5000,
                    check_every=1)
     x = torch.empty((256, 256), dtype=torch.float32, device="cuda")
     r = ad.solve(plan, y, m, x)
