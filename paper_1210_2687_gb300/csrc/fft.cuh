@@ -85,10 +85,47 @@ template <int DIR> __device__ __forceinline__ void dft8(float2 (&v)[8]) {
     v[3] = e3 + o3; v[7] = e3 - o3;
 }
 
-// twiddle exp(DIR * 2 pi i * idx / N) from the forward table tw[i] = exp(-2 pi i i / N)
+// twiddle tw[idx] of a forward table, conjugated for the inverse direction
 template <int DIR> __device__ __forceinline__ float2 twid(const float2* tw, int idx) {
     float2 w = tw[idx];
     return DIR < 0 ? w : conjf2(w);
+}
+
+// Per-pass twiddle table of a length-N transform. The radix-8 pass p runs
+// with stride Ns = R0 8^p; its entries off(p) + (r - 1) Ns + k hold
+// exp(-2 pi i r k / (8 Ns)) for r = 1..7, k < Ns, so the lanes of a warp
+// (consecutive k = t mod Ns) read consecutive entries: no bank conflicts,
+// where indexing one length-N table by r k N / (8 Ns) put up to eight lanes
+// on one bank. At most N entries.
+template <int N> struct TwiddleLayout {
+    __host__ __device__ static constexpr int off(int p) {
+        int o = 0, ns = FftShape<N>::R0;
+        for (int q = 0; q < p; ++q) {
+            o += 7 * ns;
+            ns *= 8;
+        }
+        return o;
+    }
+    static constexpr int SIZE = off(FftShape<N>::NP8);
+    static_assert(SIZE <= N, "table fits a length-N buffer");
+};
+
+// Fill the per-pass table from the 2048-entry table exp(-2 pi i k / 2048)
+// (threads tid of nthr cooperate; the caller synchronises afterwards).
+template <int N>
+__device__ __forceinline__ void load_twiddles(float2* dst, const float2* __restrict__ tw2048, int tid, int nthr) {
+    using S = FftShape<N>;
+    int ns = S::R0, o = 0;
+#pragma unroll
+    for (int p = 0; p < S::NP8; ++p) {
+        const int step = N / (ns * 8);
+        for (int e = tid; e < 7 * ns; e += nthr) {
+            const int r = e / ns + 1, k = e - (r - 1) * ns;
+            dst[o + e] = tw2048[r * k * step * (2048 / N)];
+        }
+        o += 7 * ns;
+        ns *= 8;
+    }
 }
 
 // One Stockham pass on the registers of thread t (elements t + m N/8 as
@@ -98,11 +135,11 @@ __device__ __forceinline__ void stockham_compute(float2 (&v)[8], int t, int Ns, 
                                                  int (&oidx)[8]) {
     constexpr int Q = N / 8;
     if constexpr (R == 8) {
+        // tw: this pass's block of the per-pass table (TwiddleLayout)
         const int j = t, k = j & (Ns - 1);
         if (Ns > 1) {
-            const int step = N / (Ns * 8);
 #pragma unroll
-            for (int r = 1; r < 8; ++r) v[r] = cmul(v[r], twid<DIR>(tw, r * k * step));
+            for (int r = 1; r < 8; ++r) v[r] = cmul(v[r], twid<DIR>(tw, (r - 1) * Ns + k));
         }
         dft8<DIR>(v);
         const int base = (j - k) * 8 + k;
@@ -111,12 +148,7 @@ __device__ __forceinline__ void stockham_compute(float2 (&v)[8], int t, int Ns, 
     } else if constexpr (R == 4) {
 #pragma unroll
         for (int b = 0; b < 2; ++b) {
-            const int j = t + b * Q, k = j & (Ns - 1);
-            if (Ns > 1) {
-                const int step = N / (Ns * 4);
-#pragma unroll
-                for (int q = 1; q < 4; ++q) v[2 * q + b] = cmul(v[2 * q + b], twid<DIR>(tw, q * k * step));
-            }
+            const int j = t + b * Q, k = j & (Ns - 1);   // leading pass only: Ns = 1, no twiddles
             dft4<DIR>(v[b], v[2 + b], v[4 + b], v[6 + b]);
             const int base = (j - k) * 4 + k;
 #pragma unroll
@@ -126,8 +158,7 @@ __device__ __forceinline__ void stockham_compute(float2 (&v)[8], int t, int Ns, 
         static_assert(R == 2, "radix");
 #pragma unroll
         for (int s = 0; s < 4; ++s) {
-            const int j = t + s * Q, k = j & (Ns - 1);
-            if (Ns > 1) v[s + 4] = cmul(v[s + 4], twid<DIR>(tw, k * (N / (Ns * 2))));
+            const int j = t + s * Q, k = j & (Ns - 1);   // leading pass only: Ns = 1, no twiddles
             dft2<DIR>(v[s], v[s + 4]);
             const int base = (j - k) * 2 + k;
             oidx[s] = base;
@@ -154,7 +185,7 @@ __device__ __forceinline__ void group_sync(int g) {
 // Full length-N transform for a group of N/8 threads.
 //   v    : in/out registers, element t + m N/8 in v[m] (natural order both ways)
 //   buf  : the group's shared buffer, >= N float2 (swizzled positions)
-//   tw   : forward twiddle table of length N (shared or global)
+//   tw   : per-pass twiddle table of length N (TwiddleLayout, load_twiddles)
 //   g    : index of the group in the block (threads g*N/8 .. g*N/8 + N/8 - 1)
 // Only the threads of the group synchronise (group_sync); the other groups of
 // the block run independently. Block-wide ordering is the caller's business.
@@ -177,7 +208,7 @@ __device__ __forceinline__ void fft_group(float2 (&v)[8], float2* buf, const flo
         group_sync<N>(g);
 #pragma unroll
         for (int m = 0; m < 8; ++m) v[m] = buf[swz(t + m * Q)];
-        stockham_compute<N, 8, DIR>(v, t, Ns, tw, oidx);
+        stockham_compute<N, 8, DIR>(v, t, Ns, tw + TwiddleLayout<N>::off(p), oidx);
         Ns *= 8;
     }
     // after the last radix-8 pass (Ns = N/8 before it) oidx[m] = t + m N/8:
@@ -216,10 +247,10 @@ __device__ __forceinline__ void fft_group2(float2 (&v)[8], float2 (&u)[8], float
         // shared twiddles: exp(DIR 2 pi i r k / (8 Ns)), k = t mod Ns
         const int k = t & (Ns - 1);
         if (Ns > 1) {
-            const int step = N / (Ns * 8);
+            const float2* twp = tw + TwiddleLayout<N>::off(p);
 #pragma unroll
             for (int r = 1; r < 8; ++r) {
-                const float2 w = twid<DIR>(tw, r * k * step);
+                const float2 w = twid<DIR>(twp, (r - 1) * Ns + k);
                 v[r] = cmul(v[r], w);
                 u[r] = cmul(u[r], w);
             }

@@ -57,7 +57,7 @@ haar_row_inverse(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp
     float2* tw = buf + G * ROW;
     double* red = reinterpret_cast<double*>(tw + W);
     const int tid = threadIdx.x, g = tid / FT, t = tid % FT;
-    for (int i = tid; i < W; i += kThreads) tw[i] = tw_g[i * (2048 / W)];
+    load_twiddles<W>(tw, tw_g, tid, kThreads);
     __syncthreads();
     const int q = blockIdx.x * G + g;
     float2 v[8];
@@ -320,7 +320,7 @@ haar_row_forward(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp
     float2* buf = smem;
     float2* tw = buf + G * ROW;
     const int tid = threadIdx.x, g = tid / FT, t = tid % FT;
-    for (int i = tid; i < W; i += kThreads) tw[i] = tw_g[i * (2048 / W)];
+    load_twiddles<W>(tw, tw_g, tid, kThreads);
     __syncthreads();
     const int q = blockIdx.x * G + g;
     const size_t n = (size_t)H * W;

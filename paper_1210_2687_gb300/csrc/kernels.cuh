@@ -314,7 +314,7 @@ col_phase(const ProbDesc* __restrict__ probs, SlotTable sl, int Wc, int Wp, cons
         cp_async16(stage + tile_slot<CB>(r, c), src + (size_t)r * Wp + c0 + c);
     }
     cp_async_commit();
-    for (int i = tid; i < H; i += kThreads) tw[i] = tw_g[i * (2048 / H)];
+    load_twiddles<H>(tw, tw_g, tid, kThreads);
     const int g = tid / C::FT, t = tid % C::FT;
     float2* bz = xb + (2 * g) * C::SIG;
     float2* bw = xb + (2 * g + 1) * C::SIG;
@@ -668,7 +668,7 @@ row_phase_tv(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp, co
     cp_async_commit();
 #pragma unroll
     for (int i = 0; i < D; ++i) issue(i);
-    for (int i = tid; i < W; i += NT) tw[i] = tw_g[i * (2048 / W)];
+    load_twiddles<W>(tw, tw_g, tid, NT);
     cp_async_wait<D>();          // the spectra have landed
     __syncthreads();
     const int g = tid / C::FT, t = tid % C::FT;
@@ -836,7 +836,7 @@ finalize_x(const ProbDesc* __restrict__ probs, float* const* __restrict__ xout, 
     float2* tw = buf + G * ROW;
     const ProbDesc& P = probs[blockIdx.y];
     const int tid = threadIdx.x, g = tid / FT, t = tid % FT;
-    for (int i = tid; i < W; i += kThreads) tw[i] = tw_g[i * (2048 / W)];
+    load_twiddles<W>(tw, tw_g, tid, kThreads);
     __syncthreads();
     const int q = blockIdx.x * G + g;
     float2 v[8];
@@ -867,7 +867,7 @@ warm_rows(const float* __restrict__ x0, float4* __restrict__ Sb, int H, int Wp, 
     float2* buf = smem;
     float2* tw = buf + G * ROW;
     const int tid = threadIdx.x, g = tid / FT, t = tid % FT;
-    for (int i = tid; i < W; i += kThreads) tw[i] = tw_g[i * (2048 / W)];
+    load_twiddles<W>(tw, tw_g, tid, kThreads);
     __syncthreads();
     const int q = blockIdx.x * G + g;
     float2 v[8];
