@@ -722,10 +722,11 @@ row_phase_tv(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp, co
                 const float gh = xr - x, gv = xd - x;
                 const size_t pix = (size_t)q * W + c;
                 const float2 dd = cold ? make_float2(0.f, 0.f) : *reinterpret_cast<const float2*>(slot + 2 * c);
-                // u2 = v-soft(D_i x - d2, lambda/mu2)  (Alg. 3 line 10, 0/0 = 0)
+                // u2 = v-soft(D_i x - d2, lambda/mu2)  (Alg. 3 line 10, 0/0 = 0):
+                // the scale max(0, 1 - tau / |s|), with one reciprocal square
+                // root (|s| = 0 gives -inf inside the max, so 0)
                 const float sh = gh - dd.x, sv = gv - dd.y;
-                const float nrm = sqrtf(fmaf(sh, sh, sv * sv));
-                const float sc = nrm > tau ? (nrm - tau) / nrm : 0.f;
+                const float sc = fmaxf(0.f, fmaf(-tau, rsqrtf(fmaf(sh, sh, sv * sv)), 1.f));
                 const float uh = sc * sh, uv = sc * sv;
                 // d2 <- d2 - (D_i x - u2)  (Alg. 3 line 11)
                 const float nh = uh - sh, nv = uv - sv;
@@ -767,8 +768,7 @@ row_phase_tv(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp, co
                 const float2 dd = cold ? make_float2(0.f, 0.f)
                                         : *reinterpret_cast<const float2*>(slot + 5 * W + 2 * wid);
                 const float sh = (xhr - xh) - dd.x, sv = (xl_nb_dn - xh) - dd.y;
-                const float nrm = sqrtf(fmaf(sh, sh, sv * sv));
-                const float sc = nrm > tau ? (nrm - tau) / nrm : 0.f;
+                const float sc = fmaxf(0.f, fmaf(-tau, rsqrtf(fmaf(sh, sh, sv * sv)), 1.f));
                 dh_halo = 2.f * sc * sh - sh;
             }
         }
