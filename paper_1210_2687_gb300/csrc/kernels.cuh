@@ -673,14 +673,28 @@ row_phase_tv(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp, co
     __syncthreads();
     const int g = tid / C::FT, t = tid % C::FT;
 
-    // (1) x + i A x on buffer rows 0..R+1 = image rows r0-1..r0+R: inverse row DFTs
-    for (int i = g; i < R + 2; i += C::G) {
+    // (1) x + i A x on buffer rows 0..R+1 = image rows r0-1..r0+R: inverse row
+    // DFTs, two rows per group at a time (interleaved: twice the independent
+    // work between the group's barriers)
+    for (int i = g; i < R + 2; i += 2 * C::G) {
         float2* row = buf + i * C::ROW;
         float2 v[8];
         load_row_xax<W>(v, reinterpret_cast<const float4*>(row), t);
-        fft_group<W, 1>(v, row, tw, t, g);
+        if (i + C::G < R + 2) {
+            float2* row2 = row + C::G * C::ROW;
+            float2 u[8];
+            load_row_xax<W>(u, reinterpret_cast<const float4*>(row2), t);
+            fft_group2<W, 1>(v, u, row, row2, tw, t, g);
 #pragma unroll
-        for (int m = 0; m < 8; ++m) row[swz(t + m * C::FT)] = v[m];
+            for (int m = 0; m < 8; ++m) {
+                row[swz(t + m * C::FT)] = v[m];
+                row2[swz(t + m * C::FT)] = u[m];
+            }
+        } else {
+            fft_group<W, 1>(v, row, tw, t, g);
+#pragma unroll
+            for (int m = 0; m < 8; ++m) row[swz(t + m * C::FT)] = v[m];
+        }
     }
     __syncthreads();
     // x of the neighbouring warps' boundary columns, one row per lane
@@ -804,17 +818,34 @@ row_phase_tv(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp, co
         block_reduce_comp<NT>(acc, reinterpret_cast<float*>(red), part);
     }
 
-    // (4) forward row DFTs of p = zeta1 + i w on rows 1..R and split
-    for (int i = 1 + g; i <= R; i += C::G) {
+    // (4) forward row DFTs of p = zeta1 + i w on rows 1..R and split, two
+    // rows per group at a time
+    for (int i = 1 + g; i <= R; i += 2 * C::G) {
         float2* row = buf + i * C::ROW;
         float2 v[8];
 #pragma unroll
         for (int m = 0; m < 8; ++m) v[m] = row[swz(t + m * C::FT)];
-        fft_group<W, -1>(v, row, tw, t, g);
+        if (i + C::G <= R) {
+            float2* row2 = row + C::G * C::ROW;
+            float2 u[8];
 #pragma unroll
-        for (int m = 0; m < 8; ++m) row[swz(t + m * C::FT)] = v[m];
-        group_sync<W>(g);            // the split reads this group's row only
-        store_split<W>(P.Sb + (size_t)(r0 - 1 + i) * Wp, row, t);
+            for (int m = 0; m < 8; ++m) u[m] = row2[swz(t + m * C::FT)];
+            fft_group2<W, -1>(v, u, row, row2, tw, t, g);
+#pragma unroll
+            for (int m = 0; m < 8; ++m) {
+                row[swz(t + m * C::FT)] = v[m];
+                row2[swz(t + m * C::FT)] = u[m];
+            }
+            group_sync<W>(g);        // the split reads this group's rows only
+            store_split<W>(P.Sb + (size_t)(r0 - 1 + i) * Wp, row, t);
+            store_split<W>(P.Sb + (size_t)(r0 - 1 + i + C::G) * Wp, row2, t);
+        } else {
+            fft_group<W, -1>(v, row, tw, t, g);
+#pragma unroll
+            for (int m = 0; m < 8; ++m) row[swz(t + m * C::FT)] = v[m];
+            group_sync<W>(g);
+            store_split<W>(P.Sb + (size_t)(r0 - 1 + i) * Wp, row, t);
+        }
     }
 
     // (5) the last CTA of the problem evaluates the stop rule; done last so
