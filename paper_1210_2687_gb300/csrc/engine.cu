@@ -755,7 +755,7 @@ static int solve_all(DeviceCtx* ctx, const std::vector<std::vector<int>>& classe
             CK(chunk_graph(ctx, live, chunk, &exec));
             CK(cudaGraphLaunch(exec, s));
             for (GroupRun& g : live) {
-                g_launches += (long long)chunk * g.L.n * (g.tv ? 2 : 4);
+                g_launches += (long long)chunk * g.L.n * (g.tv ? 2 : 5);
                 g.launched += chunk;
             }
         } else {
@@ -778,7 +778,7 @@ static int solve_all(DeviceCtx* ctx, const std::vector<std::vector<int>>& classe
                         } else {
                             CK(launch_haar_iteration_rows(g.W, g.H, g.Wp, dl, sl, g.L.slots[l], g.levels, ctx->tw,
                                                           nact, s));
-                            g_launches += 3;
+                            g_launches += 4;
                         }
                         if (prof) {
                             int r = prof_event(nev++, s);

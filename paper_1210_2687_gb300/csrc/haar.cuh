@@ -6,11 +6,12 @@
 //   haar_row_inverse   inverse row DFTs -> x, A x; mask-decoupled prox and
 //                      dual update (eq. prox_g_1_uBC, Alg. 2 lines 6-7, j = 1);
 //                      writes x and zeta1 = u1 + d1 to two scratch planes
-//   haar_tile          32 x 32 output tile with a halo of 2^L - 1 pixels:
-//                      analysis c = P x (a-trous Haar), u2 = soft(c - d2,
-//                      lambda/mu2) (eq. soft), d2 <- d2 - (c - u2), zeta2 =
-//                      u2 + d2, then w = gamma P^T zeta2 (the x-step right-hand
-//                      side of eq. invAnalysis divided by mu1) on the tile
+//   haar_analysis      32 x 32 tile: analysis c = P x (a-trous Haar), u2 =
+//                      soft(c - d2, lambda/mu2) (eq. soft), d2 <- d2 - (c - u2);
+//                      zeta2 = u2 + d2 replaces the previous d2 in place;
+//                      the last CTA of the problem finishes the iteration
+//   haar_synthesis     32 x 32 tile: w = gamma P^T zeta2 (the x-step right-
+//                      hand side of eq. invAnalysis divided by mu1)
 //   haar_row_forward   forward row DFT of zeta1 + i w, split into half spectra
 //
 // P is the undecimated Haar frame with periodic wrap: level j filters with
@@ -19,9 +20,11 @@
 // (3 L + 1 bands, P^T P = I). Band order per level: rows low / columns high,
 // rows high / columns low, rows high / columns high; final band low-low.
 //
-// The tile recomputes the coefficients of its halo from x and the previous
-// iteration's d2, so d2 is double-buffered by iteration parity (a CTA never
-// reads a d2 value a neighbouring CTA has already replaced).
+// d2 lives in two buffers by iteration parity: iteration k reads the previous
+// d2 from buffer (k+1)&1 and writes the new one to buffer k&1. Each
+// coefficient is read and replaced by the thread that owns it, so the
+// analysis can leave zeta2 in the buffer it has just read; the synthesis
+// (a separate launch) reads zeta2 there with its halo.
 #pragma once
 #include <cuda_runtime.h>
 #include "kernels.cuh"
@@ -103,38 +106,37 @@ haar_row_inverse(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp
     }
 }
 
-// ---------------------------------------------------------------------------
-// frame analysis, soft threshold, dual update and adjoint synthesis on a tile
-// ---------------------------------------------------------------------------
-template <int L>
-struct HaarTileCfg {
-    static constexpr int T = kHaarTile;
-    static constexpr int HALO = (1 << L) - 1;
-    static constexpr int XD = T + 2 * HALO;       // side of the x / approximation arrays
-    __host__ __device__ static constexpr int band_side(int lvl) { return T + 2 * (1 << lvl) - 1; }
-    __host__ __device__ static constexpr int zoff(int lvl) {
-        int o = 0;
-        for (int i = 0; i < lvl; ++i) o += 3 * band_side(i) * band_side(i);
-        return o;
-    }
-    static constexpr int ZTOT = zoff(L);
-    static constexpr int LLD = T + HALO;          // side of the low-low band region
-    // the reduction scratch follows the float arrays: round up to 8 bytes
-    static constexpr int RED_OFF = (2 * XD * XD + ZTOT + LLD * LLD + 1) & ~1;   // in floats
-    static_assert((RED_OFF * sizeof(float)) % sizeof(double) == 0, "double alignment");
-    static constexpr size_t SMEM = (size_t)RED_OFF * sizeof(float) + 8 * kNumPartials * sizeof(double);
-};
-
 __device__ __forceinline__ float soft_thresh(float v, float t) {
     const float a = fabsf(v) - t;
     return a > 0.f ? copysignf(a, v) : 0.f;
 }
 
+// ---------------------------------------------------------------------------
+// analysis c = P x on a T x T tile (a-trous Haar), soft threshold, dual
+// update. Every coefficient of the tile is owned by this CTA: the previous d2
+// is read and zeta2 = u2 + d2 written back in its place by the same thread,
+// the new d2 goes to the other buffer. a_{j+1}(r, c) averages a_j at
+// (r + {0, s}, c + {0, s}), so the tile needs x on [0, T + 2^L - 1)^2 only.
+// ---------------------------------------------------------------------------
+template <int L>
+struct HaarAnaCfg {
+    static constexpr int T = kHaarTile;
+    static constexpr int HALO = (1 << L) - 1;
+    static constexpr int XA = T + 16;              // stride (16-byte rows); x needs T + HALO columns
+    static constexpr int XR = T + HALO;            // rows of x
+    static_assert(HALO < 16, "halo fits the 16-column margin");
+    static constexpr int RED_OFF = (2 * XR * XA + 1) & ~1;   // floats, rounded to 8 bytes
+    static_assert((RED_OFF * sizeof(float)) % sizeof(double) == 0, "double alignment");
+    static constexpr size_t SMEM = (size_t)RED_OFF * sizeof(float) + 8 * kNumPartials * sizeof(double);
+};
+
 template <int L>
 __global__ void __launch_bounds__(kThreads)
-haar_tile(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W, int n_row_ctas, int* __restrict__ n_active) {
-    using C = HaarTileCfg<L>;
-    constexpr int T = C::T, HALO = C::HALO, XD = C::XD;
+haar_analysis(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W, int n_row_ctas,
+              int* __restrict__ n_active) {
+    using C = HaarAnaCfg<L>;
+    constexpr int T = C::T, XA = C::XA, XR = C::XR;
+    constexpr int NWARP = kThreads / 32;
     const int pi = sl.map[blockIdx.y];
     if (pi < 0) return;
     const ProbDesc& P = probs[pi];
@@ -144,145 +146,195 @@ haar_tile(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W, int n_
     const bool first = k == 1 && !P.warm;        // d2 = 0 (cold start: u0 = d0 = 0)
     const bool chk = is_check_iter(P, k), nobj = need_obj_iter(P, k);
     extern __shared__ __align__(16) float sm[];
-    float* A0 = sm;
-    float* A1 = A0 + XD * XD;
-    float* Z = A1 + XD * XD;                     // detail bands: d2 staged, then zeta2
-    float* ZLL = Z + C::ZTOT;                    // low-low band: d2 staged
+    float* Ain = sm;
+    float* Aout = sm + XR * XA;
     double* red = reinterpret_cast<double*>(sm + C::RED_OFF);
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int tiles_x = W / T;
     const int R0 = (blockIdx.x / tiles_x) * T, C0 = (blockIdx.x % tiles_x) * T;
     const size_t n = (size_t)H * W;
-    const float* __restrict__ xw = P.work;
-    float* __restrict__ ww = P.work + 2 * n;
-    const float* __restrict__ d2in = P.d2 + ((k + 1) & 1) * P.d2_stride;
+    float* __restrict__ d2io = P.d2 + ((k + 1) & 1) * P.d2_stride;   // previous d2 in, zeta2 out
     float* __restrict__ d2out = P.d2 + (k & 1) * P.d2_stride;
     const float tau = P.tau;
 
-    // Regions are visited two-dimensionally: warp w takes rows w, w + 8, ...
-    // and lane l columns l, l + 32, ... of the region, so positions come from
-    // counters rather than divisions, and the wrapped global row is computed
-    // once per row.
-    const int lane = tid & 31, warp = tid >> 5;
-    constexpr int NWARP = kThreads / 32;
-
-    // every input of the tile is requested at once (cp.async): x on
-    // [-HALO, T + HALO)^2 and the previous d2 of each band on the region where
-    // its zeta2 is needed (periodic wrap)
-    for (int rr = warp; rr < XD; rr += NWARP) {
-        const float* src = xw + (size_t)((R0 + rr - HALO) & (H - 1)) * W;
-        for (int cc = lane; cc < XD; cc += 32) cp_async4(A0 + rr * XD + cc, src + ((C0 + cc - HALO) & (W - 1)));
+    // x on [0, T + HALO) x [0, T + 16) with periodic wrap, 16-byte copies (the
+    // tile origin is a multiple of 32 columns); warp w takes rows w, w + 8, ...
+    constexpr int CH = XA / 4;
+    for (int e = tid; e < XR * CH; e += kThreads) {
+        const int rr = e / CH, ch = e - rr * CH;
+        const float* src = P.work + (size_t)((R0 + rr) & (H - 1)) * W + ((C0 + 4 * ch) & (W - 1));
+        cp_async16(Ain + rr * XA + 4 * ch, src);
     }
-    if (!first) {
+    cp_async_commit();
+    // thread (warp, lane) owns the tile pixels (warp + 8 i, lane), i < T / 8
+    constexpr int OWN = T / NWARP;
+    const size_t gp0 = (size_t)(R0 + warp) * W + (C0 + lane);
+    cp_async_wait<0>();
+    __syncthreads();
+
+    CompSum l1;
 #pragma unroll
-        for (int lvl = 0; lvl < L; ++lvl) {
-            const int BO = 2 * (1 << lvl) - 1, BD = T + 2 * (1 << lvl) - 1;
-            float* Zl = Z + C::zoff(lvl);
+    for (int lvl = 0; lvl < L; ++lvl) {
+        const int s = 1 << lvl;
+        // this level's previous d2 at the owned pixels, requested before the
+        // arithmetic that needs it
+        float dold[OWN][3];
 #pragma unroll
-            for (int j = 0; j < 3; ++j) {
-                const float* band = d2in + (size_t)(3 * lvl + j) * n;
-                for (int rr = warp; rr < BD; rr += NWARP) {
-                    const float* src = band + (size_t)((R0 + rr - BO) & (H - 1)) * W;
-                    for (int cc = lane; cc < BD; cc += 32)
-                        cp_async4(Zl + j * BD * BD + rr * BD + cc, src + ((C0 + cc - BO) & (W - 1)));
+        for (int i = 0; i < OWN; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+                dold[i][j] = first ? 0.f : d2io[(size_t)(3 * lvl + j) * n + gp0 + (size_t)(NWARP * i) * W];
+        const int D = T + (1 << L) - 2 * s;      // a_{lvl+1} is needed on [0, D)^2
+#pragma unroll
+        for (int i = 0; i * NWARP < D; ++i) {
+            const int rr = warp + NWARP * i;
+            if (rr >= D) break;
+#pragma unroll
+            for (int pass = 0; pass * 32 < D; ++pass) {
+                const int cc = lane + 32 * pass;
+                if (cc >= D) break;
+                const int i00 = rr * XA + cc;
+                const float a00 = Ain[i00], a01 = Ain[i00 + s];
+                const float a10 = Ain[i00 + s * XA], a11 = Ain[i00 + s * XA + s];
+                const float p0 = a00 + a01, m0 = a00 - a01, p1 = a10 + a11, m1 = a10 - a11;
+                Aout[i00] = 0.25f * (p0 + p1);
+                if (i < OWN && pass == 0) {
+                    // detail bands: rows low / cols high, rows high / cols low, both high
+                    const float cb[3] = {0.25f * (m0 + m1), 0.25f * (p0 - p1), 0.25f * (m0 - m1)};
+                    const size_t gp = gp0 + (size_t)(NWARP * i) * W;
+#pragma unroll
+                    for (int j = 0; j < 3; ++j) {
+                        const float sv = cb[j] - dold[i < OWN ? i : 0][j];
+                        const float u = soft_thresh(sv, tau);           // eq. soft
+                        const float nd = u - sv;                        // d2 - (c - u2)
+                        d2out[(size_t)(3 * lvl + j) * n + gp] = nd;
+                        d2io[(size_t)(3 * lvl + j) * n + gp] = u + nd;  // zeta2 = u2 + d2
+                        if (nobj) l1.add(fabsf(cb[j]));
+                    }
                 }
             }
         }
-        const float* band = d2in + (size_t)(3 * L) * n;
-        for (int rr = warp; rr < C::LLD; rr += NWARP) {
-            const float* src = band + (size_t)((R0 + rr - HALO) & (H - 1)) * W;
-            for (int cc = lane; cc < C::LLD; cc += 32)
-                cp_async4(ZLL + rr * C::LLD + cc, src + ((C0 + cc - HALO) & (W - 1)));
+        __syncthreads();
+        float* tmp = Ain;
+        Ain = Aout;
+        Aout = tmp;
+    }
+    // the last low-low band a_L on the tile
+    {
+        float dold[OWN];
+#pragma unroll
+        for (int i = 0; i < OWN; ++i) dold[i] = first ? 0.f : d2io[(size_t)(3 * L) * n + gp0 + (size_t)(NWARP * i) * W];
+#pragma unroll
+        for (int i = 0; i < OWN; ++i) {
+            const int rr = warp + NWARP * i;
+            const float cb = Ain[rr * XA + lane];
+            const size_t gp = gp0 + (size_t)(NWARP * i) * W;
+            const float sv = cb - dold[i];
+            const float u = soft_thresh(sv, tau);
+            const float nd = u - sv;
+            d2out[(size_t)(3 * L) * n + gp] = nd;
+            d2io[(size_t)(3 * L) * n + gp] = u + nd;
+            if (nobj) l1.add(fabsf(cb));
+        }
+    }
+    const CompSum acc[kNumPartials] = {CompSum(), l1, CompSum(), CompSum()};
+    double pv[kNumPartials];
+    block_reduce_comp(acc, reinterpret_cast<float*>(red), pv);
+    finish_iteration<kThreads>(P, k, chk, nobj, pv, n_active, n_row_ctas + blockIdx.x, probs, sl);
+}
+
+// ---------------------------------------------------------------------------
+// w = gamma P^T zeta2 on a T x T tile (adjoint synthesis, coarse to fine).
+// The adjoint of level j reads the coarser approximation and the level-j
+// bands at (r - {0, s}, c - {0, s}), so the tile needs zeta2 of level j on
+// [-(2^{j+1} - 1), T)^2 and the low-low band on [-(2^L - 1), T)^2.
+// Runs after haar_analysis has finished the iteration (ctl->iter = k).
+// ---------------------------------------------------------------------------
+template <int L>
+struct HaarSynCfg {
+    static constexpr int T = kHaarTile;
+    static constexpr int HALO = (1 << L) - 1;
+    static_assert(HALO < 16, "halo fits the 16-column margin");
+    // every array spans the columns [-16, T) (16-byte copies from a tile
+    // origin that is a multiple of 32 columns) and the rows it needs
+    static constexpr int XS = T + 16;              // row stride of every array
+    static constexpr int AR = T + HALO;            // approximation arrays: rows [-HALO, T)
+    __host__ __device__ static constexpr int band_rows(int lvl) { return T + 2 * (1 << lvl) - 1; }
+    __host__ __device__ static constexpr int zoff(int lvl) {
+        int o = 0;
+        for (int i = 0; i < lvl; ++i) o += 3 * band_rows(i) * XS;
+        return o;
+    }
+    static constexpr int ZTOT = zoff(L);
+    static constexpr size_t SMEM = (size_t)(2 * AR * XS + ZTOT) * sizeof(float);
+};
+
+template <int L>
+__global__ void __launch_bounds__(kThreads)
+haar_synthesis(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W) {
+    using C = HaarSynCfg<L>;
+    constexpr int T = C::T, HALO = C::HALO, XS = C::XS, AR = C::AR;
+    constexpr int CH = XS / 4;                     // 16-byte chunks per array row
+    constexpr int NWARP = kThreads / 32;
+    const int pi = sl.map[blockIdx.y];
+    if (pi < 0) return;
+    const ProbDesc& P = probs[pi];
+    // retired in this iteration, or a problem that has just taken over the slot
+    if (P.ctl->active == 0 || P.ctl->iter == 0) return;
+    const int k = P.ctl->iter;
+    extern __shared__ __align__(16) float sm[];
+    float* At = sm;
+    float* Ao = sm + AR * XS;
+    float* Z = sm + 2 * AR * XS;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tiles_x = W / T;
+    const int R0 = (blockIdx.x / tiles_x) * T, C0 = (blockIdx.x % tiles_x) * T;
+    const size_t n = (size_t)H * W;
+    const float* __restrict__ zeta = P.d2 + ((k + 1) & 1) * P.d2_stride;
+
+    // low-low band on rows [-HALO, T) and each level's bands on rows [-BO, T),
+    // all on the columns [-16, T)
+    {
+        const float* band = zeta + (size_t)(3 * L) * n;
+        for (int e = tid; e < AR * CH; e += kThreads) {
+            const int rr = e / CH, ch = e - rr * CH;
+            cp_async16(At + rr * XS + 4 * ch,
+                       band + (size_t)((R0 + rr - HALO) & (H - 1)) * W + ((C0 - 16 + 4 * ch) & (W - 1)));
+        }
+    }
+#pragma unroll
+    for (int lvl = 0; lvl < L; ++lvl) {
+        const int BO = 2 * (1 << lvl) - 1, BR = T + BO;
+        float* Zl = Z + C::zoff(lvl);
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const float* band = zeta + (size_t)(3 * lvl + j) * n;
+            for (int e = tid; e < BR * CH; e += kThreads) {
+                const int rr = e / CH, ch = e - rr * CH;
+                cp_async16(Zl + (j * BR + rr) * XS + 4 * ch,
+                           band + (size_t)((R0 + rr - BO) & (H - 1)) * W + ((C0 - 16 + 4 * ch) & (W - 1)));
+            }
         }
     }
     cp_async_commit();
     cp_async_wait<0>();
     __syncthreads();
 
-    CompSum l1;
-    float* Ain = A0;
-    float* Aout = A1;
-    // analysis, level by level: a_{j+1} and the three detail bands from a_j
-    // (levels unrolled: every region size below is a compile-time constant)
-#pragma unroll
-    for (int lvl = 0; lvl < L; ++lvl) {
-        const int s = 1 << lvl;
-        const int D = T + 2 * HALO + 1 - 2 * s;       // a_{j+1} is needed on [-HALO, D - HALO)
-        const int BO = 2 * s - 1, BD = T + 2 * s - 1;  // band region [-BO, T)
-        float* Zl = Z + C::zoff(lvl);
-        for (int rr = warp; rr < D; rr += NWARP) {
-            const int r = rr - HALO;
-            const bool band_row = r >= -BO && r < T;
-            const size_t grow = (size_t)((R0 + r) & (H - 1)) * W;
-            for (int cc = lane; cc < D; cc += 32) {
-                const int c = cc - HALO;
-                const int i00 = rr * XD + cc;
-                const float a00 = Ain[i00], a01 = Ain[i00 + s];
-                const float a10 = Ain[i00 + s * XD], a11 = Ain[i00 + s * XD + s];
-                const float p0 = a00 + a01, m0 = a00 - a01, p1 = a10 + a11, m1 = a10 - a11;
-                Aout[i00] = 0.25f * (p0 + p1);
-                if (band_row && c >= -BO && c < T) {
-                    const float cb[3] = {0.25f * (m0 + m1), 0.25f * (p0 - p1), 0.25f * (m0 - m1)};
-                    const size_t gpix = grow + ((C0 + c) & (W - 1));
-                    const bool own = r >= 0 && c >= 0;
-                    const int iz = (r + BO) * BD + (c + BO);
-#pragma unroll
-                    for (int j = 0; j < 3; ++j) {
-                        const float sv = first ? cb[j] : cb[j] - Zl[j * BD * BD + iz];
-                        const float u = soft_thresh(sv, tau);
-                        const float nd = u - sv;                   // d2 - (c - u2)
-                        Zl[j * BD * BD + iz] = u + nd;              // zeta2 = u2 + d2
-                        if (own) {
-                            d2out[(size_t)(3 * lvl + j) * n + gpix] = nd;
-                            if (nobj) l1.add(fabsf(cb[j]));
-                        }
-                    }
-                }
-            }
-        }
-        __syncthreads();
-        float* tmp = Ain; Ain = Aout; Aout = tmp;
-    }
-    // last low-low band (a_L on [-HALO, T)), thresholded in place
-    {
-        constexpr int D = T + HALO;
-        for (int rr = warp; rr < D; rr += NWARP) {
-            const int r = rr - HALO;
-            const size_t grow = (size_t)((R0 + r) & (H - 1)) * W;
-            for (int cc = lane; cc < D; cc += 32) {
-                const int c = cc - HALO;
-                const int i = rr * XD + cc;
-                const float cb = Ain[i];
-                const float sv = first ? cb : cb - ZLL[rr * C::LLD + cc];
-                const float u = soft_thresh(sv, tau);
-                const float nd = u - sv;
-                Ain[i] = u + nd;
-                if (r >= 0 && c >= 0) {
-                    d2out[(size_t)(3 * L) * n + grow + ((C0 + c) & (W - 1))] = nd;
-                    if (nobj) l1.add(fabsf(cb));
-                }
-            }
-        }
-        __syncthreads();
-    }
-    // synthesis (adjoint), coarse to fine: a~_j from a~_{j+1} and the zeta bands of level j
-    float* At = Ain;
-    float* Ao = Aout;
 #pragma unroll
     for (int lvl = L - 1; lvl >= 0; --lvl) {
         const int s = 1 << lvl;
         const int D = T + s - 1;                       // output on [-(s-1), T)
-        const int BO = 2 * s - 1, BD = T + 2 * s - 1;
+        const int BO = 2 * s - 1, BR = T + BO;
         const float* Z0 = Z + C::zoff(lvl);
-        const float* Z1 = Z0 + BD * BD;
-        const float* Z2 = Z1 + BD * BD;
-        const int ra = s * XD, rz = s * BD;
+        const float* Z1 = Z0 + BR * XS;
+        const float* Z2 = Z1 + BR * XS;
+        const int ra = s * XS, rz = s * XS;
         for (int rr = warp; rr < D; rr += NWARP) {
             const int r = rr - (s - 1);
             for (int cc = lane; cc < D; cc += 32) {
                 const int c = cc - (s - 1);
-                const int ia = (r + HALO) * XD + (c + HALO);
-                const int iz = (r + BO) * BD + (c + BO);
+                const int ia = (r + HALO) * XS + (c + 16);
+                const int iz = (r + BO) * XS + (c + 16);
                 // rows adjoint at columns c and c - s
                 const float lo_c = (At[ia] + At[ia - ra]) + (Z1[iz] - Z1[iz - rz]);
                 const float lo_l = (At[ia - s] + At[ia - ra - s]) + (Z1[iz - s] - Z1[iz - rz - s]);
@@ -292,16 +344,15 @@ haar_tile(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W, int n_
             }
         }
         __syncthreads();
-        float* tmp = At; At = Ao; Ao = tmp;
+        float* tmp = At;
+        At = Ao;
+        Ao = tmp;
     }
     // w = gamma P^T zeta2 on the tile
     const float gam = P.gamma;
+    float* __restrict__ ww = P.work + 2 * n;
     for (int r = warp; r < T; r += NWARP)
-        ww[(size_t)(R0 + r) * W + (C0 + lane)] = gam * At[(r + HALO) * XD + (lane + HALO)];
-    const CompSum acc[kNumPartials] = {CompSum(), l1, CompSum(), CompSum()};
-    double pv[kNumPartials];
-    block_reduce_comp(acc, reinterpret_cast<float*>(red), pv);
-    finish_iteration<kThreads>(P, k, chk, nobj, pv, n_active, n_row_ctas + blockIdx.x, probs, sl);
+        ww[(size_t)(R0 + r) * W + (C0 + lane)] = gam * At[(r + HALO) * XS + (lane + 16)];
 }
 
 // ---------------------------------------------------------------------------
@@ -359,10 +410,18 @@ cudaError_t launch_haar_rows_t(int H, int Wp, const ProbDesc* d, SlotTable sl, i
     if (e != cudaSuccess) return e;
     const dim3 tgrid(haar_num_tiles(H, W), count);
     switch (levels) {
-        case 1: haar_tile<1><<<tgrid, kThreads, HaarTileCfg<1>::SMEM, s>>>(d, sl, H, W, nrow, n_active); break;
-        case 2: haar_tile<2><<<tgrid, kThreads, HaarTileCfg<2>::SMEM, s>>>(d, sl, H, W, nrow, n_active); break;
-        case 3: haar_tile<3><<<tgrid, kThreads, HaarTileCfg<3>::SMEM, s>>>(d, sl, H, W, nrow, n_active); break;
-        default: haar_tile<4><<<tgrid, kThreads, HaarTileCfg<4>::SMEM, s>>>(d, sl, H, W, nrow, n_active); break;
+        case 1: haar_analysis<1><<<tgrid, kThreads, HaarAnaCfg<1>::SMEM, s>>>(d, sl, H, W, nrow, n_active); break;
+        case 2: haar_analysis<2><<<tgrid, kThreads, HaarAnaCfg<2>::SMEM, s>>>(d, sl, H, W, nrow, n_active); break;
+        case 3: haar_analysis<3><<<tgrid, kThreads, HaarAnaCfg<3>::SMEM, s>>>(d, sl, H, W, nrow, n_active); break;
+        default: haar_analysis<4><<<tgrid, kThreads, HaarAnaCfg<4>::SMEM, s>>>(d, sl, H, W, nrow, n_active); break;
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    switch (levels) {
+        case 1: haar_synthesis<1><<<tgrid, kThreads, HaarSynCfg<1>::SMEM, s>>>(d, sl, H, W); break;
+        case 2: haar_synthesis<2><<<tgrid, kThreads, HaarSynCfg<2>::SMEM, s>>>(d, sl, H, W); break;
+        case 3: haar_synthesis<3><<<tgrid, kThreads, HaarSynCfg<3>::SMEM, s>>>(d, sl, H, W); break;
+        default: haar_synthesis<4><<<tgrid, kThreads, HaarSynCfg<4>::SMEM, s>>>(d, sl, H, W); break;
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -374,13 +433,13 @@ inline cudaError_t haar_tile_attributes() {
     static bool done = false;
     if (done) return cudaSuccess;
     cudaError_t e;
-    e = cudaFuncSetAttribute(haar_tile<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)HaarTileCfg<1>::SMEM);
+    e = cudaFuncSetAttribute(haar_synthesis<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)HaarSynCfg<1>::SMEM);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(haar_tile<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)HaarTileCfg<2>::SMEM);
+    e = cudaFuncSetAttribute(haar_synthesis<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)HaarSynCfg<2>::SMEM);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(haar_tile<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)HaarTileCfg<3>::SMEM);
+    e = cudaFuncSetAttribute(haar_synthesis<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)HaarSynCfg<3>::SMEM);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(haar_tile<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)HaarTileCfg<4>::SMEM);
+    e = cudaFuncSetAttribute(haar_synthesis<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)HaarSynCfg<4>::SMEM);
     if (e != cudaSuccess) return e;
     done = true;
     return cudaSuccess;
