@@ -271,7 +271,13 @@ struct ColCfg {
     static_assert(CB % G == 0 && (CB & (CB - 1)) == 0, "column block");
     static constexpr int CPG = CB / G;               // columns per group
     static constexpr int SIG = H;                     // float2 per exchange buffer
-    static constexpr size_t SMEM = (size_t)H * CB * sizeof(float4) + (size_t)(G * 2 * SIG + H) * sizeof(float2);
+    // with one column per group, the transforms exchange through the tile
+    // itself once every group holds its column in registers (the tile is
+    // exactly G pairs of length-H buffers); otherwise separate buffers
+    static constexpr bool ALIAS = CPG == 1;
+    static constexpr size_t SMEM = (size_t)H * CB * sizeof(float4)
+                                 + (size_t)((ALIAS ? 0 : G * 2 * SIG) + H) * sizeof(float2);
+    static constexpr int MINB = ALIAS ? 4 : 2;       // CTAs per SM the registers are sized for
 };
 
 // Grid: (Wp / CB, problems). Wp (the stored half-spectrum width) is a
@@ -287,7 +293,7 @@ __device__ __forceinline__ int tile_slot(int r, int c) {
     return r * CB + ((c + (r >> SH)) & (CB - 1));
 }
 template <int H, int CB>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, ColCfg<H, CB>::MINB)
 col_phase(const ProbDesc* __restrict__ probs, SlotTable sl, int Wc, int Wp, const float2* __restrict__ tw_g) {
     using C = ColCfg<H, CB>;
     const int pi = sl.map[blockIdx.y];
@@ -304,8 +310,9 @@ col_phase(const ProbDesc* __restrict__ probs, SlotTable sl, int Wc, int Wp, cons
     }
     extern __shared__ __align__(16) float4 smem4[];
     float4* stage = smem4;                                       // H x CB
-    float2* xb = reinterpret_cast<float2*>(stage + H * CB);      // G x 2 exchange buffers
-    float2* tw = xb + C::G * 2 * C::SIG;
+    float2* xb = C::ALIAS ? reinterpret_cast<float2*>(stage)     // G x 2 exchange buffers
+                          : reinterpret_cast<float2*>(stage + H * CB);
+    float2* tw = reinterpret_cast<float2*>(stage + H * CB) + (C::ALIAS ? 0 : C::G * 2 * C::SIG);
     const int tid = threadIdx.x;
     const int c0 = blockIdx.x * CB;
     const float4* __restrict__ src = P.Sb;
@@ -344,6 +351,7 @@ col_phase(const ProbDesc* __restrict__ probs, SlotTable sl, int Wc, int Wp, cons
             v[m] = make_float2(f.x, f.y);
             u[m] = make_float2(f.z, f.w);
         }
+        if (C::ALIAS) __syncthreads();   // every column is in registers: the tile is free
         fft_group2<H, -1>(v, u, bz, bw, tw, t, g);
         if (spec) {
             // warm start: u0 = H x0 - d0 makes the first x-step return x0, whose
@@ -358,6 +366,7 @@ col_phase(const ProbDesc* __restrict__ probs, SlotTable sl, int Wc, int Wp, cons
             }
         }
         fft_group2<H, 1>(v, u, bz, bw, tw, t, g);
+        if (C::ALIAS) __syncthreads();   // every group is done exchanging through the tile
 #pragma unroll
         for (int m = 0; m < 8; ++m) {
             const int r = t + m * C::FT;
