@@ -35,9 +35,8 @@ TOL = 1e-5
 MAX_ITERS = 5000
 CHECK_EVERY = 10
 COMBOS = [("gauss", 40), ("motion", 40), ("gauss", 60), ("motion", 60)]
-ROW_KERNEL = "row_phase_tv<512,8,1,128>"
-COL_KERNEL = "col_phase<512,4>"
 STEADY_ITERS = 40
+TUNING_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "paper_1210_2687_gb300", "tuning.json")
 
 
 def parse():
@@ -54,7 +53,34 @@ def parse():
     ap.add_argument("--warm-only", action="store_true", help="only the learned warm-start comparison")
     ap.add_argument("--steady-only", action="store_true",
                     help="only the fixed-iteration pass with every slot busy (for profiler captures)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="use the default launch configurations instead of the autotuner's")
+    ap.add_argument("--retune", action="store_true", help="autotune even if the tuning cache has the class")
     return ap.parse_args()
+
+
+def tune_class(ad, torch, args, size_h, size_w, reg, levels=4):
+    """Launch configuration of a size class: the autotuner's choice (from the
+    tuning cache in the user's cache directory when it holds this GPU and
+    class, else measured now and added to it), or the defaults."""
+    if args.no_autotune:
+        cfg = ad.admm_deconv_get_tuning(size_h, size_w, reg, levels)
+        cfg["source"] = "default"
+        return cfg
+    cfg = ad.autotune_cached(size_h, size_w, reg, levels, path=TUNING_CACHE,
+                             device_name=torch.cuda.get_device_name(), retune=args.retune)
+    trials = cfg.pop("trials", None)
+    if trials:
+        cfg["trials"] = len(trials)
+        cfg["us_per_iter_default"] = next((t["us_per_iter"] for t in trials if t["row_variant"] == 0
+                                           and t["col_variant"] == 0 and t["slot_ctas"] == 0), None)
+    return cfg
+
+
+def kernel_names(cfg, size_h, size_w):
+    """Names of the TV row-phase and column-phase kernels of a configuration."""
+    return (f"row_phase_tv<{size_w},{cfg['rows_per_strip']},{cfg['walk_depth']},{cfg['row_threads']}>",
+            f"col_phase<{size_h},{cfg['col_block']}>")
 
 
 def dist_env():
@@ -98,6 +124,17 @@ def bytes_per_pixel_iter():
     row = 8 + 8 + 8 + 16 + 4 + 8.0 / CHECK_EVERY
     col = (16 + 16 + 8 + 4) * half
     return row, col
+
+
+def device_sources_sha256():
+    """Digest of the device-code sources (kernels, FFT, frame prior), which
+    ties a stored ncu traffic figure to the kernels it was measured on."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("kernels.cuh", "fft.cuh", "haar.cuh", "variants.cuh"):
+        with open(os.path.join(ROOT, "paper_1210_2687_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
 
 
 def read_peak():
@@ -169,7 +206,7 @@ class ClockSampler:
 FRAME_ITERS = 500
 
 
-def frame_secondary(ad, torch, stream):
+def frame_secondary(ad, torch, stream, args):
     """Frame-prior (FA-MD) workload: 4-level undecimated Haar, 13 x 13
     uniform blur, valid region, BSNR 50 dB, 1024^2 and 2048^2, a fixed 500
     iterations (throughput); kernel time per phase from a profiled pass.
@@ -180,6 +217,7 @@ def frame_secondary(ad, torch, stream):
     for size in (1024, 2048):
         p = S.config3_problem(0, size)
         n = size * size
+        tune = tune_class(ad, torch, args, size, size, "haar", 4)
         plan = ad.Plan(size, size, p.psf, p.lam, p.mu1, p.mu2, "haar", stop="iters", max_iters=FRAME_ITERS)
         y = torch.from_numpy(p.ybar.astype(np.float32)).to("cuda")
         m = torch.from_numpy(p.mask).to("cuda")
@@ -200,7 +238,8 @@ def frame_secondary(ad, torch, stream):
             "iters_per_s": FRAME_ITERS / sec,
             "row_side_gbs": FRAME_ITERS * n * row_b / (pf.row_ms * 1e-3) / 1e9,
             "col_phase_gbs": FRAME_ITERS * n * col_b / (pf.col_ms * 1e-3) / 1e9,
-            "bytes_per_px_iter": {"row_side": row_b, "col_phase": col_b}}
+            "bytes_per_px_iter": {"row_side": row_b, "col_phase": col_b},
+            "tuning": tune}
         plan.close()
     return out
 
@@ -363,7 +402,7 @@ def run_ours(args):
 
     dev = torch.device("cuda", local)
     if args.frame_only:
-        print(json.dumps({"secondary": frame_secondary(ad, torch, torch.cuda.current_stream())}), flush=True)
+        print(json.dumps({"secondary": frame_secondary(ad, torch, torch.cuda.current_stream(), args)}), flush=True)
         return
     if args.warm_only:
         print(json.dumps({"warm_start": warm_secondary(ad, torch, torch.cuda.current_stream())}), flush=True)
@@ -371,6 +410,8 @@ def run_ours(args):
     if args.uneven_only:
         print(json.dumps({"uneven_batch": uneven_secondary(ad, torch, torch.cuda.current_stream())}), flush=True)
         return
+    tune = tune_class(ad, torch, args, H, W, "tv")
+    row_kernel, col_kernel = kernel_names(tune, H, W)
     probs = make_batch(args.batch, rank)
     n = H * W
     plans = [ad.Plan(H, W, p.psf, p.lam, p.mu1, p.mu2, "tv", stop="rel_x", tol=TOL,
@@ -389,7 +430,7 @@ def run_ours(args):
         row_b, col_b = bytes_per_pixel_iter()
         its = STEADY_ITERS * len(fixed)
         print(json.dumps({"steady_state": {
-            "problems": len(fixed), "iters": STEADY_ITERS,
+            "problems": len(fixed), "iters": STEADY_ITERS, "kernels": [row_kernel, col_kernel],
             "row_phase_gbs": its * n * row_b / (pf.row_ms * 1e-3) / 1e9,
             "col_phase_gbs": its * n * col_b / (pf.col_ms * 1e-3) / 1e9,
             "iters_per_s": its / ((pf.row_ms + pf.col_ms) * 1e-3)}}), flush=True)
@@ -451,7 +492,7 @@ def run_ours(args):
     row_gbs = img_iters * n * row_b / (prof.row_ms * 1e-3) / 1e9 if prof.row_ms > 0 else 0.0
     col_gbs = img_iters * n * col_b / (prof.col_ms * 1e-3) / 1e9 if prof.col_ms > 0 else 0.0
     peak, peak_kind = read_peak()
-    dom = ROW_KERNEL if prof.row_ms >= prof.col_ms else COL_KERNEL
+    dom = row_kernel if prof.row_ms >= prof.col_ms else col_kernel
     ach = row_gbs if prof.row_ms >= prof.col_ms else col_gbs
 
     # ---- steady state (untimed for `value`): every slot busy for a fixed
@@ -478,13 +519,15 @@ def run_ours(args):
             f.close()
     # DRAM bytes per launch from the committed ncu capture (bytes per pixel
     # there) scaled to the pixels an average launch of this pass processed
+    # (null when the device sources have changed since the capture)
     traffic = None
     tpath = os.path.join(ROOT, "profiles", "traffic.json")
-    launches_dom = prof.row_launches if dom == ROW_KERNEL else prof.col_launches
+    launches_dom = prof.row_launches if dom == row_kernel else prof.col_launches
     if os.path.exists(tpath) and launches_dom > 0:
         try:
-            bpp = json.load(open(tpath))[dom]["bytes_per_px"]
-            traffic = bpp * n * img_iters / launches_dom
+            tj = json.load(open(tpath))
+            if tj.get("_device_sources_sha256") == device_sources_sha256():
+                traffic = tj[dom]["bytes_per_px"] * n * img_iters / launches_dom
         except Exception:
             traffic = None
 
@@ -506,7 +549,7 @@ def run_ours(args):
 
     secondary = None
     if rank == 0 and not args.no_secondary:
-        secondary = frame_secondary(ad, torch, stream)
+        secondary = frame_secondary(ad, torch, stream, args)
         secondary["uneven_batch"] = uneven_secondary(ad, torch, stream)
         secondary["warm_start"] = warm_secondary(ad, torch, stream)
 
@@ -530,6 +573,7 @@ def run_ours(args):
                        "slots": "automatic (continuous batching: queued problems start as others retire)",
                        "parallelism": f"replicas x{world}"},
             "images_per_s": images_per_s,
+            "tuning": tune,
             "iters_per_image_mean": total_iters / (args.batch * world * args.steps),
             "isnr_db_mean": float(np.mean(isnrs)),
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": peak,

@@ -213,6 +213,80 @@ typedef struct {
  */
 ADMM_API int admm_deconv_profile(int enable, admm_profile_t* out);
 
+/* ---- launch configurations and the autotuner (not in the paper) ---------
+ * The library compiles a few configurations of each phase per side length:
+ * for the TV row phase (rows per strip, walk rows kept in flight, threads
+ * per CTA) and for the column phase (spectrum columns per CTA). It also
+ * chooses how many problems of a size class iterate at once, aiming for a
+ * number of row-side CTAs per launch. A tuning table, one entry per
+ * (device, H, W, regulariser, levels), says which configuration new plans of
+ * that class use; untuned classes use index 0 of each list and 2400 CTAs.
+ * Plans keep the configuration they were created with, and a batch groups
+ * plans by shape AND configuration. The table is library-global. */
+typedef struct {
+    int    H, W;            /* [in] the size class ...                                        */
+    int    reg;             /* [in] ... ADMM_REG_TV or ADMM_REG_HAAR ...                      */
+    int    haar_levels;     /* [in] ... and levels (1..4 for Haar, 0 = 4; ignored for TV)     */
+    int    row_variant;     /* index of the TV row-phase configuration of W (0 for Haar)     */
+    int    col_variant;     /* index of the column-phase configuration of H                  */
+    int    slot_ctas;       /* row-side CTAs per launch aimed for (0 = default 2400)         */
+    int    rows_per_strip;  /* [out] meaning of row_variant: rows per row-phase CTA, ...     */
+    int    walk_depth;      /* [out] ... walk rows in flight (0 = read directly), ...        */
+    int    row_threads;     /* [out] ... threads per row-phase CTA                           */
+    int    col_block;       /* [out] meaning of col_variant: spectrum columns per CTA        */
+    double us_per_iter;     /* [out] autotuner: measured device time per problem-iteration
+                               in microseconds (0 if the entry was not measured)             */
+} admm_tuning_t;
+
+/*
+ * admm_deconv_variants -- number of compiled configurations of the class:
+ * *n_row TV row-phase configurations of width W (1 for Haar, whose row side
+ * has one), *n_col column-phase configurations of height H.
+ * Errors: ADMM_EINVAL (NULL outputs, bad reg), ADMM_EUNSUPPORTED_SIZE.
+ */
+ADMM_API int admm_deconv_variants(int H, int W, int reg, int* n_row, int* n_col);
+
+/*
+ * admm_deconv_get_tuning -- the configuration new plans of the class get on
+ * the current device. In: t->H, W, reg, haar_levels. Out: every other field
+ * (indices 0 and us_per_iter 0 for an untuned class).
+ * Errors: ADMM_EINVAL, ADMM_EUNSUPPORTED_SIZE, ADMM_ECUDA.
+ */
+ADMM_API int admm_deconv_get_tuning(admm_tuning_t* t);
+
+/*
+ * admm_deconv_set_tuning -- install a configuration for the class on the
+ * current device (e.g. one read back from a tuning cache). The [out] fields
+ * are ignored; plans created afterwards use it.
+ * Errors: ADMM_EINVAL (an index out of range, slot_ctas < 0),
+ * ADMM_EUNSUPPORTED_SIZE, ADMM_ECUDA.
+ */
+ADMM_API int admm_deconv_set_tuning(const admm_tuning_t* t);
+
+/*
+ * admm_deconv_autotune -- time every combination of the class's compiled
+ * configurations and slot targets {default 2400, 1200, 4800} on the current
+ * device and install the fastest. Each trial creates `problems` plans of the
+ * class on a synthetic observation (9 x 9 box blur, valid-region mask, rel-x
+ * rule with tolerance 0 checked every 10 iterations, so no problem retires
+ * early), runs `iters` iterations of all of them once to warm up and once
+ * timed with CUDA events on `stream`, and frees them. The score is device
+ * time per problem-iteration.
+ *   problems    problems per trial (<= 0: enough to fill the largest slot
+ *               target, at most 96)
+ *   iters       iterations per solve (<= 0: 48)
+ *   trials      [out] optional array of max_trials entries: every trial
+ *   n_trials    [out] optional: number of trials run
+ *   best        [out] optional: the configuration installed
+ * Allocates device memory for the trials (problems plans at a time). Not
+ * safe against plans of the same class being created concurrently from
+ * other threads while it runs.
+ * Errors: ADMM_EINVAL, ADMM_EUNSUPPORTED_SIZE, ADMM_ENOMEM, ADMM_ECUDA.
+ */
+ADMM_API int admm_deconv_autotune(int H, int W, int reg, int haar_levels, int problems, int iters,
+                                  admm_tuning_t* trials, int max_trials, int* n_trials, admm_tuning_t* best,
+                                  void* stream);
+
 /*
  * admm_deconv_solve_noalloc -- one TV solve that allocates no memory.
  * The paper has no counterpart: this exists for callers that must not

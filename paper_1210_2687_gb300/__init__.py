@@ -42,6 +42,7 @@ EXPORTED = ("admm_deconv_plan", "admm_deconv_solve", "admm_deconv_solve_batch",
             "admm_deconv_state_size", "admm_deconv_get_state", "admm_deconv_destroy",
             "admm_strerror", "admm_deconv_version", "admm_deconv_profile",
             "admm_deconv_solve_noalloc", "admm_deconv_set_option", "admm_deconv_warm_start",
+            "admm_deconv_variants", "admm_deconv_get_tuning", "admm_deconv_set_tuning", "admm_deconv_autotune",
             "admm_cnn_param_count", "admm_cnn_create", "admm_cnn_set_params", "admm_cnn_get_params",
             "admm_cnn_forward", "admm_cnn_gradients", "admm_cnn_train_step", "admm_cnn_predict_start",
             "admm_cnn_launches", "admm_cnn_destroy")
@@ -75,6 +76,16 @@ class admm_profile_t(ctypes.Structure):
     _fields_ = [("col_ms", ctypes.c_double), ("row_ms", ctypes.c_double),
                 ("col_launches", ctypes.c_longlong), ("row_launches", ctypes.c_longlong),
                 ("kernel_launches", ctypes.c_longlong)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class admm_tuning_t(ctypes.Structure):
+    _fields_ = [("H", ctypes.c_int), ("W", ctypes.c_int), ("reg", ctypes.c_int), ("haar_levels", ctypes.c_int),
+                ("row_variant", ctypes.c_int), ("col_variant", ctypes.c_int), ("slot_ctas", ctypes.c_int),
+                ("rows_per_strip", ctypes.c_int), ("walk_depth", ctypes.c_int), ("row_threads", ctypes.c_int),
+                ("col_block", ctypes.c_int), ("us_per_iter", ctypes.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -118,6 +129,16 @@ def _load() -> ctypes.CDLL:
     lib.admm_deconv_solve_noalloc.restype = ctypes.c_int
     lib.admm_deconv_set_option.argtypes = [ctypes.c_int, ctypes.c_longlong]
     lib.admm_deconv_set_option.restype = ctypes.c_int
+    tp = ctypes.POINTER(admm_tuning_t)
+    ip = ctypes.POINTER(ctypes.c_int)
+    lib.admm_deconv_variants.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ip, ip]
+    lib.admm_deconv_variants.restype = ctypes.c_int
+    lib.admm_deconv_get_tuning.argtypes = [tp]
+    lib.admm_deconv_get_tuning.restype = ctypes.c_int
+    lib.admm_deconv_set_tuning.argtypes = [tp]
+    lib.admm_deconv_set_tuning.restype = ctypes.c_int
+    lib.admm_deconv_autotune.argtypes = [ctypes.c_int] * 6 + [tp, ctypes.c_int, ip, tp, vp]
+    lib.admm_deconv_autotune.restype = ctypes.c_int
     ci, fp = ctypes.c_int, ctypes.c_float
     dp = ctypes.POINTER(ctypes.c_double)
     lib.admm_cnn_param_count.argtypes = []
@@ -308,6 +329,72 @@ def admm_deconv_set_option(option: int, value: int) -> None:
     rc = lib.admm_deconv_set_option(int(option), int(value))
     if rc != ADMM_OK:
         raise AdmmError(rc, "admm_deconv_set_option")
+
+
+def admm_deconv_variants(H: int, W: int, reg="tv") -> tuple[int, int]:
+    """(TV row-phase configurations of W, column-phase configurations of H)."""
+    nr, nc = ctypes.c_int(), ctypes.c_int()
+    _check(lib.admm_deconv_variants(int(H), int(W), _REG.get(reg, reg), ctypes.byref(nr), ctypes.byref(nc)),
+           "admm_deconv_variants")
+    return nr.value, nc.value
+
+
+def admm_deconv_get_tuning(H: int, W: int, reg="tv", levels: int = 4) -> dict:
+    t = admm_tuning_t(H=int(H), W=int(W), reg=_REG.get(reg, reg), haar_levels=int(levels))
+    _check(lib.admm_deconv_get_tuning(ctypes.byref(t)), "admm_deconv_get_tuning")
+    return t.as_dict()
+
+
+def admm_deconv_set_tuning(cfg: dict) -> None:
+    t = admm_tuning_t(**{k: cfg[k] for k, _ in admm_tuning_t._fields_ if k in cfg})
+    _check(lib.admm_deconv_set_tuning(ctypes.byref(t)), "admm_deconv_set_tuning")
+
+
+def admm_deconv_autotune(H: int, W: int, reg="tv", levels: int = 4, problems: int = 0, iters: int = 0,
+                         stream=None) -> tuple[dict, list[dict]]:
+    """Time every compiled configuration of the class on the current device
+    and install the fastest; returns (best, all trials)."""
+    nr, nc = admm_deconv_variants(H, W, reg)
+    cap = nr * nc * 3
+    trials = (admm_tuning_t * cap)()
+    n = ctypes.c_int()
+    best = admm_tuning_t()
+    _check(lib.admm_deconv_autotune(int(H), int(W), _REG.get(reg, reg), int(levels), int(problems), int(iters),
+                                    trials, cap, ctypes.byref(n), ctypes.byref(best), _stream(stream)),
+           "admm_deconv_autotune")
+    return best.as_dict(), [trials[i].as_dict() for i in range(min(n.value, cap))]
+
+
+def tuning_cache_key(H: int, W: int, reg="tv", levels: int = 4, device_name: str = "") -> str:
+    r = _REG.get(reg, reg)
+    return f"{device_name}|{int(H)}x{int(W)}|{'tv' if r == ADMM_REG_TV else 'haar'}|{0 if r == ADMM_REG_TV else int(levels) or 4}"
+
+
+def autotune_cached(H: int, W: int, reg="tv", levels: int = 4, path: str | None = None, device_name: str = "",
+                    retune: bool = False, stream=None) -> dict:
+    """Install the configuration of the class from the JSON tuning cache at
+    `path` (keyed by device name, size, regulariser and levels), or autotune
+    it and add it to the cache. Returns the installed configuration, with
+    "source": "cache" or "autotune" and, after a tuning run, "trials"."""
+    import json
+    key = tuning_cache_key(H, W, reg, levels, device_name)
+    cache = {}
+    if path and os.path.exists(path):
+        with open(path) as f:
+            cache = json.load(f)
+    if not retune and key in cache:
+        admm_deconv_set_tuning(cache[key])
+        out = admm_deconv_get_tuning(H, W, reg, levels)
+        out["us_per_iter"] = cache[key].get("us_per_iter", 0.0)
+        out["source"] = "cache"
+        return out
+    best, trials = admm_deconv_autotune(H, W, reg, levels, stream=stream)
+    if path:
+        cache[key] = best
+        os.makedirs(os.path.dirname(os.path.abspath(path)), exist_ok=True)
+        with open(path, "w") as f:
+            json.dump(cache, f, indent=1, sort_keys=True)
+    return dict(best, source="autotune", trials=trials)
 
 
 def admm_deconv_destroy(plan: int) -> None:

@@ -16,7 +16,8 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 LIB = os.path.join(PKG, "libadmm_deconv.so")
-SOURCES = [os.path.join(CSRC, "engine.cu"), os.path.join(CSRC, "cnn.cu")]
+SOURCES = [os.path.join(CSRC, f) for f in
+           ("engine.cu", "cols.cu", "rows_small.cu", "rows_512.cu", "rows_large.cu", "cnn.cu")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -153,111 +153,9 @@ __device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
 // observed pixels carry M^T y, unobserved ones a quiet NaN (eq. prox_g_1_uBC)
 __device__ __forceinline__ bool is_observed(float yb) { return yb == yb; }
 
-// ---------------------------------------------------------------------------
-// a0: plan precompute. Lambda[kr,kc] = sum_{a,b} h[a+lr,b+lc] exp(-2 pi i (kr a/H + kc b/W))
-// (DFT of the kernel centred at (0,0), eq. DFT_fact) for the half spectrum
-// kc = 0..W/2, and the diagonal inverse of eq. fast_inversion (TV, divided by
-// mu1) or eq. invAnalysisp1 (frame), times 1/(HW). FP64, rounded once to FP32.
-// ---------------------------------------------------------------------------
+// largest PSF side the plan accepts (the spectra kernel keeps one row of
+// phase factors per thread)
 constexpr int kMaxPsfSide = 63;
-
-__global__ void spectra_kernel(float2* __restrict__ lamT, float* __restrict__ kT,
-                               const float* __restrict__ psf, int ph, int pw, int H, int W, int Wc,
-                               int reg, double gamma) {
-    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= H * Wc) return;
-    const int kc = idx / H, kr = idx % H;
-    const int lr = ph / 2, lc = pw / 2;
-    double fre[kMaxPsfSide], fim[kMaxPsfSide];
-    for (int b = -lc; b <= lc; ++b) {
-        long long m = ((long long)kc * b) % W;
-        if (m < 0) m += W;
-        double s, c;
-        sincospi(-2.0 * (double)m / (double)W, &s, &c);
-        fre[b + lc] = c;
-        fim[b + lc] = s;
-    }
-    double re = 0.0, im = 0.0;
-    for (int a = -lr; a <= lr; ++a) {
-        double sre = 0.0, sim = 0.0;
-        const float* hr = psf + (a + lr) * pw;
-        for (int b = 0; b < pw; ++b) {
-            sre += (double)hr[b] * fre[b];
-            sim += (double)hr[b] * fim[b];
-        }
-        long long m = ((long long)kr * a) % H;
-        if (m < 0) m += H;
-        double s, c;
-        sincospi(-2.0 * (double)m / (double)H, &s, &c);
-        re += sre * c - sim * s;
-        im += sre * s + sim * c;
-    }
-    double den = re * re + im * im;
-    if (reg == 0) {
-        double sh = sinpi((double)kc / (double)W), sv = sinpi((double)kr / (double)H);
-        den += gamma * 4.0 * (sh * sh + sv * sv);
-    } else {
-        den += gamma;
-    }
-    lamT[idx] = make_float2((float)re, (float)im);
-    kT[idx] = (float)(1.0 / (den * (double)H * (double)W));
-}
-
-// ---------------------------------------------------------------------------
-// Per-solve preparation: effective mask (optionally ANDed with the valid
-// region of Sec. IV-A) and M^T y (observations zero-extended, eq.
-// prox_g_1_uBC), stored as ybar with a quiet NaN on unobserved pixels. A
-// non-finite observed value marks the problem (it then retires at once with
-// ADMM_ENONFINITE). ctl must be zeroed before this kernel runs.
-// ---------------------------------------------------------------------------
-__global__ void prepare_kernel(float* __restrict__ ybar, uint8_t* __restrict__ mask_eff,
-                               const float* __restrict__ y, const uint8_t* __restrict__ mask_in,
-                               int H, int W, int lr, int lc, int raw_mask, ProbCtl* __restrict__ ctl) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= H * W) return;
-    const int r = i / W, c = i % W;
-    bool obs = (mask_in == nullptr) ? true : (mask_in[i] != 0);
-    if (!raw_mask || mask_in == nullptr)
-        obs = obs && r >= lr && r < H - lr && c >= lc && c < W - lc;
-    mask_eff[i] = obs ? 1 : 0;
-    const float v = obs ? y[i] : 0.0f;
-    if (obs && !isfinite(v)) atomicOr(&ctl->input_bad, 1);
-    ybar[i] = obs ? v : __int_as_float(0x7fc00000);
-}
-
-__global__ void init_ctl_kernel(ProbDesc* __restrict__ probs, int count, int* __restrict__ n_active) {
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= count) return;
-    ProbCtl* c = probs[b].ctl;
-    const bool bad = c->input_bad != 0;
-    c->iter = 0;
-    c->active = bad ? 0 : 1;
-    c->converged = 0;
-    c->status = bad ? kStatusNonFinite : 0;
-    c->arrive = 0;
-    c->have_obj = 0;
-    c->obj = 0.0;
-    c->obj_prev = 0.0;
-    c->rel_x = -1.0;
-    c->rel_obj = -1.0;
-    c->t0 = device_clock_ns();
-    c->t_start = 0;
-    c->t_done = bad ? c->t0 : 0;
-    if (bad) atomicSub(n_active, 1);
-}
-
-// first `nslots` problems that are still active go to the slots (one thread)
-__global__ void assign_slots_kernel(const ProbDesc* __restrict__ probs, SlotTable sl, int nslots) {
-    if (blockIdx.x != 0 || threadIdx.x != 0) return;
-    int next = 0;
-    const unsigned long long now = device_clock_ns();
-    for (int s = 0; s < nslots; ++s) {
-        while (next < sl.pool && probs[next].ctl->active == 0) ++next;
-        sl.map[s] = next < sl.pool ? next : -1;
-        if (next < sl.pool) probs[next++].ctl->t_start = now;
-    }
-    *sl.queue = next;
-}
 
 // ---------------------------------------------------------------------------
 // Column phase. Grid: (ceil(Wc / CB), problems). CTA = CB spectrum columns of
@@ -596,16 +494,20 @@ struct RowCfg {
     static constexpr int CW = W / NWARP;                           // columns per warp
     static constexpr int CPT = CW >= 32 ? CW / 32 : 1;              // columns per thread
     static constexpr int SLOT = 5 * W + 2 * NWARP;                 // floats per ring slot
+    static constexpr int DR = D > 0 ? D : 1;                       // ring slots addressed (D = 0: none used)
     static_assert(RAW * 16 <= ROW * 8, "raw row must fit a buffer row");
     static_assert(R + 2 <= 32, "boundary capture holds one row per lane");
     static_assert(((size_t)NB * ROW * 8 + (size_t)W * 8) % 16 == 0, "ring alignment");
     static_assert(((size_t)NB * ROW * 8 + (size_t)W * 8 + (size_t)D * SLOT * 4) % 8 == 0, "scratch alignment");
     static constexpr size_t SMEM = (size_t)NB * ROW * sizeof(float2) + (size_t)W * sizeof(float2)
                                  + (size_t)D * SLOT * sizeof(float) + NWARP * 2 * kNumPartials * sizeof(float);
+    // CTAs per SM the registers are sized for (128-thread CTAs without the
+    // ring fit a fifth CTA in shared memory)
+    static constexpr int MINB = NT == 128 ? (D == 0 ? 5 : 4) : (NT == 64 ? 8 : 2);
 };
 
 template <int W, int R, int D, int NT>
-__global__ void __launch_bounds__(NT, (NT == 128 ? 4 : 2))
+__global__ void __launch_bounds__(NT, (RowCfg<W, R, D, NT>::MINB))
 row_phase_tv(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp, const float2* __restrict__ tw_g,
              int* __restrict__ n_active) {
     using C = RowCfg<W, R, D, NT>;
@@ -635,9 +537,9 @@ row_phase_tv(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp, co
     // ring slot of walk row i: d2 (float2 per column), d1, M^T y, x_prev, and
     // per warp the d2 of the pixel left of its chunk
     auto issue = [&](int i) {
-        if (i <= R && colthr) {
+        if (D > 0 && i <= R && colthr) {
             const int q = (r0 - 1 + i + H) & (H - 1);
-            float* slot = ring + (i % D) * C::SLOT;
+            float* slot = ring + (i % C::DR) * C::SLOT;
 #pragma unroll
             for (int j = 0; j < C::CPT; ++j) {
                 const int c = cbase + 32 * j;
@@ -723,8 +625,8 @@ row_phase_tv(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp, co
     for (int i = 0; i <= R; ++i) {
         const int q = (r0 - 1 + i + H) & (H - 1);
         const bool owned = i >= 1;
-        cp_async_wait<D - 1>();      // this thread's copies of walk row i have landed
-        const float* slot = ring + (i % D) * C::SLOT;
+        if (D > 0) cp_async_wait<(D > 0 ? D - 1 : 0)>();   // this thread's copies of walk row i have landed
+        const float* slot = ring + (i % C::DR) * C::SLOT;
         const float xr_nb = __shfl_sync(0xffffffffu, xnb_right, i);
         const float xl_nb = __shfl_sync(0xffffffffu, xnb_left, i);
         const float xl_nb_dn = __shfl_sync(0xffffffffu, xnb_left, i + 1);
@@ -744,7 +646,8 @@ row_phase_tv(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp, co
                 // D_i x (forward periodic differences)
                 const float gh = xr - x, gv = xd - x;
                 const size_t pix = (size_t)q * W + c;
-                const float2 dd = cold ? make_float2(0.f, 0.f) : *reinterpret_cast<const float2*>(slot + 2 * c);
+                const float2 dd = cold ? make_float2(0.f, 0.f)
+                                       : (D > 0 ? *reinterpret_cast<const float2*>(slot + 2 * c) : d2in[pix]);
                 // u2 = v-soft(D_i x - d2, lambda/mu2)  (Alg. 3 line 10, 0/0 = 0):
                 // the scale max(0, 1 - tau / |s|), with one reciprocal square
                 // root (|s| = 0 gives -inf inside the max, so 0)
@@ -760,8 +663,8 @@ row_phase_tv(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp, co
                 if (owned) {
                     d2out[pix] = make_float2(nh, nv);
                     // u1 = (M^T M + mu1 I)^{-1} (M^T y + mu1 (A x - d1))  (eq. new_line)
-                    const float dd1 = cold ? 0.f : slot[2 * W + c];
-                    const float yb = slot[3 * W + c];
+                    const float dd1 = cold ? 0.f : (D > 0 ? slot[2 * W + c] : P.d1[pix]);
+                    const float yb = D > 0 ? slot[3 * W + c] : P.ybar[pix];
                     const float s1 = ax - dd1;
                     const bool obs = is_observed(yb);
                     const float u1 = obs ? fmaf(mu1, s1, yb) * inv1 : s1;
@@ -777,7 +680,7 @@ row_phase_tv(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp, co
                         s_reg.add(sqrtf(fmaf(gh, gh, gv * gv)));
                     }
                     if (chk) {
-                        const float dx = first ? x : x - slot[4 * W + c];
+                        const float dx = first ? x : x - (D > 0 ? slot[4 * W + c] : P.xprev[pix]);
                         s_dxx.add(dx * dx);
                         s_xx.add(x * x);
                     }
@@ -789,7 +692,8 @@ row_phase_tv(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp, co
                 const float xh = xl_nb;
                 const float xhr = buf[i * C::ROW + swz(wid * C::CW)].x;
                 const float2 dd = cold ? make_float2(0.f, 0.f)
-                                        : *reinterpret_cast<const float2*>(slot + 5 * W + 2 * wid);
+                                        : (D > 0 ? *reinterpret_cast<const float2*>(slot + 5 * W + 2 * wid)
+                                                 : d2in[(size_t)q * W + chalo]);
                 const float sh = (xhr - xh) - dd.x, sv = (xl_nb_dn - xh) - dd.y;
                 const float sc = fmaxf(0.f, fmaf(-tau, rsqrtf(fmaf(sh, sh, sv * sv)), 1.f));
                 dh_halo = 2.f * sc * sh - sh;

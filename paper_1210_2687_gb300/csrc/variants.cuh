@@ -1,0 +1,81 @@
+// variants.cuh -- the kernel configurations the engine chooses between for a
+// size class, and their launchers.
+//
+// Every side length has a short list of compiled configurations of the TV
+// row phase (rows per strip R, walk rows in flight D, threads per CTA NT) and
+// of the column phase (columns per CTA CB); entry 0 of each list is the
+// default. The autotuner (admm_deconv_autotune) times the combinations on the
+// device and records the fastest per (device, H, W, regulariser, levels);
+// plans created afterwards use it. The instantiations are spread over
+// several translation units (rows_small.cu, rows_512.cu, rows_large.cu,
+// cols.cu) so that they compile in parallel.
+#pragma once
+#include "kernels.cuh"
+
+namespace admm {
+
+using RowLaunchFn = cudaError_t (*)(const ProbDesc* d, SlotTable sl, int count, int H, int Wp, const float2* tw,
+                                    int* n_active, cudaStream_t s);
+using ColLaunchFn = cudaError_t (*)(const ProbDesc* d, SlotTable sl, int count, int Wc, int Wp, const float2* tw,
+                                    cudaStream_t s);
+
+struct RowVariant {
+    int R, D, NT;
+    RowLaunchFn fn;
+};
+struct ColVariant {
+    int CB;
+    ColLaunchFn fn;
+};
+
+// candidates for one side length (entry 0 = default); returns their number,
+// 0 for an unsupported side
+int tv_row_variants(int W, const RowVariant** out);
+int col_variants(int H, const ColVariant** out);
+
+// per translation unit
+int tv_row_variants_small(int W, const RowVariant** out);   // W = 64, 128, 256
+int tv_row_variants_512(const RowVariant** out);            // W = 512
+int tv_row_variants_large(int W, const RowVariant** out);   // W = 1024, 2048
+
+template <int W, int R, int D, int NT>
+cudaError_t launch_row_tv_t(const ProbDesc* d, SlotTable sl, int count, int H, int Wp, const float2* tw,
+                            int* n_active, cudaStream_t s) {
+    static bool attr = false;
+    const size_t smem = RowCfg<W, R, D, NT>::SMEM;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(row_phase_tv<W, R, D, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    dim3 grid(H / R, count);
+    row_phase_tv<W, R, D, NT><<<grid, NT, smem, s>>>(d, sl, H, Wp, tw, n_active);
+    return cudaGetLastError();
+}
+
+template <int H, int CB>
+cudaError_t launch_col_t(const ProbDesc* d, SlotTable sl, int count, int Wc, int Wp, const float2* tw,
+                         cudaStream_t s) {
+    static bool attr = false;
+    const size_t smem = ColCfg<H, CB>::SMEM;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(col_phase<H, CB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    dim3 grid(Wp / CB, count);
+    col_phase<H, CB><<<grid, kThreads, smem, s>>>(d, sl, Wc, Wp, tw);
+    return cudaGetLastError();
+}
+
+template <int W, int R, int D, int NT>
+constexpr RowVariant row_variant() {
+    return RowVariant{R, D, NT, &launch_row_tv_t<W, R, D, NT>};
+}
+template <int H, int CB>
+constexpr ColVariant col_variant() {
+    return ColVariant{CB, &launch_col_t<H, CB>};
+}
+
+}  // namespace admm

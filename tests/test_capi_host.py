@@ -106,3 +106,35 @@ def test_cnn_null_arguments(ad):
     assert lib.admm_cnn_forward(None, 1, 16, 16, None, None, None, None) == ad.ADMM_EINVAL
     assert lib.admm_deconv_warm_start(None, None, None, None) == ad.ADMM_EINVAL
     lib.admm_cnn_destroy(None)
+
+
+def test_tuning_struct_layout(ad):
+    # admm_tuning_t: 11 ints, padding, double
+    assert ctypes.sizeof(ad.admm_tuning_t) == 56
+    assert ad.admm_tuning_t.us_per_iter.offset == 48
+
+
+def test_every_size_has_compiled_configurations(ad):
+    sides = (64, 128, 256, 512, 1024, 2048)
+    for H in sides:
+        for W in sides:
+            nr, nc = ad.admm_deconv_variants(H, W, "tv")
+            assert nr >= 2 and nc >= 2
+            nr, nc = ad.admm_deconv_variants(H, W, "haar")
+            assert nr == 1 and nc >= 2
+    n_r, n_c = ctypes.c_int(), ctypes.c_int()
+    assert ad.lib.admm_deconv_variants(384, 512, 0, ctypes.byref(n_r), ctypes.byref(n_c)) == ad.ADMM_EUNSUPPORTED_SIZE
+    assert ad.lib.admm_deconv_variants(512, 512, 7, ctypes.byref(n_r), ctypes.byref(n_c)) == ad.ADMM_EINVAL
+    assert ad.lib.admm_deconv_variants(512, 512, 0, None, None) == ad.ADMM_EINVAL
+
+
+@pytest.mark.parametrize("change", [dict(row_variant=99), dict(col_variant=-1), dict(slot_ctas=-5),
+                                    dict(reg=1, row_variant=1), dict(reg=1, haar_levels=9)])
+def test_set_tuning_rejects_out_of_range_on_host(ad, change):
+    t = ad.admm_tuning_t(H=512, W=512, reg=0, haar_levels=0, row_variant=0, col_variant=0, slot_ctas=0)
+    for k, v in change.items():
+        setattr(t, k, v)
+    assert ad.lib.admm_deconv_set_tuning(ctypes.byref(t)) == ad.ADMM_EINVAL
+    t = ad.admm_tuning_t(H=500, W=512)
+    assert ad.lib.admm_deconv_set_tuning(ctypes.byref(t)) == ad.ADMM_EUNSUPPORTED_SIZE
+    assert ad.lib.admm_deconv_set_tuning(None) == ad.ADMM_EINVAL
