@@ -125,10 +125,25 @@ struct HaarAnaCfg {
     static constexpr int XA = T + 16;              // stride (16-byte rows); x needs T + HALO columns
     static constexpr int XR = T + HALO;            // rows of x
     static_assert(HALO < 16, "halo fits the 16-column margin");
-    static constexpr int RED_OFF = (2 * XR * XA + 1) & ~1;   // floats, rounded to 8 bytes
+    static constexpr int NBAND = 3 * L + 1;
+    static constexpr int D2S_OFF = 2 * XR * XA;                // floats: previous d2 of the tile, per band
+    static constexpr int RED_OFF = D2S_OFF + NBAND * T * T;
     static_assert((RED_OFF * sizeof(float)) % sizeof(double) == 0, "double alignment");
     static constexpr size_t SMEM = (size_t)RED_OFF * sizeof(float) + 8 * kNumPartials * sizeof(double);
 };
+
+// wait until at most n of this thread's cp.async groups are pending (n
+// folds to a constant where the caller's loop is unrolled)
+__device__ __forceinline__ void cp_async_wait_n(int n) {
+    switch (n) {
+        case 0: cp_async_wait<0>(); break;
+        case 1: cp_async_wait<1>(); break;
+        case 2: cp_async_wait<2>(); break;
+        case 3: cp_async_wait<3>(); break;
+        case 4: cp_async_wait<4>(); break;
+        default: cp_async_wait<5>(); break;
+    }
+}
 
 template <int L>
 __global__ void __launch_bounds__(kThreads)
@@ -148,6 +163,7 @@ haar_analysis(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W, in
     extern __shared__ __align__(16) float sm[];
     float* Ain = sm;
     float* Aout = sm + XR * XA;
+    float* d2s = sm + C::D2S_OFF;
     double* red = reinterpret_cast<double*>(sm + C::RED_OFF);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int tiles_x = W / T;
@@ -166,24 +182,42 @@ haar_analysis(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W, in
         cp_async16(Ain + rr * XA + 4 * ch, src);
     }
     cp_async_commit();
-    // thread (warp, lane) owns the tile pixels (warp + 8 i, lane), i < T / 8
+    // thread (warp, lane) owns the tile pixels (warp + 8 i, lane), i < T / 8.
+    // Every thread stages the previous d2 of its own pixels, one cp.async
+    // group per level (the last with the low-low band), all requested now:
+    // it reads only what it copied itself, so these need no block barrier.
     constexpr int OWN = T / NWARP;
     const size_t gp0 = (size_t)(R0 + warp) * W + (C0 + lane);
-    cp_async_wait<0>();
+#pragma unroll
+    for (int lvl = 0; lvl < L; ++lvl) {
+        if (!first) {
+            const int nb = lvl == L - 1 ? 4 : 3;
+#pragma unroll
+            for (int j = 0; j < nb; ++j) {
+                const int b = 3 * lvl + j;
+#pragma unroll
+                for (int i = 0; i < OWN; ++i)
+                    cp_async4(d2s + b * T * T + (warp + NWARP * i) * T + lane,
+                              d2io + (size_t)b * n + gp0 + (size_t)(NWARP * i) * W);
+            }
+        }
+        cp_async_commit();
+    }
+    cp_async_wait<L>();          // x has landed (the d2 groups may still be in flight)
     __syncthreads();
 
     CompSum l1;
 #pragma unroll
     for (int lvl = 0; lvl < L; ++lvl) {
         const int s = 1 << lvl;
-        // this level's previous d2 at the owned pixels, requested before the
-        // arithmetic that needs it
+        // this level's previous d2 at the owned pixels (staged at entry)
+        cp_async_wait_n(L - 1 - lvl);
         float dold[OWN][3];
 #pragma unroll
         for (int i = 0; i < OWN; ++i)
 #pragma unroll
             for (int j = 0; j < 3; ++j)
-                dold[i][j] = first ? 0.f : d2io[(size_t)(3 * lvl + j) * n + gp0 + (size_t)(NWARP * i) * W];
+                dold[i][j] = first ? 0.f : d2s[(3 * lvl + j) * T * T + (warp + NWARP * i) * T + lane];
         const int D = T + (1 << L) - 2 * s;      // a_{lvl+1} is needed on [0, D)^2
 #pragma unroll
         for (int i = 0; i * NWARP < D; ++i) {
@@ -223,7 +257,7 @@ haar_analysis(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W, in
     {
         float dold[OWN];
 #pragma unroll
-        for (int i = 0; i < OWN; ++i) dold[i] = first ? 0.f : d2io[(size_t)(3 * L) * n + gp0 + (size_t)(NWARP * i) * W];
+        for (int i = 0; i < OWN; ++i) dold[i] = first ? 0.f : d2s[(3 * L) * T * T + (warp + NWARP * i) * T + lane];
 #pragma unroll
         for (int i = 0; i < OWN; ++i) {
             const int rr = warp + NWARP * i;
@@ -440,6 +474,14 @@ inline cudaError_t haar_tile_attributes() {
     e = cudaFuncSetAttribute(haar_synthesis<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)HaarSynCfg<3>::SMEM);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(haar_synthesis<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)HaarSynCfg<4>::SMEM);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(haar_analysis<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)HaarAnaCfg<1>::SMEM);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(haar_analysis<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)HaarAnaCfg<2>::SMEM);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(haar_analysis<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)HaarAnaCfg<3>::SMEM);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(haar_analysis<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)HaarAnaCfg<4>::SMEM);
     if (e != cudaSuccess) return e;
     done = true;
     return cudaSuccess;
