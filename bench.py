@@ -72,6 +72,8 @@ def tune_class(ad, torch, args, size_h, size_w, reg, levels=4):
     trials = cfg.pop("trials", None)
     if trials:
         cfg["trials"] = len(trials)
+        cfg["trial_table"] = [[t["rows_per_strip"], t["walk_depth"], t["row_threads"], t["col_block"],
+                               t["slot_ctas"], round(t["us_per_iter"], 3)] for t in trials]
         cfg["us_per_iter_default"] = next((t["us_per_iter"] for t in trials if t["row_variant"] == 0
                                            and t["col_variant"] == 0 and t["slot_ctas"] == 0), None)
     return cfg

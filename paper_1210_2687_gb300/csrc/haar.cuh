@@ -59,14 +59,30 @@ haar_row_inverse(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp
     float2* buf = smem;
     float2* tw = buf + G * ROW;
     double* red = reinterpret_cast<double*>(tw + W);
+    // per-pixel inputs of the prox (d1, M^T y, x_prev), staged by the thread
+    // that uses them while the transform runs
+    float* pre = reinterpret_cast<float*>(red + 8 * kNumPartials);
     const int tid = threadIdx.x, g = tid / FT, t = tid % FT;
+    const int q = blockIdx.x * G + g;
+    const size_t n = (size_t)H * W;
+    float* pd1 = pre + (size_t)(3 * g) * W;
+    float* pyb = pd1 + W;
+    float* pxp = pyb + W;
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+        const int c = t + m * FT;
+        const size_t pix = (size_t)q * W + c;
+        if (!cold) cp_async4(pd1 + c, P.d1 + pix);
+        cp_async4(pyb + c, P.ybar + pix);
+        if (chk && !first) cp_async4(pxp + c, P.xprev + pix);
+    }
+    cp_async_commit();
     load_twiddles<W>(tw, tw_g, tid, kThreads);
     __syncthreads();
-    const int q = blockIdx.x * G + g;
     float2 v[8];
     load_row_xax<W>(v, P.Sa + (size_t)q * Wp, t);
     fft_group<W, 1>(v, buf + g * ROW, tw, t, g);
-    const size_t n = (size_t)H * W;
+    cp_async_wait<0>();          // this thread's staged inputs have landed
     float* __restrict__ xw = P.work;
     float* __restrict__ z1w = P.work + n;
     const float mu1 = P.mu1, inv1 = P.inv1pmu1;
@@ -77,9 +93,9 @@ haar_row_inverse(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp
         const size_t pix = (size_t)q * W + c;
         const float x = v[m].x, ax = v[m].y;
         // u1 = (M^T M + mu1 I)^{-1} (M^T y + mu1 (A x - d1)); d1 <- d1 - (A x - u1)
-        const float dd1 = cold ? 0.f : P.d1[pix];
+        const float dd1 = cold ? 0.f : pd1[c];
         const float s1 = ax - dd1;
-        const float yb = P.ybar[pix];
+        const float yb = pyb[c];
         const bool obs = is_observed(yb);
         const float u1 = obs ? fmaf(mu1, s1, yb) * inv1 : s1;
         const float nd1 = dd1 - (ax - u1);
@@ -91,7 +107,7 @@ haar_row_inverse(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp
             s_data.add(0.5f * e * e);
         }
         if (chk) {
-            const float dx = first ? x : x - P.xprev[pix];
+            const float dx = first ? x : x - pxp[c];
             s_dxx.add(dx * dx);
             s_xx.add(x * x);
         }
@@ -430,16 +446,17 @@ cudaError_t launch_haar_rows_t(int H, int Wp, const ProbDesc* d, SlotTable sl, i
                                const float2* tw, int* n_active, cudaStream_t s) {
     constexpr int FT = W / 8, G = kThreads / FT;
     const size_t smem_row = (size_t)(G * W + W) * sizeof(float2) + 8 * kNumPartials * sizeof(double);
+    const size_t smem_inv = smem_row + (size_t)3 * G * W * sizeof(float);   // + staged d1, M^T y, x_prev
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(haar_row_inverse<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_row);
+        cudaError_t e = cudaFuncSetAttribute(haar_row_inverse<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_inv);
         if (e != cudaSuccess) return e;
         e = cudaFuncSetAttribute(haar_row_forward<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_row);
         if (e != cudaSuccess) return e;
         attr = true;
     }
     const int nrow = H / G;
-    haar_row_inverse<W><<<dim3(nrow, count), kThreads, smem_row, s>>>(d, sl, H, Wp, tw);
+    haar_row_inverse<W><<<dim3(nrow, count), kThreads, smem_inv, s>>>(d, sl, H, Wp, tw);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const dim3 tgrid(haar_num_tiles(H, W), count);
