@@ -45,7 +45,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--batch", type=int, default=64, help="problems per step per GPU")
+    ap.add_argument("--batch", type=int, default=256, help="problems per step per GPU")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-secondary", action="store_true", help="skip the frame-prior workload")
     ap.add_argument("--frame-only", action="store_true", help="only the frame-prior workload (profiler captures)")
@@ -322,7 +322,7 @@ def frame_secondary(ad, torch, stream, args):
 UNEVEN_COUNT = 256
 
 
-def uneven_secondary(ad, torch, stream, count=UNEVEN_COUNT):
+def uneven_secondary(ad, torch, stream, args, count=UNEVEN_COUNT):
     """Batched uneven workload: ``count`` problems (seed 0) with sides drawn
     from {128, 256, 384 (solved on 512, padding unobserved), 512, 1024},
     box / Gaussian / motion kernels of side 5..25, missing fraction
@@ -333,6 +333,12 @@ def uneven_secondary(ad, torch, stream, count=UNEVEN_COUNT):
     t_gen = time.perf_counter()
     probs = S.config4_batch(0, count)
     t_gen = time.perf_counter() - t_gen
+    # launch configuration of every size class (before the plans are made)
+    tunings = {}
+    for key in sorted({(p.ybar.shape[0], p.reg) for p in probs}):
+        cfg = tune_class(ad, torch, args, key[0], key[0], key[1], 4)
+        tunings[f"{key[0]}_{key[1]}"] = [cfg["rows_per_strip"], cfg["walk_depth"], cfg["row_threads"],
+                                         cfg["col_block"], cfg["slot_ctas"], cfg.get("source")]
     plans, ys, ms, xs = [], [], [], []
     for p in probs:
         N = p.ybar.shape[0]
@@ -379,6 +385,7 @@ def uneven_secondary(ad, torch, stream, count=UNEVEN_COUNT):
         "time_to_tol_ms_p99": float(np.percentile(solve, 99)),
         "isnr_db_mean": float(np.mean(isnr)),
         "input_generation_s": t_gen,
+        "tuning": tunings,
     }
 
 
@@ -483,7 +490,7 @@ def run_ours(args):
         print(json.dumps({"warm_start": warm_secondary(ad, torch, torch.cuda.current_stream())}), flush=True)
         return
     if args.uneven_only:
-        print(json.dumps({"uneven_batch": uneven_secondary(ad, torch, torch.cuda.current_stream())}), flush=True)
+        print(json.dumps({"uneven_batch": uneven_secondary(ad, torch, torch.cuda.current_stream(), args)}), flush=True)
         return
     tune = tune_class(ad, torch, args, H, W, "tv")
     row_kernel, col_kernel = kernel_names(tune, H, W)
@@ -627,7 +634,7 @@ def run_ours(args):
     secondary = None
     if rank == 0 and not args.no_secondary:
         secondary = frame_secondary(ad, torch, stream, args)
-        secondary["uneven_batch"] = uneven_secondary(ad, torch, stream)
+        secondary["uneven_batch"] = uneven_secondary(ad, torch, stream, args)
         secondary["warm_start"] = warm_secondary(ad, torch, stream)
 
     cpu = None
