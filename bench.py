@@ -129,11 +129,12 @@ def bytes_per_pixel_iter():
 
 
 def device_sources_sha256():
-    """Digest of the device-code sources (kernels, FFT, frame prior), which
-    ties a stored ncu traffic figure to the kernels it was measured on."""
+    """Digest of the device-code sources of the TV kernels (iteration
+    kernels, FFT, configuration list), which ties a stored ncu traffic figure
+    to the kernels it was measured on."""
     import hashlib
     h = hashlib.sha256()
-    for f in ("kernels.cuh", "fft.cuh", "haar.cuh", "variants.cuh"):
+    for f in ("kernels.cuh", "fft.cuh", "variants.cuh"):
         with open(os.path.join(ROOT, "paper_1210_2687_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()

@@ -148,18 +148,6 @@ struct HaarAnaCfg {
     static constexpr size_t SMEM = (size_t)RED_OFF * sizeof(float) + 8 * kNumPartials * sizeof(double);
 };
 
-// wait until at most n of this thread's cp.async groups are pending (n
-// folds to a constant where the caller's loop is unrolled)
-__device__ __forceinline__ void cp_async_wait_n(int n) {
-    switch (n) {
-        case 0: cp_async_wait<0>(); break;
-        case 1: cp_async_wait<1>(); break;
-        case 2: cp_async_wait<2>(); break;
-        case 3: cp_async_wait<3>(); break;
-        case 4: cp_async_wait<4>(); break;
-        default: cp_async_wait<5>(); break;
-    }
-}
 
 template <int L>
 __global__ void __launch_bounds__(kThreads)

@@ -143,6 +143,20 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N> __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
+// wait until at most n of this thread's groups are pending (n folds to a
+// constant where the caller's loop is unrolled; larger n wait for more)
+__device__ __forceinline__ void cp_async_wait_n(int n) {
+    switch (n) {
+        case 0: cp_async_wait<0>(); break;
+        case 1: cp_async_wait<1>(); break;
+        case 2: cp_async_wait<2>(); break;
+        case 3: cp_async_wait<3>(); break;
+        case 4: cp_async_wait<4>(); break;
+        case 5: cp_async_wait<5>(); break;
+        case 6: cp_async_wait<6>(); break;
+        default: cp_async_wait<7>(); break;
+    }
+}
 
 // Bulk prefetch of a contiguous global range into L2 (no shared memory and no
 // completion to wait for); `bytes` a multiple of 16, `p` 16-byte aligned.
@@ -558,7 +572,10 @@ row_phase_tv(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp, co
 
     // (0) requests: the walk's rows go to L2 in bulk (they are consumed after
     // the inverse transforms), the half spectra of rows r0-1 .. r0+R into
-    // shared memory, then the first D walk rows into the ring
+    // shared memory, then the first D walk rows into the ring. Each transform
+    // group copies the rows it will transform itself, one cp.async group per
+    // round of transforms, so that a round starts as soon as its own rows
+    // have landed while later rounds are still arriving.
     if (tid == 0) {
         const int qh = (r0 - 1 + H) & (H - 1);
         if (!cold) {
@@ -571,23 +588,35 @@ row_phase_tv(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp, co
         }
         for (int i = 0; i < R; ++i) prefetch_l2(P.ybar + (size_t)(r0 + i) * W, W * sizeof(float));
     }
-    for (int e = tid; e < (R + 2) * C::RAW; e += NT) {
-        const int i = e / C::RAW, kk = e % C::RAW;
-        const int q = (r0 - 1 + i + H) & (H - 1);
-        cp_async16(reinterpret_cast<float4*>(buf + i * C::ROW) + kk, P.Sa + (size_t)q * Wp + kk);
+    const int g = tid / C::FT, t = tid % C::FT;
+    constexpr int NR = (R + 2 + 2 * C::G - 1) / (2 * C::G);      // rounds of inverse transforms
+#pragma unroll
+    for (int rd = 0; rd < NR; ++rd) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int i = g + 2 * C::G * rd + h * C::G;
+            if (i < R + 2) {
+                const int q = (r0 - 1 + i + H) & (H - 1);
+                for (int kk = t; kk < C::RAW; kk += C::FT)
+                    cp_async16(reinterpret_cast<float4*>(buf + i * C::ROW) + kk, P.Sa + (size_t)q * Wp + kk);
+            }
+        }
+        cp_async_commit();
     }
-    cp_async_commit();
 #pragma unroll
     for (int i = 0; i < D; ++i) issue(i);
     load_twiddles<W>(tw, tw_g, tid, NT);
-    cp_async_wait<D>();          // the spectra have landed
-    __syncthreads();
-    const int g = tid / C::FT, t = tid % C::FT;
+    __syncthreads();             // the twiddles
 
     // (1) x + i A x on buffer rows 0..R+1 = image rows r0-1..r0+R: inverse row
     // DFTs, two rows per group at a time (interleaved: twice the independent
     // work between the group's barriers)
-    for (int i = g; i < R + 2; i += 2 * C::G) {
+#pragma unroll 1
+    for (int rd = 0; rd < NR; ++rd) {
+        cp_async_wait_n(NR - 1 - rd + D);   // this round's rows (copied by this group) ...
+        group_sync<W>(g);                   // ... have landed for every thread of the group
+        const int i = g + 2 * C::G * rd;
+        if (i >= R + 2) continue;
         float2* row = buf + i * C::ROW;
         float2 v[8];
         load_row_xax<W>(v, reinterpret_cast<const float4*>(row), t);
