@@ -113,12 +113,15 @@ haar_row_inverse(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp
         }
         if (sprev) P.xprev[pix] = x;
     }
-    const CompSum acc[kNumPartials] = {s_data, CompSum(), s_xx, s_dxx};
-    double pv[kNumPartials];
-    block_reduce_comp(acc, reinterpret_cast<float*>(red), pv);
-    if (tid == 0) {
+    // partial sums only where the tile kernel evaluates the stop rule
+    if (nobj || chk) {
+        const CompSum acc[kNumPartials] = {s_data, CompSum(), s_xx, s_dxx};
+        double pv[kNumPartials];
+        block_reduce_comp(acc, reinterpret_cast<float*>(red), pv);
+        if (tid == 0) {
 #pragma unroll
-        for (int j = 0; j < kNumPartials; ++j) P.partials[blockIdx.x * kNumPartials + j] = pv[j];
+            for (int j = 0; j < kNumPartials; ++j) P.partials[blockIdx.x * kNumPartials + j] = pv[j];
+        }
     }
 }
 
@@ -275,9 +278,11 @@ haar_analysis(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W, in
             if (nobj) l1.add(fabsf(cb));
         }
     }
-    const CompSum acc[kNumPartials] = {CompSum(), l1, CompSum(), CompSum()};
-    double pv[kNumPartials];
-    block_reduce_comp(acc, reinterpret_cast<float*>(red), pv);
+    double pv[kNumPartials] = {0.0, 0.0, 0.0, 0.0};
+    if (nobj || chk) {
+        const CompSum acc[kNumPartials] = {CompSum(), l1, CompSum(), CompSum()};
+        block_reduce_comp(acc, reinterpret_cast<float*>(red), pv);
+    }
     finish_iteration<kThreads>(P, k, chk, nobj, pv, n_active, n_row_ctas + blockIdx.x, probs, sl);
 }
 

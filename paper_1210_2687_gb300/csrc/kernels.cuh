@@ -331,31 +331,12 @@ __device__ __forceinline__ void store_split(float4* __restrict__ drow, const flo
     }
 }
 
-// Block reduction of kNumPartials doubles; result valid in thread 0.
-__device__ __forceinline__ void block_reduce_partials(double (&v)[kNumPartials], double* red) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int j = 0; j < kNumPartials; ++j) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v[j] += __shfl_down_sync(0xffffffffu, v[j], o);
-    }
-    if (lane == 0) {
-#pragma unroll
-        for (int j = 0; j < kNumPartials; ++j) red[warp * kNumPartials + j] = v[j];
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int w = 1; w < kThreads / 32; ++w) {
-#pragma unroll
-            for (int j = 0; j < kNumPartials; ++j) v[j] += red[w * kNumPartials + j];
-        }
-    }
-}
-
 // Block reduction of kNumPartials compensated FP32 sums: the running sums
-// and their compensation terms are reduced separately in FP32 across the
-// block (FP64 arithmetic is slow on this part) and combined in FP64 by
-// thread 0, which receives the block's totals in `out`.
+// and their compensation terms are reduced separately in FP32 within each
+// warp (FP64 arithmetic is slow on this part); across the warps, lane l of
+// warp 0 adds series l (a running sum or a compensation term) in FP64, so
+// the dependent FP64 chain is one add per warp, and thread 0 receives the
+// block's totals (sum + compensation) in `out`.
 template <int NT = kThreads>
 __device__ __forceinline__ void block_reduce_comp(const CompSum (&a)[kNumPartials], float* red,
                                                   double (&out)[kNumPartials]) {
@@ -379,16 +360,15 @@ __device__ __forceinline__ void block_reduce_comp(const CompSum (&a)[kNumPartial
         }
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (warp == 0) {
+        double acc = 0.0;
+        if (lane < 2 * kNumPartials) {
 #pragma unroll
-        for (int j = 0; j < kNumPartials; ++j) {
-            double acc = 0.0, cmp = 0.0;
-            for (int w = 0; w < NT / 32; ++w) {
-                acc += (double)red[w * 2 * kNumPartials + j];
-                cmp += (double)red[w * 2 * kNumPartials + kNumPartials + j];
-            }
-            out[j] = acc + cmp;
+            for (int w = 0; w < NT / 32; ++w) acc += (double)red[w * 2 * kNumPartials + lane];
         }
+        const double tot = acc + __shfl_down_sync(0xffffffffu, acc, kNumPartials);   // lanes j < K
+#pragma unroll
+        for (int j = 0; j < kNumPartials; ++j) out[j] = __shfl_sync(0xffffffffu, tot, j);
     }
 }
 
@@ -405,37 +385,46 @@ __device__ void finish_iteration(const ProbDesc& P, int k, bool chk, bool nobj,
     __shared__ double s_red[NT / 32][kNumPartials];
     ProbCtl* ctl = P.ctl;
     const int tid = threadIdx.x;
+    // the partial sums matter only where the stop rule or the objective is
+    // evaluated; elsewhere the CTAs only count their arrival
+    const bool need = chk || nobj;
     if (tid == 0) {
+        if (need) {
 #pragma unroll
-        for (int j = 0; j < kNumPartials; ++j) P.partials[slot * kNumPartials + j] = v[j];
-        __threadfence();
+            for (int j = 0; j < kNumPartials; ++j) P.partials[slot * kNumPartials + j] = v[j];
+            __threadfence();
+        }
         const unsigned prev = atomicAdd(&ctl->arrive, 1u);
         s_last = prev == (unsigned)(P.n_strips - 1);
     }
     __syncthreads();
     if (!s_last) return;
-    __threadfence();
-    const int nslots = P.n_slots > 0 ? P.n_slots : P.n_strips;
     double acc[kNumPartials] = {0.0, 0.0, 0.0, 0.0};
-    for (int s = tid; s < nslots; s += NT) {
+    if (need) {
+        __threadfence();
+        const int nslots = P.n_slots > 0 ? P.n_slots : P.n_strips;
+        for (int s = tid; s < nslots; s += NT) {
 #pragma unroll
-        for (int j = 0; j < kNumPartials; ++j) acc[j] += __ldcg(P.partials + s * kNumPartials + j);
+            for (int j = 0; j < kNumPartials; ++j) acc[j] += __ldcg(P.partials + s * kNumPartials + j);
+        }
+#pragma unroll
+        for (int j = 0; j < kNumPartials; ++j) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc[j] += __shfl_down_sync(0xffffffffu, acc[j], o);
+        }
+        if ((tid & 31) == 0) {
+#pragma unroll
+            for (int j = 0; j < kNumPartials; ++j) s_red[tid >> 5][j] = acc[j];
+        }
+        __syncthreads();
+        if (tid == 0) {
+            for (int w = 1; w < NT / 32; ++w) {
+#pragma unroll
+                for (int j = 0; j < kNumPartials; ++j) acc[j] += s_red[w][j];
+            }
+        }
     }
-#pragma unroll
-    for (int j = 0; j < kNumPartials; ++j) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc[j] += __shfl_down_sync(0xffffffffu, acc[j], o);
-    }
-    if ((tid & 31) == 0) {
-#pragma unroll
-        for (int j = 0; j < kNumPartials; ++j) s_red[tid >> 5][j] = acc[j];
-    }
-    __syncthreads();
     if (tid != 0) return;
-    for (int w = 1; w < NT / 32; ++w) {
-#pragma unroll
-        for (int j = 0; j < kNumPartials; ++j) acc[j] += s_red[w][j];
-    }
     bool done = false, conv = false;
     if (nobj) {
         const double f = acc[0] + (double)P.lam * acc[1];
@@ -753,9 +742,10 @@ row_phase_tv(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp, co
     cp_async_wait<0>();              // only empty groups remain; nothing left in flight
     __syncthreads();
 
-    // (3) block partial sums (published after the transforms below)
-    double part[kNumPartials];
-    {
+    // (3) block partial sums (published after the transforms below), only
+    // where the stop rule or the objective is evaluated
+    double part[kNumPartials] = {0.0, 0.0, 0.0, 0.0};
+    if (nobj || chk) {
         const CompSum acc[kNumPartials] = {s_data, s_reg, s_xx, s_dxx};
         block_reduce_comp<NT>(acc, reinterpret_cast<float*>(red), part);
     }
