@@ -59,7 +59,7 @@ def parse():
     return ap.parse_args()
 
 
-def tune_class(ad, torch, args, size_h, size_w, reg, levels=4):
+def tune_class(ad, torch, args, size_h, size_w, reg, levels=4, problems=0):
     """Launch configuration of a size class: the autotuner's choice (from the
     tuning cache in the user's cache directory when it holds this GPU and
     class, else measured now and added to it), or the defaults."""
@@ -68,7 +68,7 @@ def tune_class(ad, torch, args, size_h, size_w, reg, levels=4):
         cfg["source"] = "default"
         return cfg
     cfg = ad.autotune_cached(size_h, size_w, reg, levels, path=TUNING_CACHE,
-                             device_name=torch.cuda.get_device_name(), retune=args.retune)
+                             device_name=torch.cuda.get_device_name(), retune=args.retune, problems=problems)
     trials = cfg.pop("trials", None)
     if trials:
         cfg["trials"] = len(trials)
@@ -293,7 +293,7 @@ def frame_secondary(ad, torch, stream, args):
     for size in (1024, 2048):
         p = S.config3_problem(0, size)
         n = size * size
-        tune = tune_class(ad, torch, args, size, size, "haar", 4)
+        tune = tune_class(ad, torch, args, size, size, "haar", 4, problems=1)   # one image per solve
         plan = ad.Plan(size, size, p.psf, p.lam, p.mu1, p.mu2, "haar", stop="iters", max_iters=FRAME_ITERS)
         y = torch.from_numpy(p.ybar.astype(np.float32)).to("cuda")
         m = torch.from_numpy(p.mask).to("cuda")

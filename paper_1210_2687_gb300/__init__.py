@@ -365,19 +365,22 @@ def admm_deconv_autotune(H: int, W: int, reg="tv", levels: int = 4, problems: in
     return best.as_dict(), [trials[i].as_dict() for i in range(min(n.value, cap))]
 
 
-def tuning_cache_key(H: int, W: int, reg="tv", levels: int = 4, device_name: str = "") -> str:
+def tuning_cache_key(H: int, W: int, reg="tv", levels: int = 4, device_name: str = "", problems: int = 0) -> str:
     r = _REG.get(reg, reg)
-    return f"{device_name}|{int(H)}x{int(W)}|{'tv' if r == ADMM_REG_TV else 'haar'}|{0 if r == ADMM_REG_TV else int(levels) or 4}"
+    key = f"{device_name}|{int(H)}x{int(W)}|{'tv' if r == ADMM_REG_TV else 'haar'}|{0 if r == ADMM_REG_TV else int(levels) or 4}"
+    return key + (f"|p{int(problems)}" if problems > 0 else "")
 
 
 def autotune_cached(H: int, W: int, reg="tv", levels: int = 4, path: str | None = None, device_name: str = "",
-                    retune: bool = False, stream=None) -> dict:
+                    retune: bool = False, problems: int = 0, stream=None) -> dict:
     """Install the configuration of the class from the JSON tuning cache at
-    `path` (keyed by device name, size, regulariser and levels), or autotune
-    it and add it to the cache. Returns the installed configuration, with
-    "source": "cache" or "autotune" and, after a tuning run, "trials"."""
+    `path` (keyed by device name, size, regulariser, levels and, when given,
+    the number of problems solved together), or autotune it (with that many
+    problems per trial; 0 = enough to fill the launches) and add it to the
+    cache. Returns the installed configuration, with "source": "cache" or
+    "autotune" and, after a tuning run, "trials"."""
     import json
-    key = tuning_cache_key(H, W, reg, levels, device_name)
+    key = tuning_cache_key(H, W, reg, levels, device_name, problems)
     cache = {}
     if path and os.path.exists(path):
         with open(path) as f:
@@ -388,7 +391,7 @@ def autotune_cached(H: int, W: int, reg="tv", levels: int = 4, path: str | None 
         out["us_per_iter"] = cache[key].get("us_per_iter", 0.0)
         out["source"] = "cache"
         return out
-    best, trials = admm_deconv_autotune(H, W, reg, levels, stream=stream)
+    best, trials = admm_deconv_autotune(H, W, reg, levels, problems=problems, stream=stream)
     if path:
         cache[key] = best
         os.makedirs(os.path.dirname(os.path.abspath(path)), exist_ok=True)
