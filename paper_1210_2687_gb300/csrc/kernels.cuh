@@ -496,7 +496,7 @@ struct RowCfg {
     static constexpr int NWARP = NT / 32;
     static constexpr int CW = W / NWARP;                           // columns per warp
     static constexpr int CPT = CW >= 32 ? CW / 32 : 1;              // columns per thread
-    static constexpr int SLOT = 5 * W + 2 * NWARP;                 // floats per ring slot
+    static constexpr int SLOT = 4 * W + 2 * NWARP;                 // floats per ring slot
     static constexpr int DR = D > 0 ? D : 1;                       // ring slots addressed (D = 0: none used)
     static_assert(RAW * 16 <= ROW * 8, "raw row must fit a buffer row");
     static_assert(R + 2 <= 32, "boundary capture holds one row per lane");
@@ -537,8 +537,9 @@ row_phase_tv(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp, co
     const float2* __restrict__ d2in = reinterpret_cast<const float2*>(P.d2 + ((k + 1) & 1) * P.d2_stride);
     float2* __restrict__ d2out = reinterpret_cast<float2*>(P.d2 + (k & 1) * P.d2_stride);
 
-    // ring slot of walk row i: d2 (float2 per column), d1, M^T y, x_prev, and
-    // per warp the d2 of the pixel left of its chunk
+    // ring slot of walk row i: d2 (float2 per column), d1, M^T y, and per
+    // warp the d2 of the pixel left of its chunk (x_prev, read on check
+    // iterations only, goes through registers one row ahead)
     auto issue = [&](int i) {
         if (D > 0 && i <= R && colthr) {
             const int q = (r0 - 1 + i + H) & (H - 1);
@@ -551,10 +552,9 @@ row_phase_tv(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp, co
                 if (i >= 1) {
                     if (!cold) cp_async4(slot + 2 * W + c, P.d1 + pix);
                     cp_async4(slot + 3 * W + c, P.ybar + pix);
-                    if (chk && !first) cp_async4(slot + 4 * W + c, P.xprev + pix);
                 }
             }
-            if (lane == 0 && !cold) cp_async8(slot + 5 * W + 2 * wid, d2in + (size_t)q * W + chalo);
+            if (lane == 0 && !cold) cp_async8(slot + 4 * W + 2 * wid, d2in + (size_t)q * W + chalo);
         }
         cp_async_commit();   // possibly empty: keeps one group per walk row
     };
@@ -638,11 +638,24 @@ row_phase_tv(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp, co
     const float tau = P.tau, gam = P.gamma, mu1 = P.mu1, inv1 = P.inv1pmu1;
     CompSum s_data, s_reg, s_xx, s_dxx;
     float dvprev[C::CPT];
+    const bool need_xp = chk && !first;
+    float xpn[C::CPT];               // x_prev of the next owned row
 #pragma unroll
-    for (int j = 0; j < C::CPT; ++j) dvprev[j] = 0.f;
+    for (int j = 0; j < C::CPT; ++j) {
+        dvprev[j] = 0.f;
+        xpn[j] = (need_xp && colthr) ? P.xprev[(size_t)r0 * W + cbase + 32 * j] : 0.f;
+    }
     for (int i = 0; i <= R; ++i) {
         const int q = (r0 - 1 + i + H) & (H - 1);
         const bool owned = i >= 1;
+        float xpc[C::CPT];
+#pragma unroll
+        for (int j = 0; j < C::CPT; ++j) xpc[j] = xpn[j];
+        if (need_xp && owned && i < R && colthr) {
+            // requested a row ahead (row q + 1 is still unwritten by this iteration)
+#pragma unroll
+            for (int j = 0; j < C::CPT; ++j) xpn[j] = P.xprev[(size_t)(q + 1) * W + cbase + 32 * j];
+        }
         if (D > 0) cp_async_wait<(D > 0 ? D - 1 : 0)>();   // this thread's copies of walk row i have landed
         const float* slot = ring + (i % C::DR) * C::SLOT;
         const float xr_nb = __shfl_sync(0xffffffffu, xnb_right, i);
@@ -698,7 +711,7 @@ row_phase_tv(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp, co
                         s_reg.add(sqrtf(fmaf(gh, gh, gv * gv)));
                     }
                     if (chk) {
-                        const float dx = first ? x : x - (D > 0 ? slot[4 * W + c] : P.xprev[pix]);
+                        const float dx = first ? x : x - xpc[j];
                         s_dxx.add(dx * dx);
                         s_xx.add(x * x);
                     }
@@ -710,7 +723,7 @@ row_phase_tv(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp, co
                 const float xh = xl_nb;
                 const float xhr = buf[i * C::ROW + swz(wid * C::CW)].x;
                 const float2 dd = cold ? make_float2(0.f, 0.f)
-                                        : (D > 0 ? *reinterpret_cast<const float2*>(slot + 5 * W + 2 * wid)
+                                        : (D > 0 ? *reinterpret_cast<const float2*>(slot + 4 * W + 2 * wid)
                                                  : d2in[(size_t)q * W + chalo]);
                 const float sh = (xhr - xh) - dd.x, sv = (xl_nb_dn - xh) - dd.y;
                 const float sc = fmaxf(0.f, fmaf(-tau, rsqrtf(fmaf(sh, sh, sv * sv)), 1.f));

@@ -8,7 +8,8 @@ namespace admm {
 
 namespace {
 const RowVariant k512[] = {row_variant<512, 8, 1, 128>(), row_variant<512, 8, 0, 128>(),
-                           row_variant<512, 8, 2, 128>(), row_variant<512, 16, 2, 256>()};
+                           row_variant<512, 8, 2, 128>(), row_variant<512, 16, 2, 256>(),
+                           row_variant<512, 16, 3, 256>(), row_variant<512, 16, 4, 256>()};
 }  // namespace
 
 int tv_row_variants_512(const RowVariant** out) {

@@ -7,7 +7,7 @@ namespace admm {
 
 namespace {
 const RowVariant k1024[] = {row_variant<1024, 4, 2, 256>(), row_variant<1024, 8, 1, 256>(),
-                            row_variant<1024, 4, 1, 128>()};
+                            row_variant<1024, 4, 1, 128>(), row_variant<1024, 4, 3, 256>()};
 const RowVariant k2048[] = {row_variant<2048, 4, 1, 256>(), row_variant<2048, 4, 0, 256>(),
                             row_variant<2048, 2, 1, 256>()};
 }  // namespace

@@ -11,7 +11,7 @@ const RowVariant k64[] = {row_variant<64, 16, 4, 256>(), row_variant<64, 16, 2, 
 const RowVariant k128[] = {row_variant<128, 16, 4, 256>(), row_variant<128, 16, 2, 128>(),
                            row_variant<128, 8, 2, 128>()};
 const RowVariant k256[] = {row_variant<256, 8, 4, 256>(), row_variant<256, 8, 2, 128>(),
-                           row_variant<256, 16, 2, 256>()};
+                           row_variant<256, 16, 2, 256>(), row_variant<256, 16, 4, 256>()};
 }  // namespace
 
 int tv_row_variants_small(int W, const RowVariant** out) {
