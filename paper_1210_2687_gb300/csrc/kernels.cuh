@@ -634,11 +634,7 @@ row_phase_tv(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp, co
     }
     __syncthreads();             // nobody overwrites a row before every warp captured
 
-    // (2) proxes and dual updates, each warp walking down its columns. With
-    // two or more ring slots the walk takes two rows per step: both rows'
-    // proxes are independent (row i + 1 reads x of rows i + 1 and i + 2, not
-    // the p written back to row i), which doubles the work between the
-    // step's ring wait and warp barrier.
+    // (2) proxes and dual updates, each warp walking down its columns
     const float tau = P.tau, gam = P.gamma, mu1 = P.mu1, inv1 = P.inv1pmu1;
     CompSum s_data, s_reg, s_xx, s_dxx;
     float dvprev[C::CPT];
@@ -649,15 +645,9 @@ row_phase_tv(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp, co
         dvprev[j] = 0.f;
         xpn[j] = (need_xp && colthr) ? P.xprev[(size_t)r0 * W + cbase + 32 * j] : 0.f;
     }
-    // walk row i: v-soft and d2 update for every pixel of the row (the halo
-    // row i = 0 only for its delta_v), mask prox and d1 update on owned rows;
-    // returns delta = u2 + d2 and zeta1 = u1 + d1 of the thread's columns and,
-    // in lane 0, delta_h of the pixel left of the warp's chunk
-    auto walk_row = [&](int i, float (&dhcur)[C::CPT], float (&dvcur)[C::CPT], float (&z1cur)[C::CPT],
-                        float& dh_halo) {
+    for (int i = 0; i <= R; ++i) {
         const int q = (r0 - 1 + i + H) & (H - 1);
         const bool owned = i >= 1;
-        const float* slot = ring + (i % C::DR) * C::SLOT;
         float xpc[C::CPT];
 #pragma unroll
         for (int j = 0; j < C::CPT; ++j) xpc[j] = xpn[j];
@@ -666,119 +656,101 @@ row_phase_tv(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp, co
 #pragma unroll
             for (int j = 0; j < C::CPT; ++j) xpn[j] = P.xprev[(size_t)(q + 1) * W + cbase + 32 * j];
         }
+        if (D > 0) cp_async_wait<(D > 0 ? D - 1 : 0)>();   // this thread's copies of walk row i have landed
+        const float* slot = ring + (i % C::DR) * C::SLOT;
         const float xr_nb = __shfl_sync(0xffffffffu, xnb_right, i);
         const float xl_nb = __shfl_sync(0xffffffffu, xnb_left, i);
         const float xl_nb_dn = __shfl_sync(0xffffffffu, xnb_left, i + 1);
+        float dhcur[C::CPT], dvcur[C::CPT], z1cur[C::CPT];
 #pragma unroll
         for (int j = 0; j < C::CPT; ++j) dhcur[j] = dvcur[j] = z1cur[j] = 0.f;
-        dh_halo = 0.f;
-        if (!colthr) return;
+        float dh_halo = 0.f;
+        if (colthr) {
 #pragma unroll
-        for (int j = 0; j < C::CPT; ++j) {
-            const int c = cbase + 32 * j;
-            const float2 z = buf[i * C::ROW + swz(c)];
-            const float x = z.x, ax = z.y;
-            const bool last_col = (lane == C::CW - 1 || lane == 31) && j == C::CPT - 1;
-            const float xr = last_col ? xr_nb : buf[i * C::ROW + swz(c + 1)].x;
-            const float xd = buf[(i + 1) * C::ROW + swz(c)].x;
-            // D_i x (forward periodic differences)
-            const float gh = xr - x, gv = xd - x;
-            const size_t pix = (size_t)q * W + c;
-            const float2 dd = cold ? make_float2(0.f, 0.f)
-                                   : (D > 0 ? *reinterpret_cast<const float2*>(slot + 2 * c) : d2in[pix]);
-            // u2 = v-soft(D_i x - d2, lambda/mu2)  (Alg. 3 line 10, 0/0 = 0):
-            // the scale max(0, 1 - tau / |s|), with one reciprocal square
-            // root (|s| = 0 gives -inf inside the max, so 0)
-            const float sh = gh - dd.x, sv = gv - dd.y;
-            const float sc = fmaxf(0.f, fmaf(-tau, rsqrtf(fmaf(sh, sh, sv * sv)), 1.f));
-            const float uh = sc * sh, uv = sc * sv;
-            // d2 <- d2 - (D_i x - u2)  (Alg. 3 line 11)
-            const float nh = uh - sh, nv = uv - sv;
-            // delta = u2 + d2 for the next x-step (Alg. 3 lines 3-5)
-            dhcur[j] = uh + nh;
-            dvcur[j] = uv + nv;
-            if (owned) {
-                d2out[pix] = make_float2(nh, nv);
-                // u1 = (M^T M + mu1 I)^{-1} (M^T y + mu1 (A x - d1))  (eq. new_line)
-                const float dd1 = cold ? 0.f : (D > 0 ? slot[2 * W + c] : P.d1[pix]);
-                const float yb = D > 0 ? slot[3 * W + c] : P.ybar[pix];
-                const float s1 = ax - dd1;
-                const bool obs = is_observed(yb);
-                const float u1 = obs ? fmaf(mu1, s1, yb) * inv1 : s1;
-                // d1 <- d1 - (A x - u1)  (Alg. 3 line 8)
-                const float nd1 = dd1 - (ax - u1);
-                P.d1[pix] = nd1;
-                z1cur[j] = u1 + nd1;
-                if (nobj) {
-                    if (obs) {
-                        const float e = ax - yb;
-                        s_data.add(0.5f * e * e);
+            for (int j = 0; j < C::CPT; ++j) {
+                const int c = cbase + 32 * j;
+                const float2 z = buf[i * C::ROW + swz(c)];
+                const float x = z.x, ax = z.y;
+                const bool last_col = (lane == C::CW - 1 || lane == 31) && j == C::CPT - 1;
+                const float xr = last_col ? xr_nb : buf[i * C::ROW + swz(c + 1)].x;
+                const float xd = buf[(i + 1) * C::ROW + swz(c)].x;
+                // D_i x (forward periodic differences)
+                const float gh = xr - x, gv = xd - x;
+                const size_t pix = (size_t)q * W + c;
+                const float2 dd = cold ? make_float2(0.f, 0.f)
+                                       : (D > 0 ? *reinterpret_cast<const float2*>(slot + 2 * c) : d2in[pix]);
+                // u2 = v-soft(D_i x - d2, lambda/mu2)  (Alg. 3 line 10, 0/0 = 0):
+                // the scale max(0, 1 - tau / |s|), with one reciprocal square
+                // root (|s| = 0 gives -inf inside the max, so 0)
+                const float sh = gh - dd.x, sv = gv - dd.y;
+                const float sc = fmaxf(0.f, fmaf(-tau, rsqrtf(fmaf(sh, sh, sv * sv)), 1.f));
+                const float uh = sc * sh, uv = sc * sv;
+                // d2 <- d2 - (D_i x - u2)  (Alg. 3 line 11)
+                const float nh = uh - sh, nv = uv - sv;
+                // delta = u2 + d2 for the next x-step (Alg. 3 lines 3-5)
+                dhcur[j] = uh + nh;
+                dvcur[j] = uv + nv;
+                z1cur[j] = 0.f;
+                if (owned) {
+                    d2out[pix] = make_float2(nh, nv);
+                    // u1 = (M^T M + mu1 I)^{-1} (M^T y + mu1 (A x - d1))  (eq. new_line)
+                    const float dd1 = cold ? 0.f : (D > 0 ? slot[2 * W + c] : P.d1[pix]);
+                    const float yb = D > 0 ? slot[3 * W + c] : P.ybar[pix];
+                    const float s1 = ax - dd1;
+                    const bool obs = is_observed(yb);
+                    const float u1 = obs ? fmaf(mu1, s1, yb) * inv1 : s1;
+                    // d1 <- d1 - (A x - u1)  (Alg. 3 line 8)
+                    const float nd1 = dd1 - (ax - u1);
+                    P.d1[pix] = nd1;
+                    z1cur[j] = u1 + nd1;
+                    if (nobj) {
+                        if (obs) {
+                            const float e = ax - yb;
+                            s_data.add(0.5f * e * e);
+                        }
+                        s_reg.add(sqrtf(fmaf(gh, gh, gv * gv)));
                     }
-                    s_reg.add(sqrtf(fmaf(gh, gh, gv * gv)));
+                    if (chk) {
+                        const float dx = first ? x : x - xpc[j];
+                        s_dxx.add(dx * dx);
+                        s_xx.add(x * x);
+                    }
+                    if (sprev) P.xprev[pix] = x;
                 }
-                if (chk) {
-                    const float dx = first ? x : x - xpc[j];
-                    s_dxx.add(dx * dx);
-                    s_xx.add(x * x);
-                }
-                if (sprev) P.xprev[pix] = x;
+            }
+            if (lane == 0 && owned) {
+                // delta_h of the pixel left of the chunk (its owner updates its d2)
+                const float xh = xl_nb;
+                const float xhr = buf[i * C::ROW + swz(wid * C::CW)].x;
+                const float2 dd = cold ? make_float2(0.f, 0.f)
+                                        : (D > 0 ? *reinterpret_cast<const float2*>(slot + 4 * W + 2 * wid)
+                                                 : d2in[(size_t)q * W + chalo]);
+                const float sh = (xhr - xh) - dd.x, sv = (xl_nb_dn - xh) - dd.y;
+                const float sc = fmaxf(0.f, fmaf(-tau, rsqrtf(fmaf(sh, sh, sv * sv)), 1.f));
+                dh_halo = 2.f * sc * sh - sh;
             }
         }
-        if (lane == 0 && owned) {
-            // delta_h of the pixel left of the chunk (its owner updates its d2)
-            const float xh = xl_nb;
-            const float xhr = buf[i * C::ROW + swz(wid * C::CW)].x;
-            const float2 dd = cold ? make_float2(0.f, 0.f)
-                                   : (D > 0 ? *reinterpret_cast<const float2*>(slot + 4 * W + 2 * wid)
-                                            : d2in[(size_t)q * W + chalo]);
-            const float sh = (xhr - xh) - dd.x, sv = (xl_nb_dn - xh) - dd.y;
-            const float sc = fmaxf(0.f, fmaf(-tau, rsqrtf(fmaf(sh, sh, sv * sv)), 1.f));
-            dh_halo = 2.f * sc * sh - sh;
-        }
-    };
-    // left neighbours' delta_h within the warp
-    auto left_dh = [&](const float (&dhcur)[C::CPT], float dh_halo, float (&dhl)[C::CPT]) {
+        issue(i + D);                // slot (i % D) is consumed: refill it D rows ahead
+        // left neighbours' delta_h within the warp
+        float dhl[C::CPT];
 #pragma unroll
         for (int j = 0; j < C::CPT; ++j) {
             const float up = __shfl_up_sync(0xffffffffu, dhcur[j], 1);
             const float wrap = j > 0 ? __shfl_sync(0xffffffffu, dhcur[j > 0 ? j - 1 : 0], 31) : dh_halo;
             dhl[j] = lane == 0 ? wrap : up;
         }
-    };
-    // w = gamma (Dh^T delta_h + Dv^T delta_v) (adjoint of forward differences)
-    // and p = zeta1 + i w written back over row i
-    auto write_p = [&](int i, const float (&dhl)[C::CPT], const float (&dhcur)[C::CPT], const float (&dvup)[C::CPT],
-                       const float (&dvcur)[C::CPT], const float (&z1cur)[C::CPT]) {
+        __syncwarp();                // every lane has read row i before it is overwritten
+        if (owned && colthr) {
+            // w = gamma (Dh^T delta_h + Dv^T delta_v): adjoint of forward differences
 #pragma unroll
-        for (int j = 0; j < C::CPT; ++j) {
-            const int c = cbase + 32 * j;
-            const float w = gam * ((dhl[j] - dhcur[j]) + (dvup[j] - dvcur[j]));
-            buf[i * C::ROW + swz(c)] = make_float2(z1cur[j], w);
-        }
-    };
-    constexpr int STEP = D >= 2 ? 2 : 1;
-    for (int i = 0; i <= R; i += STEP) {
-        const bool two = STEP == 2 && i + 1 <= R;
-        // this thread's copies of walk rows i (and i + 1) have landed
-        if (STEP == 2) cp_async_wait<(D >= 2 ? D - 2 : 0)>();
-        else if (D > 0) cp_async_wait<(D > 0 ? D - 1 : 0)>();
-        float dhA[C::CPT], dvA[C::CPT], z1A[C::CPT], hA;
-        float dhB[C::CPT], dvB[C::CPT], z1B[C::CPT], hB = 0.f;
-        walk_row(i, dhA, dvA, z1A, hA);
-        if (two) walk_row(i + 1, dhB, dvB, z1B, hB);
-        // the consumed slots are refilled D rows ahead
-        issue(i + D);
-        if (STEP == 2) issue(i + D + 1);
-        float dhlA[C::CPT], dhlB[C::CPT];
-        left_dh(dhA, hA, dhlA);
-        if (two) left_dh(dhB, hB, dhlB);
-        __syncwarp();                // every lane has read rows i, i + 1 before they are overwritten
-        if (colthr) {
-            if (i >= 1) write_p(i, dhlA, dhA, dvprev, dvA, z1A);
-            if (two) write_p(i + 1, dhlB, dhB, dvA, dvB, z1B);
+            for (int j = 0; j < C::CPT; ++j) {
+                const int c = cbase + 32 * j;
+                const float w = gam * ((dhl[j] - dhcur[j]) + (dvprev[j] - dvcur[j]));
+                buf[i * C::ROW + swz(c)] = make_float2(z1cur[j], w);
+            }
         }
 #pragma unroll
-        for (int j = 0; j < C::CPT; ++j) dvprev[j] = two ? dvB[j] : dvA[j];
+        for (int j = 0; j < C::CPT; ++j) dvprev[j] = dvcur[j];
     }
     cp_async_wait<0>();              // only empty groups remain; nothing left in flight
     __syncthreads();
