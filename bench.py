@@ -73,7 +73,7 @@ def tune_class(ad, torch, args, size_h, size_w, reg, levels=4, problems=0):
     if trials:
         cfg["trials"] = len(trials)
         cfg["trial_table"] = [[t["rows_per_strip"], t["walk_depth"], t["row_threads"], t["col_block"],
-                               t["slot_ctas"], round(t["us_per_iter"], 3)] for t in trials]
+                               t["col_min_ctas"], t["slot_ctas"], round(t["us_per_iter"], 3)] for t in trials]
         cfg["us_per_iter_default"] = next((t["us_per_iter"] for t in trials if t["row_variant"] == 0
                                            and t["col_variant"] == 0 and t["slot_ctas"] == 0), None)
     return cfg
@@ -81,8 +81,9 @@ def tune_class(ad, torch, args, size_h, size_w, reg, levels=4, problems=0):
 
 def kernel_names(cfg, size_h, size_w):
     """Names of the TV row-phase and column-phase kernels of a configuration."""
+    mb = f",{cfg['col_min_ctas']}" if cfg.get("col_min_ctas") else ""
     return (f"row_phase_tv<{size_w},{cfg['rows_per_strip']},{cfg['walk_depth']},{cfg['row_threads']}>",
-            f"col_phase<{size_h},{cfg['col_block']}>")
+            f"col_phase<{size_h},{cfg['col_block']}{mb}>")
 
 
 def dist_env():

@@ -6,12 +6,15 @@
 namespace admm {
 
 namespace {
-const ColVariant c64[] = {col_variant<64, 32>(), col_variant<64, 64>()};
-const ColVariant c128[] = {col_variant<128, 16>(), col_variant<128, 32>()};
-const ColVariant c256[] = {col_variant<256, 8>(), col_variant<256, 16>()};
-const ColVariant c512[] = {col_variant<512, 4>(), col_variant<512, 8>()};
-const ColVariant c1024[] = {col_variant<1024, 4>(), col_variant<1024, 2>(), col_variant<1024, 8>()};
-const ColVariant c2048[] = {col_variant<2048, 2>(), col_variant<2048, 1>(), col_variant<2048, 4>()};
+// (the third template argument: registers sized for that many CTAs per SM)
+const ColVariant c64[] = {col_variant<64, 32>(), col_variant<64, 64>(), col_variant<64, 32, 3>()};
+const ColVariant c128[] = {col_variant<128, 16>(), col_variant<128, 32>(), col_variant<128, 16, 3>()};
+const ColVariant c256[] = {col_variant<256, 8>(), col_variant<256, 16>(), col_variant<256, 8, 3>()};
+const ColVariant c512[] = {col_variant<512, 4>(), col_variant<512, 8>(), col_variant<512, 4, 3>()};
+const ColVariant c1024[] = {col_variant<1024, 4>(), col_variant<1024, 2>(), col_variant<1024, 8>(),
+                            col_variant<1024, 2, 3>()};
+const ColVariant c2048[] = {col_variant<2048, 2>(), col_variant<2048, 1>(), col_variant<2048, 4>(),
+                            col_variant<2048, 1, 3>()};
 template <int N>
 int take(const ColVariant (&t)[N], const ColVariant** out) {
     *out = t;

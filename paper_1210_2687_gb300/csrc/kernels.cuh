@@ -204,8 +204,9 @@ __device__ __forceinline__ int tile_slot(int r, int c) {
     constexpr int SH = CB >= 8 ? 0 : (CB == 4 ? 1 : (CB == 2 ? 2 : 3));
     return r * CB + ((c + (r >> SH)) & (CB - 1));
 }
-template <int H, int CB>
-__global__ void __launch_bounds__(kThreads, ColCfg<H, CB>::MINB)
+// MB > 0 overrides the CTAs per SM that the registers are sized for
+template <int H, int CB, int MB = 0>
+__global__ void __launch_bounds__(kThreads, (MB > 0 ? MB : ColCfg<H, CB>::MINB))
 col_phase(const ProbDesc* __restrict__ probs, SlotTable sl, int Wc, int Wp, const float2* __restrict__ tw_g) {
     using C = ColCfg<H, CB>;
     const int pi = sl.map[blockIdx.y];

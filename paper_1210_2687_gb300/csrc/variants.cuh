@@ -25,6 +25,7 @@ struct RowVariant {
 };
 struct ColVariant {
     int CB;
+    int MB;   // CTAs per SM the registers are sized for (0: the default of the block)
     ColLaunchFn fn;
 };
 
@@ -54,18 +55,19 @@ cudaError_t launch_row_tv_t(const ProbDesc* d, SlotTable sl, int count, int H, i
     return cudaGetLastError();
 }
 
-template <int H, int CB>
+template <int H, int CB, int MB>
 cudaError_t launch_col_t(const ProbDesc* d, SlotTable sl, int count, int Wc, int Wp, const float2* tw,
                          cudaStream_t s) {
     static bool attr = false;
     const size_t smem = ColCfg<H, CB>::SMEM;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(col_phase<H, CB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(col_phase<H, CB, MB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
         if (e != cudaSuccess) return e;
         attr = true;
     }
     dim3 grid(Wp / CB, count);
-    col_phase<H, CB><<<grid, kThreads, smem, s>>>(d, sl, Wc, Wp, tw);
+    col_phase<H, CB, MB><<<grid, kThreads, smem, s>>>(d, sl, Wc, Wp, tw);
     return cudaGetLastError();
 }
 
@@ -73,9 +75,10 @@ template <int W, int R, int D, int NT>
 constexpr RowVariant row_variant() {
     return RowVariant{R, D, NT, &launch_row_tv_t<W, R, D, NT>};
 }
-template <int H, int CB>
+// MB > 0: registers sized for MB CTAs per SM instead of the default
+template <int H, int CB, int MB = 0>
 constexpr ColVariant col_variant() {
-    return ColVariant{CB, &launch_col_t<H, CB>};
+    return ColVariant{CB, MB, &launch_col_t<H, CB, MB>};
 }
 
 }  // namespace admm

@@ -118,7 +118,7 @@ def test_autotune_installs_the_fastest_trial(ad):
         assert all(t["us_per_iter"] > 0 for t in trials)
         assert best["us_per_iter"] == min(t["us_per_iter"] for t in trials)
         cfg = ad.admm_deconv_get_tuning(H, W, "tv")
-        for k in ("row_variant", "col_variant", "slot_ctas", "rows_per_strip", "col_block"):
+        for k in ("row_variant", "col_variant", "slot_ctas", "rows_per_strip", "col_block", "col_min_ctas"):
             assert cfg[k] == best[k], k
         # a plan made now runs the tuned configuration and still matches the oracle
         psf, ybar, mask = _problem(H, W, 99)
