@@ -73,9 +73,10 @@ def tune_class(ad, torch, args, size_h, size_w, reg, levels=4, problems=0):
     if trials:
         cfg["trials"] = len(trials)
         cfg["trial_table"] = [[t["rows_per_strip"], t["walk_depth"], t["row_threads"], t["col_block"],
-                               t["col_min_ctas"], t["slot_ctas"], round(t["us_per_iter"], 3)] for t in trials]
+                               t["col_min_ctas"], t["slot_ctas"], t["lanes"], round(t["us_per_iter"], 3)] for t in trials]
         cfg["us_per_iter_default"] = next((t["us_per_iter"] for t in trials if t["row_variant"] == 0
-                                           and t["col_variant"] == 0 and t["slot_ctas"] == 0), None)
+                                           and t["col_variant"] == 0 and t["slot_ctas"] == 0
+                                           and t["lanes"] == 0), None)
     return cfg
 
 

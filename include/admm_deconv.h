@@ -230,6 +230,8 @@ typedef struct {
     int    row_variant;     /* index of the TV row-phase configuration of W (0 for Haar)     */
     int    col_variant;     /* index of the column-phase configuration of H                  */
     int    slot_ctas;       /* row-side CTAs per launch aimed for (0 = default 2400)         */
+    int    lanes;           /* independent lanes (graph branches) the class's problems and
+                               slots are split into, 1..4 (0 = default 2)                     */
     int    rows_per_strip;  /* [out] meaning of row_variant: rows per row-phase CTA, ...     */
     int    walk_depth;      /* [out] ... walk rows in flight (0 = read directly), ...        */
     int    row_threads;     /* [out] ... threads per row-phase CTA                           */
@@ -268,7 +270,8 @@ ADMM_API int admm_deconv_set_tuning(const admm_tuning_t* t);
 /*
  * admm_deconv_autotune -- time every combination of the class's compiled
  * configurations and slot targets {default 2400, 1200, 4800} on the current
- * device and install the fastest. Each trial creates `problems` plans of the
+ * device, then 1 and 4 lanes for the fastest of those, and install the
+ * fastest. Each trial creates `problems` plans of the
  * class on a synthetic observation (9 x 9 box blur, valid-region mask, rel-x
  * rule with tolerance 0 checked every 10 iterations, so no problem retires
  * early), runs `iters` iterations of all of them once to warm up and once

@@ -84,6 +84,7 @@ class admm_profile_t(ctypes.Structure):
 class admm_tuning_t(ctypes.Structure):
     _fields_ = [("H", ctypes.c_int), ("W", ctypes.c_int), ("reg", ctypes.c_int), ("haar_levels", ctypes.c_int),
                 ("row_variant", ctypes.c_int), ("col_variant", ctypes.c_int), ("slot_ctas", ctypes.c_int),
+                ("lanes", ctypes.c_int),
                 ("rows_per_strip", ctypes.c_int), ("walk_depth", ctypes.c_int), ("row_threads", ctypes.c_int),
                 ("col_block", ctypes.c_int), ("col_min_ctas", ctypes.c_int), ("us_per_iter", ctypes.c_double)]
 
@@ -355,7 +356,7 @@ def admm_deconv_autotune(H: int, W: int, reg="tv", levels: int = 4, problems: in
     """Time every compiled configuration of the class on the current device
     and install the fastest; returns (best, all trials)."""
     nr, nc = admm_deconv_variants(H, W, reg)
-    cap = nr * nc * 3
+    cap = nr * nc * 3 + 2
     trials = (admm_tuning_t * cap)()
     n = ctypes.c_int()
     best = admm_tuning_t()

@@ -35,7 +35,7 @@ struct admm_plan_s {
     std::vector<float> psf;
     int device = 0;
     int Wc = 0, Wp = 0, cb = 0, R = 0, n_strips = 0, n_slots = 0, nb = 0, levels = 0;
-    int row_v = 0, col_v = 0, slot_ctas = 0;   // launch configuration (tuning table at plan time)
+    int row_v = 0, col_v = 0, slot_ctas = 0, lanes = 0;   // launch configuration (tuning table at plan time)
     float lam = 0.f, mu1 = 0.f, mu2 = 0.f;
     void* slab = nullptr;
     float4* Sa = nullptr;
@@ -90,9 +90,11 @@ struct DeviceCtx {
 // slots [soff[l], soff[l] + slots[l]). In a replayed chunk the lanes are
 // independent graph branches, so one lane's column phase (transform-bound)
 // can share the GPU with the other lane's row phase (memory-bound).
+constexpr int kMaxLanes = 4;
+constexpr int kDefaultLanes = 2;
 struct Lanes {
     int n = 1;
-    int off[2] = {0, 0}, cnt[2] = {0, 0}, soff[2] = {0, 0}, slots[2] = {0, 0};
+    int off[kMaxLanes] = {}, cnt[kMaxLanes] = {}, soff[kMaxLanes] = {}, slots[kMaxLanes] = {};
 };
 std::map<int, DeviceCtx> g_ctx;
 
@@ -170,7 +172,7 @@ int ensure_ctx(int dev, int count, DeviceCtx** out) {
         c.cap = 0;
         CK(cudaMalloc(&c.desc, cap * sizeof(ProbDesc)));
         CK(cudaMalloc(&c.slot_map, cap * sizeof(int)));
-        CK(cudaMalloc(&c.queue, 2 * cap * sizeof(int)));   // two lanes per size class at most
+        CK(cudaMalloc(&c.queue, kMaxLanes * cap * sizeof(int)));   // one word per lane
         CK(cudaMalloc(&c.xptr, cap * sizeof(float*)));
         CK(cudaMalloc(&c.n_active, cap * sizeof(int)));
         CK(cudaHostAlloc(&c.h_active, 2 * cap * sizeof(int), cudaHostAllocDefault));
@@ -244,7 +246,7 @@ bool describe_tuning(admm_tuning_t* t) {
         t->walk_depth = 0;
         t->row_threads = kThreads;
     }
-    if (t->slot_ctas < 0) return false;
+    if (t->slot_ctas < 0 || t->lanes < 0 || t->lanes > kMaxLanes) return false;
     return true;
 }
 
@@ -417,6 +419,7 @@ int admm_deconv_plan(admm_plan_t* out, const admm_params_t* p, void* stream) {
         pl->col_v = tu.col_variant;
         pl->row_v = tu.row_variant;
         pl->slot_ctas = tu.slot_ctas;
+        pl->lanes = tu.lanes;
         pl->cb = cv[pl->col_v].CB;
     }
     pl->Wp = (int)align_up(pl->Wc, pl->cb);
@@ -568,7 +571,7 @@ struct GroupRun {
     bool tv = true;
     int off = 0, count = 0, nslots = 0, max_iters = 0, qbase = 0;
     int gi = 0;                  // index of the class's n_active counter
-    int R = 0, row_v = 0, col_v = 0, slot_ctas = 0;
+    int R = 0, row_v = 0, col_v = 0, slot_ctas = 0, lanes = 0;
     RowLaunchFn row_fn = nullptr;  // TV row phase of the class's configuration
     ColLaunchFn col_fn = nullptr;
     long long launch_cap = 0;    // iterations after which every problem has retired
@@ -683,6 +686,7 @@ static int solve_all(DeviceCtx* ctx, const std::vector<std::vector<int>>& classe
         g.row_v = p0->row_v;
         g.col_v = p0->col_v;
         g.slot_ctas = p0->slot_ctas;
+        g.lanes = p0->lanes;
         {
             const ColVariant* cv = nullptr;
             col_variants(g.H, &cv);
@@ -726,12 +730,12 @@ static int solve_all(DeviceCtx* ctx, const std::vector<std::vector<int>>& classe
         g.nslots = choose_slots(g.H, g.W, g.tv, g.R, g.slot_ctas, g.count);
         // with per-phase timing on, one lane: every launch covers all slots,
         // so the timed phases are the full-size kernels
-        g.L.n = (!prof && g.count >= 2 && g.nslots >= 2) ? 2 : 1;
+        g.L.n = prof ? 1 : std::max(1, std::min({g.lanes > 0 ? g.lanes : kDefaultLanes, g.count, g.nslots}));
         for (int l = 0, o = g.off, so = soff; l < g.L.n; ++l) {
             g.L.off[l] = o;
-            g.L.cnt[l] = l + 1 < g.L.n ? g.count / 2 : g.off + g.count - o;
+            g.L.cnt[l] = l + 1 < g.L.n ? g.count / g.L.n : g.off + g.count - o;
             g.L.soff[l] = so;
-            g.L.slots[l] = l + 1 < g.L.n ? g.nslots / 2 : soff + g.nslots - so;
+            g.L.slots[l] = l + 1 < g.L.n ? g.nslots / g.L.n : soff + g.nslots - so;
             o += g.L.cnt[l];
             so += g.L.slots[l];
         }
@@ -763,7 +767,9 @@ static int solve_all(DeviceCtx* ctx, const std::vector<std::vector<int>>& classe
     for (GroupRun& g : groups) {
         long long work = 0;
         for (int t = g.off; t < g.off + g.count; ++t) work += plans[order[t]]->p.max_iters;
-        const int min_slots = std::max(1, std::min(g.L.slots[0], g.L.slots[g.L.n - 1]));
+        int min_slots = g.L.slots[0];
+        for (int l = 1; l < g.L.n; ++l) min_slots = std::min(min_slots, g.L.slots[l]);
+        min_slots = std::max(1, min_slots);
         g.launch_cap = std::min((work + min_slots - 1) / min_slots + g.max_iters, (long long)INT32_MAX);
     }
     // classes still iterating; a class leaves once the host has seen its
@@ -899,10 +905,11 @@ int admm_deconv_solve_batch(const admm_plan_t* plans, int count, const float* co
     if (rc != ADMM_OK) return rc;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     // a size class shares its shape and its launch configuration
-    std::map<std::tuple<int, int, int, int, int, int, int>, std::vector<int>> groups;
+    std::map<std::tuple<int, int, int, int, int, int, int, int>, std::vector<int>> groups;
     for (int i = 0; i < count; ++i) {
         const admm_plan_s* p = plans[i];
-        groups[std::make_tuple(p->p.H, p->p.W, p->p.reg, p->levels, p->row_v, p->col_v, p->slot_ctas)].push_back(i);
+        groups[std::make_tuple(p->p.H, p->p.W, p->p.reg, p->levels, p->row_v, p->col_v, p->slot_ctas, p->lanes)]
+            .push_back(i);
     }
     std::vector<std::vector<int>> classes;
     for (auto& kv : groups) classes.push_back(kv.second);
@@ -1070,6 +1077,39 @@ int admm_deconv_autotune(int H, int W, int reg, int haar_levels, int problems, i
         std::vector<const float*> ys(problems, dy);
         std::vector<float*> xs(problems);
         for (int i = 0; i < problems; ++i) xs[i] = dx + (size_t)i * n;
+        // one timed trial of configuration t (installed for the class while it runs)
+        auto trial = [&](admm_tuning_t t) -> int {
+            describe_tuning(&t);
+            {
+                std::lock_guard<std::mutex> lk(g_mutex);
+                g_tuning[TuneKey(dev, H, W, reg, levels)] = t;
+            }
+            pls.assign(problems, nullptr);
+            int r = ADMM_OK;
+            for (int i = 0; i < problems && r == ADMM_OK; ++i) r = admm_deconv_plan(&pls[i], &p, stream);
+            float ms = 0.f;
+            if (r == ADMM_OK)   // warm-up: kernel attributes, graph capture
+                r = admm_deconv_solve_batch(pls.data(), problems, ys.data(), nullptr, xs.data(), nullptr, stream);
+            if (r == ADMM_OK) {
+                if (cudaEventRecord(e0, s) != cudaSuccess) r = ADMM_ECUDA;
+                if (r == ADMM_OK)
+                    r = admm_deconv_solve_batch(pls.data(), problems, ys.data(), nullptr, xs.data(), nullptr, stream);
+                if (r == ADMM_OK && (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                                     cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+                    r = ADMM_ECUDA;
+            }
+            for (admm_plan_t q : pls) admm_deconv_destroy(q);
+            pls.clear();
+            if (r != ADMM_OK) return r;
+            t.us_per_iter = (double)ms * 1e3 / ((double)problems * (double)iters);
+            if (count < max_trials) trials[count] = t;
+            ++count;
+            if (!have_win || t.us_per_iter < win.us_per_iter) {
+                win = t;
+                have_win = true;
+            }
+            return ADMM_OK;
+        };
         for (int rv = 0; rv < nr && rc == ADMM_OK; ++rv) {
             for (int cv = 0; cv < nc && rc == ADMM_OK; ++cv) {
                 for (int st : slot_targets) {
@@ -1081,38 +1121,17 @@ int admm_deconv_autotune(int H, int W, int reg, int haar_levels, int problems, i
                     t.row_variant = rv;
                     t.col_variant = cv;
                     t.slot_ctas = st;
-                    describe_tuning(&t);
-                    {
-                        std::lock_guard<std::mutex> lk(g_mutex);
-                        g_tuning[TuneKey(dev, H, W, reg, levels)] = t;
-                    }
-                    pls.assign(problems, nullptr);
-                    for (int i = 0; i < problems && rc == ADMM_OK; ++i) rc = admm_deconv_plan(&pls[i], &p, stream);
-                    float ms = 0.f;
-                    if (rc == ADMM_OK)   // warm-up: kernel attributes, graph capture
-                        rc = admm_deconv_solve_batch(pls.data(), problems, ys.data(), nullptr, xs.data(), nullptr, stream);
-                    if (rc == ADMM_OK) {
-                        if (cudaEventRecord(e0, s) != cudaSuccess) rc = ADMM_ECUDA;
-                        if (rc == ADMM_OK)
-                            rc = admm_deconv_solve_batch(pls.data(), problems, ys.data(), nullptr, xs.data(), nullptr,
-                                                         stream);
-                        if (rc == ADMM_OK && (cudaEventRecord(e1, s) != cudaSuccess ||
-                                              cudaEventSynchronize(e1) != cudaSuccess ||
-                                              cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
-                            rc = ADMM_ECUDA;
-                    }
-                    for (admm_plan_t q : pls) admm_deconv_destroy(q);
-                    pls.clear();
+                    rc = trial(t);
                     if (rc != ADMM_OK) break;
-                    t.us_per_iter = (double)ms * 1e3 / ((double)problems * (double)iters);
-                    if (count < max_trials) trials[count] = t;
-                    ++count;
-                    if (!have_win || t.us_per_iter < win.us_per_iter) {
-                        win = t;
-                        have_win = true;
-                    }
                 }
             }
+        }
+        // lanes (independent graph branches of the class) for the best of the sweep
+        for (int ln : {1, kMaxLanes}) {
+            if (rc != ADMM_OK || !have_win) break;
+            admm_tuning_t t = win;
+            t.lanes = ln;
+            rc = trial(t);
         }
     } while (0);
     for (admm_plan_t q : pls) admm_deconv_destroy(q);

@@ -109,9 +109,9 @@ def test_cnn_null_arguments(ad):
 
 
 def test_tuning_struct_layout(ad):
-    # admm_tuning_t: 12 ints, double
-    assert ctypes.sizeof(ad.admm_tuning_t) == 56
-    assert ad.admm_tuning_t.us_per_iter.offset == 48
+    # admm_tuning_t: 13 ints, padding, double
+    assert ctypes.sizeof(ad.admm_tuning_t) == 64
+    assert ad.admm_tuning_t.us_per_iter.offset == 56
 
 
 def test_every_size_has_compiled_configurations(ad):
@@ -128,7 +128,7 @@ def test_every_size_has_compiled_configurations(ad):
     assert ad.lib.admm_deconv_variants(512, 512, 0, None, None) == ad.ADMM_EINVAL
 
 
-@pytest.mark.parametrize("change", [dict(row_variant=99), dict(col_variant=-1), dict(slot_ctas=-5),
+@pytest.mark.parametrize("change", [dict(row_variant=99), dict(col_variant=-1), dict(slot_ctas=-5), dict(lanes=5),
                                     dict(reg=1, row_variant=1), dict(reg=1, haar_levels=9)])
 def test_set_tuning_rejects_out_of_range_on_host(ad, change):
     t = ad.admm_tuning_t(H=512, W=512, reg=0, haar_levels=0, row_variant=0, col_variant=0, slot_ctas=0)

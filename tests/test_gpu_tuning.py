@@ -36,9 +36,9 @@ def _problem(H, W, seed, keep=0.7):
     return psf, ybar, mask
 
 
-def _set(ad, H, W, reg, rv, cv, st=0, levels=0):
+def _set(ad, H, W, reg, rv, cv, st=0, levels=0, lanes=0):
     ad.admm_deconv_set_tuning({"H": H, "W": W, "reg": reg, "haar_levels": levels, "row_variant": rv,
-                               "col_variant": cv, "slot_ctas": st})
+                               "col_variant": cv, "slot_ctas": st, "lanes": lanes})
 
 
 def _reset(ad, H, W, reg, levels=0):
@@ -114,11 +114,11 @@ def test_autotune_installs_the_fastest_trial(ad):
     try:
         best, trials = ad.admm_deconv_autotune(H, W, "tv", problems=6, iters=16)
         nr, nc = ad.admm_deconv_variants(H, W, "tv")
-        assert len(trials) == nr * nc * 3
+        assert len(trials) == nr * nc * 3 + 2
         assert all(t["us_per_iter"] > 0 for t in trials)
         assert best["us_per_iter"] == min(t["us_per_iter"] for t in trials)
         cfg = ad.admm_deconv_get_tuning(H, W, "tv")
-        for k in ("row_variant", "col_variant", "slot_ctas", "rows_per_strip", "col_block", "col_min_ctas"):
+        for k in ("row_variant", "col_variant", "slot_ctas", "lanes", "rows_per_strip", "col_block", "col_min_ctas"):
             assert cfg[k] == best[k], k
         # a plan made now runs the tuned configuration and still matches the oracle
         psf, ybar, mask = _problem(H, W, 99)
@@ -144,6 +144,35 @@ def test_one_class_under_two_configurations_in_one_batch(ad):
         for i, (psf, _, _) in enumerate(probs):
             _set(ad, H, W, ad.ADMM_REG_TV, i % 2, i % 2)
             plans.append(ad.Plan(H, W, psf, lam, mu1, mu2, "tv", max_iters=iters))
+    finally:
+        _reset(ad, H, W, ad.ADMM_REG_TV)
+    ys = [torch.from_numpy(p[1].astype(np.float32)).cuda() for p in probs]
+    ms = [torch.from_numpy(p[2]).cuda() for p in probs]
+    xs = [torch.empty((H, W), dtype=torch.float32, device="cuda") for _ in probs]
+    res = ad.solve_batch(plans, ys, ms, xs)
+    torch.cuda.synchronize()
+    for (psf, ybar, mask), xg, r in zip(probs, xs, res):
+        st = O.State.zeros(H, W, "tv")
+        for _ in range(iters):
+            st = O.tvmd_step(st, ybar, mask, psf, lam, mu1, mu2)
+        assert r.iters == iters
+        assert _rel(xg.cpu().numpy().astype(np.float64), st.x) <= 2e-5
+    for p in plans:
+        p.close()
+
+
+@pytest.mark.parametrize("lanes", [1, 3, 4])
+def test_lane_counts_give_the_same_iterates(ad, lanes):
+    """A class split into 1, 3 or 4 independent lanes (graph branches, each
+    with its own slots and queue) computes every problem's iterates."""
+    import torch
+    H = W = 128
+    probs = [_problem(H, W, 150 + i) for i in range(7)]
+    lam, mu1, mu2, iters = 3e-4, 1e-2, 3e-3, 20     # > one chunk of 8: graph replays
+    try:
+        _set(ad, H, W, ad.ADMM_REG_TV, 0, 0, 0, lanes=lanes)
+        assert ad.admm_deconv_get_tuning(H, W, "tv")["lanes"] == lanes
+        plans = [ad.Plan(H, W, psf, lam, mu1, mu2, "tv", max_iters=iters) for psf, _, _ in probs]
     finally:
         _reset(ad, H, W, ad.ADMM_REG_TV)
     ys = [torch.from_numpy(p[1].astype(np.float32)).cuda() for p in probs]
