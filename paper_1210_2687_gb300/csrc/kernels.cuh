@@ -499,6 +499,12 @@ struct RowCfg {
     static constexpr int CPT = CW >= 32 ? CW / 32 : 1;              // columns per thread
     static constexpr int SLOT = 4 * W + 2 * NWARP;                 // floats per ring slot
     static constexpr int DR = D > 0 ? D : 1;                       // ring slots addressed (D = 0: none used)
+    // warps of at least 64 columns walk them as pairs of adjacent columns
+    // (lane l of pair p: columns w CW + 64 p + 2 l, + 1): 16-byte ring copies,
+    // global accesses and shared-memory reads and writes
+    static constexpr bool PAIRS = CW >= 64 && D > 0;
+    static constexpr int NPAIR = CPT / 2;
+    static_assert(!PAIRS || (SLOT * 4) % 16 == 0, "16-byte ring copies need 16-byte slots");
     static_assert(RAW * 16 <= ROW * 8, "raw row must fit a buffer row");
     static_assert(R + 2 <= 32, "boundary capture holds one row per lane");
     static_assert(((size_t)NB * ROW * 8 + (size_t)W * 8) % 16 == 0, "ring alignment");
@@ -545,6 +551,18 @@ row_phase_tv(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp, co
         if (D > 0 && i <= R && colthr) {
             const int q = (r0 - 1 + i + H) & (H - 1);
             float* slot = ring + (i % C::DR) * C::SLOT;
+            if constexpr (C::PAIRS) {
+#pragma unroll
+                for (int pp = 0; pp < C::NPAIR; ++pp) {
+                    const int c = wid * C::CW + 64 * pp + 2 * lane;
+                    const size_t pix = (size_t)q * W + c;
+                    if (!cold) cp_async16(slot + 2 * c, d2in + pix);
+                    if (i >= 1) {
+                        if (!cold) cp_async8(slot + 2 * W + c, P.d1 + pix);
+                        cp_async8(slot + 3 * W + c, P.ybar + pix);
+                    }
+                }
+            } else {
 #pragma unroll
             for (int j = 0; j < C::CPT; ++j) {
                 const int c = cbase + 32 * j;
@@ -554,6 +572,7 @@ row_phase_tv(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp, co
                     if (!cold) cp_async4(slot + 2 * W + c, P.d1 + pix);
                     cp_async4(slot + 3 * W + c, P.ybar + pix);
                 }
+            }
             }
             if (lane == 0 && !cold) cp_async8(slot + 4 * W + 2 * wid, d2in + (size_t)q * W + chalo);
         }
@@ -641,10 +660,14 @@ row_phase_tv(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp, co
     float dvprev[C::CPT];
     const bool need_xp = chk && !first;
     float xpn[C::CPT];               // x_prev of the next owned row
+    // column of entry j of the thread's per-column arrays
+    auto colj = [&](int j) {
+        return C::PAIRS ? wid * C::CW + 64 * (j >> 1) + 2 * lane + (j & 1) : cbase + 32 * j;
+    };
 #pragma unroll
     for (int j = 0; j < C::CPT; ++j) {
         dvprev[j] = 0.f;
-        xpn[j] = (need_xp && colthr) ? P.xprev[(size_t)r0 * W + cbase + 32 * j] : 0.f;
+        xpn[j] = (need_xp && colthr) ? P.xprev[(size_t)r0 * W + colj(j)] : 0.f;
     }
     for (int i = 0; i <= R; ++i) {
         const int q = (r0 - 1 + i + H) & (H - 1);
@@ -655,7 +678,7 @@ row_phase_tv(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp, co
         if (need_xp && owned && i < R && colthr) {
             // requested a row ahead (row q + 1 is still unwritten by this iteration)
 #pragma unroll
-            for (int j = 0; j < C::CPT; ++j) xpn[j] = P.xprev[(size_t)(q + 1) * W + cbase + 32 * j];
+            for (int j = 0; j < C::CPT; ++j) xpn[j] = P.xprev[(size_t)(q + 1) * W + colj(j)];
         }
         if (D > 0) cp_async_wait<(D > 0 ? D - 1 : 0)>();   // this thread's copies of walk row i have landed
         const float* slot = ring + (i % C::DR) * C::SLOT;
@@ -666,6 +689,123 @@ row_phase_tv(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp, co
 #pragma unroll
         for (int j = 0; j < C::CPT; ++j) dhcur[j] = dvcur[j] = z1cur[j] = 0.f;
         float dh_halo = 0.f;
+        if constexpr (C::PAIRS) {
+            // x, A x of both columns of each pair (row i) and x below them (row
+            // i + 1): one 16-byte read each. swz keeps an even/odd column pair
+            // together (positions swz(c) ^ {0, 1}); bit 3 of c says which is first.
+            float4 xa[C::NPAIR];
+            float2 xdn[C::NPAIR];
+#pragma unroll
+            for (int pp = 0; pp < C::NPAIR; ++pp) {
+                const int c = wid * C::CW + 64 * pp + 2 * lane;
+                const int base = swz(c) & ~1;
+                const bool sw = (c >> 3) & 1;
+                const float4 t4 = *reinterpret_cast<const float4*>(buf + i * C::ROW + base);
+                const float4 u4 = *reinterpret_cast<const float4*>(buf + (i + 1) * C::ROW + base);
+                xa[pp] = sw ? make_float4(t4.z, t4.w, t4.x, t4.y) : t4;
+                xdn[pp] = sw ? make_float2(u4.z, u4.x) : make_float2(u4.x, u4.z);
+            }
+            // x right of each pair: the next lane's first column, for lane 31 the
+            // next pair's lane 0 or, after the last pair, the next warp's first
+            float xrp[C::NPAIR];
+#pragma unroll
+            for (int pp = 0; pp < C::NPAIR; ++pp) {
+                const float nx = __shfl_down_sync(0xffffffffu, xa[pp].x, 1);
+                const float wr = pp + 1 < C::NPAIR ? __shfl_sync(0xffffffffu, xa[pp + 1 < C::NPAIR ? pp + 1 : pp].x, 0)
+                                                   : xr_nb;
+                xrp[pp] = lane == 31 ? wr : nx;
+            }
+#pragma unroll
+            for (int pp = 0; pp < C::NPAIR; ++pp) {
+                const int c = wid * C::CW + 64 * pp + 2 * lane;
+                const size_t pix = (size_t)q * W + c;
+                const float4 dd = cold ? make_float4(0.f, 0.f, 0.f, 0.f)
+                                       : *reinterpret_cast<const float4*>(slot + 2 * c);
+                const float xs[2] = {xa[pp].x, xa[pp].z}, axs[2] = {xa[pp].y, xa[pp].w};
+                const float xrs[2] = {xa[pp].z, xrp[pp]}, xds[2] = {xdn[pp].x, xdn[pp].y};
+                const float ddh[2] = {dd.x, dd.z}, ddv[2] = {dd.y, dd.w};
+                float nh[2], nv[2];
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    // D_i x, u2 = v-soft(D_i x - d2, lambda/mu2), d2 <- d2 - (D_i x - u2),
+                    // delta = u2 + d2  (Alg. 3 lines 3-5, 9-11; as in the single-column walk)
+                    const float gh = xrs[e] - xs[e], gv = xds[e] - xs[e];
+                    const float sh = gh - ddh[e], sv = gv - ddv[e];
+                    const float sc = fmaxf(0.f, fmaf(-tau, rsqrtf(fmaf(sh, sh, sv * sv)), 1.f));
+                    const float uh = sc * sh, uv = sc * sv;
+                    nh[e] = uh - sh;
+                    nv[e] = uv - sv;
+                    dhcur[2 * pp + e] = uh + nh[e];
+                    dvcur[2 * pp + e] = uv + nv[e];
+                    if (owned && nobj) s_reg.add(sqrtf(fmaf(gh, gh, gv * gv)));
+                }
+                if (owned) {
+                    *reinterpret_cast<float4*>(d2out + pix) = make_float4(nh[0], nv[0], nh[1], nv[1]);
+                    const float2 d1p = cold ? make_float2(0.f, 0.f) : *reinterpret_cast<const float2*>(slot + 2 * W + c);
+                    const float2 ybp = *reinterpret_cast<const float2*>(slot + 3 * W + c);
+                    const float d1s[2] = {d1p.x, d1p.y}, ybs[2] = {ybp.x, ybp.y};
+                    float nd1[2];
+#pragma unroll
+                    for (int e = 0; e < 2; ++e) {
+                        // mask prox (eq. new_line) and d1 update (Alg. 3 line 8)
+                        const float s1 = axs[e] - d1s[e];
+                        const bool obs = is_observed(ybs[e]);
+                        const float u1 = obs ? fmaf(mu1, s1, ybs[e]) * inv1 : s1;
+                        nd1[e] = d1s[e] - (axs[e] - u1);
+                        z1cur[2 * pp + e] = u1 + nd1[e];
+                        if (nobj && obs) {
+                            const float er = axs[e] - ybs[e];
+                            s_data.add(0.5f * er * er);
+                        }
+                        if (chk) {
+                            const float dx = first ? xs[e] : xs[e] - xpc[2 * pp + e];
+                            s_dxx.add(dx * dx);
+                            s_xx.add(xs[e] * xs[e]);
+                        }
+                    }
+                    *reinterpret_cast<float2*>(P.d1 + pix) = make_float2(nd1[0], nd1[1]);
+                    if (sprev) *reinterpret_cast<float2*>(P.xprev + pix) = make_float2(xs[0], xs[1]);
+                }
+            }
+            if (lane == 0 && owned) {
+                // delta_h of the pixel left of the chunk (its owner updates its d2)
+                const float xh = xl_nb;
+                const float xhr = xa[0].x;
+                const float2 dd = cold ? make_float2(0.f, 0.f) : *reinterpret_cast<const float2*>(slot + 4 * W + 2 * wid);
+                const float sh = (xhr - xh) - dd.x, sv = (xl_nb_dn - xh) - dd.y;
+                const float sc = fmaxf(0.f, fmaf(-tau, rsqrtf(fmaf(sh, sh, sv * sv)), 1.f));
+                dh_halo = 2.f * sc * sh - sh;
+            }
+            issue(i + D);            // slot (i % D) is consumed: refill it D rows ahead
+            // delta_h left of each column: the pair's own first column for the
+            // second; the previous lane (pair) or the chunk's halo for the first
+            float dhl[C::CPT];
+#pragma unroll
+            for (int pp = 0; pp < C::NPAIR; ++pp) {
+                const float up = __shfl_up_sync(0xffffffffu, dhcur[2 * pp + 1], 1);
+                const float wr = pp > 0 ? __shfl_sync(0xffffffffu, dhcur[pp > 0 ? 2 * pp - 1 : 1], 31) : dh_halo;
+                dhl[2 * pp] = lane == 0 ? wr : up;
+                dhl[2 * pp + 1] = dhcur[2 * pp];
+            }
+            __syncwarp();            // every lane has read rows i, i + 1 before row i is overwritten
+            if (owned) {
+                // w = gamma (Dh^T delta_h + Dv^T delta_v); p = zeta1 + i w over row i
+#pragma unroll
+                for (int pp = 0; pp < C::NPAIR; ++pp) {
+                    const int c = wid * C::CW + 64 * pp + 2 * lane;
+                    const float w0 = gam * ((dhl[2 * pp] - dhcur[2 * pp]) + (dvprev[2 * pp] - dvcur[2 * pp]));
+                    const float w1 =
+                        gam * ((dhl[2 * pp + 1] - dhcur[2 * pp + 1]) + (dvprev[2 * pp + 1] - dvcur[2 * pp + 1]));
+                    const bool sw = (c >> 3) & 1;
+                    *reinterpret_cast<float4*>(buf + i * C::ROW + (swz(c) & ~1)) =
+                        sw ? make_float4(z1cur[2 * pp + 1], w1, z1cur[2 * pp], w0)
+                           : make_float4(z1cur[2 * pp], w0, z1cur[2 * pp + 1], w1);
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < C::CPT; ++j) dvprev[j] = dvcur[j];
+            continue;
+        }
         if (colthr) {
 #pragma unroll
             for (int j = 0; j < C::CPT; ++j) {
