@@ -336,7 +336,9 @@ haar_synthesis(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W) {
     const float* __restrict__ zeta = P.d2 + ((k + 1) & 1) * P.d2_stride;
 
     // low-low band on rows [-HALO, T) and each level's bands on rows [-BO, T),
-    // all on the columns [-16, T)
+    // all on the columns [-16, T), requested coarse to fine in one cp.async
+    // group per level (the low-low band with the coarsest), so that the
+    // coarse levels of the adjoint start while the fine bands still arrive
     {
         const float* band = zeta + (size_t)(3 * L) * n;
         for (int e = tid; e < AR * CH; e += kThreads) {
@@ -346,7 +348,7 @@ haar_synthesis(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W) {
         }
     }
 #pragma unroll
-    for (int lvl = 0; lvl < L; ++lvl) {
+    for (int lvl = L - 1; lvl >= 0; --lvl) {
         const int BO = 2 * (1 << lvl) - 1, BR = T + BO;
         float* Zl = Z + C::zoff(lvl);
 #pragma unroll
@@ -358,13 +360,13 @@ haar_synthesis(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W) {
                            band + (size_t)((R0 + rr - BO) & (H - 1)) * W + ((C0 - 16 + 4 * ch) & (W - 1)));
             }
         }
+        cp_async_commit();
     }
-    cp_async_commit();
-    cp_async_wait<0>();
-    __syncthreads();
 
 #pragma unroll
     for (int lvl = L - 1; lvl >= 0; --lvl) {
+        cp_async_wait_n(lvl);        // this level's bands (and the coarser ones) ...
+        __syncthreads();             // ... have landed for every thread; the previous level is done
         const int s = 1 << lvl;
         const int D = T + s - 1;                       // output on [-(s-1), T)
         const int BO = 2 * s - 1, BR = T + BO;
@@ -386,11 +388,11 @@ haar_synthesis(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W) {
                 Ao[ia] = 0.25f * ((lo_c + lo_l) + (hi_c - hi_l));
             }
         }
-        __syncthreads();
         float* tmp = At;
         At = Ao;
         Ao = tmp;
     }
+    __syncthreads();                 // the finest level is complete
     // w = gamma P^T zeta2 on the tile
     const float gam = P.gamma;
     float* __restrict__ ww = P.work + 2 * n;
