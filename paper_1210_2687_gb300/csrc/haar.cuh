@@ -226,34 +226,47 @@ haar_analysis(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W, in
             for (int j = 0; j < 3; ++j)
                 dold[i][j] = first ? 0.f : d2s[(3 * lvl + j) * T * T + (warp + NWARP * i) * T + lane];
         const int D = T + (1 << L) - 2 * s;      // a_{lvl+1} is needed on [0, D)^2
+        // owned pixels (row warp + 8 i, column lane): approximation, detail
+        // bands, soft threshold and dual updates
 #pragma unroll
-        for (int i = 0; i * NWARP < D; ++i) {
-            const int rr = warp + NWARP * i;
-            if (rr >= D) break;
+        for (int i = 0; i < OWN; ++i) {
+            const int i00 = (warp + NWARP * i) * XA + lane;
+            const float a00 = Ain[i00], a01 = Ain[i00 + s];
+            const float a10 = Ain[i00 + s * XA], a11 = Ain[i00 + s * XA + s];
+            const float p0 = a00 + a01, m0 = a00 - a01, p1 = a10 + a11, m1 = a10 - a11;
+            Aout[i00] = 0.25f * (p0 + p1);
+            // detail bands: rows low / cols high, rows high / cols low, both high
+            const float cb[3] = {0.25f * (m0 + m1), 0.25f * (p0 - p1), 0.25f * (m0 - m1)};
+            const size_t gp = gp0 + (size_t)(NWARP * i) * W;
 #pragma unroll
-            for (int pass = 0; pass * 32 < D; ++pass) {
-                const int cc = lane + 32 * pass;
-                if (cc >= D) break;
-                const int i00 = rr * XA + cc;
-                const float a00 = Ain[i00], a01 = Ain[i00 + s];
-                const float a10 = Ain[i00 + s * XA], a11 = Ain[i00 + s * XA + s];
-                const float p0 = a00 + a01, m0 = a00 - a01, p1 = a10 + a11, m1 = a10 - a11;
-                Aout[i00] = 0.25f * (p0 + p1);
-                if (i < OWN && pass == 0) {
-                    // detail bands: rows low / cols high, rows high / cols low, both high
-                    const float cb[3] = {0.25f * (m0 + m1), 0.25f * (p0 - p1), 0.25f * (m0 - m1)};
-                    const size_t gp = gp0 + (size_t)(NWARP * i) * W;
-#pragma unroll
-                    for (int j = 0; j < 3; ++j) {
-                        const float sv = cb[j] - dold[i < OWN ? i : 0][j];
-                        const float u = soft_thresh(sv, tau);           // eq. soft
-                        const float nd = u - sv;                        // d2 - (c - u2)
-                        d2out[(size_t)(3 * lvl + j) * n + gp] = nd;
-                        d2io[(size_t)(3 * lvl + j) * n + gp] = u + nd;  // zeta2 = u2 + d2
-                        if (nobj) l1.add(fabsf(cb[j]));
-                    }
-                }
+            for (int j = 0; j < 3; ++j) {
+                const float sv = cb[j] - dold[i][j];
+                const float u = soft_thresh(sv, tau);           // eq. soft
+                const float nd = u - sv;                        // d2 - (c - u2)
+                d2out[(size_t)(3 * lvl + j) * n + gp] = nd;
+                d2io[(size_t)(3 * lvl + j) * n + gp] = u + nd;  // zeta2 = u2 + d2
+                if (nobj) l1.add(fabsf(cb[j]));
             }
+        }
+        // the approximation on the rest of [0, D)^2 that later levels read
+        // (rows [0, T) x columns [T, D), then rows [T, D) x columns [0, D)),
+        // spread evenly over the block
+        const int DT = D - T;
+        const int n1 = T * DT, nh = n1 + DT * D;
+        for (int e = tid; e < nh; e += kThreads) {
+            int rr, cc;
+            if (e < n1) {
+                rr = e / (DT > 0 ? DT : 1);
+                cc = T + (e - rr * DT);
+            } else {
+                const int f = e - n1;
+                rr = T + f / D;
+                cc = f - (rr - T) * D;
+            }
+            const int i00 = rr * XA + cc;
+            const float a00 = Ain[i00], a01 = Ain[i00 + s];
+            const float a10 = Ain[i00 + s * XA], a11 = Ain[i00 + s * XA + s];
+            Aout[i00] = 0.25f * ((a00 + a01) + (a10 + a11));
         }
         __syncthreads();
         float* tmp = Ain;
@@ -374,19 +387,19 @@ haar_synthesis(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W) {
         const float* Z1 = Z0 + BR * XS;
         const float* Z2 = Z1 + BR * XS;
         const int ra = s * XS, rz = s * XS;
-        for (int rr = warp; rr < D; rr += NWARP) {
-            const int r = rr - (s - 1);
-            for (int cc = lane; cc < D; cc += 32) {
-                const int c = cc - (s - 1);
-                const int ia = (r + HALO) * XS + (c + 16);
-                const int iz = (r + BO) * XS + (c + 16);
-                // rows adjoint at columns c and c - s
-                const float lo_c = (At[ia] + At[ia - ra]) + (Z1[iz] - Z1[iz - rz]);
-                const float lo_l = (At[ia - s] + At[ia - ra - s]) + (Z1[iz - s] - Z1[iz - rz - s]);
-                const float hi_c = (Z0[iz] + Z0[iz - rz]) + (Z2[iz] - Z2[iz - rz]);
-                const float hi_l = (Z0[iz - s] + Z0[iz - rz - s]) + (Z2[iz - s] - Z2[iz - rz - s]);
-                Ao[ia] = 0.25f * ((lo_c + lo_l) + (hi_c - hi_l));
-            }
+        // the D x D outputs spread evenly over the block (D is a constant
+        // where the level loop is unrolled)
+        for (int e = tid; e < D * D; e += kThreads) {
+            const int rr = e / D, cc = e - rr * D;
+            const int r = rr - (s - 1), c = cc - (s - 1);
+            const int ia = (r + HALO) * XS + (c + 16);
+            const int iz = (r + BO) * XS + (c + 16);
+            // rows adjoint at columns c and c - s
+            const float lo_c = (At[ia] + At[ia - ra]) + (Z1[iz] - Z1[iz - rz]);
+            const float lo_l = (At[ia - s] + At[ia - ra - s]) + (Z1[iz - s] - Z1[iz - rz - s]);
+            const float hi_c = (Z0[iz] + Z0[iz - rz]) + (Z2[iz] - Z2[iz - rz]);
+            const float hi_l = (Z0[iz - s] + Z0[iz - rz - s]) + (Z2[iz - s] - Z2[iz - rz - s]);
+            Ao[ia] = 0.25f * ((lo_c + lo_l) + (hi_c - hi_l));
         }
         float* tmp = At;
         At = Ao;
