@@ -669,6 +669,11 @@ def run_ours(args):
                          "bytes_per_px_iter": {"row_phase": row_b, "col_phase": col_b},
                          "row_phase_gbs": row_gbs, "col_phase_gbs": col_gbs,
                          "row_ms": prof.row_ms, "col_ms": prof.col_ms,
+                         # the whole iteration (both phases, all lanes overlapped) over
+                         # the timed region: algorithmic bytes of every image-iteration
+                         # the job ran / wall time
+                         "iteration_gbs": total_iters * n * (row_b + col_b) / sec / 1e9,
+                         "iteration_frac": total_iters * n * (row_b + col_b) / sec / 1e9 / peak,
                          "steady_state": steady},
             "cufft_comparison": cufft,
             "cpu_baseline": cpu,
