@@ -671,9 +671,9 @@ def run_ours(args):
                          "row_ms": prof.row_ms, "col_ms": prof.col_ms,
                          # the whole iteration (both phases, all lanes overlapped) over
                          # the timed region: algorithmic bytes of every image-iteration
-                         # the job ran / wall time
+                         # the job ran / wall time (fraction of the peak of all GPUs)
                          "iteration_gbs": total_iters * n * (row_b + col_b) / sec / 1e9,
-                         "iteration_frac": total_iters * n * (row_b + col_b) / sec / 1e9 / peak,
+                         "iteration_frac": total_iters * n * (row_b + col_b) / sec / 1e9 / (peak * world),
                          "steady_state": steady},
             "cufft_comparison": cufft,
             "cpu_baseline": cpu,
