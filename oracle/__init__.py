@@ -28,6 +28,9 @@ its justification in the design notes):
   along each axis. Each level emits three detail bands and passes the
   low-low band on; the last low-low band is kept: 3 L + 1 bands. P^T P = I.
 * vector-soft maps 0 to 0 (Sec. III-C); soft(v, t) = sign(v) max(|v| - t, 0).
+* Variants beyond the paper's two priors: anisotropic TV (the l1 norm of each
+  difference component; its prox is eq. soft per component) and the frame
+  prior with the last low-low band unpenalised (its prox is the identity).
 
 Every function below is written to be checked by eye against the equation
 it cites, not for speed.
@@ -216,16 +219,25 @@ def mask_prox(v, ybar, mask, mu1):
 # --------------------------------------------------------------------------
 # objectives (eq. unconstrained_TV_uBC and eq. unconstrained_analysis_uBC)
 # --------------------------------------------------------------------------
-def objective_tv(x, ybar, mask, psf, lam):
+def objective_tv(x, ybar, mask, psf, lam, aniso=False):
+    """Isotropic TV: lam sum_i ||(Dh x, Dv x)_i||; anisotropic (aniso=True):
+    lam sum_i (|Dh x|_i + |Dv x|_i)."""
     m = mask.astype(np.float64)
     r = m * (ybar - A_fft(x, psf))
-    return 0.5 * float(np.sum(r * r)) + lam * float(np.sum(np.sqrt(Dh(x) ** 2 + Dv(x) ** 2)))
+    gh, gv = Dh(x), Dv(x)
+    reg = np.abs(gh) + np.abs(gv) if aniso else np.sqrt(gh ** 2 + gv ** 2)
+    return 0.5 * float(np.sum(r * r)) + lam * float(np.sum(reg))
 
 
-def objective_haar(x, ybar, mask, psf, lam, levels=4):
+def objective_haar(x, ybar, mask, psf, lam, levels=4, ll_free=False):
+    """lam ||P x||_1 over all 3 L + 1 bands, or (ll_free=True) over the 3 L
+    detail bands only (the coarse low-low band unpenalised)."""
     m = mask.astype(np.float64)
     r = m * (ybar - A_fft(x, psf))
-    return 0.5 * float(np.sum(r * r)) + lam * float(np.sum(np.abs(haar_analysis(x, levels))))
+    c = haar_analysis(x, levels)
+    if ll_free:
+        c = c[:-1]
+    return 0.5 * float(np.sum(r * r)) + lam * float(np.sum(np.abs(c)))
 
 
 # --------------------------------------------------------------------------
@@ -244,7 +256,7 @@ class State:
 
     @staticmethod
     def zeros(H, W, reg="tv", levels=4):
-        nb = 2 if reg == "tv" else haar_nbands(levels)
+        nb = 2 if reg in ("tv", "tv_aniso") else haar_nbands(levels)
         z = np.zeros((H, W))
         return State(z.copy(), z.copy(), np.zeros((nb, H, W)), np.zeros((nb, H, W)), z.copy(), 0)
 
@@ -253,8 +265,10 @@ class State:
                      self.x.copy(), self.k)
 
 
-def tvmd_step(st: State, ybar, mask, psf, lam, mu1, mu2, otf=None, denom=None) -> State:
-    """One iteration of TV-MD: Algorithm 3 with line 7 replaced by eq. new_line."""
+def tvmd_step(st: State, ybar, mask, psf, lam, mu1, mu2, otf=None, denom=None, aniso=False) -> State:
+    """One iteration of TV-MD: Algorithm 3 with line 7 replaced by eq. new_line.
+    aniso=True: anisotropic TV, whose prox (lines 9-10) is the soft threshold
+    of eq. soft applied to each difference component instead of vector-soft."""
     H, W = ybar.shape
     if otf is None:
         otf = psf_otf(psf, H, W)
@@ -275,14 +289,19 @@ def tvmd_step(st: State, ybar, mask, psf, lam, mu1, mu2, otf=None, denom=None) -
     d1 = st.d1 - (ax - u1)
     # lines 9-11: per pixel vector-soft and dual update
     gh, gv = Dh(x), Dv(x)
-    uh, uv = vsoft(gh - st.d2[0], gv - st.d2[1], lam / mu2)
+    if aniso:
+        uh, uv = soft(gh - st.d2[0], lam / mu2), soft(gv - st.d2[1], lam / mu2)
+    else:
+        uh, uv = vsoft(gh - st.d2[0], gv - st.d2[1], lam / mu2)
     d2 = np.stack([st.d2[0] - (gh - uh), st.d2[1] - (gv - uv)])
     return State(u1, d1, np.stack([uh, uv]), d2, x, st.k + 1)
 
 
-def famd_step(st: State, ybar, mask, psf, lam, mu1, mu2, levels=4, otf=None) -> State:
+def famd_step(st: State, ybar, mask, psf, lam, mu1, mu2, levels=4, otf=None, ll_free=False) -> State:
     """One iteration of FA-MD: Algorithm 2 with H1 = A, H2 = P, line 4 from
-    eqs. invAnalysis/invAnalysisp1 and line 6 from eqs. prox_g_1_uBC and prox_g_2."""
+    eqs. invAnalysis/invAnalysisp1 and line 6 from eqs. prox_g_1_uBC and prox_g_2.
+    ll_free=True leaves the last (low-low) band unpenalised: its prox is the
+    identity (a threshold of zero)."""
     H, W = ybar.shape
     if otf is None:
         otf = psf_otf(psf, H, W)
@@ -300,6 +319,8 @@ def famd_step(st: State, ybar, mask, psf, lam, mu1, mu2, levels=4, otf=None) -> 
     # lines 6-7, j = 2: soft threshold of the frame coefficients
     c = haar_analysis(x, levels)
     u2 = soft(c - st.d2, lam / mu2)
+    if ll_free:
+        u2[-1] = c[-1] - st.d2[-1]
     d2 = st.d2 - (c - u2)
     return State(u1, d1, u2, d2, x, st.k + 1)
 
@@ -320,13 +341,17 @@ def solve(ybar, mask, psf, lam, mu1, mu2, reg="tv", iters=200, stop="iters", tol
           levels=4, state0: State | None = None, record=False) -> SolveResult:
     """Run TV-MD or FA-MD from ``state0`` (default: u0 = d0 = 0) until ``iters``
     iterations or, for stop = 'rel_x' / 'rel_obj', until the relative change of
-    x / of the objective between consecutive iterations is below ``tol``."""
+    x / of the objective between consecutive iterations is below ``tol``.
+    reg: 'tv', 'tv_aniso' (anisotropic TV), 'haar', 'haar_ll_free' (the
+    low-low band unpenalised)."""
     H, W = ybar.shape
-    st = state0.copy() if state0 is not None else State.zeros(H, W, reg, levels)
+    tv = reg in ("tv", "tv_aniso")
+    aniso, ll_free = reg == "tv_aniso", reg == "haar_ll_free"
+    st = state0.copy() if state0 is not None else State.zeros(H, W, "tv" if tv else "haar", levels)
     otf = psf_otf(psf, H, W)
-    denom = tv_denominator_diag(psf, H, W, mu1, mu2) if reg == "tv" else None
-    obj_fn = (lambda x: objective_tv(x, ybar, mask, psf, lam)) if reg == "tv" else \
-             (lambda x: objective_haar(x, ybar, mask, psf, lam, levels))
+    denom = tv_denominator_diag(psf, H, W, mu1, mu2) if tv else None
+    obj_fn = (lambda x: objective_tv(x, ybar, mask, psf, lam, aniso)) if tv else \
+             (lambda x: objective_haar(x, ybar, mask, psf, lam, levels, ll_free))
     hist = []
     f_prev = None
     rel_x = rel_obj = float("inf")
@@ -334,10 +359,10 @@ def solve(ybar, mask, psf, lam, mu1, mu2, reg="tv", iters=200, stop="iters", tol
     n = 0
     for n in range(1, iters + 1):
         x_prev = st.x
-        if reg == "tv":
-            st = tvmd_step(st, ybar, mask, psf, lam, mu1, mu2, otf, denom)
+        if tv:
+            st = tvmd_step(st, ybar, mask, psf, lam, mu1, mu2, otf, denom, aniso)
         else:
-            st = famd_step(st, ybar, mask, psf, lam, mu1, mu2, levels, otf)
+            st = famd_step(st, ybar, mask, psf, lam, mu1, mu2, levels, otf, ll_free)
         nx = float(np.linalg.norm(st.x))
         rel_x = float(np.linalg.norm(st.x - x_prev)) / nx if nx > 0 else float("inf")
         f = obj_fn(st.x) if (stop == "rel_obj" or record) else float("nan")

@@ -202,7 +202,7 @@ def warm_state(x0, d1, d2, psf, reg="tv", levels=4) -> State:
     means zero duals."""
     H, W = x0.shape
     d1 = np.zeros((H, W)) if d1 is None else np.asarray(d1, dtype=np.float64)
-    if reg == "tv":
+    if reg in ("tv", "tv_aniso"):
         hx2 = np.stack([Dh(x0), Dv(x0)])
     else:
         hx2 = haar_analysis(x0, levels)

@@ -431,3 +431,104 @@ def test_objective_decreases_after_burn_in():
     f = [h[1] for h in r.history]
     for k in range(40, len(f)):
         assert f[k] <= f[k - 20] * (1 + 1e-12)
+
+
+# --------------------------------------------------------------------------
+# variants: anisotropic TV (soft threshold per difference component) and the
+# frame prior with the low-low band left unpenalised
+# --------------------------------------------------------------------------
+def _pdhg_tv_aniso(A, Dh, Dv, m, ybar, lam, iters=60000):
+    """Chambolle-Pock on min_x 1/2 sum_i m_i (A x - y)_i^2 + lam sum_i (|Dh x|_i + |Dv x|_i):
+    the dual step of the regulariser projects each component on [-lam, lam]."""
+    n = A.shape[1]
+    K = np.vstack([A, Dh, Dv])
+    L = np.linalg.norm(K, 2)
+    tau = sig = 0.99 / L
+    x = np.zeros(n); xb = x.copy()
+    p = np.zeros(n); q = np.zeros((2, n))
+    for _ in range(iters):
+        v = p + sig * (A @ xb)
+        p = np.where(m > 0, (v - sig * ybar) / (1.0 + sig), 0.0)
+        q = np.clip(q + sig * np.stack([Dh @ xb, Dv @ xb]), -lam, lam)
+        x_new = x - tau * (A.T @ p + Dh.T @ q[0] + Dv.T @ q[1])
+        xb = 2 * x_new - x
+        x = x_new
+    return x
+
+
+def test_aniso_tv_kkt_certificate_at_convergence():
+    """Anisotropic TV: -mu1 d1 = M^T(M A x - y), mu1 A^T d1 + mu2 D^T d2 = 0,
+    |mu2 d2| <= lambda per component with -mu2 d2 = lambda sign(D x) where D x != 0
+    (the subgradient of the l1 norm, eq. soft's optimality)."""
+    x, h, ybar, mask = _small_problem()
+    lam, mu1, mu2 = 2e-3, 1.0, 2e-2
+    r = O.solve(ybar, mask, h, lam, mu1, mu2, "tv_aniso", iters=20000, stop="rel_x", tol=1e-13)
+    assert r.converged
+    st = r.state
+    m = mask.astype(float)
+    np.testing.assert_allclose(-mu1 * st.d1, m * (O.A_fft(st.x, h) - ybar), atol=1e-9)
+    stat = mu1 * O.At_fft(st.d1, h) + mu2 * (O.DhT(st.d2[0]) + O.DvT(st.d2[1]))
+    assert np.max(np.abs(stat)) < 1e-9
+    assert np.max(np.abs(mu2 * st.d2)) <= lam * (1 + 1e-9)
+    for comp, gfun in ((0, O.Dh), (1, O.Dv)):
+        gx = gfun(st.x)
+        act = np.abs(gx) > 1e-6
+        assert act.sum() > 10
+        np.testing.assert_allclose(-mu2 * st.d2[comp][act], lam * np.sign(gx[act]), atol=1e-6 * lam)
+    # the isotropic solution of the same problem is a different point
+    ri = O.solve(ybar, mask, h, lam, mu1, mu2, "tv", iters=20000, stop="rel_x", tol=1e-13)
+    assert np.max(np.abs(ri.x - r.x)) > 1e-4
+
+
+def test_aniso_tv_optimum_matches_independent_pdhg():
+    H = W = 8
+    g = S.rng(19)
+    xt = S.shapes_image(H, W, g, 3, rmax=3.0)
+    h = S.psf_gaussian(3, 0.8)
+    keep = (g.uniform(size=(H, W)) < 0.9).astype(np.uint8)
+    ybar, mask, _ = S.observe(xt, h, keep, 30.0, g)
+    lam, mu1, mu2 = 5e-3, 1.0, 5e-2
+    r = O.solve(ybar, mask, h, lam, mu1, mu2, "tv_aniso", iters=50000, stop="rel_x", tol=1e-14)
+    A = _dense(lambda v: O.A_direct(v, h), H, W)
+    xp = _pdhg_tv_aniso(A, _dense(O.Dh, H, W), _dense(O.Dv, H, W), mask.ravel().astype(float), ybar.ravel(),
+                        lam)
+    f_pd = O.objective_tv(xp.reshape(H, W), ybar, mask, h, lam, aniso=True)
+    assert abs(r.objective - f_pd) <= 1e-8 * abs(f_pd) + 1e-12
+
+
+def test_ll_free_frame_kkt_and_zero_low_low_dual():
+    """Frame prior with the low-low band unpenalised: the low-low dual is zero
+    after every iteration (its prox is the identity), and the certificate of
+    the remaining bands holds: mu1 A^T d1 + mu2 P^T d2 = 0, |mu2 d2| <= lambda."""
+    x, h, ybar, mask = _small_problem(seed=8)
+    lam, mu1, mu2 = 1e-2, 1.0, 1e-1
+    r = O.solve(ybar, mask, h, lam, mu1, mu2, "haar_ll_free", iters=20000, stop="rel_x", tol=1e-13)
+    assert r.converged
+    st = r.state
+    assert np.max(np.abs(st.d2[-1])) < 1e-12
+    m = mask.astype(float)
+    np.testing.assert_allclose(-mu1 * st.d1, m * (O.A_fft(st.x, h) - ybar), atol=1e-9)
+    stat = mu1 * O.At_fft(st.d1, h) + mu2 * O.haar_synthesis(st.d2, 4)
+    assert np.max(np.abs(stat)) < 1e-9
+    assert np.max(np.abs(mu2 * st.d2)) <= lam * (1 + 1e-9)
+    c = O.haar_analysis(st.x, 4)[:-1]
+    act = np.abs(c) > 1e-7
+    np.testing.assert_allclose(-mu2 * st.d2[:-1][act], lam * np.sign(c[act]), atol=1e-6 * lam)
+
+
+@pytest.mark.parametrize("reg", ["tv", "tv_aniso", "haar_ll_free", "haar"])
+def test_strong_weight_limit(reg):
+    """With a weight far above the data term, a regulariser that vanishes on
+    constants (TV, anisotropic TV, details-only frame) leaves the best constant:
+    A 1 = beta 1 gives x = sum of observed y / (beta * #observed); the full frame
+    prior, which also penalises the low-low band, drives x to zero."""
+    g = S.rng(21)
+    H = W = 16
+    x = S.shapes_image(H, W, g, 4, rmax=4.0)
+    h = S.psf_gaussian(5, 1.0)
+    keep = (g.uniform(size=(H, W)) < 0.8).astype(np.uint8)
+    ybar, mask, _ = S.observe(x, h, keep, 40.0, g)
+    cstar = ybar[mask > 0].sum() / (h.sum() * mask.sum())
+    r = O.solve(ybar, mask, h, 10.0, 0.3, 3.0, reg, iters=3000)
+    target = 0.0 if reg == "haar" else cstar
+    assert np.max(np.abs(r.x - target)) < 1e-9
