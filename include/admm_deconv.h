@@ -58,6 +58,12 @@ extern "C" {
 #define ADMM_REG_TV     0   /* isotropic TV, eq. unconstrained_TV_uBC            */
 #define ADMM_REG_HAAR   1   /* l1 of undecimated Haar analysis coefficients,
                                eq. unconstrained_analysis_uBC                    */
+/* Variants beyond the paper's two priors (same x-step; only the prox of the
+   regulariser changes). */
+#define ADMM_REG_TV_ANISO      2   /* anisotropic TV, lambda sum_i (|Dh x|_i + |Dv x|_i):
+                                      eq. soft per difference component            */
+#define ADMM_REG_HAAR_LL_FREE  3   /* frame prior with the last low-low band
+                                      unpenalised (its prox is the identity)       */
 
 #define ADMM_STOP_ITERS   0 /* run exactly max_iters iterations                  */
 #define ADMM_STOP_REL_X   1 /* ||x_k - x_{k-1}|| / ||x_k|| < tol                 */
@@ -77,8 +83,9 @@ typedef struct {
                               a value <= 0 selects the default rule: mu2 = 10 lambda
                               (Sec. V) and mu1 = min(1, 3 mu2) (Sec. V's mu1 rule is
                               garbled; penalties change only the speed, Theorem 1)          */
-    int   reg;             /* ADMM_REG_TV or ADMM_REG_HAAR                                  */
-    int   haar_levels;     /* frame levels for ADMM_REG_HAAR, 1..4 (0 = 4)                 */
+    int   reg;             /* ADMM_REG_TV, ADMM_REG_HAAR, ADMM_REG_TV_ANISO or
+                              ADMM_REG_HAAR_LL_FREE                                         */
+    int   haar_levels;     /* frame levels for the frame priors, 1..4 (0 = 4)              */
     int   stop;            /* ADMM_STOP_*                                                   */
     double tol;            /* tolerance of the stop rule                                    */
     int   max_iters;       /* iteration cap (> 0)                                           */
@@ -222,7 +229,9 @@ ADMM_API int admm_deconv_profile(int enable, admm_profile_t* out);
  * (device, H, W, regulariser, levels), says which configuration new plans of
  * that class use; untuned classes use index 0 of each list and 2400 CTAs.
  * Plans keep the configuration they were created with, and a batch groups
- * plans by shape AND configuration. The table is library-global. */
+ * plans by shape AND configuration. The table is library-global. Entries are
+ * per kernel family: plans of ADMM_REG_TV_ANISO use the ADMM_REG_TV entry,
+ * plans of ADMM_REG_HAAR_LL_FREE the ADMM_REG_HAAR entry. */
 typedef struct {
     int    H, W;            /* [in] the size class ...                                        */
     int    reg;             /* [in] ... ADMM_REG_TV or ADMM_REG_HAAR ...                      */

@@ -36,6 +36,7 @@ struct admm_plan_s {
     int device = 0;
     int Wc = 0, Wp = 0, cb = 0, R = 0, n_strips = 0, n_slots = 0, nb = 0, levels = 0;
     int row_v = 0, col_v = 0, slot_ctas = 0, lanes = 0;   // launch configuration (tuning table at plan time)
+    int fam = ADMM_REG_TV;      // kernel family: ADMM_REG_TV (isotropic or anisotropic) or ADMM_REG_HAAR
     float lam = 0.f, mu1 = 0.f, mu2 = 0.f;
     void* slab = nullptr;
     float4* Sa = nullptr;
@@ -325,6 +326,12 @@ void free_plan(admm_plan_s* pl) {
     delete pl;
 }
 
+// kernel family of a regulariser (the variants share their family's kernels)
+int reg_family(int reg) { return (reg == ADMM_REG_TV || reg == ADMM_REG_TV_ANISO) ? ADMM_REG_TV : ADMM_REG_HAAR; }
+bool reg_known(int reg) {
+    return reg == ADMM_REG_TV || reg == ADMM_REG_HAAR || reg == ADMM_REG_TV_ANISO || reg == ADMM_REG_HAAR_LL_FREE;
+}
+
 ProbDesc make_desc(const admm_plan_s* pl) {
     ProbDesc d{};
     d.Sa = pl->Sa;
@@ -352,6 +359,8 @@ ProbDesc make_desc(const admm_plan_s* pl) {
     d.n_strips = pl->n_strips;
     d.n_slots = pl->n_slots;
     d.warm = pl->warm_pending ? 1 : 0;
+    d.aniso = pl->p.reg == ADMM_REG_TV_ANISO ? 1 : 0;
+    d.ll_free = pl->p.reg == ADMM_REG_HAAR_LL_FREE ? 1 : 0;
     d.tol = pl->p.tol;
     return d;
 }
@@ -382,11 +391,12 @@ int admm_deconv_plan(admm_plan_t* out, const admm_params_t* p, void* stream) {
     if (p->psf_h < 1 || p->psf_w < 1 || (p->psf_h & 1) == 0 || (p->psf_w & 1) == 0) return ADMM_EINVAL;
     if (p->psf_h > std::min(p->H, kMaxPsfSide) || p->psf_w > std::min(p->W, kMaxPsfSide)) return ADMM_EINVAL;
     if (!(p->lambda >= 0.f) || !std::isfinite(p->lambda)) return ADMM_EINVAL;
-    if (p->reg != ADMM_REG_TV && p->reg != ADMM_REG_HAAR) return ADMM_EINVAL;
+    if (!reg_known(p->reg)) return ADMM_EINVAL;
     if (p->stop < ADMM_STOP_ITERS || p->stop > ADMM_STOP_REL_OBJ) return ADMM_EINVAL;
     if (p->max_iters <= 0 || p->check_every < 1 || !(p->tol >= 0.0)) return ADMM_EINVAL;
-    const int levels = p->reg == ADMM_REG_HAAR ? (p->haar_levels == 0 ? 4 : p->haar_levels) : 0;
-    if (p->reg == ADMM_REG_HAAR && (levels < 1 || levels > kMaxHaarLevels)) return ADMM_EINVAL;
+    const int fam = reg_family(p->reg);
+    const int levels = fam == ADMM_REG_HAAR ? (p->haar_levels == 0 ? 4 : p->haar_levels) : 0;
+    if (fam == ADMM_REG_HAAR && (levels < 1 || levels > kMaxHaarLevels)) return ADMM_EINVAL;
     double psum = 0.0;
     for (int i = 0; i < p->psf_h * p->psf_w; ++i) {
         if (!std::isfinite(p->psf[i])) return ADMM_EINVAL;
@@ -413,7 +423,7 @@ int admm_deconv_plan(admm_plan_t* out, const admm_params_t* p, void* stream) {
     const size_t n = (size_t)H * W;
     pl->Wc = W / 2 + 1;
     {
-        const admm_tuning_t tu = lookup_tuning(pl->device, H, W, p->reg, levels);
+        const admm_tuning_t tu = lookup_tuning(pl->device, H, W, fam, levels);
         const ColVariant* cv = nullptr;
         col_variants(H, &cv);
         pl->col_v = tu.col_variant;
@@ -423,7 +433,8 @@ int admm_deconv_plan(admm_plan_t* out, const admm_params_t* p, void* stream) {
         pl->cb = cv[pl->col_v].CB;
     }
     pl->Wp = (int)align_up(pl->Wc, pl->cb);
-    if (p->reg == ADMM_REG_TV) {
+    pl->fam = fam;
+    if (fam == ADMM_REG_TV) {
         const RowVariant* rv = nullptr;
         tv_row_variants(W, &rv);
         pl->R = rv[pl->row_v].R;
@@ -432,7 +443,7 @@ int admm_deconv_plan(admm_plan_t* out, const admm_params_t* p, void* stream) {
         pl->R = haar_row_strip(W);
         pl->nb = 3 * levels + 1;
     }
-    if (p->reg == ADMM_REG_TV) {
+    if (fam == ADMM_REG_TV) {
         pl->n_strips = H / pl->R;
         pl->n_slots = pl->n_strips;
     } else {
@@ -450,7 +461,7 @@ int admm_deconv_plan(admm_plan_t* out, const admm_params_t* p, void* stream) {
     const size_t od2 = take(2 * (size_t)pl->nb * n * sizeof(float));
     const size_t oyb = take(n * sizeof(float));
     const size_t oxp = take(n * sizeof(float));
-    const size_t owk = take(p->reg == ADMM_REG_HAAR ? 3 * n * sizeof(float) : 0);
+    const size_t owk = take(fam == ADMM_REG_HAAR ? 3 * n * sizeof(float) : 0);
     const size_t omk = take(n);
     const size_t olm = take((size_t)pl->Wc * H * sizeof(float2));
     const size_t okt = take((size_t)pl->Wc * H * sizeof(float));
@@ -472,7 +483,7 @@ int admm_deconv_plan(admm_plan_t* out, const admm_params_t* p, void* stream) {
     pl->d2 = reinterpret_cast<float*>(b + od2);
     pl->ybar = reinterpret_cast<float*>(b + oyb);
     pl->xprev = reinterpret_cast<float*>(b + oxp);
-    pl->work = p->reg == ADMM_REG_HAAR ? reinterpret_cast<float*>(b + owk) : nullptr;
+    pl->work = fam == ADMM_REG_HAAR ? reinterpret_cast<float*>(b + owk) : nullptr;
     pl->mask = reinterpret_cast<uint8_t*>(b + omk);
     pl->lamT = reinterpret_cast<float2*>(b + olm);
     pl->kT = reinterpret_cast<float*>(b + okt);
@@ -490,7 +501,7 @@ int admm_deconv_plan(admm_plan_t* out, const admm_params_t* p, void* stream) {
             cudaSuccess) { rc = ADMM_ECUDA; break; }
         const int tot = H * pl->Wc;
         spectra_kernel<<<(tot + 255) / 256, 256, 0, s>>>(pl->lamT, pl->kT, pl->psf_dev, p->psf_h, p->psf_w, H, W,
-                                                         pl->Wc, p->reg == ADMM_REG_TV ? 0 : 1,
+                                                         pl->Wc, fam == ADMM_REG_TV ? 0 : 1,
                                                          (double)mu2 / (double)mu1);
         if (cudaGetLastError() != cudaSuccess) { rc = ADMM_ECUDA; break; }
         if (cudaStreamSynchronize(s) != cudaSuccess) { rc = ADMM_ECUDA; break; }
@@ -681,7 +692,7 @@ static int solve_all(DeviceCtx* ctx, const std::vector<std::vector<int>>& classe
         g.Wc = p0->Wc;
         g.Wp = p0->Wp;
         g.levels = p0->levels;
-        g.tv = p0->p.reg == ADMM_REG_TV;
+        g.tv = p0->fam == ADMM_REG_TV;
         g.R = p0->R;
         g.row_v = p0->row_v;
         g.col_v = p0->col_v;

@@ -273,8 +273,10 @@ haar_analysis(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W, in
         Ain = Aout;
         Aout = tmp;
     }
-    // the last low-low band a_L on the tile
+    // the last low-low band a_L on the tile (threshold 0 when it is unpenalised)
     {
+        const bool ll_free = P.ll_free != 0;
+        const float tau_ll = ll_free ? 0.f : tau;
         float dold[OWN];
 #pragma unroll
         for (int i = 0; i < OWN; ++i) dold[i] = first ? 0.f : d2s[(3 * L) * T * T + (warp + NWARP * i) * T + lane];
@@ -284,11 +286,11 @@ haar_analysis(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W, in
             const float cb = Ain[rr * XA + lane];
             const size_t gp = gp0 + (size_t)(NWARP * i) * W;
             const float sv = cb - dold[i];
-            const float u = soft_thresh(sv, tau);
+            const float u = soft_thresh(sv, tau_ll);
             const float nd = u - sv;
             d2out[(size_t)(3 * L) * n + gp] = nd;
             d2io[(size_t)(3 * L) * n + gp] = u + nd;
-            if (nobj) l1.add(fabsf(cb));
+            if (nobj && !ll_free) l1.add(fabsf(cb));
         }
     }
     double pv[kNumPartials] = {0.0, 0.0, 0.0, 0.0};

@@ -84,6 +84,8 @@ struct ProbDesc {
     int n_slots;              // partial-sum slots to reduce (0: n_strips)
     int warm;                 // 1: start from x1 = x0, d0 given (Sb holds the row-DFTs
                               // of x0, d1/d2 buffer 0 hold d0); 0: u0 = d0 = 0
+    int aniso;                // TV: 1 = anisotropic (soft threshold per component)
+    int ll_free;              // frame prior: 1 = the last low-low band unpenalised
     double tol;
 };
 
@@ -162,6 +164,25 @@ __device__ __forceinline__ void cp_async_wait_n(int n) {
 // completion to wait for); `bytes` a multiple of 16, `p` 16-byte aligned.
 __device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(p), "r"(bytes) : "memory");
+}
+
+// prox of the TV term at s = D_i x - d2_i (Alg. 3 line 10): vector-soft
+// with threshold tau (isotropic; 0/0 = 0, via the scale max(0, 1 - tau/|s|)
+// from one reciprocal square root, |s| = 0 giving -inf inside the max) or
+// eq. soft per component (anisotropic)
+__device__ __forceinline__ void tv_prox(float sh, float sv, float tau, bool aniso, float& uh, float& uv) {
+    if (aniso) {
+        uh = copysignf(fmaxf(fabsf(sh) - tau, 0.f), sh);
+        uv = copysignf(fmaxf(fabsf(sv) - tau, 0.f), sv);
+    } else {
+        const float sc = fmaxf(0.f, fmaf(-tau, rsqrtf(fmaf(sh, sh, sv * sv)), 1.f));
+        uh = sc * sh;
+        uv = sc * sv;
+    }
+}
+// the TV term of the objective at D_i x = (gh, gv)
+__device__ __forceinline__ float tv_norm(float gh, float gv, bool aniso) {
+    return aniso ? fabsf(gh) + fabsf(gv) : sqrtf(fmaf(gh, gh, gv * gv));
 }
 
 // observed pixels carry M^T y, unobserved ones a quiet NaN (eq. prox_g_1_uBC)
@@ -656,6 +677,7 @@ row_phase_tv(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp, co
 
     // (2) proxes and dual updates, each warp walking down its columns
     const float tau = P.tau, gam = P.gamma, mu1 = P.mu1, inv1 = P.inv1pmu1;
+    const bool aniso = P.aniso != 0;
     CompSum s_data, s_reg, s_xx, s_dxx;
     float dvprev[C::CPT];
     const bool need_xp = chk && !first;
@@ -727,17 +749,17 @@ row_phase_tv(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp, co
                 float nh[2], nv[2];
 #pragma unroll
                 for (int e = 0; e < 2; ++e) {
-                    // D_i x, u2 = v-soft(D_i x - d2, lambda/mu2), d2 <- d2 - (D_i x - u2),
+                    // D_i x, u2 = prox(D_i x - d2, lambda/mu2), d2 <- d2 - (D_i x - u2),
                     // delta = u2 + d2  (Alg. 3 lines 3-5, 9-11; as in the single-column walk)
                     const float gh = xrs[e] - xs[e], gv = xds[e] - xs[e];
                     const float sh = gh - ddh[e], sv = gv - ddv[e];
-                    const float sc = fmaxf(0.f, fmaf(-tau, rsqrtf(fmaf(sh, sh, sv * sv)), 1.f));
-                    const float uh = sc * sh, uv = sc * sv;
+                    float uh, uv;
+                    tv_prox(sh, sv, tau, aniso, uh, uv);
                     nh[e] = uh - sh;
                     nv[e] = uv - sv;
                     dhcur[2 * pp + e] = uh + nh[e];
                     dvcur[2 * pp + e] = uv + nv[e];
-                    if (owned && nobj) s_reg.add(sqrtf(fmaf(gh, gh, gv * gv)));
+                    if (owned && nobj) s_reg.add(tv_norm(gh, gv, aniso));
                 }
                 if (owned) {
                     *reinterpret_cast<float4*>(d2out + pix) = make_float4(nh[0], nv[0], nh[1], nv[1]);
@@ -773,8 +795,9 @@ row_phase_tv(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp, co
                 const float xhr = xa[0].x;
                 const float2 dd = cold ? make_float2(0.f, 0.f) : *reinterpret_cast<const float2*>(slot + 4 * W + 2 * wid);
                 const float sh = (xhr - xh) - dd.x, sv = (xl_nb_dn - xh) - dd.y;
-                const float sc = fmaxf(0.f, fmaf(-tau, rsqrtf(fmaf(sh, sh, sv * sv)), 1.f));
-                dh_halo = 2.f * sc * sh - sh;
+                float uh, uv;
+                tv_prox(sh, sv, tau, aniso, uh, uv);
+                dh_halo = 2.f * uh - sh;
             }
             issue(i + D);            // slot (i % D) is consumed: refill it D rows ahead
             // delta_h left of each column: the pair's own first column for the
@@ -820,12 +843,10 @@ row_phase_tv(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp, co
                 const size_t pix = (size_t)q * W + c;
                 const float2 dd = cold ? make_float2(0.f, 0.f)
                                        : (D > 0 ? *reinterpret_cast<const float2*>(slot + 2 * c) : d2in[pix]);
-                // u2 = v-soft(D_i x - d2, lambda/mu2)  (Alg. 3 line 10, 0/0 = 0):
-                // the scale max(0, 1 - tau / |s|), with one reciprocal square
-                // root (|s| = 0 gives -inf inside the max, so 0)
+                // u2 = prox(D_i x - d2, lambda/mu2)  (Alg. 3 line 10)
                 const float sh = gh - dd.x, sv = gv - dd.y;
-                const float sc = fmaxf(0.f, fmaf(-tau, rsqrtf(fmaf(sh, sh, sv * sv)), 1.f));
-                const float uh = sc * sh, uv = sc * sv;
+                float uh, uv;
+                tv_prox(sh, sv, tau, aniso, uh, uv);
                 // d2 <- d2 - (D_i x - u2)  (Alg. 3 line 11)
                 const float nh = uh - sh, nv = uv - sv;
                 // delta = u2 + d2 for the next x-step (Alg. 3 lines 3-5)
@@ -849,7 +870,7 @@ row_phase_tv(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp, co
                             const float e = ax - yb;
                             s_data.add(0.5f * e * e);
                         }
-                        s_reg.add(sqrtf(fmaf(gh, gh, gv * gv)));
+                        s_reg.add(tv_norm(gh, gv, aniso));
                     }
                     if (chk) {
                         const float dx = first ? x : x - xpc[j];
@@ -867,8 +888,9 @@ row_phase_tv(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp, co
                                         : (D > 0 ? *reinterpret_cast<const float2*>(slot + 4 * W + 2 * wid)
                                                  : d2in[(size_t)q * W + chalo]);
                 const float sh = (xhr - xh) - dd.x, sv = (xl_nb_dn - xh) - dd.y;
-                const float sc = fmaxf(0.f, fmaf(-tau, rsqrtf(fmaf(sh, sh, sv * sv)), 1.f));
-                dh_halo = 2.f * sc * sh - sh;
+                float uh, uv;
+                tv_prox(sh, sv, tau, aniso, uh, uv);
+                dh_halo = 2.f * uh - sh;
             }
         }
         issue(i + D);                // slot (i % D) is consumed: refill it D rows ahead
