@@ -359,7 +359,6 @@ ProbDesc make_desc(const admm_plan_s* pl) {
     d.n_strips = pl->n_strips;
     d.n_slots = pl->n_slots;
     d.warm = pl->warm_pending ? 1 : 0;
-    d.aniso = pl->p.reg == ADMM_REG_TV_ANISO ? 1 : 0;
     d.ll_free = pl->p.reg == ADMM_REG_HAAR_LL_FREE ? 1 : 0;
     d.tol = pl->p.tol;
     return d;
@@ -705,7 +704,7 @@ static int solve_all(DeviceCtx* ctx, const std::vector<std::vector<int>>& classe
             if (g.tv) {
                 const RowVariant* rv = nullptr;
                 tv_row_variants(g.W, &rv);
-                g.row_fn = rv[g.row_v].fn;
+                g.row_fn = p0->p.reg == ADMM_REG_TV_ANISO ? rv[g.row_v].fn_aniso : rv[g.row_v].fn;
             }
         }
         g.off = (int)order.size();

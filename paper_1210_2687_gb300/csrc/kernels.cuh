@@ -84,7 +84,6 @@ struct ProbDesc {
     int n_slots;              // partial-sum slots to reduce (0: n_strips)
     int warm;                 // 1: start from x1 = x0, d0 given (Sb holds the row-DFTs
                               // of x0, d1/d2 buffer 0 hold d0); 0: u0 = d0 = 0
-    int aniso;                // TV: 1 = anisotropic (soft threshold per component)
     int ll_free;              // frame prior: 1 = the last low-low band unpenalised
     double tol;
 };
@@ -537,7 +536,8 @@ struct RowCfg {
     static constexpr int MINB = NT == 128 ? (D == 0 ? 5 : 4) : (NT == 64 ? 8 : 2);
 };
 
-template <int W, int R, int D, int NT>
+// ANISO: anisotropic TV (soft threshold per difference component)
+template <int W, int R, int D, int NT, bool ANISO = false>
 __global__ void __launch_bounds__(NT, (RowCfg<W, R, D, NT>::MINB))
 row_phase_tv(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp, const float2* __restrict__ tw_g,
              int* __restrict__ n_active) {
@@ -677,7 +677,7 @@ row_phase_tv(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp, co
 
     // (2) proxes and dual updates, each warp walking down its columns
     const float tau = P.tau, gam = P.gamma, mu1 = P.mu1, inv1 = P.inv1pmu1;
-    const bool aniso = P.aniso != 0;
+    constexpr bool aniso = ANISO;
     CompSum s_data, s_reg, s_xx, s_dxx;
     float dvprev[C::CPT];
     const bool need_xp = chk && !first;

@@ -21,7 +21,8 @@ using ColLaunchFn = cudaError_t (*)(const ProbDesc* d, SlotTable sl, int count, 
 
 struct RowVariant {
     int R, D, NT;
-    RowLaunchFn fn;
+    RowLaunchFn fn;          // isotropic TV
+    RowLaunchFn fn_aniso;    // anisotropic TV
 };
 struct ColVariant {
     int CB;
@@ -39,19 +40,19 @@ int tv_row_variants_small(int W, const RowVariant** out);   // W = 64, 128, 256
 int tv_row_variants_512(const RowVariant** out);            // W = 512
 int tv_row_variants_large(int W, const RowVariant** out);   // W = 1024, 2048
 
-template <int W, int R, int D, int NT>
+template <int W, int R, int D, int NT, bool ANISO>
 cudaError_t launch_row_tv_t(const ProbDesc* d, SlotTable sl, int count, int H, int Wp, const float2* tw,
                             int* n_active, cudaStream_t s) {
     static bool attr = false;
     const size_t smem = RowCfg<W, R, D, NT>::SMEM;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(row_phase_tv<W, R, D, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(row_phase_tv<W, R, D, NT, ANISO>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         attr = true;
     }
     dim3 grid(H / R, count);
-    row_phase_tv<W, R, D, NT><<<grid, NT, smem, s>>>(d, sl, H, Wp, tw, n_active);
+    row_phase_tv<W, R, D, NT, ANISO><<<grid, NT, smem, s>>>(d, sl, H, Wp, tw, n_active);
     return cudaGetLastError();
 }
 
@@ -73,7 +74,7 @@ cudaError_t launch_col_t(const ProbDesc* d, SlotTable sl, int count, int Wc, int
 
 template <int W, int R, int D, int NT>
 constexpr RowVariant row_variant() {
-    return RowVariant{R, D, NT, &launch_row_tv_t<W, R, D, NT>};
+    return RowVariant{R, D, NT, &launch_row_tv_t<W, R, D, NT, false>, &launch_row_tv_t<W, R, D, NT, true>};
 }
 // MB > 0: registers sized for MB CTAs per SM instead of the default
 template <int H, int CB, int MB = 0>
