@@ -582,6 +582,7 @@ struct GroupRun {
     int off = 0, count = 0, nslots = 0, max_iters = 0, qbase = 0;
     int gi = 0;                  // index of the class's n_active counter
     int R = 0, row_v = 0, col_v = 0, slot_ctas = 0, lanes = 0;
+    int reg = 0;                 // the regulariser (variants share a family but not kernels)
     RowLaunchFn row_fn = nullptr;  // TV row phase of the class's configuration
     ColLaunchFn col_fn = nullptr;
     long long launch_cap = 0;    // iterations after which every problem has retired
@@ -608,7 +609,8 @@ static std::string graph_key(const std::vector<GroupRun>& groups, int chunk) {
     std::string k = std::to_string(chunk);
     for (const GroupRun& g : groups) {
         k += "|" + std::to_string(g.H) + "," + std::to_string(g.W) + "," + std::to_string(g.tv) + "," +
-             std::to_string(g.levels) + "," + std::to_string(g.row_v) + "," + std::to_string(g.col_v) + "," +
+             std::to_string(g.levels) + "," + std::to_string(g.reg) + "," + std::to_string(g.row_v) + "," +
+             std::to_string(g.col_v) + "," +
              std::to_string(g.off) + "," + std::to_string(g.count) + "," +
              std::to_string(g.qbase) + "," + std::to_string(g.L.n);
         for (int l = 0; l < g.L.n; ++l)
@@ -692,6 +694,7 @@ static int solve_all(DeviceCtx* ctx, const std::vector<std::vector<int>>& classe
         g.Wp = p0->Wp;
         g.levels = p0->levels;
         g.tv = p0->fam == ADMM_REG_TV;
+        g.reg = p0->p.reg;
         g.R = p0->R;
         g.row_v = p0->row_v;
         g.col_v = p0->col_v;

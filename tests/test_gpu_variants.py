@@ -122,3 +122,17 @@ def test_variants_and_paper_priors_in_one_batch(ad):
         assert _rel(xg.cpu().numpy().astype(np.float64), ref.x) <= 2e-5, r
     for p in plans:
         p.close()
+
+
+def test_replayed_graphs_follow_the_regulariser(ad):
+    """Isotropic and anisotropic TV classes of one shape and configuration have
+    the same batch layout; the replayed iteration graphs (chunks of eight
+    iterations, cached by layout) must still run each class's own kernel."""
+    psf = S.psf_box(5)
+    _, ybar, mask = _problem(64, 64, 500, psf)
+    lam, mu1, mu2, iters = 3e-4, 1e-2, 3e-3, 40
+    for reg in ("tv", "tv_aniso", "tv"):
+        ref = O.solve(ybar, mask, psf, lam, mu1, mu2, reg, iters=iters)
+        x, _, res = _gpu(ad, reg, ybar, mask, psf, lam, mu1, mu2, iters)
+        assert res.iters == iters
+        assert _rel(x, ref.x) <= 1e-4, reg
