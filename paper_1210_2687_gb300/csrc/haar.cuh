@@ -158,7 +158,6 @@ haar_analysis(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W, in
               int* __restrict__ n_active) {
     using C = HaarAnaCfg<L>;
     constexpr int T = C::T, XA = C::XA, XR = C::XR;
-    constexpr int NWARP = kThreads / 32;
     const int pi = sl.map[blockIdx.y];
     if (pi < 0) return;
     const ProbDesc& P = probs[pi];
@@ -172,7 +171,7 @@ haar_analysis(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W, in
     float* Aout = sm + XR * XA;
     float* d2s = sm + C::D2S_OFF;
     double* red = reinterpret_cast<double*>(sm + C::RED_OFF);
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x;
     const int tiles_x = W / T;
     const int R0 = (blockIdx.x / tiles_x) * T, C0 = (blockIdx.x % tiles_x) * T;
     const size_t n = (size_t)H * W;
@@ -181,7 +180,7 @@ haar_analysis(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W, in
     const float tau = P.tau;
 
     // x on [0, T + HALO) x [0, T + 16) with periodic wrap, 16-byte copies (the
-    // tile origin is a multiple of 32 columns); warp w takes rows w, w + 8, ...
+    // tile origin is a multiple of 32 columns)
     constexpr int CH = XA / 4;
     for (int e = tid; e < XR * CH; e += kThreads) {
         const int rr = e / CH, ch = e - rr * CH;
@@ -189,12 +188,15 @@ haar_analysis(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W, in
         cp_async16(Ain + rr * XA + 4 * ch, src);
     }
     cp_async_commit();
-    // thread (warp, lane) owns the tile pixels (warp + 8 i, lane), i < T / 8.
-    // Every thread stages the previous d2 of its own pixels, one cp.async
-    // group per level (the last with the low-low band), all requested now:
-    // it reads only what it copied itself, so these need no block barrier.
-    constexpr int OWN = T / NWARP;
-    const size_t gp0 = (size_t)(R0 + warp) * W + (C0 + lane);
+    // thread t owns the four adjacent tile pixels of row t / 8, columns
+    // 4 (t % 8) .. + 3: 16-byte reads of x and of the staged d2, 16-byte
+    // stores of the new d2 and of zeta2. Every thread stages the previous d2
+    // of its own pixels, one cp.async group per level (the last with the
+    // low-low band), all requested now: it reads only what it copied itself,
+    // so these need no block barrier.
+    static_assert(T * T == 4 * kThreads, "four owned pixels per thread");
+    const int orow = tid >> 3, ocol = 4 * (tid & 7);
+    const size_t gq = (size_t)(R0 + orow) * W + (C0 + ocol);
 #pragma unroll
     for (int lvl = 0; lvl < L; ++lvl) {
         if (!first) {
@@ -202,10 +204,7 @@ haar_analysis(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W, in
 #pragma unroll
             for (int j = 0; j < nb; ++j) {
                 const int b = 3 * lvl + j;
-#pragma unroll
-                for (int i = 0; i < OWN; ++i)
-                    cp_async4(d2s + b * T * T + (warp + NWARP * i) * T + lane,
-                              d2io + (size_t)b * n + gp0 + (size_t)(NWARP * i) * W);
+                cp_async16(d2s + b * T * T + orow * T + ocol, d2io + (size_t)b * n + gq);
             }
         }
         cp_async_commit();
@@ -219,34 +218,53 @@ haar_analysis(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W, in
         const int s = 1 << lvl;
         // this level's previous d2 at the owned pixels (staged at entry)
         cp_async_wait_n(L - 1 - lvl);
-        float dold[OWN][3];
+        float dold[3][4];
 #pragma unroll
-        for (int i = 0; i < OWN; ++i)
-#pragma unroll
-            for (int j = 0; j < 3; ++j)
-                dold[i][j] = first ? 0.f : d2s[(3 * lvl + j) * T * T + (warp + NWARP * i) * T + lane];
+        for (int j = 0; j < 3; ++j) {
+            const float4 v = first ? make_float4(0.f, 0.f, 0.f, 0.f)
+                                   : *reinterpret_cast<const float4*>(d2s + (3 * lvl + j) * T * T + orow * T + ocol);
+            dold[j][0] = v.x; dold[j][1] = v.y; dold[j][2] = v.z; dold[j][3] = v.w;
+        }
         const int D = T + (1 << L) - 2 * s;      // a_{lvl+1} is needed on [0, D)^2
-        // owned pixels (row warp + 8 i, column lane): approximation, detail
-        // bands, soft threshold and dual updates
+        // owned pixels: approximation, detail bands, soft threshold and dual
+        // updates. a_lvl on rows orow and orow + s, columns ocol .. ocol + 3 + s
+        float w0[12], w1[12];
+        const int NW = s > 4 ? 3 : 2;            // float4 words covering 4 + s columns
 #pragma unroll
-        for (int i = 0; i < OWN; ++i) {
-            const int i00 = (warp + NWARP * i) * XA + lane;
-            const float a00 = Ain[i00], a01 = Ain[i00 + s];
-            const float a10 = Ain[i00 + s * XA], a11 = Ain[i00 + s * XA + s];
+        for (int q = 0; q < 3; ++q) {
+            if (q < NW) {
+                const float4 u0 = *reinterpret_cast<const float4*>(Ain + orow * XA + ocol + 4 * q);
+                const float4 u1 = *reinterpret_cast<const float4*>(Ain + (orow + s) * XA + ocol + 4 * q);
+                w0[4 * q] = u0.x; w0[4 * q + 1] = u0.y; w0[4 * q + 2] = u0.z; w0[4 * q + 3] = u0.w;
+                w1[4 * q] = u1.x; w1[4 * q + 1] = u1.y; w1[4 * q + 2] = u1.z; w1[4 * q + 3] = u1.w;
+            } else {
+#pragma unroll
+                for (int e = 0; e < 4; ++e) w0[4 * q + e] = w1[4 * q + e] = 0.f;
+            }
+        }
+        float ao[4], nd4[3][4], z4[3][4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const float a00 = w0[e], a01 = w0[e + s], a10 = w1[e], a11 = w1[e + s];
             const float p0 = a00 + a01, m0 = a00 - a01, p1 = a10 + a11, m1 = a10 - a11;
-            Aout[i00] = 0.25f * (p0 + p1);
+            ao[e] = 0.25f * (p0 + p1);
             // detail bands: rows low / cols high, rows high / cols low, both high
             const float cb[3] = {0.25f * (m0 + m1), 0.25f * (p0 - p1), 0.25f * (m0 - m1)};
-            const size_t gp = gp0 + (size_t)(NWARP * i) * W;
 #pragma unroll
             for (int j = 0; j < 3; ++j) {
-                const float sv = cb[j] - dold[i][j];
+                const float sv = cb[j] - dold[j][e];
                 const float u = soft_thresh(sv, tau);           // eq. soft
-                const float nd = u - sv;                        // d2 - (c - u2)
-                d2out[(size_t)(3 * lvl + j) * n + gp] = nd;
-                d2io[(size_t)(3 * lvl + j) * n + gp] = u + nd;  // zeta2 = u2 + d2
+                nd4[j][e] = u - sv;                             // d2 - (c - u2)
+                z4[j][e] = u + nd4[j][e];                       // zeta2 = u2 + d2
                 if (nobj) l1.add(fabsf(cb[j]));
             }
+        }
+        *reinterpret_cast<float4*>(Aout + orow * XA + ocol) = make_float4(ao[0], ao[1], ao[2], ao[3]);
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const size_t bo = (size_t)(3 * lvl + j) * n + gq;
+            *reinterpret_cast<float4*>(d2out + bo) = make_float4(nd4[j][0], nd4[j][1], nd4[j][2], nd4[j][3]);
+            *reinterpret_cast<float4*>(d2io + bo) = make_float4(z4[j][0], z4[j][1], z4[j][2], z4[j][3]);
         }
         // the approximation on the rest of [0, D)^2 that later levels read
         // (rows [0, T) x columns [T, D), then rows [T, D) x columns [0, D)),
@@ -277,21 +295,22 @@ haar_analysis(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W, in
     {
         const bool ll_free = P.ll_free != 0;
         const float tau_ll = ll_free ? 0.f : tau;
-        float dold[OWN];
+        const float4 dv = first ? make_float4(0.f, 0.f, 0.f, 0.f)
+                                : *reinterpret_cast<const float4*>(d2s + (3 * L) * T * T + orow * T + ocol);
+        const float4 cv = *reinterpret_cast<const float4*>(Ain + orow * XA + ocol);
+        const float dold[4] = {dv.x, dv.y, dv.z, dv.w}, cb[4] = {cv.x, cv.y, cv.z, cv.w};
+        float nd[4], z[4];
 #pragma unroll
-        for (int i = 0; i < OWN; ++i) dold[i] = first ? 0.f : d2s[(3 * L) * T * T + (warp + NWARP * i) * T + lane];
-#pragma unroll
-        for (int i = 0; i < OWN; ++i) {
-            const int rr = warp + NWARP * i;
-            const float cb = Ain[rr * XA + lane];
-            const size_t gp = gp0 + (size_t)(NWARP * i) * W;
-            const float sv = cb - dold[i];
+        for (int e = 0; e < 4; ++e) {
+            const float sv = cb[e] - dold[e];
             const float u = soft_thresh(sv, tau_ll);
-            const float nd = u - sv;
-            d2out[(size_t)(3 * L) * n + gp] = nd;
-            d2io[(size_t)(3 * L) * n + gp] = u + nd;
-            if (nobj && !ll_free) l1.add(fabsf(cb));
+            nd[e] = u - sv;
+            z[e] = u + nd[e];
+            if (nobj && !ll_free) l1.add(fabsf(cb[e]));
         }
+        const size_t bo = (size_t)(3 * L) * n + gq;
+        *reinterpret_cast<float4*>(d2out + bo) = make_float4(nd[0], nd[1], nd[2], nd[3]);
+        *reinterpret_cast<float4*>(d2io + bo) = make_float4(z[0], z[1], z[2], z[3]);
     }
     double pv[kNumPartials] = {0.0, 0.0, 0.0, 0.0};
     if (nobj || chk) {
