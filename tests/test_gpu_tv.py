@@ -287,12 +287,27 @@ def test_nonfinite_observation_reports_status(ad):
     assert res.iters < 50
 
 
-def test_full_size_512_config_parity(ad):
+@pytest.mark.parametrize("cfg", [None, dict(row_variant=3, col_variant=0, slot_ctas=4800)],
+                         ids=["default", "tuned"])
+def test_full_size_512_config_parity(ad, cfg):
     """The 512 x 512 inpainting workload at full size (both blurs), batched as
-    the benchmark launches it, 60 iterations against the oracle."""
+    the benchmark launches it, 60 iterations against the oracle; in the
+    default configuration and in the one the autotuner picks on GB300 for this
+    class (16-row strips, walk depth 2, 256 threads; 4 columns per column CTA;
+    4800 row CTAs per launch)."""
     import torch
+    if cfg is not None:
+        t = ad.admm_deconv_get_tuning(512, 512, "tv")
+        t.update(cfg)
+        ad.admm_deconv_set_tuning(t)
+        got = ad.admm_deconv_get_tuning(512, 512, "tv")
+        assert (got["rows_per_strip"], got["walk_depth"], got["row_threads"]) == (16, 2, 256)
     probs = [S.config2_problem(s, blur, 40) for s, blur in ((0, "gauss"), (1, "motion"))]
-    plans = [ad.Plan(512, 512, p.psf, p.lam, p.mu1, p.mu2, "tv", max_iters=60) for p in probs]
+    try:
+        plans = [ad.Plan(512, 512, p.psf, p.lam, p.mu1, p.mu2, "tv", max_iters=60) for p in probs]
+    finally:
+        ad.admm_deconv_set_tuning({"H": 512, "W": 512, "reg": 0, "haar_levels": 0, "row_variant": 0,
+                                   "col_variant": 0, "slot_ctas": 0, "lanes": 0})
     ys = [torch.from_numpy(p.ybar.astype(np.float32)).cuda() for p in probs]
     ms = [torch.from_numpy(p.mask).cuda() for p in probs]
     xs = [torch.empty((512, 512), dtype=torch.float32, device="cuda") for _ in probs]
