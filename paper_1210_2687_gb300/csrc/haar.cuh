@@ -408,19 +408,55 @@ haar_synthesis(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W) {
         const float* Z1 = Z0 + BR * XS;
         const float* Z2 = Z1 + BR * XS;
         const int ra = s * XS, rz = s * XS;
-        // the D x D outputs spread evenly over the block (D is a constant
-        // where the level loop is unrolled)
-        for (int e = tid; e < D * D; e += kThreads) {
-            const int rr = e / D, cc = e - rr * D;
-            const int r = rr - (s - 1), c = cc - (s - 1);
+        // the outputs on [-(s-1), T)^2 in groups of four adjacent columns
+        // starting at 4-aligned columns (a few margin columns more, never read),
+        // spread evenly over the block: 16-byte reads of the eight input rows
+        // (At, Z0, Z1, Z2 at rows r and r - s) over columns c - s .. c + 3, one
+        // 16-byte store (s, D are constants where the level loop is unrolled)
+        const int nwd = s > 4 ? 3 : 2;                 // float4 words covering 4 + s columns
+        const int c0 = -4 * ((s - 1 + 3) / 4);         // first 4-aligned group column
+        const int ng = (T - c0) / 4;
+        for (int e = tid; e < D * ng; e += kThreads) {
+            const int rr = e / ng, gg = e - rr * ng;
+            const int r = rr - (s - 1), c = c0 + 4 * gg;
             const int ia = (r + HALO) * XS + (c + 16);
             const int iz = (r + BO) * XS + (c + 16);
-            // rows adjoint at columns c and c - s
-            const float lo_c = (At[ia] + At[ia - ra]) + (Z1[iz] - Z1[iz - rz]);
-            const float lo_l = (At[ia - s] + At[ia - ra - s]) + (Z1[iz - s] - Z1[iz - rz - s]);
-            const float hi_c = (Z0[iz] + Z0[iz - rz]) + (Z2[iz] - Z2[iz - rz]);
-            const float hi_l = (Z0[iz - s] + Z0[iz - rz - s]) + (Z2[iz - s] - Z2[iz - rz - s]);
-            Ao[ia] = 0.25f * ((lo_c + lo_l) + (hi_c - hi_l));
+            const int wb = -4 * (nwd - 1);             // window starts this many columns before c
+            float a0[12], a1[12], q0[12], q1[12], y0[12], y1[12], v0[12], v1[12];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                if (q < nwd) {
+                    const int o = wb + 4 * q;
+                    const float4 t0 = *reinterpret_cast<const float4*>(At + ia + o);
+                    const float4 t1 = *reinterpret_cast<const float4*>(At + ia - ra + o);
+                    const float4 u0 = *reinterpret_cast<const float4*>(Z1 + iz + o);
+                    const float4 u1 = *reinterpret_cast<const float4*>(Z1 + iz - rz + o);
+                    const float4 g0 = *reinterpret_cast<const float4*>(Z0 + iz + o);
+                    const float4 g1 = *reinterpret_cast<const float4*>(Z0 + iz - rz + o);
+                    const float4 h0 = *reinterpret_cast<const float4*>(Z2 + iz + o);
+                    const float4 h1 = *reinterpret_cast<const float4*>(Z2 + iz - rz + o);
+                    a0[4 * q] = t0.x; a0[4 * q + 1] = t0.y; a0[4 * q + 2] = t0.z; a0[4 * q + 3] = t0.w;
+                    a1[4 * q] = t1.x; a1[4 * q + 1] = t1.y; a1[4 * q + 2] = t1.z; a1[4 * q + 3] = t1.w;
+                    q0[4 * q] = u0.x; q0[4 * q + 1] = u0.y; q0[4 * q + 2] = u0.z; q0[4 * q + 3] = u0.w;
+                    q1[4 * q] = u1.x; q1[4 * q + 1] = u1.y; q1[4 * q + 2] = u1.z; q1[4 * q + 3] = u1.w;
+                    y0[4 * q] = g0.x; y0[4 * q + 1] = g0.y; y0[4 * q + 2] = g0.z; y0[4 * q + 3] = g0.w;
+                    y1[4 * q] = g1.x; y1[4 * q + 1] = g1.y; y1[4 * q + 2] = g1.z; y1[4 * q + 3] = g1.w;
+                    v0[4 * q] = h0.x; v0[4 * q + 1] = h0.y; v0[4 * q + 2] = h0.z; v0[4 * q + 3] = h0.w;
+                    v1[4 * q] = h1.x; v1[4 * q + 1] = h1.y; v1[4 * q + 2] = h1.z; v1[4 * q + 3] = h1.w;
+                }
+            }
+            float out[4];
+#pragma unroll
+            for (int e4 = 0; e4 < 4; ++e4) {
+                const int kc = -wb + e4, kl = kc - s;  // window positions of columns c + e4 and c + e4 - s
+                // rows adjoint at columns c and c - s (as in the scalar form)
+                const float lo_c = (a0[kc] + a1[kc]) + (q0[kc] - q1[kc]);
+                const float lo_l = (a0[kl] + a1[kl]) + (q0[kl] - q1[kl]);
+                const float hi_c = (y0[kc] + y1[kc]) + (v0[kc] - v1[kc]);
+                const float hi_l = (y0[kl] + y1[kl]) + (v0[kl] - v1[kl]);
+                out[e4] = 0.25f * ((lo_c + lo_l) + (hi_c - hi_l));
+            }
+            *reinterpret_cast<float4*>(Ao + ia) = make_float4(out[0], out[1], out[2], out[3]);
         }
         float* tmp = At;
         At = Ao;
