@@ -408,20 +408,20 @@ haar_synthesis(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W) {
         const float* Z1 = Z0 + BR * XS;
         const float* Z2 = Z1 + BR * XS;
         const int ra = s * XS, rz = s * XS;
-        // the outputs on [-(s-1), T)^2 in groups of four adjacent columns
-        // starting at 4-aligned columns (a few margin columns more, never read),
-        // spread evenly over the block: 16-byte reads of the eight input rows
-        // (At, Z0, Z1, Z2 at rows r and r - s) over columns c - s .. c + 3, one
-        // 16-byte store (s, D are constants where the level loop is unrolled)
+        // the outputs on [-(s-1), T)^2. Columns [0, T) in groups of four
+        // adjacent columns, eight groups per row, so that the eight threads of
+        // a 16-byte access phase read one 128-byte row segment: 16-byte reads of
+        // the eight input rows (At, Z0, Z1, Z2 at rows r and r - s) over columns
+        // c - s .. c + 3 and one 16-byte store. The s - 1 halo columns left of
+        // the tile one output per thread. (s, D are constants where the level
+        // loop is unrolled.)
+        static_assert(T == 32, "eight column groups per row");
         const int nwd = s > 4 ? 3 : 2;                 // float4 words covering 4 + s columns
-        const int c0 = -4 * ((s - 1 + 3) / 4);         // first 4-aligned group column
-        const int ng = (T - c0) / 4;
-        for (int e = tid; e < D * ng; e += kThreads) {
-            const int rr = e / ng, gg = e - rr * ng;
-            const int r = rr - (s - 1), c = c0 + 4 * gg;
+        const int wb = -4 * (nwd - 1);                 // the window starts this many columns before c
+        for (int e = tid; e < D * 8; e += kThreads) {
+            const int r = (e >> 3) - (s - 1), c = 4 * (e & 7);
             const int ia = (r + HALO) * XS + (c + 16);
             const int iz = (r + BO) * XS + (c + 16);
-            const int wb = -4 * (nwd - 1);             // window starts this many columns before c
             float a0[12], a1[12], q0[12], q1[12], y0[12], y1[12], v0[12], v1[12];
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
@@ -449,7 +449,7 @@ haar_synthesis(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W) {
 #pragma unroll
             for (int e4 = 0; e4 < 4; ++e4) {
                 const int kc = -wb + e4, kl = kc - s;  // window positions of columns c + e4 and c + e4 - s
-                // rows adjoint at columns c and c - s (as in the scalar form)
+                // rows adjoint at columns c and c - s
                 const float lo_c = (a0[kc] + a1[kc]) + (q0[kc] - q1[kc]);
                 const float lo_l = (a0[kl] + a1[kl]) + (q0[kl] - q1[kl]);
                 const float hi_c = (y0[kc] + y1[kc]) + (v0[kc] - v1[kc]);
@@ -457,6 +457,17 @@ haar_synthesis(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W) {
                 out[e4] = 0.25f * ((lo_c + lo_l) + (hi_c - hi_l));
             }
             *reinterpret_cast<float4*>(Ao + ia) = make_float4(out[0], out[1], out[2], out[3]);
+        }
+        for (int e = tid; e < D * (s - 1); e += kThreads) {
+            const int rr = e / (s > 1 ? s - 1 : 1), cc = e - rr * (s - 1);
+            const int r = rr - (s - 1), c = cc - (s - 1);
+            const int ia = (r + HALO) * XS + (c + 16);
+            const int iz = (r + BO) * XS + (c + 16);
+            const float lo_c = (At[ia] + At[ia - ra]) + (Z1[iz] - Z1[iz - rz]);
+            const float lo_l = (At[ia - s] + At[ia - ra - s]) + (Z1[iz - s] - Z1[iz - rz - s]);
+            const float hi_c = (Z0[iz] + Z0[iz - rz]) + (Z2[iz] - Z2[iz - rz]);
+            const float hi_l = (Z0[iz - s] + Z0[iz - rz - s]) + (Z2[iz - s] - Z2[iz - rz - s]);
+            Ao[ia] = 0.25f * ((lo_c + lo_l) + (hi_c - hi_l));
         }
         float* tmp = At;
         At = Ao;
