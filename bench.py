@@ -312,8 +312,12 @@ def frame_secondary(ad, torch, stream, args):
         pf = ad.admm_deconv_profile(False)
         row_b = 28.0 + 112.0 + 16.0 + 0.8
         col_b = 44.0 * (size // 2 + 1) / size
+        peak, _ = read_peak()
         out[f"fa_md_{size}"] = {
             "iters_per_s": FRAME_ITERS / sec,
+            # whole iteration: algorithmic bytes of both sides over the timed solve
+            "iteration_gbs": FRAME_ITERS * n * (row_b + col_b) / sec / 1e9,
+            "iteration_frac": FRAME_ITERS * n * (row_b + col_b) / sec / 1e9 / peak,
             "row_side_gbs": FRAME_ITERS * n * row_b / (pf.row_ms * 1e-3) / 1e9,
             "col_phase_gbs": FRAME_ITERS * n * col_b / (pf.col_ms * 1e-3) / 1e9,
             "bytes_per_px_iter": {"row_side": row_b, "col_phase": col_b},
