@@ -138,3 +138,21 @@ def test_set_tuning_rejects_out_of_range_on_host(ad, change):
     t = ad.admm_tuning_t(H=500, W=512)
     assert ad.lib.admm_deconv_set_tuning(ctypes.byref(t)) == ad.ADMM_EUNSUPPORTED_SIZE
     assert ad.lib.admm_deconv_set_tuning(None) == ad.ADMM_EINVAL
+
+
+def test_headers_compile_as_c99(tmp_path):
+    """The boundary is plain C: both headers compile as C99 with warnings as
+    errors (no C++ types or syntax leak into the ABI)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "abi.c"
+    src.write_text('#include "admm_deconv.h"\n#include "admm_warmstart.h"\n'
+                   "int main(void) { admm_params_t p; admm_result_t r; admm_tuning_t t; admm_profile_t f;\n"
+                   "  (void)p; (void)r; (void)t; (void)f; return 0; }\n")
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror",
+                        "-I", os.path.join(ROOT, "include"), "-c", str(src), "-o", str(tmp_path / "abi.o")],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
