@@ -73,7 +73,8 @@ def tune_class(ad, torch, args, size_h, size_w, reg, levels=4, problems=0):
     if trials:
         cfg["trials"] = len(trials)
         cfg["trial_table"] = [[t["rows_per_strip"], t["walk_depth"], t["row_threads"], t["col_block"],
-                               t["col_min_ctas"], t["slot_ctas"], t["lanes"], round(t["us_per_iter"], 3)] for t in trials]
+                               t["col_min_ctas"], t["col_persistent"], t["slot_ctas"], t["lanes"],
+                               round(t["us_per_iter"], 3)] for t in trials]
         cfg["us_per_iter_default"] = next((t["us_per_iter"] for t in trials if t["row_variant"] == 0
                                            and t["col_variant"] == 0 and t["slot_ctas"] == 0
                                            and t["lanes"] == 0), None)
@@ -83,8 +84,11 @@ def tune_class(ad, torch, args, size_h, size_w, reg, levels=4, problems=0):
 def kernel_names(cfg, size_h, size_w):
     """Names of the TV row-phase and column-phase kernels of a configuration."""
     mb = f",{cfg['col_min_ctas']}" if cfg.get("col_min_ctas") else ""
+    col = "col_phase_pers" if cfg.get("col_persistent") else "col_phase"
+    if cfg.get("col_persistent"):
+        mb = ""
     return (f"row_phase_tv<{size_w},{cfg['rows_per_strip']},{cfg['walk_depth']},{cfg['row_threads']}>",
-            f"col_phase<{size_h},{cfg['col_block']}{mb}>")
+            f"{col}<{size_h},{cfg['col_block']}{mb}>")
 
 
 def dist_env():

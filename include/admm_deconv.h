@@ -245,8 +245,10 @@ typedef struct {
     int    walk_depth;      /* [out] ... walk rows in flight (0 = read directly), ...        */
     int    row_threads;     /* [out] ... threads per row-phase CTA                           */
     int    col_block;       /* [out] meaning of col_variant: spectrum columns per CTA, ...   */
-    int    col_min_ctas;    /* [out] ... and the CTAs per SM its registers are sized for
-                               (0 = the default for that block)                             */
+    int    col_min_ctas;    /* [out] ... the CTAs per SM its registers are sized for
+                               (0 = the default for that block), ...                        */
+    int    col_persistent;  /* [out] ... and 1 if its CTAs are persistent, walking the
+                               launch's column blocks with a double-buffered tile          */
     double us_per_iter;     /* [out] autotuner: measured device time per problem-iteration
                                in microseconds (0 if the entry was not measured)             */
 } admm_tuning_t;

@@ -89,7 +89,8 @@ class admm_tuning_t(ctypes.Structure):
                 ("row_variant", ctypes.c_int), ("col_variant", ctypes.c_int), ("slot_ctas", ctypes.c_int),
                 ("lanes", ctypes.c_int),
                 ("rows_per_strip", ctypes.c_int), ("walk_depth", ctypes.c_int), ("row_threads", ctypes.c_int),
-                ("col_block", ctypes.c_int), ("col_min_ctas", ctypes.c_int), ("us_per_iter", ctypes.c_double)]
+                ("col_block", ctypes.c_int), ("col_min_ctas", ctypes.c_int), ("col_persistent", ctypes.c_int),
+                ("us_per_iter", ctypes.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -234,6 +234,7 @@ bool describe_tuning(admm_tuning_t* t) {
     if (t->col_variant < 0 || t->col_variant >= nc) return false;
     t->col_block = cv[t->col_variant].CB;
     t->col_min_ctas = cv[t->col_variant].MB;
+    t->col_persistent = cv[t->col_variant].persistent;
     if (t->reg == ADMM_REG_TV) {
         const RowVariant* rv = nullptr;
         const int nr = tv_row_variants(t->W, &rv);

@@ -315,6 +315,117 @@ col_phase(const ProbDesc* __restrict__ probs, SlotTable sl, int Wc, int Wp, cons
 }
 
 // ---------------------------------------------------------------------------
+// Persistent column phase (configurations with one column per transform
+// group): gridDim.x CTAs walk the launch's items (column block, slot), item
+// it = slot * nblk + block. The tile of the next item is requested with
+// cp.async into a second stage while the current one is transformed, so a
+// CTA's loads overlap its own arithmetic. The work per item is that of
+// col_phase.
+// ---------------------------------------------------------------------------
+template <int H, int CB>
+__global__ void __launch_bounds__(kThreads, 3)
+col_phase_pers(const ProbDesc* __restrict__ probs, SlotTable sl, int Wc, int Wp, const float2* __restrict__ tw_g,
+               int nblk, int nitems) {
+    using C = ColCfg<H, CB>;
+    static_assert(C::ALIAS, "one column per transform group");
+    extern __shared__ __align__(16) float4 smem4[];
+    float2* tw = reinterpret_cast<float2*>(smem4 + 2 * H * CB);
+    const int tid = threadIdx.x;
+    const int g = tid / C::FT, t = tid % C::FT;
+    // what an item needs: 0 nothing (no problem in the slot, or retired),
+    // 1 zeros (first iteration from u0 = d0 = 0: x1 = 0), 2 the transforms
+    auto classify = [&](int it, const ProbDesc*& q) -> int {
+        const int pi = sl.map[it / nblk];
+        if (pi < 0) return 0;
+        q = probs + pi;
+        if (q->ctl->active == 0) return 0;
+        return (q->ctl->iter == 0 && !q->warm) ? 1 : 2;
+    };
+    auto request = [&](int it, const ProbDesc* q, float4* stage) {
+        const int c0 = (it % nblk) * CB;
+        const float4* __restrict__ src = q->Sb;
+        for (int e = tid; e < H * CB; e += kThreads) {
+            const int r = e / CB, c = e % CB;
+            cp_async16(stage + tile_slot<CB>(r, c), src + (size_t)r * Wp + c0 + c);
+        }
+    };
+    int it = blockIdx.x, cur = 0;
+    const ProbDesc* Pc = nullptr;
+    int mode = it < nitems ? classify(it, Pc) : 0;
+    if (mode == 2) request(it, Pc, smem4);
+    cp_async_commit();
+    load_twiddles<H>(tw, tw_g, tid, kThreads);
+    for (; it < nitems; it += gridDim.x) {
+        const int nx = it + gridDim.x;
+        const ProbDesc* Pn = nullptr;
+        const int mode_n = nx < nitems ? classify(nx, Pn) : 0;
+        float4* stage = smem4 + cur * H * CB;
+        if (mode_n == 2) request(nx, Pn, smem4 + (cur ^ 1) * H * CB);
+        cp_async_commit();
+        cp_async_wait<1>();          // this item's tile (the next one may still be in flight)
+        __syncthreads();             // ... for every thread; the twiddles too
+        const int c0 = (it % nblk) * CB;
+        if (mode == 1) {
+            for (int e = tid; e < H * CB; e += kThreads)
+                Pc->Sa[(size_t)(e / CB) * Wp + c0 + e % CB] = make_float4(0.f, 0.f, 0.f, 0.f);
+        } else if (mode == 2) {
+            const ProbDesc& P = *Pc;
+            const bool warm0 = P.ctl->iter == 0;
+            float2* bz = reinterpret_cast<float2*>(stage) + (2 * g) * C::SIG;
+            float2* bw = reinterpret_cast<float2*>(stage) + (2 * g + 1) * C::SIG;
+            const int kc = c0 + g;
+            const bool spec = kc < Wc;
+            float2 L[8];
+            float Kv[8];
+            if (spec) {
+                const float2* __restrict__ lcol = P.lamT + (size_t)kc * H;
+                const float* __restrict__ kcol = P.kT + (size_t)kc * H;
+#pragma unroll
+                for (int m = 0; m < 8; ++m) {
+                    L[m] = lcol[t + m * C::FT];
+                    Kv[m] = kcol[t + m * C::FT];
+                }
+            }
+            float2 v[8], u[8];
+#pragma unroll
+            for (int m = 0; m < 8; ++m) {
+                const float4 f = stage[tile_slot<CB>(t + m * C::FT, g)];
+                v[m] = make_float2(f.x, f.y);
+                u[m] = make_float2(f.z, f.w);
+            }
+            __syncthreads();         // every column is in registers: the tile is free
+            fft_group2<H, -1>(v, u, bz, bw, tw, t, g);
+            if (spec) {
+                const float inv_hw = 1.0f / (float)(H * 2 * (Wc - 1));
+#pragma unroll
+                for (int m = 0; m < 8; ++m) {
+                    // x^ = K (conj(Lambda) Z1^ + W^);  (A x)^ = Lambda x^  (warm start: x0's DFT)
+                    const float2 xh = warm0 ? inv_hw * v[m] : Kv[m] * (cmulc(v[m], L[m]) + u[m]);
+                    v[m] = xh;
+                    u[m] = cmul(L[m], xh);
+                }
+            }
+            fft_group2<H, 1>(v, u, bz, bw, tw, t, g);
+            __syncthreads();         // every group is done exchanging through the tile
+#pragma unroll
+            for (int m = 0; m < 8; ++m)
+                stage[tile_slot<CB>(t + m * C::FT, g)] = make_float4(v[m].x, v[m].y, u[m].x, u[m].y);
+            __syncthreads();
+            float4* __restrict__ dst = P.Sa;
+            for (int e = tid; e < H * CB; e += kThreads) {
+                const int r = e / CB, c = e % CB;
+                dst[(size_t)r * Wp + c0 + c] = stage[tile_slot<CB>(r, c)];
+            }
+        }
+        __syncthreads();             // the stage is free before the next request into it
+        cur ^= 1;
+        mode = mode_n;
+        Pc = Pn;
+    }
+    cp_async_wait<0>();
+}
+
+// ---------------------------------------------------------------------------
 // Shared pieces of the row phase.
 // ---------------------------------------------------------------------------
 // Rebuild the full row spectrum of the complex row x + i (A x) from the

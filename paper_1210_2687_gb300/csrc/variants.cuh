@@ -10,6 +10,8 @@
 // several translation units (rows_small.cu, rows_512.cu, rows_large.cu,
 // cols.cu) so that they compile in parallel.
 #pragma once
+#include <algorithm>
+
 #include "kernels.cuh"
 
 namespace admm {
@@ -27,6 +29,7 @@ struct RowVariant {
 struct ColVariant {
     int CB;
     int MB;   // CTAs per SM the registers are sized for (0: the default of the block)
+    int persistent;   // 1: persistent CTAs with a double-buffered tile (col_phase_pers)
     ColLaunchFn fn;
 };
 
@@ -72,6 +75,27 @@ cudaError_t launch_col_t(const ProbDesc* d, SlotTable sl, int count, int Wc, int
     return cudaGetLastError();
 }
 
+// persistent column phase: three CTAs per SM (two tiles and the twiddles in
+// shared memory) over the items of the launch
+int device_sm_count();
+template <int H, int CB>
+cudaError_t launch_col_pers_t(const ProbDesc* d, SlotTable sl, int count, int Wc, int Wp, const float2* tw,
+                              cudaStream_t s) {
+    static bool attr = false;
+    const size_t smem = (size_t)2 * H * CB * sizeof(float4) + (size_t)H * sizeof(float2);
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(col_phase_pers<H, CB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const int nblk = Wp / CB, nitems = nblk * count;
+    const int grid = std::min(nitems, 3 * device_sm_count());
+    if (grid <= 0) return cudaSuccess;
+    col_phase_pers<H, CB><<<grid, kThreads, smem, s>>>(d, sl, Wc, Wp, tw, nblk, nitems);
+    return cudaGetLastError();
+}
+
 template <int W, int R, int D, int NT>
 constexpr RowVariant row_variant() {
     return RowVariant{R, D, NT, &launch_row_tv_t<W, R, D, NT, false>, &launch_row_tv_t<W, R, D, NT, true>};
@@ -79,7 +103,11 @@ constexpr RowVariant row_variant() {
 // MB > 0: registers sized for MB CTAs per SM instead of the default
 template <int H, int CB, int MB = 0>
 constexpr ColVariant col_variant() {
-    return ColVariant{CB, MB, &launch_col_t<H, CB, MB>};
+    return ColVariant{CB, MB, 0, &launch_col_t<H, CB, MB>};
+}
+template <int H>
+constexpr ColVariant col_variant_pers() {
+    return ColVariant{ColCfg<H, kThreads / (H / 8)>::G, 3, 1, &launch_col_pers_t<H, kThreads / (H / 8)>};
 }
 
 }  // namespace admm

@@ -109,7 +109,7 @@ def test_cnn_null_arguments(ad):
 
 
 def test_tuning_struct_layout(ad):
-    # admm_tuning_t: 13 ints, padding, double
+    # admm_tuning_t: 14 ints, double
     assert ctypes.sizeof(ad.admm_tuning_t) == 64
     assert ad.admm_tuning_t.us_per_iter.offset == 56
 
