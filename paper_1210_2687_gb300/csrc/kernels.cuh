@@ -604,18 +604,22 @@ __device__ void finish_iteration(const ProbDesc& P, int k, bool chk, bool nobj,
 // the inverse transforms also cover one halo row above and below (the
 // forward differences and their adjoints reach one row each way).
 //
-// Data movement: at entry every half-spectrum row of the strip (R + 2 rows)
-// is requested with cp.async into the row buffers, and the per-pixel inputs
-// of the first D rows of the walk (d2, d1, M^T y, x_prev) into a per-thread
-// ring of D row slots; each walk step consumes one slot and refills it with
-// the row D ahead, so D rows of loads stay in flight behind the arithmetic.
+// Data movement: at entry the walk's rows go to L2 in bulk; every
+// half-spectrum row of the strip (R + 2 rows) is requested with cp.async into
+// the row buffers by the transform group that will transform it (one
+// cp.async group per round of transforms); and the per-pixel inputs of the
+// first D rows of the walk (d2, d1, M^T y) go into a per-thread ring of D row
+// slots. Each walk step consumes one slot and refills it with the row D ahead,
+// so D rows of loads stay in flight behind the arithmetic; x_prev, needed on
+// check iterations only, is read one row ahead into registers.
 //
 // The walk needs no block barrier: warp w owns the contiguous columns
-// [w W/8, (w+1) W/8) and walks its rows on its own. The left neighbour's
-// delta_h comes by shuffle from the next lower lane; the first lane
-// recomputes the pixel left of the chunk itself (its d2 is in the ring's
-// halo entry). x values of the neighbouring warps' boundary columns are
-// captured in registers before any warp overwrites its rows with p.
+// [w W/NWARP, (w+1) W/NWARP) and walks its rows on its own (lane by lane at
+// stride 32, or as pairs of adjacent columns when the warp owns at least 64).
+// The left neighbour's delta_h comes by shuffle from the next lower lane; the
+// first lane recomputes the pixel left of the chunk itself (its d2 is in the
+// ring's halo entry). x values of the neighbouring warps' boundary columns
+// are captured in registers before any warp overwrites its rows with p.
 // ---------------------------------------------------------------------------
 template <int W, int R, int D, int NT>
 struct RowCfg {
