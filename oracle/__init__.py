@@ -229,6 +229,14 @@ def objective_tv(x, ybar, mask, psf, lam, aniso=False):
     return 0.5 * float(np.sum(r * r)) + lam * float(np.sum(reg))
 
 
+def objective_synthesis(theta, ybar, mask, psf, lam):
+    """Frame synthesis prior (FS): 1/2 ||M(y - A W theta)||^2 + lam ||theta||_1
+    with W = P^T (Sec. III-B)."""
+    m = mask.astype(np.float64)
+    r = m * (ybar - A_fft(haar_synthesis(theta, theta.shape[0] // 3), psf))
+    return 0.5 * float(np.sum(r * r)) + lam * float(np.sum(np.abs(theta)))
+
+
 def objective_haar(x, ybar, mask, psf, lam, levels=4, ll_free=False):
     """lam ||P x||_1 over all 3 L + 1 bands, or (ll_free=True) over the 3 L
     detail bands only (the coarse low-low band unpenalised)."""
@@ -253,6 +261,7 @@ class State:
     d2: np.ndarray
     x: np.ndarray
     k: int = 0
+    theta: np.ndarray | None = None    # synthesis coefficients (FS-MD only)
 
     @staticmethod
     def zeros(H, W, reg="tv", levels=4):
@@ -262,7 +271,7 @@ class State:
 
     def copy(self):
         return State(self.u1.copy(), self.d1.copy(), self.u2.copy(), self.d2.copy(),
-                     self.x.copy(), self.k)
+                     self.x.copy(), self.k, None if self.theta is None else self.theta.copy())
 
 
 def tvmd_step(st: State, ybar, mask, psf, lam, mu1, mu2, otf=None, denom=None, aniso=False) -> State:
@@ -325,6 +334,34 @@ def famd_step(st: State, ybar, mask, psf, lam, mu1, mu2, levels=4, otf=None, ll_
     return State(u1, d1, u2, d2, x, st.k + 1)
 
 
+def fsmd_step(st: State, ybar, mask, psf, lam, mu1, mu2, levels=4, otf=None) -> State:
+    """One iteration of FS-MD: Algorithm 2 on the synthesis formulation, the
+    unknown being the frame coefficients theta with x = W theta, W = P^T,
+    H1 = A W and H2 = I. Line 4 solves (W^T A^T A W + gamma I) theta = r,
+    r = W^T A^T zeta1 + gamma zeta2, with the Sherman-Morrison-Woodbury form
+    that W W^T = I allows:
+        theta = (r - W^T A^T (A A^T + gamma I)^{-1} A W r) / gamma,
+    (A A^T + gamma I)^{-1} diagonal in the DFT domain. Line 6: the mask prox
+    for u1 and the soft threshold of eq. soft for u2 = prox(theta - d2)."""
+    H, W = ybar.shape
+    if otf is None:
+        otf = psf_otf(psf, H, W)
+    gam = mu2 / mu1
+    zeta1 = st.u1 + st.d1
+    zeta2 = st.u2 + st.d2
+    r = haar_analysis(np.real(np.fft.ifft2(np.conj(otf) * np.fft.fft2(zeta1))), levels) + gam * zeta2
+    awr = np.fft.fft2(haar_synthesis(r, levels)) * otf
+    q = np.real(np.fft.ifft2(np.conj(otf) * awr / (np.abs(otf) ** 2 + gam)))
+    theta = (r - haar_analysis(q, levels)) / gam
+    x = haar_synthesis(theta, levels)
+    ax = np.real(np.fft.ifft2(otf * np.fft.fft2(x)))
+    u1 = mask_prox(ax - st.d1, ybar, mask, mu1)
+    d1 = st.d1 - (ax - u1)
+    u2 = soft(theta - st.d2, lam / mu2)
+    d2 = st.d2 - (theta - u2)
+    return State(u1, d1, u2, d2, x, st.k + 1, theta)
+
+
 @dataclass
 class SolveResult:
     x: np.ndarray
@@ -343,15 +380,20 @@ def solve(ybar, mask, psf, lam, mu1, mu2, reg="tv", iters=200, stop="iters", tol
     iterations or, for stop = 'rel_x' / 'rel_obj', until the relative change of
     x / of the objective between consecutive iterations is below ``tol``.
     reg: 'tv', 'tv_aniso' (anisotropic TV), 'haar', 'haar_ll_free' (the
-    low-low band unpenalised)."""
+    low-low band unpenalised), 'haar_synthesis' (FS-MD: the frame synthesis
+    prior; its objective is evaluated on the coefficients theta)."""
     H, W = ybar.shape
     tv = reg in ("tv", "tv_aniso")
-    aniso, ll_free = reg == "tv_aniso", reg == "haar_ll_free"
+    aniso, ll_free, fs = reg == "tv_aniso", reg == "haar_ll_free", reg == "haar_synthesis"
     st = state0.copy() if state0 is not None else State.zeros(H, W, "tv" if tv else "haar", levels)
     otf = psf_otf(psf, H, W)
     denom = tv_denominator_diag(psf, H, W, mu1, mu2) if tv else None
-    obj_fn = (lambda x: objective_tv(x, ybar, mask, psf, lam, aniso)) if tv else \
-             (lambda x: objective_haar(x, ybar, mask, psf, lam, levels, ll_free))
+    if fs:
+        obj_fn = lambda x: objective_synthesis(st.theta, ybar, mask, psf, lam)  # noqa: E731
+    elif tv:
+        obj_fn = lambda x: objective_tv(x, ybar, mask, psf, lam, aniso)  # noqa: E731
+    else:
+        obj_fn = lambda x: objective_haar(x, ybar, mask, psf, lam, levels, ll_free)  # noqa: E731
     hist = []
     f_prev = None
     rel_x = rel_obj = float("inf")
@@ -361,6 +403,8 @@ def solve(ybar, mask, psf, lam, mu1, mu2, reg="tv", iters=200, stop="iters", tol
         x_prev = st.x
         if tv:
             st = tvmd_step(st, ybar, mask, psf, lam, mu1, mu2, otf, denom, aniso)
+        elif fs:
+            st = fsmd_step(st, ybar, mask, psf, lam, mu1, mu2, levels, otf)
         else:
             st = famd_step(st, ybar, mask, psf, lam, mu1, mu2, levels, otf, ll_free)
         nx = float(np.linalg.norm(st.x))

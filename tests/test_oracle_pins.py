@@ -532,3 +532,98 @@ def test_strong_weight_limit(reg):
     r = O.solve(ybar, mask, h, 10.0, 0.3, 3.0, reg, iters=3000)
     target = 0.0 if reg == "haar" else cstar
     assert np.max(np.abs(r.x - target)) < 1e-9
+
+
+# --------------------------------------------------------------------------
+# FS-MD: the frame synthesis formulation (x = W theta, W = P^T)
+# --------------------------------------------------------------------------
+def test_fs_theta_step_dense_solve():
+    """The SMW theta-step equals a dense solve of (W^T A^T A W + gamma I) theta
+    = W^T A^T zeta1 + gamma zeta2 with W the dense synthesis matrix (W W^T = I
+    is not assumed by the dense side); x = W theta; then the mask prox and the
+    soft threshold of theta - d2."""
+    H = W = 8
+    g, h, st, ybar, mask = _one_step_inputs("haar")
+    mu1, mu2, lam = 0.6, 0.09, 0.02
+    gam = mu2 / mu1
+    A = _dense(lambda v: O.A_direct(v, h), H, W)
+    Wm = _dense(lambda v: O.haar_analysis(v, 4), H, W).T          # synthesis = transpose of analysis
+    Mat = Wm.T @ A.T @ A @ Wm + gam * np.eye(Wm.shape[1])
+    rhs = Wm.T @ A.T @ (st.u1 + st.d1).ravel() + gam * (st.u2 + st.d2).ravel()
+    th = np.linalg.solve(Mat, rhs)
+    nxt = O.fsmd_step(st, ybar, mask, h, lam, mu1, mu2, 4)
+    np.testing.assert_allclose(nxt.theta.ravel(), th, atol=1e-11)
+    np.testing.assert_allclose(nxt.x.ravel(), Wm @ th, atol=1e-11)
+    s = th - st.d2.ravel()
+    u2 = np.sign(s) * np.maximum(np.abs(s) - lam / mu2, 0)
+    np.testing.assert_allclose(nxt.u2.ravel(), u2, atol=1e-11)
+    np.testing.assert_allclose(nxt.d2.ravel(), st.d2.ravel() - th + u2, atol=1e-11)
+    ax = A @ (Wm @ th)
+    m = mask.ravel().astype(float)
+    u1 = (m * ybar.ravel() + mu1 * (ax - st.d1.ravel())) / (m + mu1)
+    np.testing.assert_allclose(nxt.u1.ravel(), u1, atol=1e-11)
+
+
+def test_fs_kkt_certificate_at_convergence():
+    """Synthesis problem min 1/2 ||M(y - A W theta)||^2 + lam ||theta||_1 at a
+    fixed point of FS-MD (H1 = A W, H2 = I): -mu1 d1 = M^T(M A W theta - y),
+    mu1 W^T A^T d1 + mu2 d2 = 0, |mu2 d2| <= lam with -mu2 d2 = lam sign(theta)
+    where theta != 0."""
+    g = S.rng(11)
+    x = S.shapes_image(8, 8, g, 3, rmax=3.0)
+    h = S.psf_gaussian(3, 0.8)
+    keepm = (g.uniform(size=(8, 8)) < 0.9).astype(np.uint8)
+    ybar, mask, _ = S.observe(x, h, keepm, 40.0, g)
+    lam, mu1, mu2 = 1e-2, 0.1, 0.03
+    r = O.solve(ybar, mask, h, lam, mu1, mu2, "haar_synthesis", iters=30000, stop="rel_x", tol=1e-13)
+    assert r.converged
+    st = r.state
+    m = mask.astype(float)
+    np.testing.assert_allclose(-mu1 * st.d1, m * (O.A_fft(st.x, h) - ybar), atol=1e-9)
+    stat = mu1 * O.haar_analysis(O.At_fft(st.d1, h), 4) + mu2 * st.d2
+    assert np.max(np.abs(stat)) < 1e-9
+    assert np.max(np.abs(mu2 * st.d2)) <= lam * (1 + 1e-9)
+    act = np.abs(st.theta) > 1e-7
+    assert act.sum() > 10
+    np.testing.assert_allclose(-mu2 * st.d2[act], lam * np.sign(st.theta[act]), atol=1e-6 * lam)
+    np.testing.assert_allclose(O.haar_synthesis(st.theta, 4), st.x, atol=1e-12)
+
+
+def test_fs_optimum_matches_independent_fista():
+    """8 x 8: the objective FS-MD reaches equals the one of FISTA (Beck and
+    Teboulle's accelerated proximal gradient, a published method written here
+    with dense matrices) on the same synthesis problem; and it differs from the
+    analysis (FA) problem's optimum on this redundant frame."""
+    H = W = 8
+    g = S.rng(29)
+    xt = S.shapes_image(H, W, g, 3, rmax=3.0)
+    h = S.psf_gaussian(3, 0.8)
+    keep = (g.uniform(size=(H, W)) < 0.9).astype(np.uint8)
+    ybar, mask, _ = S.observe(xt, h, keep, 30.0, g)
+    lam, mu1, mu2 = 5e-3, 0.1, 0.015
+    r = O.solve(ybar, mask, h, lam, mu1, mu2, "haar_synthesis", iters=60000, stop="rel_x", tol=1e-14)
+    A = _dense(lambda v: O.A_direct(v, h), H, W)
+    Wm = _dense(lambda v: O.haar_analysis(v, 4), H, W).T
+    K = mask.ravel().astype(float)[:, None] * (A @ Wm)
+    yv = mask.ravel().astype(float) * ybar.ravel()
+    Lc = np.linalg.norm(K, 2) ** 2
+    th = np.zeros(K.shape[1]); z = th.copy(); tk = 1.0
+    for _ in range(60000):
+        gz = z - K.T @ (K @ z - yv) / Lc
+        th_new = np.sign(gz) * np.maximum(np.abs(gz) - lam / Lc, 0)
+        tk_new = 0.5 * (1 + np.sqrt(1 + 4 * tk * tk))
+        z = th_new + (tk - 1) / tk_new * (th_new - th)
+        th, tk = th_new, tk_new
+    f_fista = 0.5 * float(np.sum((K @ th - yv) ** 2)) + lam * float(np.sum(np.abs(th)))
+    assert abs(r.objective - f_fista) <= 1e-8 * abs(f_fista) + 1e-12
+    ra = O.solve(ybar, mask, h, lam, mu1, mu2, "haar", iters=60000, stop="rel_x", tol=1e-14)
+    assert np.max(np.abs(ra.x - r.x)) > 1e-4
+
+
+def test_fs_strong_weight_gives_zero():
+    g = S.rng(21)
+    x = S.shapes_image(16, 16, g, 4, rmax=4.0)
+    h = S.psf_gaussian(5, 1.0)
+    ybar, mask, _ = S.observe(x, h, None, 40.0, g)
+    r = O.solve(ybar, mask, h, 10.0, 0.3, 3.0, "haar_synthesis", iters=3000)
+    assert np.max(np.abs(r.x)) < 1e-9 and np.max(np.abs(r.state.theta)) < 1e-9
