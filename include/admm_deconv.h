@@ -64,6 +64,11 @@ extern "C" {
                                       eq. soft per difference component            */
 #define ADMM_REG_HAAR_LL_FREE  3   /* frame prior with the last low-low band
                                       unpenalised (its prox is the identity)       */
+#define ADMM_REG_HAAR_SYNTHESIS 4  /* FS-MD: the frame synthesis formulation,
+                                      min 1/2 ||M(y - A W theta)||^2 + lambda ||theta||_1,
+                                      x = W theta with W = P^T (Sec. III-B); the
+                                      duals d2 live on the coefficients theta. No
+                                      warm start (admm_deconv_warm_start: EINVAL) */
 
 #define ADMM_STOP_ITERS   0 /* run exactly max_iters iterations                  */
 #define ADMM_STOP_REL_X   1 /* ||x_k - x_{k-1}|| / ||x_k|| < tol                 */
@@ -83,8 +88,8 @@ typedef struct {
                               a value <= 0 selects the default rule: mu2 = 10 lambda
                               (Sec. V) and mu1 = min(1, 3 mu2) (Sec. V's mu1 rule is
                               garbled; penalties change only the speed, Theorem 1)          */
-    int   reg;             /* ADMM_REG_TV, ADMM_REG_HAAR, ADMM_REG_TV_ANISO or
-                              ADMM_REG_HAAR_LL_FREE                                         */
+    int   reg;             /* ADMM_REG_TV, ADMM_REG_HAAR, ADMM_REG_TV_ANISO,
+                              ADMM_REG_HAAR_LL_FREE or ADMM_REG_HAAR_SYNTHESIS              */
     int   haar_levels;     /* frame levels for the frame priors, 1..4 (0 = 4)              */
     int   stop;            /* ADMM_STOP_*                                                   */
     double tol;            /* tolerance of the stop rule                                    */
@@ -231,7 +236,8 @@ ADMM_API int admm_deconv_profile(int enable, admm_profile_t* out);
  * Plans keep the configuration they were created with, and a batch groups
  * plans by shape AND configuration. The table is library-global. Entries are
  * per kernel family: plans of ADMM_REG_TV_ANISO use the ADMM_REG_TV entry,
- * plans of ADMM_REG_HAAR_LL_FREE the ADMM_REG_HAAR entry. */
+ * plans of ADMM_REG_HAAR_LL_FREE and ADMM_REG_HAAR_SYNTHESIS the ADMM_REG_HAAR
+ * entry. */
 typedef struct {
     int    H, W;            /* [in] the size class ...                                        */
     int    reg;             /* [in] ... ADMM_REG_TV or ADMM_REG_HAAR ...                      */

@@ -33,12 +33,13 @@ ADMM_REG_TV = 0
 ADMM_REG_HAAR = 1
 ADMM_REG_TV_ANISO = 2
 ADMM_REG_HAAR_LL_FREE = 3
+ADMM_REG_HAAR_SYNTHESIS = 4
 ADMM_STOP_ITERS = 0
 ADMM_STOP_REL_X = 1
 ADMM_STOP_REL_OBJ = 2
 
 _REG = {"tv": ADMM_REG_TV, "haar": ADMM_REG_HAAR, "tv_aniso": ADMM_REG_TV_ANISO,
-        "haar_ll_free": ADMM_REG_HAAR_LL_FREE}
+        "haar_ll_free": ADMM_REG_HAAR_LL_FREE, "haar_synthesis": ADMM_REG_HAAR_SYNTHESIS}
 _STOP = {"iters": ADMM_STOP_ITERS, "rel_x": ADMM_STOP_REL_X, "rel_obj": ADMM_STOP_REL_OBJ}
 
 EXPORTED = ("admm_deconv_plan", "admm_deconv_solve", "admm_deconv_solve_batch",

@@ -330,7 +330,8 @@ void free_plan(admm_plan_s* pl) {
 // kernel family of a regulariser (the variants share their family's kernels)
 int reg_family(int reg) { return (reg == ADMM_REG_TV || reg == ADMM_REG_TV_ANISO) ? ADMM_REG_TV : ADMM_REG_HAAR; }
 bool reg_known(int reg) {
-    return reg == ADMM_REG_TV || reg == ADMM_REG_HAAR || reg == ADMM_REG_TV_ANISO || reg == ADMM_REG_HAAR_LL_FREE;
+    return reg == ADMM_REG_TV || reg == ADMM_REG_HAAR || reg == ADMM_REG_TV_ANISO || reg == ADMM_REG_HAAR_LL_FREE ||
+           reg == ADMM_REG_HAAR_SYNTHESIS;
 }
 
 ProbDesc make_desc(const admm_plan_s* pl) {
@@ -540,6 +541,7 @@ int admm_deconv_get_state(admm_plan_t plan, float* d_out, void* stream) {
 
 int admm_deconv_warm_start(admm_plan_t plan, const float* x0, const float* d0, void* stream) {
     if (!plan) return ADMM_EINVAL;
+    if (plan->p.reg == ADMM_REG_HAAR_SYNTHESIS) return ADMM_EINVAL;   // starts live on theta, not x
     std::lock_guard<std::mutex> lk(g_mutex);
     int dev = 0;
     CK(cudaGetDevice(&dev));
@@ -603,7 +605,8 @@ static cudaError_t launch_iteration(DeviceCtx* ctx, const GroupRun& g, int l, cu
     if (e != cudaSuccess) return e;
     int* nact = ctx->n_active + g.gi;
     if (g.tv) return g.row_fn(desc, sl, g.L.slots[l], g.H, g.Wp, ctx->tw, nact, s);
-    return launch_haar_iteration_rows(g.W, g.H, g.Wp, desc, sl, g.L.slots[l], g.levels, ctx->tw, nact, s);
+    return launch_haar_iteration_rows(g.W, g.H, g.Wp, desc, sl, g.L.slots[l], g.levels,
+                                      g.reg == ADMM_REG_HAAR_SYNTHESIS, ctx->tw, nact, s);
 }
 
 static std::string graph_key(const std::vector<GroupRun>& groups, int chunk) {
@@ -826,7 +829,8 @@ static int solve_all(DeviceCtx* ctx, const std::vector<std::vector<int>>& classe
                             CK(g.row_fn(dl, sl, g.L.slots[l], g.H, g.Wp, ctx->tw, nact, s));
                             ++g_launches;
                         } else {
-                            CK(launch_haar_iteration_rows(g.W, g.H, g.Wp, dl, sl, g.L.slots[l], g.levels, ctx->tw,
+                            CK(launch_haar_iteration_rows(g.W, g.H, g.Wp, dl, sl, g.L.slots[l], g.levels,
+                                                          g.reg == ADMM_REG_HAAR_SYNTHESIS, ctx->tw,
                                                           nact, s));
                             g_launches += 4;
                         }

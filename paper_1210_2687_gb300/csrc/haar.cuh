@@ -152,7 +152,13 @@ struct HaarAnaCfg {
 };
 
 
-template <int L>
+// FS: the frame synthesis formulation (FS-MD). There the thresholded
+// coefficients are theta = P (x - P^T zeta2) + zeta2 (the theta-step of the
+// synthesis problem with W = P^T, reduced with W W^T = I and the x-step's
+// equation A^T (zeta1 - A x) = gamma (x - P^T zeta2)); P^T zeta2 = w / gamma
+// is the previous synthesis output and zeta2 the previous iteration's, still
+// in the buffer that receives the new d2.
+template <int L, bool FS = false>
 __global__ void __launch_bounds__(kThreads)
 haar_analysis(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W, int n_row_ctas,
               int* __restrict__ n_active) {
@@ -186,6 +192,11 @@ haar_analysis(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W, in
         const int rr = e / CH, ch = e - rr * CH;
         const float* src = P.work + (size_t)((R0 + rr) & (H - 1)) * W + ((C0 + 4 * ch) & (W - 1));
         cp_async16(Ain + rr * XA + 4 * ch, src);
+        if (FS && !first) {
+            // w = gamma P^T zeta2 of the previous iteration on the same region (zero at the start)
+            const float* wsrc = P.work + 2 * n + (size_t)((R0 + rr) & (H - 1)) * W + ((C0 + 4 * ch) & (W - 1));
+            cp_async16(Aout + rr * XA + 4 * ch, wsrc);
+        }
     }
     cp_async_commit();
     // thread t owns the four adjacent tile pixels of row t / 8, columns
@@ -211,6 +222,12 @@ haar_analysis(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W, in
     }
     cp_async_wait<L>();          // x has landed (the d2 groups may still be in flight)
     __syncthreads();
+    if (FS && !first) {
+        // v = x - P^T zeta2, whose analysis the levels below compute
+        const float inv_g = 1.0f / P.gamma;
+        for (int e = tid; e < XR * XA; e += kThreads) Ain[e] = fmaf(-inv_g, Aout[e], Ain[e]);
+        __syncthreads();
+    }
 
     CompSum l1;
 #pragma unroll
@@ -224,6 +241,15 @@ haar_analysis(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W, in
             const float4 v = first ? make_float4(0.f, 0.f, 0.f, 0.f)
                                    : *reinterpret_cast<const float4*>(d2s + (3 * lvl + j) * T * T + orow * T + ocol);
             dold[j][0] = v.x; dold[j][1] = v.y; dold[j][2] = v.z; dold[j][3] = v.w;
+        }
+        // FS: the previous iteration's zeta2 of this level's bands (own pixels)
+        float zprev[3][4] = {};
+        if (FS && !first) {
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                const float4 v = *reinterpret_cast<const float4*>(d2out + (size_t)(3 * lvl + j) * n + gq);
+                zprev[j][0] = v.x; zprev[j][1] = v.y; zprev[j][2] = v.z; zprev[j][3] = v.w;
+            }
         }
         const int D = T + (1 << L) - 2 * s;      // a_{lvl+1} is needed on [0, D)^2
         // owned pixels: approximation, detail bands, soft threshold and dual
@@ -249,9 +275,10 @@ haar_analysis(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W, in
             const float p0 = a00 + a01, m0 = a00 - a01, p1 = a10 + a11, m1 = a10 - a11;
             ao[e] = 0.25f * (p0 + p1);
             // detail bands: rows low / cols high, rows high / cols low, both high
-            const float cb[3] = {0.25f * (m0 + m1), 0.25f * (p0 - p1), 0.25f * (m0 - m1)};
+            float cb[3] = {0.25f * (m0 + m1), 0.25f * (p0 - p1), 0.25f * (m0 - m1)};
 #pragma unroll
             for (int j = 0; j < 3; ++j) {
+                if (FS) cb[j] += zprev[j][e];                   // theta = P v + zeta2
                 const float sv = cb[j] - dold[j][e];
                 const float u = soft_thresh(sv, tau);           // eq. soft
                 nd4[j][e] = u - sv;                             // d2 - (c - u2)
@@ -298,7 +325,12 @@ haar_analysis(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W, in
         const float4 dv = first ? make_float4(0.f, 0.f, 0.f, 0.f)
                                 : *reinterpret_cast<const float4*>(d2s + (3 * L) * T * T + orow * T + ocol);
         const float4 cv = *reinterpret_cast<const float4*>(Ain + orow * XA + ocol);
-        const float dold[4] = {dv.x, dv.y, dv.z, dv.w}, cb[4] = {cv.x, cv.y, cv.z, cv.w};
+        const float dold[4] = {dv.x, dv.y, dv.z, dv.w};
+        float cb[4] = {cv.x, cv.y, cv.z, cv.w};
+        if (FS && !first) {
+            const float4 zv = *reinterpret_cast<const float4*>(d2out + (size_t)(3 * L) * n + gq);
+            cb[0] += zv.x; cb[1] += zv.y; cb[2] += zv.z; cb[3] += zv.w;
+        }
         float nd[4], z[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
@@ -518,7 +550,7 @@ haar_row_forward(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp
 // host-side launch of the three row-side kernels of one FA-MD iteration
 // ---------------------------------------------------------------------------
 template <int W>
-cudaError_t launch_haar_rows_t(int H, int Wp, const ProbDesc* d, SlotTable sl, int count, int levels,
+cudaError_t launch_haar_rows_t(int H, int Wp, const ProbDesc* d, SlotTable sl, int count, int levels, bool fs,
                                const float2* tw, int* n_active, cudaStream_t s) {
     constexpr int FT = W / 8, G = kThreads / FT;
     const size_t smem_row = (size_t)(G * W + W) * sizeof(float2) + 8 * kNumPartials * sizeof(double);
@@ -536,10 +568,14 @@ cudaError_t launch_haar_rows_t(int H, int Wp, const ProbDesc* d, SlotTable sl, i
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const dim3 tgrid(haar_num_tiles(H, W), count);
-    switch (levels) {
-        case 1: haar_analysis<1><<<tgrid, kThreads, HaarAnaCfg<1>::SMEM, s>>>(d, sl, H, W, nrow, n_active); break;
-        case 2: haar_analysis<2><<<tgrid, kThreads, HaarAnaCfg<2>::SMEM, s>>>(d, sl, H, W, nrow, n_active); break;
-        case 3: haar_analysis<3><<<tgrid, kThreads, HaarAnaCfg<3>::SMEM, s>>>(d, sl, H, W, nrow, n_active); break;
+    switch (levels * 2 + (fs ? 1 : 0)) {
+        case 2: haar_analysis<1><<<tgrid, kThreads, HaarAnaCfg<1>::SMEM, s>>>(d, sl, H, W, nrow, n_active); break;
+        case 4: haar_analysis<2><<<tgrid, kThreads, HaarAnaCfg<2>::SMEM, s>>>(d, sl, H, W, nrow, n_active); break;
+        case 6: haar_analysis<3><<<tgrid, kThreads, HaarAnaCfg<3>::SMEM, s>>>(d, sl, H, W, nrow, n_active); break;
+        case 3: haar_analysis<1, true><<<tgrid, kThreads, HaarAnaCfg<1>::SMEM, s>>>(d, sl, H, W, nrow, n_active); break;
+        case 5: haar_analysis<2, true><<<tgrid, kThreads, HaarAnaCfg<2>::SMEM, s>>>(d, sl, H, W, nrow, n_active); break;
+        case 7: haar_analysis<3, true><<<tgrid, kThreads, HaarAnaCfg<3>::SMEM, s>>>(d, sl, H, W, nrow, n_active); break;
+        case 9: haar_analysis<4, true><<<tgrid, kThreads, HaarAnaCfg<4>::SMEM, s>>>(d, sl, H, W, nrow, n_active); break;
         default: haar_analysis<4><<<tgrid, kThreads, HaarAnaCfg<4>::SMEM, s>>>(d, sl, H, W, nrow, n_active); break;
     }
     e = cudaGetLastError();
@@ -576,21 +612,34 @@ inline cudaError_t haar_tile_attributes() {
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(haar_analysis<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)HaarAnaCfg<4>::SMEM);
     if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(haar_analysis<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)HaarAnaCfg<1>::SMEM);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(haar_analysis<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)HaarAnaCfg<2>::SMEM);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(haar_analysis<3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)HaarAnaCfg<3>::SMEM);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(haar_analysis<4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)HaarAnaCfg<4>::SMEM);
+    if (e != cudaSuccess) return e;
     done = true;
     return cudaSuccess;
 }
 
+// fs: the synthesis formulation (FS-MD) analysis tile
 inline cudaError_t launch_haar_iteration_rows(int W, int H, int Wp, const ProbDesc* d, SlotTable sl, int count,
-                                              int levels, const float2* tw, int* n_active, cudaStream_t s) {
+                                              int levels, bool fs, const float2* tw, int* n_active, cudaStream_t s) {
     cudaError_t e = haar_tile_attributes();
     if (e != cudaSuccess) return e;
     switch (W) {
-        case 64: return launch_haar_rows_t<64>(H, Wp, d, sl, count, levels, tw, n_active, s);
-        case 128: return launch_haar_rows_t<128>(H, Wp, d, sl, count, levels, tw, n_active, s);
-        case 256: return launch_haar_rows_t<256>(H, Wp, d, sl, count, levels, tw, n_active, s);
-        case 512: return launch_haar_rows_t<512>(H, Wp, d, sl, count, levels, tw, n_active, s);
-        case 1024: return launch_haar_rows_t<1024>(H, Wp, d, sl, count, levels, tw, n_active, s);
-        case 2048: return launch_haar_rows_t<2048>(H, Wp, d, sl, count, levels, tw, n_active, s);
+        case 64: return launch_haar_rows_t<64>(H, Wp, d, sl, count, levels, fs, tw, n_active, s);
+        case 128: return launch_haar_rows_t<128>(H, Wp, d, sl, count, levels, fs, tw, n_active, s);
+        case 256: return launch_haar_rows_t<256>(H, Wp, d, sl, count, levels, fs, tw, n_active, s);
+        case 512: return launch_haar_rows_t<512>(H, Wp, d, sl, count, levels, fs, tw, n_active, s);
+        case 1024: return launch_haar_rows_t<1024>(H, Wp, d, sl, count, levels, fs, tw, n_active, s);
+        case 2048: return launch_haar_rows_t<2048>(H, Wp, d, sl, count, levels, fs, tw, n_active, s);
     }
     return cudaErrorInvalidValue;
 }

@@ -64,7 +64,8 @@ def test_struct_layout_matches_header(ad):
     (dict(lam=-1.0), -1),
     (dict(reg=7), -1), (dict(stop=9), -1),
     (dict(max_iters=0), -1), (dict(check_every=0), -1),
-    (dict(reg="haar", levels=5), -1), (dict(reg="haar_ll_free", levels=5), -1), (dict(reg=4), -1),
+    (dict(reg="haar", levels=5), -1), (dict(reg="haar_ll_free", levels=5), -1), (dict(reg=5), -1),
+    (dict(reg="haar_synthesis", levels=5), -1),
     (dict(psf=np.ones((65, 65)) / 65 ** 2), -1),   # larger than supported kernel side
 ])
 def test_plan_rejects_invalid_parameters_on_host(ad, change, code):

@@ -1,9 +1,9 @@
-"""GPU parity of the two regulariser variants against the FP64 oracle,
-through the C ABI: anisotropic TV (eq. soft per difference component in
-place of vector-soft) and the frame prior with the low-low band unpenalised
-(its prox is the identity). The x-step is the paper's in both; tolerances as
-for the other short runs (2e-5 relative L2 on x after a few iterations,
-1e-4 after 200)."""
+"""GPU parity of the regulariser variants against the FP64 oracle, through
+the C ABI: anisotropic TV (eq. soft per difference component in place of
+vector-soft), the frame prior with the low-low band unpenalised (its prox is
+the identity), and FS-MD, the frame synthesis formulation (x = W theta, the
+duals on theta). Tolerances as for the other short runs (2e-5 relative L2 on
+x after a few iterations, 1e-4 after 200)."""
 import numpy as np
 import pytest
 
@@ -102,12 +102,12 @@ def test_ll_free_frame_iterates_and_duals(ad, H, W, levels):
 
 
 def test_variants_and_paper_priors_in_one_batch(ad):
-    """One solve_batch over all four regularisers of one size (four size
+    """One solve_batch over all five regularisers of one size (five size
     classes), each matching its own oracle run."""
     import torch
     H = W = 128
     psf = S.psf_gaussian(9, 2.0)
-    regs = ["tv", "tv_aniso", "haar", "haar_ll_free"]
+    regs = ["tv", "tv_aniso", "haar", "haar_ll_free", "haar_synthesis"]
     probs = [_problem(H, W, 400 + i, psf) for i in range(len(regs))]
     lam, mu1, mu2, iters = 3e-4, 1e-2, 3e-3, 9
     plans = [ad.Plan(H, W, psf, lam, mu1, mu2, r, max_iters=iters) for r in regs]
@@ -136,3 +136,47 @@ def test_replayed_graphs_follow_the_regulariser(ad):
         x, _, res = _gpu(ad, reg, ybar, mask, psf, lam, mu1, mu2, iters)
         assert res.iters == iters
         assert _rel(x, ref.x) <= 1e-4, reg
+
+
+@pytest.mark.parametrize("H,W,levels", [(128, 128, 4), (256, 512, 4), (1024, 256, 3), (64, 64, 1)])
+def test_fs_iterates_and_duals(ad, H, W, levels):
+    psf = S.psf_gaussian(9, 2.0)
+    _, ybar, mask = _problem(H, W, 600 + H + W + levels, psf, keep=0.8)
+    lam, mu1, mu2, iters = 1e-4, 1e-2, 1e-3, 6
+    st = O.State.zeros(H, W, "haar", levels)
+    for _ in range(iters):
+        st = O.fsmd_step(st, ybar, mask, psf, lam, mu1, mu2, levels=levels)
+    x, d, res = _gpu(ad, "haar_synthesis", ybar, mask, psf, lam, mu1, mu2, iters, levels=levels)
+    assert res.iters == iters and res.status == 0
+    assert _rel(x, st.x) <= 2e-5
+    n = H * W
+    d1 = d[:n].reshape(H, W)
+    d2 = d[n:].reshape(3 * levels + 1, H, W)
+    assert np.max(np.abs(d1 - st.d1)) <= 2e-5 * np.abs(st.d1).max() + 1e-9
+    assert np.max(np.abs(d2 - st.d2)) <= 2e-4 * (lam / mu2)
+    # the synthesis problem's iterates differ from the analysis problem's
+    sta = O.State.zeros(H, W, "haar", levels)
+    for _ in range(iters):
+        sta = O.famd_step(sta, ybar, mask, psf, lam, mu1, mu2, levels=levels)
+    assert _rel(st.x, sta.x) > 1e-4
+
+
+def test_fs_200_iterations_and_objective(ad):
+    psf = S.psf_box(7)
+    x_true, ybar, mask = _problem(128, 128, 700, psf, keep=0.8)
+    lam, mu1, mu2 = 1e-3, 3e-2, 1e-2
+    ref = O.solve(ybar, mask, psf, lam, mu1, mu2, "haar_synthesis", iters=200)
+    x, _, res = _gpu(ad, "haar_synthesis", ybar, mask, psf, lam, mu1, mu2, 200)
+    assert _rel(x, ref.x) <= 1e-4
+    assert abs(res.objective - ref.objective) <= 1e-5 * ref.objective
+    vm = S.valid_mask(128, 128, *psf.shape)
+    assert abs(O.isnr(x_true, ybar, x, vm) - O.isnr(x_true, ybar, ref.x, vm)) <= 0.01
+
+
+def test_fs_rejects_a_warm_start(ad):
+    psf = S.psf_box(5)
+    plan = ad.Plan(64, 64, psf, 1e-3, 0.0, 0.0, "haar_synthesis", max_iters=5)
+    with pytest.raises(ad.AdmmError) as e:
+        plan.warm_start()
+    assert e.value.code == ad.ADMM_EINVAL
+    plan.close()
