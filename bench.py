@@ -299,7 +299,8 @@ FRAME_ITERS = 500
 
 def frame_secondary(ad, torch, stream, args):
     """Frame-prior (FA-MD) workload: 4-level undecimated Haar, 13 x 13
-    uniform blur, valid region, BSNR 50 dB, 1024^2 and 2048^2, a fixed 500
+    uniform blur, valid region, BSNR 50 dB, 1024^2 and 2048^2 (and the
+    synthesis formulation FS-MD at 1024^2), a fixed 500
     iterations (throughput); kernel time per phase from a profiled pass; and
     the same problem solved to rel-x < 1e-5 (checked every 10 iterations)
     for accuracy: iterations and ISNR. Algorithmic bytes per pixel and
@@ -307,11 +308,11 @@ def frame_secondary(ad, torch, stream, args):
     (inverse rows) + 112 (Haar tile, d2 13 bands in and out) + 16 (forward
     rows)."""
     out = {}
-    for size in (1024, 2048):
+    for reg, size in (("haar", 1024), ("haar", 2048), ("haar_synthesis", 1024)):
         p = S.config3_problem(0, size)
         n = size * size
         tune = tune_class(ad, torch, args, size, size, "haar", 4, problems=1)   # one image per solve
-        plan = ad.Plan(size, size, p.psf, p.lam, p.mu1, p.mu2, "haar", stop="iters", max_iters=FRAME_ITERS)
+        plan = ad.Plan(size, size, p.psf, p.lam, p.mu1, p.mu2, reg, stop="iters", max_iters=FRAME_ITERS)
         y = torch.from_numpy(p.ybar.astype(np.float32)).to("cuda")
         m = torch.from_numpy(p.mask).to("cuda")
         x = torch.empty((size, size), dtype=torch.float32, device="cuda")
@@ -325,10 +326,12 @@ def frame_secondary(ad, torch, stream, args):
         ad.admm_deconv_profile(True)
         ad.solve(plan, y, m, x, stream)
         pf = ad.admm_deconv_profile(False)
-        row_b = 28.0 + 112.0 + 16.0
+        # synthesis form: the analysis tile also reads w and the previous zeta2 (4 + 52)
+        row_b = 28.0 + 112.0 + 16.0 + (56.0 if reg == "haar_synthesis" else 0.0)
         col_b = 44.0 * (size // 2 + 1) / size
         peak, _ = read_peak()
-        out[f"fa_md_{size}"] = {
+        key = f"{'fs' if reg == 'haar_synthesis' else 'fa'}_md_{size}"
+        out[key] = {
             "iters_per_s": FRAME_ITERS / sec,
             # whole iteration: algorithmic bytes of both sides over the timed solve
             "iteration_gbs": FRAME_ITERS * n * (row_b + col_b) / sec / 1e9,
@@ -338,12 +341,12 @@ def frame_secondary(ad, torch, stream, args):
             "bytes_per_px_iter": {"row_side": row_b, "col_phase": col_b},
             "tuning": tune}
         plan.close()
-        acc = ad.Plan(size, size, p.psf, p.lam, p.mu1, p.mu2, "haar", stop="rel_x", tol=TOL, max_iters=MAX_ITERS,
+        acc = ad.Plan(size, size, p.psf, p.lam, p.mu1, p.mu2, reg, stop="rel_x", tol=TOL, max_iters=MAX_ITERS,
                       check_every=CHECK_EVERY)
         r = ad.solve(acc, y, m, x, stream)
         torch.cuda.synchronize()
         vm = S.valid_mask(size, size, *p.psf.shape)
-        out[f"fa_md_{size}"]["to_tolerance"] = {
+        out[key]["to_tolerance"] = {
             "iters": int(r.iters), "converged": int(r.converged), "rel_x": r.rel_x,
             "isnr_db": isnr_db(p.x_true, p.ybar, x.cpu().numpy().astype(np.float64), vm)}
         acc.close()
