@@ -66,7 +66,8 @@ extern "C" {
                                       unpenalised (its prox is the identity)       */
 #define ADMM_REG_HAAR_SYNTHESIS 4  /* FS-MD: the frame synthesis formulation,
                                       min 1/2 ||M(y - A W theta)||^2 + lambda ||theta||_1,
-                                      x = W theta with W = P^T (Sec. III-B); the
+                                      x = W theta with W = P^T (Sec. IV-B, eq.
+                                      unconstrained_synthesis_uBC); the
                                       duals d2 live on the coefficients theta. No
                                       warm start (admm_deconv_warm_start: EINVAL) */
 
