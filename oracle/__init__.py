@@ -230,8 +230,8 @@ def objective_tv(x, ybar, mask, psf, lam, aniso=False):
 
 
 def objective_synthesis(theta, ybar, mask, psf, lam):
-    """Frame synthesis prior (FS): 1/2 ||M(y - A W theta)||^2 + lam ||theta||_1
-    with W = P^T (Sec. III-B)."""
+    """Frame synthesis prior (FS, eq. unconstrained_synthesis_uBC):
+    1/2 ||M(y - A W theta)||^2 + lam ||theta||_1 with W = P^T."""
     m = mask.astype(np.float64)
     r = m * (ybar - A_fft(haar_synthesis(theta, theta.shape[0] // 3), psf))
     return 0.5 * float(np.sum(r * r)) + lam * float(np.sum(np.abs(theta)))
@@ -335,11 +335,12 @@ def famd_step(st: State, ybar, mask, psf, lam, mu1, mu2, levels=4, otf=None, ll_
 
 
 def fsmd_step(st: State, ybar, mask, psf, lam, mu1, mu2, levels=4, otf=None) -> State:
-    """One iteration of FS-MD: Algorithm 2 on the synthesis formulation, the
-    unknown being the frame coefficients theta with x = W theta, W = P^T,
-    H1 = A W and H2 = I. Line 4 solves (W^T A^T A W + gamma I) theta = r,
+    """One iteration of FS-MD (Sec. IV-B): Algorithm 2 on the synthesis
+    formulation, the unknown being the frame coefficients theta with
+    x = W theta, W = P^T, H1 = A W and H2 = I (eqs. H_1_synth, H_2_synth).
+    Line 4 (eq. inverse_synth2) solves (W^T A^T A W + gamma I) theta = r,
     r = W^T A^T zeta1 + gamma zeta2, with the Sherman-Morrison-Woodbury form
-    that W W^T = I allows:
+    that W W^T = I allows (eq. inverse_synth):
         theta = (r - W^T A^T (A A^T + gamma I)^{-1} A W r) / gamma,
     (A A^T + gamma I)^{-1} diagonal in the DFT domain. Line 6: the mask prox
     for u1 and the soft threshold of eq. soft for u2 = prox(theta - d2)."""
