@@ -152,7 +152,7 @@ struct HaarAnaCfg {
 };
 
 
-// FS: the frame synthesis formulation (FS-MD). There the thresholded
+// FS: the frame synthesis formulation (FS-MD, Sec. IV-B). There the thresholded
 // coefficients are theta = P (x - P^T zeta2) + zeta2 (the theta-step of the
 // synthesis problem with W = P^T, reduced with W W^T = I and the x-step's
 // equation A^T (zeta1 - A x) = gamma (x - P^T zeta2)); P^T zeta2 = w / gamma
