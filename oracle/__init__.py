@@ -13,6 +13,9 @@ Unknown Boundaries Using the Alternating Direction Method of Multipliers":
 * TV-MD  = Algorithm 3 (ADMM-TV) with line 7 replaced by eq. new_line (Sec. IV-D)
 * FA-MD  = Algorithm 2 with H1 = A, H2 = P, x-step eqs. invAnalysis/invAnalysisp1
   and the soft threshold of eq. soft (Sec. IV-C)
+* FS-MD  = Algorithm 2 on the synthesis formulation (Sec. IV-B, eq.
+  unconstrained_synthesis_uBC): unknown theta, x = P^T theta, H1 = A P^T,
+  H2 = I, line 4 by eq. inverse_synth2
 
 Conventions (readings of points the paper leaves open; each is listed with
 its justification in the design notes):
@@ -47,8 +50,8 @@ __all__ = [
     "Dh", "Dv", "DhT", "DvT", "tv_denominator_diag",
     "haar_analysis", "haar_synthesis", "haar_nbands",
     "soft", "vsoft", "mask_prox",
-    "objective_tv", "objective_haar",
-    "State", "tvmd_step", "famd_step", "solve",
+    "objective_tv", "objective_haar", "objective_synthesis",
+    "State", "tvmd_step", "famd_step", "fsmd_step", "solve",
     "isnr", "snr",
 ]
 
