@@ -369,13 +369,11 @@ struct HaarSynCfg {
     static constexpr int XS = T + 16;              // row stride of every array
     static constexpr int AR = T + HALO;            // approximation arrays: rows [-HALO, T)
     __host__ __device__ static constexpr int band_rows(int lvl) { return T + 2 * (1 << lvl) - 1; }
-    __host__ __device__ static constexpr int zoff(int lvl) {
-        int o = 0;
-        for (int i = 0; i < lvl; ++i) o += 3 * band_rows(i) * XS;
-        return o;
-    }
-    static constexpr int ZTOT = zoff(L);
-    static constexpr size_t SMEM = (size_t)(2 * AR * XS + ZTOT) * sizeof(float);
+    // two band slots, each sized for the coarsest level: level j lives in slot
+    // j % 2, and the bands of level j - 1 are requested into the other slot as
+    // soon as level j + 1 has released it
+    static constexpr int SLOT = 3 * band_rows(L - 1) * XS;
+    static constexpr size_t SMEM = (size_t)(2 * AR * XS + 2 * SLOT) * sizeof(float);
 };
 
 template <int L>
@@ -402,21 +400,13 @@ haar_synthesis(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W) {
     const float* __restrict__ zeta = P.d2 + ((k + 1) & 1) * P.d2_stride;
 
     // low-low band on rows [-HALO, T) and each level's bands on rows [-BO, T),
-    // all on the columns [-16, T), requested coarse to fine in one cp.async
-    // group per level (the low-low band with the coarsest), so that the
-    // coarse levels of the adjoint start while the fine bands still arrive
-    {
-        const float* band = zeta + (size_t)(3 * L) * n;
-        for (int e = tid; e < AR * CH; e += kThreads) {
-            const int rr = e / CH, ch = e - rr * CH;
-            cp_async16(At + rr * XS + 4 * ch,
-                       band + (size_t)((R0 + rr - HALO) & (H - 1)) * W + ((C0 - 16 + 4 * ch) & (W - 1)));
-        }
-    }
-#pragma unroll
-    for (int lvl = L - 1; lvl >= 0; --lvl) {
+    // all on the columns [-16, T), one cp.async group per level (the low-low
+    // band with the coarsest). Two levels are requested at entry; each later
+    // level goes into the slot the level before last has just released, so
+    // its loads overlap the adjoint of the level in between.
+    auto request = [&](int lvl) {
         const int BO = 2 * (1 << lvl) - 1, BR = T + BO;
-        float* Zl = Z + C::zoff(lvl);
+        float* Zl = Z + (lvl & 1) * C::SLOT;
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
             const float* band = zeta + (size_t)(3 * lvl + j) * n;
@@ -427,16 +417,30 @@ haar_synthesis(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W) {
             }
         }
         cp_async_commit();
+    };
+    {
+        const float* band = zeta + (size_t)(3 * L) * n;
+        for (int e = tid; e < AR * CH; e += kThreads) {
+            const int rr = e / CH, ch = e - rr * CH;
+            cp_async16(At + rr * XS + 4 * ch,
+                       band + (size_t)((R0 + rr - HALO) & (H - 1)) * W + ((C0 - 16 + 4 * ch) & (W - 1)));
+        }
     }
+    request(L - 1);
+    if (L >= 2) request(L - 2);
 
 #pragma unroll
     for (int lvl = L - 1; lvl >= 0; --lvl) {
-        cp_async_wait_n(lvl);        // this level's bands (and the coarser ones) ...
-        __syncthreads();             // ... have landed for every thread; the previous level is done
+        // this level's bands have landed (at the first level the next one may
+        // still be in flight; later, the next level is requested only below)
+        if (lvl == L - 1 && L >= 2) cp_async_wait<1>();
+        else cp_async_wait<0>();
+        __syncthreads();             // ... for every thread; level lvl + 1 is done and its slot free
+        if (lvl <= L - 2 && lvl >= 1) request(lvl - 1);
         const int s = 1 << lvl;
         const int D = T + s - 1;                       // output on [-(s-1), T)
         const int BO = 2 * s - 1, BR = T + BO;
-        const float* Z0 = Z + C::zoff(lvl);
+        const float* Z0 = Z + (lvl & 1) * C::SLOT;
         const float* Z1 = Z0 + BR * XS;
         const float* Z2 = Z1 + BR * XS;
         const int ra = s * XS, rz = s * XS;
