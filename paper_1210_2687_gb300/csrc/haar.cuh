@@ -145,8 +145,11 @@ struct HaarAnaCfg {
     static constexpr int XR = T + HALO;            // rows of x
     static_assert(HALO < 16, "halo fits the 16-column margin");
     static constexpr int NBAND = 3 * L + 1;
-    static constexpr int D2S_OFF = 2 * XR * XA;                // floats: previous d2 of the tile, per band
-    static constexpr int RED_OFF = D2S_OFF + NBAND * T * T;
+    // previous d2 of the tile: two slots of four bands; level j's bands (and
+    // the low-low band with the last level) in slot j % 2
+    static constexpr int D2S_OFF = 2 * XR * XA;
+    static constexpr int SLOT = 4 * T * T;
+    static constexpr int RED_OFF = D2S_OFF + 2 * SLOT;
     static_assert((RED_OFF * sizeof(float)) % sizeof(double) == 0, "double alignment");
     static constexpr size_t SMEM = (size_t)RED_OFF * sizeof(float) + 8 * kNumPartials * sizeof(double);
 };
@@ -159,7 +162,7 @@ struct HaarAnaCfg {
 // is the previous synthesis output and zeta2 the previous iteration's, still
 // in the buffer that receives the new d2.
 template <int L, bool FS = false>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 4)
 haar_analysis(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W, int n_row_ctas,
               int* __restrict__ n_active) {
     using C = HaarAnaCfg<L>;
@@ -203,24 +206,26 @@ haar_analysis(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W, in
     // 4 (t % 8) .. + 3: 16-byte reads of x and of the staged d2, 16-byte
     // stores of the new d2 and of zeta2. Every thread stages the previous d2
     // of its own pixels, one cp.async group per level (the last with the
-    // low-low band), all requested now: it reads only what it copied itself,
-    // so these need no block barrier.
+    // low-low band), two levels ahead in two slots: it reads only what it
+    // copied itself, so neither the copies nor the reuse of a slot need a
+    // block barrier.
     static_assert(T * T == 4 * kThreads, "four owned pixels per thread");
     const int orow = tid >> 3, ocol = 4 * (tid & 7);
     const size_t gq = (size_t)(R0 + orow) * W + (C0 + ocol);
-#pragma unroll
-    for (int lvl = 0; lvl < L; ++lvl) {
+    auto stage = [&](int lvl) {
         if (!first) {
             const int nb = lvl == L - 1 ? 4 : 3;
 #pragma unroll
             for (int j = 0; j < nb; ++j) {
                 const int b = 3 * lvl + j;
-                cp_async16(d2s + b * T * T + orow * T + ocol, d2io + (size_t)b * n + gq);
+                cp_async16(d2s + (lvl & 1) * C::SLOT + j * T * T + orow * T + ocol, d2io + (size_t)b * n + gq);
             }
         }
         cp_async_commit();
-    }
-    cp_async_wait<L>();          // x has landed (the d2 groups may still be in flight)
+    };
+    stage(0);
+    if (L >= 2) stage(1);
+    cp_async_wait_n(L >= 2 ? 2 : 1);   // x has landed (the d2 groups may still be in flight)
     __syncthreads();
     if (FS && !first) {
         // v = x - P^T zeta2, whose analysis the levels below compute
@@ -233,15 +238,20 @@ haar_analysis(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W, in
 #pragma unroll
     for (int lvl = 0; lvl < L; ++lvl) {
         const int s = 1 << lvl;
-        // this level's previous d2 at the owned pixels (staged at entry)
-        cp_async_wait_n(L - 1 - lvl);
+        // this level's previous d2 at the owned pixels (the next level's
+        // group may still be in flight)
+        if (lvl + 1 < L) cp_async_wait<1>();
+        else cp_async_wait<0>();
         float dold[3][4];
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
             const float4 v = first ? make_float4(0.f, 0.f, 0.f, 0.f)
-                                   : *reinterpret_cast<const float4*>(d2s + (3 * lvl + j) * T * T + orow * T + ocol);
+                                   : *reinterpret_cast<const float4*>(d2s + (lvl & 1) * C::SLOT + j * T * T + orow * T + ocol);
             dold[j][0] = v.x; dold[j][1] = v.y; dold[j][2] = v.z; dold[j][3] = v.w;
         }
+        // the slot is consumed (the last level's low-low entries are read
+        // after the loop, and nothing is staged after the last level)
+        if (lvl + 2 < L) stage(lvl + 2);
         // FS: the previous iteration's zeta2 of this level's bands (own pixels)
         float zprev[3][4] = {};
         if (FS && !first) {
@@ -323,7 +333,8 @@ haar_analysis(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W, in
         const bool ll_free = P.ll_free != 0;
         const float tau_ll = ll_free ? 0.f : tau;
         const float4 dv = first ? make_float4(0.f, 0.f, 0.f, 0.f)
-                                : *reinterpret_cast<const float4*>(d2s + (3 * L) * T * T + orow * T + ocol);
+                                : *reinterpret_cast<const float4*>(d2s + ((L - 1) & 1) * C::SLOT + 3 * T * T +
+                                                                   orow * T + ocol);
         const float4 cv = *reinterpret_cast<const float4*>(Ain + orow * XA + ocol);
         const float dold[4] = {dv.x, dv.y, dv.z, dv.w};
         float cb[4] = {cv.x, cv.y, cv.z, cv.w};
