@@ -226,6 +226,21 @@ typedef struct {
  */
 ADMM_API int admm_deconv_profile(int enable, admm_profile_t* out);
 
+/*
+ * admm_deconv_set_launch_overlap -- how the batch engine launches the
+ * kernels of its iterations (not in the paper; a launch option only, the
+ * arithmetic is the same either way).
+ *   enable  nonzero (the default): each iteration kernel is launched with
+ *           programmatic stream serialization, so it can be scheduled while
+ *           its predecessor finishes and waits on the device for that
+ *           predecessor's completion before reading its results; zero:
+ *           plain stream-ordered launches
+ * Library-global; takes effect at the next solve call. Returns ADMM_OK.
+ * admm_deconv_get_launch_overlap returns the current setting (0 or 1).
+ */
+ADMM_API int admm_deconv_set_launch_overlap(int enable);
+ADMM_API int admm_deconv_get_launch_overlap(void);
+
 /* ---- launch configurations and the autotuner (not in the paper) ---------
  * The library compiles a few configurations of each phase per side length:
  * for the TV row phase (rows per strip, walk rows kept in flight, threads

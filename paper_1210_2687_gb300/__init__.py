@@ -45,6 +45,7 @@ _STOP = {"iters": ADMM_STOP_ITERS, "rel_x": ADMM_STOP_REL_X, "rel_obj": ADMM_STO
 EXPORTED = ("admm_deconv_plan", "admm_deconv_solve", "admm_deconv_solve_batch",
             "admm_deconv_state_size", "admm_deconv_get_state", "admm_deconv_destroy",
             "admm_strerror", "admm_deconv_version", "admm_deconv_profile",
+            "admm_deconv_set_launch_overlap", "admm_deconv_get_launch_overlap",
             "admm_deconv_solve_noalloc", "admm_deconv_set_option", "admm_deconv_warm_start",
             "admm_deconv_variants", "admm_deconv_get_tuning", "admm_deconv_set_tuning", "admm_deconv_autotune",
             "admm_cnn_param_count", "admm_cnn_create", "admm_cnn_set_params", "admm_cnn_get_params",
@@ -130,6 +131,10 @@ def _load() -> ctypes.CDLL:
     lib.admm_deconv_version.restype = ctypes.c_char_p
     lib.admm_deconv_profile.argtypes = [ctypes.c_int, ctypes.POINTER(admm_profile_t)]
     lib.admm_deconv_profile.restype = ctypes.c_int
+    lib.admm_deconv_set_launch_overlap.argtypes = [ctypes.c_int]
+    lib.admm_deconv_set_launch_overlap.restype = ctypes.c_int
+    lib.admm_deconv_get_launch_overlap.argtypes = []
+    lib.admm_deconv_get_launch_overlap.restype = ctypes.c_int
     lib.admm_deconv_solve_noalloc.argtypes = [ctypes.POINTER(admm_params_t), vp, vp, vp,
                                               ctypes.POINTER(admm_result_t), vp]
     lib.admm_deconv_solve_noalloc.restype = ctypes.c_int
@@ -227,6 +232,16 @@ def admm_deconv_warm_start(plan: int, x0_ptr, d0_ptr, stream=None) -> None:
                                     ctypes.c_void_p(d0_ptr), _stream(stream))
     if rc != ADMM_OK:
         raise AdmmError(rc, "admm_deconv_warm_start")
+
+
+def admm_deconv_set_launch_overlap(enable: bool) -> None:
+    """Launch the batch engine's iteration kernels as a programmatic
+    dependent chain (True, the default) or as plain stream-ordered launches."""
+    lib.admm_deconv_set_launch_overlap(int(bool(enable)))
+
+
+def admm_deconv_get_launch_overlap() -> bool:
+    return bool(lib.admm_deconv_get_launch_overlap())
 
 
 def admm_deconv_profile(enable: bool) -> admm_profile_t:

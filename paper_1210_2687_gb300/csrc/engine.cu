@@ -12,6 +12,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -610,7 +611,7 @@ static cudaError_t launch_iteration(DeviceCtx* ctx, const GroupRun& g, int l, cu
 }
 
 static std::string graph_key(const std::vector<GroupRun>& groups, int chunk) {
-    std::string k = std::to_string(chunk);
+    std::string k = std::to_string(chunk) + (t_chain_overlap ? "o" : "s");
     for (const GroupRun& g : groups) {
         k += "|" + std::to_string(g.H) + "," + std::to_string(g.W) + "," + std::to_string(g.tv) + "," +
              std::to_string(g.levels) + "," + std::to_string(g.reg) + "," + std::to_string(g.row_v) + "," +
@@ -681,9 +682,27 @@ static cudaError_t chunk_graph(DeviceCtx* ctx, const std::vector<GroupRun>& grou
 
 // Solve every problem of a batch: all size classes iterate in the same loop
 // (their lanes are independent branches of one replayed graph).
+static int solve_all_impl(DeviceCtx* ctx, const std::vector<std::vector<int>>& classes, const admm_plan_t* plans,
+                          const float* const* y, const uint8_t* const* masks, float* const* x_out,
+                          admm_result_t* res, cudaStream_t s);
+
+// the iteration kernels of a batch go out as a launch chain (programmatic
+// dependent launch) unless switched off with admm_deconv_set_launch_overlap
+static std::atomic<int> g_overlap{1};
 static int solve_all(DeviceCtx* ctx, const std::vector<std::vector<int>>& classes, const admm_plan_t* plans,
                      const float* const* y, const uint8_t* const* masks, float* const* x_out,
                      admm_result_t* res, cudaStream_t s) {
+    struct Guard {
+        bool prev;
+        ~Guard() { t_chain_overlap = prev; }
+    } guard{t_chain_overlap};
+    t_chain_overlap = g_overlap.load() != 0;
+    return solve_all_impl(ctx, classes, plans, y, masks, x_out, res, s);
+}
+
+static int solve_all_impl(DeviceCtx* ctx, const std::vector<std::vector<int>>& classes, const admm_plan_t* plans,
+                          const float* const* y, const uint8_t* const* masks, float* const* x_out,
+                          admm_result_t* res, cudaStream_t s) {
     const bool prof = g_prof.on;
     std::vector<GroupRun> groups;
     std::vector<int> order;                       // table position -> index into plans
@@ -943,6 +962,13 @@ int admm_deconv_set_option(int option, long long value) {
     }
     return ADMM_EINVAL;
 }
+
+int admm_deconv_set_launch_overlap(int enable) {
+    g_overlap.store(enable != 0 ? 1 : 0);
+    return ADMM_OK;
+}
+
+int admm_deconv_get_launch_overlap(void) { return g_overlap.load(); }
 
 int admm_deconv_profile(int enable, admm_profile_t* out) {
     std::lock_guard<std::mutex> lk(g_mutex);

@@ -46,6 +46,7 @@ inline int haar_num_tiles(int H, int W) { return (H / kHaarTile) * (W / kHaarTil
 template <int W>
 __global__ void __launch_bounds__(kThreads)
 haar_row_inverse(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp, const float2* __restrict__ tw_g) {
+    chain_wait();   // (launch chain: the predecessor's writes are visible)
     constexpr int FT = W / 8, G = kThreads / FT, ROW = W;
     const int pi = sl.map[blockIdx.y];
     if (pi < 0) return;
@@ -165,6 +166,7 @@ template <int L, bool FS = false>
 __global__ void __launch_bounds__(kThreads, 4)
 haar_analysis(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W, int n_row_ctas,
               int* __restrict__ n_active) {
+    chain_wait();   // (launch chain: the predecessor's writes are visible)
     using C = HaarAnaCfg<L>;
     constexpr int T = C::T, XA = C::XA, XR = C::XR;
     const int pi = sl.map[blockIdx.y];
@@ -390,6 +392,7 @@ struct HaarSynCfg {
 template <int L>
 __global__ void __launch_bounds__(kThreads)
 haar_synthesis(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W) {
+    chain_wait();   // (launch chain: the predecessor's writes are visible)
     using C = HaarSynCfg<L>;
     constexpr int T = C::T, HALO = C::HALO, XS = C::XS, AR = C::AR;
     constexpr int CH = XS / 4;                     // 16-byte chunks per array row
@@ -534,6 +537,7 @@ haar_synthesis(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W) {
 template <int W>
 __global__ void __launch_bounds__(kThreads)
 haar_row_forward(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp, const float2* __restrict__ tw_g) {
+    chain_wait();   // (launch chain: the predecessor's writes are visible)
     constexpr int FT = W / 8, G = kThreads / FT, ROW = W;
     const int pi = sl.map[blockIdx.y];
     if (pi < 0) return;
@@ -579,32 +583,30 @@ cudaError_t launch_haar_rows_t(int H, int Wp, const ProbDesc* d, SlotTable sl, i
         attr = true;
     }
     const int nrow = H / G;
-    haar_row_inverse<W><<<dim3(nrow, count), kThreads, smem_inv, s>>>(d, sl, H, Wp, tw);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = launch_chain(haar_row_inverse<W>, dim3(nrow, count), dim3(kThreads), smem_inv, s, d, sl, H, Wp, tw);
     if (e != cudaSuccess) return e;
     const dim3 tgrid(haar_num_tiles(H, W), count);
     switch (levels * 2 + (fs ? 1 : 0)) {
-        case 2: haar_analysis<1><<<tgrid, kThreads, HaarAnaCfg<1>::SMEM, s>>>(d, sl, H, W, nrow, n_active); break;
-        case 4: haar_analysis<2><<<tgrid, kThreads, HaarAnaCfg<2>::SMEM, s>>>(d, sl, H, W, nrow, n_active); break;
-        case 6: haar_analysis<3><<<tgrid, kThreads, HaarAnaCfg<3>::SMEM, s>>>(d, sl, H, W, nrow, n_active); break;
-        case 3: haar_analysis<1, true><<<tgrid, kThreads, HaarAnaCfg<1>::SMEM, s>>>(d, sl, H, W, nrow, n_active); break;
-        case 5: haar_analysis<2, true><<<tgrid, kThreads, HaarAnaCfg<2>::SMEM, s>>>(d, sl, H, W, nrow, n_active); break;
-        case 7: haar_analysis<3, true><<<tgrid, kThreads, HaarAnaCfg<3>::SMEM, s>>>(d, sl, H, W, nrow, n_active); break;
-        case 9: haar_analysis<4, true><<<tgrid, kThreads, HaarAnaCfg<4>::SMEM, s>>>(d, sl, H, W, nrow, n_active); break;
-        default: haar_analysis<4><<<tgrid, kThreads, HaarAnaCfg<4>::SMEM, s>>>(d, sl, H, W, nrow, n_active); break;
+        case 2: e = launch_chain(haar_analysis<1>, tgrid, dim3(kThreads), HaarAnaCfg<1>::SMEM, s, d, sl, H, W, nrow, n_active); break;
+        case 4: e = launch_chain(haar_analysis<2>, tgrid, dim3(kThreads), HaarAnaCfg<2>::SMEM, s, d, sl, H, W, nrow, n_active); break;
+        case 6: e = launch_chain(haar_analysis<3>, tgrid, dim3(kThreads), HaarAnaCfg<3>::SMEM, s, d, sl, H, W, nrow, n_active); break;
+        case 3: e = launch_chain(haar_analysis<1, true>, tgrid, dim3(kThreads), HaarAnaCfg<1>::SMEM, s, d, sl, H, W, nrow, n_active); break;
+        case 5: e = launch_chain(haar_analysis<2, true>, tgrid, dim3(kThreads), HaarAnaCfg<2>::SMEM, s, d, sl, H, W, nrow, n_active); break;
+        case 7: e = launch_chain(haar_analysis<3, true>, tgrid, dim3(kThreads), HaarAnaCfg<3>::SMEM, s, d, sl, H, W, nrow, n_active); break;
+        case 9: e = launch_chain(haar_analysis<4, true>, tgrid, dim3(kThreads), HaarAnaCfg<4>::SMEM, s, d, sl, H, W, nrow, n_active); break;
+        default: e = launch_chain(haar_analysis<4>, tgrid, dim3(kThreads), HaarAnaCfg<4>::SMEM, s, d, sl, H, W, nrow, n_active); break;
     }
-    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     switch (levels) {
-        case 1: haar_synthesis<1><<<tgrid, kThreads, HaarSynCfg<1>::SMEM, s>>>(d, sl, H, W); break;
-        case 2: haar_synthesis<2><<<tgrid, kThreads, HaarSynCfg<2>::SMEM, s>>>(d, sl, H, W); break;
-        case 3: haar_synthesis<3><<<tgrid, kThreads, HaarSynCfg<3>::SMEM, s>>>(d, sl, H, W); break;
-        default: haar_synthesis<4><<<tgrid, kThreads, HaarSynCfg<4>::SMEM, s>>>(d, sl, H, W); break;
+        case 1: e = launch_chain(haar_synthesis<1>, tgrid, dim3(kThreads), HaarSynCfg<1>::SMEM, s, d, sl, H, W); break;
+        case 2: e = launch_chain(haar_synthesis<2>, tgrid, dim3(kThreads), HaarSynCfg<2>::SMEM, s, d, sl, H, W); break;
+        case 3: e = launch_chain(haar_synthesis<3>, tgrid, dim3(kThreads), HaarSynCfg<3>::SMEM, s, d, sl, H, W); break;
+        default: e = launch_chain(haar_synthesis<4>, tgrid, dim3(kThreads), HaarSynCfg<4>::SMEM, s, d, sl, H, W); break;
     }
-    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    haar_row_forward<W><<<dim3(nrow, count), kThreads, smem_row, s>>>(d, sl, H, Wp, tw);
-    return cudaGetLastError();
+    return launch_chain(haar_row_forward<W>, dim3(nrow, count), dim3(kThreads), smem_row, s, d, sl, H, Wp, tw);
 }
 
 inline cudaError_t haar_tile_attributes() {

@@ -159,6 +159,41 @@ __device__ __forceinline__ void cp_async_wait_n(int n) {
     }
 }
 
+// Programmatic dependent launch of the iteration's kernel chain (column
+// phase, row side, next column phase, ...). A chain kernel may be launched
+// before its predecessor in the stream has completed: its CTAs are scheduled
+// once every CTA of the predecessor has exited, and the first thing they do
+// is wait for the predecessor's completion and the visibility of its writes
+// (chain_wait), so nothing the predecessor writes is touched before that.
+// The launch processing overlaps the predecessor's completion. (Releasing the
+// successor earlier, from the top of each kernel, measured slower: its
+// waiting CTAs held resources the predecessor's last wave could use.)
+// Launched without the attribute, the wait is a no-op.
+__device__ __forceinline__ void chain_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// Host side: while `t_chain_overlap` is set on the launching thread, chain
+// kernels go out with programmatic stream serialization (the batch engine
+// sets it around its iteration launches and graph captures).
+inline thread_local bool t_chain_overlap = false;
+template <typename... KArgs, typename... Args>
+cudaError_t launch_chain(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args... args) {
+    if (!t_chain_overlap) {
+        kern<<<grid, block, smem, s>>>(args...);
+        return cudaGetLastError();
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 // Bulk prefetch of a contiguous global range into L2 (no shared memory and no
 // completion to wait for); `bytes` a multiple of 16, `p` 16-byte aligned.
 __device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
@@ -228,6 +263,7 @@ __device__ __forceinline__ int tile_slot(int r, int c) {
 template <int H, int CB, int MB = 0>
 __global__ void __launch_bounds__(kThreads, (MB > 0 ? MB : ColCfg<H, CB>::MINB))
 col_phase(const ProbDesc* __restrict__ probs, SlotTable sl, int Wc, int Wp, const float2* __restrict__ tw_g) {
+    chain_wait();   // (launch chain: the predecessor's writes are visible)
     using C = ColCfg<H, CB>;
     const int pi = sl.map[blockIdx.y];
     if (pi < 0) return;
@@ -326,6 +362,7 @@ template <int H, int CB>
 __global__ void __launch_bounds__(kThreads, 3)
 col_phase_pers(const ProbDesc* __restrict__ probs, SlotTable sl, int Wc, int Wp, const float2* __restrict__ tw_g,
                int nblk, int nitems) {
+    chain_wait();   // (launch chain: the predecessor's writes are visible)
     using C = ColCfg<H, CB>;
     static_assert(C::ALIAS, "one column per transform group");
     extern __shared__ __align__(16) float4 smem4[];
@@ -656,6 +693,7 @@ template <int W, int R, int D, int NT, bool ANISO = false>
 __global__ void __launch_bounds__(NT, (RowCfg<W, R, D, NT>::MINB))
 row_phase_tv(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp, const float2* __restrict__ tw_g,
              int* __restrict__ n_active) {
+    chain_wait();   // (launch chain: the predecessor's writes are visible)
     using C = RowCfg<W, R, D, NT>;
     const int pi = sl.map[blockIdx.y];
     if (pi < 0) return;

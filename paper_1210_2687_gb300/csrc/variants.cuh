@@ -55,8 +55,7 @@ cudaError_t launch_row_tv_t(const ProbDesc* d, SlotTable sl, int count, int H, i
         attr = true;
     }
     dim3 grid(H / R, count);
-    row_phase_tv<W, R, D, NT, ANISO><<<grid, NT, smem, s>>>(d, sl, H, Wp, tw, n_active);
-    return cudaGetLastError();
+    return launch_chain(row_phase_tv<W, R, D, NT, ANISO>, grid, dim3(NT), smem, s, d, sl, H, Wp, tw, n_active);
 }
 
 template <int H, int CB, int MB>
@@ -71,8 +70,7 @@ cudaError_t launch_col_t(const ProbDesc* d, SlotTable sl, int count, int Wc, int
         attr = true;
     }
     dim3 grid(Wp / CB, count);
-    col_phase<H, CB, MB><<<grid, kThreads, smem, s>>>(d, sl, Wc, Wp, tw);
-    return cudaGetLastError();
+    return launch_chain(col_phase<H, CB, MB>, grid, dim3(kThreads), smem, s, d, sl, Wc, Wp, tw);
 }
 
 // persistent column phase: three CTAs per SM (two tiles and the twiddles in
@@ -92,8 +90,7 @@ cudaError_t launch_col_pers_t(const ProbDesc* d, SlotTable sl, int count, int Wc
     const int nblk = Wp / CB, nitems = nblk * count;
     const int grid = std::min(nitems, 3 * device_sm_count());
     if (grid <= 0) return cudaSuccess;
-    col_phase_pers<H, CB><<<grid, kThreads, smem, s>>>(d, sl, Wc, Wp, tw, nblk, nitems);
-    return cudaGetLastError();
+    return launch_chain(col_phase_pers<H, CB>, dim3(grid), dim3(kThreads), smem, s, d, sl, Wc, Wp, tw, nblk, nitems);
 }
 
 template <int W, int R, int D, int NT>

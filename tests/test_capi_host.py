@@ -157,3 +157,16 @@ def test_headers_compile_as_c99(tmp_path):
                         "-I", os.path.join(ROOT, "include"), "-c", str(src), "-o", str(tmp_path / "abi.o")],
                        capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
+
+
+def test_launch_overlap_switch_on_host(ad):
+    """The launch-chain switch is a host-side setting (no device needed):
+    on by default, and it reads back what was set."""
+    assert ad.admm_deconv_get_launch_overlap() is True
+    try:
+        ad.admm_deconv_set_launch_overlap(False)
+        assert ad.admm_deconv_get_launch_overlap() is False
+        assert ad.lib.admm_deconv_set_launch_overlap(7) == ad.ADMM_OK
+        assert ad.lib.admm_deconv_get_launch_overlap() == 1
+    finally:
+        ad.admm_deconv_set_launch_overlap(True)
