@@ -532,7 +532,9 @@ haar_synthesis(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W) {
 }
 
 // ---------------------------------------------------------------------------
-// forward row DFT of zeta1 + i w and Hermitian split into the half spectra
+// forward row DFT of zeta1 + i w and Hermitian split into the half spectra;
+// each transform group takes two rows (g and g + G of the CTA's 2 G rows)
+// interleaved pass by pass (fft_group2)
 // ---------------------------------------------------------------------------
 template <int W>
 __global__ void __launch_bounds__(kThreads)
@@ -546,23 +548,33 @@ haar_row_forward(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp
     if (P.ctl->active == 0 || P.ctl->iter == 0) return;
     extern __shared__ __align__(16) float2 smem[];
     float2* buf = smem;
-    float2* tw = buf + G * ROW;
+    float2* tw = buf + 2 * G * ROW;
     const int tid = threadIdx.x, g = tid / FT, t = tid % FT;
+    const int q0 = blockIdx.x * 2 * G + g, q1 = q0 + G;
+    const size_t n = (size_t)H * W;
+    const float* __restrict__ z1a = P.work + n + (size_t)q0 * W;
+    const float* __restrict__ wa = P.work + 2 * n + (size_t)q0 * W;
+    const float* __restrict__ z1b = P.work + n + (size_t)q1 * W;
+    const float* __restrict__ wb = P.work + 2 * n + (size_t)q1 * W;
+    float2 v[8], u[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+        v[m] = make_float2(z1a[t + m * FT], wa[t + m * FT]);
+        u[m] = make_float2(z1b[t + m * FT], wb[t + m * FT]);
+    }
     load_twiddles<W>(tw, tw_g, tid, kThreads);
     __syncthreads();
-    const int q = blockIdx.x * G + g;
-    const size_t n = (size_t)H * W;
-    const float* __restrict__ z1w = P.work + n + (size_t)q * W;
-    const float* __restrict__ ww = P.work + 2 * n + (size_t)q * W;
-    float2 v[8];
+    float2* row0 = buf + g * ROW;
+    float2* row1 = buf + (g + G) * ROW;
+    fft_group2<W, -1>(v, u, row0, row1, tw, t, g);
 #pragma unroll
-    for (int m = 0; m < 8; ++m) v[m] = make_float2(z1w[t + m * FT], ww[t + m * FT]);
-    float2* row = buf + g * ROW;
-    fft_group<W, -1>(v, row, tw, t, g);
-#pragma unroll
-    for (int m = 0; m < 8; ++m) row[swz(t + m * FT)] = v[m];
-    group_sync<W>(g);                // the split reads this group's row only
-    store_split<W>(P.Sb + (size_t)q * Wp, row, t);
+    for (int m = 0; m < 8; ++m) {
+        row0[swz(t + m * FT)] = v[m];
+        row1[swz(t + m * FT)] = u[m];
+    }
+    group_sync<W>(g);                // the split reads this group's rows only
+    store_split<W>(P.Sb + (size_t)q0 * Wp, row0, t);
+    store_split<W>(P.Sb + (size_t)q1 * Wp, row1, t);
 }
 
 // ---------------------------------------------------------------------------
@@ -574,11 +586,12 @@ cudaError_t launch_haar_rows_t(int H, int Wp, const ProbDesc* d, SlotTable sl, i
     constexpr int FT = W / 8, G = kThreads / FT;
     const size_t smem_row = (size_t)(G * W + W) * sizeof(float2) + 8 * kNumPartials * sizeof(double);
     const size_t smem_inv = smem_row + (size_t)3 * G * W * sizeof(float);   // + staged d1, M^T y, x_prev
+    const size_t smem_fwd = (size_t)(2 * G * W + W) * sizeof(float2);       // two rows per group
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(haar_row_inverse<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_inv);
         if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(haar_row_forward<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_row);
+        e = cudaFuncSetAttribute(haar_row_forward<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_fwd);
         if (e != cudaSuccess) return e;
         attr = true;
     }
@@ -606,7 +619,7 @@ cudaError_t launch_haar_rows_t(int H, int Wp, const ProbDesc* d, SlotTable sl, i
     }
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    return launch_chain(haar_row_forward<W>, dim3(nrow, count), dim3(kThreads), smem_row, s, d, sl, H, Wp, tw);
+    return launch_chain(haar_row_forward<W>, dim3(nrow / 2, count), dim3(kThreads), smem_fwd, s, d, sl, H, Wp, tw);
 }
 
 inline cudaError_t haar_tile_attributes() {
