@@ -208,7 +208,7 @@ ADMM_API int admm_deconv_set_option(int option, long long value);
 typedef struct {
     double    col_ms;            /* summed device time of column-phase launches          */
     double    row_ms;            /* summed device time of the row-side launches of each
-                                    iteration (one kernel for TV, three for the frame)  */
+                                    iteration (one kernel for TV, four for the frame)   */
     long long col_launches;      /* column-phase launches timed                          */
     long long row_launches;      /* iterations whose row side was timed                  */
     long long kernel_launches;   /* every kernel the library launched (always counted)   */
