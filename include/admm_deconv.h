@@ -116,6 +116,10 @@ typedef struct {
     double t_start_ms;     /* device clock: from the call's set-up until the problem started
                               iterating (later than 0 when it waited for a free slot)       */
     double t_done_ms;      /* device clock: from the call's set-up until it retired        */
+    double primal_res;     /* ||d_k - d_{k-1}|| over both splits, i.e. the norm of the
+                              primal residual H z_k - u_k of Algorithm 2, at the last
+                              iteration that evaluated the objective (FP32 data,
+                              compensated reduction), or -1 if none did               */
 } admm_result_t;
 
 /*

@@ -71,7 +71,7 @@ class admm_result_t(ctypes.Structure):
                 ("status", ctypes.c_int), ("reserved", ctypes.c_int),
                 ("objective", ctypes.c_double), ("rel_x", ctypes.c_double),
                 ("rel_obj", ctypes.c_double), ("t_start_ms", ctypes.c_double),
-                ("t_done_ms", ctypes.c_double)]
+                ("t_done_ms", ctypes.c_double), ("primal_res", ctypes.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}

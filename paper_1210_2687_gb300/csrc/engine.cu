@@ -915,6 +915,7 @@ static int solve_all_impl(DeviceCtx* ctx, const std::vector<std::vector<int>>& c
             r.objective = c.have_obj ? c.obj : NAN;
             r.rel_x = c.rel_x;
             r.rel_obj = c.rel_obj;
+            r.primal_res = c.primal_res;
             r.t_start_ms = c.t_start >= c.t0 ? (double)(c.t_start - c.t0) * 1e-6 : 0.0;
             r.t_done_ms = c.t_done >= c.t0 ? (double)(c.t_done - c.t0) * 1e-6 : 0.0;
         }
@@ -1411,6 +1412,7 @@ extern "C" int admm_deconv_solve_noalloc(const admm_params_t* p, const float* y,
         res->objective = c.have_obj ? c.obj : NAN;
         res->rel_x = c.rel_x;
         res->rel_obj = c.rel_obj;
+        res->primal_res = c.primal_res;
         res->t_start_ms = c.t_start >= c.t0 ? (double)(c.t_start - c.t0) * 1e-6 : 0.0;
         res->t_done_ms = c.t_done >= c.t0 ? (double)(c.t_done - c.t0) * 1e-6 : 0.0;
     }

@@ -87,7 +87,7 @@ haar_row_inverse(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp
     float* __restrict__ xw = P.work;
     float* __restrict__ z1w = P.work + n;
     const float mu1 = P.mu1, inv1 = P.inv1pmu1;
-    CompSum s_data, s_xx, s_dxx;
+    CompSum s_data, s_xx, s_dxx, s_pr;
 #pragma unroll
     for (int m = 0; m < 8; ++m) {
         const int c = t + m * FT;
@@ -103,9 +103,13 @@ haar_row_inverse(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp
         P.d1[pix] = nd1;
         z1w[pix] = u1 + nd1;
         xw[pix] = x;
-        if (nobj && obs) {
-            const float e = ax - yb;
-            s_data.add(0.5f * e * e);
+        if (nobj) {
+            if (obs) {
+                const float e = ax - yb;
+                s_data.add(0.5f * e * e);
+            }
+            const float e1 = nd1 - dd1;       // d1 part of d_k - d_{k-1}
+            s_pr.add(e1 * e1);
         }
         if (chk) {
             const float dx = first ? x : x - pxp[c];
@@ -116,7 +120,7 @@ haar_row_inverse(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp
     }
     // partial sums only where the tile kernel evaluates the stop rule
     if (nobj || chk) {
-        const CompSum acc[kNumPartials] = {s_data, CompSum(), s_xx, s_dxx};
+        const CompSum acc[kNumPartials] = {s_data, CompSum(), s_xx, s_dxx, s_pr};
         double pv[kNumPartials];
         block_reduce_comp(acc, reinterpret_cast<float*>(red), pv);
         if (tid == 0) {
@@ -236,7 +240,7 @@ haar_analysis(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W, in
         __syncthreads();
     }
 
-    CompSum l1;
+    CompSum l1, pr;
 #pragma unroll
     for (int lvl = 0; lvl < L; ++lvl) {
         const int s = 1 << lvl;
@@ -281,6 +285,7 @@ haar_analysis(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W, in
             }
         }
         float ao[4], nd4[3][4], z4[3][4];
+        float prl = 0.f;                         // this level's share of ||d_k - d_{k-1}||^2
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             const float a00 = w0[e], a01 = w0[e + s], a10 = w1[e], a11 = w1[e + s];
@@ -295,9 +300,14 @@ haar_analysis(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W, in
                 const float u = soft_thresh(sv, tau);           // eq. soft
                 nd4[j][e] = u - sv;                             // d2 - (c - u2)
                 z4[j][e] = u + nd4[j][e];                       // zeta2 = u2 + d2
-                if (nobj) l1.add(fabsf(cb[j]));
+                if (nobj) {
+                    l1.add(fabsf(cb[j]));
+                    const float e2 = nd4[j][e] - dold[j][e];    // d2 part of d_k - d_{k-1}
+                    prl = fmaf(e2, e2, prl);
+                }
             }
         }
+        if (nobj) pr.add(prl);
         *reinterpret_cast<float4*>(Aout + orow * XA + ocol) = make_float4(ao[0], ao[1], ao[2], ao[3]);
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
@@ -345,21 +355,27 @@ haar_analysis(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W, in
             cb[0] += zv.x; cb[1] += zv.y; cb[2] += zv.z; cb[3] += zv.w;
         }
         float nd[4], z[4];
+        float prl = 0.f;
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             const float sv = cb[e] - dold[e];
             const float u = soft_thresh(sv, tau_ll);
             nd[e] = u - sv;
             z[e] = u + nd[e];
-            if (nobj && !ll_free) l1.add(fabsf(cb[e]));
+            if (nobj) {
+                if (!ll_free) l1.add(fabsf(cb[e]));
+                const float e2 = nd[e] - dold[e];
+                prl = fmaf(e2, e2, prl);
+            }
         }
+        if (nobj) pr.add(prl);
         const size_t bo = (size_t)(3 * L) * n + gq;
         *reinterpret_cast<float4*>(d2out + bo) = make_float4(nd[0], nd[1], nd[2], nd[3]);
         *reinterpret_cast<float4*>(d2io + bo) = make_float4(z[0], z[1], z[2], z[3]);
     }
-    double pv[kNumPartials] = {0.0, 0.0, 0.0, 0.0};
+    double pv[kNumPartials] = {0.0};
     if (nobj || chk) {
-        const CompSum acc[kNumPartials] = {CompSum(), l1, CompSum(), CompSum()};
+        const CompSum acc[kNumPartials] = {CompSum(), l1, CompSum(), CompSum(), pr};
         block_reduce_comp(acc, reinterpret_cast<float*>(red), pv);
     }
     finish_iteration<kThreads>(P, k, chk, nobj, pv, n_active, n_row_ctas + blockIdx.x, probs, sl);

@@ -31,7 +31,7 @@
 namespace admm {
 
 constexpr int kThreads = 256;
-constexpr int kNumPartials = 4;   // data term, regulariser sum, ||x||^2, ||x - x_prev||^2
+constexpr int kNumPartials = 5;   // data term, regulariser sum, ||x||^2, ||x - x_prev||^2, ||d - d_prev||^2
 
 // Mutable per-problem control block.
 struct ProbCtl {
@@ -45,6 +45,7 @@ struct ProbCtl {
     double obj_prev;
     double rel_x;      // -1 until evaluated
     double rel_obj;    // -1 until evaluated
+    double primal_res; // ||d_k - d_{k-1}|| = ||H z_k - u_k|| (Alg. 2), -1 until evaluated
     int input_bad;     // set by prepare_kernel: an observed value is not finite
     int pad_;
     unsigned long long t0;       // device clock (ns) when the batch was set up
@@ -568,7 +569,7 @@ __device__ void finish_iteration(const ProbDesc& P, int k, bool chk, bool nobj,
     }
     __syncthreads();
     if (!s_last) return;
-    double acc[kNumPartials] = {0.0, 0.0, 0.0, 0.0};
+    double acc[kNumPartials] = {0.0};
     if (need) {
         __threadfence();
         const int nslots = P.n_slots > 0 ? P.n_slots : P.n_strips;
@@ -609,6 +610,7 @@ __device__ void finish_iteration(const ProbDesc& P, int k, bool chk, bool nobj,
         ctl->obj_prev = f;
         ctl->obj = f;
         ctl->have_obj = 1;
+        ctl->primal_res = sqrt(fmax(acc[4], 0.0));
     }
     if (chk) {
         if (!isfinite(acc[2]) || !isfinite(acc[3])) {
@@ -831,7 +833,7 @@ row_phase_tv(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp, co
     // (2) proxes and dual updates, each warp walking down its columns
     const float tau = P.tau, gam = P.gamma, mu1 = P.mu1, inv1 = P.inv1pmu1;
     constexpr bool aniso = ANISO;
-    CompSum s_data, s_reg, s_xx, s_dxx;
+    CompSum s_data, s_reg, s_xx, s_dxx, s_pr;
     float dvprev[C::CPT];
     const bool need_xp = chk && !first;
     float xpn[C::CPT];               // x_prev of the next owned row
@@ -900,6 +902,7 @@ row_phase_tv(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp, co
                 const float xrs[2] = {xa[pp].z, xrp[pp]}, xds[2] = {xdn[pp].x, xdn[pp].y};
                 const float ddh[2] = {dd.x, dd.z}, ddv[2] = {dd.y, dd.w};
                 float nh[2], nv[2];
+                float prp = 0.f;         // the pair's share of ||d_k - d_{k-1}||^2
 #pragma unroll
                 for (int e = 0; e < 2; ++e) {
                     // D_i x, u2 = prox(D_i x - d2, lambda/mu2), d2 <- d2 - (D_i x - u2),
@@ -912,7 +915,11 @@ row_phase_tv(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp, co
                     nv[e] = uv - sv;
                     dhcur[2 * pp + e] = uh + nh[e];
                     dvcur[2 * pp + e] = uv + nv[e];
-                    if (owned && nobj) s_reg.add(tv_norm(gh, gv, aniso));
+                    if (owned && nobj) {
+                        s_reg.add(tv_norm(gh, gv, aniso));
+                        const float eh = nh[e] - ddh[e], ev = nv[e] - ddv[e];
+                        prp = fmaf(eh, eh, fmaf(ev, ev, prp));
+                    }
                 }
                 if (owned) {
                     *reinterpret_cast<float4*>(d2out + pix) = make_float4(nh[0], nv[0], nh[1], nv[1]);
@@ -928,9 +935,13 @@ row_phase_tv(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp, co
                         const float u1 = obs ? fmaf(mu1, s1, ybs[e]) * inv1 : s1;
                         nd1[e] = d1s[e] - (axs[e] - u1);
                         z1cur[2 * pp + e] = u1 + nd1[e];
-                        if (nobj && obs) {
-                            const float er = axs[e] - ybs[e];
-                            s_data.add(0.5f * er * er);
+                        if (nobj) {
+                            if (obs) {
+                                const float er = axs[e] - ybs[e];
+                                s_data.add(0.5f * er * er);
+                            }
+                            const float e1 = nd1[e] - d1s[e];
+                            prp = fmaf(e1, e1, prp);
                         }
                         if (chk) {
                             const float dx = first ? xs[e] : xs[e] - xpc[2 * pp + e];
@@ -940,6 +951,7 @@ row_phase_tv(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp, co
                     }
                     *reinterpret_cast<float2*>(P.d1 + pix) = make_float2(nd1[0], nd1[1]);
                     if (sprev) *reinterpret_cast<float2*>(P.xprev + pix) = make_float2(xs[0], xs[1]);
+                    if (nobj) s_pr.add(prp);
                 }
             }
             if (lane == 0 && owned) {
@@ -1024,6 +1036,9 @@ row_phase_tv(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp, co
                             s_data.add(0.5f * e * e);
                         }
                         s_reg.add(tv_norm(gh, gv, aniso));
+                        // d_k - d_{k-1} of both splits (Alg. 2: H z - u)
+                        const float e1 = nd1 - dd1, eh = nh - dd.x, ev = nv - dd.y;
+                        s_pr.add(fmaf(e1, e1, fmaf(eh, eh, ev * ev)));
                     }
                     if (chk) {
                         const float dx = first ? x : x - xpc[j];
@@ -1073,9 +1088,9 @@ row_phase_tv(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp, co
 
     // (3) block partial sums (published after the transforms below), only
     // where the stop rule or the objective is evaluated
-    double part[kNumPartials] = {0.0, 0.0, 0.0, 0.0};
+    double part[kNumPartials] = {0.0};
     if (nobj || chk) {
-        const CompSum acc[kNumPartials] = {s_data, s_reg, s_xx, s_dxx};
+        const CompSum acc[kNumPartials] = {s_data, s_reg, s_xx, s_dxx, s_pr};
         block_reduce_comp<NT>(acc, reinterpret_cast<float*>(red), part);
     }
 

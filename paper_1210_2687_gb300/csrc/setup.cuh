@@ -91,6 +91,7 @@ __global__ void init_ctl_kernel(ProbDesc* __restrict__ probs, int count, int* __
     c->obj_prev = 0.0;
     c->rel_x = -1.0;
     c->rel_obj = -1.0;
+    c->primal_res = -1.0;
     c->t0 = device_clock_ns();
     c->t_start = 0;
     c->t_done = bad ? c->t0 : 0;

@@ -54,7 +54,8 @@ def test_struct_layout_matches_header(ad):
     # admm_params_t: 4 ints, pointer, 3 floats, 3 ints, double, 3 ints
     assert ctypes.sizeof(ad.admm_params_t) == 72
     assert ad.admm_params_t.tol.offset == 48
-    assert ctypes.sizeof(ad.admm_result_t) == 56
+    assert ctypes.sizeof(ad.admm_result_t) == 64
+    assert ad.admm_result_t.primal_res.offset == 56
 
 
 @pytest.mark.parametrize("change,code", [

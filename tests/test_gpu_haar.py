@@ -140,3 +140,31 @@ def test_mixed_tv_and_frame_batch(ad):
         torch.cuda.synchronize()
         assert r.iters == res[i].iters == 13
         assert torch.equal(xo, xs[i])
+
+
+@pytest.mark.parametrize("reg", ["haar", "haar_synthesis"])
+def test_frame_primal_residual_matches_oracle(ad, reg):
+    """d_k - d_{k-1} over d1 and all 13 bands of d2 (the primal residual of
+    Algorithm 2) on the last iteration, against the oracle's duals."""
+    import torch
+    psf = S.psf_gaussian(7, 1.5)
+    _, ybar, mask = _problem(128, 128, psf, 0.8, 17)
+    lam, mu1, mu2 = 1e-3, 3e-2, 1e-2
+    k = 6
+    st = O.State.zeros(128, 128, "haar", 4)
+    for _ in range(k):
+        prev = st
+        if reg == "haar":
+            st = O.famd_step(st, ybar, mask, psf, lam, mu1, mu2, 4)
+        else:
+            st = O.fsmd_step(st, ybar, mask, psf, lam, mu1, mu2, 4)
+    ref = float(np.sqrt(np.sum((st.d1 - prev.d1) ** 2) + np.sum((st.d2 - prev.d2) ** 2)))
+    plan = ad.Plan(128, 128, psf, lam, mu1, mu2, reg, levels=4, max_iters=k)
+    y = torch.from_numpy(ybar.astype(np.float32)).cuda()
+    m = torch.from_numpy(mask).cuda()
+    x = torch.empty((128, 128), dtype=torch.float32, device="cuda")
+    res = ad.solve(plan, y, m, x)
+    torch.cuda.synchronize()
+    plan.close()
+    assert ref > 0
+    assert abs(res.primal_res - ref) <= 1e-3 * ref, (res.primal_res, ref)

@@ -343,3 +343,19 @@ def test_strip_halo_reads_old_duals(ad):
 
 def test_empty_batch_is_ok(ad):
     assert ad.lib.admm_deconv_solve_batch(None, 0, None, None, None, None, None) == 0
+
+
+@pytest.mark.parametrize("reg", ["tv", "tv_aniso"])
+def test_primal_residual_matches_oracle(ad, reg):
+    """The primal residual H z_k - u_k = d_k - d_{k-1} of Algorithm 2, reduced
+    over both splits on the last iteration, against the oracle's duals."""
+    p = S.config1_problem(3)
+    k = 6
+    st = O.State.zeros(64, 64, "tv")
+    for _ in range(k):
+        prev = st
+        st = O.tvmd_step(st, p.ybar, p.mask, p.psf, p.lam, p.mu1, p.mu2, aniso=reg == "tv_aniso")
+    ref = math.sqrt(float(np.sum((st.d1 - prev.d1) ** 2) + np.sum((st.d2 - prev.d2) ** 2)))
+    x, res, _ = _gpu_solve(ad, p.ybar, p.mask, p.psf, p.lam, p.mu1, p.mu2, k, reg=reg)
+    assert ref > 0
+    assert abs(res.primal_res - ref) <= 1e-3 * ref, (res.primal_res, ref)
