@@ -6,7 +6,7 @@
  * convolutional network that predicts a starting image x0 and duals d0 from
  * the observation, which admm_deconv_warm_start (admm_deconv.h) turns into
  * the start u0 = H x0 - d0. The solver then runs to its usual stop rule, so
- * the plain ADMM remains the judge of the result.
+ * the plain ADMM still decides the result.
  *
  * Network: 8 convolutions of 3 x 3 (zero padding, "same" size), 32 channels,
  * ReLU between them:

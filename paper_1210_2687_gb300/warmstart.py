@@ -5,7 +5,7 @@ that this ADMM itself computes: for each synthetic TV problem the solver runs
 from u0 = d0 = 0 to rel-x < 1e-5 and its (x*, d1*, d2*) is the target. At
 solve time the prediction feeds admm_deconv_warm_start and the solver runs
 to the same stop rule as from a cold start (Theorem 1: any start converges),
-so the plain ADMM stays the judge of the result.
+so the plain ADMM still decides the result.
 
     python -m paper_1210_2687_gb300.warmstart train        # writes weights/warmstart_tv.npz
     python -m paper_1210_2687_gb300.warmstart eval --weights weights.npz --count 64
