@@ -20,8 +20,11 @@ Unknown Boundaries Using the Alternating Direction Method of Multipliers":
 Conventions (readings of points the paper leaves open; each is listed with
 its justification in the design notes):
 
-* DFT: unnormalised forward, 1/n inverse (numpy.fft); U of eq. DFT_fact is the
-  unitary version, the diagonal ratios of eq. fast_inversion are unchanged.
+* DFT: the oracle's own, written out as its definition: the 2-D DFT of an
+  H x W array is F_H X F_W with the DFT matrices F_N[j, k] = exp(-2 pi i j k / N)
+  (unnormalised forward), and the inverse is conj(F_H) X conj(F_W) / (H W).
+  U of eq. DFT_fact is the unitary version; the diagonal ratios of eq.
+  fast_inversion are unchanged. No FFT library is used.
 * A is periodic convolution on the full domain with the kernel centred at
   (0, 0):  (A x)[r,c] = sum_{a,b} h[a+l_r, b+l_c] x[(r-a) mod H, (c-b) mod W].
 * D^h, D^v are forward periodic differences:
@@ -46,7 +49,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 __all__ = [
-    "psf_otf", "A_fft", "At_fft", "A_direct", "At_direct",
+    "dft2", "idft2", "psf_otf", "A_fft", "At_fft", "A_direct", "At_direct",
     "Dh", "Dv", "DhT", "DvT", "tv_denominator_diag",
     "haar_analysis", "haar_synthesis", "haar_nbands",
     "soft", "vsoft", "mask_prox",
@@ -54,6 +57,36 @@ __all__ = [
     "State", "tvmd_step", "famd_step", "fsmd_step", "solve",
     "isnr", "snr",
 ]
+
+
+# --------------------------------------------------------------------------
+# the discrete Fourier transform (Sec. III-C: U and U* of eq. DFT_fact, up to
+# the 1/sqrt(n) normalisation), by its definition
+# --------------------------------------------------------------------------
+_DFT_CACHE: dict = {}
+
+
+def _dft_matrix(N: int) -> np.ndarray:
+    """F_N[j, k] = exp(-2 pi i j k / N); the exponent is reduced as (j k mod N)
+    so that every entry is one of the N exact N-th roots of unity."""
+    F = _DFT_CACHE.get(N)
+    if F is None:
+        jk = np.mod(np.outer(np.arange(N), np.arange(N)), N)
+        F = np.exp(-2j * np.pi * jk / N)
+        _DFT_CACHE[N] = F
+    return F
+
+
+def dft2(x: np.ndarray) -> np.ndarray:
+    """X[kr, kc] = sum_{r, c} x[r, c] exp(-2 pi i (kr r / H + kc c / W))."""
+    H, W = x.shape
+    return _dft_matrix(H) @ np.asarray(x, dtype=np.complex128) @ _dft_matrix(W)
+
+
+def idft2(X: np.ndarray) -> np.ndarray:
+    """x[r, c] = (1 / (H W)) sum_{kr, kc} X[kr, kc] exp(+2 pi i (kr r / H + kc c / W))."""
+    H, W = X.shape
+    return (np.conj(_dft_matrix(H)) @ np.asarray(X, dtype=np.complex128) @ np.conj(_dft_matrix(W))) / (H * W)
 
 
 # --------------------------------------------------------------------------
@@ -72,19 +105,19 @@ def _centred_kernel(psf: np.ndarray, H: int, W: int) -> np.ndarray:
 
 def psf_otf(psf: np.ndarray, H: int, W: int) -> np.ndarray:
     """Lambda: the DFT of the convolution kernel (diagonal of eq. DFT_fact)."""
-    return np.fft.fft2(_centred_kernel(psf, H, W))
+    return dft2(_centred_kernel(psf, H, W))
 
 
 def A_fft(x: np.ndarray, psf: np.ndarray) -> np.ndarray:
     """A x = U* Lambda U x (eq. DFT_fact)."""
     H, W = x.shape
-    return np.real(np.fft.ifft2(psf_otf(psf, H, W) * np.fft.fft2(x)))
+    return np.real(idft2(psf_otf(psf, H, W) * dft2(x)))
 
 
 def At_fft(x: np.ndarray, psf: np.ndarray) -> np.ndarray:
     """A^T x = U* conj(Lambda) U x."""
     H, W = x.shape
-    return np.real(np.fft.ifft2(np.conj(psf_otf(psf, H, W)) * np.fft.fft2(x)))
+    return np.real(idft2(np.conj(psf_otf(psf, H, W)) * dft2(x)))
 
 
 def A_direct(x: np.ndarray, psf: np.ndarray) -> np.ndarray:
@@ -136,8 +169,8 @@ def tv_denominator_diag(psf, H, W, mu1, mu2):
     lam = psf_otf(psf, H, W)
     eh = np.zeros((H, W)); eh[0, 0] = -1.0; eh[0, (-1) % W] += 1.0   # D^h x = e_h (*) x
     ev = np.zeros((H, W)); ev[0, 0] = -1.0; ev[(-1) % H, 0] += 1.0
-    dh = np.fft.fft2(eh)
-    dv = np.fft.fft2(ev)
+    dh = dft2(eh)
+    dv = dft2(ev)
     return mu1 * np.abs(lam) ** 2 + mu2 * np.abs(dh) ** 2 + mu2 * np.abs(dv) ** 2
 
 
@@ -291,11 +324,11 @@ def tvmd_step(st: State, ybar, mask, psf, lam, mu1, mu2, otf=None, denom=None, a
     delta_h = st.u2[0] + st.d2[0]
     delta_v = st.u2[1] + st.d2[1]
     # line 6: z = K (mu1 A^T zeta1 + mu2 Dh^T delta_h + mu2 Dv^T delta_v), K of eq. fast_inversion
-    rhs = mu1 * np.real(np.fft.ifft2(np.conj(otf) * np.fft.fft2(zeta1))) \
+    rhs = mu1 * np.real(idft2(np.conj(otf) * dft2(zeta1))) \
         + mu2 * DhT(delta_h) + mu2 * DvT(delta_v)
-    x = np.real(np.fft.ifft2(np.fft.fft2(rhs) / denom))
+    x = np.real(idft2(dft2(rhs) / denom))
     # line 7 -> eq. new_line: u1 = (M^T M + mu1 I)^{-1} (M^T y + mu1 (A z - d1))
-    ax = np.real(np.fft.ifft2(otf * np.fft.fft2(x)))
+    ax = np.real(idft2(otf * dft2(x)))
     u1 = mask_prox(ax - st.d1, ybar, mask, mu1)
     # line 8: d1 = d1 - (A z - u1)
     d1 = st.d1 - (ax - u1)
@@ -322,10 +355,10 @@ def famd_step(st: State, ybar, mask, psf, lam, mu1, mu2, levels=4, otf=None, ll_
     zeta1 = st.u1 + st.d1
     zeta2 = st.u2 + st.d2
     # line 4 with P^T P = I: z = U* (|Lambda|^2 + gamma)^{-1} U (A^T zeta1 + gamma P^T zeta2)
-    rhs = np.real(np.fft.ifft2(np.conj(otf) * np.fft.fft2(zeta1))) + gam * haar_synthesis(zeta2, levels)
-    x = np.real(np.fft.ifft2(np.fft.fft2(rhs) / (np.abs(otf) ** 2 + gam)))
+    rhs = np.real(idft2(np.conj(otf) * dft2(zeta1))) + gam * haar_synthesis(zeta2, levels)
+    x = np.real(idft2(dft2(rhs) / (np.abs(otf) ** 2 + gam)))
     # lines 6-7, j = 1: mask-decoupled prox and dual update
-    ax = np.real(np.fft.ifft2(otf * np.fft.fft2(x)))
+    ax = np.real(idft2(otf * dft2(x)))
     u1 = mask_prox(ax - st.d1, ybar, mask, mu1)
     d1 = st.d1 - (ax - u1)
     # lines 6-7, j = 2: soft threshold of the frame coefficients
@@ -353,12 +386,12 @@ def fsmd_step(st: State, ybar, mask, psf, lam, mu1, mu2, levels=4, otf=None) -> 
     gam = mu2 / mu1
     zeta1 = st.u1 + st.d1
     zeta2 = st.u2 + st.d2
-    r = haar_analysis(np.real(np.fft.ifft2(np.conj(otf) * np.fft.fft2(zeta1))), levels) + gam * zeta2
-    awr = np.fft.fft2(haar_synthesis(r, levels)) * otf
-    q = np.real(np.fft.ifft2(np.conj(otf) * awr / (np.abs(otf) ** 2 + gam)))
+    r = haar_analysis(np.real(idft2(np.conj(otf) * dft2(zeta1))), levels) + gam * zeta2
+    awr = dft2(haar_synthesis(r, levels)) * otf
+    q = np.real(idft2(np.conj(otf) * awr / (np.abs(otf) ** 2 + gam)))
     theta = (r - haar_analysis(q, levels)) / gam
     x = haar_synthesis(theta, levels)
-    ax = np.real(np.fft.ifft2(otf * np.fft.fft2(x)))
+    ax = np.real(idft2(otf * dft2(x)))
     u1 = mask_prox(ax - st.d1, ybar, mask, mu1)
     d1 = st.d1 - (ax - u1)
     u2 = soft(theta - st.d2, lam / mu2)

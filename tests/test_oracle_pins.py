@@ -627,3 +627,222 @@ def test_fs_strong_weight_gives_zero():
     ybar, mask, _ = S.observe(x, h, None, 40.0, g)
     r = O.solve(ybar, mask, h, 10.0, 0.3, 3.0, "haar_synthesis", iters=3000)
     assert np.max(np.abs(r.x)) < 1e-9 and np.max(np.abs(r.state.theta)) < 1e-9
+
+
+# ----------------------------------------------------------------------------
+# the oracle's own DFT (Sec. III-C, eq. DFT_fact)
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("H,W", [(5, 7), (9, 3), (8, 12), (1, 6)])
+def test_own_dft_closed_forms_and_library(H, W):
+    """dft2 / idft2 against closed forms -- a unit impulse at (r0, c0) has the
+    spectrum exp(-2 pi i (k_r r0 / H + k_c c0 / W)); a constant has all its
+    energy at k = 0; the complex exponential of frequency (k0, l0) is n times
+    the impulse there -- against an independent FFT library (numpy.fft), and
+    the inverse and Parseval's identity on random data, including odd sides."""
+    g = S.rng(40)
+    kr = np.arange(H)[:, None]
+    kc = np.arange(W)[None, :]
+    r0, c0 = H // 2, W - 1
+    e = np.zeros((H, W))
+    e[r0, c0] = 1.0
+    np.testing.assert_allclose(O.dft2(e), np.exp(-2j * np.pi * (kr * r0 / H + kc * c0 / W)), atol=1e-14)
+    const = np.full((H, W), 2.5)
+    expect = np.zeros((H, W), dtype=complex)
+    expect[0, 0] = 2.5 * H * W
+    np.testing.assert_allclose(O.dft2(const), expect, atol=1e-12)
+    k0, l0 = (1 % H), (2 % W)
+    rr = np.arange(H)[:, None]
+    cc = np.arange(W)[None, :]
+    wave = np.exp(2j * np.pi * (k0 * rr / H + l0 * cc / W))
+    expect = np.zeros((H, W), dtype=complex)
+    expect[k0, l0] = H * W
+    np.testing.assert_allclose(O.dft2(wave), expect, atol=1e-12)
+    x = g.standard_normal((H, W)) + 1j * g.standard_normal((H, W))
+    X = O.dft2(x)
+    np.testing.assert_allclose(X, np.fft.fft2(x), atol=1e-12)
+    np.testing.assert_allclose(O.idft2(X), x, atol=1e-13)
+    np.testing.assert_allclose(O.idft2(x), np.fft.ifft2(x), atol=1e-13)
+    np.testing.assert_allclose(np.sum(np.abs(X) ** 2), H * W * np.sum(np.abs(x) ** 2), rtol=1e-12)
+
+
+def test_psf_otf_odd_size_explicit_sum():
+    """Lambda on an odd, non-square domain equals the DFT sum of the centred
+    kernel written out tap by tap: sum_{a,b} h[a+l_r, b+l_c] exp(-2 pi i
+    (k_r a / H + k_c b / W)) (reading 1: the kernel's centre at (0, 0))."""
+    g = S.rng(41)
+    H, W = 9, 11
+    h = _rand_psf(g, 5, 3)
+    lam = np.zeros((H, W), dtype=complex)
+    for kr in range(H):
+        for kc in range(W):
+            acc = 0j
+            for a in range(-2, 3):
+                for b in range(-1, 2):
+                    acc += h[a + 2, b + 1] * np.exp(-2j * np.pi * (kr * a / H + kc * b / W))
+            lam[kr, kc] = acc
+    np.testing.assert_allclose(O.psf_otf(h, H, W), lam, atol=1e-14)
+
+
+# ----------------------------------------------------------------------------
+# the objectives (eq. unconstrained_TV_uBC, eq. unconstrained_analysis_uBC) and
+# the figure of merit ISNR (Sec. V)
+# ----------------------------------------------------------------------------
+def test_objective_tv_closed_forms():
+    """Closed forms of eq. unconstrained_TV_uBC that a dropped 1/2, a missing
+    mask in the data term, a wrong lambda factor or a wrong TV norm would fail:
+      x = 0:                      f = 1/2 sum over observed pixels of y^2
+      x = c (constant):           f = 1/2 sum_obs (y - beta c)^2, beta = sum(h)
+                                  (A 1 = beta 1, and D 1 = 0)
+      x[r, c] = c (column ramp):  forward periodic differences are 1, except
+                                  1 - W at the wrap; TV = H (W - 1) + H (W - 1)
+      x[r, c] = r + c:            isotropic TV is sqrt(2) on the (H-1)(W-1)
+                                  interior pixels, sqrt((W-1)^2 + 1) on the last
+                                  column, sqrt((H-1)^2 + 1) on the last row and
+                                  sqrt((H-1)^2 + (W-1)^2) at the corner;
+                                  anisotropic TV is 2 H (W - 1) + 2 W (H - 1)."""
+    g = S.rng(42)
+    H, W = 7, 10
+    h = _rand_psf(g, 3, 5) * 0.8
+    beta = h.sum()
+    ybar = g.standard_normal((H, W))
+    mask = (g.uniform(size=(H, W)) > 0.4).astype(np.uint8)
+    obs = mask.astype(bool)
+    lam = 0.37
+    zero = np.zeros((H, W))
+    np.testing.assert_allclose(O.objective_tv(zero, ybar, mask, h, lam), 0.5 * np.sum(ybar[obs] ** 2), rtol=1e-13)
+    np.testing.assert_allclose(O.objective_tv(zero, ybar, mask, h, lam, aniso=True),
+                               0.5 * np.sum(ybar[obs] ** 2), rtol=1e-13)
+    c = 0.6
+    np.testing.assert_allclose(O.objective_tv(np.full((H, W), c), ybar, mask, h, lam),
+                               0.5 * np.sum((ybar[obs] - beta * c) ** 2), rtol=1e-12)
+    rr, cc = np.meshgrid(np.arange(H, dtype=float), np.arange(W, dtype=float), indexing="ij")
+    # with nothing observed only the regulariser remains
+    none = np.zeros((H, W), dtype=np.uint8)
+    np.testing.assert_allclose(O.objective_tv(cc, ybar, none, h, lam), lam * 2 * H * (W - 1), rtol=1e-13)
+    iso = ((H - 1) * (W - 1) * math.sqrt(2.0) + (H - 1) * math.hypot(W - 1, 1) + (W - 1) * math.hypot(H - 1, 1)
+           + math.hypot(H - 1, W - 1))
+    np.testing.assert_allclose(O.objective_tv(rr + cc, ybar, none, h, lam), lam * iso, rtol=1e-13)
+    np.testing.assert_allclose(O.objective_tv(rr + cc, ybar, none, h, lam, aniso=True),
+                               lam * (2 * H * (W - 1) + 2 * W * (H - 1)), rtol=1e-13)
+
+
+def test_objective_haar_closed_forms():
+    """Closed forms of eq. unconstrained_analysis_uBC with the 13-band frame:
+    for x = a (-1)^(r+c) + b on an even torus the level-0 high-high band is
+    a (-1)^(r+c), every other detail band is zero and the final low-low band
+    is b, so ||P x||_1 = n (|a| + |b|), and n |a| with the low-low band
+    unpenalised; for x = a (-1)^c + b only the level-0 rows-low/columns-high
+    band and the low-low band survive, with the same sums. The data term is
+    checked at x = 0 and at a constant, where A x = beta x."""
+    g = S.rng(43)
+    H, W = 16, 16
+    n = H * W
+    h = _rand_psf(g, 5, 5) * 1.3
+    beta = h.sum()
+    ybar = g.standard_normal((H, W))
+    mask = (g.uniform(size=(H, W)) > 0.3).astype(np.uint8)
+    obs = mask.astype(bool)
+    lam = 0.21
+    none = np.zeros((H, W), dtype=np.uint8)
+    rr, cc = np.meshgrid(np.arange(H), np.arange(W), indexing="ij")
+    a, b = -0.7, 0.45
+    for x in (a * (-1.0) ** (rr + cc) + b, a * (-1.0) ** cc + b):
+        np.testing.assert_allclose(O.objective_haar(x, ybar, none, h, lam), lam * n * (abs(a) + abs(b)), rtol=1e-12)
+        np.testing.assert_allclose(O.objective_haar(x, ybar, none, h, lam, ll_free=True), lam * n * abs(a),
+                                   rtol=1e-12)
+    zero = np.zeros((H, W))
+    np.testing.assert_allclose(O.objective_haar(zero, ybar, mask, h, lam), 0.5 * np.sum(ybar[obs] ** 2), rtol=1e-13)
+    cst = np.full((H, W), b)
+    np.testing.assert_allclose(O.objective_haar(cst, ybar, mask, h, lam),
+                               0.5 * np.sum((ybar[obs] - beta * b) ** 2) + lam * n * abs(b), rtol=1e-12)
+    np.testing.assert_allclose(O.objective_haar(cst, ybar, mask, h, lam, ll_free=True),
+                               0.5 * np.sum((ybar[obs] - beta * b) ** 2), rtol=1e-12)
+
+
+def _dense_conv_loops(h, H, W):
+    """The matrix of periodic convolution, entry by entry from its definition
+    (reading 1): row (r, c) has h[a + l_r, b + l_c] at column ((r-a) mod H, (c-b) mod W)."""
+    ph, pw = h.shape
+    lr, lc = ph // 2, pw // 2
+    A = np.zeros((H * W, H * W))
+    for r in range(H):
+        for c in range(W):
+            for a in range(-lr, lr + 1):
+                for b in range(-lc, lc + 1):
+                    A[r * W + c, ((r - a) % H) * W + (c - b) % W] += h[a + lr, b + lc]
+    return A
+
+
+def test_objectives_brute_force_on_random_inputs():
+    """On random x, y, masks and asymmetric kernels: the data term from the
+    convolution matrix built entry by entry, and the regularisers summed pixel
+    by pixel (TV with forward periodic differences, reading 3; the frame
+    coefficients from the bands' defining two-tap sums, reading 6)."""
+    g = S.rng(44)
+    H, W = 6, 8
+    h = _rand_psf(g, 3, 5)
+    A = _dense_conv_loops(h, H, W)
+    x = g.standard_normal((H, W))
+    ybar = g.standard_normal((H, W))
+    mask = (g.uniform(size=(H, W)) > 0.35).astype(np.uint8)
+    lam = 0.13
+    ax = (A @ x.ravel()).reshape(H, W)
+    data = 0.0
+    for r in range(H):
+        for c in range(W):
+            if mask[r, c]:
+                data += 0.5 * (ybar[r, c] - ax[r, c]) ** 2
+    iso = aniso = 0.0
+    for r in range(H):
+        for c in range(W):
+            gh = x[r, (c + 1) % W] - x[r, c]
+            gv = x[(r + 1) % H, c] - x[r, c]
+            iso += math.sqrt(gh * gh + gv * gv)
+            aniso += abs(gh) + abs(gv)
+    np.testing.assert_allclose(O.objective_tv(x, ybar, mask, h, lam), data + lam * iso, rtol=1e-12)
+    np.testing.assert_allclose(O.objective_tv(x, ybar, mask, h, lam, aniso=True), data + lam * aniso, rtol=1e-12)
+    # one-level frame (2 x 2 Haar at taps {0, 1}) on an 8 x 8 torus, by its sums
+    H = W = 8
+    A = _dense_conv_loops(h, H, W)
+    x = g.standard_normal((H, W))
+    ybar = g.standard_normal((H, W))
+    mask = (g.uniform(size=(H, W)) > 0.35).astype(np.uint8)
+    ax = (A @ x.ravel()).reshape(H, W)
+    data = 0.5 * sum((ybar[r, c] - ax[r, c]) ** 2 for r in range(H) for c in range(W) if mask[r, c])
+    l1 = l1_ll = 0.0
+    for r in range(H):
+        for c in range(W):
+            p, q = x[r, c], x[r, (c + 1) % W]
+            s, t = x[(r + 1) % H, c], x[(r + 1) % H, (c + 1) % W]
+            lh = 0.25 * ((p - q) + (s - t))      # rows low, columns high
+            hl = 0.25 * ((p + q) - (s + t))      # rows high, columns low
+            hh = 0.25 * ((p - q) - (s - t))
+            ll = 0.25 * (p + q + s + t)
+            l1 += abs(lh) + abs(hl) + abs(hh) + abs(ll)
+            l1_ll += abs(lh) + abs(hl) + abs(hh)
+    np.testing.assert_allclose(O.objective_haar(x, ybar, mask, h, lam, levels=1), data + lam * l1, rtol=1e-12)
+    np.testing.assert_allclose(O.objective_haar(x, ybar, mask, h, lam, levels=1, ll_free=True),
+                               data + lam * l1_ll, rtol=1e-12)
+
+
+def test_isnr_hand_computed():
+    """ISNR = 10 log10(||x - ybar||^2 / ||x - x_hat||^2) over the region
+    (reading 13), on a 3 x 3 case computed by hand: inside the region (the
+    top-left 2 x 2) the observation errs by 1 and the estimate by 0.1, so the
+    ratio is 100 and ISNR = 20 dB; pixels outside the region do not count."""
+    x = np.array([[1.0, 2.0, 3.0], [4.0, 5.0, 6.0], [7.0, 8.0, 9.0]])
+    ybar = x.copy()
+    ybar[:2, :2] -= 1.0
+    ybar[2, 2] = 100.0            # outside the region: ignored
+    xh = x.copy()
+    xh[:2, :2] += 0.1
+    xh[0, 2] = -50.0              # outside the region: ignored
+    region = np.zeros((3, 3), dtype=bool)
+    region[:2, :2] = True
+    assert abs(O.isnr(x, ybar, xh, region) - 20.0) < 1e-12
+    # halving the estimate's error adds 10 log10(4) dB
+    xh2 = x.copy()
+    xh2[:2, :2] += 0.05
+    assert abs(O.isnr(x, ybar, xh2, region) - (20.0 + 10.0 * math.log10(4.0))) < 1e-12
+    # SNR = 10 log10(||x||^2 / ||x - x_hat||^2) over the whole image
+    assert abs(O.snr(x, x + 0.1 * np.sign(x)) - 10.0 * math.log10(np.sum(x ** 2) / (9 * 0.01))) < 1e-12
