@@ -16,6 +16,11 @@ Unknown Boundaries Using the Alternating Direction Method of Multipliers":
 * FS-MD  = Algorithm 2 on the synthesis formulation (Sec. IV-B, eq.
   unconstrained_synthesis_uBC): unknown theta, x = P^T theta, H1 = A P^T,
   H2 = I, line 4 by eq. inverse_synth2
+* TV-CG, FA-CG = the Reeves-Sorel variants (Sec. IV-D and IV-C, "Using the
+  Reeves-Sorel technique"): H1 = M A with g1(u) = 1/2 ||y - u||^2, the x-step
+  inverse applied as C - C B^T (B C B^T - I)^{-1} B C (eqs. ReevesTV, reeves3)
+  with one conjugate-gradient iteration per outer iteration, warm-started
+  from the previous one (Sec. IV-B, "Using the Reeves-Sorel technique")
 
 Conventions (readings of points the paper leaves open; each is listed with
 its justification in the design notes):
@@ -54,7 +59,7 @@ __all__ = [
     "haar_analysis", "haar_synthesis", "haar_nbands",
     "soft", "vsoft", "mask_prox",
     "objective_tv", "objective_haar", "objective_synthesis",
-    "State", "tvmd_step", "famd_step", "fsmd_step", "solve",
+    "State", "tvmd_step", "famd_step", "fsmd_step", "tvcg_step", "facg_step", "solve",
     "isnr", "snr",
 ]
 
@@ -298,6 +303,9 @@ class State:
     x: np.ndarray
     k: int = 0
     theta: np.ndarray | None = None    # synthesis coefficients (FS-MD only)
+    xi: np.ndarray | None = None       # TV-CG / FA-CG: the conjugate-gradient iterate of
+                                       # (B C B^T - I) xi = B C r, one entry per unobserved
+                                       # pixel, stored on the full grid (0 elsewhere)
 
     @staticmethod
     def zeros(H, W, reg="tv", levels=4):
@@ -307,7 +315,8 @@ class State:
 
     def copy(self):
         return State(self.u1.copy(), self.d1.copy(), self.u2.copy(), self.d2.copy(),
-                     self.x.copy(), self.k, None if self.theta is None else self.theta.copy())
+                     self.x.copy(), self.k, None if self.theta is None else self.theta.copy(),
+                     None if self.xi is None else self.xi.copy())
 
 
 def tvmd_step(st: State, ybar, mask, psf, lam, mu1, mu2, otf=None, denom=None, aniso=False) -> State:
@@ -399,6 +408,113 @@ def fsmd_step(st: State, ybar, mask, psf, lam, mu1, mu2, levels=4, otf=None) -> 
     return State(u1, d1, u2, d2, x, st.k + 1, theta)
 
 
+def reeves_sorel_xstep(r, mask, psf, denom, xi_prev, cg_iters=1, otf=None):
+    """x = C r - C B^T xi with xi ~ (B C B^T - I)^{-1} B C r (eqs. ReevesTV and
+    reeves3, Sec. IV-B's eq. reeves): C is the circulant inverse whose DFT
+    diagonal is 1 / denom; B holds the rows of A at the unobserved pixels
+    (mask == 0), so B v = (A v) on those pixels and B^T w = A^T of w placed on
+    them. The system for xi is solved by `cg_iters` conjugate-gradient
+    iterations started from xi_prev (Sec. IV-B: one iteration, warm-started).
+    B C B^T - I is negative definite; CG on it takes the same steps as on its
+    negation. Returns (x, xi)."""
+    H, W = r.shape
+    if otf is None:
+        otf = psf_otf(psf, H, W)
+    unobs = mask == 0
+
+    def C(v):
+        return np.real(idft2(dft2(v) / denom))
+
+    def B(v):
+        return np.real(idft2(otf * dft2(v)))[unobs]
+
+    def Bt(w):
+        full = np.zeros((H, W))
+        full[unobs] = w
+        return np.real(idft2(np.conj(otf) * dft2(full)))
+
+    def S(w):                      # (B C B^T - I) w
+        return B(C(Bt(w))) - w
+
+    Cr = C(r)
+    b = B(Cr)
+    xi = xi_prev[unobs].copy()
+    res = b - S(xi)
+    p = res.copy()
+    rr = float(res @ res)
+    for _ in range(cg_iters):
+        if rr == 0.0:
+            break
+        Sp = S(p)
+        alpha = rr / float(p @ Sp)
+        xi = xi + alpha * p
+        res = res - alpha * Sp
+        rr_new = float(res @ res)
+        p = res + (rr_new / rr) * p
+        rr = rr_new
+    x = Cr - C(Bt(xi))
+    xi_full = np.zeros((H, W))
+    xi_full[unobs] = xi
+    return x, xi_full
+
+
+def tvcg_step(st: State, ybar, mask, psf, lam, mu1, mu2, otf=None, denom=None, cg_iters=1) -> State:
+    """One iteration of TV-CG (Sec. IV-D, "Using the Reeves-Sorel technique"):
+    Algorithm 3 with H1 = M A (eq. H_1_analysis_sorel), g1(u) = 1/2 ||y - u||^2
+    (eq. g_1), so that in line 6 A^T becomes A^T M^T and K is eq. ReevesTV,
+    and in line 8 A becomes M A. u1 and d1 live on the observed pixels only
+    (zero elsewhere in these full-grid arrays)."""
+    H, W = ybar.shape
+    if otf is None:
+        otf = psf_otf(psf, H, W)
+    gam = mu2 / mu1
+    if denom is None:
+        denom = tv_denominator_diag(psf, H, W, 1.0, gam)     # C^{-1} = A^T A + gamma D^T D
+    obs = mask != 0
+    xi_prev = st.xi if st.xi is not None else np.zeros((H, W))
+    # lines 3-5
+    zeta1 = np.where(obs, st.u1 + st.d1, 0.0)               # M^T zeta1
+    delta_h = st.u2[0] + st.d2[0]
+    delta_v = st.u2[1] + st.d2[1]
+    # line 6: x = K (mu1 A^T M^T zeta1 + mu2 D^T delta), K = (1/mu1)(C - C B^T (B C B^T - I)^{-1} B C)
+    r = np.real(idft2(np.conj(otf) * dft2(zeta1))) + gam * (DhT(delta_h) + DvT(delta_v))
+    x, xi = reeves_sorel_xstep(r, mask, psf, denom, xi_prev, cg_iters, otf)
+    # line 7 with g1 = 1/2 ||y - u||^2: u1 = (y + mu1 (M A x - d1)) / (1 + mu1)
+    max_ = np.where(obs, np.real(idft2(otf * dft2(x))), 0.0)
+    u1 = np.where(obs, (ybar + mu1 * (max_ - st.d1)) / (1.0 + mu1), 0.0)
+    # line 8 with M A: d1 = d1 - (M A x - u1)
+    d1 = np.where(obs, st.d1 - (max_ - u1), 0.0)
+    # lines 9-11 unchanged
+    gh, gv = Dh(x), Dv(x)
+    uh, uv = vsoft(gh - st.d2[0], gv - st.d2[1], lam / mu2)
+    d2 = np.stack([st.d2[0] - (gh - uh), st.d2[1] - (gv - uv)])
+    return State(u1, d1, np.stack([uh, uv]), d2, x, st.k + 1, None, xi)
+
+
+def facg_step(st: State, ybar, mask, psf, lam, mu1, mu2, levels=4, otf=None, cg_iters=1) -> State:
+    """One iteration of FA-CG (Sec. IV-C, "Using the Reeves-Sorel technique"):
+    Algorithm 2 with H1 = M A (eq. H_1_analysis_sorel), H2 = P, g1(u) =
+    1/2 ||y - u||^2; line 4 is eq. invAnalysis_sorel applied as eq. reeves3,
+    C = (gamma I + A^T A)^{-1}; line 6 the prox of g1 and eq. soft."""
+    H, W = ybar.shape
+    if otf is None:
+        otf = psf_otf(psf, H, W)
+    gam = mu2 / mu1
+    obs = mask != 0
+    xi_prev = st.xi if st.xi is not None else np.zeros((H, W))
+    zeta1 = np.where(obs, st.u1 + st.d1, 0.0)
+    zeta2 = st.u2 + st.d2
+    r = np.real(idft2(np.conj(otf) * dft2(zeta1))) + gam * haar_synthesis(zeta2, levels)
+    x, xi = reeves_sorel_xstep(r, mask, psf, np.abs(otf) ** 2 + gam, xi_prev, cg_iters, otf)
+    max_ = np.where(obs, np.real(idft2(otf * dft2(x))), 0.0)
+    u1 = np.where(obs, (ybar + mu1 * (max_ - st.d1)) / (1.0 + mu1), 0.0)
+    d1 = np.where(obs, st.d1 - (max_ - u1), 0.0)
+    c = haar_analysis(x, levels)
+    u2 = soft(c - st.d2, lam / mu2)
+    d2 = st.d2 - (c - u2)
+    return State(u1, d1, u2, d2, x, st.k + 1, None, xi)
+
+
 @dataclass
 class SolveResult:
     x: np.ndarray
@@ -418,13 +534,18 @@ def solve(ybar, mask, psf, lam, mu1, mu2, reg="tv", iters=200, stop="iters", tol
     x / of the objective between consecutive iterations is below ``tol``.
     reg: 'tv', 'tv_aniso' (anisotropic TV), 'haar', 'haar_ll_free' (the
     low-low band unpenalised), 'haar_synthesis' (FS-MD: the frame synthesis
-    prior; its objective is evaluated on the coefficients theta)."""
+    prior; its objective is evaluated on the coefficients theta), 'tv_cg',
+    'haar_cg' (the Reeves-Sorel variants TV-CG and FA-CG)."""
     H, W = ybar.shape
-    tv = reg in ("tv", "tv_aniso")
+    tv = reg in ("tv", "tv_aniso", "tv_cg")
     aniso, ll_free, fs = reg == "tv_aniso", reg == "haar_ll_free", reg == "haar_synthesis"
+    cg = reg in ("tv_cg", "haar_cg")
     st = state0.copy() if state0 is not None else State.zeros(H, W, "tv" if tv else "haar", levels)
     otf = psf_otf(psf, H, W)
-    denom = tv_denominator_diag(psf, H, W, mu1, mu2) if tv else None
+    if reg == "tv_cg":
+        denom = tv_denominator_diag(psf, H, W, 1.0, mu2 / mu1)
+    else:
+        denom = tv_denominator_diag(psf, H, W, mu1, mu2) if tv else None
     if fs:
         obj_fn = lambda x: objective_synthesis(st.theta, ybar, mask, psf, lam)  # noqa: E731
     elif tv:
@@ -438,7 +559,11 @@ def solve(ybar, mask, psf, lam, mu1, mu2, reg="tv", iters=200, stop="iters", tol
     n = 0
     for n in range(1, iters + 1):
         x_prev = st.x
-        if tv:
+        if reg == "tv_cg":
+            st = tvcg_step(st, ybar, mask, psf, lam, mu1, mu2, otf, denom)
+        elif reg == "haar_cg":
+            st = facg_step(st, ybar, mask, psf, lam, mu1, mu2, levels, otf)
+        elif tv:
             st = tvmd_step(st, ybar, mask, psf, lam, mu1, mu2, otf, denom, aniso)
         elif fs:
             st = fsmd_step(st, ybar, mask, psf, lam, mu1, mu2, levels, otf)

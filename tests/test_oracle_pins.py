@@ -846,3 +846,123 @@ def test_isnr_hand_computed():
     assert abs(O.isnr(x, ybar, xh2, region) - (20.0 + 10.0 * math.log10(4.0))) < 1e-12
     # SNR = 10 log10(||x||^2 / ||x - x_hat||^2) over the whole image
     assert abs(O.snr(x, x + 0.1 * np.sign(x)) - 10.0 * math.log10(np.sum(x ** 2) / (9 * 0.01))) < 1e-12
+
+
+# ----------------------------------------------------------------------------
+# the Reeves-Sorel variants TV-CG and FA-CG (Sec. IV-B/C/D, eqs. reeves,
+# reeves3 and ReevesTV)
+# ----------------------------------------------------------------------------
+def _cg_inputs(H=8, W=8, seed=61, keep=0.6):
+    g = S.rng(seed)
+    h = _rand_psf(g, 3, 3)
+    mask = (g.uniform(size=(H, W)) < keep).astype(np.uint8)
+    return g, h, mask
+
+
+@pytest.mark.parametrize("reg", ["tv", "haar"])
+def test_reeves_sorel_inverse_dense(reg):
+    """With the inner system solved exactly (CG run to convergence), the
+    x-step equals the dense solve of (A^T M^T M A + gamma D^T D) x = r (TV,
+    eq. ReevesTV) or (A^T M^T M A + gamma I) x = r (frame, eqs.
+    invAnalysis_sorel and reeves3): the Sherman-Morrison-Woodbury identity of
+    eq. reeves, checked against matrices built from the operators' definitions."""
+    H = W = 8
+    g, h, mask = _cg_inputs()
+    gam = 0.07
+    A = _dense_conv_loops(h, H, W)
+    Mm = np.diag(mask.ravel().astype(float))
+    if reg == "tv":
+        Dh = _dense(O.Dh, H, W)
+        Dv = _dense(O.Dv, H, W)
+        Mat = A.T @ Mm @ A + gam * (Dh.T @ Dh + Dv.T @ Dv)
+        denom = O.tv_denominator_diag(h, H, W, 1.0, gam)
+    else:
+        Mat = A.T @ Mm @ A + gam * np.eye(H * W)
+        denom = np.abs(O.psf_otf(h, H, W)) ** 2 + gam
+    r = g.standard_normal((H, W))
+    x_dense = np.linalg.solve(Mat, r.ravel())
+    x, xi = O.reeves_sorel_xstep(r, mask, h, denom, np.zeros((H, W)), cg_iters=400)
+    np.testing.assert_allclose(x.ravel(), x_dense, atol=1e-10)
+    assert np.all(xi[mask != 0] == 0)
+
+
+def test_reeves_sorel_single_cg_step_is_exact_line_minimiser():
+    """One CG iteration from a warm start xi0 on S xi = b (S = B C B^T - I,
+    negative definite) is the exact minimiser of the quadratic
+    1/2 xi^T (-S) xi + b^T xi along the residual direction: with dense B
+    (rows of the convolution matrix at the unobserved pixels) and C, the new
+    residual is orthogonal to the old one, and the error in the (-S) norm
+    drops. Also: x = C r - C B^T xi for the returned xi."""
+    H = W = 8
+    g, h, mask = _cg_inputs(seed=62)
+    gam = 0.11
+    A = _dense_conv_loops(h, H, W)
+    Dh = _dense(O.Dh, H, W)
+    Dv = _dense(O.Dv, H, W)
+    C = np.linalg.inv(A.T @ A + gam * (Dh.T @ Dh + Dv.T @ Dv))
+    U = np.flatnonzero(mask.ravel() == 0)
+    B = A[U]
+    S_ = B @ C @ B.T - np.eye(len(U))
+    r = g.standard_normal((H, W))
+    b = B @ C @ r.ravel()
+    xi0 = np.zeros((H, W))
+    xi0.ravel()[U] = g.standard_normal(len(U))
+    denom = O.tv_denominator_diag(h, H, W, 1.0, gam)
+    x, xi = O.reeves_sorel_xstep(r, mask, h, denom, xi0, cg_iters=1)
+    res0 = b - S_ @ xi0.ravel()[U]
+    res1 = b - S_ @ xi.ravel()[U]
+    assert abs(res0 @ res1) <= 1e-10 * (res0 @ res0)
+    xs = np.linalg.solve(S_, b)
+    e0, e1 = xi0.ravel()[U] - xs, xi.ravel()[U] - xs
+    assert -(e1 @ S_ @ e1) < -(e0 @ S_ @ e0)
+    np.testing.assert_allclose(x.ravel(), C @ r.ravel() - C @ B.T @ xi.ravel()[U], atol=1e-11)
+
+
+def test_tvcg_equals_tvmd_when_everything_is_observed():
+    """With M = I the set of unobserved pixels is empty: B has no rows, the
+    x-step is the plain inverse, and TV-CG's iterates are TV-MD's (Sec. IV-D:
+    the two methods differ only in how they treat M)."""
+    g = S.rng(63)
+    H, W = 16, 12
+    h = S.psf_gaussian(5, 1.0)
+    ybar = g.standard_normal((H, W))
+    mask = np.ones((H, W), dtype=np.uint8)
+    lam, mu1, mu2 = 0.02, 0.5, 0.2
+    a = O.solve(ybar, mask, h, lam, mu1, mu2, "tv", iters=30)
+    b = O.solve(ybar, mask, h, lam, mu1, mu2, "tv_cg", iters=30)
+    np.testing.assert_allclose(b.x, a.x, atol=1e-11)
+    c = O.solve(ybar, mask, h, lam, mu1, mu2, "haar", iters=20)
+    d = O.solve(ybar, mask, h, lam, mu1, mu2, "haar_cg", iters=20)
+    np.testing.assert_allclose(d.x, c.x, atol=1e-11)
+
+
+@pytest.mark.parametrize("reg", ["tv", "haar"])
+def test_cg_variants_reach_the_md_optimum(reg):
+    """TV-CG / FA-CG and TV-MD / FA-MD minimise the same objective (eqs.
+    unconstrained_TV_uBC and unconstrained_analysis_uBC): run to convergence
+    on a 16 x 16 problem with the valid region and missing pixels, they reach
+    the same objective value and the same x."""
+    x, h, ybar, mask = _small_problem(seed=64)
+    lam = 2e-3
+    mu1, mu2 = 0.1, 10 * lam
+    md = O.solve(ybar, mask, h, lam, mu1, mu2, reg, iters=6000, stop="rel_x", tol=1e-12)
+    cg = O.solve(ybar, mask, h, lam, mu1, mu2, reg + "_cg", iters=6000, stop="rel_x", tol=1e-12)
+    np.testing.assert_allclose(cg.objective, md.objective, rtol=1e-7)
+    assert np.linalg.norm(cg.x - md.x) <= 1e-4 * np.linalg.norm(md.x)
+
+
+def test_tvcg_kkt_certificate_at_convergence():
+    """At a fixed point of TV-CG (u1 on the observed pixels only): -mu1 d1 =
+    M A x - y on the observed pixels, mu1 A^T M^T d1 + mu2 D^T d2 = 0, and
+    ||mu2 d2_i|| <= lambda."""
+    x, h, ybar, mask = _small_problem(seed=65)
+    lam = 2e-3
+    mu1, mu2 = 0.1, 10 * lam
+    r = O.solve(ybar, mask, h, lam, mu1, mu2, "tv_cg", iters=8000, stop="rel_x", tol=1e-13)
+    st = r.state
+    obs = mask != 0
+    ax = O.A_direct(r.x, h)
+    np.testing.assert_allclose(-mu1 * st.d1[obs], ax[obs] - ybar[obs], atol=1e-8)
+    stat = mu1 * O.At_direct(np.where(obs, st.d1, 0.0), h) + mu2 * (O.DhT(st.d2[0]) + O.DvT(st.d2[1]))
+    assert np.abs(stat).max() < 1e-8
+    assert np.max(np.hypot(mu2 * st.d2[0], mu2 * st.d2[1])) <= lam * (1 + 1e-8)
