@@ -383,11 +383,11 @@ def uneven_secondary(ad, torch, stream, args, count=UNEVEN_COUNT):
         ys.append(torch.from_numpy(p.ybar.astype(np.float32)).to("cuda"))
         ms.append(torch.from_numpy(p.mask).to("cuda"))
         xs.append(torch.empty((N, N), dtype=torch.float32, device="cuda"))
-    ad.solve_batch(plans, ys, ms, xs, stream)          # warm-up: graphs, attributes
+    ad.solve_batch(plans, ys, ms, xs, stream=stream)          # warm-up: graphs, attributes
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    res = ad.solve_batch(plans, ys, ms, xs, stream)
+    res = ad.solve_batch(plans, ys, ms, xs, stream=stream)
     e1.record(stream)
     torch.cuda.synchronize()
     sec = e0.elapsed_time(e1) * 1e-3
@@ -541,9 +541,9 @@ def run_ours(args):
 
     if args.steady_only:
         fixed = [ad.Plan(H, W, p.psf, p.lam, p.mu1, p.mu2, "tv", max_iters=STEADY_ITERS) for p in probs]
-        ad.solve_batch(fixed, ys, ms, xs, stream)
+        ad.solve_batch(fixed, ys, ms, xs, stream=stream)
         ad.admm_deconv_profile(True)
-        ad.solve_batch(fixed, ys, ms, xs, stream)
+        ad.solve_batch(fixed, ys, ms, xs, stream=stream)
         pf = ad.admm_deconv_profile(False)
         row_b, col_b = bytes_per_pixel_iter()
         its = STEADY_ITERS * len(fixed)
@@ -555,7 +555,7 @@ def run_ours(args):
         return
 
     def step():
-        return ad.solve_batch(plans, ys, ms, xs, stream)
+        return ad.solve_batch(plans, ys, ms, xs, stream=stream)
 
     for _ in range(args.warmup):
         res = step()
@@ -587,13 +587,13 @@ def run_ours(args):
         yh = [torch.from_numpy(p.ybar.astype(np.float32)).pin_memory() for p in probs]
         mh = [torch.from_numpy(p.mask).pin_memory() for p in probs]
         xh = [torch.empty((H, W), dtype=torch.float32).pin_memory() for _ in probs]
-        ad.solve_batch(plans, yh, mh, xh, stream)
+        ad.solve_batch(plans, yh, mh, xh, stream=stream)
         torch.cuda.synchronize()
         barrier()
         t0 = time.perf_counter()
         e2e_iters = 0
         for _ in range(args.steps):
-            r2 = ad.solve_batch(plans, yh, mh, xh, stream)
+            r2 = ad.solve_batch(plans, yh, mh, xh, stream=stream)
             e2e_iters += sum(r.iters for r in r2)
         torch.cuda.synchronize()
         e2e_sec = time.perf_counter() - t0
@@ -635,14 +635,14 @@ def run_ours(args):
     cufft = None
     if rank == 0:
         fixed = [ad.Plan(H, W, p.psf, p.lam, p.mu1, p.mu2, "tv", max_iters=STEADY_ITERS) for p in probs[:32]]
-        ad.solve_batch(fixed, ys[:32], ms[:32], xs[:32], stream)
+        ad.solve_batch(fixed, ys[:32], ms[:32], xs[:32], stream=stream)
         ad.admm_deconv_profile(True)
-        ad.solve_batch(fixed, ys[:32], ms[:32], xs[:32], stream)
+        ad.solve_batch(fixed, ys[:32], ms[:32], xs[:32], stream=stream)
         pf = ad.admm_deconv_profile(False)
         its = STEADY_ITERS * len(fixed)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        ad.solve_batch(fixed, ys[:32], ms[:32], xs[:32], stream)
+        ad.solve_batch(fixed, ys[:32], ms[:32], xs[:32], stream=stream)
         e1.record(stream)
         torch.cuda.synchronize()
         steady = {"problems": len(fixed), "iters": STEADY_ITERS,

@@ -49,10 +49,13 @@ extern "C" {
 #define ADMM_EINVAL              -1  /* bad argument (null, non-odd kernel, mu <= 0, ...) */
 #define ADMM_ENOMEM              -2  /* device or host allocation failed                   */
 #define ADMM_ECUDA               -3  /* a CUDA runtime call failed                         */
-#define ADMM_EUNSUPPORTED_SIZE   -4  /* H or W not in {64,...,2048} powers of two          */
+#define ADMM_EUNSUPPORTED_SIZE   -4  /* H or W not in {64,...,2048} powers of two (with
+                                        fft_pad_policy ADMM_PAD_EXACT), or above 2048      */
 #define ADMM_ENONFINITE          -5  /* an observed value or the iterate is NaN/Inf
                                         (divergence, Theorem 1)                            */
-#define ADMM_ETIMEOUT            -6  /* a bounded device wait expired                      */
+#define ADMM_ETIMEOUT            -6  /* reserved for a bounded device wait that expires. No
+                                        call returns it today: no kernel of the solver waits
+                                        on a flag, a peer or a barrier that could stall     */
 
 /* ---- enums -------------------------------------------------------------- */
 #define ADMM_REG_TV     0   /* isotropic TV, eq. unconstrained_TV_uBC            */
@@ -71,6 +74,19 @@ extern "C" {
                                       duals d2 live on the coefficients theta. No
                                       warm start (admm_deconv_warm_start: EINVAL) */
 
+/* Reeves-Sorel variants (Sec. IV-B/C/D, "Using the Reeves-Sorel technique"):
+   the observation split is u1 = M A x with g1(u1) = 1/2 ||y - u1||^2 on the
+   observed pixels, and the x-step's inverse (A^T M^T M A + gamma D^T D)^{-1}
+   (TV) or (A^T M^T M A + gamma I)^{-1} (frame) is applied as
+   C - C B^T (B C B^T - I)^{-1} B C (eqs. ReevesTV and reeves3), B the rows of
+   A at the unobserved pixels, with one conjugate-gradient iteration per
+   outer iteration warm-started from the previous one. */
+#define ADMM_REG_TV_CG   5  /* TV-CG: the TV prior of eq. unconstrained_TV_uBC    */
+#define ADMM_REG_HAAR_CG 6  /* FA-CG: the frame analysis prior of
+                               eq. unconstrained_analysis_uBC
+                               (both: no admm_deconv_warm_start, EINVAL; their
+                               d1 is zero on unobserved pixels)                   */
+
 #define ADMM_STOP_ITERS   0 /* run exactly max_iters iterations                  */
 #define ADMM_STOP_REL_X   1 /* ||x_k - x_{k-1}|| / ||x_k|| < tol                 */
 #define ADMM_STOP_REL_OBJ 2 /* |f_k - f_{k-1}| / |f_k| < tol (Sec. V's rule)     */
@@ -79,7 +95,8 @@ typedef struct admm_plan_s* admm_plan_t;   /* opaque; owned by the library */
 
 /* Parameters of one problem (one image). */
 typedef struct {
-    int   H, W;            /* full unknown-image domain; powers of two in [64, 2048]        */
+    int   H, W;            /* full unknown-image domain; powers of two in [64, 2048], or
+                              any size in [1, 2048] with fft_pad_policy = ADMM_PAD_NEXT     */
     int   psf_h, psf_w;    /* odd kernel sides, each <= the matching image side             */
     const float* psf;      /* HOST pointer, psf_h x psf_w row-major, centre at
                               (psf_h/2, psf_w/2); copied during admm_deconv_plan; the
@@ -90,7 +107,8 @@ typedef struct {
                               (Sec. V) and mu1 = min(1, 3 mu2) (Sec. V's mu1 rule is
                               garbled; penalties change only the speed, Theorem 1)          */
     int   reg;             /* ADMM_REG_TV, ADMM_REG_HAAR, ADMM_REG_TV_ANISO,
-                              ADMM_REG_HAAR_LL_FREE or ADMM_REG_HAAR_SYNTHESIS              */
+                              ADMM_REG_HAAR_LL_FREE, ADMM_REG_HAAR_SYNTHESIS,
+                              ADMM_REG_TV_CG or ADMM_REG_HAAR_CG                            */
     int   haar_levels;     /* frame levels for the frame priors, 1..4 (0 = 4)              */
     int   stop;            /* ADMM_STOP_*                                                   */
     double tol;            /* tolerance of the stop rule                                    */
@@ -101,7 +119,18 @@ typedef struct {
                               (pixels whose blurred value does not touch the unknown
                               boundary, Sec. IV-A); 1: use the mask exactly as given
                               (e.g. M = I for periodic deconvolution)                        */
+    int   fft_pad_policy;  /* ADMM_PAD_EXACT (0): H and W must be transform sizes the
+                              library supports (powers of two 64..2048), else
+                              ADMM_EUNSUPPORTED_SIZE; ADMM_PAD_NEXT (1): any H, W in
+                              1..2048 -- the plan solves on the next supported size,
+                              the image in its top-left corner and the added rows and
+                              columns never observed (more unknown boundary, Sec. IV-A:
+                              the domain only has to hold the image and the kernel
+                              support); y, mask and x_out keep the caller's H x W      */
 } admm_params_t;
+
+#define ADMM_PAD_EXACT 0
+#define ADMM_PAD_NEXT  1
 
 /* Per-problem outcome, written before a solve call returns. */
 typedef struct {
@@ -156,11 +185,33 @@ ADMM_API int admm_deconv_solve(admm_plan_t plan, const float* y, const uint8_t* 
  * entries with the meaning of admm_deconv_solve; masks may be NULL (then
  * every mask is the valid region) and any masks[i] may be NULL.
  * A plan may appear at most once per call.
+ *   use_warmstart  0: every problem starts as admm_deconv_solve does (or from
+ *                  its pending admm_deconv_warm_start / admm_deconv_set_state);
+ *                  1: every ADMM_REG_TV problem without such a pending start
+ *                  starts from the learned network loaded by
+ *                  admm_warmstart_load (the network predicts x0 and the duals
+ *                  d0 from [M^T y, mask] on the device, then the start of
+ *                  admm_deconv_warm_start is used). Other regularisers start
+ *                  cold. ADMM_EINVAL if no network is loaded.
  * Errors: as admm_deconv_solve; the first failing problem's code is returned.
  */
 ADMM_API int admm_deconv_solve_batch(const admm_plan_t* plans, int count, const float* const* y,
                             const uint8_t* const* masks, float* const* x_out,
-                            admm_result_t* res, void* stream);
+                            admm_result_t* res, int use_warmstart, void* stream);
+
+/*
+ * admm_warmstart_load -- load the learned warm-start network (not in the
+ * paper; see admm_warmstart.h) from a weights file into the library, for
+ * admm_deconv_solve_batch(..., use_warmstart = 1, ...). The file is the
+ * little-endian binary written by `python -m paper_1210_2687_gb300.warmstart
+ * export`: 8 bytes "ADMMCNN1", int32 version (1), int32 reserved, int64
+ * parameter count (admm_cnn_param_count()), float32 scales[4] (s0, s1, s2,
+ * unused), float32 parameters in the layout of admm_cnn_set_params.
+ * The network is created lazily on the device of the first solve that uses
+ * it and grown to the largest image it meets. path = NULL unloads it.
+ * Errors: ADMM_EINVAL (unreadable file, bad header or size), ADMM_ENOMEM.
+ */
+ADMM_API int admm_warmstart_load(const char* path);
 
 /*
  * admm_deconv_state_size -- number of floats of the dual state d = (d1, d2)
@@ -176,6 +227,55 @@ ADMM_API long long admm_deconv_state_size(admm_plan_t plan);
  * Errors: ADMM_EINVAL, ADMM_ECUDA.
  */
 ADMM_API int admm_deconv_get_state(admm_plan_t plan, float* d_out, void* stream);
+
+/*
+ * admm_deconv_domain -- the domain the plan solves on: H x W as given, or the
+ * padded size with fft_pad_policy = ADMM_PAD_NEXT. The state (admm_deconv_
+ * get_state, get_full_state, set_state) and admm_deconv_warm_start's x0 and
+ * d0 live on this domain, the image in its top-left corner.
+ * Errors: ADMM_EINVAL (NULL arguments).
+ */
+ADMM_API int admm_deconv_domain(admm_plan_t plan, int* H, int* W);
+
+/*
+ * admm_deconv_full_state_size -- floats of the complete iteration state that
+ * admm_deconv_get_full_state returns: the duals d (state_size floats), then
+ * the row spectra of the next x-step's right-hand side, Hd x (Wd/2 + 1)
+ * entries of four floats (Re, Im of zeta1's row DFT, Re, Im of w's row DFT;
+ * Hd x Wd the plan's domain), and for ADMM_REG_HAAR_SYNTHESIS also the last
+ * synthesis output w (Hd Wd floats) and zeta2 (3 L + 1 planes); for the
+ * Reeves-Sorel variants also the conjugate-gradient iterate on the
+ * unobserved pixels (Hd Wd floats, zero on observed ones).
+ */
+ADMM_API long long admm_deconv_full_state_size(admm_plan_t plan);
+
+/*
+ * admm_deconv_get_full_state -- copy the complete state left by the last
+ * solve of the plan (device or host, full_state_size floats) and, if `iters`
+ * is not NULL, the number of iterations that solve ran. Algorithm 2 carries
+ * (u_k, d_k) from one iteration to the next; this library keeps d_k and, in
+ * place of u_k, what the next x-step reads of zeta_k = u_k + d_k (the row
+ * spectra of its right-hand side), so a solve started from this state with
+ * admm_deconv_set_state continues the same iterate sequence bit for bit.
+ * Errors: ADMM_EINVAL, ADMM_ECUDA.
+ */
+ADMM_API int admm_deconv_get_full_state(admm_plan_t plan, float* state, int* iters, void* stream);
+
+/*
+ * admm_deconv_set_state -- make the next solve of the plan resume from a
+ * state returned by admm_deconv_get_full_state (checkpoint / restart). The
+ * next solve's first iteration is iteration k + 1 of the solve that produced
+ * the state; its iterates (x, d) are bit-identical to those of one
+ * uninterrupted solve. The stop rules restart their memory: the relative
+ * changes are first evaluated at the second iteration after the restart,
+ * and `iters` of the result counts from the restart. The state is consumed
+ * by the next solve, like a warm start; it must come from a plan with the
+ * same domain and regulariser (other parameters may differ, which then
+ * changes the iteration from the restart on). Returns after the copies have
+ * completed on `stream`, so `state` may be released then.
+ * Errors: ADMM_EINVAL (NULL arguments, a plan made on another device), ADMM_ECUDA.
+ */
+ADMM_API int admm_deconv_set_state(admm_plan_t plan, const float* state, void* stream);
 
 /*
  * admm_deconv_warm_start -- make the next solve of `plan` (admm_deconv_solve
@@ -201,6 +301,11 @@ ADMM_API int admm_deconv_warm_start(admm_plan_t plan, const float* x0, const flo
                                   iterate at once in admm_deconv_solve_batch; the rest
                                   wait in a queue and start as problems retire.
                                   0 (default): chosen from the launch size            */
+#define ADMM_OPT_FAIL_ALLOC 2  /* fault injection on the host, for testing the
+                                  ADMM_ENOMEM paths: value n > 0 makes the n-th
+                                  device or pinned-host allocation the library
+                                  attempts from now on fail as if memory were
+                                  exhausted (once); 0 (default) disarms it        */
 
 /*
  * admm_deconv_set_option -- set a library-wide option (see ADMM_OPT_*).
@@ -345,11 +450,18 @@ ADMM_API int admm_deconv_autotune(int H, int W, int reg, int haar_levels, int pr
  *   mask   [in]  H x W uint8, DEVICE memory, or NULL (valid region only)
  *   x_out  [out] H x W float32, DEVICE memory
  *   res    [out] host pointer, may be NULL
- * The first call on each device resolves the array's device address on that
- * device (set-up); make that first call before any stream capture. Every call
- * shares the array and clears what must start at zero; calls whose device
- * work overlaps (e.g. on two streams) race on it. Returns after the solve has
- * finished on `stream`.
+ * Every call resolves the array's device address on the current device with
+ * that device current and rewrites the array's constant part (the twiddle
+ * table), so it stays correct after a cudaDeviceReset. Under lazy module
+ * loading (the CUDA default) the first call on a device loads the library's
+ * device code there and with it the array: that first call may allocate, so
+ * callers that must never allocate make one call during their initialisation.
+ * Every call shares the array and clears what must start at zero; calls whose
+ * device work overlaps (e.g. on two streams) race on it. The call holds the
+ * library's lock for the whole solve, so other threads' library calls wait
+ * meanwhile, and it synchronises `stream` (also when it fails after queueing
+ * work), so it cannot be called while `stream` is being captured into a CUDA
+ * graph. Returns after the solve has finished on `stream`.
  * Errors: ADMM_EINVAL (also for host pointers or a non-TV regulariser),
  * ADMM_EUNSUPPORTED_SIZE, ADMM_ECUDA, ADMM_ENONFINITE.
  */

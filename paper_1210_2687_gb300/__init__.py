@@ -34,12 +34,17 @@ ADMM_REG_HAAR = 1
 ADMM_REG_TV_ANISO = 2
 ADMM_REG_HAAR_LL_FREE = 3
 ADMM_REG_HAAR_SYNTHESIS = 4
+ADMM_REG_TV_CG = 5
+ADMM_REG_HAAR_CG = 6
+ADMM_PAD_EXACT = 0
+ADMM_PAD_NEXT = 1
 ADMM_STOP_ITERS = 0
 ADMM_STOP_REL_X = 1
 ADMM_STOP_REL_OBJ = 2
 
 _REG = {"tv": ADMM_REG_TV, "haar": ADMM_REG_HAAR, "tv_aniso": ADMM_REG_TV_ANISO,
-        "haar_ll_free": ADMM_REG_HAAR_LL_FREE, "haar_synthesis": ADMM_REG_HAAR_SYNTHESIS}
+        "haar_ll_free": ADMM_REG_HAAR_LL_FREE, "haar_synthesis": ADMM_REG_HAAR_SYNTHESIS,
+        "tv_cg": ADMM_REG_TV_CG, "haar_cg": ADMM_REG_HAAR_CG}
 _STOP = {"iters": ADMM_STOP_ITERS, "rel_x": ADMM_STOP_REL_X, "rel_obj": ADMM_STOP_REL_OBJ}
 
 EXPORTED = ("admm_deconv_plan", "admm_deconv_solve", "admm_deconv_solve_batch",
@@ -50,9 +55,12 @@ EXPORTED = ("admm_deconv_plan", "admm_deconv_solve", "admm_deconv_solve_batch",
             "admm_deconv_variants", "admm_deconv_get_tuning", "admm_deconv_set_tuning", "admm_deconv_autotune",
             "admm_cnn_param_count", "admm_cnn_create", "admm_cnn_set_params", "admm_cnn_get_params",
             "admm_cnn_forward", "admm_cnn_gradients", "admm_cnn_train_step", "admm_cnn_predict_start",
-            "admm_cnn_launches", "admm_cnn_destroy")
+            "admm_cnn_launches", "admm_cnn_destroy",
+            "admm_deconv_domain", "admm_deconv_full_state_size", "admm_deconv_get_full_state",
+            "admm_deconv_set_state", "admm_warmstart_load")
 
 ADMM_OPT_MAX_SLOTS = 1
+ADMM_OPT_FAIL_ALLOC = 2
 
 
 class admm_params_t(ctypes.Structure):
@@ -63,7 +71,7 @@ class admm_params_t(ctypes.Structure):
                 ("reg", ctypes.c_int), ("haar_levels", ctypes.c_int),
                 ("stop", ctypes.c_int), ("tol", ctypes.c_double),
                 ("max_iters", ctypes.c_int), ("check_every", ctypes.c_int),
-                ("raw_mask", ctypes.c_int)]
+                ("raw_mask", ctypes.c_int), ("fft_pad_policy", ctypes.c_int)]
 
 
 class admm_result_t(ctypes.Structure):
@@ -115,8 +123,18 @@ def _load() -> ctypes.CDLL:
     lib.admm_deconv_solve.restype = ctypes.c_int
     lib.admm_deconv_solve_batch.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(vp),
                                             ctypes.POINTER(vp), ctypes.POINTER(vp),
-                                            ctypes.POINTER(admm_result_t), vp]
+                                            ctypes.POINTER(admm_result_t), ctypes.c_int, vp]
     lib.admm_deconv_solve_batch.restype = ctypes.c_int
+    lib.admm_deconv_domain.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+    lib.admm_deconv_domain.restype = ctypes.c_int
+    lib.admm_deconv_full_state_size.argtypes = [vp]
+    lib.admm_deconv_full_state_size.restype = ctypes.c_longlong
+    lib.admm_deconv_get_full_state.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_int), vp]
+    lib.admm_deconv_get_full_state.restype = ctypes.c_int
+    lib.admm_deconv_set_state.argtypes = [vp, vp, vp]
+    lib.admm_deconv_set_state.restype = ctypes.c_int
+    lib.admm_warmstart_load.argtypes = [ctypes.c_char_p]
+    lib.admm_warmstart_load.restype = ctypes.c_int
     lib.admm_deconv_state_size.argtypes = [vp]
     lib.admm_deconv_state_size.restype = ctypes.c_longlong
     lib.admm_deconv_get_state.argtypes = [vp, vp, vp]
@@ -204,14 +222,14 @@ def admm_deconv_solve(plan: int, y_ptr: int, mask_ptr: int | None, x_ptr: int, s
     return res
 
 
-def admm_deconv_solve_batch(plans: Sequence[int], y_ptrs, mask_ptrs, x_ptrs, stream=None):
+def admm_deconv_solve_batch(plans: Sequence[int], y_ptrs, mask_ptrs, x_ptrs, use_warmstart=False, stream=None):
     n = len(plans)
     P = (ctypes.c_void_p * n)(*plans)
     Y = (ctypes.c_void_p * n)(*y_ptrs)
     M = (ctypes.c_void_p * n)(*[m or 0 for m in mask_ptrs]) if mask_ptrs is not None else None
     X = (ctypes.c_void_p * n)(*x_ptrs)
     R = (admm_result_t * n)()
-    rc = lib.admm_deconv_solve_batch(P, n, Y, M, X, R, _stream(stream))
+    rc = lib.admm_deconv_solve_batch(P, n, Y, M, X, R, int(bool(use_warmstart)), _stream(stream))
     if rc != ADMM_OK and rc != ADMM_ENONFINITE:
         raise AdmmError(rc, "admm_deconv_solve_batch")
     return list(R)
@@ -225,6 +243,41 @@ def admm_deconv_get_state(plan: int, out_ptr: int, stream=None) -> None:
     rc = lib.admm_deconv_get_state(ctypes.c_void_p(plan), ctypes.c_void_p(out_ptr), _stream(stream))
     if rc != ADMM_OK:
         raise AdmmError(rc, "admm_deconv_get_state")
+
+
+def admm_deconv_domain(plan: int) -> tuple[int, int]:
+    h, w = ctypes.c_int(), ctypes.c_int()
+    rc = lib.admm_deconv_domain(ctypes.c_void_p(plan), ctypes.byref(h), ctypes.byref(w))
+    if rc != ADMM_OK:
+        raise AdmmError(rc, "admm_deconv_domain")
+    return h.value, w.value
+
+
+def admm_deconv_full_state_size(plan: int) -> int:
+    return int(lib.admm_deconv_full_state_size(ctypes.c_void_p(plan)))
+
+
+def admm_deconv_get_full_state(plan: int, out_ptr: int, stream=None) -> int:
+    """Copy the complete iteration state out; returns the iterations of the last solve."""
+    it = ctypes.c_int()
+    rc = lib.admm_deconv_get_full_state(ctypes.c_void_p(plan), ctypes.c_void_p(out_ptr), ctypes.byref(it),
+                                        _stream(stream))
+    if rc != ADMM_OK:
+        raise AdmmError(rc, "admm_deconv_get_full_state")
+    return it.value
+
+
+def admm_deconv_set_state(plan: int, state_ptr: int, stream=None) -> None:
+    rc = lib.admm_deconv_set_state(ctypes.c_void_p(plan), ctypes.c_void_p(state_ptr), _stream(stream))
+    if rc != ADMM_OK:
+        raise AdmmError(rc, "admm_deconv_set_state")
+
+
+def admm_warmstart_load(path: str | None) -> None:
+    """Load the learned warm-start network from a weights file (None unloads it)."""
+    rc = lib.admm_warmstart_load(None if path is None else os.fsencode(path))
+    if rc != ADMM_OK:
+        raise AdmmError(rc, "admm_warmstart_load")
 
 
 def admm_deconv_warm_start(plan: int, x0_ptr, d0_ptr, stream=None) -> None:
@@ -459,7 +512,7 @@ class Plan:
     """Owns one admm_plan_t. psf: 2-D array with odd sides (host)."""
 
     def __init__(self, H, W, psf, lam, mu1=0.0, mu2=0.0, reg="tv", levels=4, stop="iters",
-                 tol=0.0, max_iters=200, check_every=1, raw_mask=False, stream=None):
+                 tol=0.0, max_iters=200, check_every=1, raw_mask=False, pad=False, stream=None):
         k = np.ascontiguousarray(np.asarray(psf, dtype=np.float32))
         self._psf = k
         p = admm_params_t()
@@ -475,12 +528,29 @@ class Plan:
         p.max_iters = int(max_iters)
         p.check_every = int(check_every)
         p.raw_mask = int(bool(raw_mask))
+        p.fft_pad_policy = ADMM_PAD_NEXT if pad else ADMM_PAD_EXACT
         self.params = p
         self.H, self.W = p.H, p.W
         self.handle = admm_deconv_plan(p, stream)
 
+    def domain(self) -> tuple[int, int]:
+        """The domain the plan solves on (H x W, or the padded size)."""
+        return admm_deconv_domain(self.handle)
+
     def state_size(self) -> int:
         return admm_deconv_state_size(self.handle)
+
+    def full_state_size(self) -> int:
+        return admm_deconv_full_state_size(self.handle)
+
+    def get_full_state(self, out, stream=None) -> int:
+        """Copy the complete state (full_state_size float32) into `out`;
+        returns the iterations of the last solve."""
+        return admm_deconv_get_full_state(self.handle, _ptr(out, np.float32), stream)
+
+    def set_state(self, state, stream=None) -> None:
+        """Resume the next solve from a state of get_full_state."""
+        admm_deconv_set_state(self.handle, _ptr(state, np.float32), stream)
 
     def warm_start(self, x0=None, d0=None, stream=None) -> None:
         """Start the next solve from x0 (H x W) and duals d0 (state_size
@@ -505,7 +575,7 @@ def solve(plan: Plan, y, mask, x_out, stream=None) -> admm_result_t:
                              stream)
 
 
-def solve_batch(plans: Sequence[Plan], ys, masks, x_outs, stream=None):
+def solve_batch(plans: Sequence[Plan], ys, masks, x_outs, use_warmstart=False, stream=None):
     return admm_deconv_solve_batch([p.handle for p in plans], [_ptr(y, np.float32) for y in ys],
                                    None if masks is None else [_ptr(m, np.uint8) for m in masks],
-                                   [_ptr(x, np.float32) for x in x_outs], stream)
+                                   [_ptr(x, np.float32) for x in x_outs], use_warmstart, stream)

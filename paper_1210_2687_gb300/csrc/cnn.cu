@@ -30,12 +30,17 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <cstdio>
 #include <cstring>
 #include <mutex>
 #include <new>
 #include <vector>
 
 #include "../../include/admm_warmstart.h"
+
+namespace admm {
+bool alloc_fault_fire();   // ADMM_OPT_FAIL_ALLOC (engine.cu)
+}
 
 namespace {
 
@@ -485,6 +490,7 @@ namespace {
 template <typename T>
 int dalloc(admm_cnn_s* n, T** p, size_t count) {
     void* q = nullptr;
+    if (admm::alloc_fault_fire()) return ADMM_ENOMEM;
     if (cudaMalloc(&q, count * sizeof(T)) != cudaSuccess) {
         cudaGetLastError();
         return ADMM_ENOMEM;
@@ -619,7 +625,10 @@ int admm_cnn_create(admm_cnn_t* out, long long max_pixels, int training) {
             (rc = dalloc(n, &n->gbuf[0], px * kWidth)) || (rc = dalloc(n, &n->gbuf[1], px * kWidth)) ||
             (rc = dalloc(n, &n->gout, px * 16)) || (rc = dalloc(n, &n->loss, 1)))
             return bail(rc);
-        if (cudaHostAlloc(&n->h_loss, sizeof(double), cudaHostAllocDefault) != cudaSuccess) return bail(ADMM_ENOMEM);
+        if (admm::alloc_fault_fire() || cudaHostAlloc(&n->h_loss, sizeof(double), cudaHostAllocDefault) != cudaSuccess) {
+            n->h_loss = nullptr;
+            return bail(ADMM_ENOMEM);
+        }
     }
     if (cudaMemset(n->params, 0, P * sizeof(float)) != cudaSuccess) return bail(ADMM_ECUDA);
     if (pack_all(n, nullptr) != ADMM_OK || cudaDeviceSynchronize() != cudaSuccess) return bail(ADMM_ECUDA);
@@ -721,4 +730,94 @@ int admm_cnn_predict_start(admm_cnn_t net, int count, int H, int W, const float*
     return ADMM_OK;
 }
 
+// ---------------------------------------------------------------------------
+// The library-global warm-start network of admm_warmstart_load, used by
+// admm_deconv_solve_batch(..., use_warmstart = 1, ...): parameters and scales
+// on the host; the inference network is created on first use on the current
+// device and grown to the largest image it meets.
+// ---------------------------------------------------------------------------
+namespace {
+struct WarmStartNet {
+    bool loaded = false;
+    std::vector<float> params;
+    float scales[4] = {0.f, 0.f, 0.f, 0.f};
+    admm_cnn_t net = nullptr;
+    int device = -1;
+    long long cap = 0;
+};
+std::mutex g_ws_mutex;
+WarmStartNet g_ws;
+}  // namespace
+
+int admm_warmstart_load(const char* path) {
+    std::lock_guard<std::mutex> lk(g_ws_mutex);
+    if (!path) {
+        if (g_ws.net) admm_cnn_destroy(g_ws.net);
+        g_ws = WarmStartNet();
+        return ADMM_OK;
+    }
+    FILE* f = std::fopen(path, "rb");
+    if (!f) return ADMM_EINVAL;
+    char magic[8];
+    int32_t version = 0, reserved = 0;
+    int64_t count = 0;
+    float scales[4];
+    bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, "ADMMCNN1", 8) == 0 &&
+              std::fread(&version, sizeof(version), 1, f) == 1 && version == 1 &&
+              std::fread(&reserved, sizeof(reserved), 1, f) == 1 &&
+              std::fread(&count, sizeof(count), 1, f) == 1 && count == param_count() &&
+              std::fread(scales, sizeof(float), 4, f) == 4;
+    std::vector<float> params;
+    if (ok) {
+        params.resize((size_t)count);
+        ok = std::fread(params.data(), sizeof(float), params.size(), f) == params.size();
+        char extra;
+        ok = ok && std::fread(&extra, 1, 1, f) == 0;   // nothing after the parameters
+    }
+    std::fclose(f);
+    if (!ok) return ADMM_EINVAL;
+    for (float v : params)
+        if (!std::isfinite(v)) return ADMM_EINVAL;
+    if (g_ws.net) admm_cnn_destroy(g_ws.net);
+    g_ws = WarmStartNet();
+    g_ws.params.swap(params);
+    std::memcpy(g_ws.scales, scales, sizeof(scales));
+    g_ws.loaded = true;
+    return ADMM_OK;
+}
+
 }  // extern "C"
+
+namespace admm {
+bool ws_loaded() {
+    std::lock_guard<std::mutex> lk(g_ws_mutex);
+    return g_ws.loaded;
+}
+
+// predicted start of one H x W TV problem: x0 (H W floats) and d0 (3 H W
+// floats in the layout of admm_deconv_get_state), device pointers, on `s`
+int ws_predict_start(int H, int W, const float* ybar, const uint8_t* mask, float* x0, float* d0, cudaStream_t s) {
+    std::lock_guard<std::mutex> lk(g_ws_mutex);
+    if (!g_ws.loaded) return ADMM_EINVAL;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return ADMM_ECUDA;
+    const long long px = (long long)H * W;
+    if (!g_ws.net || g_ws.device != dev || g_ws.cap < px) {
+        if (g_ws.net) admm_cnn_destroy(g_ws.net);
+        g_ws.net = nullptr;
+        const long long cap = std::max(px, 512LL * 512LL);
+        admm_cnn_t n = nullptr;
+        int rc = admm_cnn_create(&n, cap, 0);
+        if (rc != ADMM_OK) return rc;
+        rc = admm_cnn_set_params(n, g_ws.params.data());
+        if (rc != ADMM_OK) {
+            admm_cnn_destroy(n);
+            return rc;
+        }
+        g_ws.net = n;
+        g_ws.device = dev;
+        g_ws.cap = cap;
+    }
+    return admm_cnn_predict_start(g_ws.net, 1, H, W, ybar, mask, g_ws.scales, x0, d0, s);
+}
+}  // namespace admm

@@ -26,10 +26,27 @@
 #include "../../include/admm_deconv.h"
 #include "kernels.cuh"
 #include "haar.cuh"
+#include "cg.cuh"
 #include "setup.cuh"
 #include "variants.cuh"
 
 using namespace admm;
+
+namespace admm {
+// the learned warm start of admm_warmstart_load (cnn.cu)
+bool ws_loaded();
+int ws_predict_start(int H, int W, const float* ybar, const uint8_t* mask, float* x0, float* d0, cudaStream_t s);
+
+// ADMM_OPT_FAIL_ALLOC: allocations left before the injected failure (0 = off)
+static std::atomic<long long> g_fail_alloc{0};
+bool alloc_fault_fire() {
+    long long v = g_fail_alloc.load();
+    while (v > 0) {
+        if (g_fail_alloc.compare_exchange_weak(v, v - 1)) return v == 1;
+    }
+    return false;
+}
+}  // namespace admm
 
 struct admm_plan_s {
     admm_params_t p{};
@@ -46,7 +63,9 @@ struct admm_plan_s {
     float* d2 = nullptr;
     float* ybar = nullptr;
     float* xprev = nullptr;
-    float* work = nullptr;      // frame prior: x / zeta1 / w scratch planes
+    float* work = nullptr;      // frame prior and Reeves-Sorel variants: x / zeta1 / w scratch planes
+    float* cg = nullptr;        // Reeves-Sorel variants: x~, A x~, v, A v, s, z planes
+    double* cg_part = nullptr;  // ... and the CG step's partial sums
     uint8_t* mask = nullptr;
     float2* lamT = nullptr;
     float* kT = nullptr;
@@ -57,7 +76,10 @@ struct admm_plan_s {
     float* xstage = nullptr;
     float* psf_dev = nullptr;
     int last_iter = 0;          // iterations of the last solve: d2 lives in buffer last_iter & 1
-    bool warm_pending = false;  // the next solve starts from admm_deconv_warm_start's state
+    int warm_mode = 0;          // the next solve starts from: 0 u0 = d0 = 0; 1 admm_deconv_warm_start's
+                                // (x0, d0); 2 admm_deconv_set_state's state (resume)
+    int Hu = 0, Wu = 0;         // the caller's image size (p.H x p.W is the domain solved on)
+    bool padded = false;        // Hu x Wu sits in the top-left corner of a larger domain
 };
 
 namespace {
@@ -120,9 +142,16 @@ int prof_event(size_t i, cudaStream_t s) {
 
 bool is_pow2_size(int n) { return n >= 64 && n <= 2048 && (n & (n - 1)) == 0; }
 
+// smallest supported transform size >= n (-1 if there is none)
+int next_supported_size(int n) {
+    if (n < 1 || n > 2048) return -1;
+    int m = 64;
+    while (m < n) m <<= 1;
+    return m;
+}
+
 int cuda_fail(cudaError_t e) {
-    (void)e;
-    return ADMM_ECUDA;
+    return e == cudaErrorMemoryAllocation ? ADMM_ENOMEM : ADMM_ECUDA;
 }
 #define CK(call)                                   \
     do {                                           \
@@ -132,28 +161,62 @@ int cuda_fail(cudaError_t e) {
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
+// device and pinned-host allocations of the library go through these, so
+// that ADMM_OPT_FAIL_ALLOC can make one of them fail (host-side fault
+// injection for the ADMM_ENOMEM paths)
+cudaError_t dev_alloc(void** p, size_t bytes) {
+    if (alloc_fault_fire()) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(p, bytes);
+}
+template <typename T> cudaError_t dev_alloc(T** p, size_t bytes) {
+    void* v = nullptr;
+    const cudaError_t e = dev_alloc(&v, bytes);
+    *p = static_cast<T*>(v);
+    return e;
+}
+template <typename T> cudaError_t host_alloc(T** p, size_t bytes) {
+    if (alloc_fault_fire()) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    void* v = nullptr;
+    const cudaError_t e = cudaHostAlloc(&v, bytes, cudaHostAllocDefault);
+    *p = static_cast<T*>(v);
+    return e;
+}
+
 int ensure_ctx(int dev, int count, DeviceCtx** out) {
     DeviceCtx& c = g_ctx[dev];
     if (!c.ready) {
-        std::vector<float2> tw(2048);
-        for (int k = 0; k < 2048; ++k) {
-            // exact reduction: angle = 2 pi k / 2048
-            const double a = 2.0 * M_PI * (double)k / 2048.0;
-            tw[k] = make_float2((float)std::cos(a), (float)(-std::sin(a)));
+        // each resource is created once; a failed attempt resumes where it stopped
+        if (!c.tw) {
+            std::vector<float2> tw(2048);
+            for (int k = 0; k < 2048; ++k) {
+                // exact reduction: angle = 2 pi k / 2048
+                const double a = 2.0 * M_PI * (double)k / 2048.0;
+                tw[k] = make_float2((float)std::cos(a), (float)(-std::sin(a)));
+            }
+            float2* t = nullptr;
+            CK(dev_alloc(&t, 2048 * sizeof(float2)));
+            if (cudaMemcpy(t, tw.data(), 2048 * sizeof(float2), cudaMemcpyHostToDevice) != cudaSuccess) {
+                cudaFree(t);
+                return ADMM_ECUDA;
+            }
+            c.tw = t;
         }
-        CK(cudaMalloc(&c.tw, 2048 * sizeof(float2)));
-        CK(cudaMemcpy(c.tw, tw.data(), 2048 * sizeof(float2), cudaMemcpyHostToDevice));
-
-        CK(cudaEventCreateWithFlags(&c.ev[0], cudaEventDisableTiming));
-        CK(cudaEventCreateWithFlags(&c.ev[1], cudaEventDisableTiming));
+        for (int i = 0; i < 2; ++i)
+            if (!c.ev[i]) CK(cudaEventCreateWithFlags(&c.ev[i], cudaEventDisableTiming));
         for (int b = 0; b < DeviceCtx::kBranches; ++b) {
-            CK(cudaStreamCreateWithFlags(&c.branch[b], cudaStreamNonBlocking));
-            CK(cudaEventCreateWithFlags(&c.join_ev[b], cudaEventDisableTiming));
+            if (!c.branch[b]) CK(cudaStreamCreateWithFlags(&c.branch[b], cudaStreamNonBlocking));
+            if (!c.join_ev[b]) CK(cudaEventCreateWithFlags(&c.join_ev[b], cudaEventDisableTiming));
         }
-        CK(cudaEventCreateWithFlags(&c.fork_ev, cudaEventDisableTiming));
+        if (!c.fork_ev) CK(cudaEventCreateWithFlags(&c.fork_ev, cudaEventDisableTiming));
         c.ready = true;
     }
-    if (count > c.cap) {
+    if (count > c.cap || !c.desc) {
         int cap = std::max(count, 2 * c.cap);
         for (auto& kv : c.graphs) cudaGraphExecDestroy(kv.second);
         c.graphs.clear();
@@ -172,15 +235,17 @@ int ensure_ctx(int dev, int count, DeviceCtx** out) {
         c.n_active = nullptr;
         c.h_active = nullptr;
         c.cap = 0;
-        CK(cudaMalloc(&c.desc, cap * sizeof(ProbDesc)));
-        CK(cudaMalloc(&c.slot_map, cap * sizeof(int)));
-        CK(cudaMalloc(&c.queue, kMaxLanes * cap * sizeof(int)));   // one word per lane
-        CK(cudaMalloc(&c.xptr, cap * sizeof(float*)));
-        CK(cudaMalloc(&c.n_active, cap * sizeof(int)));
-        CK(cudaHostAlloc(&c.h_active, 2 * cap * sizeof(int), cudaHostAllocDefault));
-        CK(cudaHostAlloc(&c.h_ctl, cap * sizeof(ProbCtl), cudaHostAllocDefault));
-        CK(cudaHostAlloc(&c.h_desc, cap * sizeof(ProbDesc), cudaHostAllocDefault));
-        CK(cudaHostAlloc(&c.h_xptr, cap * sizeof(float*), cudaHostAllocDefault));
+        // (on a failure the pointers allocated so far stay set with cap = 0: the
+        // next call frees them and tries again)
+        CK(dev_alloc(&c.desc, cap * sizeof(ProbDesc)));
+        CK(dev_alloc(&c.slot_map, cap * sizeof(int)));
+        CK(dev_alloc(&c.queue, kMaxLanes * cap * sizeof(int)));   // one word per lane
+        CK(dev_alloc(&c.xptr, cap * sizeof(float*)));
+        CK(dev_alloc(&c.n_active, cap * sizeof(int)));
+        CK(host_alloc(&c.h_active, 2 * cap * sizeof(int)));
+        CK(host_alloc(&c.h_ctl, cap * sizeof(ProbCtl)));
+        CK(host_alloc(&c.h_desc, cap * sizeof(ProbDesc)));
+        CK(host_alloc(&c.h_xptr, cap * sizeof(float*)));
         c.cap = cap;
     }
     *out = &c;
@@ -328,12 +393,18 @@ void free_plan(admm_plan_s* pl) {
     delete pl;
 }
 
-// kernel family of a regulariser (the variants share their family's kernels)
+// kernel family of a regulariser: ADMM_REG_TV for the priors whose row side
+// is the TV row phase (isotropic or anisotropic), ADMM_REG_HAAR for those
+// whose row side is a chain of row and tile kernels (the frame priors and the
+// Reeves-Sorel variants); the family picks the tuning entry
 int reg_family(int reg) { return (reg == ADMM_REG_TV || reg == ADMM_REG_TV_ANISO) ? ADMM_REG_TV : ADMM_REG_HAAR; }
 bool reg_known(int reg) {
     return reg == ADMM_REG_TV || reg == ADMM_REG_HAAR || reg == ADMM_REG_TV_ANISO || reg == ADMM_REG_HAAR_LL_FREE ||
-           reg == ADMM_REG_HAAR_SYNTHESIS;
+           reg == ADMM_REG_HAAR_SYNTHESIS || reg == ADMM_REG_TV_CG || reg == ADMM_REG_HAAR_CG;
 }
+bool reg_cg(int reg) { return reg == ADMM_REG_TV_CG || reg == ADMM_REG_HAAR_CG; }
+// the TV prior (its x-step denominator has the difference spectra)
+bool reg_tv_prior(int reg) { return reg == ADMM_REG_TV || reg == ADMM_REG_TV_ANISO || reg == ADMM_REG_TV_CG; }
 
 ProbDesc make_desc(const admm_plan_s* pl) {
     ProbDesc d{};
@@ -348,6 +419,8 @@ ProbDesc make_desc(const admm_plan_s* pl) {
     d.kT = pl->kT;
     d.xprev = pl->xprev;
     d.work = pl->work;
+    d.cg = pl->cg;
+    d.cg_part = pl->cg_part;
     d.partials = pl->partials;
     d.ctl = pl->ctl;
     d.lam = pl->lam;
@@ -361,7 +434,7 @@ ProbDesc make_desc(const admm_plan_s* pl) {
     d.check_every = pl->p.check_every;
     d.n_strips = pl->n_strips;
     d.n_slots = pl->n_slots;
-    d.warm = pl->warm_pending ? 1 : 0;
+    d.warm = pl->warm_mode;
     d.ll_free = pl->p.reg == ADMM_REG_HAAR_LL_FREE ? 1 : 0;
     d.tol = pl->p.tol;
     return d;
@@ -389,7 +462,16 @@ const char* admm_strerror(int code) {
 
 int admm_deconv_plan(admm_plan_t* out, const admm_params_t* p, void* stream) {
     if (!out || !p || !p->psf) return ADMM_EINVAL;
-    if (!is_pow2_size(p->H) || !is_pow2_size(p->W)) return ADMM_EUNSUPPORTED_SIZE;
+    if (p->fft_pad_policy != ADMM_PAD_EXACT && p->fft_pad_policy != ADMM_PAD_NEXT) return ADMM_EINVAL;
+    // the domain solved on: the caller's, or the next supported size (the
+    // added rows and columns are more unknown boundary, Sec. IV-A)
+    int Hd = p->H, Wd = p->W;
+    if (!is_pow2_size(Hd) || !is_pow2_size(Wd)) {
+        if (p->fft_pad_policy != ADMM_PAD_NEXT) return ADMM_EUNSUPPORTED_SIZE;
+        Hd = next_supported_size(p->H);
+        Wd = next_supported_size(p->W);
+        if (Hd < 0 || Wd < 0) return ADMM_EUNSUPPORTED_SIZE;
+    }
     if (p->psf_h < 1 || p->psf_w < 1 || (p->psf_h & 1) == 0 || (p->psf_w & 1) == 0) return ADMM_EINVAL;
     if (p->psf_h > std::min(p->H, kMaxPsfSide) || p->psf_w > std::min(p->W, kMaxPsfSide)) return ADMM_EINVAL;
     if (!(p->lambda >= 0.f) || !std::isfinite(p->lambda)) return ADMM_EINVAL;
@@ -397,8 +479,9 @@ int admm_deconv_plan(admm_plan_t* out, const admm_params_t* p, void* stream) {
     if (p->stop < ADMM_STOP_ITERS || p->stop > ADMM_STOP_REL_OBJ) return ADMM_EINVAL;
     if (p->max_iters <= 0 || p->check_every < 1 || !(p->tol >= 0.0)) return ADMM_EINVAL;
     const int fam = reg_family(p->reg);
-    const int levels = fam == ADMM_REG_HAAR ? (p->haar_levels == 0 ? 4 : p->haar_levels) : 0;
-    if (fam == ADMM_REG_HAAR && (levels < 1 || levels > kMaxHaarLevels)) return ADMM_EINVAL;
+    const bool cg = reg_cg(p->reg), tvp = reg_tv_prior(p->reg);
+    const int levels = tvp ? 0 : (p->haar_levels == 0 ? 4 : p->haar_levels);
+    if (!tvp && (levels < 1 || levels > kMaxHaarLevels)) return ADMM_EINVAL;
     double psum = 0.0;
     for (int i = 0; i < p->psf_h * p->psf_w; ++i) {
         if (!std::isfinite(p->psf[i])) return ADMM_EINVAL;
@@ -415,13 +498,18 @@ int admm_deconv_plan(admm_plan_t* out, const admm_params_t* p, void* stream) {
     if (!pl) return ADMM_ENOMEM;
     pl->p = *p;
     pl->p.psf = nullptr;
+    pl->Hu = p->H;
+    pl->Wu = p->W;
+    pl->p.H = Hd;
+    pl->p.W = Wd;
+    pl->padded = Hd != p->H || Wd != p->W;
     pl->psf.assign(p->psf, p->psf + p->psf_h * p->psf_w);
     pl->lam = p->lambda;
     pl->mu1 = mu1;
     pl->mu2 = mu2;
     pl->levels = levels;
     if (cudaGetDevice(&pl->device) != cudaSuccess) { free_plan(pl); return ADMM_ECUDA; }
-    const int H = p->H, W = p->W;
+    const int H = Hd, W = Wd;
     const size_t n = (size_t)H * W;
     pl->Wc = W / 2 + 1;
     {
@@ -443,14 +531,14 @@ int admm_deconv_plan(admm_plan_t* out, const admm_params_t* p, void* stream) {
         pl->nb = 2;
     } else {
         pl->R = haar_row_strip(W);
-        pl->nb = 3 * levels + 1;
+        pl->nb = tvp ? 2 : 3 * levels + 1;
     }
     if (fam == ADMM_REG_TV) {
         pl->n_strips = H / pl->R;
         pl->n_slots = pl->n_strips;
     } else {
-        // the tile kernel finishes the iteration; it also sums the row kernel's partials
-        pl->n_strips = haar_num_tiles(H, W);
+        // the tile kernel finishes the iteration; it also sums the row kernels' partials
+        pl->n_strips = cg && tvp ? cg_num_tiles(H, W) : haar_num_tiles(H, W);
         pl->n_slots = haar_num_row_ctas(H, W) + pl->n_strips;
     }
 
@@ -464,6 +552,8 @@ int admm_deconv_plan(admm_plan_t* out, const admm_params_t* p, void* stream) {
     const size_t oyb = take(n * sizeof(float));
     const size_t oxp = take(n * sizeof(float));
     const size_t owk = take(fam == ADMM_REG_HAAR ? 3 * n * sizeof(float) : 0);
+    const size_t ocg = take(cg ? 6 * n * sizeof(float) : 0);
+    const size_t ocp = take(cg ? 2 * (size_t)haar_num_row_ctas(H, W) * sizeof(double) : 0);
     const size_t omk = take(n);
     const size_t olm = take((size_t)pl->Wc * H * sizeof(float2));
     const size_t okt = take((size_t)pl->Wc * H * sizeof(float));
@@ -473,8 +563,9 @@ int admm_deconv_plan(admm_plan_t* out, const admm_params_t* p, void* stream) {
     const size_t oms = take(n);
     const size_t oxs = take(n * sizeof(float));
     const size_t ops = take(pl->psf.size() * sizeof(float));
-    if (cudaMalloc(&pl->slab, off) != cudaSuccess) {
+    if (dev_alloc(&pl->slab, off) != cudaSuccess) {
         cudaGetLastError();
+        pl->slab = nullptr;
         free_plan(pl);
         return ADMM_ENOMEM;
     }
@@ -486,6 +577,8 @@ int admm_deconv_plan(admm_plan_t* out, const admm_params_t* p, void* stream) {
     pl->ybar = reinterpret_cast<float*>(b + oyb);
     pl->xprev = reinterpret_cast<float*>(b + oxp);
     pl->work = fam == ADMM_REG_HAAR ? reinterpret_cast<float*>(b + owk) : nullptr;
+    pl->cg = cg ? reinterpret_cast<float*>(b + ocg) : nullptr;
+    pl->cg_part = cg ? reinterpret_cast<double*>(b + ocp) : nullptr;
     pl->mask = reinterpret_cast<uint8_t*>(b + omk);
     pl->lamT = reinterpret_cast<float2*>(b + olm);
     pl->kT = reinterpret_cast<float*>(b + okt);
@@ -503,7 +596,7 @@ int admm_deconv_plan(admm_plan_t* out, const admm_params_t* p, void* stream) {
             cudaSuccess) { rc = ADMM_ECUDA; break; }
         const int tot = H * pl->Wc;
         spectra_kernel<<<(tot + 255) / 256, 256, 0, s>>>(pl->lamT, pl->kT, pl->psf_dev, p->psf_h, p->psf_w, H, W,
-                                                         pl->Wc, fam == ADMM_REG_TV ? 0 : 1,
+                                                         pl->Wc, tvp ? 0 : 1,
                                                          (double)mu2 / (double)mu1);
         if (cudaGetLastError() != cudaSuccess) { rc = ADMM_ECUDA; break; }
         if (cudaStreamSynchronize(s) != cudaSuccess) { rc = ADMM_ECUDA; break; }
@@ -542,7 +635,9 @@ int admm_deconv_get_state(admm_plan_t plan, float* d_out, void* stream) {
 
 int admm_deconv_warm_start(admm_plan_t plan, const float* x0, const float* d0, void* stream) {
     if (!plan) return ADMM_EINVAL;
-    if (plan->p.reg == ADMM_REG_HAAR_SYNTHESIS) return ADMM_EINVAL;   // starts live on theta, not x
+    // FS-MD's starts live on theta, not x; the Reeves-Sorel variants' u1 lives
+    // on the observed pixels only
+    if (plan->p.reg == ADMM_REG_HAAR_SYNTHESIS || reg_cg(plan->p.reg)) return ADMM_EINVAL;
     std::lock_guard<std::mutex> lk(g_mutex);
     int dev = 0;
     CK(cudaGetDevice(&dev));
@@ -573,7 +668,120 @@ int admm_deconv_warm_start(admm_plan_t plan, const float* x0, const float* d0, v
         CK(cudaMemsetAsync(plan->d2, 0, (size_t)plan->nb * n * sizeof(float), s));
     }
     CK(cudaStreamSynchronize(s));       // host sources may be released on return
-    plan->warm_pending = true;
+    plan->warm_mode = 1;
+    return ADMM_OK;
+}
+
+int admm_deconv_domain(admm_plan_t plan, int* H, int* W) {
+    if (!plan || !H || !W) return ADMM_EINVAL;
+    *H = plan->p.H;
+    *W = plan->p.W;
+    return ADMM_OK;
+}
+
+// Layout of the complete state (admm_deconv_get_full_state): d1, d2, the row
+// spectra of the next x-step's right-hand side (Hd x Wc float4, the stored
+// half spectrum without the column padding), then for FS-MD the last w and
+// zeta2.
+static size_t full_state_floats(const admm_plan_s* pl, size_t* spec_off, size_t* extra_off) {
+    const size_t n = (size_t)pl->p.H * pl->p.W;
+    const size_t d = (size_t)(1 + pl->nb) * n;
+    const size_t spec = (size_t)pl->p.H * pl->Wc * 4;
+    size_t extra = 0;
+    if (pl->p.reg == ADMM_REG_HAAR_SYNTHESIS) extra = (size_t)(1 + pl->nb) * n;
+    if (reg_cg(pl->p.reg)) extra = n;                   // the CG iterate z
+    if (spec_off) *spec_off = d;
+    if (extra_off) *extra_off = d + spec;
+    return d + spec + extra;
+}
+
+long long admm_deconv_full_state_size(admm_plan_t plan) {
+    if (!plan) return -1;
+    return (long long)full_state_floats(plan, nullptr, nullptr);
+}
+
+int admm_deconv_get_full_state(admm_plan_t plan, float* state, int* iters, void* stream) {
+    if (!plan || !state) return ADMM_EINVAL;
+    std::lock_guard<std::mutex> lk(g_mutex);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int H = plan->p.H;
+    const size_t n = (size_t)H * plan->p.W;
+    size_t spec_off = 0, extra_off = 0;
+    full_state_floats(plan, &spec_off, &extra_off);
+    const int K = plan->last_iter;
+    if (plan->fam != ADMM_REG_TV && K > 0) {
+        // The frame prior's iteration ends with the synthesis and the forward
+        // row DFTs, which the last iteration skipped: the problem had retired
+        // when they ran. Run them now for this plan alone (they read zeta2 and
+        // zeta1 of iteration K, still in place), marking it active meanwhile.
+        int dev = 0;
+        CK(cudaGetDevice(&dev));
+        if (plan->device != dev) return ADMM_EINVAL;
+        DeviceCtx* ctx = nullptr;
+        int rc = ensure_ctx(dev, 1, &ctx);
+        if (rc != ADMM_OK) return rc;
+        // the batch tables are borrowed: every solve uploads them afresh
+        ctx->h_desc[0] = make_desc(plan);
+        ctx->h_active[0] = 0;   // slot 0 -> problem 0
+        static const int one = 1, zero = 0;
+        CK(cudaMemcpyAsync(ctx->desc, ctx->h_desc, sizeof(ProbDesc), cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(ctx->slot_map, ctx->h_active, sizeof(int), cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(&plan->ctl->active, &one, sizeof(int), cudaMemcpyHostToDevice, s));
+        const SlotTable sl{ctx->slot_map, ctx->queue, 1};
+        CK(launch_row_tail(plan->p.W, H, plan->Wp, ctx->desc, sl, 1, plan->levels,
+                           plan->p.reg != ADMM_REG_TV_CG, ctx->tw, s));
+        g_launches += 2;
+        CK(cudaMemcpyAsync(&plan->ctl->active, &zero, sizeof(int), cudaMemcpyHostToDevice, s));
+        CK(cudaStreamSynchronize(s));
+    }
+    CK(cudaMemcpyAsync(state, plan->d1, n * sizeof(float), cudaMemcpyDefault, s));
+    // the duals of iteration K live in buffer K & 1
+    const float* d2 = plan->d2 + (size_t)(K & 1) * plan->nb * n;
+    CK(cudaMemcpyAsync(state + n, d2, (size_t)plan->nb * n * sizeof(float), cudaMemcpyDefault, s));
+    CK(cudaMemcpy2DAsync(state + spec_off, (size_t)plan->Wc * sizeof(float4), plan->Sb,
+                         (size_t)plan->Wp * sizeof(float4), (size_t)plan->Wc * sizeof(float4), (size_t)H,
+                         cudaMemcpyDefault, s));
+    if (plan->p.reg == ADMM_REG_HAAR_SYNTHESIS) {
+        // FS-MD's next iteration also reads the last w and zeta2 (left in the
+        // d2 buffer the next iteration writes)
+        CK(cudaMemcpyAsync(state + extra_off, plan->work + 2 * n, n * sizeof(float), cudaMemcpyDefault, s));
+        const float* z2 = plan->d2 + (size_t)((K + 1) & 1) * plan->nb * n;
+        CK(cudaMemcpyAsync(state + extra_off + n, z2, (size_t)plan->nb * n * sizeof(float), cudaMemcpyDefault, s));
+    }
+    if (reg_cg(plan->p.reg))
+        CK(cudaMemcpyAsync(state + extra_off, plan->cg + 5 * n, n * sizeof(float), cudaMemcpyDefault, s));
+    CK(cudaStreamSynchronize(s));
+    if (iters) *iters = K;
+    return ADMM_OK;
+}
+
+int admm_deconv_set_state(admm_plan_t plan, const float* state, void* stream) {
+    if (!plan || !state) return ADMM_EINVAL;
+    std::lock_guard<std::mutex> lk(g_mutex);
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    if (plan->device != dev) return ADMM_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int H = plan->p.H;
+    const size_t n = (size_t)H * plan->p.W;
+    size_t spec_off = 0, extra_off = 0;
+    full_state_floats(plan, &spec_off, &extra_off);
+    // the restarted solve's iteration 1 reads d2 buffer (1 + 1) & 1 = 0 and
+    // (FS-MD) the previous zeta2 from buffer 1
+    CK(cudaMemcpyAsync(plan->d1, state, n * sizeof(float), cudaMemcpyDefault, s));
+    CK(cudaMemcpyAsync(plan->d2, state + n, (size_t)plan->nb * n * sizeof(float), cudaMemcpyDefault, s));
+    CK(cudaMemcpy2DAsync(plan->Sb, (size_t)plan->Wp * sizeof(float4), state + spec_off,
+                         (size_t)plan->Wc * sizeof(float4), (size_t)plan->Wc * sizeof(float4), (size_t)H,
+                         cudaMemcpyDefault, s));
+    if (plan->p.reg == ADMM_REG_HAAR_SYNTHESIS) {
+        CK(cudaMemcpyAsync(plan->work + 2 * n, state + extra_off, n * sizeof(float), cudaMemcpyDefault, s));
+        CK(cudaMemcpyAsync(plan->d2 + (size_t)plan->nb * n, state + extra_off + n, (size_t)plan->nb * n * sizeof(float),
+                           cudaMemcpyDefault, s));
+    }
+    if (reg_cg(plan->p.reg))
+        CK(cudaMemcpyAsync(plan->cg + 5 * n, state + extra_off, n * sizeof(float), cudaMemcpyDefault, s));
+    CK(cudaStreamSynchronize(s));       // host sources may be released on return
+    plan->warm_mode = 2;
     return ADMM_OK;
 }
 
@@ -582,7 +790,8 @@ int admm_deconv_warm_start(admm_plan_t plan, const float* x0, const float* d0, v
 // uses queue word qbase + l).
 struct GroupRun {
     int H = 0, W = 0, Wc = 0, Wp = 0, levels = 0;
-    bool tv = true;
+    bool tv = true;              // the TV row phase (TV, anisotropic TV)
+    bool cg = false;             // a Reeves-Sorel variant
     int off = 0, count = 0, nslots = 0, max_iters = 0, qbase = 0;
     int gi = 0;                  // index of the class's n_active counter
     int R = 0, row_v = 0, col_v = 0, slot_ctas = 0, lanes = 0;
@@ -602,12 +811,21 @@ static SlotTable lane_slots(DeviceCtx* ctx, const GroupRun& g, int l) {
 static cudaError_t launch_iteration(DeviceCtx* ctx, const GroupRun& g, int l, cudaStream_t s) {
     const ProbDesc* desc = ctx->desc + g.L.off[l];
     const SlotTable sl = lane_slots(ctx, g, l);
+    if (g.cg)
+        return launch_cg_iteration(g.W, g.H, g.Wc, g.Wp, desc, sl, g.L.slots[l], g.levels, g.reg == ADMM_REG_TV_CG,
+                                   g.col_fn, ctx->tw, ctx->n_active + g.gi, s);
     cudaError_t e = g.col_fn(desc, sl, g.L.slots[l], g.Wc, g.Wp, ctx->tw, s);
     if (e != cudaSuccess) return e;
     int* nact = ctx->n_active + g.gi;
     if (g.tv) return g.row_fn(desc, sl, g.L.slots[l], g.H, g.Wp, ctx->tw, nact, s);
     return launch_haar_iteration_rows(g.W, g.H, g.Wp, desc, sl, g.L.slots[l], g.levels,
                                       g.reg == ADMM_REG_HAAR_SYNTHESIS, ctx->tw, nact, s);
+}
+
+// kernels one iteration of a lane launches
+static int launches_per_iteration(const GroupRun& g) {
+    if (g.cg) return g.reg == ADMM_REG_TV_CG ? 7 : 8;
+    return g.tv ? 2 : 5;
 }
 
 static std::string graph_key(const std::vector<GroupRun>& groups, int chunk) {
@@ -684,25 +902,25 @@ static cudaError_t chunk_graph(DeviceCtx* ctx, const std::vector<GroupRun>& grou
 // (their lanes are independent branches of one replayed graph).
 static int solve_all_impl(DeviceCtx* ctx, const std::vector<std::vector<int>>& classes, const admm_plan_t* plans,
                           const float* const* y, const uint8_t* const* masks, float* const* x_out,
-                          admm_result_t* res, cudaStream_t s);
+                          admm_result_t* res, int use_ws, cudaStream_t s);
 
 // the iteration kernels of a batch go out as a launch chain (programmatic
 // dependent launch) unless switched off with admm_deconv_set_launch_overlap
 static std::atomic<int> g_overlap{1};
 static int solve_all(DeviceCtx* ctx, const std::vector<std::vector<int>>& classes, const admm_plan_t* plans,
                      const float* const* y, const uint8_t* const* masks, float* const* x_out,
-                     admm_result_t* res, cudaStream_t s) {
+                     admm_result_t* res, int use_ws, cudaStream_t s) {
     struct Guard {
         bool prev;
         ~Guard() { t_chain_overlap = prev; }
     } guard{t_chain_overlap};
     t_chain_overlap = g_overlap.load() != 0;
-    return solve_all_impl(ctx, classes, plans, y, masks, x_out, res, s);
+    return solve_all_impl(ctx, classes, plans, y, masks, x_out, res, use_ws, s);
 }
 
 static int solve_all_impl(DeviceCtx* ctx, const std::vector<std::vector<int>>& classes, const admm_plan_t* plans,
                           const float* const* y, const uint8_t* const* masks, float* const* x_out,
-                          admm_result_t* res, cudaStream_t s) {
+                          admm_result_t* res, int use_ws, cudaStream_t s) {
     const bool prof = g_prof.on;
     std::vector<GroupRun> groups;
     std::vector<int> order;                       // table position -> index into plans
@@ -717,6 +935,7 @@ static int solve_all_impl(DeviceCtx* ctx, const std::vector<std::vector<int>>& c
         g.Wp = p0->Wp;
         g.levels = p0->levels;
         g.tv = p0->fam == ADMM_REG_TV;
+        g.cg = reg_cg(p0->p.reg);
         g.reg = p0->p.reg;
         g.R = p0->R;
         g.row_v = p0->row_v;
@@ -742,23 +961,39 @@ static int solve_all_impl(DeviceCtx* ctx, const std::vector<std::vector<int>>& c
             admm_plan_s* pl = plans[j];
             const float* yj = y[j];
             const uint8_t* mj = masks ? masks[j] : nullptr;
+            const size_t nu = (size_t)pl->Hu * pl->Wu;   // the caller's image (<= n)
             if (!is_device_ptr(yj)) {
-                CK(cudaMemcpyAsync(pl->ystage, yj, n * sizeof(float), cudaMemcpyHostToDevice, s));
+                CK(cudaMemcpyAsync(pl->ystage, yj, nu * sizeof(float), cudaMemcpyHostToDevice, s));
                 yj = pl->ystage;
             }
             if (mj && !is_device_ptr(mj)) {
-                CK(cudaMemcpyAsync(pl->mstage, mj, n, cudaMemcpyHostToDevice, s));
+                CK(cudaMemcpyAsync(pl->mstage, mj, nu, cudaMemcpyHostToDevice, s));
                 mj = pl->mstage;
             }
             CK(cudaMemsetAsync(pl->ctl, 0, sizeof(ProbCtl), s));
             prepare_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(pl->ybar, pl->mask, yj, mj, g.H, g.W,
+                                                                       pl->Hu, pl->Wu,
                                                                        pl->p.psf_h / 2, pl->p.psf_w / 2,
                                                                        pl->p.raw_mask, pl->ctl);
             CK(cudaGetLastError());
             ++g_launches;
+            if (use_ws && pl->warm_mode == 0 && pl->p.reg == ADMM_REG_TV) {
+                // learned start: the network reads [M^T y, mask] just prepared and
+                // writes x0 (to the staging plane) and d0 = (d1, d2 buffer 0),
+                // contiguous in the plan's slab; u0 = H x0 - d0 as in
+                // admm_deconv_warm_start
+                // (d2 follows d1 directly: H W floats are a multiple of the slab's 256-byte alignment)
+                if (pl->d2 != pl->d1 + n) return ADMM_ECUDA;
+                int r = ws_predict_start(g.H, g.W, pl->ybar, pl->mask, pl->xstage, pl->d1, s);
+                if (r != ADMM_OK) return r;
+                CK(launch_warm_rows(g.W, pl->xstage, pl->Sb, g.H, pl->Wp, ctx->tw, s));
+                ++g_launches;
+                pl->warm_mode = 1;
+            }
             const int t = (int)order.size();
             ctx->h_desc[t] = make_desc(pl);
-            x_host.push_back(!is_device_ptr(x_out[j]));
+            // padded plans finalize on their domain and copy the caller's window out
+            x_host.push_back(pl->padded || !is_device_ptr(x_out[j]));
             ctx->h_xptr[t] = x_host.back() ? pl->xstage : x_out[j];
             order.push_back(j);
             g.max_iters = std::max(g.max_iters, pl->p.max_iters);
@@ -827,7 +1062,7 @@ static int solve_all_impl(DeviceCtx* ctx, const std::vector<std::vector<int>>& c
             CK(chunk_graph(ctx, live, chunk, &exec));
             CK(cudaGraphLaunch(exec, s));
             for (GroupRun& g : live) {
-                g_launches += (long long)chunk * g.L.n * (g.tv ? 2 : 5);
+                g_launches += (long long)chunk * g.L.n * launches_per_iteration(g);
                 g.launched += chunk;
             }
         } else {
@@ -838,6 +1073,20 @@ static int solve_all_impl(DeviceCtx* ctx, const std::vector<std::vector<int>>& c
                         const ProbDesc* dl = ctx->desc + g.L.off[l];
                         const SlotTable sl = lane_slots(ctx, g, l);
                         int* nact = ctx->n_active + g.gi;
+                        if (g.cg) {
+                            // (timed as one row-side interval when profiling)
+                            if (prof) {
+                                int r = prof_event(nev++, s);
+                                if (r != ADMM_OK) return r;
+                            }
+                            CK(launch_iteration(ctx, g, l, s));
+                            g_launches += launches_per_iteration(g);
+                            if (prof) {
+                                int r = prof_event(nev++, s);
+                                if (r != ADMM_OK) return r;
+                            }
+                            continue;
+                        }
                         CK(g.col_fn(dl, sl, g.L.slots[l], g.Wc, g.Wp, ctx->tw, s));
                         ++g_launches;
                         if (prof) {
@@ -878,14 +1127,23 @@ static int solve_all_impl(DeviceCtx* ctx, const std::vector<std::vector<int>>& c
         live.swap(next);
     }
     for (const GroupRun& g : groups) {
+        if (g.cg) {
+            // the Reeves-Sorel variants form x = x~ + alpha v on the row side
+            // (the last column-phase output is v): it is in the scratch plane
+            for (int t = g.off; t < g.off + g.count; ++t)
+                CK(cudaMemcpyAsync(ctx->h_xptr[t], plans[order[t]]->work, (size_t)g.H * g.W * sizeof(float),
+                                   cudaMemcpyDeviceToDevice, s));
+            continue;
+        }
         CK(launch_fin(g.W, ctx->desc + g.off, ctx->xptr + g.off, g.count, g.H, g.Wp, ctx->tw, s));
         ++g_launches;
     }
     for (int t = 0; t < total; ++t) {
         admm_plan_s* pl = plans[order[t]];
         if (x_host[t])
-            CK(cudaMemcpyAsync(x_out[order[t]], pl->xstage, (size_t)pl->p.H * pl->p.W * sizeof(float),
-                               cudaMemcpyDeviceToHost, s));
+            CK(cudaMemcpy2DAsync(x_out[order[t]], (size_t)pl->Wu * sizeof(float), pl->xstage,
+                                 (size_t)pl->p.W * sizeof(float), (size_t)pl->Wu * sizeof(float), (size_t)pl->Hu,
+                                 cudaMemcpyDefault, s));
         CK(cudaMemcpyAsync(&ctx->h_ctl[t], pl->ctl, sizeof(ProbCtl), cudaMemcpyDeviceToHost, s));
     }
     CK(cudaStreamSynchronize(s));
@@ -904,7 +1162,7 @@ static int solve_all_impl(DeviceCtx* ctx, const std::vector<std::vector<int>>& c
     for (int t = 0; t < total; ++t) {
         const ProbCtl& c = ctx->h_ctl[t];
         plans[order[t]]->last_iter = c.iter;
-        plans[order[t]]->warm_pending = false;   // a warm start serves one solve
+        plans[order[t]]->warm_mode = 0;          // a warm start or a restored state serves one solve
         if (c.status != 0 && rc == ADMM_OK) rc = c.status;
         if (res) {
             admm_result_t& r = res[order[t]];
@@ -924,8 +1182,11 @@ static int solve_all_impl(DeviceCtx* ctx, const std::vector<std::vector<int>>& c
 }
 
 int admm_deconv_solve_batch(const admm_plan_t* plans, int count, const float* const* y,
-                            const uint8_t* const* masks, float* const* x_out, admm_result_t* res, void* stream) {
+                            const uint8_t* const* masks, float* const* x_out, admm_result_t* res, int use_warmstart,
+                            void* stream) {
     if (count < 0) return ADMM_EINVAL;
+    if (use_warmstart != 0 && use_warmstart != 1) return ADMM_EINVAL;
+    if (use_warmstart && !ws_loaded()) return ADMM_EINVAL;
     if (count == 0) return ADMM_OK;
     if (!plans || !y || !x_out) return ADMM_EINVAL;
     for (int i = 0; i < count; ++i) {
@@ -951,7 +1212,7 @@ int admm_deconv_solve_batch(const admm_plan_t* plans, int count, const float* co
     }
     std::vector<std::vector<int>> classes;
     for (auto& kv : groups) classes.push_back(kv.second);
-    return solve_all(ctx, classes, plans, y, masks, x_out, res, s);
+    return solve_all(ctx, classes, plans, y, masks, x_out, res, use_warmstart, s);
 }
 
 int admm_deconv_set_option(int option, long long value) {
@@ -959,6 +1220,11 @@ int admm_deconv_set_option(int option, long long value) {
     if (option == ADMM_OPT_MAX_SLOTS) {
         if (value < 0 || value > INT32_MAX) return ADMM_EINVAL;
         g_max_slots = (int)value;
+        return ADMM_OK;
+    }
+    if (option == ADMM_OPT_FAIL_ALLOC) {
+        if (value < 0) return ADMM_EINVAL;
+        g_fail_alloc.store(value);
         return ADMM_OK;
     }
     return ADMM_EINVAL;
@@ -1108,8 +1374,8 @@ int admm_deconv_autotune(int H, int W, int reg, int haar_levels, int problems, i
     int count = 0;
     rc = ADMM_OK;
     do {
-        if (cudaMalloc(&dy, n * sizeof(float)) != cudaSuccess ||
-            cudaMalloc(&dx, (size_t)problems * n * sizeof(float)) != cudaSuccess) {
+        if (dev_alloc(&dy, n * sizeof(float)) != cudaSuccess ||
+            dev_alloc(&dx, (size_t)problems * n * sizeof(float)) != cudaSuccess) {
             cudaGetLastError();
             rc = ADMM_ENOMEM;
             break;
@@ -1134,11 +1400,12 @@ int admm_deconv_autotune(int H, int W, int reg, int haar_levels, int problems, i
             for (int i = 0; i < problems && r == ADMM_OK; ++i) r = admm_deconv_plan(&pls[i], &p, stream);
             float ms = 0.f;
             if (r == ADMM_OK)   // warm-up: kernel attributes, graph capture
-                r = admm_deconv_solve_batch(pls.data(), problems, ys.data(), nullptr, xs.data(), nullptr, stream);
+                r = admm_deconv_solve_batch(pls.data(), problems, ys.data(), nullptr, xs.data(), nullptr, 0, stream);
             if (r == ADMM_OK) {
                 if (cudaEventRecord(e0, s) != cudaSuccess) r = ADMM_ECUDA;
                 if (r == ADMM_OK)
-                    r = admm_deconv_solve_batch(pls.data(), problems, ys.data(), nullptr, xs.data(), nullptr, stream);
+                    r = admm_deconv_solve_batch(pls.data(), problems, ys.data(), nullptr, xs.data(), nullptr, 0,
+                                                stream);
                 if (r == ADMM_OK && (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
                                      cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
                     r = ADMM_ECUDA;
@@ -1203,7 +1470,7 @@ int admm_deconv_autotune(int H, int W, int reg, int haar_levels, int problems, i
 int admm_deconv_solve(admm_plan_t plan, const float* y, const uint8_t* mask, float* x_out, admm_result_t* res,
                       void* stream) {
     const uint8_t* m[1] = {mask};
-    return admm_deconv_solve_batch(&plan, 1, &y, m, &x_out, res, stream);
+    return admm_deconv_solve_batch(&plan, 1, &y, m, &x_out, res, 0, stream);
 }
 
 }  // extern "C"
@@ -1222,17 +1489,12 @@ int admm_deconv_solve(admm_plan_t plan, const float* y, const uint8_t* mask, flo
 namespace {
 constexpr int kNoAllocMaxSide = 256;
 constexpr size_t kNoAllocBytes = size_t(4) << 20;   // 4 MiB
-constexpr int kNoAllocMaxDevices = 64;
 }  // namespace
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
 namespace {
-struct NoAllocDevice {
-    bool ready = false;
-    unsigned char* base = nullptr;   // device address of g_noalloc_scratch on this device
-};
-NoAllocDevice g_noalloc_dev[kNoAllocMaxDevices];
+bool g_noalloc_tw_ready = false;
 float2 g_noalloc_tw_host[2048];     // staging for the twiddle upload (static, not heap)
 
 struct NoAllocLayout {
@@ -1270,25 +1532,26 @@ NoAllocLayout noalloc_layout(int H, int W, int psf_elems) {
     return L;
 }
 
-// first call on a device: resolve the array's device address with that device current
-int noalloc_setup(int dev, unsigned char** base) {
-    NoAllocDevice& d = g_noalloc_dev[dev];
-    if (!d.ready) {
-        void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr) {
-            cudaGetLastError();
-            return ADMM_ECUDA;
-        }
+// every call, with the calling device current: resolve the array's device
+// address and rewrite the twiddle table at its start. Nothing is cached per
+// device, so a context torn down in between (cudaDeviceReset, which zeroes
+// the array) is set up again; both steps are cheap next to a solve.
+int noalloc_setup(unsigned char** base, cudaStream_t s) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr) {
+        cudaGetLastError();
+        return ADMM_ECUDA;
+    }
+    if (!g_noalloc_tw_ready) {
         for (int k = 0; k < 2048; ++k) {
             const double a = 2.0 * M_PI * (double)k / 2048.0;
             g_noalloc_tw_host[k] = make_float2((float)std::cos(a), (float)(-std::sin(a)));
         }
-        if (cudaMemcpy(p, g_noalloc_tw_host, sizeof(g_noalloc_tw_host), cudaMemcpyHostToDevice) != cudaSuccess)
-            return ADMM_ECUDA;
-        d.base = static_cast<unsigned char*>(p);
-        d.ready = true;
+        g_noalloc_tw_ready = true;
     }
-    *base = d.base;
+    if (cudaMemcpyAsync(p, g_noalloc_tw_host, sizeof(g_noalloc_tw_host), cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return ADMM_ECUDA;
+    *base = static_cast<unsigned char*>(p);
     return ADMM_OK;
 }
 }  // namespace
@@ -1317,17 +1580,32 @@ extern "C" int admm_deconv_solve_noalloc(const admm_params_t* p, const float* y,
     if (!is_device_ptr(y) || !is_device_ptr(x_out) || (mask && !is_device_ptr(mask))) return ADMM_EINVAL;
 
     std::lock_guard<std::mutex> lk(g_mutex);
-    int dev = 0;
-    CK(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= kNoAllocMaxDevices) return ADMM_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // From the first queued operation on, a failing call waits for the work it
+    // has queued before it returns: kernels still in flight would otherwise
+    // write the shared array while the next call clears and reuses it.
+#define CKQ(call)                                       \
+    do {                                                \
+        cudaError_t e_ = (call);                        \
+        if (e_ != cudaSuccess) {                        \
+            cudaStreamSynchronize(s);                   \
+            cudaGetLastError();                         \
+            return cuda_fail(e_);                       \
+        }                                               \
+    } while (0)
     unsigned char* base = nullptr;
-    int rc = noalloc_setup(dev, &base);
-    if (rc != ADMM_OK) return rc;
+    int rc = noalloc_setup(&base, s);
+    if (rc != ADMM_OK) {
+        cudaStreamSynchronize(s);
+        return rc;
+    }
     const int H = p->H, W = p->W;
     const size_t n = (size_t)H * W;
     const NoAllocLayout L = noalloc_layout(H, W, p->psf_h * p->psf_w);
-    if (L.end > kNoAllocBytes) return ADMM_EUNSUPPORTED_SIZE;
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (L.end > kNoAllocBytes) {
+        cudaStreamSynchronize(s);
+        return ADMM_EUNSUPPORTED_SIZE;
+    }
     const float2* tw = reinterpret_cast<const float2*>(base + L.tw);
     ProbDesc* desc = reinterpret_cast<ProbDesc*>(base + L.desc);
     float** xptr = reinterpret_cast<float**>(base + L.xptr);
@@ -1340,15 +1618,15 @@ extern "C" int admm_deconv_solve_noalloc(const admm_params_t* p, const float* y,
     uint8_t* mk = reinterpret_cast<uint8_t*>(base + L.mk);
 
     // the array keeps the previous call's contents: clear everything after the twiddles
-    CK(cudaMemsetAsync(base + L.desc, 0, L.end - L.desc, s));
-    CK(cudaMemcpyAsync(psf_dev, p->psf, (size_t)p->psf_h * p->psf_w * sizeof(float), cudaMemcpyHostToDevice, s));
+    CKQ(cudaMemsetAsync(base + L.desc, 0, L.end - L.desc, s));
+    CKQ(cudaMemcpyAsync(psf_dev, p->psf, (size_t)p->psf_h * p->psf_w * sizeof(float), cudaMemcpyHostToDevice, s));
     const int tot = H * L.Wc;
     spectra_kernel<<<(tot + 255) / 256, 256, 0, s>>>(lamT, kT, psf_dev, p->psf_h, p->psf_w, H, W, L.Wc, 0,
                                                      (double)mu2 / (double)mu1);
-    CK(cudaGetLastError());
-    prepare_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(ybar, mk, y, mask, H, W, p->psf_h / 2,
+    CKQ(cudaGetLastError());
+    prepare_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(ybar, mk, y, mask, H, W, H, W, p->psf_h / 2,
                                                                p->psf_w / 2, p->raw_mask, ctl);
-    CK(cudaGetLastError());
+    CKQ(cudaGetLastError());
     ProbDesc d{};
     d.Sa = reinterpret_cast<float4*>(base + L.Sa);
     d.Sb = reinterpret_cast<float4*>(base + L.Sb);
@@ -1375,35 +1653,35 @@ extern "C" int admm_deconv_solve_noalloc(const admm_params_t* p, const float* y,
     d.n_strips = L.n_strips;
     d.tol = p->tol;
     const int one = 1;
-    CK(cudaMemcpyAsync(desc, &d, sizeof(d), cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(xptr, &x_out, sizeof(float*), cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(nact, &one, sizeof(int), cudaMemcpyHostToDevice, s));
+    CKQ(cudaMemcpyAsync(desc, &d, sizeof(d), cudaMemcpyHostToDevice, s));
+    CKQ(cudaMemcpyAsync(xptr, &x_out, sizeof(float*), cudaMemcpyHostToDevice, s));
+    CKQ(cudaMemcpyAsync(nact, &one, sizeof(int), cudaMemcpyHostToDevice, s));
     init_ctl_kernel<<<1, 32, 0, s>>>(desc, 1, nact);
-    CK(cudaGetLastError());
+    CKQ(cudaGetLastError());
     int* slot_words = reinterpret_cast<int*>(base + L.slots);
     const SlotTable sl{slot_words, slot_words + 1, 1};
     assign_slots_kernel<<<1, 32, 0, s>>>(desc, sl, 1);
-    CK(cudaGetLastError());
-    CK(cudaStreamSynchronize(s));   // the host-side sources above are locals
+    CKQ(cudaGetLastError());
+    CKQ(cudaStreamSynchronize(s));   // the host-side sources above are locals
 
     const int chunk = 8;
     int launched = 0;
     while (launched < p->max_iters) {
         const int nit = std::min(chunk, p->max_iters - launched);
         for (int it = 0; it < nit; ++it) {
-            CK(launch_col(H, desc, sl, 1, L.Wc, L.Wp, tw, s));
-            CK(launch_row_tv(W, desc, sl, 1, H, L.Wp, tw, nact, s));
+            CKQ(launch_col(H, desc, sl, 1, L.Wc, L.Wp, tw, s));
+            CKQ(launch_row_tv(W, desc, sl, 1, H, L.Wp, tw, nact, s));
         }
         launched += nit;
         int act = 0;
-        CK(cudaMemcpyAsync(&act, nact, sizeof(int), cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
+        CKQ(cudaMemcpyAsync(&act, nact, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CKQ(cudaStreamSynchronize(s));
         if (act == 0) break;
     }
-    CK(launch_fin(W, desc, xptr, 1, H, L.Wp, tw, s));
+    CKQ(launch_fin(W, desc, xptr, 1, H, L.Wp, tw, s));
     ProbCtl c{};
-    CK(cudaMemcpyAsync(&c, ctl, sizeof(ProbCtl), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
+    CKQ(cudaMemcpyAsync(&c, ctl, sizeof(ProbCtl), cudaMemcpyDeviceToHost, s));
+    CKQ(cudaStreamSynchronize(s));
     if (res) {
         res->iters = c.iter;
         res->converged = c.converged;
@@ -1417,4 +1695,5 @@ extern "C" int admm_deconv_solve_noalloc(const admm_params_t* p, const float* y,
         res->t_done_ms = c.t_done >= c.t0 ? (double)(c.t_done - c.t0) * 1e-6 : 0.0;
     }
     return c.status != 0 ? c.status : ADMM_OK;
+#undef CKQ
 }

@@ -638,7 +638,40 @@ cudaError_t launch_haar_rows_t(int H, int Wp, const ProbDesc* d, SlotTable sl, i
     return launch_chain(haar_row_forward<W>, dim3(nrow / 2, count), dim3(kThreads), smem_fwd, s, d, sl, H, Wp, tw);
 }
 
-inline cudaError_t haar_tile_attributes() {
+// The kernels of an iteration that run after the one that finishes it: for
+// the frame prior the synthesis (w = gamma P^T zeta2) and the forward row
+// DFTs of zeta1 + i w; with synth = false only the forward row DFTs. A
+// problem that retires skips them in its last iteration (it is inactive by
+// then); admm_deconv_get_full_state runs them for it afterwards, so that the
+// saved state holds the right-hand side the next x-step would read.
+template <int W>
+cudaError_t launch_row_tail_t(int H, int Wp, const ProbDesc* d, SlotTable sl, int count, int levels, bool synth,
+                              const float2* tw, cudaStream_t s) {
+    constexpr int FT = W / 8, G = kThreads / FT;
+    const size_t smem_fwd = (size_t)(2 * G * W + W) * sizeof(float2);
+    cudaError_t e = cudaFuncSetAttribute(haar_row_forward<W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem_fwd);
+    if (e != cudaSuccess) return e;
+    if (synth) {
+        const dim3 tgrid(haar_num_tiles(H, W), count);
+        switch (levels) {
+            case 1: haar_synthesis<1><<<tgrid, kThreads, HaarSynCfg<1>::SMEM, s>>>(d, sl, H, W); break;
+            case 2: haar_synthesis<2><<<tgrid, kThreads, HaarSynCfg<2>::SMEM, s>>>(d, sl, H, W); break;
+            case 3: haar_synthesis<3><<<tgrid, kThreads, HaarSynCfg<3>::SMEM, s>>>(d, sl, H, W); break;
+            default: haar_synthesis<4><<<tgrid, kThreads, HaarSynCfg<4>::SMEM, s>>>(d, sl, H, W); break;
+        }
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    haar_row_forward<W><<<dim3(H / G / 2, count), kThreads, smem_fwd, s>>>(d, sl, H, Wp, tw);
+    return cudaGetLastError();
+}
+
+// Each translation unit has its own copy (internal linkage): a kernel
+// launched from two translation units is registered once per unit, and the
+// attribute must be set on the copy that the unit launches. A flag shared
+// across units (an inline function's static) left one unit's copies unset.
+static cudaError_t haar_tile_attributes() {
     static bool done = false;
     if (done) return cudaSuccess;
     cudaError_t e;
@@ -674,8 +707,23 @@ inline cudaError_t haar_tile_attributes() {
     return cudaSuccess;
 }
 
+static inline cudaError_t launch_row_tail(int W, int H, int Wp, const ProbDesc* d, SlotTable sl, int count, int levels,
+                                   bool synth, const float2* tw, cudaStream_t s) {
+    cudaError_t e = haar_tile_attributes();
+    if (e != cudaSuccess) return e;
+    switch (W) {
+        case 64: return launch_row_tail_t<64>(H, Wp, d, sl, count, levels, synth, tw, s);
+        case 128: return launch_row_tail_t<128>(H, Wp, d, sl, count, levels, synth, tw, s);
+        case 256: return launch_row_tail_t<256>(H, Wp, d, sl, count, levels, synth, tw, s);
+        case 512: return launch_row_tail_t<512>(H, Wp, d, sl, count, levels, synth, tw, s);
+        case 1024: return launch_row_tail_t<1024>(H, Wp, d, sl, count, levels, synth, tw, s);
+        case 2048: return launch_row_tail_t<2048>(H, Wp, d, sl, count, levels, synth, tw, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
 // fs: the synthesis formulation (FS-MD) analysis tile
-inline cudaError_t launch_haar_iteration_rows(int W, int H, int Wp, const ProbDesc* d, SlotTable sl, int count,
+static inline cudaError_t launch_haar_iteration_rows(int W, int H, int Wp, const ProbDesc* d, SlotTable sl, int count,
                                               int levels, bool fs, const float2* tw, int* n_active, cudaStream_t s) {
     cudaError_t e = haar_tile_attributes();
     if (e != cudaSuccess) return e;

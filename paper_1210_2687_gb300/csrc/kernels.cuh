@@ -48,6 +48,8 @@ struct ProbCtl {
     double primal_res; // ||d_k - d_{k-1}|| = ||H z_k - u_k|| (Alg. 2), -1 until evaluated
     int input_bad;     // set by prepare_kernel: an observed value is not finite
     int pad_;
+    unsigned cg_arrive;  // Reeves-Sorel variants: row CTAs that have added their share of alpha's denominator
+    float cg_alpha;      // ... and the step of the iteration's conjugate-gradient update
     unsigned long long t0;       // device clock (ns) when the batch was set up
     unsigned long long t_start;  // ... when the problem took a slot
     unsigned long long t_done;   // ... when it retired
@@ -76,7 +78,10 @@ struct ProbDesc {
     const float2* lamT;       // Wc x H, Lambda (column-major half spectrum)
     const float* kT;          // Wc x H, diagonal inverse with 1/(HW) folded in
     float* xprev;             // H x W, x of the previous iteration (rel-x rule)
-    float* work;              // frame prior: 3 x H x W scratch planes (x, zeta1, w)
+    float* work;              // frame prior and Reeves-Sorel variants: 3 x H x W scratch
+                              // planes (x, zeta1, w)
+    float* cg;                // Reeves-Sorel variants: 6 x H x W planes (x~, A x~, v, A v, s, z)
+    double* cg_part;          // ... and 2 x (row CTAs) partial sums of the CG step
     double* partials;         // n_strips x kNumPartials
     ProbCtl* ctl;
     float lam, mu1, mu2, gamma, tau, inv1pmu1;
@@ -84,7 +89,10 @@ struct ProbDesc {
     int n_strips;             // CTAs per problem of the kernel that finishes an iteration
     int n_slots;              // partial-sum slots to reduce (0: n_strips)
     int warm;                 // 1: start from x1 = x0, d0 given (Sb holds the row-DFTs
-                              // of x0, d1/d2 buffer 0 hold d0); 0: u0 = d0 = 0
+                              // of x0, d1/d2 buffer 0 hold d0); 2: resume a saved
+                              // state (Sb holds the row-DFTs of the right-hand side,
+                              // d1/d2 buffer 0 the duals: the first x-step solves as
+                              // usual); 0: u0 = d0 = 0
     int ll_free;              // frame prior: 1 = the last low-low band unpenalised
     double tol;
 };
@@ -270,8 +278,9 @@ col_phase(const ProbDesc* __restrict__ probs, SlotTable sl, int Wc, int Wp, cons
     if (pi < 0) return;
     const ProbDesc& P = probs[pi];
     if (P.ctl->active == 0) return;
-    const bool warm0 = P.ctl->iter == 0;         // (only reached with a warm start)
-    if (warm0 && !P.warm) {
+    const bool it0 = P.ctl->iter == 0;
+    const bool warm0 = it0 && P.warm == 1;       // the first x-step returns x0
+    if (it0 && !P.warm) {
         // first iteration from u0 = d0 = 0: the right-hand side is zero, so x1 = 0
         const int c0 = blockIdx.x * CB;
         for (int e = threadIdx.x; e < H * CB; e += kThreads)
@@ -408,7 +417,7 @@ col_phase_pers(const ProbDesc* __restrict__ probs, SlotTable sl, int Wc, int Wp,
                 Pc->Sa[(size_t)(e / CB) * Wp + c0 + e % CB] = make_float4(0.f, 0.f, 0.f, 0.f);
         } else if (mode == 2) {
             const ProbDesc& P = *Pc;
-            const bool warm0 = P.ctl->iter == 0;
+            const bool warm0 = P.ctl->iter == 0 && P.warm == 1;   // the first x-step returns x0
             float2* bz = reinterpret_cast<float2*>(stage) + (2 * g) * C::SIG;
             float2* bw = reinterpret_cast<float2*>(stage) + (2 * g + 1) * C::SIG;
             const int kc = c0 + g;

@@ -60,18 +60,24 @@ __global__ void spectra_kernel(float2* __restrict__ lamT, float* __restrict__ kT
 // prox_g_1_uBC), stored as ybar with a quiet NaN on unobserved pixels. A
 // non-finite observed value marks the problem (it then retires at once with
 // ADMM_ENONFINITE). ctl must be zeroed before this kernel runs.
+// The caller's image is Hu x Wu (row stride Wu) in the top-left corner of the
+// H x W domain; pixels outside it are never observed (more unknown boundary),
+// and the valid region is that of the caller's image.
 // ---------------------------------------------------------------------------
 __global__ void prepare_kernel(float* __restrict__ ybar, uint8_t* __restrict__ mask_eff,
                                const float* __restrict__ y, const uint8_t* __restrict__ mask_in,
-                               int H, int W, int lr, int lc, int raw_mask, ProbCtl* __restrict__ ctl) {
+                               int H, int W, int Hu, int Wu, int lr, int lc, int raw_mask,
+                               ProbCtl* __restrict__ ctl) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= H * W) return;
     const int r = i / W, c = i % W;
-    bool obs = (mask_in == nullptr) ? true : (mask_in[i] != 0);
+    const bool inside = r < Hu && c < Wu;
+    const size_t iu = (size_t)r * Wu + c;
+    bool obs = inside && ((mask_in == nullptr) ? true : (mask_in[iu] != 0));
     if (!raw_mask || mask_in == nullptr)
-        obs = obs && r >= lr && r < H - lr && c >= lc && c < W - lc;
+        obs = obs && r >= lr && r < Hu - lr && c >= lc && c < Wu - lc;
     mask_eff[i] = obs ? 1 : 0;
-    const float v = obs ? y[i] : 0.0f;
+    const float v = obs ? y[iu] : 0.0f;
     if (obs && !isfinite(v)) atomicOr(&ctl->input_bad, 1);
     ybar[i] = obs ? v : __int_as_float(0x7fc00000);
 }

@@ -9,6 +9,7 @@ so the plain ADMM still decides the result.
 
     python -m paper_1210_2687_gb300.warmstart train        # writes weights/warmstart_tv.npz
     python -m paper_1210_2687_gb300.warmstart eval --weights weights.npz --count 64
+    python -m paper_1210_2687_gb300.warmstart export       # weights/warmstart_tv.bin for admm_warmstart_load
 
 Training problems (256 x 256): an image from the piecewise-constant law
 (20 rectangles / disks) or the textured law with probability 1/2; a kernel
@@ -46,6 +47,7 @@ LAM = 1e-3
 TOL = 1e-5
 MAX_ITERS = 5000
 WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights", "warmstart_tv.npz")
+WEIGHTS_BIN = os.path.splitext(WEIGHTS)[0] + ".bin"
 
 
 def mu():
@@ -224,6 +226,21 @@ def load(path=WEIGHTS):
     return z["params"].astype(np.float32), z["scales"].astype(np.float32), json.loads(str(z["meta"]))
 
 
+def export_binary(params, scales, path=WEIGHTS_BIN):
+    """The weights file of admm_warmstart_load (include/admm_deconv.h): magic
+    "ADMMCNN1", int32 version 1, int32 0, int64 parameter count, float32
+    scales[4], float32 parameters; little-endian."""
+    params = np.ascontiguousarray(params, dtype="<f4")
+    scales = np.ascontiguousarray(np.resize(np.asarray(scales, dtype="<f4"), 4))
+    with open(path, "wb") as f:
+        f.write(b"ADMMCNN1")
+        f.write(np.array([1, 0], dtype="<i4").tobytes())
+        f.write(np.array([params.size], dtype="<i8").tobytes())
+        f.write(scales.tobytes())
+        f.write(params.tobytes())
+    return path
+
+
 # --------------------------------------------------------------------------
 # evaluation: cold vs warm start to the same stop rule
 # --------------------------------------------------------------------------
@@ -312,6 +329,9 @@ def main(argv=None):
     t.add_argument("--out", default=WEIGHTS)
     t.add_argument("--eval-count", type=int, default=32)
     t.add_argument("--cw", type=float, nargs=4, default=(1.0, 1.0, 1.0, 1.0))
+    x = sub.add_parser("export")
+    x.add_argument("--weights", default=WEIGHTS)
+    x.add_argument("--out", default=WEIGHTS_BIN)
     v = sub.add_parser("eval")
     v.add_argument("--weights", default=WEIGHTS)
     v.add_argument("--count", type=int, default=64)
@@ -322,7 +342,11 @@ def main(argv=None):
         if a.eval_count > 0:
             meta["eval"] = evaluate(params, scales, a.eval_count)
         save(a.out, params, scales, meta)
+        export_binary(params, scales, os.path.splitext(a.out)[0] + ".bin")
         print(json.dumps({k: v for k, v in meta.items() if k != "loss_history"}), flush=True)
+    elif a.cmd == "export":
+        params, scales, _ = load(a.weights)
+        print(export_binary(params, scales, a.out))
     else:
         params, scales, meta = load(a.weights)
         print(json.dumps(evaluate(params, scales, a.count, check_every=a.check_every)), flush=True)

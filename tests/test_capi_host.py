@@ -51,9 +51,10 @@ def test_strerror_and_version(ad):
 
 
 def test_struct_layout_matches_header(ad):
-    # admm_params_t: 4 ints, pointer, 3 floats, 3 ints, double, 3 ints
+    # admm_params_t: 4 ints, pointer, 3 floats, 3 ints, double, 4 ints
     assert ctypes.sizeof(ad.admm_params_t) == 72
     assert ad.admm_params_t.tol.offset == 48
+    assert ad.admm_params_t.fft_pad_policy.offset == 68
     assert ctypes.sizeof(ad.admm_result_t) == 64
     assert ad.admm_result_t.primal_res.offset == 56
 
@@ -65,9 +66,12 @@ def test_struct_layout_matches_header(ad):
     (dict(lam=-1.0), -1),
     (dict(reg=7), -1), (dict(stop=9), -1),
     (dict(max_iters=0), -1), (dict(check_every=0), -1),
-    (dict(reg="haar", levels=5), -1), (dict(reg="haar_ll_free", levels=5), -1), (dict(reg=5), -1),
+    (dict(reg="haar", levels=5), -1), (dict(reg="haar_ll_free", levels=5), -1), (dict(reg=8), -1),
+    (dict(reg="haar_cg", levels=5), -1),
     (dict(reg="haar_synthesis", levels=5), -1),
     (dict(psf=np.ones((65, 65)) / 65 ** 2), -1),   # larger than supported kernel side
+    (dict(H=4096, pad=True), -4), (dict(W=2049, pad=True), -4),   # no supported size to pad to
+    (dict(H=100, W=100, psf=np.ones((101, 3)) / 303, pad=True), -1),   # kernel taller than the image
 ])
 def test_plan_rejects_invalid_parameters_on_host(ad, change, code):
     kw = dict(H=64, W=64, psf=np.ones((3, 3)) / 9, lam=1e-3, reg="tv", levels=4, stop="iters",
@@ -82,15 +86,57 @@ def test_plan_rejects_invalid_parameters_on_host(ad, change, code):
 def test_null_arguments(ad):
     lib = ad.lib
     assert lib.admm_deconv_plan(None, None, None) == ad.ADMM_EINVAL
-    assert lib.admm_deconv_solve_batch(None, 1, None, None, None, None, None) == ad.ADMM_EINVAL
-    assert lib.admm_deconv_solve_batch(None, 0, None, None, None, None, None) == ad.ADMM_OK
-    assert lib.admm_deconv_solve_batch(None, -1, None, None, None, None, None) == ad.ADMM_EINVAL
+    assert lib.admm_deconv_solve_batch(None, 1, None, None, None, None, 0, None) == ad.ADMM_EINVAL
+    assert lib.admm_deconv_solve_batch(None, 0, None, None, None, None, 0, None) == ad.ADMM_OK
+    assert lib.admm_deconv_solve_batch(None, -1, None, None, None, None, 0, None) == ad.ADMM_EINVAL
     assert lib.admm_deconv_state_size(None) == -1
+    assert lib.admm_deconv_full_state_size(None) == -1
+    assert lib.admm_deconv_get_full_state(None, None, None, None) == ad.ADMM_EINVAL
+    assert lib.admm_deconv_set_state(None, None, None) == ad.ADMM_EINVAL
+    assert lib.admm_deconv_domain(None, None, None) == ad.ADMM_EINVAL
+    # use_warmstart must be 0 or 1
+    assert lib.admm_deconv_solve_batch(None, 1, None, None, None, None, 2, None) == ad.ADMM_EINVAL
     lib.admm_deconv_destroy(None)   # no-op
+
+
+def test_pad_policy_must_be_known(ad):
+    p = ad.admm_params_t()
+    k = (ctypes.c_float * 9)(*([1.0 / 9] * 9))
+    p.H = p.W = 64
+    p.psf_h = p.psf_w = 3
+    p.psf = ctypes.cast(k, ctypes.POINTER(ctypes.c_float))
+    p.max_iters, p.check_every = 10, 1
+    p.fft_pad_policy = 2
+    h = ctypes.c_void_p()
+    assert ad.lib.admm_deconv_plan(ctypes.byref(h), ctypes.byref(p), None) == ad.ADMM_EINVAL
+
+
+def test_warmstart_file_loads_and_bad_files_are_rejected(ad, tmp_path):
+    """admm_warmstart_load reads the committed weights (parsed on the host;
+    the network is created on the device only when a solve uses it) and
+    rejects a wrong magic, a wrong count, a truncated file, trailing bytes and
+    non-finite parameters; use_warmstart without a loaded network is EINVAL."""
+    from paper_1210_2687_gb300 import warmstart as ws
+    assert os.path.exists(ws.WEIGHTS_BIN)
+    ad.admm_warmstart_load(None)
+    assert ad.lib.admm_deconv_solve_batch(None, 1, None, None, None, None, 1, None) == ad.ADMM_EINVAL
+    ad.admm_warmstart_load(ws.WEIGHTS_BIN)
+    good = open(ws.WEIGHTS_BIN, "rb").read()
+    bad = {"magic": b"ADMMCNN2" + good[8:], "count": good[:16] + np.array([5], "<i8").tobytes() + good[24:],
+           "short": good[:-4], "long": good + b"\0\0\0\0",
+           "nan": good[:40] + np.array([np.nan], "<f4").tobytes() + good[44:]}
+    for name, blob in bad.items():
+        f = tmp_path / f"{name}.bin"
+        f.write_bytes(blob)
+        assert ad.lib.admm_warmstart_load(os.fsencode(str(f))) == ad.ADMM_EINVAL, name
+    assert ad.lib.admm_warmstart_load(os.fsencode(str(tmp_path / "missing.bin"))) == ad.ADMM_EINVAL
+    ad.admm_warmstart_load(None)
 
 
 def test_set_option_validates(ad):
     assert ad.lib.admm_deconv_set_option(ad.ADMM_OPT_MAX_SLOTS, -1) == ad.ADMM_EINVAL
+    assert ad.lib.admm_deconv_set_option(ad.ADMM_OPT_FAIL_ALLOC, -1) == ad.ADMM_EINVAL
+    assert ad.lib.admm_deconv_set_option(ad.ADMM_OPT_FAIL_ALLOC, 0) == ad.ADMM_OK
     assert ad.lib.admm_deconv_set_option(99, 1) == ad.ADMM_EINVAL
     assert ad.lib.admm_deconv_set_option(ad.ADMM_OPT_MAX_SLOTS, 0) == ad.ADMM_OK
 

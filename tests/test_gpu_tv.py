@@ -342,7 +342,7 @@ def test_strip_halo_reads_old_duals(ad):
 
 
 def test_empty_batch_is_ok(ad):
-    assert ad.lib.admm_deconv_solve_batch(None, 0, None, None, None, None, None) == 0
+    assert ad.lib.admm_deconv_solve_batch(None, 0, None, None, None, None, 0, None) == 0
 
 
 @pytest.mark.parametrize("reg", ["tv", "tv_aniso"])

@@ -15,6 +15,7 @@ last."""
 import numpy as np
 import pytest
 
+import oracle as O
 import synth as S
 
 pytestmark = pytest.mark.gpu
@@ -68,6 +69,36 @@ def test_noalloc_matches_plan_solve_on_two_calls_in_a_row(ad):
         assert np.all(np.isfinite(a))
         assert np.linalg.norm(a - b) <= TOL_SHORT * np.linalg.norm(b)
         plan.close()
+
+
+def test_noalloc_allocates_nothing_and_matches_the_oracle(ad):
+    """After one call (which may load the library's device code and with it
+    the fixed array), further calls leave the device's free memory unchanged;
+    the result follows the FP64 oracle's iterate sequence."""
+    import torch
+    H = W = 128
+    psf = S.psf_box(9)
+    ybar, mask = _problem(H, W, psf, 0.8, 33)
+    lam = 1e-3
+    mu1, mu2 = S.default_mu(lam)
+    plan = ad.Plan(H, W, psf, lam, mu1, mu2, "tv", max_iters=50)
+    params = plan.params
+    y = torch.from_numpy(ybar.astype(np.float32)).cuda()
+    m = torch.from_numpy(mask).cuda()
+    x = torch.empty((H, W), dtype=torch.float32, device="cuda")
+    rc, _ = ad.admm_deconv_solve_noalloc(params, y.data_ptr(), m.data_ptr(), x.data_ptr())
+    assert rc == ad.ADMM_OK
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(2):
+        rc, r = ad.admm_deconv_solve_noalloc(params, y.data_ptr(), m.data_ptr(), x.data_ptr())
+        assert rc == ad.ADMM_OK and r.iters == 50
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    ref = O.solve(ybar.astype(np.float64), mask, psf, lam, mu1, mu2, "tv", iters=50)
+    xg = x.cpu().numpy().astype(np.float64)
+    assert np.linalg.norm(xg - ref.x) <= 1e-4 * np.linalg.norm(ref.x)
+    plan.close()
 
 
 def test_noalloc_rejects_sizes_beyond_its_array(ad):
