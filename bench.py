@@ -49,8 +49,14 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-secondary", action="store_true", help="skip the frame-prior workload")
     ap.add_argument("--frame-only", action="store_true", help="only the frame-prior workload (profiler captures)")
+    ap.add_argument("--frame-sizes", default="1024,2048,fs1024",
+                    help="frame workloads to run: sides, 'fs' prefix for the synthesis formulation")
+    ap.add_argument("--frame-iters", type=int, default=500, help="fixed iterations of the frame workloads")
+    ap.add_argument("--frame-no-accuracy", action="store_true", help="skip the frame workloads' solve to tolerance")
     ap.add_argument("--uneven-only", action="store_true", help="only the batched uneven workload")
     ap.add_argument("--warm-only", action="store_true", help="only the learned warm-start comparison")
+    ap.add_argument("--cg-only", action="store_true", help="only the mask-decoupling vs Reeves-Sorel comparison")
+    ap.add_argument("--oracle-only", action="store_true", help="only the CPU oracle timing table")
     ap.add_argument("--steady-only", action="store_true",
                     help="only the fixed-iteration pass with every slot busy (for profiler captures)")
     ap.add_argument("--no-autotune", action="store_true",
@@ -298,6 +304,8 @@ def cufft_comparison(torch, probs, iters, x_ref, stream):
 
 
 FRAME_ITERS = 500
+TV_ALG_BYTES = 67.0      # TV-MD: d (3 planes) in and out 24, M^T y and mask 5, Lambda and K 6, two complex round trips 32
+FRAME_ALG_BYTES = 155.0  # FA-MD, 4 levels: d (14 planes) in and out 112, 5, 6, 32
 
 
 def frame_secondary(ad, torch, stream, args):
@@ -306,12 +314,22 @@ def frame_secondary(ad, torch, stream, args):
     synthesis formulation FS-MD at 1024^2), a fixed 500
     iterations (throughput); kernel time per phase from a profiled pass; and
     the same problem solved to rel-x < 1e-5 (checked every 10 iterations)
-    for accuracy: iterations and ISNR. Algorithmic bytes per pixel and
-    iteration of the fixed-count run: column phase 22.1, row side 28
-    (inverse rows) + 112 (Haar tile, d2 13 bands in and out) + 16 (forward
-    rows)."""
+    for accuracy: iterations and ISNR. The fraction of the HBM roofline is
+    taken on the method's algorithmic bytes per pixel and iteration, 155 for
+    the 13-band frame prior: d1 and d2 (14 planes) read and written (112),
+    M^T y and the mask (5), Lambda and K over the half spectrum (6), and two
+    complex round trips between the row and column phases (32). The kernels
+    themselves move more (the zeta2 store and its re-read by the synthesis,
+    the x and zeta1 scratch planes): column phase 22.1, row side 28 (inverse
+    rows) + 112 (Haar tile) + 16 (forward rows); that figure is reported
+    beside it, and the extra bytes count as overhead, not work."""
     out = {}
-    for reg, size in (("haar", 1024), ("haar", 2048), ("haar_synthesis", 1024)):
+    FRAME_ITERS = args.frame_iters
+    cases = []
+    for tok in args.frame_sizes.split(","):
+        tok = tok.strip()
+        cases.append(("haar_synthesis", int(tok[2:])) if tok.startswith("fs") else ("haar", int(tok)))
+    for reg, size in cases:
         p = S.config3_problem(0, size)
         n = size * size
         tune = tune_class(ad, torch, args, size, size, "haar", 4, problems=1)   # one image per solve
@@ -332,18 +350,24 @@ def frame_secondary(ad, torch, stream, args):
         # synthesis form: the analysis tile also reads w and the previous zeta2 (4 + 52)
         row_b = 28.0 + 112.0 + 16.0 + (56.0 if reg == "haar_synthesis" else 0.0)
         col_b = 44.0 * (size // 2 + 1) / size
+        alg_b = FRAME_ALG_BYTES
         peak, _ = read_peak()
         key = f"{'fs' if reg == 'haar_synthesis' else 'fa'}_md_{size}"
         out[key] = {
             "iters_per_s": FRAME_ITERS / sec,
-            # whole iteration: algorithmic bytes of both sides over the timed solve
-            "iteration_gbs": FRAME_ITERS * n * (row_b + col_b) / sec / 1e9,
-            "iteration_frac": FRAME_ITERS * n * (row_b + col_b) / sec / 1e9 / peak,
+            # whole iteration: the method's algorithmic bytes over the timed solve
+            "iteration_gbs": FRAME_ITERS * n * alg_b / sec / 1e9,
+            "iteration_frac": FRAME_ITERS * n * alg_b / sec / 1e9 / peak,
+            "alg_bytes_per_px_iter": alg_b,
+            # the same with the bytes the kernels move (their overhead included)
+            "iteration_frac_kernel_bytes": FRAME_ITERS * n * (row_b + col_b) / sec / 1e9 / peak,
             "row_side_gbs": FRAME_ITERS * n * row_b / (pf.row_ms * 1e-3) / 1e9,
             "col_phase_gbs": FRAME_ITERS * n * col_b / (pf.col_ms * 1e-3) / 1e9,
             "bytes_per_px_iter": {"row_side": row_b, "col_phase": col_b},
             "tuning": tune}
         plan.close()
+        if args.frame_no_accuracy:
+            continue
         acc = ad.Plan(size, size, p.psf, p.lam, p.mu1, p.mu2, reg, stop="rel_x", tol=TOL, max_iters=MAX_ITERS,
                       check_every=CHECK_EVERY)
         r = ad.solve(acc, y, m, x, stream)
@@ -395,6 +419,10 @@ def uneven_secondary(ad, torch, stream, args, count=UNEVEN_COUNT):
     solve = np.array([r.t_done_ms - r.t_start_ms for r in res])
     iters = np.array([r.iters for r in res])
     px_iters = sum(int(r.iters) * p.ybar.size for r, p in zip(res, probs))
+    # algorithmic bytes of every problem-iteration, each on its (padded) domain
+    alg_bytes = sum(int(r.iters) * p.ybar.size * (TV_ALG_BYTES if p.reg == "tv" else FRAME_ALG_BYTES)
+                    for r, p in zip(res, probs))
+    peak, _ = read_peak()
     isnr = []
     for p, x in zip(probs, xs):
         n = p.meta["window"]
@@ -410,6 +438,9 @@ def uneven_secondary(ad, torch, stream, args, count=UNEVEN_COUNT):
         "images_per_s": count / sec,
         "iters_per_s": float(iters.sum()) / sec,
         "mpix_iters_per_s": px_iters / sec / 1e6,
+        "hbm_gbs_algorithmic": alg_bytes / sec / 1e9,
+        "hbm_frac": alg_bytes / sec / 1e9 / peak,
+        "hbm_frac_note": "67 B/px (TV) or 155 B/px (4-level Haar) per iteration on the padded domain",
         "wall_s": sec,
         "converged": int(sum(r.converged for r in res)),
         "iters_mean": float(iters.mean()),
@@ -423,6 +454,77 @@ def uneven_secondary(ad, torch, stream, args, count=UNEVEN_COUNT):
         "input_generation_s": t_gen,
         "tuning": tunings,
     }
+
+
+CG_ITERS = 200
+
+
+def cg_secondary(ad, torch, stream, batch=64):
+    """Mask decoupling against the Reeves-Sorel method (the paper's MD vs CG
+    comparison, Table IV: 256 x 256 domain, 19 x 19 uniform blur, the valid
+    region observed, i.e. 238 x 238, BSNR 40 dB): device time per iteration
+    of TV-MD, TV-CG, FA-MD and FA-CG for one image and for a batch of
+    `batch` images (fixed 200 iterations), and each method's iterations and
+    time to the paper's stop rule (relative change of the objective < 1e-4)
+    on one image with its ISNR."""
+    size = 256
+    psf = S.psf_box(19)
+    probs = []
+    for i in range(batch):
+        g = S.rng(5000 + i)
+        x = S.shapes_image(size, size, g, 20, rmax=size / 4.0) if i % 2 == 0 else S.textured_image(size, size, g)
+        ybar, mask, _ = S.observe(x, psf, None, 40.0, g)
+        probs.append((x, ybar.astype(np.float32), mask))
+    lam = {"tv": 2e-4, "haar": 2e-4}
+    ys = [torch.from_numpy(p[1]).cuda() for p in probs]
+    ms = [torch.from_numpy(p[2]).cuda() for p in probs]
+    xs = [torch.empty((size, size), dtype=torch.float32, device="cuda") for _ in probs]
+    vm = S.valid_mask(size, size, 19, 19)
+
+    def timed(plans, k):
+        ad.solve_batch(plans, ys[:k], ms[:k], xs[:k], stream=stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ad.solve_batch(plans, ys[:k], ms[:k], xs[:k], stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) * 1e-3
+
+    out = {"workload": "256x256 domain, 19x19 uniform blur, valid region (238x238 observed), BSNR 40, "
+                       f"lambda 2e-4; {CG_ITERS} iterations; batch {batch}"}
+    for prior in ("tv", "haar"):
+        mu1, mu2 = S.default_mu(lam[prior])
+        row = {}
+        for method in ("md", "cg"):
+            reg = prior if method == "md" else prior + "_cg"
+            r = {}
+            for k in (1, batch):
+                plans = [ad.Plan(size, size, psf, lam[prior], mu1, mu2, reg, max_iters=CG_ITERS) for _ in range(k)]
+                sec = timed(plans, k)
+                r[f"us_per_iter_batch{k}"] = sec / CG_ITERS * 1e6
+                r[f"us_per_problem_iter_batch{k}"] = sec / (CG_ITERS * k) * 1e6
+                for pl in plans:
+                    pl.close()
+            acc = ad.Plan(size, size, psf, lam[prior], mu1, mu2, reg, stop="rel_obj", tol=1e-4, max_iters=MAX_ITERS)
+            ad.solve(acc, ys[0], ms[0], xs[0], stream)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            res = ad.solve(acc, ys[0], ms[0], xs[0], stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            r["to_rel_obj_1e-4"] = {"iters": int(res.iters), "converged": int(res.converged),
+                                    "ms": e0.elapsed_time(e1),
+                                    "isnr_db": isnr_db(probs[0][0], probs[0][1],
+                                                       xs[0].cpu().numpy().astype(np.float64), vm)}
+            acc.close()
+            row[method] = r
+        row["cg_over_md_per_iter_single"] = row["cg"]["us_per_iter_batch1"] / row["md"]["us_per_iter_batch1"]
+        row["cg_over_md_per_iter_batch"] = (row["cg"][f"us_per_iter_batch{batch}"]
+                                            / row["md"][f"us_per_iter_batch{batch}"])
+        row["cg_over_md_time_to_tol"] = row["cg"]["to_rel_obj_1e-4"]["ms"] / row["md"]["to_rel_obj_1e-4"]["ms"]
+        out[prior] = row
+    out["paper"] = "MD 1.6-1.8x faster per iteration, 1.5-2x in total (Sec. V, Table IV; MATLAB, Core i5)"
+    return out
 
 
 CNN_FLOP_PER_PX = 2 * 9 * (2 * 32 + 6 * 32 * 32 + 32 * 4)   # eight 3x3 convolutions
@@ -461,6 +563,66 @@ def warm_secondary(ad, torch, stream, count=32):
     return ev
 
 
+_ORACLE_TIMING = r"""
+import json, os, resource, sys, time
+sys.path.insert(0, sys.argv[1])
+import numpy as np
+import oracle as O
+import synth as S
+size, reg, budget, min_it, max_it = int(sys.argv[2]), sys.argv[3], float(sys.argv[4]), int(sys.argv[5]), int(sys.argv[6])
+if reg == "tv":
+    p = S.config1_problem(0) if size == 64 else S.config2_problem(0, "gauss", 40, size=size)
+else:
+    p = S.config3_problem(0, size)
+H, W = p.ybar.shape
+st = O.State.zeros(H, W, reg)
+otf = O.psf_otf(p.psf, H, W)
+den = O.tv_denominator_diag(p.psf, H, W, p.mu1, p.mu2) if reg == "tv" else None
+r0 = resource.getrusage(resource.RUSAGE_SELF)
+t0 = time.perf_counter()
+n = 0
+while n < max_it and (n < min_it or time.perf_counter() - t0 < budget):
+    if reg == "tv":
+        st = O.tvmd_step(st, p.ybar, p.mask, p.psf, p.lam, p.mu1, p.mu2, otf, den)
+    else:
+        st = O.famd_step(st, p.ybar, p.mask, p.psf, p.lam, p.mu1, p.mu2, 4, otf)
+    n += 1
+dt = time.perf_counter() - t0
+r1 = resource.getrusage(resource.RUSAGE_SELF)
+cpu = (r1.ru_utime - r0.ru_utime) + (r1.ru_stime - r0.ru_stime)
+print(json.dumps({"iters": n, "seconds": dt, "iters_per_s": n / dt, "cpu_util": cpu / dt}))
+"""
+
+
+def oracle_timing(cores):
+    """The FP64 oracle timed as it stands on the host cores, in fresh
+    processes whose BLAS thread count is set by the environment: one thread,
+    and all `cores` the process may run on. Sizes 64^2 and 512^2 run TV-MD
+    (the 64^2 and 512^2 workloads), 1024^2 and 2048^2 FA-MD (the frame
+    workload; at least 5 iterations). One thread is timed at 64^2 and 512^2
+    only (at 2048^2 one FP64 iteration of the oracle's matrix DFTs takes
+    minutes on one core). `cpu_util` = CPU time / wall time of the loop."""
+    cases = [(64, "tv", 3.0, 5, 10 ** 6), (512, "tv", 6.0, 3, 10 ** 6),
+             (1024, "haar", 0.0, 5, 5), (2048, "haar", 0.0, 5, 5)]
+    out = {"cores_available": cores, "runs": []}
+    for threads in (1, cores):
+        env = dict(os.environ)
+        for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+            env[k] = str(threads)
+        for size, reg, budget, lo, hi in cases:
+            if threads == 1 and size > 512:
+                continue
+            r = subprocess.run([sys.executable, "-c", _ORACLE_TIMING, ROOT, str(size), reg, str(budget), str(lo),
+                                str(hi)], capture_output=True, text=True, env=env, timeout=1200)
+            if r.returncode != 0:
+                out["runs"].append({"size": size, "reg": reg, "threads": threads, "error": r.stderr[-300:]})
+                continue
+            d = json.loads(r.stdout.strip().splitlines()[-1])
+            d.update({"size": size, "reg": reg, "threads": threads})
+            out["runs"].append(d)
+    return out
+
+
 def cpu_baseline_oracle(probs, seconds=12.0):
     """The FP64 oracle as it stands on one 512^2 problem of the workload,
     iterating until about `seconds` of CPU time; iterations per second."""
@@ -482,6 +644,10 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
+    import resource
+    cores = len(os.sched_getaffinity(0))
+    r0 = resource.getrusage(resource.RUSAGE_SELF)
+    w0 = time.perf_counter()
     probs = make_batch(1, 0)
     per_step = []
     iters_step = 0
@@ -493,6 +659,8 @@ def run_reference(args):
     tot_n = sum(n for n, _ in per_step)
     tot_t = sum(t for _, t in per_step)
     value = tot_n / tot_t
+    r1 = resource.getrusage(resource.RUSAGE_SELF)
+    util = ((r1.ru_utime - r0.ru_utime) + (r1.ru_stime - r0.ru_stime)) / (time.perf_counter() - w0)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "iters/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
@@ -500,14 +668,18 @@ def run_reference(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": "tv_md_512x512_inpaint40_gauss19_motion15_relx1e-5",
                    "sample": f"{iters_step} oracle iterations on one 512x512 problem per step"},
-        "cpu_baseline": {"value": value, "unit": "iters/s", "cores": 1, "kind": "oracle",
-                         "sample": "TV-MD FP64 numpy oracle, one 512x512 problem, ~3 s per step"},
+        "cpu_baseline": {"value": value, "unit": "iters/s", "cores": cores, "kind": "oracle",
+                         "sample": f"TV-MD FP64 oracle (matrix DFTs on the host's BLAS), one 512x512 problem, "
+                                   f"~3 s per step, CPU utilisation {util:.1f} cores"},
         "e2e": {"value": value, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
 def run_ours(args):
+    if args.oracle_only:      # host only (no GPU work)
+        print(json.dumps({"oracle_timing": oracle_timing(len(os.sched_getaffinity(0)))}), flush=True)
+        return
     import torch
     rank, world, local = dist_env()
     if world > 1:
@@ -524,6 +696,9 @@ def run_ours(args):
         return
     if args.warm_only:
         print(json.dumps({"warm_start": warm_secondary(ad, torch, torch.cuda.current_stream())}), flush=True)
+        return
+    if args.cg_only:
+        print(json.dumps({"md_vs_cg_256": cg_secondary(ad, torch, torch.cuda.current_stream())}), flush=True)
         return
     if args.uneven_only:
         print(json.dumps({"uneven_batch": uneven_secondary(ad, torch, torch.cuda.current_stream(), args)}), flush=True)
@@ -672,13 +847,19 @@ def run_ours(args):
         secondary = frame_secondary(ad, torch, stream, args)
         secondary["uneven_batch"] = uneven_secondary(ad, torch, stream, args)
         secondary["warm_start"] = warm_secondary(ad, torch, stream)
+        secondary["md_vs_cg_256"] = cg_secondary(ad, torch, stream)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, nit, dt = cpu_baseline_oracle(probs, seconds=12.0)
-        cpu = {"value": v, "unit": "iters/s", "cores": 1, "kind": "oracle",
-               "sample": f"{nit} TV-MD iterations of the FP64 numpy oracle on one 512x512 problem "
-                         f"({dt:.1f} s, single thread)"}
+        cores = len(os.sched_getaffinity(0))
+        ot = oracle_timing(cores)
+        all512 = next((r for r in ot["runs"] if r["size"] == 512 and r["threads"] == cores and "iters" in r), None)
+        if all512 is not None:
+            cpu = {"value": all512["iters_per_s"], "unit": "iters/s", "cores": cores, "kind": "oracle",
+                   "sample": f"{all512['iters']} TV-MD iterations of the FP64 oracle on one 512x512 problem "
+                             f"({all512['seconds']:.1f} s, BLAS threads = {cores}, "
+                             f"CPU utilisation {all512['cpu_util']:.1f} cores)",
+                   "timing_table": ot}
 
     if rank == 0:
         line = {
