@@ -49,8 +49,9 @@ extern "C" {
 #define ADMM_EINVAL              -1  /* bad argument (null, non-odd kernel, mu <= 0, ...) */
 #define ADMM_ENOMEM              -2  /* device or host allocation failed                   */
 #define ADMM_ECUDA               -3  /* a CUDA runtime call failed                         */
-#define ADMM_EUNSUPPORTED_SIZE   -4  /* H or W not in {64,...,2048} powers of two (with
-                                        fft_pad_policy ADMM_PAD_EXACT), or above 2048      */
+#define ADMM_EUNSUPPORTED_SIZE   -4  /* a side that is not m 2^k (m = 1, 3, 5), a multiple
+                                        of 32 in 64..2048 (with fft_pad_policy
+                                        ADMM_PAD_EXACT), or a side above 2048              */
 #define ADMM_ENONFINITE          -5  /* an observed value or the iterate is NaN/Inf
                                         (divergence, Theorem 1)                            */
 #define ADMM_ETIMEOUT            -6  /* reserved for a bounded device wait that expires. No
@@ -95,8 +96,11 @@ typedef struct admm_plan_s* admm_plan_t;   /* opaque; owned by the library */
 
 /* Parameters of one problem (one image). */
 typedef struct {
-    int   H, W;            /* full unknown-image domain; powers of two in [64, 2048], or
-                              any size in [1, 2048] with fft_pad_policy = ADMM_PAD_NEXT     */
+    int   H, W;            /* full unknown-image domain: sides m 2^k (m = 1, 3 or 5) that are
+                              multiples of 32 in [64, 2048] (powers of two run the tuned
+                              kernels, the others mixed-radix kernels on the exact domain;
+                              the Reeves-Sorel variants take powers of two only), or any
+                              size in [1, 2048] with fft_pad_policy = ADMM_PAD_NEXT          */
     int   psf_h, psf_w;    /* odd kernel sides, each <= the matching image side             */
     const float* psf;      /* HOST pointer, psf_h x psf_w row-major, centre at
                               (psf_h/2, psf_w/2); copied during admm_deconv_plan; the
@@ -119,13 +123,14 @@ typedef struct {
                               (pixels whose blurred value does not touch the unknown
                               boundary, Sec. IV-A); 1: use the mask exactly as given
                               (e.g. M = I for periodic deconvolution)                        */
-    int   fft_pad_policy;  /* ADMM_PAD_EXACT (0): H and W must be transform sizes the
-                              library supports (powers of two 64..2048), else
-                              ADMM_EUNSUPPORTED_SIZE; ADMM_PAD_NEXT (1): any H, W in
-                              1..2048 -- the plan solves on the next supported size,
-                              the image in its top-left corner and the added rows and
-                              columns never observed (more unknown boundary, Sec. IV-A:
-                              the domain only has to hold the image and the kernel
+    int   fft_pad_policy;  /* ADMM_PAD_EXACT (0): H and W must be sides the library
+                              solves exactly (see H, W), else ADMM_EUNSUPPORTED_SIZE;
+                              ADMM_PAD_NEXT (1): any H, W in 1..2048 -- a side that is not
+                              solved exactly goes to the next one that is (300 -> 320;
+                              the next power of two for the Reeves-Sorel variants), the
+                              image in the domain's top-left corner and the added rows
+                              and columns never observed (more unknown boundary, Sec.
+                              IV-A: the domain only has to hold the image and the kernel
                               support); y, mask and x_out keep the caller's H x W      */
 } admm_params_t;
 

@@ -17,7 +17,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 LIB = os.path.join(PKG, "libadmm_deconv.so")
 SOURCES = [os.path.join(CSRC, f) for f in
-           ("engine.cu", "cg.cu", "cols.cu", "rows_small.cu", "rows_512.cu", "rows_large.cu", "cnn.cu")]
+           ("engine.cu", "cg.cu", "gen.cu", "cols.cu", "rows_small.cu", "rows_512.cu", "rows_large.cu", "cnn.cu")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -31,7 +31,7 @@ cudaError_t launch_cg_t(int H, int Wc, int Wp, const ProbDesc* d, SlotTable sl, 
     if (e == cudaSuccess) e = launch_chain(cg_obs<W>, rgrid, blk, (size_t)0, s, d, sl, H);
     if (e != cudaSuccess) return e;
     if (tv) {
-        e = launch_chain(tv_cg_tile<0>, dim3(cg_num_tiles(H, W), count), blk, (size_t)0, s, d, sl, H, W, nrow,
+        e = launch_chain(tv_tile<false>, dim3(cg_num_tiles(H, W), count), blk, (size_t)0, s, d, sl, H, W, nrow,
                          n_active);
     } else {
         e = haar_tile_attributes();

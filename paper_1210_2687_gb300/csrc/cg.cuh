@@ -26,7 +26,7 @@
 //                                       its last CTA divides)
 //   5. x = x~ + alpha v, A x likewise, z += alpha s; then the observation
 //      prox and dual update on the observed pixels (cg_obs), and the
-//      regulariser side as for the MD methods (tv_cg_tile for TV; the frame
+//      regulariser side as for the MD methods (tv_tile for TV; the frame
 //      analysis and synthesis tiles for the frame prior), which finishes
 //      the iteration; the forward row DFTs of zeta~ + i w close it.
 // Per-pixel planes (ProbDesc::cg): x~, A x~, v, A v, s, z.
@@ -269,20 +269,24 @@ cg_obs(const ProbDesc* __restrict__ probs, SlotTable sl, int H) {
 }
 
 // ---------------------------------------------------------------------------
-// TV-CG regulariser side on a 32 x 32 tile (Alg. 3 lines 9-11 and lines 3-5
-// of the next iteration): D x with forward periodic differences, vector-soft
-// with tau = lambda / mu2, d2 <- d2 - (D x - u2), delta = u2 + d2 and
-// w = gamma (Dh^T delta_h + Dv^T delta_v). w at a pixel needs delta one
-// column left and one row up, so the tile recomputes delta on that halo from
-// x (one more row and column of x) and the previous d2 (double-buffered by
-// iteration parity, so a neighbour's halo always sees the old d2). Finishes
-// the iteration. Grid: (tiles, slots).
+// TV regulariser side on a 32 x 32 tile (Alg. 3 lines 9-11 and lines 3-5 of
+// the next iteration), for TV-CG and for TV-MD on domains whose sides are
+// not both powers of two: D x with forward periodic differences, vector-soft
+// (ANISO: eq. soft per component) with tau = lambda / mu2, d2 <- d2 -
+// (D x - u2), delta = u2 + d2 and w = gamma (Dh^T delta_h + Dv^T delta_v).
+// w at a pixel needs delta one column left and one row up, so the tile
+// recomputes delta on that halo from x (one more row and column of x) and
+// the previous d2 (double-buffered by iteration parity, so a neighbour's halo
+// always sees the old d2). Finishes the iteration. Grid: (tiles, slots).
+// H and W are multiples of 32 (not necessarily powers of two).
 // ---------------------------------------------------------------------------
 constexpr int kCgTile = 32;
-template <int dummy = 0>
+// periodic index for x in [-n, 2n)
+__device__ __forceinline__ int wrapi(int x, int n) { return x < 0 ? x + n : (x >= n ? x - n : x); }
+template <bool ANISO = false>
 __global__ void __launch_bounds__(kThreads)
-tv_cg_tile(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W, int n_row_ctas,
-           int* __restrict__ n_active) {
+tv_tile(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W, int n_row_ctas,
+        int* __restrict__ n_active) {
     chain_wait();   // (launch chain: the predecessor's writes are visible)
     constexpr int T = kCgTile, XR = T + 2, XS = T + 3, DR = T + 1;
     const int pi = sl.map[blockIdx.y];
@@ -302,7 +306,7 @@ tv_cg_tile(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W, int n
     const float* __restrict__ xw = P.work;
     for (int e = tid; e < XR * XR; e += kThreads) {
         const int rr = e / XR, cc = e - rr * XR;
-        const int r = (R0 - 1 + rr + H) & (H - 1), c = (C0 - 1 + cc + W) & (W - 1);
+        const int r = wrapi(R0 - 1 + rr, H), c = wrapi(C0 - 1 + cc, W);
         xs[rr * XS + cc] = xw[(size_t)r * W + c];
     }
     __syncthreads();
@@ -312,20 +316,20 @@ tv_cg_tile(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W, int n
     CompSum tvs, prs;
     for (int e = tid; e < DR * DR; e += kThreads) {
         const int rr = e / DR, cc = e - rr * DR;
-        const int r = (R0 - 1 + rr + H) & (H - 1), c = (C0 - 1 + cc + W) & (W - 1);
+        const int r = wrapi(R0 - 1 + rr, H), c = wrapi(C0 - 1 + cc, W);
         const size_t pix = (size_t)r * W + c;
         const float x0 = xs[rr * XS + cc];
         const float gh = xs[rr * XS + cc + 1] - x0;
         const float gv = xs[(rr + 1) * XS + cc] - x0;
         const float2 dold = first ? make_float2(0.f, 0.f) : d2in[pix];
         float uh, uv;
-        tv_prox(gh - dold.x, gv - dold.y, tau, false, uh, uv);
+        tv_prox(gh - dold.x, gv - dold.y, tau, ANISO, uh, uv);
         const float ndh = dold.x - (gh - uh), ndv = dold.y - (gv - uv);
         dl[rr * DR + cc] = make_float2(uh + ndh, uv + ndv);
         if (rr >= 1 && cc >= 1) {                // a pixel of the tile: owned
             d2out[pix] = make_float2(ndh, ndv);
             if (nobj) {
-                tvs.add(tv_norm(gh, gv, false));
+                tvs.add(tv_norm(gh, gv, ANISO));
                 const float eh = ndh - dold.x, ev = ndv - dold.y;
                 prs.add(fmaf(eh, eh, ev * ev));
             }

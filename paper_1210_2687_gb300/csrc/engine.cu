@@ -27,6 +27,7 @@
 #include "kernels.cuh"
 #include "haar.cuh"
 #include "cg.cuh"
+#include "gen.cuh"
 #include "setup.cuh"
 #include "variants.cuh"
 
@@ -80,6 +81,7 @@ struct admm_plan_s {
                                 // (x0, d0); 2 admm_deconv_set_state's state (resume)
     int Hu = 0, Wu = 0;         // the caller's image size (p.H x p.W is the domain solved on)
     bool padded = false;        // Hu x Wu sits in the top-left corner of a larger domain
+    bool gen = false;           // a side is not a power of two: the mixed-radix kernels (gen.cuh)
 };
 
 namespace {
@@ -107,6 +109,8 @@ struct DeviceCtx {
     // chunk graphs keyed by the batch's layout (size classes, offsets, slots,
     // lanes); cleared whenever the descriptor or slot tables move
     std::map<std::string, cudaGraphExec_t> graphs;
+    // mixed-radix twiddles exp(-2 pi i k / N), k < N, per length N
+    std::map<int, float2*> gtw;
 };
 
 // A group's problems split into `n` lanes that iterate independently: lane
@@ -142,12 +146,20 @@ int prof_event(size_t i, cudaStream_t s) {
 
 bool is_pow2_size(int n) { return n >= 64 && n <= 2048 && (n & (n - 1)) == 0; }
 
-// smallest supported transform size >= n (-1 if there is none)
+// smallest power-of-two transform size >= n (-1 if there is none)
 int next_supported_size(int n) {
     if (n < 1 || n > 2048) return -1;
     int m = 64;
     while (m < n) m <<= 1;
     return m;
+}
+// sides of the mixed-radix path: m 2^k, m in {1, 3, 5}, multiples of 32, 64..2048
+bool is_gen_size(int n) { return gfft_length_ok(n); }
+// smallest side >= n the mixed-radix path takes (-1 if there is none)
+int next_gen_size(int n) {
+    for (int m = std::max(n, 64); m <= 2048; ++m)
+        if (is_gen_size(m)) return m;
+    return -1;
 }
 
 int cuda_fail(cudaError_t e) {
@@ -249,6 +261,30 @@ int ensure_ctx(int dev, int count, DeviceCtx** out) {
         c.cap = cap;
     }
     *out = &c;
+    return ADMM_OK;
+}
+
+// the mixed-radix twiddle table of length N on this context (made on first use)
+int gen_twiddles(DeviceCtx* c, int N, const float2** out) {
+    auto it = c->gtw.find(N);
+    if (it != c->gtw.end()) {
+        *out = it->second;
+        return ADMM_OK;
+    }
+    std::vector<float2> tw(N);
+    for (int k = 0; k < N; ++k) {
+        // exact reduction: angle = 2 pi k / N
+        const double a = 2.0 * M_PI * (double)k / (double)N;
+        tw[k] = make_float2((float)std::cos(a), (float)(-std::sin(a)));
+    }
+    float2* t = nullptr;
+    CK(dev_alloc(&t, (size_t)N * sizeof(float2)));
+    if (cudaMemcpy(t, tw.data(), (size_t)N * sizeof(float2), cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaFree(t);
+        return ADMM_ECUDA;
+    }
+    c->gtw[N] = t;
+    *out = t;
     return ADMM_OK;
 }
 
@@ -465,12 +501,23 @@ int admm_deconv_plan(admm_plan_t* out, const admm_params_t* p, void* stream) {
     if (p->fft_pad_policy != ADMM_PAD_EXACT && p->fft_pad_policy != ADMM_PAD_NEXT) return ADMM_EINVAL;
     // the domain solved on: the caller's, or the next supported size (the
     // added rows and columns are more unknown boundary, Sec. IV-A)
+    // Sides that are powers of two take the tuned power-of-two kernels; other
+    // sides m 2^k (m = 3, 5) the mixed-radix kernels on the exact domain
+    // (the Reeves-Sorel variants have no mixed-radix form and pad).
     int Hd = p->H, Wd = p->W;
+    bool gen = false;
     if (!is_pow2_size(Hd) || !is_pow2_size(Wd)) {
-        if (p->fft_pad_policy != ADMM_PAD_NEXT) return ADMM_EUNSUPPORTED_SIZE;
-        Hd = next_supported_size(p->H);
-        Wd = next_supported_size(p->W);
-        if (Hd < 0 || Wd < 0) return ADMM_EUNSUPPORTED_SIZE;
+        const bool gen_reg = !reg_cg(p->reg);
+        if (gen_reg && is_gen_size(Hd) && is_gen_size(Wd)) {
+            gen = true;
+        } else if (p->fft_pad_policy == ADMM_PAD_NEXT) {
+            Hd = gen_reg ? next_gen_size(p->H) : next_supported_size(p->H);
+            Wd = gen_reg ? next_gen_size(p->W) : next_supported_size(p->W);
+            if (Hd < 0 || Wd < 0) return ADMM_EUNSUPPORTED_SIZE;
+            gen = !is_pow2_size(Hd) || !is_pow2_size(Wd);
+        } else {
+            return ADMM_EUNSUPPORTED_SIZE;
+        }
     }
     if (p->psf_h < 1 || p->psf_w < 1 || (p->psf_h & 1) == 0 || (p->psf_w & 1) == 0) return ADMM_EINVAL;
     if (p->psf_h > std::min(p->H, kMaxPsfSide) || p->psf_w > std::min(p->W, kMaxPsfSide)) return ADMM_EINVAL;
@@ -503,6 +550,7 @@ int admm_deconv_plan(admm_plan_t* out, const admm_params_t* p, void* stream) {
     pl->p.H = Hd;
     pl->p.W = Wd;
     pl->padded = Hd != p->H || Wd != p->W;
+    pl->gen = gen;
     pl->psf.assign(p->psf, p->psf + p->psf_h * p->psf_w);
     pl->lam = p->lambda;
     pl->mu1 = mu1;
@@ -512,7 +560,10 @@ int admm_deconv_plan(admm_plan_t* out, const admm_params_t* p, void* stream) {
     const int H = Hd, W = Wd;
     const size_t n = (size_t)H * W;
     pl->Wc = W / 2 + 1;
-    {
+    if (gen) {
+        // one configuration (no tuning); the row side is a kernel chain
+        pl->cb = gen_col_block(H);
+    } else {
         const admm_tuning_t tu = lookup_tuning(pl->device, H, W, fam, levels);
         const ColVariant* cv = nullptr;
         col_variants(H, &cv);
@@ -523,8 +574,13 @@ int admm_deconv_plan(admm_plan_t* out, const admm_params_t* p, void* stream) {
         pl->cb = cv[pl->col_v].CB;
     }
     pl->Wp = (int)align_up(pl->Wc, pl->cb);
-    pl->fam = fam;
-    if (fam == ADMM_REG_TV) {
+    pl->fam = gen ? ADMM_REG_HAAR : fam;
+    if (gen) {
+        pl->R = gen_rows_per_cta(W);
+        pl->nb = tvp ? 2 : 3 * levels + 1;
+        pl->n_strips = tvp ? cg_num_tiles(H, W) : haar_num_tiles(H, W);
+        pl->n_slots = H / pl->R + pl->n_strips;
+    } else if (fam == ADMM_REG_TV) {
         const RowVariant* rv = nullptr;
         tv_row_variants(W, &rv);
         pl->R = rv[pl->row_v].R;
@@ -533,7 +589,8 @@ int admm_deconv_plan(admm_plan_t* out, const admm_params_t* p, void* stream) {
         pl->R = haar_row_strip(W);
         pl->nb = tvp ? 2 : 3 * levels + 1;
     }
-    if (fam == ADMM_REG_TV) {
+    if (gen) {
+    } else if (fam == ADMM_REG_TV) {
         pl->n_strips = H / pl->R;
         pl->n_slots = pl->n_strips;
     } else {
@@ -551,7 +608,7 @@ int admm_deconv_plan(admm_plan_t* out, const admm_params_t* p, void* stream) {
     const size_t od2 = take(2 * (size_t)pl->nb * n * sizeof(float));
     const size_t oyb = take(n * sizeof(float));
     const size_t oxp = take(n * sizeof(float));
-    const size_t owk = take(fam == ADMM_REG_HAAR ? 3 * n * sizeof(float) : 0);
+    const size_t owk = take(pl->fam == ADMM_REG_HAAR ? 3 * n * sizeof(float) : 0);
     const size_t ocg = take(cg ? 6 * n * sizeof(float) : 0);
     const size_t ocp = take(cg ? 2 * (size_t)haar_num_row_ctas(H, W) * sizeof(double) : 0);
     const size_t omk = take(n);
@@ -576,7 +633,7 @@ int admm_deconv_plan(admm_plan_t* out, const admm_params_t* p, void* stream) {
     pl->d2 = reinterpret_cast<float*>(b + od2);
     pl->ybar = reinterpret_cast<float*>(b + oyb);
     pl->xprev = reinterpret_cast<float*>(b + oxp);
-    pl->work = fam == ADMM_REG_HAAR ? reinterpret_cast<float*>(b + owk) : nullptr;
+    pl->work = pl->fam == ADMM_REG_HAAR ? reinterpret_cast<float*>(b + owk) : nullptr;
     pl->cg = cg ? reinterpret_cast<float*>(b + ocg) : nullptr;
     pl->cg_part = cg ? reinterpret_cast<double*>(b + ocp) : nullptr;
     pl->mask = reinterpret_cast<uint8_t*>(b + omk);
@@ -654,7 +711,14 @@ int admm_deconv_warm_start(admm_plan_t plan, const float* x0, const float* d0, v
             CK(cudaMemcpyAsync(plan->xstage, x0, n * sizeof(float), cudaMemcpyHostToDevice, s));
             src = plan->xstage;
         }
-        CK(launch_warm_rows(W, src, plan->Sb, H, plan->Wp, ctx->tw, s));
+        if (plan->gen) {
+            const float2* twW = nullptr;
+            const int r = gen_twiddles(ctx, W, &twW);
+            if (r != ADMM_OK) return r;
+            CK(launch_gen_warm_rows(W, H, plan->Wp, src, plan->Sb, twW, s));
+        } else {
+            CK(launch_warm_rows(W, src, plan->Sb, H, plan->Wp, ctx->tw, s));
+        }
         ++g_launches;
     } else {
         CK(cudaMemsetAsync(plan->Sb, 0, n / W * plan->Wp * sizeof(float4), s));
@@ -728,8 +792,16 @@ int admm_deconv_get_full_state(admm_plan_t plan, float* state, int* iters, void*
         CK(cudaMemcpyAsync(ctx->slot_map, ctx->h_active, sizeof(int), cudaMemcpyHostToDevice, s));
         CK(cudaMemcpyAsync(&plan->ctl->active, &one, sizeof(int), cudaMemcpyHostToDevice, s));
         const SlotTable sl{ctx->slot_map, ctx->queue, 1};
-        CK(launch_row_tail(plan->p.W, H, plan->Wp, ctx->desc, sl, 1, plan->levels,
-                           plan->p.reg != ADMM_REG_TV_CG, ctx->tw, s));
+        if (plan->gen) {
+            const float2* twW = nullptr;
+            rc = gen_twiddles(ctx, plan->p.W, &twW);
+            if (rc != ADMM_OK) return rc;
+            CK(launch_gen_tail(plan->p.W, H, plan->Wp, ctx->desc, sl, 1, plan->levels, !reg_tv_prior(plan->p.reg),
+                               twW, s));
+        } else {
+            CK(launch_row_tail(plan->p.W, H, plan->Wp, ctx->desc, sl, 1, plan->levels,
+                               plan->p.reg != ADMM_REG_TV_CG, ctx->tw, s));
+        }
         g_launches += 2;
         CK(cudaMemcpyAsync(&plan->ctl->active, &zero, sizeof(int), cudaMemcpyHostToDevice, s));
         CK(cudaStreamSynchronize(s));
@@ -792,6 +864,9 @@ struct GroupRun {
     int H = 0, W = 0, Wc = 0, Wp = 0, levels = 0;
     bool tv = true;              // the TV row phase (TV, anisotropic TV)
     bool cg = false;             // a Reeves-Sorel variant
+    bool gen = false;            // mixed-radix kernels (a side is not a power of two)
+    const float2* twH = nullptr; // ... their twiddle tables
+    const float2* twW = nullptr;
     int off = 0, count = 0, nslots = 0, max_iters = 0, qbase = 0;
     int gi = 0;                  // index of the class's n_active counter
     int R = 0, row_v = 0, col_v = 0, slot_ctas = 0, lanes = 0;
@@ -814,6 +889,9 @@ static cudaError_t launch_iteration(DeviceCtx* ctx, const GroupRun& g, int l, cu
     if (g.cg)
         return launch_cg_iteration(g.W, g.H, g.Wc, g.Wp, desc, sl, g.L.slots[l], g.levels, g.reg == ADMM_REG_TV_CG,
                                    g.col_fn, ctx->tw, ctx->n_active + g.gi, s);
+    if (g.gen)
+        return launch_gen_iteration(g.W, g.H, g.Wc, g.Wp, desc, sl, g.L.slots[l], g.reg, g.levels, g.twH, g.twW,
+                                    ctx->n_active + g.gi, s);
     cudaError_t e = g.col_fn(desc, sl, g.L.slots[l], g.Wc, g.Wp, ctx->tw, s);
     if (e != cudaSuccess) return e;
     int* nact = ctx->n_active + g.gi;
@@ -825,6 +903,7 @@ static cudaError_t launch_iteration(DeviceCtx* ctx, const GroupRun& g, int l, cu
 // kernels one iteration of a lane launches
 static int launches_per_iteration(const GroupRun& g) {
     if (g.cg) return g.reg == ADMM_REG_TV_CG ? 7 : 8;
+    if (g.gen) return reg_tv_prior(g.reg) ? 4 : 5;
     return g.tv ? 2 : 5;
 }
 
@@ -936,13 +1015,19 @@ static int solve_all_impl(DeviceCtx* ctx, const std::vector<std::vector<int>>& c
         g.levels = p0->levels;
         g.tv = p0->fam == ADMM_REG_TV;
         g.cg = reg_cg(p0->p.reg);
+        g.gen = p0->gen;
         g.reg = p0->p.reg;
+        if (g.gen) {
+            int r = gen_twiddles(ctx, g.H, &g.twH);
+            if (r == ADMM_OK) r = gen_twiddles(ctx, g.W, &g.twW);
+            if (r != ADMM_OK) return r;
+        }
         g.R = p0->R;
         g.row_v = p0->row_v;
         g.col_v = p0->col_v;
         g.slot_ctas = p0->slot_ctas;
         g.lanes = p0->lanes;
-        {
+        if (!g.gen) {
             const ColVariant* cv = nullptr;
             col_variants(g.H, &cv);
             g.col_fn = cv[g.col_v].fn;
@@ -986,7 +1071,10 @@ static int solve_all_impl(DeviceCtx* ctx, const std::vector<std::vector<int>>& c
                 if (pl->d2 != pl->d1 + n) return ADMM_ECUDA;
                 int r = ws_predict_start(g.H, g.W, pl->ybar, pl->mask, pl->xstage, pl->d1, s);
                 if (r != ADMM_OK) return r;
-                CK(launch_warm_rows(g.W, pl->xstage, pl->Sb, g.H, pl->Wp, ctx->tw, s));
+                if (pl->gen)
+                    CK(launch_gen_warm_rows(g.W, g.H, pl->Wp, pl->xstage, pl->Sb, g.twW, s));
+                else
+                    CK(launch_warm_rows(g.W, pl->xstage, pl->Sb, g.H, pl->Wp, ctx->tw, s));
                 ++g_launches;
                 pl->warm_mode = 1;
             }
@@ -1073,7 +1161,7 @@ static int solve_all_impl(DeviceCtx* ctx, const std::vector<std::vector<int>>& c
                         const ProbDesc* dl = ctx->desc + g.L.off[l];
                         const SlotTable sl = lane_slots(ctx, g, l);
                         int* nact = ctx->n_active + g.gi;
-                        if (g.cg) {
+                        if (g.cg || g.gen) {
                             // (timed as one row-side interval when profiling)
                             if (prof) {
                                 int r = prof_event(nev++, s);
@@ -1127,9 +1215,10 @@ static int solve_all_impl(DeviceCtx* ctx, const std::vector<std::vector<int>>& c
         live.swap(next);
     }
     for (const GroupRun& g : groups) {
-        if (g.cg) {
+        if (g.cg || g.gen) {
             // the Reeves-Sorel variants form x = x~ + alpha v on the row side
-            // (the last column-phase output is v): it is in the scratch plane
+            // (the last column-phase output is v), and the mixed-radix chain
+            // writes x on its row side: it is in the scratch plane
             for (int t = g.off; t < g.off + g.count; ++t)
                 CK(cudaMemcpyAsync(ctx->h_xptr[t], plans[order[t]]->work, (size_t)g.H * g.W * sizeof(float),
                                    cudaMemcpyDeviceToDevice, s));

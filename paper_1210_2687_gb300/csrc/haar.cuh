@@ -34,6 +34,10 @@ namespace admm {
 constexpr int kMaxHaarLevels = 4;
 constexpr int kHaarTile = 32;
 
+// periodic index for x in [-n, 2n): sides are multiples of 32, not
+// necessarily powers of two (exact generic domains)
+__device__ __forceinline__ int hwrap(int x, int n) { return x < 0 ? x + n : (x >= n ? x - n : x); }
+
 // rows per CTA of the two row kernels: one row transform per thread group
 inline int haar_rows_per_cta(int W) { return kThreads / (W / 8); }
 inline int haar_row_strip(int W) { return haar_rows_per_cta(W); }
@@ -199,11 +203,11 @@ haar_analysis(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W, in
     constexpr int CH = XA / 4;
     for (int e = tid; e < XR * CH; e += kThreads) {
         const int rr = e / CH, ch = e - rr * CH;
-        const float* src = P.work + (size_t)((R0 + rr) & (H - 1)) * W + ((C0 + 4 * ch) & (W - 1));
+        const float* src = P.work + (size_t)hwrap(R0 + rr, H) * W + hwrap(C0 + 4 * ch, W);
         cp_async16(Ain + rr * XA + 4 * ch, src);
         if (FS && !first) {
             // w = gamma P^T zeta2 of the previous iteration on the same region (zero at the start)
-            const float* wsrc = P.work + 2 * n + (size_t)((R0 + rr) & (H - 1)) * W + ((C0 + 4 * ch) & (W - 1));
+            const float* wsrc = P.work + 2 * n + (size_t)hwrap(R0 + rr, H) * W + hwrap(C0 + 4 * ch, W);
             cp_async16(Aout + rr * XA + 4 * ch, wsrc);
         }
     }
@@ -443,7 +447,7 @@ haar_synthesis(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W) {
             for (int e = tid; e < BR * CH; e += kThreads) {
                 const int rr = e / CH, ch = e - rr * CH;
                 cp_async16(Zl + (j * BR + rr) * XS + 4 * ch,
-                           band + (size_t)((R0 + rr - BO) & (H - 1)) * W + ((C0 - 16 + 4 * ch) & (W - 1)));
+                           band + (size_t)hwrap(R0 + rr - BO, H) * W + hwrap(C0 - 16 + 4 * ch, W));
             }
         }
         cp_async_commit();
@@ -453,7 +457,7 @@ haar_synthesis(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W) {
         for (int e = tid; e < AR * CH; e += kThreads) {
             const int rr = e / CH, ch = e - rr * CH;
             cp_async16(At + rr * XS + 4 * ch,
-                       band + (size_t)((R0 + rr - HALO) & (H - 1)) * W + ((C0 - 16 + 4 * ch) & (W - 1)));
+                       band + (size_t)hwrap(R0 + rr - HALO, H) * W + hwrap(C0 - 16 + 4 * ch, W));
         }
     }
     request(L - 1);

@@ -365,14 +365,16 @@ def config4_psf(g: np.random.Generator):
     return psf_motion(float(length), angle, length + 1 - length % 2), "motion"
 
 
-def config4_problem(g: np.random.Generator, size: int | None = None, reg: str | None = None) -> Problem:
+def config4_problem(g: np.random.Generator, size: int | None = None, reg: str | None = None,
+                    pad: bool = True) -> Problem:
     """One problem of the batched uneven workload: side uniform over
     CONFIG4_SIZES, kernel from config4_psf, missing fraction U[0, 0.5],
     TV or 4-level Haar with probability 1/2, BSNR 40 dB, textured image.
-    A side that is not a power of two is solved on the padded domain
-    fft_domain(side): the image sits in the top-left corner and the padding
-    is unobserved; meta["window"] is the image's side, x_true is zero on the
-    padding."""
+    With pad = True a side that is not a power of two is embedded in the
+    padded domain fft_domain(side): the image sits in the top-left corner and
+    the padding is unobserved; meta["window"] is the image's side, x_true is
+    zero on the padding. With pad = False the problem keeps its own side
+    (solved on the exact domain). The random draws do not depend on pad."""
     if size is None:
         size = CONFIG4_SIZES[int(g.integers(len(CONFIG4_SIZES)))]
     psf, family = config4_psf(g)
@@ -382,7 +384,7 @@ def config4_problem(g: np.random.Generator, size: int | None = None, reg: str | 
     x = textured_image(size, size, g)
     keep = (g.uniform(0.0, 1.0, size=(size, size)) >= missing).astype(np.uint8)
     ybar, mask, sigma = observe(x, psf, keep, 40.0, g, fast=True)
-    N = fft_domain(size)
+    N = fft_domain(size) if pad else size
     if N != size:
         xp = np.zeros((N, N))
         yp = np.zeros((N, N))
@@ -398,14 +400,15 @@ def config4_problem(g: np.random.Generator, size: int | None = None, reg: str | 
                     "window": size, "family": family, "missing": missing})
 
 
-def config4_batch(seed: int = 0, count: int = 256, sizes=None) -> list:
+def config4_batch(seed: int = 0, count: int = 256, sizes=None, pad: bool = True) -> list:
     """``count`` problems of the batched uneven workload from one stream;
-    ``sizes`` (optional) restricts the side law to a subset."""
+    ``sizes`` (optional) restricts the side law to a subset; ``pad`` as in
+    config4_problem."""
     g = rng(seed)
     out = []
     for _ in range(count):
         size = None
         if sizes is not None:
             size = sizes[int(g.integers(len(sizes)))]
-        out.append(config4_problem(g, size))
+        out.append(config4_problem(g, size, pad=pad))
     return out

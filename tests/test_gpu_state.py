@@ -120,14 +120,29 @@ def test_restart_resumes_the_oracle_sequence(ad):
     b.close()
 
 
+def _next_side(n):
+    """The next side the library solves on exactly: m 2^k with m in {1, 3, 5},
+    a multiple of 32, at least 64."""
+    m = max(n, 64)
+    while True:
+        odd = m
+        while odd % 2 == 0:
+            odd //= 2
+        if m % 32 == 0 and odd in (1, 3, 5):
+            return m
+        m += 1
+
+
 @pytest.mark.parametrize("reg,H,W,psf_fn,keep", [
     ("tv", 200, 300, lambda: S.psf_gaussian(7, 1.5), 0.7),
+    ("tv", 130, 700, lambda: S.psf_box(5), 0.8),
     ("haar", 96, 100, lambda: S.psf_box(5), None),
     ("tv", 384, 384, lambda: S.psf_motion(11.0, 60.0, 11), 0.8),
 ])
 def test_padded_domain_matches_oracle(ad, reg, H, W, psf_fn, keep):
-    """ADMM_PAD_NEXT: the plan's domain is the next supported size; the
-    oracle solves the same problem on that domain (the image top-left, the
+    """ADMM_PAD_NEXT: the plan's domain is the next supported size (200 ->
+    256, 300 -> 320, 130 -> 160, 700 -> 768, 100 -> 128; 96 and 384 are
+    solved as they are); the oracle solves the same problem on that domain (the image top-left, the
     rest never observed; the valid region is the image's own); x is returned
     on the caller's H x W window and matches the oracle there."""
     import torch
@@ -138,7 +153,7 @@ def test_padded_domain_matches_oracle(ad, reg, H, W, psf_fn, keep):
     iters = 40
     plan = ad.Plan(H, W, psf, lam, mu1, mu2, reg, max_iters=iters, pad=True)
     Hd, Wd = plan.domain()
-    assert (Hd, Wd) == (S.fft_domain(H), S.fft_domain(W))
+    assert (Hd, Wd) == (_next_side(H), _next_side(W))
     yb = np.zeros((Hd, Wd))
     mk = np.zeros((Hd, Wd), dtype=np.uint8)
     yb[:H, :W] = ybar
