@@ -56,7 +56,7 @@ import numpy as np
 __all__ = [
     "dft2", "idft2", "psf_otf", "A_fft", "At_fft", "A_direct", "At_direct",
     "Dh", "Dv", "DhT", "DvT", "tv_denominator_diag",
-    "haar_analysis", "haar_synthesis", "haar_nbands",
+    "haar_analysis", "haar_synthesis", "haar_nbands", "haar_band_spectra",
     "soft", "vsoft", "mask_prox",
     "objective_tv", "objective_haar", "objective_synthesis",
     "State", "tvmd_step", "famd_step", "fsmd_step", "tvcg_step", "facg_step", "solve",
@@ -351,14 +351,46 @@ def tvmd_step(st: State, ybar, mask, psf, lam, mu1, mu2, otf=None, denom=None, a
     return State(u1, d1, np.stack([uh, uv]), d2, x, st.k + 1)
 
 
-def famd_step(st: State, ybar, mask, psf, lam, mu1, mu2, levels=4, otf=None, ll_free=False) -> State:
+def haar_band_spectra(H, W, levels=4):
+    """|DFT|^2 of each band's filter: the bands of P applied to a unit
+    impulse at (0, 0), transformed (P_b is a periodic convolution, so
+    P_b^T P_b is the circulant with this diagonal). Shape (3 L + 1, H, W)."""
+    e = np.zeros((H, W))
+    e[0, 0] = 1.0
+    return np.stack([np.abs(dft2(b)) ** 2 for b in haar_analysis(e, levels)])
+
+
+def famd_step(st: State, ybar, mask, psf, lam, mu1, mu2, levels=4, otf=None, ll_free=False,
+              mu_bands=None) -> State:
     """One iteration of FA-MD: Algorithm 2 with H1 = A, H2 = P, line 4 from
     eqs. invAnalysis/invAnalysisp1 and line 6 from eqs. prox_g_1_uBC and prox_g_2.
     ll_free=True leaves the last (low-low) band unpenalised: its prox is the
-    identity (a threshold of zero)."""
+    identity (a threshold of zero). mu_bands (3 L + 1 values, optional): one
+    penalty per band instead of mu2 for all, i.e. Algorithm 2 with J = 3 L + 2
+    functions and the block-diagonal Upsilon of eq. diagonal_penalty; line 4 is
+    then eq. quadratic_problem, (mu1 A^T A + sum_b mu_b P_b^T P_b)^{-1}
+    (mu1 A^T zeta1 + sum_b mu_b P_b^T zeta_b), diagonal in the DFT domain since
+    each P_b is a convolution, and band b is thresholded at lambda / mu_b."""
     H, W = ybar.shape
     if otf is None:
         otf = psf_otf(psf, H, W)
+    if mu_bands is not None:
+        mub = np.asarray(mu_bands, dtype=np.float64)
+        gb = mub / mu1
+        zeta1 = st.u1 + st.d1
+        zeta2 = st.u2 + st.d2
+        rhs = np.real(idft2(np.conj(otf) * dft2(zeta1))) + haar_synthesis(gb[:, None, None] * zeta2, levels)
+        denom = np.abs(otf) ** 2 + np.tensordot(gb, haar_band_spectra(H, W, levels), axes=1)
+        x = np.real(idft2(dft2(rhs) / denom))
+        ax = np.real(idft2(otf * dft2(x)))
+        u1 = mask_prox(ax - st.d1, ybar, mask, mu1)
+        d1 = st.d1 - (ax - u1)
+        c = haar_analysis(x, levels)
+        u2 = soft(c - st.d2, (lam / mub)[:, None, None])
+        if ll_free:
+            u2[-1] = c[-1] - st.d2[-1]
+        d2 = st.d2 - (c - u2)
+        return State(u1, d1, u2, d2, x, st.k + 1)
     gam = mu2 / mu1
     # line 3
     zeta1 = st.u1 + st.d1
@@ -528,7 +560,7 @@ class SolveResult:
 
 
 def solve(ybar, mask, psf, lam, mu1, mu2, reg="tv", iters=200, stop="iters", tol=0.0,
-          levels=4, state0: State | None = None, record=False) -> SolveResult:
+          levels=4, state0: State | None = None, record=False, mu_bands=None) -> SolveResult:
     """Run TV-MD or FA-MD from ``state0`` (default: u0 = d0 = 0) until ``iters``
     iterations or, for stop = 'rel_x' / 'rel_obj', until the relative change of
     x / of the objective between consecutive iterations is below ``tol``.
@@ -568,7 +600,7 @@ def solve(ybar, mask, psf, lam, mu1, mu2, reg="tv", iters=200, stop="iters", tol
         elif fs:
             st = fsmd_step(st, ybar, mask, psf, lam, mu1, mu2, levels, otf)
         else:
-            st = famd_step(st, ybar, mask, psf, lam, mu1, mu2, levels, otf, ll_free)
+            st = famd_step(st, ybar, mask, psf, lam, mu1, mu2, levels, otf, ll_free, mu_bands)
         nx = float(np.linalg.norm(st.x))
         rel_x = float(np.linalg.norm(st.x - x_prev)) / nx if nx > 0 else float("inf")
         f = obj_fn(st.x) if (stop == "rel_obj" or record) else float("nan")

@@ -966,3 +966,77 @@ def test_tvcg_kkt_certificate_at_convergence():
     stat = mu1 * O.At_direct(np.where(obs, st.d1, 0.0), h) + mu2 * (O.DhT(st.d2[0]) + O.DvT(st.d2[1]))
     assert np.abs(stat).max() < 1e-8
     assert np.max(np.hypot(mu2 * st.d2[0], mu2 * st.d2[1])) <= lam * (1 + 1e-8)
+
+
+# ----------------------------------------------------------------------------
+# one penalty per band (Sec. II, eq. diagonal_penalty: a positive diagonal
+# Upsilon, block-constant over each function g_j)
+# ----------------------------------------------------------------------------
+def _band_mu(levels=4, mu2=0.05):
+    return mu2 * np.array([0.5, 2.0, 1.0] * levels + [0.25])[: 3 * levels + 1]
+
+
+def test_band_spectra_closed_form_and_parseval():
+    """|H_b|^2 of the a-trous Haar bands: with c_j = cos^2(pi k 2^j / N) and
+    s_j = sin^2(pi k 2^j / N) per axis, level j's bands are prod_{i<j} c_i(r)
+    c_i(c) times c_j(r) s_j(c), s_j(r) c_j(c), s_j(r) s_j(c) (rows low /
+    columns high, rows high / columns low, both high), the last band
+    prod_{i<L} c_i(r) c_i(c); they sum to 1 (P^T P = I)."""
+    H, W, L = 16, 24, 3
+    S_ = O.haar_band_spectra(H, W, L)
+    kr = np.arange(H)[:, None] * np.ones((1, W))
+    kc = np.ones((H, 1)) * np.arange(W)[None, :]
+    cr = lambda j: np.cos(np.pi * kr * 2 ** j / H) ** 2
+    sr = lambda j: np.sin(np.pi * kr * 2 ** j / H) ** 2
+    cc = lambda j: np.cos(np.pi * kc * 2 ** j / W) ** 2
+    sc = lambda j: np.sin(np.pi * kc * 2 ** j / W) ** 2
+    chain = np.ones((H, W))
+    for j in range(L):
+        np.testing.assert_allclose(S_[3 * j], chain * cr(j) * sc(j), atol=1e-13)
+        np.testing.assert_allclose(S_[3 * j + 1], chain * sr(j) * cc(j), atol=1e-13)
+        np.testing.assert_allclose(S_[3 * j + 2], chain * sr(j) * sc(j), atol=1e-13)
+        chain = chain * cr(j) * cc(j)
+    np.testing.assert_allclose(S_[3 * L], chain, atol=1e-13)
+    np.testing.assert_allclose(S_.sum(axis=0), 1.0, atol=1e-13)
+
+
+def test_band_penalty_xstep_dense_solve():
+    """eq. quadratic_problem with Upsilon = diag(mu1 I, mu_1 I, ..., mu_13 I)
+    (one penalty per band) against a dense solve built from the dense band
+    matrices; and the band thresholds lambda / mu_b."""
+    H = W = 8
+    g, h, st, ybar, mask = _one_step_inputs("haar")
+    mu1, lam = 0.6, 0.02
+    mub = _band_mu(4, 0.09)
+    A = _dense(lambda v: O.A_direct(v, h), H, W)
+    Pb = [_dense(lambda v, b=b: O.haar_analysis(v, 4)[b], H, W) for b in range(13)]
+    Mat = mu1 * A.T @ A + sum(mub[b] * Pb[b].T @ Pb[b] for b in range(13))
+    z2 = st.u2 + st.d2
+    rhs = mu1 * A.T @ (st.u1 + st.d1).ravel() + sum(mub[b] * Pb[b].T @ z2[b].ravel() for b in range(13))
+    x_dense = np.linalg.solve(Mat, rhs)
+    nxt = O.famd_step(st, ybar, mask, h, lam, mu1, 0.09, 4, mu_bands=mub)
+    np.testing.assert_allclose(nxt.x.ravel(), x_dense, atol=1e-11)
+    c = np.stack([(Pb[b] @ x_dense).reshape(H, W) for b in range(13)])
+    for b in range(13):
+        s_ = c[b] - st.d2[b]
+        np.testing.assert_allclose(nxt.u2[b], np.sign(s_) * np.maximum(np.abs(s_) - lam / mub[b], 0), atol=1e-11)
+    # uniform band penalties give the scalar-penalty step exactly
+    a = O.famd_step(st, ybar, mask, h, lam, mu1, 0.09, 4)
+    b_ = O.famd_step(st, ybar, mask, h, lam, mu1, 0.09, 4, mu_bands=np.full(13, 0.09))
+    np.testing.assert_allclose(b_.x, a.x, atol=1e-12)
+    np.testing.assert_allclose(b_.d2, a.d2, atol=1e-12)
+
+
+def test_band_penalties_reach_the_same_optimum():
+    """Theorem 1 holds for any positive penalties: with one penalty per band
+    the iteration converges to the same minimiser of eq.
+    unconstrained_analysis_uBC as with a single mu2."""
+    x, h, ybar, mask = _small_problem(seed=66)
+    lam = 2e-3
+    mu1, mu2 = 0.1, 10 * lam
+    a = O.solve(ybar, mask, h, lam, mu1, mu2, "haar", iters=30000, stop="rel_x", tol=1e-13)
+    b = O.solve(ybar, mask, h, lam, mu1, mu2, "haar", iters=30000, stop="rel_x", tol=1e-13,
+                mu_bands=_band_mu(4, mu2))
+    assert a.converged and b.converged
+    np.testing.assert_allclose(b.objective, a.objective, rtol=1e-7)
+    assert np.linalg.norm(b.x - a.x) <= 1e-4 * np.linalg.norm(a.x)
