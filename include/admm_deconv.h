@@ -132,6 +132,17 @@ typedef struct {
                               and columns never observed (more unknown boundary, Sec.
                               IV-A: the domain only has to hold the image and the kernel
                               support); y, mask and x_out keep the caller's H x W      */
+    const float* band_mu;  /* HOST pointer or NULL. ADMM_REG_HAAR and ADMM_REG_HAAR_LL_FREE
+                              only: 3 L + 1 penalties, one per frame band, in the band order
+                              of admm_deconv_get_state, replacing mu2 for that band. This is
+                              Algorithm 2 with one function per band and the positive
+                              diagonal Upsilon of eq. diagonal_penalty (Sec. II): the
+                              x-step becomes (mu1 A^T A + sum_b mu_b P_b^T P_b)^{-1}
+                              (mu1 A^T zeta1 + sum_b mu_b P_b^T zeta_b), still diagonal in
+                              the DFT domain because each band is a convolution, and band b
+                              is thresholded at lambda / mu_b. The minimiser is the same
+                              (Theorem 1); only the speed changes. Each value finite and
+                              > 0; copied during admm_deconv_plan. NULL: mu2 for every band */
 } admm_params_t;
 
 #define ADMM_PAD_EXACT 0

@@ -71,7 +71,8 @@ class admm_params_t(ctypes.Structure):
                 ("reg", ctypes.c_int), ("haar_levels", ctypes.c_int),
                 ("stop", ctypes.c_int), ("tol", ctypes.c_double),
                 ("max_iters", ctypes.c_int), ("check_every", ctypes.c_int),
-                ("raw_mask", ctypes.c_int), ("fft_pad_policy", ctypes.c_int)]
+                ("raw_mask", ctypes.c_int), ("fft_pad_policy", ctypes.c_int),
+                ("band_mu", ctypes.POINTER(ctypes.c_float))]
 
 
 class admm_result_t(ctypes.Structure):
@@ -512,7 +513,7 @@ class Plan:
     """Owns one admm_plan_t. psf: 2-D array with odd sides (host)."""
 
     def __init__(self, H, W, psf, lam, mu1=0.0, mu2=0.0, reg="tv", levels=4, stop="iters",
-                 tol=0.0, max_iters=200, check_every=1, raw_mask=False, pad=False, stream=None):
+                 tol=0.0, max_iters=200, check_every=1, raw_mask=False, pad=False, band_mu=None, stream=None):
         k = np.ascontiguousarray(np.asarray(psf, dtype=np.float32))
         self._psf = k
         p = admm_params_t()
@@ -529,6 +530,9 @@ class Plan:
         p.check_every = int(check_every)
         p.raw_mask = int(bool(raw_mask))
         p.fft_pad_policy = ADMM_PAD_NEXT if pad else ADMM_PAD_EXACT
+        if band_mu is not None:
+            self._band_mu = np.ascontiguousarray(np.asarray(band_mu, dtype=np.float32))
+            p.band_mu = self._band_mu.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
         self.params = p
         self.H, self.W = p.H, p.W
         self.handle = admm_deconv_plan(p, stream)

@@ -52,6 +52,7 @@ bool alloc_fault_fire() {
 struct admm_plan_s {
     admm_params_t p{};
     std::vector<float> psf;
+    std::vector<float> band_mu;  // one penalty per frame band (empty: mu2 for all)
     int device = 0;
     int Wc = 0, Wp = 0, cb = 0, R = 0, n_strips = 0, n_slots = 0, nb = 0, levels = 0;
     int row_v = 0, col_v = 0, slot_ctas = 0, lanes = 0;   // launch configuration (tuning table at plan time)
@@ -473,6 +474,11 @@ ProbDesc make_desc(const admm_plan_s* pl) {
     d.warm = pl->warm_mode;
     d.ll_free = pl->p.reg == ADMM_REG_HAAR_LL_FREE ? 1 : 0;
     d.tol = pl->p.tol;
+    for (int b = 0; b < 13; ++b) {
+        const bool per = b < (int)pl->band_mu.size();
+        d.band_tau[b] = per ? (float)((double)pl->lam / (double)pl->band_mu[b]) : d.tau;
+        d.band_zs[b] = per ? (float)((double)pl->band_mu[b] / (double)pl->mu2) : 1.0f;
+    }
     return d;
 }
 
@@ -539,12 +545,21 @@ int admm_deconv_plan(admm_plan_t* out, const admm_params_t* p, void* stream) {
     if (mu2 <= 0.f) mu2 = 10.f * p->lambda;
     if (mu1 <= 0.f) mu1 = std::min(1.f, 3.f * mu2);
     if (!(mu1 > 0.f) || !(mu2 > 0.f)) return ADMM_EINVAL;
+    // one penalty per frame band (eq. diagonal_penalty): FA-MD and its
+    // low-low-free variant only
+    if (p->band_mu) {
+        if (p->reg != ADMM_REG_HAAR && p->reg != ADMM_REG_HAAR_LL_FREE) return ADMM_EINVAL;
+        for (int b = 0; b < 3 * levels + 1; ++b)
+            if (!(p->band_mu[b] > 0.f) || !std::isfinite(p->band_mu[b])) return ADMM_EINVAL;
+    }
 
     std::lock_guard<std::mutex> lk(g_mutex);
     admm_plan_s* pl = new (std::nothrow) admm_plan_s();
     if (!pl) return ADMM_ENOMEM;
     pl->p = *p;
     pl->p.psf = nullptr;
+    pl->p.band_mu = nullptr;
+    if (p->band_mu) pl->band_mu.assign(p->band_mu, p->band_mu + 3 * levels + 1);
     pl->Hu = p->H;
     pl->Wu = p->W;
     pl->p.H = Hd;
@@ -652,9 +667,14 @@ int admm_deconv_plan(admm_plan_t* out, const admm_params_t* p, void* stream) {
         if (cudaMemcpyAsync(pl->psf_dev, pl->psf.data(), pl->psf.size() * sizeof(float), cudaMemcpyHostToDevice, s) !=
             cudaSuccess) { rc = ADMM_ECUDA; break; }
         const int tot = H * pl->Wc;
+        BandWeights bw{};
+        if (!pl->band_mu.empty()) {
+            bw.levels = levels;
+            for (int b = 0; b < 3 * levels + 1; ++b) bw.g[b] = (double)pl->band_mu[b] / (double)mu1;
+        }
         spectra_kernel<<<(tot + 255) / 256, 256, 0, s>>>(pl->lamT, pl->kT, pl->psf_dev, p->psf_h, p->psf_w, H, W,
                                                          pl->Wc, tvp ? 0 : 1,
-                                                         (double)mu2 / (double)mu1);
+                                                         (double)mu2 / (double)mu1, bw);
         if (cudaGetLastError() != cudaSuccess) { rc = ADMM_ECUDA; break; }
         if (cudaStreamSynchronize(s) != cudaSuccess) { rc = ADMM_ECUDA; break; }
     } while (0);
@@ -1711,7 +1731,7 @@ extern "C" int admm_deconv_solve_noalloc(const admm_params_t* p, const float* y,
     CKQ(cudaMemcpyAsync(psf_dev, p->psf, (size_t)p->psf_h * p->psf_w * sizeof(float), cudaMemcpyHostToDevice, s));
     const int tot = H * L.Wc;
     spectra_kernel<<<(tot + 255) / 256, 256, 0, s>>>(lamT, kT, psf_dev, p->psf_h, p->psf_w, H, W, L.Wc, 0,
-                                                     (double)mu2 / (double)mu1);
+                                                     (double)mu2 / (double)mu1, BandWeights{});
     CKQ(cudaGetLastError());
     prepare_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(ybar, mk, y, mask, H, W, H, W, p->psf_h / 2,
                                                                p->psf_w / 2, p->raw_mask, ctl);

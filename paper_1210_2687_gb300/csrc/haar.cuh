@@ -196,7 +196,6 @@ haar_analysis(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W, in
     const size_t n = (size_t)H * W;
     float* __restrict__ d2io = P.d2 + ((k + 1) & 1) * P.d2_stride;   // previous d2 in, zeta2 out
     float* __restrict__ d2out = P.d2 + (k & 1) * P.d2_stride;
-    const float tau = P.tau;
 
     // x on [0, T + HALO) x [0, T + 16) with periodic wrap, 16-byte copies (the
     // tile origin is a multiple of 32 columns)
@@ -301,9 +300,10 @@ haar_analysis(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W, in
             for (int j = 0; j < 3; ++j) {
                 if (FS) cb[j] += zprev[j][e];                   // theta = P v + zeta2
                 const float sv = cb[j] - dold[j][e];
-                const float u = soft_thresh(sv, tau);           // eq. soft
+                const float u = soft_thresh(sv, P.band_tau[3 * lvl + j]);   // eq. soft
                 nd4[j][e] = u - sv;                             // d2 - (c - u2)
-                z4[j][e] = u + nd4[j][e];                       // zeta2 = u2 + d2
+                // zeta2 = u2 + d2, times gamma_b / gamma for the synthesis
+                z4[j][e] = (u + nd4[j][e]) * P.band_zs[3 * lvl + j];
                 if (nobj) {
                     l1.add(fabsf(cb[j]));
                     const float e2 = nd4[j][e] - dold[j][e];    // d2 part of d_k - d_{k-1}
@@ -347,7 +347,7 @@ haar_analysis(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W, in
     // the last low-low band a_L on the tile (threshold 0 when it is unpenalised)
     {
         const bool ll_free = P.ll_free != 0;
-        const float tau_ll = ll_free ? 0.f : tau;
+        const float tau_ll = ll_free ? 0.f : P.band_tau[3 * L];
         const float4 dv = first ? make_float4(0.f, 0.f, 0.f, 0.f)
                                 : *reinterpret_cast<const float4*>(d2s + ((L - 1) & 1) * C::SLOT + 3 * T * T +
                                                                    orow * T + ocol);
@@ -365,7 +365,7 @@ haar_analysis(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W, in
             const float sv = cb[e] - dold[e];
             const float u = soft_thresh(sv, tau_ll);
             nd[e] = u - sv;
-            z[e] = u + nd[e];
+            z[e] = (u + nd[e]) * P.band_zs[3 * L];
             if (nobj) {
                 if (!ll_free) l1.add(fabsf(cb[e]));
                 const float e2 = nd[e] - dold[e];

@@ -95,6 +95,12 @@ struct ProbDesc {
                               // usual); 0: u0 = d0 = 0
     int ll_free;              // frame prior: 1 = the last low-low band unpenalised
     double tol;
+    // frame prior, per band b (3 L + 1 bands): the threshold lambda / mu_b and
+    // the factor gamma_b / gamma applied to zeta_b before the synthesis, so that
+    // w = gamma P^T (scaled zeta2) = sum_b gamma_b P_b^T zeta_b (one penalty per
+    // band, eq. diagonal_penalty); tau and 1 when every band has mu2
+    float band_tau[13];
+    float band_zs[13];
 };
 
 // Continuous batching: a launch covers gridDim.y slots; slot s works on

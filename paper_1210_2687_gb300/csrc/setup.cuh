@@ -12,9 +12,32 @@ namespace admm {
 // kc = 0..W/2, and the diagonal inverse of eq. fast_inversion (TV, divided by
 // mu1) or eq. invAnalysisp1 (frame), times 1/(HW). FP64, rounded once to FP32.
 // ---------------------------------------------------------------------------
+// Per-band weights gamma_b = mu_b / mu1 of the frame prior (one penalty per
+// band, eq. diagonal_penalty): sum_b gamma_b |H_b|^2 replaces gamma in the
+// denominator, |H_b|^2 the power spectrum of band b of the a-trous Haar frame
+// (per axis cos^2 / sin^2 of pi k 2^j / N for the low / high filter of
+// level j, the low filters of the earlier levels in front). levels = 0: off.
+struct BandWeights {
+    double g[13];
+    int levels;
+};
+
+__device__ __forceinline__ double band_weighted_power(const BandWeights& bw, int kr, int kc, int H, int W) {
+    double acc = 0.0, chain = 1.0;
+    for (int j = 0; j < bw.levels; ++j) {
+        const long long mr = ((long long)kr << j) % H, mc = ((long long)kc << j) % W;
+        const double cr = cospi((double)mr / (double)H), cc = cospi((double)mc / (double)W);
+        const double lr = cr * cr, lc = cc * cc;          // low-pass power of level j per axis
+        const double hr = 1.0 - lr, hc = 1.0 - lc;        // high-pass power
+        acc += chain * (bw.g[3 * j] * lr * hc + bw.g[3 * j + 1] * hr * lc + bw.g[3 * j + 2] * hr * hc);
+        chain *= lr * lc;
+    }
+    return acc + bw.g[3 * bw.levels] * chain;
+}
+
 __global__ void spectra_kernel(float2* __restrict__ lamT, float* __restrict__ kT,
                                const float* __restrict__ psf, int ph, int pw, int H, int W, int Wc,
-                               int reg, double gamma) {
+                               int reg, double gamma, BandWeights bw) {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= H * Wc) return;
     const int kc = idx / H, kr = idx % H;
@@ -47,6 +70,8 @@ __global__ void spectra_kernel(float2* __restrict__ lamT, float* __restrict__ kT
     if (reg == 0) {
         double sh = sinpi((double)kc / (double)W), sv = sinpi((double)kr / (double)H);
         den += gamma * 4.0 * (sh * sh + sv * sv);
+    } else if (bw.levels > 0) {
+        den += band_weighted_power(bw, kr, kc, H, W);
     } else {
         den += gamma;
     }

@@ -51,10 +51,11 @@ def test_strerror_and_version(ad):
 
 
 def test_struct_layout_matches_header(ad):
-    # admm_params_t: 4 ints, pointer, 3 floats, 3 ints, double, 4 ints
-    assert ctypes.sizeof(ad.admm_params_t) == 72
+    # admm_params_t: 4 ints, pointer, 3 floats, 3 ints, double, 4 ints, pointer
+    assert ctypes.sizeof(ad.admm_params_t) == 80
     assert ad.admm_params_t.tol.offset == 48
     assert ad.admm_params_t.fft_pad_policy.offset == 68
+    assert ad.admm_params_t.band_mu.offset == 72
     assert ctypes.sizeof(ad.admm_result_t) == 64
     assert ad.admm_result_t.primal_res.offset == 56
 
@@ -72,6 +73,11 @@ def test_struct_layout_matches_header(ad):
     (dict(psf=np.ones((65, 65)) / 65 ** 2), -1),   # larger than supported kernel side
     (dict(H=4096, pad=True), -4), (dict(W=2049, pad=True), -4),   # no supported size to pad to
     (dict(H=100, W=100, psf=np.ones((101, 3)) / 303, pad=True), -1),   # kernel taller than the image
+    (dict(reg="tv", band_mu=np.ones(13)), -1),                 # per-band penalties: frame priors only
+    (dict(reg="haar", band_mu=np.r_[np.ones(12), 0.0]), -1),   # a penalty that is not > 0
+    (dict(reg="haar", band_mu=np.r_[np.ones(12), np.nan]), -1),
+    (dict(reg="haar_synthesis", band_mu=np.ones(13)), -1),
+    (dict(reg="haar_cg", band_mu=np.ones(13)), -1),
 ])
 def test_plan_rejects_invalid_parameters_on_host(ad, change, code):
     kw = dict(H=64, W=64, psf=np.ones((3, 3)) / 9, lam=1e-3, reg="tv", levels=4, stop="iters",
