@@ -239,6 +239,208 @@ conv3x3_kernel(const bf16* __restrict__ in, const bf16* __restrict__ wpk, const 
 }
 
 // ---------------------------------------------------------------------------
+// 3 x 3 convolution with 32 output channels on the fifth-generation tensor
+// cores (tcgen05.mma, accumulator in tensor memory).
+//
+// A CTA of four warps walks output tiles of 8 x 16 pixels (M = 128, one
+// accumulator row per pixel: tile row oy, column ox at M row 8 oy + ox), N =
+// 32 output channels, K = 9 taps x CIN input channels. Operands sit in shared
+// memory in the no-swizzle K-major layout of 8-row x 16-byte core matrices:
+//   A: the 10 x 18 halo tile as [CIN/8][180 halo pixels][8 channels]; the A
+//      matrix of tap (dy, dx) starts at halo pixel 10 dy + dx, its 8-row
+//      groups (one tile row each) are 10 pixels = 160 B apart and its K
+//      chunks 180 x 16 B apart, so no im2col copy is needed;
+//   B: the weights as [tap][CIN/8][32 output channels][8].
+// One thread issues the 9 x CIN/16 MMAs of a tile (K = 16 each) and commits
+// them to an mbarrier; the four warps wait (bounded), read their 32 lanes of
+// the accumulator (tcgen05.ld) and apply bias + ReLU (forward) or the ReLU
+// gate of the layer below (input gradient), storing NHWC BF16.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t sh_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// shared-memory matrix descriptor: start, leading (K) and stride (M/N) byte
+// offsets >> 4, descriptor version 1, no swizzle
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// instruction descriptor, kind::f16: F32 accumulator, BF16 A and B, both
+// K-major, N = 32, M = 128
+constexpr uint32_t kIdescM128N32 = (1u << 4) | (1u << 7) | (1u << 10) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
+
+__device__ __forceinline__ void umma_f16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accum) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(idesc), "r"(accum)
+        : "memory");
+}
+
+__device__ __forceinline__ unsigned long long gtimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// wait for phase `parity` of the mbarrier, at most about a second
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t parity) {
+    const unsigned long long t0 = gtimer_ns();
+    for (;;) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(done)
+            : "r"(mbar), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (gtimer_ns() - t0 > 1000000000ull) return false;
+        __nanosleep(32);
+    }
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_shared() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// 32 consecutive FP32 columns of this thread's accumulator lane
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n\t"
+        "tcgen05.wait::ld.sync.aligned;\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+constexpr int kTcTW = 8, kTcTH = 16;                 // output tile (M = 128)
+constexpr int kTcHW = kTcTW + 2, kTcHH = kTcTH + 2;  // halo tile
+constexpr int kTcNP = kTcHW * kTcHH;                 // 180 halo pixels
+
+// in: [img][H][W][CIN]; wpk: [9][32][CIN]; out: bf16 [img][H][W][32];
+// MODE kModeReluBf16 (bias, ReLU) or kModeGateBf16 (gate [img][H][W][32]);
+// err: set to 1 if a wait ran out (the CTA then stops)
+template <int CIN, int MODE>
+__global__ void __launch_bounds__(128)
+conv3x3_tc(const bf16* __restrict__ in, const bf16* __restrict__ wpk, const float* __restrict__ bias,
+           bf16* __restrict__ out, const bf16* __restrict__ gate, int H, int W, int count, int* __restrict__ err) {
+    constexpr int COUT = 32, CH = CIN / 8;
+    static_assert(CIN == 16 || CIN == 32, "input channels");
+    __shared__ __align__(128) unsigned char smA[CH * kTcNP * 16];
+    __shared__ __align__(128) unsigned char smW[9 * CH * COUT * 16];
+    __shared__ __align__(8) unsigned long long mbar;
+    __shared__ uint32_t tmem_base;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    for (int e = tid; e < 9 * COUT * CH; e += 128) {
+        const int tc = e / CH, k = e - tc * CH;       // tc = tap * 32 + output channel
+        const int tap = tc / COUT, co = tc - tap * COUT;
+        cp_async16(smW + ((tap * CH + k) * COUT + co) * 16, wpk + (size_t)tc * CIN + k * 8);
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" ::"r"(sh_addr(&tmem_base))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sh_addr(&mbar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    cp_async_wait_all();
+    fence_async_shared();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;
+    const uint32_t aBase = sh_addr(smA), wBase = sh_addr(smW), mb = sh_addr(&mbar);
+    const int tiles_x = W / kTcTW, per_img = tiles_x * (H / kTcTH);
+    const int ntiles = per_img * count;
+    uint32_t phase = 0;
+    bool ok = true;
+    for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+        const int img = tile / per_img, rem = tile - img * per_img;
+        const int y0 = (rem / tiles_x) * kTcTH, x0 = (rem % tiles_x) * kTcTW;
+        const size_t ibase = (size_t)img * H * W;
+        for (int e = tid; e < kTcNP * CH; e += 128) {
+            const int p = e / CH, k = e - p * CH;
+            const int hy = p / kTcHW, hx = p - hy * kTcHW;
+            const int gy = y0 - 1 + hy, gx = x0 - 1 + hx;
+            unsigned char* dst = smA + (k * kTcNP + p) * 16;
+            if (gy >= 0 && gy < H && gx >= 0 && gx < W)
+                cp_async16(dst, in + (ibase + (size_t)gy * W + gx) * CIN + k * 8);
+            else
+                *reinterpret_cast<uint4*>(dst) = make_uint4(0u, 0u, 0u, 0u);
+        }
+        cp_async_wait_all();
+        fence_async_shared();        // the halo (generic proxy) is visible to the tensor cores
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+#pragma unroll
+            for (int tap = 0; tap < 9; ++tap) {
+                const int dy = tap / 3, dx = tap - 3 * (tap / 3);
+#pragma unroll
+                for (int j = 0; j < CH / 2; ++j) {
+                    const uint64_t a = umma_desc(aBase + (2 * j * kTcNP + dy * kTcHW + dx) * 16, kTcNP * 16, kTcHW * 16);
+                    const uint64_t b = umma_desc(wBase + (tap * CH + 2 * j) * COUT * 16, COUT * 16, 8 * 16);
+                    umma_f16(tmem, a, b, kIdescM128N32, (tap | j) != 0 ? 1u : 0u);
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mb)
+                         : "memory");
+        }
+        const bool got = mbar_wait_bounded(mb, phase);
+        phase ^= 1u;
+        ok = __syncthreads_and(got) != 0;
+        if (!ok) break;
+        tc_fence_after();
+        float v[32];
+        tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16), v);
+        const int oy = 4 * warp + (lane >> 3), ox = lane & 7;
+        const size_t px = ibase + (size_t)(y0 + oy) * W + (x0 + ox);
+        uint32_t pk[16];
+        if (MODE == kModeReluBf16) {
+#pragma unroll
+            for (int c = 0; c < 16; ++c)
+                pk[c] = pack2(__float2bfloat16(fmaxf(v[2 * c] + bias[2 * c], 0.f)),
+                              __float2bfloat16(fmaxf(v[2 * c + 1] + bias[2 * c + 1], 0.f)));
+        } else {
+            const uint4* gp = reinterpret_cast<const uint4*>(gate + px * COUT);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const uint4 gv = gp[q];
+                const uint32_t gw[4] = {gv.x, gv.y, gv.z, gv.w};
+#pragma unroll
+                for (int h = 0; h < 4; ++h) {
+                    const int c = 8 * q + 2 * h;
+                    const float g0 = __bfloat162float(__ushort_as_bfloat16((unsigned short)(gw[h] & 0xFFFFu)));
+                    const float g1 = __bfloat162float(__ushort_as_bfloat16((unsigned short)(gw[h] >> 16)));
+                    pk[4 * q + h] = pack2(__float2bfloat16(g0 > 0.f ? v[c] : 0.f),
+                                          __float2bfloat16(g1 > 0.f ? v[c + 1] : 0.f));
+                }
+            }
+        }
+        uint4* op = reinterpret_cast<uint4*>(out + px * COUT);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) op[q] = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
+        tc_fence_before();
+        __syncthreads();             // the halo buffer and the accumulator are free for the next tile
+    }
+    if (!ok && tid == 0) atomicExch(err, 1);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tmem) : "memory");
+}
+
+// ---------------------------------------------------------------------------
 // weight and bias gradients of one layer
 // a: [img][H][W][CIN] (layer input), g: [img][H][W][COUT] (gradient in the
 // layer's pre-activation output). dw: FP32 [cout_real][cin_real][9] slice of
@@ -450,6 +652,17 @@ cudaError_t conv(const bf16* in, const bf16* w, const float* bias, int cout_real
     return cudaGetLastError();
 }
 
+// 32-output-channel layers on tcgen05 (persistent CTAs over 8 x 16 tiles)
+template <int CIN, int MODE>
+cudaError_t conv_tc(const bf16* in, const bf16* w, const float* bias, bf16* out, const bf16* gate, int count, int H,
+                    int W, int sms, int* err, cudaStream_t s) {
+    const int ntiles = (W / kTcTW) * (H / kTcTH) * count;
+    const int grid = std::min(ntiles, 6 * sms);
+    conv3x3_tc<CIN, MODE><<<grid, 128, 0, s>>>(in, w, bias, out, gate, H, W, count, err);
+    ++g_cnn_launches;
+    return cudaGetLastError();
+}
+
 template <int CIN, int COUT>
 cudaError_t wgrad(const bf16* a, const bf16* g, float* dw, float* db, int cin_real, int cout_real, int count,
                   int H, int W, int sms, cudaStream_t s) {
@@ -482,6 +695,7 @@ struct admm_cnn_s {
     bf16* gout = nullptr;          // output gradient, 16 channels
     double* loss = nullptr;        // device accumulator
     double* h_loss = nullptr;      // pinned
+    int* tc_err = nullptr;         // set by a tensor-core convolution whose bounded wait ran out
     std::vector<void*> allocs;
 };
 
@@ -536,9 +750,9 @@ int forward(admm_cnn_s* n, int count, int H, int W, const float* ybar, const uin
         } else {
             bf16* dst = keep ? n->act[l] : n->act[l & 1];
             if (l == 0)
-                CKC((conv<16, 32, kModeReluBf16>(cur, n->wf[l], b, kWidth, dst, nullptr, count, H, W, s)));
+                CKC((conv_tc<16, kModeReluBf16>(cur, n->wf[l], b, dst, nullptr, count, H, W, n->sms, n->tc_err, s)));
             else
-                CKC((conv<32, 32, kModeReluBf16>(cur, n->wf[l], b, kWidth, dst, nullptr, count, H, W, s)));
+                CKC((conv_tc<32, kModeReluBf16>(cur, n->wf[l], b, dst, nullptr, count, H, W, n->sms, n->tc_err, s)));
             cur = dst;
         }
     }
@@ -568,9 +782,9 @@ int backward(admm_cnn_s* n, int count, int H, int W, const float* target, const 
         if (l == 0) break;
         bf16* gnext = n->gbuf[l & 1];
         if (l == kLayers - 1)
-            CKC((conv<16, 32, kModeGateBf16>(g, n->wb[l], nullptr, kWidth, gnext, a_in, count, H, W, s)));
+            CKC((conv_tc<16, kModeGateBf16>(g, n->wb[l], nullptr, gnext, a_in, count, H, W, n->sms, n->tc_err, s)));
         else
-            CKC((conv<32, 32, kModeGateBf16>(g, n->wb[l], nullptr, kWidth, gnext, a_in, count, H, W, s)));
+            CKC((conv_tc<32, kModeGateBf16>(g, n->wb[l], nullptr, gnext, a_in, count, H, W, n->sms, n->tc_err, s)));
         g = gnext;
     }
     return ADMM_OK;
@@ -611,7 +825,8 @@ int admm_cnn_create(admm_cnn_t* out, long long max_pixels, int training) {
     n->training = training != 0;
     const long long P = param_count();
     const size_t px = (size_t)max_pixels;
-    if ((rc = dalloc(n, &n->params, P)) || (rc = dalloc(n, &n->a0, px * 16)) || (rc = dalloc(n, &n->out, px * 4)))
+    if ((rc = dalloc(n, &n->params, P)) || (rc = dalloc(n, &n->a0, px * 16)) || (rc = dalloc(n, &n->out, px * 4)) ||
+        (rc = dalloc(n, &n->tc_err, 1)))
         return bail(rc);
     for (int l = 0; l < kLayers; ++l) {
         if ((rc = dalloc(n, &n->wf[l], (size_t)9 * layer_coutp(l) * layer_cinp(l)))) return bail(rc);
@@ -631,6 +846,7 @@ int admm_cnn_create(admm_cnn_t* out, long long max_pixels, int training) {
         }
     }
     if (cudaMemset(n->params, 0, P * sizeof(float)) != cudaSuccess) return bail(ADMM_ECUDA);
+    if (cudaMemset(n->tc_err, 0, sizeof(int)) != cudaSuccess) return bail(ADMM_ECUDA);
     if (pack_all(n, nullptr) != ADMM_OK || cudaDeviceSynchronize() != cudaSuccess) return bail(ADMM_ECUDA);
     *out = n;
     return ADMM_OK;
