@@ -534,6 +534,10 @@ def cg_secondary(ad, torch, stream, batch=64):
 
 
 CNN_FLOP_PER_PX = 2 * 9 * (2 * 32 + 6 * 32 * 32 + 32 * 4)   # eight 3x3 convolutions
+# HBM bytes per pixel of one forward: the input kernel (M^T y 4 + mask 1 in,
+# 16 BF16 channels out 32), layer 0 (32 in, 64 out), six 32-channel layers
+# (64 in, 64 out each), the last layer (64 in, 4 FP32 channels out 16)
+CNN_BYTES_PER_PX = (4 + 1 + 32) + (32 + 64) + 6 * (64 + 64) + (64 + 16)
 
 
 def warm_secondary(ad, torch, stream, count=32):
@@ -563,8 +567,13 @@ def warm_secondary(ad, torch, stream, count=32):
     sec = e0.elapsed_time(e1) * 1e-3 / reps
     tflops = CNN_FLOP_PER_PX * n * 512 * 512 / sec / 1e12
     net.close()
+    peak, _ = read_peak()
+    hbm = CNN_BYTES_PER_PX * n * 512 * 512 / sec / 1e9
     ev["cnn_forward"] = {"images": n, "size": 512, "ms": sec * 1e3, "tflops": tflops,
-                         "note": "mma.sync BF16 m16n8k16, FP32 accumulate; 9 launches per forward"}
+                         "hbm_gbs": hbm, "hbm_frac": hbm / peak, "bytes_per_px": CNN_BYTES_PER_PX,
+                         "note": "hidden 32-channel layers: tcgen05.mma (TMEM accumulator) fed by TMA halo "
+                                 "tiles, double-buffered; last layer mma.sync; 9 launches per forward; each "
+                                 "layer reads and writes its activations in HBM (memory-bound)"}
     ev["trained"] = {k: meta[k] for k in ("count", "epochs", "lr", "train_s", "steps") if k in meta}
     return ev
 

@@ -24,6 +24,8 @@
 // activation tiles are stored channel-major in shared memory so the MMA
 // operands are pixel pairs of one channel; the CTA's FP32 partial sums go to
 // global memory with one atomic add per element at the end.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -251,10 +253,16 @@ conv3x3_kernel(const bf16* __restrict__ in, const bf16* __restrict__ wpk, const 
 //      groups (one tile row each) are 10 pixels = 160 B apart and its K
 //      chunks 180 x 16 B apart, so no im2col copy is needed;
 //   B: the weights as [tap][CIN/8][32 output channels][8].
-// One thread issues the 9 x CIN/16 MMAs of a tile (K = 16 each) and commits
-// them to an mbarrier; the four warps wait (bounded), read their 32 lanes of
-// the accumulator (tcgen05.ld) and apply bias + ReLU (forward) or the ReLU
-// gate of the layer below (input gradient), storing NHWC BF16.
+// The halo tile arrives by one TMA copy (cp.async.bulk.tensor, a 5-D view of
+// the NHWC activations whose innermost box dimension is 8 channels and whose
+// outermost is the 16-byte channel chunk, so the box lands in shared memory
+// already in the A layout; rows and columns outside the image read as zero),
+// double-buffered: the next tile's copy is in flight while the current tile
+// is multiplied and written out. One thread issues the 9 x CIN/16 MMAs of a
+// tile (K = 16 each) and commits them to an mbarrier; the four warps wait
+// (bounded), read their 32 lanes of the accumulator (tcgen05.ld) and apply
+// bias + ReLU (forward) or the ReLU gate of the layer below (input gradient),
+// storing NHWC BF16.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t sh_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -325,18 +333,18 @@ constexpr int kTcTW = 8, kTcTH = 16;                 // output tile (M = 128)
 constexpr int kTcHW = kTcTW + 2, kTcHH = kTcTH + 2;  // halo tile
 constexpr int kTcNP = kTcHW * kTcHH;                 // 180 halo pixels
 
-// in: [img][H][W][CIN]; wpk: [9][32][CIN]; out: bf16 [img][H][W][32];
-// MODE kModeReluBf16 (bias, ReLU) or kModeGateBf16 (gate [img][H][W][32]);
-// err: set to 1 if a wait ran out (the CTA then stops)
+// tin: TMA view of the input [img][H][W][CIN] (see conv_tc); wpk: [9][32][CIN];
+// out: bf16 [img][H][W][32]; MODE kModeReluBf16 (bias, ReLU) or kModeGateBf16
+// (gate [img][H][W][32]); err: set to 1 if a wait ran out (the CTA then stops)
 template <int CIN, int MODE>
 __global__ void __launch_bounds__(128)
-conv3x3_tc(const bf16* __restrict__ in, const bf16* __restrict__ wpk, const float* __restrict__ bias,
+conv3x3_tc(const __grid_constant__ CUtensorMap tin, const bf16* __restrict__ wpk, const float* __restrict__ bias,
            bf16* __restrict__ out, const bf16* __restrict__ gate, int H, int W, int count, int* __restrict__ err) {
-    constexpr int COUT = 32, CH = CIN / 8;
+    constexpr int COUT = 32, CH = CIN / 8, ABYTES = CH * kTcNP * 16;
     static_assert(CIN == 16 || CIN == 32, "input channels");
-    __shared__ __align__(128) unsigned char smA[CH * kTcNP * 16];
+    __shared__ __align__(128) unsigned char smA[2][ABYTES];
     __shared__ __align__(128) unsigned char smW[9 * CH * COUT * 16];
-    __shared__ __align__(8) unsigned long long mbar;
+    __shared__ __align__(8) unsigned long long bars[3];   // 0, 1: halo of buffer 0 / 1 landed; 2: MMAs done
     __shared__ uint32_t tmem_base;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     for (int e = tid; e < 9 * COUT * CH; e += 128) {
@@ -349,40 +357,53 @@ conv3x3_tc(const bf16* __restrict__ in, const bf16* __restrict__ wpk, const floa
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
+    const int tiles_x = W / kTcTW, per_img = tiles_x * (H / kTcTH);
+    const int ntiles = per_img * count;
+    const uint64_t tmap = reinterpret_cast<uint64_t>(&tin);
+    // one TMA copy of tile t's halo into buffer b
+    auto issue = [&](int t, int b) {
+        const int img = t / per_img, rem = t - img * per_img;
+        const int y0 = (rem / tiles_x) * kTcTH, x0 = (rem % tiles_x) * kTcTW;
+        const uint32_t bar = sh_addr(&bars[b]);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(ABYTES) : "memory");
+        asm volatile(
+            "cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, "
+            "%6}], [%7];" ::"r"(sh_addr(smA[b])),
+            "l"(tmap), "r"(0), "r"(x0 - 1), "r"(y0 - 1), "r"(img), "r"(0), "r"(bar)
+            : "memory");
+    };
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sh_addr(&mbar)) : "memory");
+        for (int i = 0; i < 3; ++i)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sh_addr(&bars[i])) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(tmap) : "memory");
+        if ((int)blockIdx.x < ntiles) issue(blockIdx.x, 0);
     }
     cp_async_wait_all();
-    fence_async_shared();
+    fence_async_shared();        // the weights (generic proxy) are visible to the tensor cores
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_base;
-    const uint32_t aBase = sh_addr(smA), wBase = sh_addr(smW), mb = sh_addr(&mbar);
-    const int tiles_x = W / kTcTW, per_img = tiles_x * (H / kTcTH);
-    const int ntiles = per_img * count;
-    uint32_t phase = 0;
+    const uint32_t wBase = sh_addr(smW), mb = sh_addr(&bars[2]);
+    uint32_t full_phase0 = 0, full_phase1 = 0, mma_phase = 0;
     bool ok = true;
-    for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+    int it = 0;
+    for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++it) {
+        const int buf = it & 1;
+        // the other buffer was last read by the previous tile's MMAs, which are complete
+        if (tid == 0 && tile + (int)gridDim.x < ntiles) issue(tile + gridDim.x, buf ^ 1);
+        const uint32_t fp = buf ? full_phase1 : full_phase0;
+        bool got = mbar_wait_bounded(sh_addr(&bars[buf]), fp);
+        if (buf) full_phase1 ^= 1u; else full_phase0 ^= 1u;
+        ok = __syncthreads_and(got) != 0;
+        if (!ok) break;
         const int img = tile / per_img, rem = tile - img * per_img;
         const int y0 = (rem / tiles_x) * kTcTH, x0 = (rem % tiles_x) * kTcTW;
         const size_t ibase = (size_t)img * H * W;
-        for (int e = tid; e < kTcNP * CH; e += 128) {
-            const int p = e / CH, k = e - p * CH;
-            const int hy = p / kTcHW, hx = p - hy * kTcHW;
-            const int gy = y0 - 1 + hy, gx = x0 - 1 + hx;
-            unsigned char* dst = smA + (k * kTcNP + p) * 16;
-            if (gy >= 0 && gy < H && gx >= 0 && gx < W)
-                cp_async16(dst, in + (ibase + (size_t)gy * W + gx) * CIN + k * 8);
-            else
-                *reinterpret_cast<uint4*>(dst) = make_uint4(0u, 0u, 0u, 0u);
-        }
-        cp_async_wait_all();
-        fence_async_shared();        // the halo (generic proxy) is visible to the tensor cores
-        __syncthreads();
         if (tid == 0) {
             tc_fence_after();
+            const uint32_t aBase = sh_addr(smA[buf]);
 #pragma unroll
             for (int tap = 0; tap < 9; ++tap) {
                 const int dy = tap / 3, dx = tap - 3 * (tap / 3);
@@ -396,8 +417,8 @@ conv3x3_tc(const bf16* __restrict__ in, const bf16* __restrict__ wpk, const floa
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mb)
                          : "memory");
         }
-        const bool got = mbar_wait_bounded(mb, phase);
-        phase ^= 1u;
+        got = mbar_wait_bounded(mb, mma_phase);
+        mma_phase ^= 1u;
         ok = __syncthreads_and(got) != 0;
         if (!ok) break;
         tc_fence_after();
@@ -431,7 +452,7 @@ conv3x3_tc(const bf16* __restrict__ in, const bf16* __restrict__ wpk, const floa
 #pragma unroll
         for (int q = 0; q < 4; ++q) op[q] = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
         tc_fence_before();
-        __syncthreads();             // the halo buffer and the accumulator are free for the next tile
+        __syncthreads();             // the accumulator is free for the next tile's MMAs
     }
     if (!ok && tid == 0) atomicExch(err, 1);
     tc_fence_before();
@@ -652,13 +673,42 @@ cudaError_t conv(const bf16* in, const bf16* w, const float* bias, int cout_real
     return cudaGetLastError();
 }
 
-// 32-output-channel layers on tcgen05 (persistent CTAs over 8 x 16 tiles)
+// the driver's tensor-map encoder (through the runtime, no link to the driver library)
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+// 32-output-channel layers on tcgen05 (persistent CTAs over 8 x 16 tiles).
+// The input is viewed by TMA as a 5-D tensor (8 channels, W, H, images,
+// CIN / 8 chunks) with strides (2, 2 CIN, 2 CIN W, 2 CIN W H, 16) bytes, and
+// a box of (8, 10, 18, 1, CIN / 8): one halo tile per copy, laid out in
+// shared memory as [chunk][halo row][halo column][8 channels].
 template <int CIN, int MODE>
 cudaError_t conv_tc(const bf16* in, const bf16* w, const float* bias, bf16* out, const bf16* gate, int count, int H,
                     int W, int sms, int* err, cudaStream_t s) {
+    const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return cudaErrorNotSupported;
+    CUtensorMap tm;
+    const cuuint64_t dims[5] = {8, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)count, (cuuint64_t)(CIN / 8)};
+    const cuuint64_t strides[4] = {(cuuint64_t)CIN * 2, (cuuint64_t)W * CIN * 2, (cuuint64_t)H * W * CIN * 2, 16};
+    const cuuint32_t box[5] = {8, (cuuint32_t)kTcHW, (cuuint32_t)kTcHH, 1, (cuuint32_t)(CIN / 8)};
+    const cuuint32_t es[5] = {1, 1, 1, 1, 1};
+    if (enc(&tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<bf16*>(in), dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return cudaErrorInvalidValue;
     const int ntiles = (W / kTcTW) * (H / kTcTH) * count;
-    const int grid = std::min(ntiles, 6 * sms);
-    conv3x3_tc<CIN, MODE><<<grid, 128, 0, s>>>(in, w, bias, out, gate, H, W, count, err);
+    const int grid = std::min(ntiles, 5 * sms);
+    conv3x3_tc<CIN, MODE><<<grid, 128, 0, s>>>(tm, w, bias, out, gate, H, W, count, err);
     ++g_cnn_launches;
     return cudaGetLastError();
 }
