@@ -54,9 +54,10 @@ extern "C" {
                                         ADMM_PAD_EXACT), or a side above 2048              */
 #define ADMM_ENONFINITE          -5  /* an observed value or the iterate is NaN/Inf
                                         (divergence, Theorem 1)                            */
-#define ADMM_ETIMEOUT            -6  /* reserved for a bounded device wait that expires. No
-                                        call returns it today: no kernel of the solver waits
-                                        on a flag, a peer or a barrier that could stall     */
+#define ADMM_ETIMEOUT            -6  /* a bounded device wait expired: the TV row phase
+                                        waits (at most about a second) for the bulk copies
+                                        of its spectrum rows; a problem whose wait ran out
+                                        retires with this status (also in res->status)     */
 
 /* ---- enums -------------------------------------------------------------- */
 #define ADMM_REG_TV     0   /* isotropic TV, eq. unconstrained_TV_uBC            */
@@ -188,7 +189,8 @@ ADMM_API int admm_deconv_plan(admm_plan_t* out, const admm_params_t* p, void* st
  *   x_out  [out] H x W float32 estimate of the full image; device or host memory
  *   res    [out] host pointer, may be NULL
  * The solve starts from u0 = d0 = 0 (Algorithm 3 initialisation).
- * Errors: ADMM_EINVAL, ADMM_ECUDA, ADMM_ENONFINITE (also in res->status).
+ * Errors: ADMM_EINVAL, ADMM_ECUDA, ADMM_ENONFINITE or ADMM_ETIMEOUT (also in
+ * res->status).
  */
 ADMM_API int admm_deconv_solve(admm_plan_t plan, const float* y, const uint8_t* mask, float* x_out,
                       admm_result_t* res, void* stream);

@@ -118,6 +118,7 @@ struct SlotTable {
 // stop rules (values of ADMM_STOP_*)
 constexpr int kStopIters = 0, kStopRelX = 1, kStopRelObj = 2;
 constexpr int kStatusNonFinite = -5;
+constexpr int kStatusTimeout = -6;     // a bounded wait for an asynchronous copy ran out
 
 __device__ __forceinline__ bool is_check_iter(const ProbDesc& P, int k) {
     return P.stop == kStopRelX && ((k % P.check_every) == 0 || k == P.max_iters);
@@ -207,6 +208,39 @@ cudaError_t launch_chain(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t s
     cfg.attrs = at;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
+// Bulk asynchronous copies (the copy engine, cp.async.bulk) completing on an
+// mbarrier: `bytes` a multiple of 16, both addresses 16-byte aligned.
+__device__ __forceinline__ void mbar_init1(uint32_t bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+// wait for phase `parity` of an mbarrier, at most about a second; false if
+// the wait ran out (the caller then marks the problem and carries on)
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
+    const unsigned long long t0 = device_clock_ns();
+    for (;;) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (device_clock_ns() - t0 > 1000000000ull) return false;
+        __nanosleep(20);
+    }
 }
 
 // Bulk prefetch of a contiguous global range into L2 (no shared memory and no
@@ -610,7 +644,8 @@ __device__ void finish_iteration(const ProbDesc& P, int k, bool chk, bool nobj,
         }
     }
     if (tid != 0) return;
-    bool done = false, conv = false;
+    bool done = ctl->status != 0;     // a timed-out copy marked the problem
+    bool conv = false;
     if (nobj) {
         const double f = acc[0] + (double)P.lam * acc[1];
         if (!isfinite(f)) {
@@ -681,6 +716,7 @@ struct RowCfg {
     static constexpr int G = NT / FT;                              // row transforms in flight
     static_assert(G >= 1 && NT % FT == 0, "block too small for one row transform");
     static constexpr int NB = R + 2;                               // buffer rows
+    static constexpr int NR = (R + 2 + 2 * G - 1) / (2 * G);       // rounds of inverse transforms
     static constexpr int ROW = W + 2;                              // float2 per buffer row (raw spectrum fits)
     static constexpr int RAW = W / 2 + 1;                          // float4 per half-spectrum row
     static constexpr int NWARP = NT / 32;
@@ -789,19 +825,27 @@ row_phase_tv(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp, co
         for (int i = 0; i < R; ++i) prefetch_l2(P.ybar + (size_t)(r0 + i) * W, W * sizeof(float));
     }
     const int g = tid / C::FT, t = tid % C::FT;
-    constexpr int NR = (R + 2 + 2 * C::G - 1) / (2 * C::G);      // rounds of inverse transforms
-#pragma unroll
-    for (int rd = 0; rd < NR; ++rd) {
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int i = g + 2 * C::G * rd + h * C::G;
-            if (i < R + 2) {
-                const int q = (r0 - 1 + i + H) & (H - 1);
-                for (int kk = t; kk < C::RAW; kk += C::FT)
-                    cp_async16(reinterpret_cast<float4*>(buf + i * C::ROW) + kk, P.Sa + (size_t)q * Wp + kk);
+    constexpr int NR = C::NR;
+    // The half-spectrum rows go to shared memory by bulk copies (one per row,
+    // RAW float4 = the buffer row's bytes), issued by one thread; the rows of
+    // round rd of transform group g complete on mbarrier g NR + rd, so a
+    // round starts as soon as its own two rows have landed.
+    __shared__ __align__(8) unsigned long long spec_bar[C::G * C::NR];
+    if (tid == 0) {
+        for (int b = 0; b < C::G * NR; ++b) mbar_init1(smem_u32(&spec_bar[b]));
+        mbar_init_fence();
+        for (int gg = 0; gg < C::G; ++gg) {
+            for (int rd = 0; rd < NR; ++rd) {
+                const int i0 = gg + 2 * C::G * rd, i1 = i0 + C::G;
+                if (i0 >= R + 2) continue;
+                const uint32_t bar = smem_u32(&spec_bar[gg * NR + rd]);
+                mbar_expect_tx(bar, (uint32_t)((i1 < R + 2 ? 2 : 1) * C::RAW * sizeof(float4)));
+                for (int i = i0; i < R + 2 && i <= i1; i += C::G) {
+                    const int q = (r0 - 1 + i + H) & (H - 1);
+                    bulk_copy_g2s(buf + i * C::ROW, P.Sa + (size_t)q * Wp, C::RAW * sizeof(float4), bar);
+                }
             }
         }
-        cp_async_commit();
     }
 #pragma unroll
     for (int i = 0; i < D; ++i) issue(i);
@@ -813,10 +857,11 @@ row_phase_tv(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp, co
     // work between the group's barriers)
 #pragma unroll 1
     for (int rd = 0; rd < NR; ++rd) {
-        cp_async_wait_n(NR - 1 - rd + D);   // this round's rows (copied by this group) ...
-        group_sync<W>(g);                   // ... have landed for every thread of the group
         const int i = g + 2 * C::G * rd;
         if (i >= R + 2) continue;
+        // this round's rows have landed (every thread of the group waits itself)
+        if (!mbar_wait_bounded(smem_u32(&spec_bar[g * NR + rd]), 0u) && t == 0)
+            atomicExch(&ctl->status, kStatusTimeout);
         float2* row = buf + i * C::ROW;
         float2 v[8];
         load_row_xax<W>(v, reinterpret_cast<const float4*>(row), t);
