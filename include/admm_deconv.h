@@ -324,6 +324,13 @@ ADMM_API int admm_deconv_warm_start(admm_plan_t plan, const float* x0, const flo
                                   device or pinned-host allocation the library
                                   attempts from now on fail as if memory were
                                   exhausted (once); 0 (default) disarms it        */
+#define ADMM_OPT_TEST_STALL 3  /* test hook for the bounded device waits: value 1
+                                  makes the next solve's TV row phase (power-of-two
+                                  domains) withhold one of its bulk copies in every
+                                  CTA, so that the wait for it runs out (about a
+                                  second) and each problem retires with
+                                  ADMM_ETIMEOUT, the device staying usable; the
+                                  option then resets to 0                         */
 
 /*
  * admm_deconv_set_option -- set a library-wide option (see ADMM_OPT_*).

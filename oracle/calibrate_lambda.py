@@ -12,6 +12,11 @@ Conditions:
   batched uneven workload  (regularizer, blur family) in {TV, Haar}
                            x {box 13, Gaussian 17 sigma 2.5, motion 15 at 30},
                            25 % missing, 40 dB -> synth.CONFIG4_LAMBDA
+  frame workload           {analysis (FA-MD), synthesis (FS-MD)} prior, box 13,
+                           valid region only, 50 dB -> the lambda of each prior
+                           on the 1024^2 / 2048^2 frame workload (run with
+                           `frame` as the first argument; the synthesis prior
+                           converges slowly, so its cap is 20000 iterations)
 
 Run as a script (prints the tables). Test infrastructure: uses the oracle
 only."""
@@ -35,14 +40,15 @@ def _kernel(name):
 
 
 def _isnr(job):
-    table, key, kname, bsnr, missing, reg, lam, size = job
+    table, key, kname, bsnr, missing, reg, lam, size = job[:8]
+    cap = job[8] if len(job) > 8 else 3000
     psf = _kernel(kname)
     g = S.rng(1000)
     x = S.textured_image(size, size, g)
     keep = (g.uniform(0.0, 1.0, size=(size, size)) >= missing).astype("uint8")
     ybar, mask, _ = S.observe(x, psf, keep, float(bsnr), g, fast=True)
     mu1, mu2 = S.default_mu(lam)
-    r = O.solve(ybar, mask, psf, lam, mu1, mu2, reg, iters=3000, stop="rel_x", tol=1e-5)
+    r = O.solve(ybar, mask, psf, lam, mu1, mu2, reg, iters=cap, stop="rel_x", tol=1e-5)
     v = O.isnr(x, ybar, r.x, S.valid_mask(size, size, *psf.shape))
     return table, key, lam, v, r.iters, r.converged
 
@@ -60,10 +66,25 @@ def jobs(size):
     return out
 
 
-def main(size=128, procs=8):
+# the synthesis prior is the weaker of the two at equal lambda (its minimum over
+# the coefficients of one image is at most the analysis l1), so its grid goes
+# further up
+FS_GRID = GRID + [1e-2, 3e-2, 1e-1]
+
+
+def frame_jobs(size):
+    out = []
+    for reg, cap, grid in (("haar", 3000, GRID), ("haar_synthesis", 20000, FS_GRID)):
+        for lam in grid:
+            out.append(("FRAME_LAMBDA", (reg, "box13"), "box13", 50, 0.0, reg, lam, size, cap))
+    return out
+
+
+def main(size=128, procs=8, which="all"):
     best = {}
+    todo = frame_jobs(size) if which == "frame" else jobs(size)
     with mp.get_context("spawn").Pool(procs) as pool:
-        for table, key, lam, v, it, conv in pool.imap_unordered(_isnr, jobs(size)):
+        for table, key, lam, v, it, conv in pool.imap_unordered(_isnr, todo):
             print(table, key, lam, round(v, 3), it, "converged" if conv else "not converged", flush=True)
             k = (table, key)
             if conv and (k not in best or v > best[k][1]):
@@ -73,4 +94,8 @@ def main(size=128, procs=8):
 
 
 if __name__ == "__main__":
-    main(*(int(a) for a in sys.argv[1:]))
+    args = sys.argv[1:]
+    which = "frame" if args and args[0] == "frame" else "all"
+    if which == "frame":
+        args = args[1:]
+    main(*(int(a) for a in args), which=which)

@@ -61,6 +61,7 @@ EXPORTED = ("admm_deconv_plan", "admm_deconv_solve", "admm_deconv_solve_batch",
 
 ADMM_OPT_MAX_SLOTS = 1
 ADMM_OPT_FAIL_ALLOC = 2
+ADMM_OPT_TEST_STALL = 3
 
 
 class admm_params_t(ctypes.Structure):
@@ -218,7 +219,7 @@ def admm_deconv_solve(plan: int, y_ptr: int, mask_ptr: int | None, x_ptr: int, s
     res = admm_result_t()
     rc = lib.admm_deconv_solve(ctypes.c_void_p(plan), ctypes.c_void_p(y_ptr), ctypes.c_void_p(mask_ptr or 0),
                                ctypes.c_void_p(x_ptr), ctypes.byref(res), _stream(stream))
-    if rc != ADMM_OK and rc != ADMM_ENONFINITE:
+    if rc not in (ADMM_OK, ADMM_ENONFINITE, ADMM_ETIMEOUT):   # per-problem statuses: in the result
         raise AdmmError(rc, "admm_deconv_solve")
     return res
 
@@ -231,7 +232,7 @@ def admm_deconv_solve_batch(plans: Sequence[int], y_ptrs, mask_ptrs, x_ptrs, use
     X = (ctypes.c_void_p * n)(*x_ptrs)
     R = (admm_result_t * n)()
     rc = lib.admm_deconv_solve_batch(P, n, Y, M, X, R, int(bool(use_warmstart)), _stream(stream))
-    if rc != ADMM_OK and rc != ADMM_ENONFINITE:
+    if rc not in (ADMM_OK, ADMM_ENONFINITE, ADMM_ETIMEOUT):   # per-problem statuses: in the results
         raise AdmmError(rc, "admm_deconv_solve_batch")
     return list(R)
 

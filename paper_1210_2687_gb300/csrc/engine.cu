@@ -135,6 +135,7 @@ struct Profile {
 
 long long g_launches = 0;            // every kernel launched (under g_mutex)
 int g_max_slots = 0;                 // ADMM_OPT_MAX_SLOTS
+int g_test_stall = 0;                // ADMM_OPT_TEST_STALL: armed for the next solve
 
 int prof_event(size_t i, cudaStream_t s) {
     while (g_prof.ev.size() <= i) {
@@ -472,6 +473,7 @@ ProbDesc make_desc(const admm_plan_s* pl) {
     d.n_strips = pl->n_strips;
     d.n_slots = pl->n_slots;
     d.warm = pl->warm_mode;
+    d.test_stall = g_test_stall;
     d.ll_free = pl->p.reg == ADMM_REG_HAAR_LL_FREE ? 1 : 0;
     d.tol = pl->p.tol;
     for (int b = 0; b < 13; ++b) {
@@ -1124,6 +1126,7 @@ static int solve_all_impl(DeviceCtx* ctx, const std::vector<std::vector<int>>& c
     }
     const int total = (int)order.size();
     const int ng = (int)groups.size();
+    g_test_stall = 0;                    // the test hook serves one solve
     CK(cudaMemcpyAsync(ctx->desc, ctx->h_desc, total * sizeof(ProbDesc), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(ctx->xptr, ctx->h_xptr, total * sizeof(float*), cudaMemcpyHostToDevice, s));
     for (int gi = 0; gi < ng; ++gi) ctx->h_active[gi] = groups[gi].count;
@@ -1334,6 +1337,11 @@ int admm_deconv_set_option(int option, long long value) {
     if (option == ADMM_OPT_FAIL_ALLOC) {
         if (value < 0) return ADMM_EINVAL;
         g_fail_alloc.store(value);
+        return ADMM_OK;
+    }
+    if (option == ADMM_OPT_TEST_STALL) {
+        if (value != 0 && value != 1) return ADMM_EINVAL;
+        g_test_stall = (int)value;
         return ADMM_OK;
     }
     return ADMM_EINVAL;

@@ -101,6 +101,8 @@ struct ProbDesc {
     // band, eq. diagonal_penalty); tau and 1 when every band has mu2
     float band_tau[13];
     float band_zs[13];
+    int test_stall;           // test hook (ADMM_OPT_TEST_STALL): the TV row phase withholds
+                              // one of its bulk copies, so that its bounded wait runs out
 };
 
 // Continuous batching: a launch covers gridDim.y slots; slot s works on
@@ -840,6 +842,8 @@ row_phase_tv(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp, co
                 if (i0 >= R + 2) continue;
                 const uint32_t bar = smem_u32(&spec_bar[gg * NR + rd]);
                 mbar_expect_tx(bar, (uint32_t)((i1 < R + 2 ? 2 : 1) * C::RAW * sizeof(float4)));
+                // (test hook: the first round of group 0 gets no copy, its wait runs out)
+                if (P.test_stall && gg == 0 && rd == 0) continue;
                 for (int i = i0; i < R + 2 && i <= i1; i += C::G) {
                     const int q = (r0 - 1 + i + H) & (H - 1);
                     bulk_copy_g2s(buf + i * C::ROW, P.Sa + (size_t)q * Wp, C::RAW * sizeof(float4), bar);

@@ -143,6 +143,8 @@ def test_set_option_validates(ad):
     assert ad.lib.admm_deconv_set_option(ad.ADMM_OPT_MAX_SLOTS, -1) == ad.ADMM_EINVAL
     assert ad.lib.admm_deconv_set_option(ad.ADMM_OPT_FAIL_ALLOC, -1) == ad.ADMM_EINVAL
     assert ad.lib.admm_deconv_set_option(ad.ADMM_OPT_FAIL_ALLOC, 0) == ad.ADMM_OK
+    assert ad.lib.admm_deconv_set_option(ad.ADMM_OPT_TEST_STALL, 2) == ad.ADMM_EINVAL
+    assert ad.lib.admm_deconv_set_option(ad.ADMM_OPT_TEST_STALL, 0) == ad.ADMM_OK
     assert ad.lib.admm_deconv_set_option(99, 1) == ad.ADMM_EINVAL
     assert ad.lib.admm_deconv_set_option(ad.ADMM_OPT_MAX_SLOTS, 0) == ad.ADMM_OK
 

@@ -13,7 +13,10 @@
   admm_deconv_warm_start give by hand, bit for bit;
 * ADMM_OPT_FAIL_ALLOC: every allocation a plan, a batch or a network makes
   can fail, the call returns ADMM_ENOMEM, frees what it took, and the next
-  call works.
+  call works;
+* ADMM_OPT_TEST_STALL: a bulk copy the TV row phase waits for is withheld,
+  the bounded wait runs out, the problem retires with ADMM_ETIMEOUT, and the
+  device stays usable (no fault, no hang).
 """
 import numpy as np
 import pytest
@@ -225,6 +228,35 @@ def test_use_warmstart_equals_the_manual_learned_start(ad):
             p.close()
     finally:
         ad.admm_warmstart_load(None)
+
+
+def test_bounded_wait_runs_out_and_the_device_stays_usable(ad):
+    """The row phase's wait for its spectrum rows is bounded (about a second):
+    with one copy withheld the problem retires after its first iteration with
+    ADMM_ETIMEOUT (also the call's return code); the hook serves one solve,
+    and the next solves give the bits of an undisturbed plan."""
+    import torch
+    H = W = 128
+    psf = S.psf_box(7)
+    _, ybar, mask = _problem(H, W, psf, 0.8, 54)
+    lam = 1e-3
+    mu1, mu2 = S.default_mu(lam)
+    y = torch.from_numpy(ybar).cuda()
+    m = torch.from_numpy(mask).cuda()
+    plan = ad.Plan(H, W, psf, lam, mu1, mu2, "tv", max_iters=6)
+    x = torch.empty((H, W), dtype=torch.float32, device="cuda")
+    ad.admm_deconv_set_option(ad.ADMM_OPT_TEST_STALL, 1)
+    res = ad.solve(plan, y, m, x)
+    assert res.status == ad.ADMM_ETIMEOUT and res.iters == 1 and res.converged == 0
+    res = ad.solve(plan, y, m, x)
+    torch.cuda.synchronize()
+    assert res.status == ad.ADMM_OK and res.iters == 6
+    other = ad.Plan(H, W, psf, lam, mu1, mu2, "tv", max_iters=6)
+    x2 = torch.empty_like(x)
+    ad.solve(other, y, m, x2)
+    assert torch.equal(x, x2)
+    plan.close()
+    other.close()
 
 
 _FAULT_SCRIPT = r"""
