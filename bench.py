@@ -333,7 +333,7 @@ def frame_secondary(ad, torch, stream, args):
         tok = tok.strip()
         cases.append(("haar_synthesis", int(tok[2:])) if tok.startswith("fs") else ("haar", int(tok)))
     for reg, size in cases:
-        p = S.config3_problem(0, size)
+        p = S.config3_problem(0, size, lam=S.FS_FRAME_LAMBDA) if reg == "haar_synthesis" else S.config3_problem(0, size)
         n = size * size
         tune = tune_class(ad, torch, args, size, size, "haar", 4, problems=1)   # one image per solve
         plan = ad.Plan(size, size, p.psf, p.lam, p.mu1, p.mu2, reg, stop="iters", max_iters=FRAME_ITERS)

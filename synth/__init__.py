@@ -313,6 +313,16 @@ def config2_problem(seed: int = 0, blur: str = "gauss", bsnr: int = 40,
                    {"config": f"tv{size}_{blur}_bsnr{bsnr}_miss{missing}"})
 
 
+# lambda of the synthesis prior (FS-MD) on the frame workload, by the same rule
+# (best converged oracle ISNR) on one 128 x 128 calibration image of that
+# workload (13 x 13 box, valid region, 50 dB); oracle/calibrate_lambda.py,
+# run with `frame`. On that image every lambda from 1e-5 to 1e-1 leaves the
+# synthesis prior's ISNR below zero (best -1.45 dB at 3e-3); the analysis
+# prior's best converged value there is 3e-5 (14.0 dB), next to this
+# workload's 5e-5.
+FS_FRAME_LAMBDA = 3e-3
+
+
 def config3_problem(seed: int = 0, size: int = 1024, lam: float = 5e-5) -> Problem:
     """size^2 textured image, 13 x 13 uniform blur, valid region only,
     BSNR 50 dB, 4-level undecimated Haar analysis prior."""
