@@ -10,7 +10,7 @@ cudaError_t launch_cg_t(int H, int Wc, int Wp, const ProbDesc* d, SlotTable sl, 
                         ColLaunchFn col_fn, const float2* tw, int* n_active, cudaStream_t s) {
     constexpr int FT = W / 8, G = kThreads / FT;
     const size_t smem_row = (size_t)(G * W + W) * sizeof(float2) + 2 * (kThreads / 32) * sizeof(double);
-    const size_t smem_fwd = (size_t)(2 * G * W + W) * sizeof(float2);
+    constexpr size_t smem_fwd = haar_fwd_smem<W>();
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(cg_row_a<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_row);

@@ -91,7 +91,7 @@ std::mutex g_mutex;
 
 struct DeviceCtx {
     bool ready = false;
-    float2* tw = nullptr;            // exp(-2 pi i k / 2048), k < 2048
+    float2* tw = nullptr;            // exp(-2 pi i k / 2048), k < 2048, then the per-pass tables
     ProbDesc* desc = nullptr;        // descriptor table
     float** xptr = nullptr;          // finalize destinations
     int cap = 0;
@@ -207,15 +207,18 @@ int ensure_ctx(int dev, int count, DeviceCtx** out) {
     if (!c.ready) {
         // each resource is created once; a failed attempt resumes where it stopped
         if (!c.tw) {
-            std::vector<float2> tw(2048);
+            // the 2048-entry table, then the per-pass tables of every length
+            std::vector<float2> tw(kTwiddleEntries, make_float2(0.f, 0.f));
             for (int k = 0; k < 2048; ++k) {
                 // exact reduction: angle = 2 pi k / 2048
                 const double a = 2.0 * M_PI * (double)k / 2048.0;
                 tw[k] = make_float2((float)std::cos(a), (float)(-std::sin(a)));
             }
+            for (int lg = 6, slot = 1; lg <= 11; ++lg, ++slot)
+                fill_pass_table(1 << lg, tw.data(), tw.data() + 2048 * slot);
             float2* t = nullptr;
-            CK(dev_alloc(&t, 2048 * sizeof(float2)));
-            if (cudaMemcpy(t, tw.data(), 2048 * sizeof(float2), cudaMemcpyHostToDevice) != cudaSuccess) {
+            CK(dev_alloc(&t, kTwiddleEntries * sizeof(float2)));
+            if (cudaMemcpy(t, tw.data(), kTwiddleEntries * sizeof(float2), cudaMemcpyHostToDevice) != cudaSuccess) {
                 cudaFree(t);
                 return ADMM_ECUDA;
             }

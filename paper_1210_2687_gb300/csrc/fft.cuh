@@ -110,6 +110,36 @@ template <int N> struct TwiddleLayout {
     static_assert(SIZE <= N, "table fits a length-N buffer");
 };
 
+// The device twiddle buffer holds the 2048-entry table exp(-2 pi i k / 2048)
+// followed by the per-pass table of every length 64..2048, each in a slot of
+// 2048 entries (filled on the host from the same float values that
+// load_twiddles copies). Kernels whose shared memory is better spent on
+// concurrency read their transform's table there, through L1, instead of
+// staging it.
+constexpr int kTwiddleEntries = 2048 * 7;
+template <int N>
+__host__ __device__ constexpr int pass_table_offset() {
+    return 2048 * (1 + FftShape<N>::LOG - 6);
+}
+// host: the per-pass table of length n (a power of two, 64..2048) into dst
+// from the 2048-entry table tw2048 (the order load_twiddles produces)
+inline void fill_pass_table(int n, const float2* tw2048, float2* dst) {
+    int log = 0;
+    while ((1 << log) < n) ++log;
+    const int r0 = (log % 3 == 0) ? 8 : (log % 3 == 1) ? 2 : 4;
+    const int np8 = (log - (r0 == 8 ? 3 : r0 == 4 ? 2 : 1)) / 3;
+    int ns = r0, o = 0;
+    for (int p = 0; p < np8; ++p) {
+        const int step = n / (ns * 8);
+        for (int e = 0; e < 7 * ns; ++e) {
+            const int r = e / ns + 1, k = e - (r - 1) * ns;
+            dst[o + e] = tw2048[r * k * step * (2048 / n)];
+        }
+        o += 7 * ns;
+        ns *= 8;
+    }
+}
+
 // Fill the per-pass table from the 2048-entry table exp(-2 pi i k / 2048)
 // (threads tid of nthr cooperate; the caller synchronises afterwards).
 template <int N>

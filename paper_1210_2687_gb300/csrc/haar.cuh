@@ -44,6 +44,21 @@ inline int haar_row_strip(int W) { return haar_rows_per_cta(W); }
 inline int haar_num_row_ctas(int H, int W) { return H / haar_rows_per_cta(W); }
 inline int haar_num_tiles(int H, int W) { return (H / kHaarTile) * (W / kHaarTile); }
 
+// Rows of 1024 and more read their per-pass twiddle table from the device
+// buffer (through L1) instead of staging W float2 in shared memory: the
+// 8-16 KB go to more CTAs per SM on these latency-bound row kernels.
+template <int W> __host__ __device__ constexpr bool haar_tw_global() { return W >= 1024; }
+template <int W> __host__ __device__ constexpr int haar_tw_smem() { return haar_tw_global<W>() ? 0 : W; }
+template <int W> constexpr size_t haar_inv_smem() {
+    constexpr int G = kThreads / (W / 8);
+    return (size_t)(G * W + haar_tw_smem<W>()) * sizeof(float2) + 8 * kNumPartials * sizeof(double) +
+           (size_t)3 * G * W * sizeof(float);   // + staged d1, M^T y, x_prev
+}
+template <int W> constexpr size_t haar_fwd_smem() {
+    constexpr int G = kThreads / (W / 8);
+    return (size_t)(2 * G * W + haar_tw_smem<W>()) * sizeof(float2);   // two rows per group
+}
+
 // ---------------------------------------------------------------------------
 // inverse row DFT + mask prox + d1 dual (no halo: every row is owned)
 // ---------------------------------------------------------------------------
@@ -62,8 +77,9 @@ haar_row_inverse(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp
     const bool chk = is_check_iter(P, k), sprev = store_prev_iter(P, k), nobj = need_obj_iter(P, k);
     extern __shared__ __align__(16) float2 smem[];
     float2* buf = smem;
-    float2* tw = buf + G * ROW;
-    double* red = reinterpret_cast<double*>(tw + W);
+    float2* tws = buf + G * ROW;
+    const float2* tw = haar_tw_global<W>() ? tw_g + pass_table_offset<W>() : tws;
+    double* red = reinterpret_cast<double*>(tws + haar_tw_smem<W>());
     // per-pixel inputs of the prox (d1, M^T y, x_prev), staged by the thread
     // that uses them while the transform runs
     float* pre = reinterpret_cast<float*>(red + 8 * kNumPartials);
@@ -82,7 +98,7 @@ haar_row_inverse(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp
         if (chk && !first) cp_async4(pxp + c, P.xprev + pix);
     }
     cp_async_commit();
-    load_twiddles<W>(tw, tw_g, tid, kThreads);
+    if (!haar_tw_global<W>()) load_twiddles<W>(tws, tw_g, tid, kThreads);
     __syncthreads();
     float2 v[8];
     load_row_xax<W>(v, P.Sa + (size_t)q * Wp, t);
@@ -568,7 +584,8 @@ haar_row_forward(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp
     if (P.ctl->active == 0 || P.ctl->iter == 0) return;
     extern __shared__ __align__(16) float2 smem[];
     float2* buf = smem;
-    float2* tw = buf + 2 * G * ROW;
+    float2* tws = buf + 2 * G * ROW;
+    const float2* tw = haar_tw_global<W>() ? tw_g + pass_table_offset<W>() : tws;
     const int tid = threadIdx.x, g = tid / FT, t = tid % FT;
     const int q0 = blockIdx.x * 2 * G + g, q1 = q0 + G;
     const size_t n = (size_t)H * W;
@@ -582,7 +599,7 @@ haar_row_forward(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp
         v[m] = make_float2(z1a[t + m * FT], wa[t + m * FT]);
         u[m] = make_float2(z1b[t + m * FT], wb[t + m * FT]);
     }
-    load_twiddles<W>(tw, tw_g, tid, kThreads);
+    if (!haar_tw_global<W>()) load_twiddles<W>(tws, tw_g, tid, kThreads);
     __syncthreads();
     float2* row0 = buf + g * ROW;
     float2* row1 = buf + (g + G) * ROW;
@@ -604,9 +621,7 @@ template <int W>
 cudaError_t launch_haar_rows_t(int H, int Wp, const ProbDesc* d, SlotTable sl, int count, int levels, bool fs,
                                const float2* tw, int* n_active, cudaStream_t s) {
     constexpr int FT = W / 8, G = kThreads / FT;
-    const size_t smem_row = (size_t)(G * W + W) * sizeof(float2) + 8 * kNumPartials * sizeof(double);
-    const size_t smem_inv = smem_row + (size_t)3 * G * W * sizeof(float);   // + staged d1, M^T y, x_prev
-    const size_t smem_fwd = (size_t)(2 * G * W + W) * sizeof(float2);       // two rows per group
+    constexpr size_t smem_inv = haar_inv_smem<W>(), smem_fwd = haar_fwd_smem<W>();
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(haar_row_inverse<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_inv);
@@ -652,7 +667,7 @@ template <int W>
 cudaError_t launch_row_tail_t(int H, int Wp, const ProbDesc* d, SlotTable sl, int count, int levels, bool synth,
                               const float2* tw, cudaStream_t s) {
     constexpr int FT = W / 8, G = kThreads / FT;
-    const size_t smem_fwd = (size_t)(2 * G * W + W) * sizeof(float2);
+    constexpr size_t smem_fwd = haar_fwd_smem<W>();
     cudaError_t e = cudaFuncSetAttribute(haar_row_forward<W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem_fwd);
     if (e != cudaSuccess) return e;

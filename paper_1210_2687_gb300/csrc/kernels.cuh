@@ -293,8 +293,12 @@ struct ColCfg {
     // itself once every group holds its column in registers (the tile is
     // exactly G pairs of length-H buffers); otherwise separate buffers
     static constexpr bool ALIAS = CPG == 1;
+    // columns of 1024 and more read their per-pass twiddle table from the
+    // device buffer (through L1): the 8-16 KB go to more CTAs per SM
+    static constexpr bool TWG = H >= 1024;
+    static constexpr int TWN = TWG ? 0 : H;          // float2 of staged twiddles
     static constexpr size_t SMEM = (size_t)H * CB * sizeof(float4)
-                                 + (size_t)((ALIAS ? 0 : G * 2 * SIG) + H) * sizeof(float2);
+                                 + (size_t)((ALIAS ? 0 : G * 2 * SIG) + TWN) * sizeof(float2);
     static constexpr int MINB = ALIAS ? 4 : 2;       // CTAs per SM the registers are sized for
 };
 
@@ -333,7 +337,8 @@ col_phase(const ProbDesc* __restrict__ probs, SlotTable sl, int Wc, int Wp, cons
     float4* stage = smem4;                                       // H x CB
     float2* xb = C::ALIAS ? reinterpret_cast<float2*>(stage)     // G x 2 exchange buffers
                           : reinterpret_cast<float2*>(stage + H * CB);
-    float2* tw = reinterpret_cast<float2*>(stage + H * CB) + (C::ALIAS ? 0 : C::G * 2 * C::SIG);
+    float2* tws = reinterpret_cast<float2*>(stage + H * CB) + (C::ALIAS ? 0 : C::G * 2 * C::SIG);
+    const float2* tw = C::TWG ? tw_g + pass_table_offset<H>() : tws;
     const int tid = threadIdx.x;
     const int c0 = blockIdx.x * CB;
     const float4* __restrict__ src = P.Sb;
@@ -342,7 +347,7 @@ col_phase(const ProbDesc* __restrict__ probs, SlotTable sl, int Wc, int Wp, cons
         cp_async16(stage + tile_slot<CB>(r, c), src + (size_t)r * Wp + c0 + c);
     }
     cp_async_commit();
-    load_twiddles<H>(tw, tw_g, tid, kThreads);
+    if (!C::TWG) load_twiddles<H>(tws, tw_g, tid, kThreads);
     const int g = tid / C::FT, t = tid % C::FT;
     float2* bz = xb + (2 * g) * C::SIG;
     float2* bw = xb + (2 * g + 1) * C::SIG;
@@ -418,7 +423,8 @@ col_phase_pers(const ProbDesc* __restrict__ probs, SlotTable sl, int Wc, int Wp,
     using C = ColCfg<H, CB>;
     static_assert(C::ALIAS, "one column per transform group");
     extern __shared__ __align__(16) float4 smem4[];
-    float2* tw = reinterpret_cast<float2*>(smem4 + 2 * H * CB);
+    float2* tws = reinterpret_cast<float2*>(smem4 + 2 * H * CB);
+    const float2* tw = C::TWG ? tw_g + pass_table_offset<H>() : tws;
     const int tid = threadIdx.x;
     const int g = tid / C::FT, t = tid % C::FT;
     // what an item needs: 0 nothing (no problem in the slot, or retired),
@@ -443,7 +449,7 @@ col_phase_pers(const ProbDesc* __restrict__ probs, SlotTable sl, int Wc, int Wp,
     int mode = it < nitems ? classify(it, Pc) : 0;
     if (mode == 2) request(it, Pc, smem4);
     cp_async_commit();
-    load_twiddles<H>(tw, tw_g, tid, kThreads);
+    if (!C::TWG) load_twiddles<H>(tws, tw_g, tid, kThreads);
     for (; it < nitems; it += gridDim.x) {
         const int nx = it + gridDim.x;
         const ProbDesc* Pn = nullptr;

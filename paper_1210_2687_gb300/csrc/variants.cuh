@@ -80,7 +80,7 @@ template <int H, int CB>
 cudaError_t launch_col_pers_t(const ProbDesc* d, SlotTable sl, int count, int Wc, int Wp, const float2* tw,
                               cudaStream_t s) {
     static bool attr = false;
-    const size_t smem = (size_t)2 * H * CB * sizeof(float4) + (size_t)H * sizeof(float2);
+    const size_t smem = (size_t)2 * H * CB * sizeof(float4) + (size_t)ColCfg<H, CB>::TWN * sizeof(float2);
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(col_phase_pers<H, CB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
