@@ -1055,6 +1055,10 @@ int admm_warmstart_load(const char* path) {
 }  // extern "C"
 
 namespace admm {
+// the driver's tensor-map encoder, for the other translation units (null when
+// the driver does not provide it)
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encode_fn() { return tensor_map_encoder(); }
+
 bool ws_loaded() {
     std::lock_guard<std::mutex> lk(g_ws_mutex);
     return g_ws.loaded;

@@ -9,6 +9,8 @@
 // rule holds (Sec. V: relative change of the objective; or of x; or a fixed
 // iteration count). The host polls the number of active problems once per
 // chunk of iterations, one chunk behind the device.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -37,6 +39,8 @@ namespace admm {
 // the learned warm start of admm_warmstart_load (cnn.cu)
 bool ws_loaded();
 int ws_predict_start(int H, int W, const float* ybar, const uint8_t* mask, float* x0, float* d0, cudaStream_t s);
+// the driver's tensor-map encoder (cnn.cu)
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encode_fn();
 
 // ADMM_OPT_FAIL_ALLOC: allocations left before the injected failure (0 = off)
 static std::atomic<long long> g_fail_alloc{0};
@@ -77,6 +81,7 @@ struct admm_plan_s {
     uint8_t* mstage = nullptr;
     float* xstage = nullptr;
     float* psf_dev = nullptr;
+    void* zmap = nullptr;        // frame prior: the synthesis tile's TMA tensor maps (levels + 1)
     int last_iter = 0;          // iterations of the last solve: d2 lives in buffer last_iter & 1
     int warm_mode = 0;          // the next solve starts from: 0 u0 = d0 = 0; 1 admm_deconv_warm_start's
                                 // (x0, d0); 2 admm_deconv_set_state's state (resume)
@@ -477,6 +482,7 @@ ProbDesc make_desc(const admm_plan_s* pl) {
     d.n_slots = pl->n_slots;
     d.warm = pl->warm_mode;
     d.test_stall = g_test_stall;
+    d.zmap = pl->zmap;
     d.ll_free = pl->p.reg == ADMM_REG_HAAR_LL_FREE ? 1 : 0;
     d.tol = pl->p.tol;
     for (int b = 0; b < 13; ++b) {
@@ -640,6 +646,7 @@ int admm_deconv_plan(admm_plan_t* out, const admm_params_t* p, void* stream) {
     const size_t oms = take(n);
     const size_t oxs = take(n * sizeof(float));
     const size_t ops = take(pl->psf.size() * sizeof(float));
+    const size_t ozm = take(tvp ? 0 : (size_t)(levels + 1) * sizeof(CUtensorMap));
     if (dev_alloc(&pl->slab, off) != cudaSuccess) {
         cudaGetLastError();
         pl->slab = nullptr;
@@ -667,8 +674,25 @@ int admm_deconv_plan(admm_plan_t* out, const admm_params_t* p, void* stream) {
     pl->psf_dev = reinterpret_cast<float*>(b + ops);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     int rc = ADMM_OK;
+    CUtensorMap zmaps[kMaxHaarLevels + 1];
     do {
         if (cudaMemsetAsync(pl->slab, 0, off, s) != cudaSuccess) { rc = ADMM_ECUDA; break; }
+        if (!tvp) {
+            // the synthesis tile's TMA maps of the d2 buffers (without an
+            // encoder every tile copies its halo with cp.async)
+            const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encode_fn();
+            auto encode = [&](CUtensorMap* m, float* base, const cuuint64_t* dims, const cuuint64_t* strides,
+                              const cuuint32_t* box, const cuuint32_t* es) {
+                return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, dims, strides, box, es,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+            };
+            if (enc && haar_synthesis_maps(encode, zmaps, pl->d2, H, W, levels)) {
+                if (cudaMemcpyAsync(b + ozm, zmaps, (size_t)(levels + 1) * sizeof(CUtensorMap), cudaMemcpyHostToDevice,
+                                    s) != cudaSuccess) { rc = ADMM_ECUDA; break; }
+                pl->zmap = b + ozm;
+            }
+        }
         if (cudaMemcpyAsync(pl->psf_dev, pl->psf.data(), pl->psf.size() * sizeof(float), cudaMemcpyHostToDevice, s) !=
             cudaSuccess) { rc = ADMM_ECUDA; break; }
         const int tot = H * pl->Wc;

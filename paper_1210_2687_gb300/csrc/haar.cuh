@@ -27,6 +27,7 @@
 // (a separate launch) reads zeta2 there with its halo.
 #pragma once
 #include <cuda_runtime.h>
+#include <cstdint>
 #include "kernels.cuh"
 
 namespace admm {
@@ -420,10 +421,36 @@ struct HaarSynCfg {
     __host__ __device__ static constexpr int band_rows(int lvl) { return T + 2 * (1 << lvl) - 1; }
     // two band slots, each sized for the coarsest level: level j lives in slot
     // j % 2, and the bands of level j - 1 are requested into the other slot as
-    // soon as level j + 1 has released it
-    static constexpr int SLOT = 3 * band_rows(L - 1) * XS;
-    static constexpr size_t SMEM = (size_t)(2 * AR * XS + 2 * SLOT) * sizeof(float);
+    // soon as level j + 1 has released it. Array sizes are rounded to 32
+    // floats, so that the TMA destinations (the low-low array and the two
+    // slots) start on 128-byte boundaries; two mbarriers follow.
+    static constexpr int ARS = (AR * XS + 31) / 32 * 32;
+    static constexpr int SLOT = (3 * band_rows(L - 1) * XS + 31) / 32 * 32;
+    static constexpr size_t BAR_OFF = (size_t)(2 * ARS + 2 * SLOT) * sizeof(float);
+    static constexpr size_t SMEM = BAR_OFF + 2 * sizeof(unsigned long long);
 };
+
+// Host: the L + 1 tensor maps the synthesis tile loads its halo boxes with,
+// over both d2 buffers of a problem viewed as a 4-D tensor (W columns, H rows,
+// 3 L + 1 bands, 2 buffers; FP32): map 0 the low-low band's box (T + 16
+// columns x T + 2^L - 1 rows x 1 band), map 1 + j level j's three bands
+// (T + 16 columns x T + 2^{j+1} - 1 rows x 3 bands). `enc` is the driver's
+// cuTensorMapEncodeTiled; false if a map cannot be encoded.
+template <typename Enc, typename Map>
+bool haar_synthesis_maps(Enc enc, Map* maps, float* d2, int H, int W, int levels) {
+    const int nb = 3 * levels + 1;
+    const uint64_t n = (uint64_t)H * W;
+    const uint64_t dims[4] = {(uint64_t)W, (uint64_t)H, (uint64_t)nb, 2};
+    const uint64_t strides[3] = {(uint64_t)W * 4, n * 4, (uint64_t)nb * n * 4};
+    const uint32_t es[4] = {1, 1, 1, 1};
+    for (int i = 0; i <= levels; ++i) {
+        const uint32_t rows = i == 0 ? (uint32_t)(kHaarTile + (1 << levels) - 1)
+                                     : (uint32_t)(kHaarTile + 2 * (1 << (i - 1)) - 1);
+        const uint32_t box[4] = {(uint32_t)(kHaarTile + 16), rows, i == 0 ? 1u : 3u, 1u};
+        if (!enc(&maps[i], d2, dims, strides, box, es)) return false;
+    }
+    return true;
+}
 
 template <int L>
 __global__ void __launch_bounds__(kThreads)
@@ -439,15 +466,33 @@ haar_synthesis(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W) {
     // retired in this iteration, or a problem that has just taken over the slot
     if (P.ctl->active == 0 || P.ctl->iter == 0) return;
     const int k = P.ctl->iter;
-    extern __shared__ __align__(16) float sm[];
+    extern __shared__ __align__(128) float syn_sm[];
+    float* sm = syn_sm;
     float* At = sm;
-    float* Ao = sm + AR * XS;
-    float* Z = sm + 2 * AR * XS;
+    float* Ao = sm + C::ARS;
+    float* Z = sm + 2 * C::ARS;
+    unsigned long long* bars = reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(sm) + C::BAR_OFF);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int tiles_x = W / T;
     const int R0 = (blockIdx.x / tiles_x) * T, C0 = (blockIdx.x % tiles_x) * T;
     const size_t n = (size_t)H * W;
     const float* __restrict__ zeta = P.d2 + ((k + 1) & 1) * P.d2_stride;
+    // Tiles whose halo stays inside the image (every tile but the first row
+    // and column; the halo lies above and to the left) take their boxes by
+    // TMA, one thread issuing one copy per level (and one for the low-low
+    // band) on the level slot's mbarrier; the others copy with cp.async and
+    // wrap periodically.
+    const bool tma = P.zmap != nullptr && R0 > 0 && C0 > 0 && (smem_u32(sm) & 127u) == 0;
+    const char* zmaps = static_cast<const char*>(P.zmap);
+    const int zb = (k + 1) & 1;
+    auto tma_request = [&](int lvl) {
+        const int BO = 2 * (1 << lvl) - 1;
+        const uint32_t bar = smem_u32(&bars[lvl & 1]);
+        const uint32_t bytes = 3u * (uint32_t)((T + BO) * XS) * 4u + (lvl == L - 1 ? (uint32_t)(AR * XS) * 4u : 0u);
+        mbar_expect_tx(bar, bytes);
+        if (lvl == L - 1) tma_load_4d(At, zmaps, C0 - 16, R0 - HALO, 3 * L, zb, bar);
+        tma_load_4d(Z + (lvl & 1) * C::SLOT, zmaps + 128 * (1 + lvl), C0 - 16, R0 - BO, 3 * lvl, zb, bar);
+    };
 
     // low-low band on rows [-HALO, T) and each level's bands on rows [-BO, T),
     // all on the columns [-16, T), one cp.async group per level (the low-low
@@ -468,25 +513,49 @@ haar_synthesis(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W) {
         }
         cp_async_commit();
     };
-    {
+    if (tma) {
+        if (tid == 0) {
+            mbar_init1(smem_u32(&bars[0]));
+            mbar_init1(smem_u32(&bars[1]));
+            mbar_init_fence();
+            tma_request(L - 1);
+            if (L >= 2) tma_request(L - 2);
+        }
+        __syncthreads();             // the barriers are initialised before anyone waits on them
+    } else {
         const float* band = zeta + (size_t)(3 * L) * n;
         for (int e = tid; e < AR * CH; e += kThreads) {
             const int rr = e / CH, ch = e - rr * CH;
             cp_async16(At + rr * XS + 4 * ch,
                        band + (size_t)hwrap(R0 + rr - HALO, H) * W + hwrap(C0 - 16 + 4 * ch, W));
         }
+        request(L - 1);
+        if (L >= 2) request(L - 2);
     }
-    request(L - 1);
-    if (L >= 2) request(L - 2);
 
 #pragma unroll
     for (int lvl = L - 1; lvl >= 0; --lvl) {
         // this level's bands have landed (at the first level the next one may
         // still be in flight; later, the next level is requested only below)
-        if (lvl == L - 1 && L >= 2) cp_async_wait<1>();
-        else cp_async_wait<0>();
+        if (tma) {
+            // slot lvl % 2 completes its ((L - 1 - lvl) / 2)-th phase with this level
+            const uint32_t parity = (uint32_t)((L - 1 - lvl) >> 1) & 1u;
+            if (!mbar_wait_bounded(smem_u32(&bars[lvl & 1]), parity) && tid == 0)
+                atomicExch(&P.ctl->status, kStatusTimeout);
+        } else if (lvl == L - 1 && L >= 2) {
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
         __syncthreads();             // ... for every thread; level lvl + 1 is done and its slot free
-        if (lvl <= L - 2 && lvl >= 1) request(lvl - 1);
+        if (lvl <= L - 2 && lvl >= 1) {
+            if (!tma) {
+                request(lvl - 1);
+            } else if (tid == 0) {
+                fence_proxy_async_smem();   // the slot's generic reads before the copy's writes
+                tma_request(lvl - 1);
+            }
+        }
         const int s = 1 << lvl;
         const int D = T + s - 1;                       // output on [-(s-1), T)
         const int BO = 2 * s - 1, BR = T + BO;

@@ -103,6 +103,8 @@ struct ProbDesc {
     float band_zs[13];
     int test_stall;           // test hook (ADMM_OPT_TEST_STALL): the TV row phase withholds
                               // one of its bulk copies, so that its bounded wait runs out
+    const void* zmap;         // frame prior: L + 1 TMA tensor maps (128 bytes each) of the d2
+                              // buffers, the synthesis tile's halo boxes (null: cp.async)
 };
 
 // Continuous batching: a launch covers gridDim.y slots; slot s works on
@@ -227,6 +229,22 @@ __device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32
                  "l"(src), "r"(bytes), "r"(bar)
                  : "memory");
 }
+// TMA (cp.async.bulk.tensor) load of one box of a 4-D tensor map at the
+// coordinates (c0 innermost .. c3), completing on an mbarrier; `tmap` is the
+// address of a 64-byte-aligned CUtensorMap in global memory, `dst` 128-byte
+// aligned shared memory
+__device__ __forceinline__ void tma_load_4d(void* dst, const void* tmap, int c0, int c1, int c2, int c3,
+                                            uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+        "[%6];" ::"r"(smem_u32(dst)),
+        "l"(tmap), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
+        : "memory");
+}
+// order this thread's earlier generic accesses to shared memory before its
+// later asynchronous-proxy (TMA) accesses
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
 // wait for phase `parity` of an mbarrier, at most about a second; false if
 // the wait ran out (the caller then marks the problem and carries on)
 __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
