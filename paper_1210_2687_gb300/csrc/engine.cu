@@ -82,6 +82,7 @@ struct admm_plan_s {
     float* xstage = nullptr;
     float* psf_dev = nullptr;
     void* zmap = nullptr;        // frame prior: the synthesis tile's TMA tensor maps (levels + 1)
+    uint32_t* zbits = nullptr;   // frame analysis prior: two bits per band and pixel (beside zeta2)
     int last_iter = 0;          // iterations of the last solve: d2 lives in buffer last_iter & 1
     int warm_mode = 0;          // the next solve starts from: 0 u0 = d0 = 0; 1 admm_deconv_warm_start's
                                 // (x0, d0); 2 admm_deconv_set_state's state (resume)
@@ -483,12 +484,14 @@ ProbDesc make_desc(const admm_plan_s* pl) {
     d.warm = pl->warm_mode;
     d.test_stall = g_test_stall;
     d.zmap = pl->zmap;
+    d.zbits = pl->zbits;
     d.ll_free = pl->p.reg == ADMM_REG_HAAR_LL_FREE ? 1 : 0;
     d.tol = pl->p.tol;
     for (int b = 0; b < 13; ++b) {
         const bool per = b < (int)pl->band_mu.size();
         d.band_tau[b] = per ? (float)((double)pl->lam / (double)pl->band_mu[b]) : d.tau;
         d.band_zs[b] = per ? (float)((double)pl->band_mu[b] / (double)pl->mu2) : 1.0f;
+        d.band_izs[b] = per ? (float)((double)pl->mu2 / (double)pl->band_mu[b]) : 1.0f;
     }
     return d;
 }
@@ -647,6 +650,8 @@ int admm_deconv_plan(admm_plan_t* out, const admm_params_t* p, void* stream) {
     const size_t oxs = take(n * sizeof(float));
     const size_t ops = take(pl->psf.size() * sizeof(float));
     const size_t ozm = take(tvp ? 0 : (size_t)(levels + 1) * sizeof(CUtensorMap));
+    const bool zstate = !tvp && p->reg != ADMM_REG_HAAR_SYNTHESIS;   // zeta2 + bits (not FS-MD)
+    const size_t ozb = take(zstate ? n * sizeof(uint32_t) : 0);
     if (dev_alloc(&pl->slab, off) != cudaSuccess) {
         cudaGetLastError();
         pl->slab = nullptr;
@@ -672,6 +677,7 @@ int admm_deconv_plan(admm_plan_t* out, const admm_params_t* p, void* stream) {
     pl->mstage = reinterpret_cast<uint8_t*>(b + oms);
     pl->xstage = reinterpret_cast<float*>(b + oxs);
     pl->psf_dev = reinterpret_cast<float*>(b + ops);
+    pl->zbits = zstate ? reinterpret_cast<uint32_t*>(b + ozb) : nullptr;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     int rc = ADMM_OK;
     CUtensorMap zmaps[kMaxHaarLevels + 1];
@@ -727,13 +733,38 @@ long long admm_deconv_state_size(admm_plan_t plan) {
     return (long long)(1 + plan->nb) * plan->p.H * plan->p.W;
 }
 
+// The second dual after iteration K (K >= 0), on the device: buffer K & 1 for
+// the TV priors and FS-MD (and buffer 0 before the first iteration); for the
+// frame analysis prior, d2 rebuilt from zeta2 (buffer 0) and the bits into
+// buffer 1, which its iterations do not use.
+static cudaError_t second_dual(admm_plan_s* plan, int K, const float** d2, cudaStream_t s) {
+    const size_t n = (size_t)plan->p.H * plan->p.W;
+    if (!plan->zbits || K < 1) {
+        *d2 = plan->d2 + (size_t)(plan->zbits ? 0 : (K & 1)) * plan->nb * n;
+        return cudaSuccess;
+    }
+    const ProbDesc pd = make_desc(plan);
+    BandConv c{};
+    for (int b = 0; b < plan->nb && b < 3 * kMaxHaarLevels + 1; ++b) {
+        c.tau[b] = pd.band_tau[b];
+        c.izs[b] = pd.band_izs[b];
+    }
+    if (pd.ll_free) c.tau[plan->nb - 1] = 0.f;
+    float* out = plan->d2 + (size_t)plan->nb * n;
+    const int blocks = (int)std::min<size_t>((n + kThreads - 1) / kThreads, (size_t)152 * 8);
+    haar_dual_from_state<<<blocks, kThreads, 0, s>>>(plan->d2, plan->zbits, out, (long long)n, plan->nb, c);
+    *d2 = out;
+    return cudaGetLastError();
+}
+
 int admm_deconv_get_state(admm_plan_t plan, float* d_out, void* stream) {
     if (!plan || !d_out) return ADMM_EINVAL;
     std::lock_guard<std::mutex> lk(g_mutex);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const size_t n = (size_t)plan->p.H * plan->p.W;
     CK(cudaMemcpyAsync(d_out, plan->d1, n * sizeof(float), cudaMemcpyDefault, s));
-    const float* d2 = plan->d2 + (size_t)(plan->last_iter & 1) * plan->nb * n;
+    const float* d2 = nullptr;
+    CK(second_dual(plan, plan->last_iter, &d2, s));
     CK(cudaMemcpyAsync(d_out + n, d2, (size_t)plan->nb * n * sizeof(float), cudaMemcpyDefault, s));
     CK(cudaStreamSynchronize(s));
     return ADMM_OK;
@@ -856,8 +887,8 @@ int admm_deconv_get_full_state(admm_plan_t plan, float* state, int* iters, void*
         CK(cudaStreamSynchronize(s));
     }
     CK(cudaMemcpyAsync(state, plan->d1, n * sizeof(float), cudaMemcpyDefault, s));
-    // the duals of iteration K live in buffer K & 1
-    const float* d2 = plan->d2 + (size_t)(K & 1) * plan->nb * n;
+    const float* d2 = nullptr;
+    CK(second_dual(plan, K, &d2, s));
     CK(cudaMemcpyAsync(state + n, d2, (size_t)plan->nb * n * sizeof(float), cudaMemcpyDefault, s));
     CK(cudaMemcpy2DAsync(state + spec_off, (size_t)plan->Wc * sizeof(float4), plan->Sb,
                          (size_t)plan->Wp * sizeof(float4), (size_t)plan->Wc * sizeof(float4), (size_t)H,

@@ -8,8 +8,9 @@
 //                      writes x and zeta1 = u1 + d1 to two scratch planes
 //   haar_analysis      32 x 32 tile: analysis c = P x (a-trous Haar), u2 =
 //                      soft(c - d2, lambda/mu2) (eq. soft), d2 <- d2 - (c - u2);
-//                      zeta2 = u2 + d2 replaces the previous d2 in place;
-//                      the last CTA of the problem finishes the iteration
+//                      zeta2 = u2 + d2 and two bits per coefficient replace
+//                      the previous state in place (see below); the last CTA
+//                      of the problem finishes the iteration
 //   haar_synthesis     32 x 32 tile: w = gamma P^T zeta2 (the x-step right-
 //                      hand side of eq. invAnalysis divided by mu1)
 //   haar_row_forward   forward row DFT of zeta1 + i w, split into half spectra
@@ -20,11 +21,19 @@
 // (3 L + 1 bands, P^T P = I). Band order per level: rows low / columns high,
 // rows high / columns low, rows high / columns high; final band low-low.
 //
-// d2 lives in two buffers by iteration parity: iteration k reads the previous
-// d2 from buffer (k+1)&1 and writes the new one to buffer k&1. Each
-// coefficient is read and replaced by the thread that owns it, so the
-// analysis can leave zeta2 in the buffer it has just read; the synthesis
-// (a separate launch) reads zeta2 there with its halo.
+// State of the analysis prior: with s = c - d2 the argument of the soft
+// threshold (tau = lambda/mu_b of the band), the new dual is d2' = u2 - s =
+// -clamp(s, -tau, tau): -tau sign(s) where the threshold passes s (u2 != 0),
+// -s elsewhere, where zeta2 = u2 + d2' = d2'. So zeta2 and two bits per
+// coefficient (u2 != 0; s < 0) carry d2' exactly: the analysis stores
+// (gamma_b/gamma) zeta2 in d2 buffer 0 over the state it has just read (each
+// coefficient is read and replaced by the thread that owns it) and the bits
+// of all bands of a pixel in one word (zbits); the synthesis (a separate
+// launch) reads zeta2 there with its halo. Iteration 1 reads d2 itself from
+// buffer 0 (zero, a warm start or a restored state). The synthesis
+// formulation (FS-MD) keeps d2 in two buffers by iteration parity (iteration
+// k reads buffer (k+1)&1 and writes buffer k&1) and zeta2 over the d2 it has
+// read, where its next analysis also reads the previous zeta2.
 #pragma once
 #include <cuda_runtime.h>
 #include <cstdint>
@@ -156,6 +165,19 @@ __device__ __forceinline__ float soft_thresh(float v, float t) {
     return a > 0.f ? copysignf(a, v) : 0.f;
 }
 
+// the two state bits of a coefficient: bit 0 the threshold passed s (|s| >
+// tau), bit 1 the sign bit of s
+__device__ __forceinline__ uint32_t state_bits(float sv, float tau) {
+    return (fabsf(sv) > tau ? 1u : 0u) | ((__float_as_uint(sv) >> 30) & 2u);
+}
+// d2 of one coefficient from its stored (gamma_b/gamma) zeta2 `z` and its two
+// bits: -tau sign(s) where the threshold passed, else zeta2 itself (izs =
+// gamma / gamma_b)
+__device__ __forceinline__ float dual_from_zeta(float z, uint32_t bits, float tau, float izs) {
+    const float dt = __uint_as_float(__float_as_uint(tau) ^ ((~bits & 2u) << 30));   // -tau sign(s)
+    return (bits & 1u) ? dt : z * izs;
+}
+
 // ---------------------------------------------------------------------------
 // analysis c = P x on a T x T tile (a-trous Haar), soft threshold, dual
 // update. Every coefficient of the tile is owned by this CTA: the previous d2
@@ -201,6 +223,7 @@ haar_analysis(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W, in
     if (ctl->active == 0) return;
     const int k = ctl->iter + 1;
     const bool first = k == 1 && !P.warm;        // d2 = 0 (cold start: u0 = d0 = 0)
+    const bool raw = FS || k == 1;               // buffer holds d2 itself (not zeta2 and bits)
     const bool chk = is_check_iter(P, k), nobj = need_obj_iter(P, k);
     extern __shared__ __align__(16) float sm[];
     float* Ain = sm;
@@ -211,7 +234,8 @@ haar_analysis(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W, in
     const int tiles_x = W / T;
     const int R0 = (blockIdx.x / tiles_x) * T, C0 = (blockIdx.x % tiles_x) * T;
     const size_t n = (size_t)H * W;
-    float* __restrict__ d2io = P.d2 + ((k + 1) & 1) * P.d2_stride;   // previous d2 in, zeta2 out
+    // previous state in, zeta2 out (FS-MD: the parity buffers, the new d2 to d2out)
+    float* __restrict__ d2io = P.d2 + (FS ? ((k + 1) & 1) * P.d2_stride : 0);
     float* __restrict__ d2out = P.d2 + (k & 1) * P.d2_stride;
 
     // x on [0, T + HALO) x [0, T + 16) with periodic wrap, 16-byte copies (the
@@ -238,6 +262,13 @@ haar_analysis(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W, in
     static_assert(T * T == 4 * kThreads, "four owned pixels per thread");
     const int orow = tid >> 3, ocol = 4 * (tid & 7);
     const size_t gq = (size_t)(R0 + orow) * W + (C0 + ocol);
+    // the bits of the previous iteration at the owned pixels (two per band)
+    uint32_t obits[4] = {0u, 0u, 0u, 0u};
+    if (!raw) {
+        const uint4 bv = *reinterpret_cast<const uint4*>(P.zbits + gq);
+        obits[0] = bv.x; obits[1] = bv.y; obits[2] = bv.z; obits[3] = bv.w;
+    }
+    uint32_t nbits[4] = {0u, 0u, 0u, 0u};
     auto stage = [&](int lvl) {
         if (!first) {
             const int nb = lvl == L - 1 ? 4 : 3;
@@ -274,6 +305,12 @@ haar_analysis(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W, in
             const float4 v = first ? make_float4(0.f, 0.f, 0.f, 0.f)
                                    : *reinterpret_cast<const float4*>(d2s + (lvl & 1) * C::SLOT + j * T * T + orow * T + ocol);
             dold[j][0] = v.x; dold[j][1] = v.y; dold[j][2] = v.z; dold[j][3] = v.w;
+            if (!raw) {
+                const int b = 3 * lvl + j;
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    dold[j][e] = dual_from_zeta(dold[j][e], obits[e] >> (2 * b), P.band_tau[b], P.band_izs[b]);
+            }
         }
         // the slot is consumed (the last level's low-low entries are read
         // after the loop, and nothing is staged after the last level)
@@ -317,8 +354,18 @@ haar_analysis(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W, in
             for (int j = 0; j < 3; ++j) {
                 if (FS) cb[j] += zprev[j][e];                   // theta = P v + zeta2
                 const float sv = cb[j] - dold[j][e];
-                const float u = soft_thresh(sv, P.band_tau[3 * lvl + j]);   // eq. soft
-                nd4[j][e] = u - sv;                             // d2 - (c - u2)
+                const float tb = P.band_tau[3 * lvl + j];
+                float u;
+                if (FS) {
+                    u = soft_thresh(sv, tb);                    // eq. soft
+                    nd4[j][e] = u - sv;                         // d2 - (c - u2)
+                } else {
+                    // the same, exactly: d2 - (c - u2) = -clamp(s, -tau, tau), and
+                    // u2 = s + that (= soft(s, tau), eq. soft, with its rounding)
+                    nd4[j][e] = copysignf(fminf(fabsf(sv), tb), -sv);
+                    u = sv + nd4[j][e];
+                    nbits[e] |= state_bits(sv, tb) << (2 * (3 * lvl + j));
+                }
                 // zeta2 = u2 + d2, times gamma_b / gamma for the synthesis
                 z4[j][e] = (u + nd4[j][e]) * P.band_zs[3 * lvl + j];
                 if (nobj) {
@@ -333,7 +380,7 @@ haar_analysis(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W, in
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
             const size_t bo = (size_t)(3 * lvl + j) * n + gq;
-            *reinterpret_cast<float4*>(d2out + bo) = make_float4(nd4[j][0], nd4[j][1], nd4[j][2], nd4[j][3]);
+            if (FS) *reinterpret_cast<float4*>(d2out + bo) = make_float4(nd4[j][0], nd4[j][1], nd4[j][2], nd4[j][3]);
             *reinterpret_cast<float4*>(d2io + bo) = make_float4(z4[j][0], z4[j][1], z4[j][2], z4[j][3]);
         }
         // the approximation on the rest of [0, D)^2 that later levels read
@@ -369,7 +416,12 @@ haar_analysis(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W, in
                                 : *reinterpret_cast<const float4*>(d2s + ((L - 1) & 1) * C::SLOT + 3 * T * T +
                                                                    orow * T + ocol);
         const float4 cv = *reinterpret_cast<const float4*>(Ain + orow * XA + ocol);
-        const float dold[4] = {dv.x, dv.y, dv.z, dv.w};
+        float dold[4] = {dv.x, dv.y, dv.z, dv.w};
+        if (!raw) {
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                dold[e] = dual_from_zeta(dold[e], obits[e] >> (2 * 3 * L), tau_ll, P.band_izs[3 * L]);
+        }
         float cb[4] = {cv.x, cv.y, cv.z, cv.w};
         if (FS && !first) {
             const float4 zv = *reinterpret_cast<const float4*>(d2out + (size_t)(3 * L) * n + gq);
@@ -380,8 +432,15 @@ haar_analysis(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W, in
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             const float sv = cb[e] - dold[e];
-            const float u = soft_thresh(sv, tau_ll);
-            nd[e] = u - sv;
+            float u;
+            if (FS) {
+                u = soft_thresh(sv, tau_ll);
+                nd[e] = u - sv;
+            } else {
+                nd[e] = copysignf(fminf(fabsf(sv), tau_ll), -sv);
+                u = sv + nd[e];
+                nbits[e] |= state_bits(sv, tau_ll) << (2 * 3 * L);
+            }
             z[e] = (u + nd[e]) * P.band_zs[3 * L];
             if (nobj) {
                 if (!ll_free) l1.add(fabsf(cb[e]));
@@ -391,8 +450,9 @@ haar_analysis(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W, in
         }
         if (nobj) pr.add(prl);
         const size_t bo = (size_t)(3 * L) * n + gq;
-        *reinterpret_cast<float4*>(d2out + bo) = make_float4(nd[0], nd[1], nd[2], nd[3]);
+        if (FS) *reinterpret_cast<float4*>(d2out + bo) = make_float4(nd[0], nd[1], nd[2], nd[3]);
         *reinterpret_cast<float4*>(d2io + bo) = make_float4(z[0], z[1], z[2], z[3]);
+        if (!FS) *reinterpret_cast<uint4*>(P.zbits + gq) = make_uint4(nbits[0], nbits[1], nbits[2], nbits[3]);
     }
     double pv[kNumPartials] = {0.0};
     if (nobj || chk) {
@@ -476,7 +536,9 @@ haar_synthesis(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W) {
     const int tiles_x = W / T;
     const int R0 = (blockIdx.x / tiles_x) * T, C0 = (blockIdx.x % tiles_x) * T;
     const size_t n = (size_t)H * W;
-    const float* __restrict__ zeta = P.d2 + ((k + 1) & 1) * P.d2_stride;
+    // zeta2: buffer 0 (FS-MD: buffer (k+1)&1, over the d2 its analysis read)
+    const int zb = P.zbits ? 0 : ((k + 1) & 1);
+    const float* __restrict__ zeta = P.d2 + zb * P.d2_stride;
     // Tiles whose halo stays inside the image (every tile but the first row
     // and column; the halo lies above and to the left) take their boxes by
     // TMA, one thread issuing one copy per level (and one for the low-low
@@ -484,7 +546,6 @@ haar_synthesis(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W) {
     // wrap periodically.
     const bool tma = P.zmap != nullptr && R0 > 0 && C0 > 0 && (smem_u32(sm) & 127u) == 0;
     const char* zmaps = static_cast<const char*>(P.zmap);
-    const int zb = (k + 1) & 1;
     auto tma_request = [&](int lvl) {
         const int BO = 2 * (1 << lvl) - 1;
         const uint32_t bar = smem_u32(&bars[lvl & 1]);
@@ -681,6 +742,24 @@ haar_row_forward(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp
     group_sync<W>(g);                // the split reads this group's rows only
     store_split<W>(P.Sb + (size_t)q0 * Wp, row0, t);
     store_split<W>(P.Sb + (size_t)q1 * Wp, row1, t);
+}
+
+// ---------------------------------------------------------------------------
+// d2 of every band from the analysis prior's state (zeta2 in d2 buffer 0 and
+// the bits), for the state read-out calls
+// ---------------------------------------------------------------------------
+struct BandConv {
+    float tau[3 * kMaxHaarLevels + 1];   // threshold per band (0 on an unpenalised low-low band)
+    float izs[3 * kMaxHaarLevels + 1];   // gamma / gamma_b
+};
+
+static __global__ void __launch_bounds__(kThreads)
+haar_dual_from_state(const float* __restrict__ zeta, const uint32_t* __restrict__ bits, float* __restrict__ d2,
+                     long long n, int nb, BandConv c) {
+    for (long long p = (long long)blockIdx.x * kThreads + threadIdx.x; p < n; p += (long long)gridDim.x * kThreads) {
+        const uint32_t w = bits[p];
+        for (int b = 0; b < nb; ++b) d2[b * n + p] = dual_from_zeta(zeta[b * n + p], w >> (2 * b), c.tau[b], c.izs[b]);
+    }
 }
 
 // ---------------------------------------------------------------------------

@@ -101,6 +101,10 @@ struct ProbDesc {
     // band, eq. diagonal_penalty); tau and 1 when every band has mu2
     float band_tau[13];
     float band_zs[13];
+    float band_izs[13];       // gamma / gamma_b (1 when every band has mu2)
+    uint32_t* zbits;          // frame analysis prior: H x W words, two bits per band of the
+                              // last analysis (threshold passed; argument negative), beside
+                              // zeta2 in d2 buffer 0; null for FS-MD and the TV priors
     int test_stall;           // test hook (ADMM_OPT_TEST_STALL): the TV row phase withholds
                               // one of its bulk copies, so that its bounded wait runs out
     const void* zmap;         // frame prior: L + 1 TMA tensor maps (128 bytes each) of the d2
