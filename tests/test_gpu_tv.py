@@ -247,6 +247,29 @@ def test_host_buffers_equal_device_buffers(ad):
     assert np.array_equal(xh, xd.cpu().numpy())
 
 
+def test_pinned_host_buffers_equal_device_buffers(ad):
+    """Page-locked host buffers (inputs and x_out) in a batch of two
+    problems; same bits as device buffers."""
+    import torch
+    outs = []
+    for seed in (13, 14):
+        xt, psf, ybar, mask = _case_problem(128, 256, lambda: S.psf_motion(9.0, 60.0, 9), 0.7, seed)
+        outs.append((psf, ybar, mask))
+    plans = [ad.Plan(128, 256, psf, 3e-4, 1.0, 3e-3, "tv", max_iters=11) for psf, _, _ in outs]
+    yp = [torch.from_numpy(np.ascontiguousarray(yb.astype(np.float32))).pin_memory() for _, yb, _ in outs]
+    mp = [torch.from_numpy(np.ascontiguousarray(m)).pin_memory() for _, _, m in outs]
+    xp = [torch.zeros((128, 256), dtype=torch.float32).pin_memory() for _ in outs]
+    r1 = ad.solve_batch(plans, yp, mp, xp)
+    yd = [t.cuda() for t in yp]
+    md = [t.cuda() for t in mp]
+    xd = [torch.empty((128, 256), dtype=torch.float32, device="cuda") for _ in outs]
+    r2 = ad.solve_batch(plans, yd, md, xd)
+    torch.cuda.synchronize()
+    for a, b, ra, rb in zip(xp, xd, r1, r2):
+        assert ra.iters == rb.iters == 11
+        assert torch.equal(a, b.cpu())
+
+
 def test_mask_null_means_valid_region(ad):
     """mask = NULL observes exactly the valid region (Sec. IV-A)."""
     import torch
