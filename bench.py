@@ -53,6 +53,8 @@ def parse():
                     help="frame workloads to run: sides, 'fs' prefix for the synthesis formulation")
     ap.add_argument("--frame-iters", type=int, default=500, help="fixed iterations of the frame workloads")
     ap.add_argument("--frame-no-accuracy", action="store_true", help="skip the frame workloads' solve to tolerance")
+    ap.add_argument("--frame-batch", type=int, default=1,
+                    help="problems per solve in the frame workloads' throughput leg (copies of the image)")
     ap.add_argument("--uneven-only", action="store_true", help="only the batched uneven workload")
     ap.add_argument("--warm-only", action="store_true", help="only the learned warm-start comparison")
     ap.add_argument("--cg-only", action="store_true", help="only the mask-decoupling vs Reeves-Sorel comparison")
@@ -322,10 +324,14 @@ def frame_secondary(ad, torch, stream, args):
     the 13-band frame prior: d1 and d2 (14 planes) read and written (112),
     M^T y and the mask (5), Lambda and K over the half spectrum (6), and two
     complex round trips between the row and column phases (32). The kernels
-    themselves move more (the zeta2 store and its re-read by the synthesis,
+    themselves move more (the zeta2 re-read by the synthesis with its halo,
     the x and zeta1 scratch planes): column phase 22.1, row side 28 (inverse
-    rows) + 112 (Haar tile) + 16 (forward rows); that figure is reported
-    beside it, and the extra bytes count as overhead, not work."""
+    rows) + 116 (analysis tile: x, zeta2 in and out, the state bits) + 56
+    (synthesis tile: zeta2, w) + 16 (forward rows); FS-MD's analysis tile
+    also stores d2 and reads w and the previous zeta2 (+100). That figure is
+    reported beside it, and the extra bytes count as overhead, not work. With
+    --frame-batch B > 1 the throughput leg solves B copies of the image in
+    one call (key suffix _xB; iterations/s counts problem-iterations)."""
     out = {}
     FRAME_ITERS = args.frame_iters
     cases = []
@@ -335,27 +341,35 @@ def frame_secondary(ad, torch, stream, args):
     for reg, size in cases:
         p = S.config3_problem(0, size, lam=S.FS_FRAME_LAMBDA) if reg == "haar_synthesis" else S.config3_problem(0, size)
         n = size * size
-        tune = tune_class(ad, torch, args, size, size, "haar", 4, problems=1)   # one image per solve
-        plan = ad.Plan(size, size, p.psf, p.lam, p.mu1, p.mu2, reg, stop="iters", max_iters=FRAME_ITERS)
+        B = max(1, args.frame_batch)
+        tune = tune_class(ad, torch, args, size, size, "haar", 4, problems=B)
+        plans = [ad.Plan(size, size, p.psf, p.lam, p.mu1, p.mu2, reg, stop="iters", max_iters=FRAME_ITERS)
+                 for _ in range(B)]
         y = torch.from_numpy(p.ybar.astype(np.float32)).to("cuda")
         m = torch.from_numpy(p.mask).to("cuda")
-        x = torch.empty((size, size), dtype=torch.float32, device="cuda")
-        ad.solve(plan, y, m, x, stream)
+        xs = [torch.empty((size, size), dtype=torch.float32, device="cuda") for _ in range(B)]
+        x = xs[0]
+
+        def run():
+            ad.solve_batch(plans, [y] * B, [m] * B, xs, stream=stream)
+
+        run()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        ad.solve(plan, y, m, x, stream)
+        run()
         e1.record(stream)
         torch.cuda.synchronize()
-        sec = e0.elapsed_time(e1) * 1e-3
+        sec = e0.elapsed_time(e1) * 1e-3 / B      # per problem
         ad.admm_deconv_profile(True)
-        ad.solve(plan, y, m, x, stream)
+        run()
         pf = ad.admm_deconv_profile(False)
-        # synthesis form: the analysis tile also reads w and the previous zeta2 (4 + 52)
-        row_b = 28.0 + 112.0 + 16.0 + (56.0 if reg == "haar_synthesis" else 0.0)
+        pf_row_ms, pf_col_ms = pf.row_ms / B, pf.col_ms / B
+        # synthesis form: the analysis tile also stores d2 and reads w and the previous zeta2
+        row_b = 28.0 + 116.0 + 56.0 + 16.0 + (100.0 if reg == "haar_synthesis" else 0.0)
         col_b = 44.0 * (size // 2 + 1) / size
         alg_b = FRAME_ALG_BYTES
         peak, _ = read_peak()
-        key = f"{'fs' if reg == 'haar_synthesis' else 'fa'}_md_{size}"
+        key = f"{'fs' if reg == 'haar_synthesis' else 'fa'}_md_{size}" + (f"_x{B}" if B > 1 else "")
         out[key] = {
             "iters_per_s": FRAME_ITERS / sec,
             # whole iteration: the method's algorithmic bytes over the timed solve
@@ -364,11 +378,13 @@ def frame_secondary(ad, torch, stream, args):
             "alg_bytes_per_px_iter": alg_b,
             # the same with the bytes the kernels move (their overhead included)
             "iteration_frac_kernel_bytes": FRAME_ITERS * n * (row_b + col_b) / sec / 1e9 / peak,
-            "row_side_gbs": FRAME_ITERS * n * row_b / (pf.row_ms * 1e-3) / 1e9,
-            "col_phase_gbs": FRAME_ITERS * n * col_b / (pf.col_ms * 1e-3) / 1e9,
+            "row_side_gbs": FRAME_ITERS * n * row_b / (pf_row_ms * 1e-3) / 1e9,
+            "col_phase_gbs": FRAME_ITERS * n * col_b / (pf_col_ms * 1e-3) / 1e9,
             "bytes_per_px_iter": {"row_side": row_b, "col_phase": col_b},
+            "problems_per_solve": B,
             "tuning": tune}
-        plan.close()
+        for pl in plans:
+            pl.close()
         if args.frame_no_accuracy:
             continue
         acc = ad.Plan(size, size, p.psf, p.lam, p.mu1, p.mu2, reg, stop="rel_x", tol=TOL, max_iters=MAX_ITERS,
@@ -429,6 +445,16 @@ def uneven_secondary(ad, torch, stream, args, count=UNEVEN_COUNT):
     alg_bytes = sum(int(r.iters) * p.ybar.size * (TV_ALG_BYTES if p.reg == "tv" else FRAME_ALG_BYTES)
                     for r, p in zip(res, probs))
     peak, _ = read_peak()
+    # where the work is: per size class and prior, problems, mean iterations
+    # and the share of the algorithmic bytes
+    classes = {}
+    for r, p in zip(res, probs):
+        c = classes.setdefault(f"{p.ybar.shape[0]}_{p.reg}", {"problems": 0, "iters": 0, "bytes": 0.0})
+        c["problems"] += 1
+        c["iters"] += int(r.iters)
+        c["bytes"] += int(r.iters) * p.ybar.size * (TV_ALG_BYTES if p.reg == "tv" else FRAME_ALG_BYTES)
+    class_table = {k: {"problems": v["problems"], "iters_mean": v["iters"] / v["problems"],
+                       "alg_bytes_share": v["bytes"] / alg_bytes} for k, v in sorted(classes.items())}
     isnr = []
     for p, x in zip(probs, xs):
         n = p.meta["window"]
@@ -458,6 +484,7 @@ def uneven_secondary(ad, torch, stream, args, count=UNEVEN_COUNT):
         "time_to_tol_ms_p99": float(np.percentile(solve, 99)),
         "isnr_db_mean": float(np.mean(isnr)),
         "input_generation_s": t_gen,
+        "classes": class_table,
         "tuning": tunings,
     }
 
