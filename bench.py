@@ -328,7 +328,8 @@ def frame_secondary(ad, torch, stream, args):
     the x and zeta1 scratch planes): column phase 22.1, row side 28 (inverse
     rows) + 116 (analysis tile: x, zeta2 in and out, the state bits) + 56
     (synthesis tile: zeta2, w) + 16 (forward rows); FS-MD's analysis tile
-    also stores d2 and reads w and the previous zeta2 (+100). That figure is
+    also reads the previous w (+4; its previous zeta2 is the state it reads
+    anyway). That figure is
     reported beside it, and the extra bytes count as overhead, not work. With
     --frame-batch B > 1 the throughput leg solves B copies of the image in
     one call (key suffix _xB; iterations/s counts problem-iterations)."""
@@ -364,8 +365,8 @@ def frame_secondary(ad, torch, stream, args):
         run()
         pf = ad.admm_deconv_profile(False)
         pf_row_ms, pf_col_ms = pf.row_ms / B, pf.col_ms / B
-        # synthesis form: the analysis tile also stores d2 and reads w and the previous zeta2
-        row_b = 28.0 + 116.0 + 56.0 + 16.0 + (100.0 if reg == "haar_synthesis" else 0.0)
+        # synthesis form: the analysis tile also reads the previous w
+        row_b = 28.0 + 116.0 + 56.0 + 16.0 + (4.0 if reg == "haar_synthesis" else 0.0)
         col_b = 44.0 * (size // 2 + 1) / size
         alg_b = FRAME_ALG_BYTES
         peak, _ = read_peak()

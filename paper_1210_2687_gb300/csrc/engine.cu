@@ -650,7 +650,7 @@ int admm_deconv_plan(admm_plan_t* out, const admm_params_t* p, void* stream) {
     const size_t oxs = take(n * sizeof(float));
     const size_t ops = take(pl->psf.size() * sizeof(float));
     const size_t ozm = take(tvp ? 0 : (size_t)(levels + 1) * sizeof(CUtensorMap));
-    const bool zstate = !tvp && p->reg != ADMM_REG_HAAR_SYNTHESIS;   // zeta2 + bits (not FS-MD)
+    const bool zstate = !tvp;   // the frame priors' state: zeta2 + two bits per coefficient
     const size_t ozb = take(zstate ? n * sizeof(uint32_t) : 0);
     if (dev_alloc(&pl->slab, off) != cudaSuccess) {
         cudaGetLastError();
@@ -734,9 +734,9 @@ long long admm_deconv_state_size(admm_plan_t plan) {
 }
 
 // The second dual after iteration K (K >= 0), on the device: buffer K & 1 for
-// the TV priors and FS-MD (and buffer 0 before the first iteration); for the
-// frame analysis prior, d2 rebuilt from zeta2 (buffer 0) and the bits into
-// buffer 1, which its iterations do not use.
+// the TV priors (and buffer 0 before the first iteration); for the frame
+// priors, d2 rebuilt from zeta2 (buffer 0) and the bits into buffer 1, which
+// their iterations read only at iteration 1 of a restored FS-MD state.
 static cudaError_t second_dual(admm_plan_s* plan, int K, const float** d2, cudaStream_t s) {
     const size_t n = (size_t)plan->p.H * plan->p.W;
     if (!plan->zbits || K < 1) {
@@ -894,10 +894,10 @@ int admm_deconv_get_full_state(admm_plan_t plan, float* state, int* iters, void*
                          (size_t)plan->Wp * sizeof(float4), (size_t)plan->Wc * sizeof(float4), (size_t)H,
                          cudaMemcpyDefault, s));
     if (plan->p.reg == ADMM_REG_HAAR_SYNTHESIS) {
-        // FS-MD's next iteration also reads the last w and zeta2 (left in the
-        // d2 buffer the next iteration writes)
+        // FS-MD's next iteration also reads the last w and zeta2 (zeta2 in
+        // d2 buffer 0 after an iteration; before one, a restored zeta2 in buffer 1)
         CK(cudaMemcpyAsync(state + extra_off, plan->work + 2 * n, n * sizeof(float), cudaMemcpyDefault, s));
-        const float* z2 = plan->d2 + (size_t)((K + 1) & 1) * plan->nb * n;
+        const float* z2 = plan->d2 + (size_t)(K >= 1 ? 0 : 1) * plan->nb * n;
         CK(cudaMemcpyAsync(state + extra_off + n, z2, (size_t)plan->nb * n * sizeof(float), cudaMemcpyDefault, s));
     }
     if (reg_cg(plan->p.reg))

@@ -31,9 +31,9 @@
 // of all bands of a pixel in one word (zbits); the synthesis (a separate
 // launch) reads zeta2 there with its halo. Iteration 1 reads d2 itself from
 // buffer 0 (zero, a warm start or a restored state). The synthesis
-// formulation (FS-MD) keeps d2 in two buffers by iteration parity (iteration
-// k reads buffer (k+1)&1 and writes buffer k&1) and zeta2 over the d2 it has
-// read, where its next analysis also reads the previous zeta2.
+// formulation (FS-MD) keeps the same state: its analysis also needs the
+// previous zeta2, which is the value it reads there (at iteration 1 of a
+// restored state, from buffer 1).
 #pragma once
 #include <cuda_runtime.h>
 #include <cstdint>
@@ -223,7 +223,7 @@ haar_analysis(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W, in
     if (ctl->active == 0) return;
     const int k = ctl->iter + 1;
     const bool first = k == 1 && !P.warm;        // d2 = 0 (cold start: u0 = d0 = 0)
-    const bool raw = FS || k == 1;               // buffer holds d2 itself (not zeta2 and bits)
+    const bool raw = k == 1;                     // buffer holds d2 itself (not zeta2 and bits)
     const bool chk = is_check_iter(P, k), nobj = need_obj_iter(P, k);
     extern __shared__ __align__(16) float sm[];
     float* Ain = sm;
@@ -234,9 +234,10 @@ haar_analysis(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W, in
     const int tiles_x = W / T;
     const int R0 = (blockIdx.x / tiles_x) * T, C0 = (blockIdx.x % tiles_x) * T;
     const size_t n = (size_t)H * W;
-    // previous state in, zeta2 out (FS-MD: the parity buffers, the new d2 to d2out)
-    float* __restrict__ d2io = P.d2 + (FS ? ((k + 1) & 1) * P.d2_stride : 0);
-    float* __restrict__ d2out = P.d2 + (k & 1) * P.d2_stride;
+    // previous state in, zeta2 out; FS-MD at iteration 1 of a restored state:
+    // the previous zeta2 in buffer 1
+    float* __restrict__ d2io = P.d2;
+    const float* __restrict__ z1in = P.d2 + P.d2_stride;
 
     // x on [0, T + HALO) x [0, T + 16) with periodic wrap, 16-byte copies (the
     // tile origin is a multiple of 32 columns)
@@ -300,6 +301,8 @@ haar_analysis(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W, in
         if (lvl + 1 < L) cp_async_wait<1>();
         else cp_async_wait<0>();
         float dold[3][4];
+        // FS: the previous iteration's zeta2 of this level's bands (own pixels)
+        float zprev[3][4] = {};
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
             const float4 v = first ? make_float4(0.f, 0.f, 0.f, 0.f)
@@ -308,22 +311,18 @@ haar_analysis(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W, in
             if (!raw) {
                 const int b = 3 * lvl + j;
 #pragma unroll
-                for (int e = 0; e < 4; ++e)
+                for (int e = 0; e < 4; ++e) {
+                    if (FS) zprev[j][e] = dold[j][e];
                     dold[j][e] = dual_from_zeta(dold[j][e], obits[e] >> (2 * b), P.band_tau[b], P.band_izs[b]);
+                }
+            } else if (FS && !first) {
+                const float4 zv = *reinterpret_cast<const float4*>(z1in + (size_t)(3 * lvl + j) * n + gq);
+                zprev[j][0] = zv.x; zprev[j][1] = zv.y; zprev[j][2] = zv.z; zprev[j][3] = zv.w;
             }
         }
         // the slot is consumed (the last level's low-low entries are read
         // after the loop, and nothing is staged after the last level)
         if (lvl + 2 < L) stage(lvl + 2);
-        // FS: the previous iteration's zeta2 of this level's bands (own pixels)
-        float zprev[3][4] = {};
-        if (FS && !first) {
-#pragma unroll
-            for (int j = 0; j < 3; ++j) {
-                const float4 v = *reinterpret_cast<const float4*>(d2out + (size_t)(3 * lvl + j) * n + gq);
-                zprev[j][0] = v.x; zprev[j][1] = v.y; zprev[j][2] = v.z; zprev[j][3] = v.w;
-            }
-        }
         const int D = T + (1 << L) - 2 * s;      // a_{lvl+1} is needed on [0, D)^2
         // owned pixels: approximation, detail bands, soft threshold and dual
         // updates. a_lvl on rows orow and orow + s, columns ocol .. ocol + 3 + s
@@ -355,17 +354,11 @@ haar_analysis(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W, in
                 if (FS) cb[j] += zprev[j][e];                   // theta = P v + zeta2
                 const float sv = cb[j] - dold[j][e];
                 const float tb = P.band_tau[3 * lvl + j];
-                float u;
-                if (FS) {
-                    u = soft_thresh(sv, tb);                    // eq. soft
-                    nd4[j][e] = u - sv;                         // d2 - (c - u2)
-                } else {
-                    // the same, exactly: d2 - (c - u2) = -clamp(s, -tau, tau), and
-                    // u2 = s + that (= soft(s, tau), eq. soft, with its rounding)
-                    nd4[j][e] = copysignf(fminf(fabsf(sv), tb), -sv);
-                    u = sv + nd4[j][e];
-                    nbits[e] |= state_bits(sv, tb) << (2 * (3 * lvl + j));
-                }
+                // d2 - (c - u2) = -clamp(s, -tau, tau), exactly, and u2 = s +
+                // that (= soft(s, tau), eq. soft, with its rounding)
+                nd4[j][e] = copysignf(fminf(fabsf(sv), tb), -sv);
+                const float u = sv + nd4[j][e];
+                nbits[e] |= state_bits(sv, tb) << (2 * (3 * lvl + j));
                 // zeta2 = u2 + d2, times gamma_b / gamma for the synthesis
                 z4[j][e] = (u + nd4[j][e]) * P.band_zs[3 * lvl + j];
                 if (nobj) {
@@ -380,7 +373,6 @@ haar_analysis(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W, in
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
             const size_t bo = (size_t)(3 * lvl + j) * n + gq;
-            if (FS) *reinterpret_cast<float4*>(d2out + bo) = make_float4(nd4[j][0], nd4[j][1], nd4[j][2], nd4[j][3]);
             *reinterpret_cast<float4*>(d2io + bo) = make_float4(z4[j][0], z4[j][1], z4[j][2], z4[j][3]);
         }
         // the approximation on the rest of [0, D)^2 that later levels read
@@ -417,14 +409,15 @@ haar_analysis(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W, in
                                                                    orow * T + ocol);
         const float4 cv = *reinterpret_cast<const float4*>(Ain + orow * XA + ocol);
         float dold[4] = {dv.x, dv.y, dv.z, dv.w};
+        float cb[4] = {cv.x, cv.y, cv.z, cv.w};
         if (!raw) {
 #pragma unroll
-            for (int e = 0; e < 4; ++e)
+            for (int e = 0; e < 4; ++e) {
+                if (FS) cb[e] += dold[e];                     // theta = P v + zeta2
                 dold[e] = dual_from_zeta(dold[e], obits[e] >> (2 * 3 * L), tau_ll, P.band_izs[3 * L]);
-        }
-        float cb[4] = {cv.x, cv.y, cv.z, cv.w};
-        if (FS && !first) {
-            const float4 zv = *reinterpret_cast<const float4*>(d2out + (size_t)(3 * L) * n + gq);
+            }
+        } else if (FS && !first) {
+            const float4 zv = *reinterpret_cast<const float4*>(z1in + (size_t)(3 * L) * n + gq);
             cb[0] += zv.x; cb[1] += zv.y; cb[2] += zv.z; cb[3] += zv.w;
         }
         float nd[4], z[4];
@@ -432,15 +425,9 @@ haar_analysis(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W, in
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             const float sv = cb[e] - dold[e];
-            float u;
-            if (FS) {
-                u = soft_thresh(sv, tau_ll);
-                nd[e] = u - sv;
-            } else {
-                nd[e] = copysignf(fminf(fabsf(sv), tau_ll), -sv);
-                u = sv + nd[e];
-                nbits[e] |= state_bits(sv, tau_ll) << (2 * 3 * L);
-            }
+            nd[e] = copysignf(fminf(fabsf(sv), tau_ll), -sv);
+            const float u = sv + nd[e];
+            nbits[e] |= state_bits(sv, tau_ll) << (2 * 3 * L);
             z[e] = (u + nd[e]) * P.band_zs[3 * L];
             if (nobj) {
                 if (!ll_free) l1.add(fabsf(cb[e]));
@@ -450,9 +437,8 @@ haar_analysis(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W, in
         }
         if (nobj) pr.add(prl);
         const size_t bo = (size_t)(3 * L) * n + gq;
-        if (FS) *reinterpret_cast<float4*>(d2out + bo) = make_float4(nd[0], nd[1], nd[2], nd[3]);
         *reinterpret_cast<float4*>(d2io + bo) = make_float4(z[0], z[1], z[2], z[3]);
-        if (!FS) *reinterpret_cast<uint4*>(P.zbits + gq) = make_uint4(nbits[0], nbits[1], nbits[2], nbits[3]);
+        *reinterpret_cast<uint4*>(P.zbits + gq) = make_uint4(nbits[0], nbits[1], nbits[2], nbits[3]);
     }
     double pv[kNumPartials] = {0.0};
     if (nobj || chk) {
@@ -525,7 +511,6 @@ haar_synthesis(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W) {
     const ProbDesc& P = probs[pi];
     // retired in this iteration, or a problem that has just taken over the slot
     if (P.ctl->active == 0 || P.ctl->iter == 0) return;
-    const int k = P.ctl->iter;
     extern __shared__ __align__(128) float syn_sm[];
     float* sm = syn_sm;
     float* At = sm;
@@ -536,9 +521,9 @@ haar_synthesis(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W) {
     const int tiles_x = W / T;
     const int R0 = (blockIdx.x / tiles_x) * T, C0 = (blockIdx.x % tiles_x) * T;
     const size_t n = (size_t)H * W;
-    // zeta2: buffer 0 (FS-MD: buffer (k+1)&1, over the d2 its analysis read)
-    const int zb = P.zbits ? 0 : ((k + 1) & 1);
-    const float* __restrict__ zeta = P.d2 + zb * P.d2_stride;
+    // zeta2: in d2 buffer 0, where the analysis has just written it
+    constexpr int zb = 0;
+    const float* __restrict__ zeta = P.d2;
     // Tiles whose halo stays inside the image (every tile but the first row
     // and column; the halo lies above and to the left) take their boxes by
     // TMA, one thread issuing one copy per level (and one for the low-low
