@@ -38,7 +38,8 @@ cudaError_t set_row_attrs() {
     static bool attr = false;
     if (attr) return cudaSuccess;
     constexpr int smem = (int)grow_smem<W>();
-    cudaError_t e = cudaFuncSetAttribute(grow_inv<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = cudaFuncSetAttribute(grow_inv<W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)grow_inv_smem<W>());
     if (e == cudaSuccess) e = cudaFuncSetAttribute(grow_fwd<W, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(grow_fwd<W, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e == cudaSuccess) attr = true;
@@ -54,7 +55,7 @@ cudaError_t rows_t(int H, int Wc, int Wp, const ProbDesc* d, SlotTable sl, int c
     const int nrow = H / G;
     const dim3 rgrid(nrow, count), blk(kThreads);
     const size_t smem = grow_smem<W>();
-    e = launch_chain(grow_inv<W>, rgrid, blk, smem, s, d, sl, H, Wp, twW);
+    e = launch_chain(grow_inv<W>, rgrid, blk, grow_inv_smem<W>(), s, d, sl, H, Wp, twW);
     if (e != cudaSuccess) return e;
     if (reg == 0 || reg == 2) {          // ADMM_REG_TV, ADMM_REG_TV_ANISO
         const dim3 tg(cg_num_tiles(H, W), count);

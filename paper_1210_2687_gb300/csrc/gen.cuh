@@ -29,13 +29,17 @@ template <int W> struct GRow {
 
 // ---------------------------------------------------------------------------
 // column phase. Grid (Wp / CB, slots), CB = columns per CTA = one per group.
-// The H x CB tile is staged in shared memory; once every group holds its
-// column in registers the tile doubles as the groups' exchange buffers.
+// The H x CB tile, the twiddles and the spectra Lambda, K of the CB columns
+// are requested with cp.async at entry (the spectra are read from shared
+// memory between the transforms instead of from global memory there); once
+// every group holds its column in registers the tile doubles as the groups'
+// exchange buffers.
 // ---------------------------------------------------------------------------
 template <int H> struct GCol {
     static constexpr int T = GShape<H>::T, E = GShape<H>::E;
     static constexpr int CB = kThreads / T;
-    static constexpr size_t SMEM = (size_t)H * CB * sizeof(float4) + (size_t)H * sizeof(float2);
+    static constexpr size_t SMEM = (size_t)H * CB * sizeof(float4) + (size_t)H * sizeof(float2)
+                                 + (size_t)H * CB * (sizeof(float2) + sizeof(float));
 };
 
 template <int H>
@@ -60,12 +64,24 @@ gcol_phase(const ProbDesc* __restrict__ probs, SlotTable sl, int Wc, int Wp, con
     extern __shared__ __align__(16) float4 gsm4[];
     float4* stage = gsm4;                        // H x CB, row-major
     float2* tw = reinterpret_cast<float2*>(stage + H * CB);
+    float2* lks = tw + H;                        // Lambda of the CB columns (H each), then K
+    float* kks = reinterpret_cast<float*>(lks + H * CB);
     const int tid = threadIdx.x, g = tid / T, t = tid % T;
     for (int e = tid; e < H * CB; e += kThreads) {
         const int r = e / CB, c = e % CB;
-        stage[e] = P.Sb[(size_t)r * Wp + c0 + c];
+        cp_async16(stage + e, P.Sb + (size_t)r * Wp + c0 + c);
     }
-    for (int e = tid; e < H; e += kThreads) tw[e] = twH[e];
+    for (int e = tid; e < H / 2; e += kThreads) cp_async16(tw + 2 * e, twH + 2 * e);
+#pragma unroll 1
+    for (int c = 0; c < CB; ++c) {
+        if (c0 + c >= Wc) break;
+        const float2* __restrict__ lcol = P.lamT + (size_t)(c0 + c) * H;
+        const float* __restrict__ kcol = P.kT + (size_t)(c0 + c) * H;
+        for (int e = tid; e < H / 2; e += kThreads) cp_async16(lks + c * H + 2 * e, lcol + 2 * e);
+        for (int e = tid; e < H / 4; e += kThreads) cp_async16(kks + c * H + 4 * e, kcol + 4 * e);
+    }
+    cp_async_commit();
+    cp_async_wait<0>();
     __syncthreads();
     const int kc = c0 + g;
     const bool spec = kc < Wc;
@@ -82,8 +98,8 @@ gcol_phase(const ProbDesc* __restrict__ probs, SlotTable sl, int Wc, int Wp, con
     gfft<H, -1>(v, t, g, tw, bv);
     gfft<H, -1>(u, t, g, tw, bu);
     if (spec) {
-        const float2* __restrict__ lcol = P.lamT + (size_t)kc * H;
-        const float* __restrict__ kcol = P.kT + (size_t)kc * H;
+        const float2* lcol = lks + g * H;
+        const float* kcol = kks + g * H;
         const float inv_hw = 1.0f / (float)(H * 2 * (Wc - 1));
 #pragma unroll
         for (int e = 0; e < E; ++e) {
@@ -126,10 +142,25 @@ grow_inv(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp, const 
     extern __shared__ __align__(16) float2 gsm2[];
     float2* buf = gsm2;                          // G x W
     float2* tw = buf + G * W;
+    // d1, M^T y and x_prev of this thread's own pixels, requested before the
+    // transform (the thread reads back only what it copied itself)
+    float* pre = reinterpret_cast<float*>(tw + W);   // 3 x G x W
     __shared__ float red[kThreads / 32 * 2 * kNumPartials];
     const int tid = threadIdx.x, g = tid / T, t = tid % T;
     const int q = blockIdx.x * G + g;
     const size_t n = (size_t)H * W;
+    float* pd1 = pre + (size_t)(3 * g) * W;
+    float* pyb = pd1 + W;
+    float* pxp = pyb + W;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int c = t + T * e;
+        const size_t pix = (size_t)q * W + c;
+        if (!cold) cp_async4(pd1 + c, P.d1 + pix);
+        cp_async4(pyb + c, P.ybar + pix);
+        if (chk && !first) cp_async4(pxp + c, P.xprev + pix);
+    }
+    cp_async_commit();
     for (int e = tid; e < W; e += kThreads) tw[e] = twW[e];
     __syncthreads();
     // the full spectrum of the complex row x + i A x from the two stored halves
@@ -147,6 +178,7 @@ grow_inv(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp, const 
         }
     }
     gfft<W, 1>(v, t, g, tw, buf + (size_t)g * W);
+    cp_async_wait<0>();          // this thread's staged inputs have landed
     float* __restrict__ xw = P.work;
     float* __restrict__ z1w = P.work + n;
     const float mu1 = P.mu1, inv1 = P.inv1pmu1;
@@ -156,9 +188,9 @@ grow_inv(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp, const 
         const size_t pix = (size_t)q * W + t + T * e;
         const float x = v[e].x, ax = v[e].y;
         // u1 = (M^T M + mu1 I)^{-1} (M^T y + mu1 (A x - d1)); d1 <- d1 - (A x - u1)
-        const float dd1 = cold ? 0.f : P.d1[pix];
+        const float dd1 = cold ? 0.f : pd1[t + T * e];
         const float s1 = ax - dd1;
-        const float yb = P.ybar[pix];
+        const float yb = pyb[t + T * e];
         const bool obs = is_observed(yb);
         const float u1 = obs ? fmaf(mu1, s1, yb) * inv1 : s1;
         const float nd1 = dd1 - (ax - u1);
@@ -174,7 +206,7 @@ grow_inv(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp, const 
             s_pr.add(e1 * e1);
         }
         if (chk) {
-            const float dx = first ? x : x - P.xprev[pix];
+            const float dx = first ? x : x - pxp[t + T * e];
             s_dxx.add(dx * dx);
             s_xx.add(x * x);
         }
@@ -251,6 +283,10 @@ grow_fwd(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp, const 
 }
 
 template <int W> constexpr size_t grow_smem() { return (size_t)(GRow<W>::G * W + W) * sizeof(float2); }
+// the inverse rows also stage d1, M^T y and x_prev of their G rows
+template <int W> constexpr size_t grow_inv_smem() {
+    return grow_smem<W>() + (size_t)3 * GRow<W>::G * W * sizeof(float);
+}
 
 // Launch chain of one iteration on an exact generic domain (gen.cu).
 cudaError_t launch_gen_iteration(int W, int H, int Wc, int Wp, const ProbDesc* d, SlotTable sl, int count,
