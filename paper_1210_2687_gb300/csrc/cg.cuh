@@ -298,20 +298,31 @@ tv_tile(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W, int n_ro
     const bool chk = is_check_iter(P, k), nobj = need_obj_iter(P, k);
     __shared__ float xs[XR * XS];                // x on rows R0-1 .. R0+T, columns C0-1 .. C0+T
     __shared__ float2 dl[DR * DR];               // delta on rows R0-1 .. R0+T-1, columns C0-1 .. C0+T-1
+    __shared__ __align__(8) float2 d2s[DR * DR]; // the previous d2 on the same region
     __shared__ float red[kThreads / 32 * 2 * kNumPartials];
     const int tid = threadIdx.x;
     const int tiles_x = W / T;
     const int R0 = (blockIdx.x / tiles_x) * T, C0 = (blockIdx.x % tiles_x) * T;
     const size_t n = (size_t)H * W;
     const float* __restrict__ xw = P.work;
+    const float2* __restrict__ d2in = reinterpret_cast<const float2*>(P.d2 + ((k + 1) & 1) * P.d2_stride);
+    float2* __restrict__ d2out = reinterpret_cast<float2*>(P.d2 + (k & 1) * P.d2_stride);
+    // x and the previous d2 of the region requested together (cp.async)
     for (int e = tid; e < XR * XR; e += kThreads) {
         const int rr = e / XR, cc = e - rr * XR;
         const int r = wrapi(R0 - 1 + rr, H), c = wrapi(C0 - 1 + cc, W);
-        xs[rr * XS + cc] = xw[(size_t)r * W + c];
+        cp_async4(&xs[rr * XS + cc], xw + (size_t)r * W + c);
     }
+    if (!first) {
+        for (int e = tid; e < DR * DR; e += kThreads) {
+            const int rr = e / DR, cc = e - rr * DR;
+            const int r = wrapi(R0 - 1 + rr, H), c = wrapi(C0 - 1 + cc, W);
+            cp_async8(&d2s[e], d2in + (size_t)r * W + c);
+        }
+    }
+    cp_async_commit();
+    cp_async_wait<0>();
     __syncthreads();
-    const float2* __restrict__ d2in = reinterpret_cast<const float2*>(P.d2 + ((k + 1) & 1) * P.d2_stride);
-    float2* __restrict__ d2out = reinterpret_cast<float2*>(P.d2 + (k & 1) * P.d2_stride);
     const float tau = P.tau;
     CompSum tvs, prs;
     for (int e = tid; e < DR * DR; e += kThreads) {
@@ -321,7 +332,7 @@ tv_tile(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W, int n_ro
         const float x0 = xs[rr * XS + cc];
         const float gh = xs[rr * XS + cc + 1] - x0;
         const float gv = xs[(rr + 1) * XS + cc] - x0;
-        const float2 dold = first ? make_float2(0.f, 0.f) : d2in[pix];
+        const float2 dold = first ? make_float2(0.f, 0.f) : d2s[e];
         float uh, uv;
         tv_prox(gh - dold.x, gv - dold.y, tau, ANISO, uh, uv);
         const float ndh = dold.x - (gh - uh), ndv = dold.y - (gv - uv);
