@@ -67,9 +67,11 @@ struct ProbDesc {
     float4* Sb;               // H x Wp: row-phase output (row-DFTs of zeta1, w)
     float* d1;                // H x W
     float* d2;                // two buffers of d2_stride floats each (TV: H x W float2
-                              // (h, v); frame: nb x H x W planes); iteration k reads
-                              // buffer (k+1)&1 and writes buffer k&1, so CTAs that
-                              // recompute a neighbour's halo always see the old d2
+                              // (h, v); frame: nb x H x W planes). TV: iteration k
+                              // reads buffer (k+1)&1 and writes buffer k&1, so CTAs
+                              // that recompute a neighbour's halo always see the old
+                              // d2. Frame priors: zeta2 in place in buffer 0, beside
+                              // zbits (haar.cuh)
     long long d2_stride;
     const float* ybar;        // H x W, M^T y (0 where unobserved)
     const uint8_t* mask;      // H x W, 1 = observed (effective mask); the iteration
