@@ -714,6 +714,10 @@ int admm_deconv_plan(admm_plan_t* out, const admm_params_t* p, void* stream) {
         if (cudaStreamSynchronize(s) != cudaSuccess) { rc = ADMM_ECUDA; break; }
     } while (0);
     if (rc != ADMM_OK) {
+        // the copies queued above read host memory of this call (the PSF, the
+        // tensor maps): let them finish before it goes away
+        cudaStreamSynchronize(s);
+        cudaGetLastError();
         free_plan(pl);
         return rc;
     }
