@@ -98,6 +98,29 @@ def test_restart_from_full_state_is_bit_identical(ad, reg, H, W, psf_fn, keep, l
         p.close()
 
 
+@pytest.mark.parametrize("reg", ["tv", "haar", "haar_synthesis", "haar_cg"])
+def test_state_round_trip_before_any_iteration(ad, reg):
+    """set_state on a fresh plan, then get_full_state and get_state before
+    any solve: the same floats come back (the frame priors keep zeta2 and
+    bits only once an iteration has run; before that the buffers hold the
+    restored d2, and for FS-MD the restored zeta2, as given)."""
+    import torch
+    H, W = 64, 128                # the Reeves-Sorel variants take powers of two
+    psf = S.psf_box(5)
+    plan = ad.Plan(H, W, psf, 1e-3, 3e-3, 1e-2, reg, max_iters=5)
+    g = np.random.default_rng(5)
+    st = g.standard_normal(plan.full_state_size()).astype(np.float32)
+    plan.set_state(st)
+    out = torch.empty(plan.full_state_size(), dtype=torch.float32, device="cuda")
+    plan.get_full_state(out)
+    assert np.array_equal(out.cpu().numpy(), st)
+    d = torch.empty(plan.state_size(), dtype=torch.float32, device="cuda")
+    ad.admm_deconv_get_state(plan.handle, d.data_ptr())
+    torch.cuda.synchronize()
+    assert np.array_equal(d.cpu().numpy(), st[:plan.state_size()])
+    plan.close()
+
+
 def test_restart_resumes_the_oracle_sequence(ad):
     """The restarted GPU run follows the FP64 oracle's 60-iteration sequence
     (TV, 128 x 128) to the tolerance of the fixed-iteration parity tests."""
