@@ -207,8 +207,9 @@ struct HaarAnaCfg {
 // coefficients are theta = P (x - P^T zeta2) + zeta2 (the theta-step of the
 // synthesis problem with W = P^T, reduced with W W^T = I and the x-step's
 // equation A^T (zeta1 - A x) = gamma (x - P^T zeta2)); P^T zeta2 = w / gamma
-// is the previous synthesis output and zeta2 the previous iteration's, still
-// in the buffer that receives the new d2.
+// is the previous synthesis output and zeta2 the previous iteration's: the
+// stored state the tile reads anyway (buffer 1 at iteration 1 of a restored
+// state).
 template <int L, bool FS = false>
 __global__ void __launch_bounds__(kThreads, 4)
 haar_analysis(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int W, int n_row_ctas,
