@@ -55,8 +55,9 @@ extern "C" {
 #define ADMM_ENONFINITE          -5  /* an observed value or the iterate is NaN/Inf
                                         (divergence, Theorem 1)                            */
 #define ADMM_ETIMEOUT            -6  /* a bounded device wait expired: the TV row phase
-                                        waits (at most about a second) for the bulk copies
-                                        of its spectrum rows; a problem whose wait ran out
+                                        (the bulk copies of its spectrum rows) and the frame
+                                        synthesis tile (its TMA halo boxes) wait at most
+                                        about a second; a problem whose wait ran out
                                         retires with this status (also in res->status)     */
 
 /* ---- enums -------------------------------------------------------------- */
