@@ -55,6 +55,8 @@ CASES = [
     (128, 128, lambda: S.psf_box(5), 0.9, 4, 2),
     (512, 512, lambda: S.psf_box(13), None, 5, 4),
     (64, 1024, lambda: S.psf_gaussian(5, 1.0), None, 6, 3),
+    # 2048-point rows: the row kernels read their twiddles through L1
+    (64, 2048, lambda: S.psf_box(5), 0.8, 7, 4),
 ]
 
 
