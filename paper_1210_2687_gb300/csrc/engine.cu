@@ -107,6 +107,8 @@ struct DeviceCtx {
     int* h_active = nullptr;         // pinned, 2 x cap (double-buffered copy of n_active)
     ProbCtl* h_ctl = nullptr;        // pinned copy-back area
     ProbDesc* h_desc = nullptr;      // pinned staging for the table
+    PrepItem* prep = nullptr;        // input preparation of a batch call (cap entries)
+    PrepItem* h_prep = nullptr;      // ... pinned staging
     float** h_xptr = nullptr;
     cudaEvent_t ev[2] = {nullptr, nullptr};
     static constexpr int kBranches = 8;             // capture streams (graph branches)
@@ -252,7 +254,10 @@ int ensure_ctx(int dev, int count, DeviceCtx** out) {
         if (c.h_ctl) cudaFreeHost(c.h_ctl);
         if (c.h_desc) cudaFreeHost(c.h_desc);
         if (c.h_xptr) cudaFreeHost(c.h_xptr);
+        if (c.prep) cudaFree(c.prep);
+        if (c.h_prep) cudaFreeHost(c.h_prep);
         c.desc = nullptr; c.xptr = nullptr; c.h_ctl = nullptr; c.h_desc = nullptr; c.h_xptr = nullptr;
+        c.prep = nullptr; c.h_prep = nullptr;
         c.slot_map = nullptr;
         c.queue = nullptr;
         c.n_active = nullptr;
@@ -269,6 +274,8 @@ int ensure_ctx(int dev, int count, DeviceCtx** out) {
         CK(host_alloc(&c.h_ctl, cap * sizeof(ProbCtl)));
         CK(host_alloc(&c.h_desc, cap * sizeof(ProbDesc)));
         CK(host_alloc(&c.h_xptr, cap * sizeof(float*)));
+        CK(dev_alloc(&c.prep, cap * sizeof(PrepItem)));
+        CK(host_alloc(&c.h_prep, cap * sizeof(PrepItem)));
         c.cap = cap;
     }
     *out = &c;
@@ -1089,6 +1096,29 @@ static int solve_all_impl(DeviceCtx* ctx, const std::vector<std::vector<int>>& c
     std::vector<int> order;                       // table position -> index into plans
     std::vector<char> x_host;
     int soff = 0, qbase = 0;
+    // input preparation, batched: items [prep_done, prep_n) of the pinned
+    // staging table are prepared by the next flush (before a learned start
+    // reads its problem's prepared input, and after the last problem)
+    int prep_done = 0, prep_n = 0, prep_maxn = 0;
+    auto flush_prep = [&]() -> int {
+        const int cnt = prep_n - prep_done;
+        if (cnt <= 0) return ADMM_OK;
+        CK(cudaMemcpyAsync(ctx->prep + prep_done, ctx->h_prep + prep_done, cnt * sizeof(PrepItem),
+                           cudaMemcpyHostToDevice, s));
+        constexpr int words = (int)(sizeof(ProbCtl) / sizeof(int));
+        zero_ctl_kernel<<<(unsigned)((cnt * words + 255) / 256), 256, 0, s>>>(ctx->prep + prep_done, cnt);
+        CK(cudaGetLastError());
+        const unsigned bx = (unsigned)std::min((prep_maxn + 255) / 256, 512);
+        for (int o = 0; o < cnt; o += 65535) {   // (grid.y limit)
+            prepare_items_kernel<<<dim3(bx, (unsigned)std::min(cnt - o, 65535)), 256, 0, s>>>(ctx->prep + prep_done + o);
+            CK(cudaGetLastError());
+            ++g_launches;
+        }
+        ++g_launches;
+        prep_done = prep_n;
+        prep_maxn = 0;
+        return ADMM_OK;
+    };
     for (const std::vector<int>& idx : classes) {
         GroupRun g;
         const admm_plan_s* p0 = plans[idx[0]];
@@ -1139,14 +1169,12 @@ static int solve_all_impl(DeviceCtx* ctx, const std::vector<std::vector<int>>& c
                 CK(cudaMemcpyAsync(pl->mstage, mj, nu, cudaMemcpyHostToDevice, s));
                 mj = pl->mstage;
             }
-            CK(cudaMemsetAsync(pl->ctl, 0, sizeof(ProbCtl), s));
-            prepare_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(pl->ybar, pl->mask, yj, mj, g.H, g.W,
-                                                                       pl->Hu, pl->Wu,
-                                                                       pl->p.psf_h / 2, pl->p.psf_w / 2,
-                                                                       pl->p.raw_mask, pl->ctl);
-            CK(cudaGetLastError());
-            ++g_launches;
+            ctx->h_prep[prep_n++] = PrepItem{pl->ybar, pl->mask, yj, mj, pl->ctl, g.H, g.W, pl->Hu, pl->Wu,
+                                             pl->p.psf_h / 2, pl->p.psf_w / 2, pl->p.raw_mask};
+            prep_maxn = std::max(prep_maxn, (int)n);
             if (use_ws && pl->warm_mode == 0 && pl->p.reg == ADMM_REG_TV) {
+                int rp = flush_prep();
+                if (rp != ADMM_OK) return rp;
                 // learned start: the network reads [M^T y, mask] just prepared and
                 // writes x0 (to the staging plane) and d0 = (d1, d2 buffer 0),
                 // contiguous in the plan's slab; u0 = H x0 - d0 as in
@@ -1185,6 +1213,10 @@ static int solve_all_impl(DeviceCtx* ctx, const std::vector<std::vector<int>>& c
         soff += g.nslots;
         qbase += g.L.n;
         groups.push_back(g);
+    }
+    {
+        const int rp = flush_prep();     // the inputs of the problems not prepared yet
+        if (rp != ADMM_OK) return rp;
     }
     const int total = (int)order.size();
     const int ng = (int)groups.size();

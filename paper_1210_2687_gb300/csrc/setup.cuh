@@ -107,6 +107,43 @@ __global__ void prepare_kernel(float* __restrict__ ybar, uint8_t* __restrict__ m
     ybar[i] = obs ? v : __int_as_float(0x7fc00000);
 }
 
+// The same preparation for many problems in one launch (grid.y = problem),
+// after zero_ctl_kernel has cleared their control blocks: a batch call then
+// issues two launches instead of a copy and a launch per problem.
+struct PrepItem {
+    float* ybar;
+    uint8_t* mask;
+    const float* y;
+    const uint8_t* m;
+    ProbCtl* ctl;
+    int H, W, Hu, Wu, lr, lc, raw;
+};
+
+__global__ void zero_ctl_kernel(const PrepItem* __restrict__ items, int count) {
+    constexpr int words = (int)(sizeof(ProbCtl) / sizeof(int));
+    static_assert(sizeof(ProbCtl) % sizeof(int) == 0, "control block of whole words");
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count * words) return;
+    reinterpret_cast<int*>(items[i / words].ctl)[i % words] = 0;
+}
+
+__global__ void prepare_items_kernel(const PrepItem* __restrict__ items) {
+    const PrepItem it = items[blockIdx.y];
+    const int n = it.H * it.W;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int r = i / it.W, c = i % it.W;
+        const bool inside = r < it.Hu && c < it.Wu;
+        const size_t iu = (size_t)r * it.Wu + c;
+        bool obs = inside && ((it.m == nullptr) ? true : (it.m[iu] != 0));
+        if (!it.raw || it.m == nullptr)
+            obs = obs && r >= it.lr && r < it.Hu - it.lr && c >= it.lc && c < it.Wu - it.lc;
+        it.mask[i] = obs ? 1 : 0;
+        const float v = obs ? it.y[iu] : 0.0f;
+        if (obs && !isfinite(v)) atomicOr(&it.ctl->input_bad, 1);
+        it.ybar[i] = obs ? v : __int_as_float(0x7fc00000);
+    }
+}
+
 __global__ void init_ctl_kernel(ProbDesc* __restrict__ probs, int count, int* __restrict__ n_active) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= count) return;
