@@ -3,21 +3,23 @@
 // Adam. Not part of the paper; Theorem 1 (convergence from any u0, d0) is
 // what lets a predicted start feed Algorithm 2.
 //
-// Layout. Activations are NHWC BF16 with the channel count padded to 16 or
-// 32 (64 B per pixel at 32 channels), so a pixel's channels are one
-// contiguous run: the input tile of a CTA is a few coalesced row segments.
-// Packed weights are BF16 [tap][cout][cin] (cin contiguous), the order in
-// which the B operand of the MMA consumes them.
+// Layout. Activations and their gradients are BF16 in planes of eight
+// channels: [image][C / 8][H][W][8], C padded to 16 or 32. One plane row is
+// W x 16 contiguous bytes, so a halo tile of a plane is a few long row
+// segments (one TMA box of 160-byte rows for the tensor-core layers), and a
+// pixel's eight channels are the 16-byte K slice the MMAs consume. The
+// network's 4-channel output is FP32 [image][H][W][4]. Packed weights are
+// BF16 [tap][cout][cin] (cin contiguous), the order in which the B operand of
+// the MMA consumes them.
 //
-// Forward / input-gradient kernel: a CTA computes a 16 x 16 pixel tile for
-// all output channels. Its input tile (18 x 18 pixels with halo, zero outside
-// the image) and all nine taps of the weights sit in shared memory with the
-// pixel and weight-row strides padded by 8 elements, which makes every
-// fragment load conflict-free. Warp w owns tile rows 2w and 2w + 1 (one
-// m16 block each: 16 pixels of a row); the K loop runs over the 9 taps and
-// the input channels in steps of 16. The same kernel computes the gradient
-// in the input of a layer (a convolution with the flipped, transposed
-// weights), gated by the ReLU of the layer below.
+// The 32-channel layers (forward with bias and ReLU, and the input gradients)
+// run on tcgen05 (conv3x3_tc below). The last layer (4 outputs, padded to 8)
+// uses mma.sync: a CTA computes a 16 x 16 pixel tile; its input tile (18 x 18
+// pixels with halo, zero outside the image) and all nine taps of the weights
+// sit in shared memory with the pixel and weight-row strides padded by 8
+// elements, which makes every fragment load conflict-free. Warp w owns tile
+// rows 2w and 2w + 1 (one m16 block each: 16 pixels of a row); the K loop
+// runs over the 9 taps and the input channels in steps of 16.
 //
 // Weight-gradient kernel: per tap, dW_tap = G^T A_tap, a contraction over
 // pixels. A CTA of 9 warps (one per tap) loops over tiles; the gradient and
@@ -105,23 +107,25 @@ __device__ __forceinline__ void cp_async_wait_all() {
 
 // ---------------------------------------------------------------------------
 // network input: [M^T y, mask] in channels 0 and 1 of a 16-channel tensor
+// (two planes of eight channels; hw = H W)
 // ---------------------------------------------------------------------------
 __global__ void cnn_input_kernel(const float* __restrict__ ybar, const uint8_t* __restrict__ mask,
-                                 bf16* __restrict__ a0, long long npx) {
+                                 bf16* __restrict__ a0, long long npx, long long hw) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= npx) return;
     const bool obs = mask[i] != 0;
     const float y = obs ? ybar[i] : 0.f;
-    uint4 lo = make_uint4(pack2(__float2bfloat16(y), __float2bfloat16(obs ? 1.f : 0.f)), 0u, 0u, 0u);
-    uint4* dst = reinterpret_cast<uint4*>(a0 + i * 16);
-    dst[0] = lo;
-    dst[1] = make_uint4(0u, 0u, 0u, 0u);
+    const long long img = i / hw, px = i - img * hw;
+    uint4* dst = reinterpret_cast<uint4*>(a0 + (img * 2 * hw + px) * 8);
+    dst[0] = make_uint4(pack2(__float2bfloat16(y), __float2bfloat16(obs ? 1.f : 0.f)), 0u, 0u, 0u);
+    dst[hw] = make_uint4(0u, 0u, 0u, 0u);
 }
 
 // ---------------------------------------------------------------------------
-// 3 x 3 convolution on a 16 x 16 output tile (see the file comment)
+// the last layer: 3 x 3 convolution on a 16 x 16 output tile (see the file
+// comment), FP32 output with bias
 // ---------------------------------------------------------------------------
-enum { kModeReluBf16 = 0, kModeOutF32 = 1, kModeGateBf16 = 2 };
+enum { kModeReluBf16 = 0, kModeGateBf16 = 2 };   // epilogues of conv3x3_tc
 
 template <int CIN, int COUT>
 struct ConvCfg {
@@ -135,30 +139,29 @@ struct ConvCfg {
     static_assert(SMEM <= 48 * 1024, "fits the default shared-memory window");
 };
 
-// in: [img][H][W][CIN]; wpk: [9][COUT][CIN]; bias: [COUT real] or null;
-// out: bf16 [img][H][W][COUT] (modes 0, 2) or float [img][H][W][4] (mode 1);
-// gate (mode 2): bf16 [img][H][W][COUT], the gradient passes where gate > 0.
-template <int CIN, int COUT, int MODE>
+// in: [img][CIN / 8][H][W][8]; wpk: [9][COUT][CIN]; bias: [4];
+// out: float [img][H][W][4] (output channels 0..3 of the COUT computed).
+template <int CIN, int COUT>
 __global__ void __launch_bounds__(256)
 conv3x3_kernel(const bf16* __restrict__ in, const bf16* __restrict__ wpk, const float* __restrict__ bias,
-               int cout_real, void* __restrict__ out, const bf16* __restrict__ gate, int H, int W) {
+               float* __restrict__ out, int H, int W) {
     using C = ConvCfg<CIN, COUT>;
     extern __shared__ __align__(16) bf16 sm[];
     bf16* sIn = sm;
     bf16* sW = sm + C::IN_ELEMS;
     const int tid = threadIdx.x;
     const int c0 = blockIdx.x * kTile, r0 = blockIdx.y * kTile;
-    const size_t img = (size_t)blockIdx.z * H * W;
+    const size_t hw = (size_t)H * W, img = (size_t)blockIdx.z * hw;
 
-    // input tile with halo: CIN / 8 chunks of 16 B per pixel
-    constexpr int CH = CIN / 8;
-    for (int e = tid; e < C::HALO * C::HALO * CH; e += 256) {
-        const int pix = e / CH, ch = e % CH;
+    // input tile with halo: CIN / 8 planes, 16 B per pixel and plane
+    constexpr int CH = CIN / 8, NP = C::HALO * C::HALO;
+    for (int e = tid; e < NP * CH; e += 256) {
+        const int ch = e / NP, pix = e - ch * NP;
         const int ty = pix / C::HALO, tx = pix % C::HALO;
         const int gr = r0 + ty - 1, gc = c0 + tx - 1;
         bf16* dst = sIn + pix * C::PS + ch * 8;
         if (gr >= 0 && gr < H && gc >= 0 && gc < W)
-            cp_async16(dst, in + (img + (size_t)gr * W + gc) * CIN + ch * 8);
+            cp_async16(dst, in + (((size_t)blockIdx.z * CH + ch) * hw + (size_t)gr * W + gc) * 8);
         else
             *reinterpret_cast<uint4*>(dst) = make_uint4(0u, 0u, 0u, 0u);
     }
@@ -218,23 +221,9 @@ conv3x3_kernel(const bf16* __restrict__ in, const bf16* __restrict__ wpk, const 
 #pragma unroll
             for (int nt = 0; nt < NT; ++nt) {
                 const int ch = nt * 8 + 2 * t;
-                float v0 = acc[mt][nt][2 * half], v1 = acc[mt][nt][2 * half + 1];
-                if (MODE == kModeReluBf16) {
-                    v0 = ch < cout_real ? fmaxf(v0 + bias[ch], 0.f) : 0.f;
-                    v1 = ch + 1 < cout_real ? fmaxf(v1 + bias[ch + 1], 0.f) : 0.f;
-                    *reinterpret_cast<__nv_bfloat162*>(static_cast<bf16*>(out) + px * COUT + ch) =
-                        __floats2bfloat162_rn(v0, v1);
-                } else if (MODE == kModeOutF32) {
-                    if (ch < kOut)
-                        *reinterpret_cast<float2*>(static_cast<float*>(out) + px * kOut + ch) =
-                            make_float2(v0 + bias[ch], v1 + bias[ch + 1]);
-                } else {
-                    const __nv_bfloat162 gt = *reinterpret_cast<const __nv_bfloat162*>(gate + px * COUT + ch);
-                    v0 = __bfloat162float(gt.x) > 0.f ? v0 : 0.f;
-                    v1 = __bfloat162float(gt.y) > 0.f ? v1 : 0.f;
-                    *reinterpret_cast<__nv_bfloat162*>(static_cast<bf16*>(out) + px * COUT + ch) =
-                        __floats2bfloat162_rn(v0, v1);
-                }
+                if (ch < kOut)
+                    *reinterpret_cast<float2*>(out + px * kOut + ch) =
+                        make_float2(acc[mt][nt][2 * half] + bias[ch], acc[mt][nt][2 * half + 1] + bias[ch + 1]);
             }
         }
     }
@@ -253,16 +242,15 @@ conv3x3_kernel(const bf16* __restrict__ in, const bf16* __restrict__ wpk, const 
 //      groups (one tile row each) are 10 pixels = 160 B apart and its K
 //      chunks 180 x 16 B apart, so no im2col copy is needed;
 //   B: the weights as [tap][CIN/8][32 output channels][8].
-// The halo tile arrives by one TMA copy (cp.async.bulk.tensor, a 5-D view of
-// the NHWC activations whose innermost box dimension is 8 channels and whose
-// outermost is the 16-byte channel chunk, so the box lands in shared memory
-// already in the A layout; rows and columns outside the image read as zero),
-// double-buffered: the next tile's copy is in flight while the current tile
-// is multiplied and written out. One thread issues the 9 x CIN/16 MMAs of a
-// tile (K = 16 each) and commits them to an mbarrier; the four warps wait
-// (bounded), read their 32 lanes of the accumulator (tcgen05.ld) and apply
-// bias + ReLU (forward) or the ReLU gate of the layer below (input gradient),
-// storing NHWC BF16.
+// The halo tile arrives by one TMA copy (cp.async.bulk.tensor, a 4-D view of
+// the eight-channel planes whose innermost dimension merges a plane row's
+// columns and channels, so each box row is 10 pixels x 16 B = 160 contiguous
+// bytes and the box lands in shared memory already in the A layout; rows and
+// columns outside the image read as zero), double-buffered. One thread issues
+// the 9 x CIN/16 MMAs of a tile (K = 16 each) and commits them to an
+// mbarrier; the four warps wait (bounded), read their 32 lanes of the
+// accumulator (tcgen05.ld) and apply bias + ReLU (forward) or the ReLU gate of
+// the layer below (input gradient), storing four BF16 planes.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t sh_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -291,20 +279,21 @@ __device__ __forceinline__ unsigned long long gtimer_ns() {
     return t;
 }
 
-// wait for phase `parity` of the mbarrier, at most about a second
+// wait for phase `parity` of the mbarrier, at most about a second; try_wait
+// suspends the thread in hardware until the phase completes or a short
+// hardware time limit passes, so the loop does not spin
 __device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t parity) {
     const unsigned long long t0 = gtimer_ns();
     for (;;) {
         uint32_t done;
         asm volatile(
-            "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
             "selp.u32 %0, 1, 0, p;\n\t}\n"
             : "=r"(done)
             : "r"(mbar), "r"(parity)
             : "memory");
         if (done) return true;
         if (gtimer_ns() - t0 > 1000000000ull) return false;
-        __nanosleep(32);
     }
 }
 
@@ -333,9 +322,17 @@ constexpr int kTcTW = 8, kTcTH = 16;                 // output tile (M = 128)
 constexpr int kTcHW = kTcTW + 2, kTcHH = kTcTH + 2;  // halo tile
 constexpr int kTcNP = kTcHW * kTcHH;                 // 180 halo pixels
 
-// tin: TMA view of the input [img][H][W][CIN] (see conv_tc); wpk: [9][32][CIN];
-// out: bf16 [img][H][W][32]; MODE kModeReluBf16 (bias, ReLU) or kModeGateBf16
-// (gate [img][H][W][32]); err: set to 1 if a wait ran out (the CTA then stops)
+// tin: TMA view of the input [img][CIN / 8][H][W][8] (see conv_tc); wpk:
+// [9][32][CIN]; out: bf16 [img][4][H][W][8]; MODE kModeReluBf16 (bias, ReLU)
+// or kModeGateBf16 (gate [img][4][H][W][8]); err: set to 1 if a wait ran out (the CTA then stops,
+// after a bounded wait for its own copies and MMAs still in flight).
+//
+// Pipeline of the CTA's i-th tile (halo buffer and accumulator i & 1): thread
+// 0 waits for the halo of tile i + 1 and issues its MMAs into the other
+// accumulator; all four warps then wait for tile i's MMAs, thread 0 starts the
+// copy of tile i + 2's halo into the buffer they have finished reading, and
+// the warps read tile i's accumulator and store it while the tensor cores work
+// on tile i + 1.
 template <int CIN, int MODE>
 __global__ void __launch_bounds__(128)
 conv3x3_tc(const __grid_constant__ CUtensorMap tin, const bf16* __restrict__ wpk, const float* __restrict__ bias,
@@ -344,7 +341,9 @@ conv3x3_tc(const __grid_constant__ CUtensorMap tin, const bf16* __restrict__ wpk
     static_assert(CIN == 16 || CIN == 32, "input channels");
     __shared__ __align__(128) unsigned char smA[2][ABYTES];
     __shared__ __align__(128) unsigned char smW[9 * CH * COUT * 16];
-    __shared__ __align__(8) unsigned long long bars[3];   // 0, 1: halo of buffer 0 / 1 landed; 2: MMAs done
+    __shared__ float smB[COUT];
+    // 0, 1: halo of buffer 0 / 1 landed; 2, 3: MMAs into accumulator 0 / 1 done
+    __shared__ __align__(8) unsigned long long bars[4];
     __shared__ uint32_t tmem_base;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     for (int e = tid; e < 9 * COUT * CH; e += 128) {
@@ -352,32 +351,40 @@ conv3x3_tc(const __grid_constant__ CUtensorMap tin, const bf16* __restrict__ wpk
         const int tap = tc / COUT, co = tc - tap * COUT;
         cp_async16(smW + ((tap * CH + k) * COUT + co) * 16, wpk + (size_t)tc * CIN + k * 8);
     }
+    if (MODE == kModeReluBf16 && tid < COUT) smB[tid] = bias[tid];
     if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" ::"r"(sh_addr(&tmem_base))
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;" ::"r"(sh_addr(&tmem_base))
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     const int tiles_x = W / kTcTW, per_img = tiles_x * (H / kTcTH);
-    const int ntiles = per_img * count;
+    const int ntiles = per_img * count, G = gridDim.x;
     const uint64_t tmap = reinterpret_cast<uint64_t>(&tin);
-    // one TMA copy of tile t's halo into buffer b
+    // phase bits (bit b: barrier of buffer / accumulator b) and, in thread 0,
+    // the copies and MMA groups issued but not yet seen complete
+    uint32_t hph = 0, mph = 0, pend_h = 0, pend_m = 0;
+    // one TMA copy of tile t's halo into buffer b (thread 0)
     auto issue = [&](int t, int b) {
         const int img = t / per_img, rem = t - img * per_img;
         const int y0 = (rem / tiles_x) * kTcTH, x0 = (rem % tiles_x) * kTcTW;
         const uint32_t bar = sh_addr(&bars[b]);
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(ABYTES) : "memory");
+        // x: element (column x0 - 1, channel 0) of the merged row, a multiple of 8
+        // elements (16 B); column -1 and columns past W - 1 read as zero
         asm volatile(
-            "cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, "
-            "%6}], [%7];" ::"r"(sh_addr(smA[b])),
-            "l"(tmap), "r"(0), "r"(x0 - 1), "r"(y0 - 1), "r"(img), "r"(0), "r"(bar)
+            "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+            "%5}], [%6];" ::"r"(sh_addr(smA[b])),
+            "l"(tmap), "r"((x0 - 1) * 8), "r"(y0 - 1), "r"(0), "r"(img), "r"(bar)
             : "memory");
+        pend_h |= 1u << b;
     };
     if (tid == 0) {
-        for (int i = 0; i < 3; ++i)
+        for (int i = 0; i < 4; ++i)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sh_addr(&bars[i])) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("prefetch.tensormap [%0];" ::"l"(tmap) : "memory");
         if ((int)blockIdx.x < ntiles) issue(blockIdx.x, 0);
+        if ((int)blockIdx.x + G < ntiles) issue(blockIdx.x + G, 1);
     }
     cp_async_wait_all();
     fence_async_shared();        // the weights (generic proxy) are visible to the tensor cores
@@ -385,58 +392,68 @@ conv3x3_tc(const __grid_constant__ CUtensorMap tin, const bf16* __restrict__ wpk
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_base;
-    const uint32_t wBase = sh_addr(smW), mb = sh_addr(&bars[2]);
-    uint32_t full_phase0 = 0, full_phase1 = 0, mma_phase = 0;
+    const uint32_t wBase = sh_addr(smW);
+    // thread 0: wait for the halo in buffer b, then issue the tile's MMAs into
+    // accumulator b (columns 32 b) and commit them to bars[2 + b]
+    auto mma_tile = [&](int b) -> bool {
+        if (!mbar_wait_bounded(sh_addr(&bars[b]), (hph >> b) & 1u)) return false;
+        hph ^= 1u << b;
+        pend_h &= ~(1u << b);
+        tc_fence_after();
+        const uint32_t aBase = sh_addr(smA[b]), d = tmem + 32u * b;
+#pragma unroll
+        for (int tap = 0; tap < 9; ++tap) {
+            const int dy = tap / 3, dx = tap - 3 * (tap / 3);
+#pragma unroll
+            for (int j = 0; j < CH / 2; ++j) {
+                const uint64_t a = umma_desc(aBase + (2 * j * kTcNP + dy * kTcHW + dx) * 16, kTcNP * 16, kTcHW * 16);
+                const uint64_t bd = umma_desc(wBase + (tap * CH + 2 * j) * COUT * 16, COUT * 16, 8 * 16);
+                umma_f16(d, a, bd, kIdescM128N32, (tap | j) != 0 ? 1u : 0u);
+            }
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         sh_addr(&bars[2 + b]))
+                     : "memory");
+        pend_m |= 1u << b;
+        return true;
+    };
     bool ok = true;
+    if (tid == 0 && (int)blockIdx.x < ntiles) ok = mma_tile(0);
     int it = 0;
-    for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++it) {
-        const int buf = it & 1;
-        // the other buffer was last read by the previous tile's MMAs, which are complete
-        if (tid == 0 && tile + (int)gridDim.x < ntiles) issue(tile + gridDim.x, buf ^ 1);
-        const uint32_t fp = buf ? full_phase1 : full_phase0;
-        bool got = mbar_wait_bounded(sh_addr(&bars[buf]), fp);
-        if (buf) full_phase1 ^= 1u; else full_phase0 ^= 1u;
-        ok = __syncthreads_and(got) != 0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += G, ++it) {
+        const int b = it & 1;
+        // accumulator b ^ 1 was last read by the previous tile's epilogue,
+        // which ended at the block barrier below
+        if (tid == 0 && ok && tile + G < ntiles) ok = mma_tile(b ^ 1);
+        const bool got = mbar_wait_bounded(sh_addr(&bars[2 + b]), (mph >> b) & 1u);
+        if (got) {
+            mph ^= 1u << b;
+            pend_m &= ~(1u << b);
+        }
+        ok = __syncthreads_and(got && ok) != 0;
         if (!ok) break;
+        // tile's MMAs are complete, so its halo buffer is free
+        if (tid == 0 && tile + 2 * G < ntiles) issue(tile + 2 * G, b);
+        tc_fence_after();
         const int img = tile / per_img, rem = tile - img * per_img;
         const int y0 = (rem / tiles_x) * kTcTH, x0 = (rem % tiles_x) * kTcTW;
-        const size_t ibase = (size_t)img * H * W;
-        if (tid == 0) {
-            tc_fence_after();
-            const uint32_t aBase = sh_addr(smA[buf]);
-#pragma unroll
-            for (int tap = 0; tap < 9; ++tap) {
-                const int dy = tap / 3, dx = tap - 3 * (tap / 3);
-#pragma unroll
-                for (int j = 0; j < CH / 2; ++j) {
-                    const uint64_t a = umma_desc(aBase + (2 * j * kTcNP + dy * kTcHW + dx) * 16, kTcNP * 16, kTcHW * 16);
-                    const uint64_t b = umma_desc(wBase + (tap * CH + 2 * j) * COUT * 16, COUT * 16, 8 * 16);
-                    umma_f16(tmem, a, b, kIdescM128N32, (tap | j) != 0 ? 1u : 0u);
-                }
-            }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mb)
-                         : "memory");
-        }
-        got = mbar_wait_bounded(mb, mma_phase);
-        mma_phase ^= 1u;
-        ok = __syncthreads_and(got) != 0;
-        if (!ok) break;
-        tc_fence_after();
         float v[32];
-        tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16), v);
+        tmem_ld32(tmem + 32u * b + ((uint32_t)(32 * warp) << 16), v);
         const int oy = 4 * warp + (lane >> 3), ox = lane & 7;
-        const size_t px = ibase + (size_t)(y0 + oy) * W + (x0 + ox);
+        const size_t hw = (size_t)H * W;
+        // pixel's slot in plane 0 of its image; plane q is q hw slots further
+        const size_t px = (size_t)img * 4 * hw + (size_t)(y0 + oy) * W + (x0 + ox);
         uint32_t pk[16];
         if (MODE == kModeReluBf16) {
 #pragma unroll
             for (int c = 0; c < 16; ++c)
-                pk[c] = pack2(__float2bfloat16(fmaxf(v[2 * c] + bias[2 * c], 0.f)),
-                              __float2bfloat16(fmaxf(v[2 * c + 1] + bias[2 * c + 1], 0.f)));
+                pk[c] = pack2(__float2bfloat16(fmaxf(v[2 * c] + smB[2 * c], 0.f)),
+                              __float2bfloat16(fmaxf(v[2 * c + 1] + smB[2 * c + 1], 0.f)));
         } else {
-            const uint4* gp = reinterpret_cast<const uint4*>(gate + px * COUT);
+            const uint4* gp = reinterpret_cast<const uint4*>(gate) + px;
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                const uint4 gv = gp[q];
+                const uint4 gv = gp[q * hw];
                 const uint32_t gw[4] = {gv.x, gv.y, gv.z, gv.w};
 #pragma unroll
                 for (int h = 0; h < 4; ++h) {
@@ -448,17 +465,25 @@ conv3x3_tc(const __grid_constant__ CUtensorMap tin, const bf16* __restrict__ wpk
                 }
             }
         }
-        uint4* op = reinterpret_cast<uint4*>(out + px * COUT);
+        uint4* op = reinterpret_cast<uint4*>(out) + px;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) op[q] = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
+        for (int q = 0; q < 4; ++q) op[q * hw] = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
         tc_fence_before();
-        __syncthreads();             // the accumulator is free for the next tile's MMAs
+        __syncthreads();             // accumulator b is free for tile + 2 G's MMAs
     }
-    if (!ok && tid == 0) atomicExch(err, 1);
+    if (!ok && tid == 0) {
+        atomicExch(err, 1);
+        // let this CTA's own copies and MMAs still in flight finish (bounded)
+        // before its tensor memory is released
+        for (int b = 0; b < 2; ++b) {
+            if (pend_h & (1u << b)) mbar_wait_bounded(sh_addr(&bars[b]), (hph >> b) & 1u);
+            if (pend_m & (1u << b)) mbar_wait_bounded(sh_addr(&bars[2 + b]), (mph >> b) & 1u);
+        }
+    }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tmem) : "memory");
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(tmem) : "memory");
 }
 
 // ---------------------------------------------------------------------------
@@ -504,24 +529,27 @@ conv3x3_wgrad_kernel(const bf16* __restrict__ a, const bf16* __restrict__ gr, fl
     for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
         const int im = tile / (tx * ty), rem = tile % (tx * ty);
         const int r0 = (rem / tx) * kTile, c0 = (rem % tx) * kTile;
-        const size_t img = (size_t)im * H * W;
+        const size_t hw = (size_t)H * W;
         __syncthreads();                             // previous tile's operands are consumed
-        // activation tile with halo, channel-major (8 channels per thread and pixel)
-        for (int e = tid; e < C::HALO * C::HALO * (CIN / 8); e += 288) {
-            const int pix = e / (CIN / 8), ch = (e % (CIN / 8)) * 8;
+        // activation tile with halo, channel-major (8 channels of one plane per
+        // thread and pixel)
+        constexpr int NPA = C::HALO * C::HALO;
+        for (int e = tid; e < NPA * (CIN / 8); e += 288) {
+            const int pl = e / NPA, pix = e - pl * NPA, ch = pl * 8;
             const int yy = pix / C::HALO, xx = pix % C::HALO;
             const int gy = r0 + yy - 1, gx = c0 + xx - 1;
             uint4 v = make_uint4(0u, 0u, 0u, 0u);
             if (gy >= 0 && gy < H && gx >= 0 && gx < W)
-                v = *reinterpret_cast<const uint4*>(a + (img + (size_t)gy * W + gx) * CIN + ch);
+                v = *reinterpret_cast<const uint4*>(a + (((size_t)im * (CIN / 8) + pl) * hw + (size_t)gy * W + gx) * 8);
             const bf16* vv = reinterpret_cast<const bf16*>(&v);
 #pragma unroll
             for (int j = 0; j < 8; ++j) sA[(ch + j) * C::PA + pix] = vv[j];
         }
         for (int e = tid; e < kTile * kTile * (COUT / 8); e += 288) {
-            const int pix = e / (COUT / 8), ch = (e % (COUT / 8)) * 8;
+            const int pl = e / (kTile * kTile), pix = e - pl * (kTile * kTile), ch = pl * 8;
             const int gy = r0 + pix / kTile, gx = c0 + pix % kTile;
-            const uint4 v = *reinterpret_cast<const uint4*>(gr + (img + (size_t)gy * W + gx) * COUT + ch);
+            const uint4 v =
+                *reinterpret_cast<const uint4*>(gr + (((size_t)im * (COUT / 8) + pl) * hw + (size_t)gy * W + gx) * 8);
             const bf16* vv = reinterpret_cast<const bf16*>(&v);
 #pragma unroll
             for (int j = 0; j < 8; ++j) sG[(ch + j) * C::PG + pix] = vv[j];
@@ -577,11 +605,11 @@ conv3x3_wgrad_kernel(const bf16* __restrict__ a, const bf16* __restrict__ gr, fl
 }
 
 // ---------------------------------------------------------------------------
-// loss and its gradient in the output: g = 2 c_k (o - t) / npx (16 channels,
-// 4 used); per-block FP64 partial sums of the loss
+// loss and its gradient in the output: g = 2 c_k (o - t) / npx (16 channels
+// in two planes, 4 used; hw = H W); per-block FP64 partial sums of the loss
 // ---------------------------------------------------------------------------
 __global__ void cnn_loss_kernel(const float* __restrict__ o, const float* __restrict__ tg, float4 cw,
-                                bf16* __restrict__ gout, double* __restrict__ loss, long long npx) {
+                                bf16* __restrict__ gout, double* __restrict__ loss, long long npx, long long hw) {
     __shared__ double red[8];
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     double l = 0.0;
@@ -591,10 +619,11 @@ __global__ void cnn_loss_kernel(const float* __restrict__ o, const float* __rest
         const float e0 = ov.x - tv.x, e1 = ov.y - tv.y, e2 = ov.z - tv.z, e3 = ov.w - tv.w;
         l = (double)cw.x * e0 * e0 + (double)cw.y * e1 * e1 + (double)cw.z * e2 * e2 + (double)cw.w * e3 * e3;
         const float s = 2.0f / (float)npx;
-        uint4* dst = reinterpret_cast<uint4*>(gout + i * 16);
+        const long long img = i / hw, px = i - img * hw;
+        uint4* dst = reinterpret_cast<uint4*>(gout + (img * 2 * hw + px) * 8);
         dst[0] = make_uint4(pack2(__float2bfloat16(s * cw.x * e0), __float2bfloat16(s * cw.y * e1)),
                             pack2(__float2bfloat16(s * cw.z * e2), __float2bfloat16(s * cw.w * e3)), 0u, 0u);
-        dst[1] = make_uint4(0u, 0u, 0u, 0u);
+        dst[hw] = make_uint4(0u, 0u, 0u, 0u);
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) l += __shfl_down_sync(0xffffffffu, l, off);
@@ -663,12 +692,11 @@ __global__ void split_start_kernel(const float* __restrict__ o, float s0, float 
 // ---------------------------------------------------------------------------
 // launch helpers
 // ---------------------------------------------------------------------------
-template <int CIN, int COUT, int MODE>
-cudaError_t conv(const bf16* in, const bf16* w, const float* bias, int cout_real, void* out, const bf16* gate,
-                 int count, int H, int W, cudaStream_t s) {
+template <int CIN, int COUT>
+cudaError_t conv_out(const bf16* in, const bf16* w, const float* bias, float* out, int count, int H, int W,
+                     cudaStream_t s) {
     dim3 grid(W / kTile, H / kTile, count);
-    conv3x3_kernel<CIN, COUT, MODE><<<grid, 256, ConvCfg<CIN, COUT>::SMEM, s>>>(in, w, bias, cout_real, out, gate,
-                                                                                 H, W);
+    conv3x3_kernel<CIN, COUT><<<grid, 256, ConvCfg<CIN, COUT>::SMEM, s>>>(in, w, bias, out, H, W);
     ++g_cnn_launches;
     return cudaGetLastError();
 }
@@ -688,21 +716,23 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 }
 
 // 32-output-channel layers on tcgen05 (persistent CTAs over 8 x 16 tiles).
-// The input is viewed by TMA as a 5-D tensor (8 channels, W, H, images,
-// CIN / 8 chunks) with strides (2, 2 CIN, 2 CIN W, 2 CIN W H, 16) bytes, and
-// a box of (8, 10, 18, 1, CIN / 8): one halo tile per copy, laid out in
-// shared memory as [chunk][halo row][halo column][8 channels].
+// The input planes [img][CIN / 8][H][W][8] are viewed by TMA as a 4-D tensor
+// (8 W elements of a plane row, H, CIN / 8 planes, images) with strides
+// (16 W, 16 W H, 16 W H CIN / 8) bytes, and a box of (80, 18, CIN / 8, 1):
+// one halo tile per copy, laid out in shared memory as
+// [plane][halo row][halo column][8 channels].
 template <int CIN, int MODE>
 cudaError_t conv_tc(const bf16* in, const bf16* w, const float* bias, bf16* out, const bf16* gate, int count, int H,
                     int W, int sms, int* err, cudaStream_t s) {
     const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
     if (!enc) return cudaErrorNotSupported;
     CUtensorMap tm;
-    const cuuint64_t dims[5] = {8, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)count, (cuuint64_t)(CIN / 8)};
-    const cuuint64_t strides[4] = {(cuuint64_t)CIN * 2, (cuuint64_t)W * CIN * 2, (cuuint64_t)H * W * CIN * 2, 16};
-    const cuuint32_t box[5] = {8, (cuuint32_t)kTcHW, (cuuint32_t)kTcHH, 1, (cuuint32_t)(CIN / 8)};
-    const cuuint32_t es[5] = {1, 1, 1, 1, 1};
-    if (enc(&tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<bf16*>(in), dims, strides, box, es,
+    const cuuint64_t plane = (cuuint64_t)W * H * 16;
+    const cuuint64_t dims[4] = {(cuuint64_t)W * 8, (cuuint64_t)H, (cuuint64_t)(CIN / 8), (cuuint64_t)count};
+    const cuuint64_t strides[3] = {(cuuint64_t)W * 16, plane, plane * (CIN / 8)};
+    const cuuint32_t box[4] = {(cuuint32_t)kTcHW * 8, (cuuint32_t)kTcHH, (cuuint32_t)(CIN / 8), 1};
+    const cuuint32_t es[4] = {1, 1, 1, 1};
+    if (enc(&tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16*>(in), dims, strides, box, es,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return cudaErrorInvalidValue;
@@ -789,14 +819,14 @@ int pack_all(admm_cnn_s* n, cudaStream_t s) {
 int forward(admm_cnn_s* n, int count, int H, int W, const float* ybar, const uint8_t* mask, bool keep,
             cudaStream_t s) {
     const long long npx = (long long)count * H * W;
-    cnn_input_kernel<<<(unsigned)((npx + 255) / 256), 256, 0, s>>>(ybar, mask, n->a0, npx);
+    cnn_input_kernel<<<(unsigned)((npx + 255) / 256), 256, 0, s>>>(ybar, mask, n->a0, npx, (long long)H * W);
     ++g_cnn_launches;
     CKC(cudaGetLastError());
     const bf16* cur = n->a0;
     for (int l = 0; l < kLayers; ++l) {
         const float* b = n->params + param_offset(l) + (long long)layer_cout(l) * layer_cin(l) * 9;
         if (l == kLayers - 1) {
-            CKC((conv<32, 8, kModeOutF32>(cur, n->wf[l], b, kOut, n->out, nullptr, count, H, W, s)));
+            CKC((conv_out<32, 8>(cur, n->wf[l], b, n->out, count, H, W, s)));
         } else {
             bf16* dst = keep ? n->act[l] : n->act[l & 1];
             if (l == 0)
@@ -815,7 +845,8 @@ int backward(admm_cnn_s* n, int count, int H, int W, const float* target, const 
     CKC(cudaMemsetAsync(n->loss, 0, sizeof(double), s));
     CKC(cudaMemsetAsync(n->grads, 0, param_count() * sizeof(float), s));
     const float4 cw = make_float4(chan_w[0], chan_w[1], chan_w[2], chan_w[3]);
-    cnn_loss_kernel<<<(unsigned)((npx + 255) / 256), 256, 0, s>>>(n->out, target, cw, n->gout, n->loss, npx);
+    cnn_loss_kernel<<<(unsigned)((npx + 255) / 256), 256, 0, s>>>(n->out, target, cw, n->gout, n->loss, npx,
+                                                                   (long long)H * W);
     ++g_cnn_launches;
     CKC(cudaGetLastError());
     const bf16* g = n->gout;                        // gradient in the output of layer l
