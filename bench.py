@@ -603,10 +603,10 @@ def warm_secondary(ad, torch, stream, count=32):
     hbm = CNN_BYTES_PER_PX * n * 512 * 512 / sec / 1e9
     ev["cnn_forward"] = {"images": n, "size": 512, "ms": sec * 1e3, "tflops": tflops,
                          "hbm_gbs": hbm, "hbm_frac": hbm / peak, "bytes_per_px": CNN_BYTES_PER_PX,
-                         "note": "hidden 32-channel layers: tcgen05.mma (two TMEM accumulators) fed by "
+                         "note": "all 8 convolutions on tcgen05.mma (two TMEM accumulators) fed by "
                                  "double-buffered TMA halo boxes of 160-byte rows (activations in planes of "
-                                 "8 channels); last layer mma.sync; 9 launches per forward; each layer reads "
-                                 "and writes its activations in HBM"}
+                                 "8 channels); 9 launches per forward; each layer reads and writes its "
+                                 "activations in HBM"}
     ev["trained"] = {k: meta[k] for k in ("count", "epochs", "lr", "train_s", "steps") if k in meta}
     return ev
 

@@ -1,6 +1,6 @@
 // cnn.cu -- the learned warm start: a stack of 3 x 3 convolutions on BF16
-// tensor cores (mma.sync m16n8k16, FP32 accumulate), its backward pass and
-// Adam. Not part of the paper; Theorem 1 (convergence from any u0, d0) is
+// tensor cores (tcgen05.mma, FP32 accumulate in tensor memory), its backward
+// pass (weight gradients on mma.sync m16n8k16) and Adam. Not part of the paper; Theorem 1 (convergence from any u0, d0) is
 // what lets a predicted start feed Algorithm 2.
 //
 // Layout. Activations and their gradients are BF16 in planes of eight
@@ -12,14 +12,10 @@
 // BF16 [tap][cout][cin] (cin contiguous), the order in which the B operand of
 // the MMA consumes them.
 //
-// The 32-channel layers (forward with bias and ReLU, and the input gradients)
-// run on tcgen05 (conv3x3_tc below). The last layer (4 outputs, padded to 8)
-// uses mma.sync: a CTA computes a 16 x 16 pixel tile; its input tile (18 x 18
-// pixels with halo, zero outside the image) and all nine taps of the weights
-// sit in shared memory with the pixel and weight-row strides padded by 8
-// elements, which makes every fragment load conflict-free. Warp w owns tile
-// rows 2w and 2w + 1 (one m16 block each: 16 pixels of a row); the K loop
-// runs over the 9 taps and the input channels in steps of 16.
+// Every convolution of the forward pass and every input gradient runs on
+// tcgen05 (conv3x3_tc below): the 32-channel layers with bias and ReLU, the
+// input gradients gated by the ReLU of the layer below, and the last layer
+// (4 outputs padded to 16) with bias into FP32.
 //
 // Weight-gradient kernel: per tap, dW_tap = G^T A_tap, a contraction over
 // pixels. A CTA of 9 warps (one per tap) loops over tiles; the gradient and
@@ -60,7 +56,7 @@ __host__ __device__ constexpr int layer_cin(int l) { return l == 0 ? kIn : kWidt
 __host__ __device__ constexpr int layer_cout(int l) { return l == kLayers - 1 ? kOut : kWidth; }
 constexpr int pad16(int c) { return c <= 16 ? 16 : 32; }
 constexpr int layer_cinp(int l) { return pad16(layer_cin(l)); }
-constexpr int layer_coutp(int l) { return l == kLayers - 1 ? 8 : kWidth; }
+constexpr int layer_coutp(int l) { return l == kLayers - 1 ? 16 : kWidth; }
 
 long long param_offset(int l) {
     long long o = 0;
@@ -121,127 +117,22 @@ __global__ void cnn_input_kernel(const float* __restrict__ ybar, const uint8_t* 
     dst[hw] = make_uint4(0u, 0u, 0u, 0u);
 }
 
-// ---------------------------------------------------------------------------
-// the last layer: 3 x 3 convolution on a 16 x 16 output tile (see the file
-// comment), FP32 output with bias
-// ---------------------------------------------------------------------------
-enum { kModeReluBf16 = 0, kModeGateBf16 = 2 };   // epilogues of conv3x3_tc
-
-template <int CIN, int COUT>
-struct ConvCfg {
-    static constexpr int PS = CIN + 8;               // pixel stride in shared memory (elements)
-    static constexpr int WS = CIN + 8;               // weight row stride
-    static constexpr int HALO = kTile + 2;
-    static constexpr int IN_ELEMS = HALO * HALO * PS;
-    static constexpr int W_ELEMS = 9 * COUT * WS;
-    static constexpr size_t SMEM = (size_t)(IN_ELEMS + W_ELEMS) * sizeof(bf16);
-    static_assert(CIN % 16 == 0 && COUT % 8 == 0, "channel padding");
-    static_assert(SMEM <= 48 * 1024, "fits the default shared-memory window");
-};
-
-// in: [img][CIN / 8][H][W][8]; wpk: [9][COUT][CIN]; bias: [4];
-// out: float [img][H][W][4] (output channels 0..3 of the COUT computed).
-template <int CIN, int COUT>
-__global__ void __launch_bounds__(256)
-conv3x3_kernel(const bf16* __restrict__ in, const bf16* __restrict__ wpk, const float* __restrict__ bias,
-               float* __restrict__ out, int H, int W) {
-    using C = ConvCfg<CIN, COUT>;
-    extern __shared__ __align__(16) bf16 sm[];
-    bf16* sIn = sm;
-    bf16* sW = sm + C::IN_ELEMS;
-    const int tid = threadIdx.x;
-    const int c0 = blockIdx.x * kTile, r0 = blockIdx.y * kTile;
-    const size_t hw = (size_t)H * W, img = (size_t)blockIdx.z * hw;
-
-    // input tile with halo: CIN / 8 planes, 16 B per pixel and plane
-    constexpr int CH = CIN / 8, NP = C::HALO * C::HALO;
-    for (int e = tid; e < NP * CH; e += 256) {
-        const int ch = e / NP, pix = e - ch * NP;
-        const int ty = pix / C::HALO, tx = pix % C::HALO;
-        const int gr = r0 + ty - 1, gc = c0 + tx - 1;
-        bf16* dst = sIn + pix * C::PS + ch * 8;
-        if (gr >= 0 && gr < H && gc >= 0 && gc < W)
-            cp_async16(dst, in + (((size_t)blockIdx.z * CH + ch) * hw + (size_t)gr * W + gc) * 8);
-        else
-            *reinterpret_cast<uint4*>(dst) = make_uint4(0u, 0u, 0u, 0u);
-    }
-    for (int e = tid; e < 9 * COUT * CH; e += 256) {
-        const int row = e / CH, ch = e % CH;
-        cp_async16(sW + row * C::WS + ch * 8, wpk + (size_t)row * CIN + ch * 8);
-    }
-    cp_async_wait_all();
-    __syncthreads();
-
-    const int lane = tid & 31, warp = tid >> 5;
-    const int g = lane >> 2, t = lane & 3;
-    constexpr int NT = COUT / 8;
-    float acc[2][NT][4];
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-        for (int nt = 0; nt < NT; ++nt)
-#pragma unroll
-            for (int j = 0; j < 4; ++j) acc[mt][nt][j] = 0.f;
-
-#pragma unroll
-    for (int tap = 0; tap < 9; ++tap) {
-        const int p = tap / 3, q = tap % 3;           // input offset (p - 1, q - 1)
-#pragma unroll
-        for (int kc = 0; kc < CIN / 16; ++kc) {
-            uint32_t b[NT][2];
-#pragma unroll
-            for (int nt = 0; nt < NT; ++nt) {
-                const bf16* wr = sW + (tap * COUT + nt * 8 + g) * C::WS + kc * 16 + 2 * t;
-                b[nt][0] = ld32(wr);
-                b[nt][1] = ld32(wr + 8);
-            }
-#pragma unroll
-            for (int mt = 0; mt < 2; ++mt) {
-                const int rr = 2 * warp + mt;         // tile row of this m block
-                // A[m][k]: m = output column, k = input channel; halo offset +1 cancels -1
-                const bf16* ar = sIn + ((rr + p) * C::HALO + q) * C::PS + kc * 16 + 2 * t;
-                const uint32_t a0 = ld32(ar + g * C::PS);
-                const uint32_t a1 = ld32(ar + (g + 8) * C::PS);
-                const uint32_t a2 = ld32(ar + g * C::PS + 8);
-                const uint32_t a3 = ld32(ar + (g + 8) * C::PS + 8);
-#pragma unroll
-                for (int nt = 0; nt < NT; ++nt) mma_bf16(acc[mt][nt], a0, a1, a2, a3, b[nt][0], b[nt][1]);
-            }
-        }
-    }
-
-    // epilogue: c0, c1 -> (column g, channels 2t, 2t+1); c2, c3 -> column g + 8
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt) {
-        const int gr = r0 + 2 * warp + mt;
-#pragma unroll
-        for (int half = 0; half < 2; ++half) {
-            const int gc = c0 + g + 8 * half;
-            const size_t px = img + (size_t)gr * W + gc;
-#pragma unroll
-            for (int nt = 0; nt < NT; ++nt) {
-                const int ch = nt * 8 + 2 * t;
-                if (ch < kOut)
-                    *reinterpret_cast<float2*>(out + px * kOut + ch) =
-                        make_float2(acc[mt][nt][2 * half] + bias[ch], acc[mt][nt][2 * half + 1] + bias[ch + 1]);
-            }
-        }
-    }
-}
+enum { kModeReluBf16 = 0, kModeOutF32 = 1, kModeGateBf16 = 2 };   // epilogues of conv3x3_tc
 
 // ---------------------------------------------------------------------------
-// 3 x 3 convolution with 32 output channels on the fifth-generation tensor
-// cores (tcgen05.mma, accumulator in tensor memory).
+// 3 x 3 convolution on the fifth-generation tensor cores (tcgen05.mma,
+// accumulator in tensor memory).
 //
 // A CTA of four warps walks output tiles of 8 x 16 pixels (M = 128, one
 // accumulator row per pixel: tile row oy, column ox at M row 8 oy + ox), N =
-// 32 output channels, K = 9 taps x CIN input channels. Operands sit in shared
+// COUT output channels (32, or 16 for the last layer's 4 outputs), K = 9 taps
+// x CIN input channels. Operands sit in shared
 // memory in the no-swizzle K-major layout of 8-row x 16-byte core matrices:
 //   A: the 10 x 18 halo tile as [CIN/8][180 halo pixels][8 channels]; the A
 //      matrix of tap (dy, dx) starts at halo pixel 10 dy + dx, its 8-row
 //      groups (one tile row each) are 10 pixels = 160 B apart and its K
 //      chunks 180 x 16 B apart, so no im2col copy is needed;
-//   B: the weights as [tap][CIN/8][32 output channels][8].
+//   B: the weights as [tap][CIN/8][COUT output channels][8].
 // The halo tile arrives by one TMA copy (cp.async.bulk.tensor, a 4-D view of
 // the eight-channel planes whose innermost dimension merges a plane row's
 // columns and channels, so each box row is 10 pixels x 16 B = 160 contiguous
@@ -250,7 +141,8 @@ conv3x3_kernel(const bf16* __restrict__ in, const bf16* __restrict__ wpk, const 
 // the 9 x CIN/16 MMAs of a tile (K = 16 each) and commits them to an
 // mbarrier; the four warps wait (bounded), read their 32 lanes of the
 // accumulator (tcgen05.ld) and apply bias + ReLU (forward) or the ReLU gate of
-// the layer below (input gradient), storing four BF16 planes.
+// the layer below (input gradient), storing four BF16 planes, or bias alone
+// into the network's FP32 output (last layer).
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t sh_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -262,8 +154,10 @@ __device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint
 }
 
 // instruction descriptor, kind::f16: F32 accumulator, BF16 A and B, both
-// K-major, N = 32, M = 128
-constexpr uint32_t kIdescM128N32 = (1u << 4) | (1u << 7) | (1u << 10) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
+// K-major, M = 128, N = n (a multiple of 16)
+__host__ __device__ constexpr uint32_t idesc_m128(uint32_t n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((n >> 3) << 17) | ((128u >> 4) << 24);
+}
 
 __device__ __forceinline__ void umma_f16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accum) {
     asm volatile(
@@ -318,13 +212,28 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// 16 consecutive FP32 columns of this thread's accumulator lane
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n\t"
+        "tcgen05.wait::ld.sync.aligned;\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 constexpr int kTcTW = 8, kTcTH = 16;                 // output tile (M = 128)
 constexpr int kTcHW = kTcTW + 2, kTcHH = kTcTH + 2;  // halo tile
 constexpr int kTcNP = kTcHW * kTcHH;                 // 180 halo pixels
 
 // tin: TMA view of the input [img][CIN / 8][H][W][8] (see conv_tc); wpk:
-// [9][32][CIN]; out: bf16 [img][4][H][W][8]; MODE kModeReluBf16 (bias, ReLU)
-// or kModeGateBf16 (gate [img][4][H][W][8]); err: set to 1 if a wait ran out (the CTA then stops,
+// [9][COUT][CIN]; MODE kModeReluBf16 (bias, ReLU; out bf16 [img][4][H][W][8]),
+// kModeGateBf16 (gate and out bf16 [img][4][H][W][8]) or kModeOutF32 (bias of
+// the 4 outputs; out float [img][H][W][4]); err: set to 1 if a wait ran out (the CTA then stops,
 // after a bounded wait for its own copies and MMAs still in flight).
 //
 // Pipeline of the CTA's i-th tile (halo buffer and accumulator i & 1): thread
@@ -336,12 +245,13 @@ constexpr int kTcNP = kTcHW * kTcHH;                 // 180 halo pixels
 template <int CIN, int MODE>
 __global__ void __launch_bounds__(128)
 conv3x3_tc(const __grid_constant__ CUtensorMap tin, const bf16* __restrict__ wpk, const float* __restrict__ bias,
-           bf16* __restrict__ out, const bf16* __restrict__ gate, int H, int W, int count, int* __restrict__ err) {
-    constexpr int COUT = 32, CH = CIN / 8, ABYTES = CH * kTcNP * 16;
+           void* __restrict__ out, const bf16* __restrict__ gate, int H, int W, int count, int* __restrict__ err) {
+    constexpr int COUT = MODE == kModeOutF32 ? 16 : 32, CH = CIN / 8, ABYTES = CH * kTcNP * 16;
+    constexpr uint32_t kTmemCols = 2 * COUT;   // two accumulators
     static_assert(CIN == 16 || CIN == 32, "input channels");
     __shared__ __align__(128) unsigned char smA[2][ABYTES];
     __shared__ __align__(128) unsigned char smW[9 * CH * COUT * 16];
-    __shared__ float smB[COUT];
+    __shared__ float smB[32];
     // 0, 1: halo of buffer 0 / 1 landed; 2, 3: MMAs into accumulator 0 / 1 done
     __shared__ __align__(8) unsigned long long bars[4];
     __shared__ uint32_t tmem_base;
@@ -351,9 +261,10 @@ conv3x3_tc(const __grid_constant__ CUtensorMap tin, const bf16* __restrict__ wpk
         const int tap = tc / COUT, co = tc - tap * COUT;
         cp_async16(smW + ((tap * CH + k) * COUT + co) * 16, wpk + (size_t)tc * CIN + k * 8);
     }
-    if (MODE == kModeReluBf16 && tid < COUT) smB[tid] = bias[tid];
+    if ((MODE == kModeReluBf16 && tid < COUT) || (MODE == kModeOutF32 && tid < kOut)) smB[tid] = bias[tid];
     if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;" ::"r"(sh_addr(&tmem_base))
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(sh_addr(&tmem_base)),
+                     "n"(kTmemCols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -394,13 +305,13 @@ conv3x3_tc(const __grid_constant__ CUtensorMap tin, const bf16* __restrict__ wpk
     const uint32_t tmem = tmem_base;
     const uint32_t wBase = sh_addr(smW);
     // thread 0: wait for the halo in buffer b, then issue the tile's MMAs into
-    // accumulator b (columns 32 b) and commit them to bars[2 + b]
+    // accumulator b (columns COUT b) and commit them to bars[2 + b]
     auto mma_tile = [&](int b) -> bool {
         if (!mbar_wait_bounded(sh_addr(&bars[b]), (hph >> b) & 1u)) return false;
         hph ^= 1u << b;
         pend_h &= ~(1u << b);
         tc_fence_after();
-        const uint32_t aBase = sh_addr(smA[b]), d = tmem + 32u * b;
+        const uint32_t aBase = sh_addr(smA[b]), d = tmem + (uint32_t)COUT * b;
 #pragma unroll
         for (int tap = 0; tap < 9; ++tap) {
             const int dy = tap / 3, dx = tap - 3 * (tap / 3);
@@ -408,7 +319,7 @@ conv3x3_tc(const __grid_constant__ CUtensorMap tin, const bf16* __restrict__ wpk
             for (int j = 0; j < CH / 2; ++j) {
                 const uint64_t a = umma_desc(aBase + (2 * j * kTcNP + dy * kTcHW + dx) * 16, kTcNP * 16, kTcHW * 16);
                 const uint64_t bd = umma_desc(wBase + (tap * CH + 2 * j) * COUT * 16, COUT * 16, 8 * 16);
-                umma_f16(d, a, bd, kIdescM128N32, (tap | j) != 0 ? 1u : 0u);
+                umma_f16(d, a, bd, idesc_m128(COUT), (tap | j) != 0 ? 1u : 0u);
             }
         }
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -437,37 +348,47 @@ conv3x3_tc(const __grid_constant__ CUtensorMap tin, const bf16* __restrict__ wpk
         tc_fence_after();
         const int img = tile / per_img, rem = tile - img * per_img;
         const int y0 = (rem / tiles_x) * kTcTH, x0 = (rem % tiles_x) * kTcTW;
-        float v[32];
-        tmem_ld32(tmem + 32u * b + ((uint32_t)(32 * warp) << 16), v);
         const int oy = 4 * warp + (lane >> 3), ox = lane & 7;
         const size_t hw = (size_t)H * W;
-        // pixel's slot in plane 0 of its image; plane q is q hw slots further
-        const size_t px = (size_t)img * 4 * hw + (size_t)(y0 + oy) * W + (x0 + ox);
-        uint32_t pk[16];
-        if (MODE == kModeReluBf16) {
-#pragma unroll
-            for (int c = 0; c < 16; ++c)
-                pk[c] = pack2(__float2bfloat16(fmaxf(v[2 * c] + smB[2 * c], 0.f)),
-                              __float2bfloat16(fmaxf(v[2 * c + 1] + smB[2 * c + 1], 0.f)));
+        const uint32_t tacc = tmem + (uint32_t)COUT * b + ((uint32_t)(32 * warp) << 16);
+        if constexpr (MODE == kModeOutF32) {
+            float v[16];
+            tmem_ld16(tacc, v);
+            const size_t px = (size_t)img * hw + (size_t)(y0 + oy) * W + (x0 + ox);
+            reinterpret_cast<float4*>(out)[px] =
+                make_float4(v[0] + smB[0], v[1] + smB[1], v[2] + smB[2], v[3] + smB[3]);
         } else {
-            const uint4* gp = reinterpret_cast<const uint4*>(gate) + px;
+            float v[32];
+            tmem_ld32(tacc, v);
+            // pixel's slot in plane 0 of its image; plane q is q hw slots further
+            const size_t px = (size_t)img * 4 * hw + (size_t)(y0 + oy) * W + (x0 + ox);
+            uint32_t pk[16];
+            if (MODE == kModeReluBf16) {
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const uint4 gv = gp[q * hw];
-                const uint32_t gw[4] = {gv.x, gv.y, gv.z, gv.w};
+                for (int c = 0; c < 16; ++c)
+                    pk[c] = pack2(__float2bfloat16(fmaxf(v[2 * c] + smB[2 * c], 0.f)),
+                                  __float2bfloat16(fmaxf(v[2 * c + 1] + smB[2 * c + 1], 0.f)));
+            } else {
+                const uint4* gp = reinterpret_cast<const uint4*>(gate) + px;
 #pragma unroll
-                for (int h = 0; h < 4; ++h) {
-                    const int c = 8 * q + 2 * h;
-                    const float g0 = __bfloat162float(__ushort_as_bfloat16((unsigned short)(gw[h] & 0xFFFFu)));
-                    const float g1 = __bfloat162float(__ushort_as_bfloat16((unsigned short)(gw[h] >> 16)));
-                    pk[4 * q + h] = pack2(__float2bfloat16(g0 > 0.f ? v[c] : 0.f),
-                                          __float2bfloat16(g1 > 0.f ? v[c + 1] : 0.f));
+                for (int q = 0; q < 4; ++q) {
+                    const uint4 gv = gp[q * hw];
+                    const uint32_t gw[4] = {gv.x, gv.y, gv.z, gv.w};
+#pragma unroll
+                    for (int h = 0; h < 4; ++h) {
+                        const int c = 8 * q + 2 * h;
+                        const float g0 = __bfloat162float(__ushort_as_bfloat16((unsigned short)(gw[h] & 0xFFFFu)));
+                        const float g1 = __bfloat162float(__ushort_as_bfloat16((unsigned short)(gw[h] >> 16)));
+                        pk[4 * q + h] = pack2(__float2bfloat16(g0 > 0.f ? v[c] : 0.f),
+                                              __float2bfloat16(g1 > 0.f ? v[c + 1] : 0.f));
+                    }
                 }
             }
-        }
-        uint4* op = reinterpret_cast<uint4*>(out) + px;
+            uint4* op = reinterpret_cast<uint4*>(out) + px;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) op[q * hw] = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
+            for (int q = 0; q < 4; ++q)
+                op[q * hw] = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
+        }
         tc_fence_before();
         __syncthreads();             // accumulator b is free for tile + 2 G's MMAs
     }
@@ -483,7 +404,8 @@ conv3x3_tc(const __grid_constant__ CUtensorMap tin, const bf16* __restrict__ wpk
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(tmem) : "memory");
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(kTmemCols) : "memory");
 }
 
 // ---------------------------------------------------------------------------
@@ -692,15 +614,6 @@ __global__ void split_start_kernel(const float* __restrict__ o, float s0, float 
 // ---------------------------------------------------------------------------
 // launch helpers
 // ---------------------------------------------------------------------------
-template <int CIN, int COUT>
-cudaError_t conv_out(const bf16* in, const bf16* w, const float* bias, float* out, int count, int H, int W,
-                     cudaStream_t s) {
-    dim3 grid(W / kTile, H / kTile, count);
-    conv3x3_kernel<CIN, COUT><<<grid, 256, ConvCfg<CIN, COUT>::SMEM, s>>>(in, w, bias, out, H, W);
-    ++g_cnn_launches;
-    return cudaGetLastError();
-}
-
 // the driver's tensor-map encoder (through the runtime, no link to the driver library)
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -715,15 +628,35 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
     return fn;
 }
 
-// 32-output-channel layers on tcgen05 (persistent CTAs over 8 x 16 tiles).
-// The input planes [img][CIN / 8][H][W][8] are viewed by TMA as a 4-D tensor
+// One layer on tcgen05 (persistent CTAs over 8 x 16 tiles, as many per SM as
+// registers, shared memory and tensor memory allow). The input planes [img][CIN / 8][H][W][8] are viewed by TMA as a 4-D tensor
 // (8 W elements of a plane row, H, CIN / 8 planes, images) with strides
 // (16 W, 16 W H, 16 W H CIN / 8) bytes, and a box of (80, 18, CIN / 8, 1):
 // one halo tile per copy, laid out in shared memory as
 // [plane][halo row][halo column][8 channels].
 template <int CIN, int MODE>
-cudaError_t conv_tc(const bf16* in, const bf16* w, const float* bias, bf16* out, const bf16* gate, int count, int H,
+cudaError_t conv_tc(const bf16* in, const bf16* w, const float* bias, void* out, const bf16* gate, int count, int H,
                     int W, int sms, int* err, cudaStream_t s) {
+    static int per_sm = 0;
+    if (per_sm == 0) {
+        // CTAs one SM holds, from the kernel's registers and static shared
+        // memory (the whole unified L1 / shared array given to shared memory)
+        // and the 2 x cout tensor-memory columns each CTA allocates of 512
+        cudaFuncAttributes fa;
+        int dev = 0, smem_sm = 0, smem_rsv = 0, regs_sm = 0;
+        if (cudaFuncSetAttribute(conv3x3_tc<CIN, MODE>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess ||
+            cudaFuncGetAttributes(&fa, conv3x3_tc<CIN, MODE>) != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&smem_rsv, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev) != cudaSuccess)
+            return cudaErrorInvalidConfiguration;
+        const int regs_cta = ((fa.numRegs + 7) / 8) * 8 * 128;
+        const int by_regs = regs_sm / std::max(regs_cta, 1);
+        const int by_smem = smem_sm / (int)(fa.sharedSizeBytes + smem_rsv);
+        const int cout = MODE == kModeOutF32 ? 16 : 32;
+        per_sm = std::max(1, std::min({by_regs, by_smem, 16, 512 / (2 * cout)}));
+    }
     const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
     if (!enc) return cudaErrorNotSupported;
     CUtensorMap tm;
@@ -737,7 +670,7 @@ cudaError_t conv_tc(const bf16* in, const bf16* w, const float* bias, bf16* out,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return cudaErrorInvalidValue;
     const int ntiles = (W / kTcTW) * (H / kTcTH) * count;
-    const int grid = std::min(ntiles, 5 * sms);
+    const int grid = std::min(ntiles, per_sm * sms);
     conv3x3_tc<CIN, MODE><<<grid, 128, 0, s>>>(tm, w, bias, out, gate, H, W, count, err);
     ++g_cnn_launches;
     return cudaGetLastError();
@@ -826,7 +759,7 @@ int forward(admm_cnn_s* n, int count, int H, int W, const float* ybar, const uin
     for (int l = 0; l < kLayers; ++l) {
         const float* b = n->params + param_offset(l) + (long long)layer_cout(l) * layer_cin(l) * 9;
         if (l == kLayers - 1) {
-            CKC((conv_out<32, 8>(cur, n->wf[l], b, n->out, count, H, W, s)));
+            CKC((conv_tc<32, kModeOutF32>(cur, n->wf[l], b, n->out, nullptr, count, H, W, n->sms, n->tc_err, s)));
         } else {
             bf16* dst = keep ? n->act[l] : n->act[l & 1];
             if (l == 0)
