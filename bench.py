@@ -579,7 +579,7 @@ def warm_secondary(ad, torch, stream, count=32):
     cores (16 images of 512^2, FLOPs of the eight convolutions)."""
     import paper_1210_2687_gb300.warmstart as WS
     params, scales, meta = WS.load()
-    ev = WS.evaluate(params, scales, count=count, seed=1)
+    ev = WS.evaluate(params, scales, count=count, seed=1, api_weights=WS.WEIGHTS_BIN)
     n = 16
     net = ad.Cnn(n * 512 * 512)
     net.set_params(params)

@@ -210,8 +210,11 @@ ADMM_API int admm_deconv_solve(admm_plan_t plan, const float* y, const uint8_t* 
  *                  starts from the learned network loaded by
  *                  admm_warmstart_load (the network predicts x0 and the duals
  *                  d0 from [M^T y, mask] on the device, then the start of
- *                  admm_deconv_warm_start is used). Other regularisers start
- *                  cold. ADMM_EINVAL if no network is loaded.
+ *                  admm_deconv_warm_start is used). One pass of the network
+ *                  serves up to 16 problems of one size (no more than
+ *                  16 x 512 x 512 pixels); each problem's start has the bits
+ *                  of a pass over it alone. Other regularisers start cold.
+ *                  ADMM_EINVAL if no network is loaded.
  * Errors: as admm_deconv_solve; the first failing problem's code is returned.
  */
 ADMM_API int admm_deconv_solve_batch(const admm_plan_t* plans, int count, const float* const* y,

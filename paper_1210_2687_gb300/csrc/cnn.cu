@@ -611,6 +611,41 @@ __global__ void split_start_kernel(const float* __restrict__ o, float s0, float 
     reinterpret_cast<float2*>(d + n)[px] = make_float2(s2 * v.z, s2 * v.w);
 }
 
+// the same two steps for a group of separately stored problems (the learned
+// start of a batch solve): per-image device pointers, passed by value
+constexpr int kWsBatch = 16;
+struct ImgPtrs {
+    const float* y[kWsBatch];
+    const uint8_t* m[kWsBatch];
+    float* x0[kWsBatch];
+    float* d0[kWsBatch];
+};
+
+// grid (ceil(hw / 256), images)
+__global__ void cnn_input_ptrs_kernel(ImgPtrs P, bf16* __restrict__ a0, long long hw) {
+    const long long px = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (px >= hw) return;
+    const int img = blockIdx.y;
+    const bool obs = P.m[img][px] != 0;
+    const float y = obs ? P.y[img][px] : 0.f;
+    uint4* dst = reinterpret_cast<uint4*>(a0 + ((long long)img * 2 * hw + px) * 8);
+    dst[0] = make_uint4(pack2(__float2bfloat16(y), __float2bfloat16(obs ? 1.f : 0.f)), 0u, 0u, 0u);
+    dst[hw] = make_uint4(0u, 0u, 0u, 0u);
+}
+
+// grid (ceil(hw / 256), images)
+__global__ void split_start_ptrs_kernel(const float* __restrict__ o, float s0, float s1, float s2, ImgPtrs P,
+                                        long long hw) {
+    const long long px = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (px >= hw) return;
+    const int img = blockIdx.y;
+    const float4 v = reinterpret_cast<const float4*>(o)[(long long)img * hw + px];
+    P.x0[img][px] = s0 * v.x;
+    float* d = P.d0[img];
+    d[px] = s1 * v.y;
+    reinterpret_cast<float2*>(d + hw)[px] = make_float2(s2 * v.z, s2 * v.w);
+}
+
 // ---------------------------------------------------------------------------
 // launch helpers
 // ---------------------------------------------------------------------------
@@ -747,14 +782,9 @@ int pack_all(admm_cnn_s* n, cudaStream_t s) {
     return ADMM_OK;
 }
 
-// forward pass; with `keep` every activation is stored for the backward pass,
-// otherwise two buffers alternate
-int forward(admm_cnn_s* n, int count, int H, int W, const float* ybar, const uint8_t* mask, bool keep,
-            cudaStream_t s) {
-    const long long npx = (long long)count * H * W;
-    cnn_input_kernel<<<(unsigned)((npx + 255) / 256), 256, 0, s>>>(ybar, mask, n->a0, npx, (long long)H * W);
-    ++g_cnn_launches;
-    CKC(cudaGetLastError());
+// the eight layers on the prepared input n->a0; with `keep` every activation
+// is stored for the backward pass, otherwise two buffers alternate
+int run_layers(admm_cnn_s* n, int count, int H, int W, bool keep, cudaStream_t s) {
     const bf16* cur = n->a0;
     for (int l = 0; l < kLayers; ++l) {
         const float* b = n->params + param_offset(l) + (long long)layer_cout(l) * layer_cin(l) * 9;
@@ -770,6 +800,16 @@ int forward(admm_cnn_s* n, int count, int H, int W, const float* ybar, const uin
         }
     }
     return ADMM_OK;
+}
+
+// forward pass from [M^T y, mask] stored contiguously for the count images
+int forward(admm_cnn_s* n, int count, int H, int W, const float* ybar, const uint8_t* mask, bool keep,
+            cudaStream_t s) {
+    const long long npx = (long long)count * H * W;
+    cnn_input_kernel<<<(unsigned)((npx + 255) / 256), 256, 0, s>>>(ybar, mask, n->a0, npx, (long long)H * W);
+    ++g_cnn_launches;
+    CKC(cudaGetLastError());
+    return run_layers(n, count, H, W, keep, s);
 }
 
 // loss, gradients into n->grads (zeroed first)
@@ -1028,14 +1068,27 @@ bool ws_loaded() {
     return g_ws.loaded;
 }
 
-// predicted start of one H x W TV problem: x0 (H W floats) and d0 (3 H W
-// floats in the layout of admm_deconv_get_state), device pointers, on `s`
-int ws_predict_start(int H, int W, const float* ybar, const uint8_t* mask, float* x0, float* d0, cudaStream_t s) {
+// images of H x W that one ws_predict_starts call takes: up to 16, and no
+// more than 16 x 512 x 512 pixels (the network's buffers hold about 180 B per
+// pixel)
+int ws_batch_limit(int H, int W) {
+    const long long px = std::max(1LL, (long long)H * W);
+    return (int)std::max(1LL, std::min((long long)kWsBatch, 16LL * 512 * 512 / px));
+}
+
+// predicted starts of `count` H x W TV problems (count <= ws_batch_limit):
+// for image i, [M^T y, mask] from ybar[i], mask[i], and x0[i] (H W floats)
+// and d0[i] (3 H W floats in the layout of admm_deconv_get_state) written,
+// device pointers, on `s`. One pass of the network over the group; each
+// image's result has the bits of a pass over that image alone.
+int ws_predict_starts(int count, int H, int W, const float* const* ybar, const uint8_t* const* mask,
+                      float* const* x0, float* const* d0, cudaStream_t s) {
+    if (count < 1 || count > ws_batch_limit(H, W)) return ADMM_EINVAL;
     std::lock_guard<std::mutex> lk(g_ws_mutex);
     if (!g_ws.loaded) return ADMM_EINVAL;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return ADMM_ECUDA;
-    const long long px = (long long)H * W;
+    const long long hw = (long long)H * W, px = hw * count;
     if (!g_ws.net || g_ws.device != dev || g_ws.cap < px) {
         if (g_ws.net) admm_cnn_destroy(g_ws.net);
         g_ws.net = nullptr;
@@ -1052,6 +1105,26 @@ int ws_predict_start(int H, int W, const float* ybar, const uint8_t* mask, float
         g_ws.device = dev;
         g_ws.cap = cap;
     }
-    return admm_cnn_predict_start(g_ws.net, 1, H, W, ybar, mask, g_ws.scales, x0, d0, s);
+    admm_cnn_s* net = g_ws.net;
+    std::lock_guard<std::mutex> lk2(g_cnn_mutex);
+    int rc = check_shape(net, count, H, W);
+    if (rc != ADMM_OK) return rc;
+    ImgPtrs P{};
+    for (int i = 0; i < count; ++i) {
+        if (!ybar[i] || !mask[i] || !x0[i] || !d0[i]) return ADMM_EINVAL;
+        P.y[i] = ybar[i];
+        P.m[i] = mask[i];
+        P.x0[i] = x0[i];
+        P.d0[i] = d0[i];
+    }
+    const dim3 grid((unsigned)((hw + 255) / 256), (unsigned)count);
+    cnn_input_ptrs_kernel<<<grid, 256, 0, s>>>(P, net->a0, hw);
+    ++g_cnn_launches;
+    CKC(cudaGetLastError());
+    if ((rc = run_layers(net, count, H, W, false, s)) != ADMM_OK) return rc;
+    split_start_ptrs_kernel<<<grid, 256, 0, s>>>(net->out, g_ws.scales[0], g_ws.scales[1], g_ws.scales[2], P, hw);
+    ++g_cnn_launches;
+    CKC(cudaGetLastError());
+    return ADMM_OK;
 }
 }  // namespace admm

@@ -38,7 +38,9 @@ using namespace admm;
 namespace admm {
 // the learned warm start of admm_warmstart_load (cnn.cu)
 bool ws_loaded();
-int ws_predict_start(int H, int W, const float* ybar, const uint8_t* mask, float* x0, float* d0, cudaStream_t s);
+int ws_batch_limit(int H, int W);
+int ws_predict_starts(int count, int H, int W, const float* const* ybar, const uint8_t* const* mask,
+                      float* const* x0, float* const* d0, cudaStream_t s);
 // the driver's tensor-map encoder (cnn.cu)
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encode_fn();
 
@@ -1156,6 +1158,7 @@ static int solve_all_impl(DeviceCtx* ctx, const std::vector<std::vector<int>>& c
         g.qbase = qbase;
         g.gi = (int)groups.size();
         const size_t n = (size_t)g.H * g.W;
+        std::vector<admm_plan_s*> ws_pend;            // this class's problems that take the learned start
         for (int j : idx) {
             admm_plan_s* pl = plans[j];
             const float* yj = y[j];
@@ -1173,22 +1176,11 @@ static int solve_all_impl(DeviceCtx* ctx, const std::vector<std::vector<int>>& c
                                              pl->p.psf_h / 2, pl->p.psf_w / 2, pl->p.raw_mask};
             prep_maxn = std::max(prep_maxn, (int)n);
             if (use_ws && pl->warm_mode == 0 && pl->p.reg == ADMM_REG_TV) {
-                int rp = flush_prep();
-                if (rp != ADMM_OK) return rp;
-                // learned start: the network reads [M^T y, mask] just prepared and
-                // writes x0 (to the staging plane) and d0 = (d1, d2 buffer 0),
-                // contiguous in the plan's slab; u0 = H x0 - d0 as in
-                // admm_deconv_warm_start
+                // learned start, run for the class's problems together below
                 // (d2 follows d1 directly: H W floats are a multiple of the slab's 256-byte alignment)
                 if (pl->d2 != pl->d1 + n) return ADMM_ECUDA;
-                int r = ws_predict_start(g.H, g.W, pl->ybar, pl->mask, pl->xstage, pl->d1, s);
-                if (r != ADMM_OK) return r;
-                if (pl->gen)
-                    CK(launch_gen_warm_rows(g.W, g.H, pl->Wp, pl->xstage, pl->Sb, g.twW, s));
-                else
-                    CK(launch_warm_rows(g.W, pl->xstage, pl->Sb, g.H, pl->Wp, ctx->tw, s));
-                ++g_launches;
                 pl->warm_mode = 1;
+                ws_pend.push_back(pl);
             }
             const int t = (int)order.size();
             ctx->h_desc[t] = make_desc(pl);
@@ -1197,6 +1189,48 @@ static int solve_all_impl(DeviceCtx* ctx, const std::vector<std::vector<int>>& c
             ctx->h_xptr[t] = x_host.back() ? pl->xstage : x_out[j];
             order.push_back(j);
             g.max_iters = std::max(g.max_iters, pl->p.max_iters);
+        }
+        if (!ws_pend.empty()) {
+            // the network reads each problem's [M^T y, mask] once prepared and
+            // writes x0 (to the staging plane) and d0 = (d1, d2 buffer 0),
+            // contiguous in the plan's slab, for up to ws_batch_limit problems
+            // per pass; then u0 = H x0 - d0 as in admm_deconv_warm_start
+            auto learned = [&]() -> int {
+                int r = flush_prep();
+                if (r != ADMM_OK) return r;
+                const int lim = ws_batch_limit(g.H, g.W);
+                std::vector<const float*> yb;
+                std::vector<const uint8_t*> mk;
+                std::vector<float*> x0, d0;
+                for (size_t a = 0; a < ws_pend.size(); a += lim) {
+                    const size_t e = std::min(ws_pend.size(), a + (size_t)lim);
+                    yb.clear();
+                    mk.clear();
+                    x0.clear();
+                    d0.clear();
+                    for (size_t k = a; k < e; ++k) {
+                        yb.push_back(ws_pend[k]->ybar);
+                        mk.push_back(ws_pend[k]->mask);
+                        x0.push_back(ws_pend[k]->xstage);
+                        d0.push_back(ws_pend[k]->d1);
+                    }
+                    r = ws_predict_starts((int)(e - a), g.H, g.W, yb.data(), mk.data(), x0.data(), d0.data(), s);
+                    if (r != ADMM_OK) return r;
+                }
+                for (admm_plan_s* pl : ws_pend) {
+                    if (pl->gen)
+                        CK(launch_gen_warm_rows(g.W, g.H, pl->Wp, pl->xstage, pl->Sb, g.twW, s));
+                    else
+                        CK(launch_warm_rows(g.W, pl->xstage, pl->Sb, g.H, pl->Wp, ctx->tw, s));
+                    ++g_launches;
+                }
+                return ADMM_OK;
+            };
+            const int r = learned();
+            if (r != ADMM_OK) {
+                for (admm_plan_s* pl : ws_pend) pl->warm_mode = 0;
+                return r;
+            }
         }
         g.nslots = choose_slots(g.H, g.W, g.tv, g.R, g.slot_ctas, g.count);
         // with per-phase timing on, one lane: every launch covers all slots,

@@ -35,7 +35,7 @@ import time
 
 import numpy as np
 
-from . import Cnn, Plan, admm_deconv_get_state, solve_batch
+from . import Cnn, Plan, admm_deconv_get_state, admm_warmstart_load, solve_batch
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 if ROOT not in sys.path:
@@ -244,7 +244,7 @@ def export_binary(params, scales, path=WEIGHTS_BIN):
 # --------------------------------------------------------------------------
 # evaluation: cold vs warm start to the same stop rule
 # --------------------------------------------------------------------------
-def evaluate(params, scales, count=64, size=512, seed=0, check_every=1, probs=None):
+def evaluate(params, scales, count=64, size=512, seed=0, check_every=1, probs=None, api_weights=None):
     import torch
     if probs is None:
         probs = generate("eval", range(20_000_000 + seed, 20_000_000 + seed + count), size)
@@ -283,6 +283,24 @@ def evaluate(params, scales, count=64, size=512, seed=0, check_every=1, probs=No
     rw = solve_batch(plans, ys, ms, xw)
     e[3].record()
     torch.cuda.synchronize()
+    api = None
+    if api_weights is not None:
+        # the same warm start through the library's own path: the weights file
+        # loaded by admm_warmstart_load, the network run inside solve_batch
+        xa = [torch.empty((H, W), dtype=torch.float32, device="cuda") for _ in probs]
+        admm_warmstart_load(api_weights)
+        try:
+            solve_batch(plans, ys, ms, xa, use_warmstart=True)   # warm-up (the network's buffers)
+            ea = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            ea[0].record()
+            ra = solve_batch(plans, ys, ms, xa, use_warmstart=True)
+            ea[1].record()
+            torch.cuda.synchronize()
+        finally:
+            admm_warmstart_load(None)
+        api = {"images_per_s": count / (ea[0].elapsed_time(ea[1]) * 1e-3),
+               "iters_mean": float(np.mean([r.iters for r in ra])),
+               "x_equal_to_manual_start": all(bool(torch.equal(a, b)) for a, b in zip(xa, xw))}
     # prediction error against the cold solution, relative L2 per field
     xs = torch.stack(xc)
 
@@ -314,6 +332,7 @@ def evaluate(params, scales, count=64, size=512, seed=0, check_every=1, probs=No
         "cold_isnr_db": float(dis[:, 0].mean()), "warm_isnr_db": float(dis[:, 1].mean()),
         "isnr_diff_db_max_abs": float(np.abs(dis[:, 1] - dis[:, 0]).max()),
         "prediction_rel_err": pred_err,
+        **({"api_warm": api} if api is not None else {}),
     }
 
 
