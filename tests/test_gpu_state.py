@@ -253,6 +253,54 @@ def test_use_warmstart_equals_the_manual_learned_start(ad):
         ad.admm_warmstart_load(None)
 
 
+def test_use_warmstart_groups_match_one_image_passes(ad):
+    """18 problems of 128 x 256 take the learned start in two passes of the
+    network (16 + 2 images, per-image pointer tables); after 25 iterations
+    each x has the bits of a solve started from a one-image prediction and
+    admm_deconv_warm_start."""
+    import torch
+    from paper_1210_2687_gb300 import warmstart as ws
+    params, scales, _ = ws.load()
+    H, W = 128, 256
+    lam = ws.LAM
+    mu1, mu2 = S.default_mu(lam)
+    rng = np.random.default_rng(5)
+    count = 18
+    psfs = [S.psf_box(5), S.psf_gaussian(7, 1.2), S.psf_box(3)]
+    probs = []
+    for i in range(count):
+        y = rng.uniform(0.0, 1.0, size=(H, W)).astype(np.float32)
+        m = (rng.uniform(size=(H, W)) > 0.3).astype(np.uint8)
+        probs.append((y, m, psfs[i % 3]))
+    ad.admm_warmstart_load(ws.WEIGHTS_BIN)
+    try:
+        plans = [ad.Plan(H, W, p[2], lam, mu1, mu2, "tv", stop="iters", max_iters=25) for p in probs]
+        ys = [torch.from_numpy(p[0]).cuda() for p in probs]
+        ms = [torch.from_numpy(p[1]).cuda() for p in probs]
+        xs = [torch.empty((H, W), dtype=torch.float32, device="cuda") for _ in probs]
+        res = ad.solve_batch(plans, ys, ms, xs, use_warmstart=True)
+        assert all(r.iters == 25 for r in res)
+        net = ad.Cnn(H * W)
+        net.set_params(params)
+        x0 = torch.empty((1, H, W), dtype=torch.float32, device="cuda")
+        d0 = torch.empty((1, 3 * H * W), dtype=torch.float32, device="cuda")
+        for i, pl in enumerate(plans):
+            vm = S.valid_mask(H, W, *probs[i][2].shape).astype(bool) & (probs[i][1] != 0)
+            yb = torch.from_numpy(np.where(vm, probs[i][0], 0).astype(np.float32)).cuda()[None]
+            mk = torch.from_numpy(vm.astype(np.uint8)).cuda()[None]
+            net.predict_start(yb, mk, scales, x0, d0)
+            pl.warm_start(x0[0], d0[0])
+            xm = torch.empty((H, W), dtype=torch.float32, device="cuda")
+            ad.solve(pl, ys[i], ms[i], xm)
+            torch.cuda.synchronize()
+            assert torch.equal(xm, xs[i]), i
+        net.close()
+        for pl in plans:
+            pl.close()
+    finally:
+        ad.admm_warmstart_load(None)
+
+
 def test_bounded_wait_runs_out_and_the_device_stays_usable(ad):
     """The row phase's wait for its spectrum rows is bounded (about a second):
     with one copy withheld the problem retires after its first iteration with
