@@ -567,9 +567,10 @@ def cg_secondary(ad, torch, stream, batch=64):
 
 CNN_FLOP_PER_PX = 2 * 9 * (2 * 32 + 6 * 32 * 32 + 32 * 4)   # eight 3x3 convolutions
 # HBM bytes per pixel of one forward: the input kernel (M^T y 4 + mask 1 in,
-# 16 BF16 channels out 32), layer 0 (32 in, 64 out), six 32-channel layers
-# (64 in, 64 out each), the last layer (64 in, 4 FP32 channels out 16)
-CNN_BYTES_PER_PX = (4 + 1 + 32) + (32 + 64) + 6 * (64 + 64) + (64 + 16)
+# one plane of 8 BF16 channels out 16), layer 0 (16 in, 64 out), six
+# 32-channel layers (64 in, 64 out each), the last layer (64 in, 4 FP32
+# channels out 16)
+CNN_BYTES_PER_PX = (4 + 1 + 16) + (16 + 64) + 6 * (64 + 64) + (64 + 16)
 
 
 def warm_secondary(ad, torch, stream, count=32):

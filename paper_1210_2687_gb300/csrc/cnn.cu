@@ -4,7 +4,8 @@
 // what lets a predicted start feed Algorithm 2.
 //
 // Layout. Activations and their gradients are BF16 in planes of eight
-// channels: [image][C / 8][H][W][8], C padded to 16 or 32. One plane row is
+// channels: [image][C / 8][H][W][8], C padded to 8 (the network's input),
+// 16 or 32. One plane row is
 // W x 16 contiguous bytes, so a halo tile of a plane is a few long row
 // segments (one TMA box of 160-byte rows for the tensor-core layers), and a
 // pixel's eight channels are the 16-byte K slice the MMAs consume. The
@@ -55,7 +56,8 @@ constexpr int kTile = 16;
 __host__ __device__ constexpr int layer_cin(int l) { return l == 0 ? kIn : kWidth; }
 __host__ __device__ constexpr int layer_cout(int l) { return l == kLayers - 1 ? kOut : kWidth; }
 constexpr int pad16(int c) { return c <= 16 ? 16 : 32; }
-constexpr int layer_cinp(int l) { return pad16(layer_cin(l)); }
+// the first layer's 2 input channels fill one plane of eight
+constexpr int layer_cinp(int l) { return l == 0 ? 8 : pad16(layer_cin(l)); }
 constexpr int layer_coutp(int l) { return l == kLayers - 1 ? 16 : kWidth; }
 
 long long param_offset(int l) {
@@ -102,19 +104,16 @@ __device__ __forceinline__ void cp_async_wait_all() {
 }
 
 // ---------------------------------------------------------------------------
-// network input: [M^T y, mask] in channels 0 and 1 of a 16-channel tensor
-// (two planes of eight channels; hw = H W)
+// network input: [M^T y, mask] in channels 0 and 1 of one plane of eight
 // ---------------------------------------------------------------------------
 __global__ void cnn_input_kernel(const float* __restrict__ ybar, const uint8_t* __restrict__ mask,
-                                 bf16* __restrict__ a0, long long npx, long long hw) {
+                                 bf16* __restrict__ a0, long long npx) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= npx) return;
     const bool obs = mask[i] != 0;
     const float y = obs ? ybar[i] : 0.f;
-    const long long img = i / hw, px = i - img * hw;
-    uint4* dst = reinterpret_cast<uint4*>(a0 + (img * 2 * hw + px) * 8);
-    dst[0] = make_uint4(pack2(__float2bfloat16(y), __float2bfloat16(obs ? 1.f : 0.f)), 0u, 0u, 0u);
-    dst[hw] = make_uint4(0u, 0u, 0u, 0u);
+    reinterpret_cast<uint4*>(a0)[i] =
+        make_uint4(pack2(__float2bfloat16(y), __float2bfloat16(obs ? 1.f : 0.f)), 0u, 0u, 0u);
 }
 
 enum { kModeReluBf16 = 0, kModeOutF32 = 1, kModeGateBf16 = 2 };   // epilogues of conv3x3_tc
@@ -246,20 +245,31 @@ template <int CIN, int MODE>
 __global__ void __launch_bounds__(128)
 conv3x3_tc(const __grid_constant__ CUtensorMap tin, const bf16* __restrict__ wpk, const float* __restrict__ bias,
            void* __restrict__ out, const bf16* __restrict__ gate, int H, int W, int count, int* __restrict__ err) {
-    constexpr int COUT = MODE == kModeOutF32 ? 16 : 32, CH = CIN / 8, ABYTES = CH * kTcNP * 16;
+    constexpr int COUT = MODE == kModeOutF32 ? 16 : 32, CH = CIN / 8;
+    constexpr int BOXBYTES = CH * kTcNP * 16;                  // one halo box
+    constexpr int ABYTES = (BOXBYTES + 127) / 128 * 128;        // (each halo buffer on a 128-byte boundary)
     constexpr uint32_t kTmemCols = 2 * COUT;   // two accumulators
-    static_assert(CIN == 16 || CIN == 32, "input channels");
+    // weight slots: the 9 taps, or with one plane of input channels (CIN = 8)
+    // taps 0..7, a zero slot and tap 8, so that the MMAs take the taps in
+    // pairs (0,1) (2,3) (4,5) (6,7) (zero,8), one per K = 16
+    constexpr int NSLOT = CIN == 8 ? 10 : 9;
+    static_assert(CIN == 8 || CIN == 16 || CIN == 32, "input channels");
     __shared__ __align__(128) unsigned char smA[2][ABYTES];
-    __shared__ __align__(128) unsigned char smW[9 * CH * COUT * 16];
+    __shared__ __align__(128) unsigned char smW[NSLOT * CH * COUT * 16];
     __shared__ float smB[32];
     // 0, 1: halo of buffer 0 / 1 landed; 2, 3: MMAs into accumulator 0 / 1 done
     __shared__ __align__(8) unsigned long long bars[4];
     __shared__ uint32_t tmem_base;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    for (int e = tid; e < 9 * COUT * CH; e += 128) {
-        const int tc = e / CH, k = e - tc * CH;       // tc = tap * 32 + output channel
-        const int tap = tc / COUT, co = tc - tap * COUT;
-        cp_async16(smW + ((tap * CH + k) * COUT + co) * 16, wpk + (size_t)tc * CIN + k * 8);
+    for (int e = tid; e < NSLOT * COUT * CH; e += 128) {
+        const int sc = e / CH, k = e - sc * CH;       // sc = slot * COUT + output channel
+        const int slot = sc / COUT, co = sc - slot * COUT;
+        const int tap = CIN == 8 ? (slot < 8 ? slot : (slot == 9 ? 8 : -1)) : slot;
+        unsigned char* dst = smW + ((slot * CH + k) * COUT + co) * 16;
+        if (tap >= 0)
+            cp_async16(dst, wpk + ((size_t)tap * COUT + co) * CIN + k * 8);
+        else
+            *reinterpret_cast<uint4*>(dst) = make_uint4(0u, 0u, 0u, 0u);
     }
     if ((MODE == kModeReluBf16 && tid < COUT) || (MODE == kModeOutF32 && tid < kOut)) smB[tid] = bias[tid];
     if (warp == 0) {
@@ -279,7 +289,7 @@ conv3x3_tc(const __grid_constant__ CUtensorMap tin, const bf16* __restrict__ wpk
         const int img = t / per_img, rem = t - img * per_img;
         const int y0 = (rem / tiles_x) * kTcTH, x0 = (rem % tiles_x) * kTcTW;
         const uint32_t bar = sh_addr(&bars[b]);
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(ABYTES) : "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(BOXBYTES) : "memory");
         // x: element (column x0 - 1, channel 0) of the merged row, a multiple of 8
         // elements (16 B); column -1 and columns past W - 1 read as zero
         asm volatile(
@@ -312,14 +322,29 @@ conv3x3_tc(const __grid_constant__ CUtensorMap tin, const bf16* __restrict__ wpk
         pend_h &= ~(1u << b);
         tc_fence_after();
         const uint32_t aBase = sh_addr(smA[b]), d = tmem + (uint32_t)COUT * b;
+        if constexpr (CIN == 8) {
+            // K chunk 0 of pair j is tap a (or the zero slot), chunk 1 tap b: the
+            // A descriptor starts at tap a's halo pixel and steps to tap b's by
+            // its K-chunk offset (halo pixel of a tap (dy, dx): 10 dy + dx)
+            constexpr int pa[5] = {0, 2, 11, 20, 21};   // chunk 0: taps 0, 2, 4, 6; any pixel for the zero slot
+            constexpr int pd[5] = {1, 8, 1, 1, 1};      // chunk 1: taps 1, 3, 5, 7, 8
 #pragma unroll
-        for (int tap = 0; tap < 9; ++tap) {
-            const int dy = tap / 3, dx = tap - 3 * (tap / 3);
+            for (int j = 0; j < 5; ++j) {
+                const uint64_t a = umma_desc(aBase + pa[j] * 16, pd[j] * 16, kTcHW * 16);
+                const uint64_t bd = umma_desc(wBase + 2 * j * COUT * 16, COUT * 16, 8 * 16);
+                umma_f16(d, a, bd, idesc_m128(COUT), j != 0 ? 1u : 0u);
+            }
+        } else {
 #pragma unroll
-            for (int j = 0; j < CH / 2; ++j) {
-                const uint64_t a = umma_desc(aBase + (2 * j * kTcNP + dy * kTcHW + dx) * 16, kTcNP * 16, kTcHW * 16);
-                const uint64_t bd = umma_desc(wBase + (tap * CH + 2 * j) * COUT * 16, COUT * 16, 8 * 16);
-                umma_f16(d, a, bd, idesc_m128(COUT), (tap | j) != 0 ? 1u : 0u);
+            for (int tap = 0; tap < 9; ++tap) {
+                const int dy = tap / 3, dx = tap - 3 * (tap / 3);
+#pragma unroll
+                for (int j = 0; j < CH / 2; ++j) {
+                    const uint64_t a =
+                        umma_desc(aBase + (2 * j * kTcNP + dy * kTcHW + dx) * 16, kTcNP * 16, kTcHW * 16);
+                    const uint64_t bd = umma_desc(wBase + (tap * CH + 2 * j) * COUT * 16, COUT * 16, 8 * 16);
+                    umma_f16(d, a, bd, idesc_m128(COUT), (tap | j) != 0 ? 1u : 0u);
+                }
             }
         }
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -628,9 +653,8 @@ __global__ void cnn_input_ptrs_kernel(ImgPtrs P, bf16* __restrict__ a0, long lon
     const int img = blockIdx.y;
     const bool obs = P.m[img][px] != 0;
     const float y = obs ? P.y[img][px] : 0.f;
-    uint4* dst = reinterpret_cast<uint4*>(a0 + ((long long)img * 2 * hw + px) * 8);
-    dst[0] = make_uint4(pack2(__float2bfloat16(y), __float2bfloat16(obs ? 1.f : 0.f)), 0u, 0u, 0u);
-    dst[hw] = make_uint4(0u, 0u, 0u, 0u);
+    reinterpret_cast<uint4*>(a0)[(long long)img * hw + px] =
+        make_uint4(pack2(__float2bfloat16(y), __float2bfloat16(obs ? 1.f : 0.f)), 0u, 0u, 0u);
 }
 
 // grid (ceil(hw / 256), images)
@@ -736,7 +760,7 @@ struct admm_cnn_s {
     long long adam_t = 0;
     bf16* wf[kLayers] = {};        // packed forward weights
     bf16* wb[kLayers] = {};        // packed input-gradient weights (layers 1..)
-    bf16* a0 = nullptr;            // input, 16 channels
+    bf16* a0 = nullptr;            // input, one plane of 8 channels
     bf16* act[kLayers - 1] = {};   // activations after layers 0..6 (training keeps all)
     float* out = nullptr;          // output, 4 channels FP32
     bf16* gbuf[2] = {};            // gradient ping-pong, 32 channels
@@ -793,7 +817,7 @@ int run_layers(admm_cnn_s* n, int count, int H, int W, bool keep, cudaStream_t s
         } else {
             bf16* dst = keep ? n->act[l] : n->act[l & 1];
             if (l == 0)
-                CKC((conv_tc<16, kModeReluBf16>(cur, n->wf[l], b, dst, nullptr, count, H, W, n->sms, n->tc_err, s)));
+                CKC((conv_tc<8, kModeReluBf16>(cur, n->wf[l], b, dst, nullptr, count, H, W, n->sms, n->tc_err, s)));
             else
                 CKC((conv_tc<32, kModeReluBf16>(cur, n->wf[l], b, dst, nullptr, count, H, W, n->sms, n->tc_err, s)));
             cur = dst;
@@ -806,7 +830,7 @@ int run_layers(admm_cnn_s* n, int count, int H, int W, bool keep, cudaStream_t s
 int forward(admm_cnn_s* n, int count, int H, int W, const float* ybar, const uint8_t* mask, bool keep,
             cudaStream_t s) {
     const long long npx = (long long)count * H * W;
-    cnn_input_kernel<<<(unsigned)((npx + 255) / 256), 256, 0, s>>>(ybar, mask, n->a0, npx, (long long)H * W);
+    cnn_input_kernel<<<(unsigned)((npx + 255) / 256), 256, 0, s>>>(ybar, mask, n->a0, npx);
     ++g_cnn_launches;
     CKC(cudaGetLastError());
     return run_layers(n, count, H, W, keep, s);
@@ -830,7 +854,7 @@ int backward(admm_cnn_s* n, int count, int H, int W, const float* target, const 
         if (l == kLayers - 1)
             CKC((wgrad<32, 16>(a_in, g, dw, db, kWidth, kOut, count, H, W, n->sms, s)));
         else if (l == 0)
-            CKC((wgrad<16, 32>(a_in, g, dw, db, kIn, kWidth, count, H, W, n->sms, s)));
+            CKC((wgrad<8, 32>(a_in, g, dw, db, kIn, kWidth, count, H, W, n->sms, s)));
         else
             CKC((wgrad<32, 32>(a_in, g, dw, db, kWidth, kWidth, count, H, W, n->sms, s)));
         if (l == 0) break;
@@ -879,7 +903,7 @@ int admm_cnn_create(admm_cnn_t* out, long long max_pixels, int training) {
     n->training = training != 0;
     const long long P = param_count();
     const size_t px = (size_t)max_pixels;
-    if ((rc = dalloc(n, &n->params, P)) || (rc = dalloc(n, &n->a0, px * 16)) || (rc = dalloc(n, &n->out, px * 4)) ||
+    if ((rc = dalloc(n, &n->params, P)) || (rc = dalloc(n, &n->a0, px * 8)) || (rc = dalloc(n, &n->out, px * 4)) ||
         (rc = dalloc(n, &n->tc_err, 1)))
         return bail(rc);
     for (int l = 0; l < kLayers; ++l) {
