@@ -840,21 +840,24 @@ row_phase_tv(const ProbDesc* __restrict__ probs, SlotTable sl, int H, int Wp, co
 
     // (0) requests: the walk's rows go to L2 in bulk (they are consumed after
     // the inverse transforms), the half spectra of rows r0-1 .. r0+R into
-    // shared memory, then the first D walk rows into the ring. Each transform
-    // group copies the rows it will transform itself, one cp.async group per
-    // round of transforms, so that a round starts as soon as its own rows
-    // have landed while later rounds are still arriving.
-    if (tid == 0) {
-        const int qh = (r0 - 1 + H) & (H - 1);
-        if (!cold) {
-            prefetch_l2(d2in + (size_t)qh * W, W * sizeof(float2));
-            for (int i = 0; i < R; ++i) {
-                prefetch_l2(d2in + (size_t)(r0 + i) * W, W * sizeof(float2));
-                prefetch_l2(P.d1 + (size_t)(r0 + i) * W, W * sizeof(float));
-                if (chk && !first) prefetch_l2(P.xprev + (size_t)(r0 + i) * W, W * sizeof(float));
+    // shared memory, then the first D walk rows into the ring. The L2
+    // prefetches are spread over lane 0 of the warps after the first, whose
+    // thread 0 issues the spectrum rows' bulk copies (the first transforms
+    // wait for those) without queueing behind them.
+    {
+        constexpr int NPF = C::NWARP > 1 ? C::NWARP - 1 : 1;   // prefetching warps
+        const int pw = C::NWARP > 1 ? wid - 1 : 0;
+        if (lane == 0 && pw >= 0) {
+            if (!cold && pw == 0) prefetch_l2(d2in + (size_t)((r0 - 1 + H) & (H - 1)) * W, W * sizeof(float2));
+            for (int i = pw; i < R; i += NPF) {
+                if (!cold) {
+                    prefetch_l2(d2in + (size_t)(r0 + i) * W, W * sizeof(float2));
+                    prefetch_l2(P.d1 + (size_t)(r0 + i) * W, W * sizeof(float));
+                    if (chk && !first) prefetch_l2(P.xprev + (size_t)(r0 + i) * W, W * sizeof(float));
+                }
+                prefetch_l2(P.ybar + (size_t)(r0 + i) * W, W * sizeof(float));
             }
         }
-        for (int i = 0; i < R; ++i) prefetch_l2(P.ybar + (size_t)(r0 + i) * W, W * sizeof(float));
     }
     const int g = tid / C::FT, t = tid % C::FT;
     constexpr int NR = C::NR;
