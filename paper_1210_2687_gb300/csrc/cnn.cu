@@ -132,13 +132,17 @@ enum { kModeReluBf16 = 0, kModeOutF32 = 1, kModeGateBf16 = 2 };   // epilogues o
 //      groups (one tile row each) are 10 pixels = 160 B apart and its K
 //      chunks 180 x 16 B apart, so no im2col copy is needed;
 //   B: the weights as [tap][CIN/8][COUT output channels][8].
+// With one plane of input channels (CIN = 8, the first layer) the taps go in
+// pairs, one per K = 16 MMA: the A descriptor's K-chunk offset is then the
+// pixel distance from the pair's first tap to its second (5 MMAs per tile,
+// the ninth tap paired with a zero weight slot).
 // The halo tile arrives by one TMA copy (cp.async.bulk.tensor, a 4-D view of
 // the eight-channel planes whose innermost dimension merges a plane row's
 // columns and channels, so each box row is 10 pixels x 16 B = 160 contiguous
 // bytes and the box lands in shared memory already in the A layout; rows and
 // columns outside the image read as zero), double-buffered. One thread issues
-// the 9 x CIN/16 MMAs of a tile (K = 16 each) and commits them to an
-// mbarrier; the four warps wait (bounded), read their 32 lanes of the
+// the 9 x CIN/16 MMAs of a tile (K = 16 each; 5 for CIN = 8) and commits them
+// to an mbarrier; the four warps wait (bounded), read their 32 lanes of the
 // accumulator (tcgen05.ld) and apply bias + ReLU (forward) or the ReLU gate of
 // the layer below (input gradient), storing four BF16 planes, or bias alone
 // into the network's FP32 output (last layer).
